@@ -1,0 +1,172 @@
+/*
+ * sap.h — C ABI of libsap, a GB300-native (sm_103a) dense-banded
+ * split-and-parallelize (SaP) solver: banded LU/UL block factorisation
+ * without pivoting (boosted pivots), SaP-D / SaP-C preconditioning and an
+ * outer BiCGStab(2), in FP64 or with an FP32 preconditioner (FP64 Krylov).
+ *
+ * Method: Li, Serban, Negrut, "Analysis of a splitting approach for the
+ * parallel solution of linear systems on GPU cards", Sections 2.1-2.2
+ * (method), 3.1 (storage, partition, LU/UL, mixed precision).
+ *
+ * Conventions shared by every entry point
+ *   Band storage (Sec. 3.1 "Matrix storage"): the N x N matrix A with
+ *     half-bandwidth K is an N x (2K+1) array in column-major order with the
+ *     diagonal in column K, i.e. a_ij = band[(K + i - j) * N + j], 0-based,
+ *     float64.  Slots whose row index i = j + c - K lies outside [0, N) are
+ *     padding: never read, written as 0 where the library writes a band.
+ *   Pointers named *_dev are device pointers on the current CUDA device;
+ *     pointers named *_host are host pointers.  Vectors are float64, length N.
+ *   Streams: every call is ordered on the given stream (0 = legacy default).
+ *     Calls that return solver status synchronise that stream before they
+ *     return; the others are asynchronous.
+ *   Errors: no call throws or aborts; each returns a sap_status_t.  On an
+ *     error the output buffers hold unspecified values and the handle stays
+ *     usable unless the status is SAP_ERR_CUDA.
+ *   Threading: a handle must not be used from two host threads at once.
+ */
+#ifndef SAP_H
+#define SAP_H
+
+#include <stdint.h>
+#include <cuda_runtime_api.h>
+
+#if defined(__GNUC__)
+#define SAP_API __attribute__((visibility("default")))
+#else
+#define SAP_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sap_handle *sap_handle_t;
+
+typedef enum {
+    SAP_OK = 0,
+    SAP_ERR_INVALID_ARG = 1,   /* bad size or option, see each call */
+    SAP_ERR_OOM = 2,           /* device allocation failed */
+    SAP_ERR_NOT_CONVERGED = 3, /* iteration cap reached; x holds the last iterate */
+    SAP_ERR_BREAKDOWN = 4,     /* BiCGStab(2) scalar rho, gamma, sigma or omega became 0 */
+    SAP_ERR_TIMEOUT = 5,       /* a device-side wait hit its spin limit */
+    SAP_ERR_CUDA = 6,          /* a CUDA runtime call failed */
+    SAP_ERR_NOT_IMPLEMENTED = 7,
+    SAP_ERR_SINGULAR = 8       /* an exactly singular reduced matrix Rbar_i */
+} sap_status_t;
+
+typedef enum { SAP_D = 0, SAP_C = 1 } sap_variant_t;          /* Sec. 2.1.1 */
+typedef enum { SAP_FP64 = 0, SAP_FP32 = 1 } sap_precision_t;  /* Sec. 3.1 mixed precision */
+
+typedef struct {
+    int32_t P;            /* number of diagonal blocks, 1 <= P <= N (Sec. 3.1) */
+    int32_t variant;      /* sap_variant_t */
+    int32_t precision;    /* sap_precision_t: precision of factors, tips and sweeps;
+                             the Krylov vectors, SpMV, dot products, the true
+                             residual and the reduced systems Rbar_i are FP64 */
+    int32_t max_iters;    /* BiCGStab(2) iteration cap (default 500 if <= 0) */
+    double tol;           /* target ||b - A x||_2 / ||b||_2 (default 1e-10 if <= 0) */
+    double boost_eps;     /* relative pivot-boost threshold (Sec. 2.2): a pivot with
+                             |p| < boost_eps * max|a_ij| becomes sign(p) times that
+                             value; <= 0 selects the unit roundoff of `precision` */
+    int64_t spin_limit;   /* reserved for device-side waits (0 = default) */
+} sap_options_t;
+
+typedef struct {
+    double iters;         /* BiCGStab(2) iterations in quarters (Sec. 4.1.1) */
+    double relres;        /* final true ||b - A x||_2 / ||b||_2 (FP64) */
+    int64_t n_boosted;    /* boosted pivots in all LU and UL factorisations */
+    int64_t n_matvec;     /* preconditioned matvecs M^{-1} A v performed */
+    int64_t n_restarts;   /* residual replacements after a failed true-residual check */
+    float t_factor_ms;    /* device time of the factorisation (LU, BC, SPK, LUrdcd) */
+    float t_solve_ms;     /* device time of the Krylov phase of the last solve */
+} sap_info_t;
+
+/* Defaults as documented above. */
+SAP_API void sap_default_options(sap_options_t *opt);
+
+/* Factor the SaP preconditioner of A (Sec. 2.1, 3.1): partition into P
+ * blocks, LU of every block A_i; for SaP-C also the UL of every block, the
+ * coupling blocks B_i, C_{i+1}, the spike tips V^(b)_i, W^(t)_{i+1}
+ * (Eq. (2.2) via the bottom LU / top UL blocks) and the reduced matrices
+ * Rbar_i = I - W^(t)_{i+1} V^(b)_i factored by partial pivoting (Eq. (2.5a)).
+ *   band_dev: device band of A (borrowed: it must stay allocated and
+ *             unchanged until sap_destroy, the SpMV reads it).
+ *   N >= 2, 1 <= K < N.  SaP-C needs every block to have >= 2K rows.
+ *   *out receives a new handle owning all other device memory.
+ * Errors: INVALID_ARG (sizes, options, N_i < 2K for SaP-C), NOT_IMPLEMENTED
+ * (K above sap_max_K, or above the SaP-C spike limit: 98 in FP64, 120 in
+ * FP32), OOM, SINGULAR, CUDA.  Synchronises `stream`. */
+SAP_API sap_status_t sap_factor(const double *band_dev, int64_t N, int32_t K,
+                        const sap_options_t *opt, cudaStream_t stream,
+                        sap_handle_t *out);
+
+/* Solve A x = b by left-preconditioned BiCGStab(2) (Sec. 2.1.1) from
+ * x0 = 0 to the handle's tolerance.  b_dev, x_dev: device, length N, must
+ * not alias.  info may be NULL.  Synchronises `stream`. */
+SAP_API sap_status_t sap_solve(sap_handle_t h, const double *b_dev, double *x_dev,
+                       sap_info_t *info, cudaStream_t stream);
+
+/* Solve A^T lambda = gbar with the same machinery on A^T: SpMV with A^T and
+ * SaP on A^T built from the stored factors transposed (A_i^T = U_i^T L_i^T;
+ * couplings B'_i = C_{i+1}^T, C'_{i+1} = B_i^T; its own reduced matrices,
+ * built on the first call).  Synchronises `stream`. */
+SAP_API sap_status_t sap_solve_adjoint(sap_handle_t h, const double *gbar_dev, double *lambda_dev,
+                               sap_info_t *info, cudaStream_t stream);
+
+/* grad_band = -lambda x^T restricted to the band (the gradient of a scalar
+ * loss l(x), x = A^{-1} b, with respect to the band entries, given
+ * lambda = A^{-T} dl/dx); padding slots are written as 0.  grad_band_dev has
+ * (2K+1) N float64.  Asynchronous. */
+SAP_API sap_status_t sap_grad_band(sap_handle_t h, const double *lambda_dev, const double *x_dev,
+                           double *grad_band_dev, cudaStream_t stream);
+
+/* One preconditioner application z = M^{-1} r (transpose = 0) or the SaP
+ * preconditioner of A^T (transpose = 1): SaP-D Eq. (2.3), SaP-C Eq. (2.5)
+ * plus purification (Sec. 2.1).  Asynchronous. */
+SAP_API sap_status_t sap_apply_preconditioner(sap_handle_t h, const double *r_dev, double *z_dev,
+                                      int32_t transpose, cudaStream_t stream);
+
+/* y = A x (transpose = 0) or y = A^T x (transpose = 1) on the band, FP64.
+ * Stateless; x and y must not alias.  Asynchronous. */
+SAP_API sap_status_t sap_spmv(const double *band_dev, int64_t N, int32_t K, const double *x_dev,
+                      double *y_dev, int32_t transpose, cudaStream_t stream);
+
+/* Solve with host buffers: copies b_host to the device, runs sap_solve and
+ * copies x back into x_host (host <-> device copies included). */
+SAP_API sap_status_t sap_solve_host(sap_handle_t h, const double *b_host, double *x_host,
+                            sap_info_t *info, cudaStream_t stream);
+
+/* Inspection of the factorisation, for tests.  Copies into host buffers.
+ *   sap_get_partition: off_host[P+1] block offsets.
+ *   sap_get_block_lu:  LU of block i as a dense-band row-major n_i x (2K+1)
+ *     float64 array f[r*(2K+1) + (c - r + K)] (unit L below, U on/above).
+ *   sap_get_interface: K x K row-major float64 matrix of interface i
+ *     (0 <= i < P-1): which 0 = B_i, 1 = C_{i+1}, 2 = V^(b)_i,
+ *     3 = W^(t)_{i+1}, 4 = Rbar_i before factoring; adjoint = 1 gives the
+ *     matrices of the SaP preconditioner of A^T (built on demand).
+ * Synchronise `stream`. */
+SAP_API sap_status_t sap_get_partition(sap_handle_t h, int64_t *off_host);
+SAP_API sap_status_t sap_get_block_lu(sap_handle_t h, int32_t i, double *f_host, cudaStream_t stream);
+SAP_API sap_status_t sap_get_interface(sap_handle_t h, int32_t i, int32_t which, int32_t adjoint,
+                               double *m_host, cudaStream_t stream);
+
+/* Number of boosted pivots so far (LU and UL). */
+SAP_API int64_t sap_n_boosted(sap_handle_t h);
+
+/* Release the handle and its device memory (synchronises the device). */
+SAP_API sap_status_t sap_destroy(sap_handle_t h);
+
+/* Static description of a status code. */
+SAP_API const char *sap_status_string(sap_status_t s);
+
+/* Number of CUDA kernels this library has launched in this process so far
+ * (host-side counter, all handles and threads). */
+SAP_API int64_t sap_kernel_launches(void);
+
+/* Largest half-bandwidth K this build factors, per precision. */
+SAP_API int32_t sap_max_K(int32_t precision);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SAP_H */

@@ -1,0 +1,227 @@
+"""GB300-native dense-banded SaP solver: Python binding of libsap.
+
+The binding is argument marshalling only: every step of the solver runs in
+the CUDA kernels of ``libsap.so`` (built in-tree by ``_build.build()``).
+Importing this package loads the library and raises if it is missing; there
+is no CPU fallback.  Tensors are torch CUDA float64 tensors; the stream is
+torch's current CUDA stream unless one is given.
+
+The functions below carry the names of the C entry points in
+``include/sap.h``.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libsap.so")
+
+SAP_OK, SAP_ERR_INVALID_ARG, SAP_ERR_OOM, SAP_ERR_NOT_CONVERGED, SAP_ERR_BREAKDOWN = 0, 1, 2, 3, 4
+SAP_ERR_TIMEOUT, SAP_ERR_CUDA, SAP_ERR_NOT_IMPLEMENTED, SAP_ERR_SINGULAR = 5, 6, 7, 8
+SAP_D, SAP_C = 0, 1
+SAP_FP64, SAP_FP32 = 0, 1
+
+
+class SapError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {sap_status_string(status)} (status {status})")
+
+
+class sap_options_t(C.Structure):
+    _fields_ = [("P", C.c_int32), ("variant", C.c_int32), ("precision", C.c_int32),
+                ("max_iters", C.c_int32), ("tol", C.c_double), ("boost_eps", C.c_double),
+                ("spin_limit", C.c_int64)]
+
+
+class sap_info_t(C.Structure):
+    _fields_ = [("iters", C.c_double), ("relres", C.c_double), ("n_boosted", C.c_int64),
+                ("n_matvec", C.c_int64), ("n_restarts", C.c_int64),
+                ("t_factor_ms", C.c_float), ("t_solve_ms", C.c_float)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libsap.so is not built ({LIB_PATH}); run __graft_entry__.build()")
+    lib = C.CDLL(LIB_PATH)
+    vp, i32, i64, dbl = C.c_void_p, C.c_int32, C.c_int64, C.c_double
+    P = C.POINTER
+    sig = {
+        "sap_default_options": (None, [P(sap_options_t)]),
+        "sap_factor": (C.c_int, [vp, i64, i32, P(sap_options_t), vp, P(vp)]),
+        "sap_solve": (C.c_int, [vp, vp, vp, P(sap_info_t), vp]),
+        "sap_solve_adjoint": (C.c_int, [vp, vp, vp, P(sap_info_t), vp]),
+        "sap_grad_band": (C.c_int, [vp, vp, vp, vp, vp]),
+        "sap_apply_preconditioner": (C.c_int, [vp, vp, vp, i32, vp]),
+        "sap_spmv": (C.c_int, [vp, i64, i32, vp, vp, i32, vp]),
+        "sap_solve_host": (C.c_int, [vp, vp, vp, P(sap_info_t), vp]),
+        "sap_get_partition": (C.c_int, [vp, vp]),
+        "sap_get_block_lu": (C.c_int, [vp, i32, vp, vp]),
+        "sap_get_interface": (C.c_int, [vp, i32, i32, i32, vp, vp]),
+        "sap_n_boosted": (i64, [vp]),
+        "sap_destroy": (C.c_int, [vp]),
+        "sap_status_string": (C.c_char_p, [C.c_int]),
+        "sap_max_K": (i32, [i32]),
+        "sap_kernel_launches": (i64, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+_lib = _load()
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def _ptr(t: torch.Tensor) -> int:
+    if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise ValueError("expected a contiguous CUDA float64 tensor")
+    return t.data_ptr()
+
+
+def _check(st: int, where: str, ok=(SAP_OK,)):
+    if st not in ok:
+        raise SapError(st, where)
+    return st
+
+
+def sap_status_string(status: int) -> str:
+    return _lib.sap_status_string(int(status)).decode()
+
+
+def sap_max_K(precision: int = SAP_FP32) -> int:
+    return int(_lib.sap_max_K(precision))
+
+
+def sap_default_options(**kw) -> sap_options_t:
+    o = sap_options_t()
+    _lib.sap_default_options(C.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+class Handle:
+    """Owns a sap_handle_t and keeps the borrowed band tensor alive."""
+
+    def __init__(self, ptr: int, band: torch.Tensor, N: int, K: int, opts: sap_options_t):
+        self.ptr = C.c_void_p(ptr)
+        self.band, self.N, self.K, self.opts = band, N, K, opts
+
+    def __del__(self):
+        if getattr(self, "ptr", None) is not None and self.ptr.value and _lib is not None:
+            _lib.sap_destroy(self.ptr)
+            self.ptr = None
+
+
+def sap_factor(band: torch.Tensor, N: int, K: int, opts: sap_options_t | None = None, stream=None,
+               **kw) -> Handle:
+    opts = opts or sap_default_options(**kw)
+    out = C.c_void_p()
+    st = _lib.sap_factor(_ptr(band), N, K, C.byref(opts), _stream(stream), C.byref(out))
+    _check(st, "sap_factor")
+    return Handle(out.value, band, N, K, opts)
+
+
+def sap_solve(h: Handle, b: torch.Tensor, x: torch.Tensor | None = None, stream=None,
+              raise_on_error: bool = True):
+    x = torch.empty_like(b) if x is None else x
+    info = sap_info_t()
+    st = _lib.sap_solve(h.ptr, _ptr(b), _ptr(x), C.byref(info), _stream(stream))
+    if raise_on_error:
+        _check(st, "sap_solve")
+    return x, info, st
+
+
+def sap_solve_adjoint(h: Handle, gbar: torch.Tensor, lam: torch.Tensor | None = None, stream=None,
+                      raise_on_error: bool = True):
+    lam = torch.empty_like(gbar) if lam is None else lam
+    info = sap_info_t()
+    st = _lib.sap_solve_adjoint(h.ptr, _ptr(gbar), _ptr(lam), C.byref(info), _stream(stream))
+    if raise_on_error:
+        _check(st, "sap_solve_adjoint")
+    return lam, info, st
+
+
+def sap_solve_host(h: Handle, b_host, x_host, stream=None, raise_on_error: bool = True):
+    """b_host / x_host: CPU float64 tensors (pinned for best transfer speed)."""
+    info = sap_info_t()
+    st = _lib.sap_solve_host(h.ptr, C.c_void_p(b_host.data_ptr()), C.c_void_p(x_host.data_ptr()),
+                             C.byref(info), _stream(stream))
+    if raise_on_error:
+        _check(st, "sap_solve_host")
+    return x_host, info, st
+
+
+def sap_grad_band(h: Handle, lam: torch.Tensor, x: torch.Tensor, out: torch.Tensor | None = None,
+                  stream=None) -> torch.Tensor:
+    out = torch.empty_like(h.band) if out is None else out
+    _check(_lib.sap_grad_band(h.ptr, _ptr(lam), _ptr(x), _ptr(out), _stream(stream)), "sap_grad_band")
+    return out
+
+
+def sap_apply_preconditioner(h: Handle, r: torch.Tensor, z: torch.Tensor | None = None,
+                             transpose: bool = False, stream=None) -> torch.Tensor:
+    z = torch.empty_like(r) if z is None else z
+    _check(_lib.sap_apply_preconditioner(h.ptr, _ptr(r), _ptr(z), int(transpose), _stream(stream)),
+           "sap_apply_preconditioner")
+    return z
+
+
+def sap_spmv(band: torch.Tensor, N: int, K: int, x: torch.Tensor, y: torch.Tensor | None = None,
+             transpose: bool = False, stream=None) -> torch.Tensor:
+    y = torch.empty_like(x) if y is None else y
+    _check(_lib.sap_spmv(_ptr(band), N, K, _ptr(x), _ptr(y), int(transpose), _stream(stream)), "sap_spmv")
+    return y
+
+
+def sap_get_partition(h: Handle):
+    import numpy as np
+    off = np.zeros(h.opts.P + 1, dtype=np.int64)
+    _check(_lib.sap_get_partition(h.ptr, C.c_void_p(off.ctypes.data)), "sap_get_partition")
+    return off
+
+
+def sap_get_block_lu(h: Handle, i: int, stream=None):
+    import numpy as np
+    off = sap_get_partition(h)
+    n = int(off[i + 1] - off[i])
+    f = np.zeros((n, 2 * h.K + 1))
+    _check(_lib.sap_get_block_lu(h.ptr, i, C.c_void_p(f.ctypes.data), _stream(stream)), "sap_get_block_lu")
+    return f
+
+
+def sap_get_interface(h: Handle, i: int, which: str, adjoint: bool = False, stream=None):
+    import numpy as np
+    code = {"B": 0, "C": 1, "V": 2, "W": 3, "R": 4}[which]
+    m = np.zeros((h.K, h.K))
+    _check(_lib.sap_get_interface(h.ptr, i, code, int(adjoint), C.c_void_p(m.ctypes.data), _stream(stream)),
+           "sap_get_interface")
+    return m
+
+
+def sap_kernel_launches() -> int:
+    """Kernels launched by libsap in this process so far."""
+    return int(_lib.sap_kernel_launches())
+
+
+def sap_n_boosted(h: Handle) -> int:
+    return int(_lib.sap_n_boosted(h.ptr))
+
+
+from .autograd import SapSolve, sap_solve_autograd  # noqa: E402
+
+__all__ = [n for n in dir() if n.startswith("sap_") or n in ("Handle", "SapError", "SapSolve")]

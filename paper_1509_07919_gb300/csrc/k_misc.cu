@@ -1,0 +1,372 @@
+// FP64 banded SpMV (y = A x, y = A^T x) over the band storage of Sec. 3.1,
+// the band gradient -lambda x^T, and the fused FP64 vector kernels of the
+// BiCGStab(2) iteration (Sleijpen & Fokkema 1993, l = 2; Sec. 2.1.1).
+//
+// Reductions are deterministic: a fixed grid writes one partial per block,
+// and the last block to finish (atomic ticket) sums the partials in block
+// order and evaluates the iteration's scalar recurrences on the device, so
+// the host never round-trips for alpha, beta, omega, gamma.
+#include <cuda_runtime.h>
+#include <cstdint>
+#include "sap_internal.cuh"
+#include "krylov.cuh"
+
+namespace sap {
+
+// ------------------------------------------------------------------ SpMV --
+namespace {
+constexpr int SPMV_T = 256;
+
+// y_i = sum_c band[c N + j] x_j, j = i + K - c  (A x)
+// y_j = sum_c band[c N + j] x_i, i = j + c - K  (A^T x)
+// x is staged in shared memory for the CTA's rows plus a K-halo each side.
+template <bool TRANS>
+__global__ void __launch_bounds__(SPMV_T)
+k_spmv(const double* __restrict__ band, int64_t N, int K, const double* __restrict__ x,
+       double* __restrict__ y) {
+  extern __shared__ double xs[];
+  const int64_t i0 = (int64_t)blockIdx.x * SPMV_T;
+  const int span = SPMV_T + 2 * K;
+  for (int t = threadIdx.x; t < span; t += SPMV_T) {
+    int64_t j = i0 - K + t;
+    xs[t] = (j >= 0 && j < N) ? x[j] : 0.0;
+  }
+  __syncthreads();
+  const int64_t i = i0 + threadIdx.x;
+  if (i >= N) return;
+  const int W = 2 * K + 1;
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+  // local index of x_j in xs: j - (i0 - K)
+  if (!TRANS) {
+    // j = i + K - c; in-range j <=> c in [max(0, i+K-(N-1)), min(2K, i+K)]
+    int clo = (int)max((int64_t)0, i + K - (N - 1));
+    int chi = (int)min((int64_t)(W - 1), i + K);
+    const double* bp = band + i + K;            // band[c N + i + K - c] = bp[c (N - 1)]
+    const int64_t stride = N - 1;
+    const int xl = threadIdx.x + 2 * K;         // xs index of j = i + K - c is xl - c
+    int c = clo;
+    for (; c + 3 <= chi; c += 4) {
+      a0 += bp[(int64_t)c * stride] * xs[xl - c];
+      a1 += bp[(int64_t)(c + 1) * stride] * xs[xl - c - 1];
+      a2 += bp[(int64_t)(c + 2) * stride] * xs[xl - c - 2];
+      a3 += bp[(int64_t)(c + 3) * stride] * xs[xl - c - 3];
+    }
+    for (; c <= chi; ++c) a0 += bp[(int64_t)c * stride] * xs[xl - c];
+  } else {
+    // i' = i + c - K in range <=> c in [max(0, K-i), min(2K, N-1-i+K)]
+    int clo = (int)max((int64_t)0, (int64_t)K - i);
+    int chi = (int)min((int64_t)(W - 1), N - 1 - i + K);
+    const double* bp = band + i;
+    const int xl = threadIdx.x;                 // xs index of i + c - K is xl + c
+    int c = clo;
+    for (; c + 3 <= chi; c += 4) {
+      a0 += bp[(int64_t)c * N] * xs[xl + c];
+      a1 += bp[(int64_t)(c + 1) * N] * xs[xl + c + 1];
+      a2 += bp[(int64_t)(c + 2) * N] * xs[xl + c + 2];
+      a3 += bp[(int64_t)(c + 3) * N] * xs[xl + c + 3];
+    }
+    for (; c <= chi; ++c) a0 += bp[(int64_t)c * N] * xs[xl + c];
+  }
+  y[i] = (a0 + a1) + (a2 + a3);
+}
+
+__global__ void k_grad_band(const double* __restrict__ lam, const double* __restrict__ x, int64_t N, int K,
+                            double* __restrict__ g) {
+  const int64_t total = (int64_t)(2 * K + 1) * N;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t c = e / N, j = e - c * N;
+    int64_t i = j + c - K;
+    g[e] = (i >= 0 && i < N) ? -lam[i] * x[j] : 0.0;
+  }
+}
+}  // namespace
+
+cudaError_t launch_spmv(const double* band, int64_t N, int K, const double* x, double* y, bool transpose,
+                        cudaStream_t s) {
+  int64_t nb = (N + SPMV_T - 1) / SPMV_T;
+  size_t smem = (SPMV_T + 2 * (size_t)K) * sizeof(double);
+  cudaError_t e;
+  if (transpose) {
+    e = cudaFuncSetAttribute(k_spmv<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    count_launches(1);
+    k_spmv<true><<<(unsigned)nb, SPMV_T, smem, s>>>(band, N, K, x, y);
+  } else {
+    e = cudaFuncSetAttribute(k_spmv<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    count_launches(1);
+    k_spmv<false><<<(unsigned)nb, SPMV_T, smem, s>>>(band, N, K, x, y);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_grad_band(const double* lam, const double* x, int64_t N, int K, double* g, cudaStream_t s) {
+  count_launches(1);
+  k_grad_band<<<152 * 8, 256, 0, s>>>(lam, x, N, K, g);
+  return cudaGetLastError();
+}
+
+// --------------------------------------------------------------- Krylov --
+namespace {
+constexpr int RT = 256;
+
+// Block-reduce ND values; the last block sums all partials in block order
+// into red[0..ND) and returns true (its thread 0 then runs the epilogue).
+template <int ND>
+__device__ __forceinline__ bool reduce_last(double (&v)[ND], KrylovDev& kd, double* red) {
+  __shared__ double ws[RT / 32][ND];
+  __shared__ bool last;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < ND; ++k) {
+    double a = v[k];
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    if (lane == 0) ws[w][k] = a;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < ND; ++k) {
+      double a = 0.0;
+      for (int q = 0; q < RT / 32; ++q) a += ws[q][k];
+      kd.part[blockIdx.x * ND + k] = a;
+    }
+    __threadfence();
+    unsigned t = atomicAdd(kd.ticket, 1u);
+    last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!last) return false;
+  if (threadIdx.x == 0) {
+    __threadfence();
+#pragma unroll
+    for (int k = 0; k < ND; ++k) {
+      double a = 0.0;
+      for (unsigned b = 0; b < gridDim.x; ++b) a += ((volatile double*)kd.part)[b * ND + k];
+      red[k] = a;
+    }
+    *kd.ticket = 0u;
+  }
+  return true;
+}
+
+#define GRID_LOOP(i) for (int64_t i = blockIdx.x * (int64_t)RT + threadIdx.x; i < n; i += (int64_t)gridDim.x * RT)
+
+// ||a||^2 -> S[slot]
+__global__ void __launch_bounds__(RT) k_norm2(const double* __restrict__ a, int64_t n, KrylovDev kd, int slot) {
+  double v[1] = {0.0};
+  GRID_LOOP(i) v[0] += a[i] * a[i];
+  double red[1];
+  if (reduce_last<1>(v, kd, red) && threadIdx.x == 0) kd.S[slot] = red[0];
+}
+
+// t = b - y, ||t||^2 -> S[slot]
+__global__ void __launch_bounds__(RT) k_residual(const double* __restrict__ b, const double* __restrict__ y,
+                                                 double* __restrict__ t, int64_t n, KrylovDev kd, int slot) {
+  double v[1] = {0.0};
+  GRID_LOOP(i) {
+    double r = b[i] - y[i];
+    t[i] = r;
+    v[0] += r * r;
+  }
+  double red[1];
+  if (reduce_last<1>(v, kd, red) && threadIdx.x == 0) kd.S[slot] = red[0];
+}
+
+// BiCG part, start of step j: (j == 0: rho0 = -omega rho0), rho1 = <r_j, rt>,
+// beta = alpha rho1 / rho0, rho0 = rho1.
+__global__ void __launch_bounds__(RT) k_bicg_rho(const double* __restrict__ rj, const double* __restrict__ rt,
+                                                 int64_t n, KrylovDev kd, int j) {
+  double v[1] = {0.0};
+  GRID_LOOP(i) v[0] += rj[i] * rt[i];
+  double red[1];
+  if (reduce_last<1>(v, kd, red) && threadIdx.x == 0) {
+    double* S = kd.S;
+    if (j == 0) S[S_RHO0] = -S[S_OMEGA] * S[S_RHO0];
+    double rho1 = red[0];
+    if (S[S_RHO0] == 0.0) S[S_BREAK] = 1.0;
+    S[S_BETA] = (S[S_RHO0] != 0.0) ? S[S_ALPHA] * rho1 / S[S_RHO0] : 0.0;
+    S[S_RHO0] = rho1;
+  }
+}
+
+// u_i = r_i - beta u_i, i = 0..j
+__global__ void __launch_bounds__(RT) k_bicg_u(double* __restrict__ u0, double* __restrict__ u1,
+                                               const double* __restrict__ r0, const double* __restrict__ r1,
+                                               int64_t n, const double* __restrict__ S, int j) {
+  const double beta = S[S_BETA];
+  GRID_LOOP(i) {
+    u0[i] = r0[i] - beta * u0[i];
+    if (j >= 1) u1[i] = r1[i] - beta * u1[i];
+  }
+}
+
+// gamma = <u_{j+1}, rt>, alpha = rho0 / gamma
+__global__ void __launch_bounds__(RT) k_bicg_gamma(const double* __restrict__ uj1, const double* __restrict__ rt,
+                                                   int64_t n, KrylovDev kd) {
+  double v[1] = {0.0};
+  GRID_LOOP(i) v[0] += uj1[i] * rt[i];
+  double red[1];
+  if (reduce_last<1>(v, kd, red) && threadIdx.x == 0) {
+    double* S = kd.S;
+    double g = red[0];
+    if (g == 0.0) S[S_BREAK] = 1.0;
+    S[S_ALPHA] = (g != 0.0) ? S[S_RHO0] / g : 0.0;
+  }
+}
+
+// r_i -= alpha u_{i+1} (i = 0..j), x += alpha u_0, ||r_0||^2 -> S[S_RN2]
+__global__ void __launch_bounds__(RT) k_bicg_r(double* __restrict__ r0, double* __restrict__ r1,
+                                               const double* __restrict__ u0, const double* __restrict__ u1,
+                                               const double* __restrict__ u2, double* __restrict__ x,
+                                               int64_t n, KrylovDev kd, int j) {
+  const double alpha = kd.S[S_ALPHA];
+  double v[1] = {0.0};
+  GRID_LOOP(i) {
+    double a = r0[i] - alpha * u1[i];
+    r0[i] = a;
+    if (j >= 1) r1[i] = r1[i] - alpha * u2[i];
+    x[i] = x[i] + alpha * u0[i];
+    v[0] += a * a;
+  }
+  double red[1];
+  if (reduce_last<1>(v, kd, red) && threadIdx.x == 0) kd.S[S_RN2] = red[0];
+}
+
+// MR part (1): sigma1 = <r1,r1>, gamma'_1 = <r0,r1>/sigma1, tau12 = <r2,r1>/sigma1
+__global__ void __launch_bounds__(RT) k_mr1(const double* __restrict__ r0, const double* __restrict__ r1,
+                                            const double* __restrict__ r2, int64_t n, KrylovDev kd) {
+  double v[3] = {0.0, 0.0, 0.0};
+  GRID_LOOP(i) {
+    double a = r1[i];
+    v[0] += a * a;
+    v[1] += r0[i] * a;
+    v[2] += r2[i] * a;
+  }
+  double red[3];
+  if (reduce_last<3>(v, kd, red) && threadIdx.x == 0) {
+    double* S = kd.S;
+    double s1 = red[0];
+    if (s1 == 0.0) S[S_BREAK] = 1.0;
+    S[S_SIGMA1] = s1;
+    S[S_GP1] = (s1 != 0.0) ? red[1] / s1 : 0.0;
+    S[S_TAU12] = (s1 != 0.0) ? red[2] / s1 : 0.0;
+  }
+}
+
+// MR part (2): r2 -= tau12 r1; sigma2 = <r2,r2>; gamma'_2 = <r0,r2>/sigma2;
+// gamma_2 = gamma'_2, omega = gamma_2, gamma_1 = gamma'_1 - tau12 gamma_2, gamma''_1 = gamma_2
+__global__ void __launch_bounds__(RT) k_mr2(const double* __restrict__ r0, const double* __restrict__ r1,
+                                            double* __restrict__ r2, int64_t n, KrylovDev kd) {
+  const double tau = kd.S[S_TAU12];
+  double v[2] = {0.0, 0.0};
+  GRID_LOOP(i) {
+    double a = r2[i] - tau * r1[i];
+    r2[i] = a;
+    v[0] += a * a;
+    v[1] += r0[i] * a;
+  }
+  double red[2];
+  if (reduce_last<2>(v, kd, red) && threadIdx.x == 0) {
+    double* S = kd.S;
+    double s2 = red[0];
+    if (s2 == 0.0) S[S_BREAK] = 1.0;
+    double gp2 = (s2 != 0.0) ? red[1] / s2 : 0.0;
+    S[S_GP2] = gp2;
+    S[S_G2] = gp2;
+    S[S_OMEGA] = gp2;
+    if (gp2 == 0.0) S[S_BREAK] = 1.0;
+    S[S_G1] = S[S_GP1] - S[S_TAU12] * gp2;
+    S[S_GPP1] = gp2;
+  }
+}
+
+// MR part (3): x += g1 r0 + gpp1 r1; r0 -= gp2 r2 + gp1 r1; u0 -= g2 u2 + g1 u1; ||r0||^2
+__global__ void __launch_bounds__(RT) k_mr3(double* __restrict__ x, double* __restrict__ r0,
+                                            const double* __restrict__ r1, const double* __restrict__ r2,
+                                            double* __restrict__ u0, const double* __restrict__ u1,
+                                            const double* __restrict__ u2, int64_t n, KrylovDev kd) {
+  const double* S = kd.S;
+  const double g1 = S[S_G1], gpp1 = S[S_GPP1], gp2 = S[S_GP2], gp1 = S[S_GP1], g2 = S[S_G2];
+  double v[1] = {0.0};
+  GRID_LOOP(i) {
+    double a0 = r0[i], a1 = r1[i];
+    x[i] = x[i] + (g1 * a0 + gpp1 * a1);
+    double nr = a0 - (gp2 * r2[i] + gp1 * a1);
+    r0[i] = nr;
+    u0[i] = u0[i] - (g2 * u2[i] + g1 * u1[i]);
+    v[0] += nr * nr;
+  }
+  double red[1];
+  if (reduce_last<1>(v, kd, red) && threadIdx.x == 0) kd.S[S_RN2] = red[0];
+}
+
+__global__ void k_init_scalars(double* S) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    for (int k = 0; k < S_COUNT; ++k) S[k] = 0.0;
+    S[S_RHO0] = 1.0;
+    S[S_ALPHA] = 0.0;
+    S[S_OMEGA] = 1.0;
+  }
+}
+}  // namespace
+
+int krylov_grid(int64_t n) {
+  int64_t g = (n + RT - 1) / RT;
+  if (g > kKrylovBlocks) g = kKrylovBlocks;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+cudaError_t kr_init(KrylovDev kd, cudaStream_t s) {
+  count_launches(1);
+  k_init_scalars<<<1, 32, 0, s>>>(kd.S);
+  return cudaGetLastError();
+}
+cudaError_t kr_norm2(const double* a, int64_t n, KrylovDev kd, int slot, cudaStream_t s) {
+  count_launches(1);
+  k_norm2<<<krylov_grid(n), RT, 0, s>>>(a, n, kd, slot);
+  return cudaGetLastError();
+}
+cudaError_t kr_residual(const double* b, const double* y, double* t, int64_t n, KrylovDev kd, int slot,
+                        cudaStream_t s) {
+  count_launches(1);
+  k_residual<<<krylov_grid(n), RT, 0, s>>>(b, y, t, n, kd, slot);
+  return cudaGetLastError();
+}
+cudaError_t kr_bicg_rho(const double* rj, const double* rt, int64_t n, KrylovDev kd, int j, cudaStream_t s) {
+  count_launches(1);
+  k_bicg_rho<<<krylov_grid(n), RT, 0, s>>>(rj, rt, n, kd, j);
+  return cudaGetLastError();
+}
+cudaError_t kr_bicg_u(double* u0, double* u1, const double* r0, const double* r1, int64_t n, KrylovDev kd, int j,
+                      cudaStream_t s) {
+  count_launches(1);
+  k_bicg_u<<<krylov_grid(n), RT, 0, s>>>(u0, u1, r0, r1, n, kd.S, j);
+  return cudaGetLastError();
+}
+cudaError_t kr_bicg_gamma(const double* uj1, const double* rt, int64_t n, KrylovDev kd, cudaStream_t s) {
+  count_launches(1);
+  k_bicg_gamma<<<krylov_grid(n), RT, 0, s>>>(uj1, rt, n, kd);
+  return cudaGetLastError();
+}
+cudaError_t kr_bicg_r(double* r0, double* r1, const double* u0, const double* u1, const double* u2, double* x,
+                      int64_t n, KrylovDev kd, int j, cudaStream_t s) {
+  count_launches(1);
+  k_bicg_r<<<krylov_grid(n), RT, 0, s>>>(r0, r1, u0, u1, u2, x, n, kd, j);
+  return cudaGetLastError();
+}
+cudaError_t kr_mr(double* x, double* r0, double* r1, double* r2, double* u0, const double* u1, const double* u2,
+                  int64_t n, KrylovDev kd, cudaStream_t s) {
+  int g = krylov_grid(n);
+  count_launches(1);
+  k_mr1<<<g, RT, 0, s>>>(r0, r1, r2, n, kd);
+  count_launches(1);
+  k_mr2<<<g, RT, 0, s>>>(r0, r1, r2, n, kd);
+  count_launches(1);
+  k_mr3<<<g, RT, 0, s>>>(x, r0, r1, r2, u0, u1, u2, n, kd);
+  return cudaGetLastError();
+}
+
+}  // namespace sap

@@ -1,0 +1,41 @@
+// Device scalars and launchers of the fused BiCGStab(2) vector kernels.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace sap {
+
+// Slots of the device scalar array of one Krylov solve.
+enum ScalarSlot {
+  S_RHO0 = 0, S_ALPHA, S_OMEGA, S_BETA, S_SIGMA1, S_GP1, S_TAU12, S_GP2, S_G1, S_G2, S_GPP1,
+  S_RN2,      // ||r^0||^2 after the last update
+  S_BN2,      // ||b||^2
+  S_BTN2,     // ||M^{-1} b||^2
+  S_TN2,      // ||b - A x||^2 (true residual)
+  S_BREAK,    // breakdown flag (nonzero)
+  S_COUNT
+};
+
+constexpr int kKrylovBlocks = 2 * 152;  // fixed reduction grid (two CTAs per SM)
+
+struct KrylovDev {
+  double* S;           // S_COUNT scalars
+  double* part;        // kKrylovBlocks * 4 partial sums
+  unsigned* ticket;    // last-block counter (returns to 0 after each reduction)
+};
+
+int krylov_grid(int64_t n);
+cudaError_t kr_init(KrylovDev kd, cudaStream_t s);
+cudaError_t kr_norm2(const double* a, int64_t n, KrylovDev kd, int slot, cudaStream_t s);
+cudaError_t kr_residual(const double* b, const double* y, double* t, int64_t n, KrylovDev kd, int slot,
+                        cudaStream_t s);
+cudaError_t kr_bicg_rho(const double* rj, const double* rt, int64_t n, KrylovDev kd, int j, cudaStream_t s);
+cudaError_t kr_bicg_u(double* u0, double* u1, const double* r0, const double* r1, int64_t n, KrylovDev kd, int j,
+                      cudaStream_t s);
+cudaError_t kr_bicg_gamma(const double* uj1, const double* rt, int64_t n, KrylovDev kd, cudaStream_t s);
+cudaError_t kr_bicg_r(double* r0, double* r1, const double* u0, const double* u1, const double* u2, double* x,
+                      int64_t n, KrylovDev kd, int j, cudaStream_t s);
+cudaError_t kr_mr(double* x, double* r0, double* r1, double* r2, double* u0, const double* u1, const double* u2,
+                  int64_t n, KrylovDev kd, cudaStream_t s);
+
+}  // namespace sap

@@ -1,0 +1,503 @@
+// C ABI of libsap (include/sap.h): handle management, the factor pipeline
+// and the outer BiCGStab(2) loop (Sec. 2.1.1) around the device kernels.
+#include <cuda_runtime.h>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <atomic>
+#include <memory>
+#include <new>
+#include <vector>
+#include "sap_internal.cuh"
+#include "krylov.cuh"
+
+using namespace sap;
+
+namespace sap {
+static std::atomic<long long> g_launches{0};
+void count_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+}  // namespace sap
+
+namespace {
+
+#define CK(x)                                    \
+  do {                                           \
+    cudaError_t e_ = (x);                        \
+    if (e_ != cudaSuccess) return SAP_ERR_CUDA;  \
+  } while (0)
+
+struct DevMem {
+  std::vector<void*> ptrs;
+  template <typename T>
+  sap_status_t alloc(T** p, size_t n) {
+    void* q = nullptr;
+    if (n == 0) n = 1;
+    if (cudaMalloc(&q, n * sizeof(T)) != cudaSuccess) {
+      cudaGetLastError();
+      return SAP_ERR_OOM;
+    }
+    ptrs.push_back(q);
+    *p = static_cast<T*>(q);
+    return SAP_OK;
+  }
+  ~DevMem() {
+    for (void* p : ptrs) cudaFree(p);
+  }
+};
+
+#define TRY(x)                           \
+  do {                                   \
+    sap_status_t s_ = (x);               \
+    if (s_ != SAP_OK) return s_;         \
+  } while (0)
+
+// Precision-independent part of the solver.
+struct SolverBase {
+  virtual ~SolverBase() = default;
+  virtual sap_status_t factor(cudaStream_t s) = 0;
+  virtual sap_status_t build_adjoint(cudaStream_t s) = 0;
+  virtual sap_status_t apply(const double* r, double* z, bool transpose, cudaStream_t s) = 0;
+  virtual sap_status_t block_lu(int i, double* host, cudaStream_t s) = 0;
+  virtual sap_status_t interface(int i, int which, bool adjoint, double* host, cudaStream_t s) = 0;
+};
+
+}  // namespace
+
+struct sap_handle {
+  Layout L;
+  sap_options_t opt{};
+  const double* band = nullptr;
+  DevMem mem;
+  Dev d{};
+  double* absmax = nullptr;
+  unsigned long long* n_boosted = nullptr;
+  int* singular = nullptr;
+  // Krylov workspace
+  double* vec = nullptr;      // 9 N doubles: r0 r1 r2 u0 u1 u2 rt tmp t
+  KrylovDev kd{};
+  double* host_s = nullptr;   // pinned scalar readback
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  float t_factor_ms = 0.f;
+  double* host_stage = nullptr;  // 2 N doubles for sap_solve_host, allocated on first use
+  std::unique_ptr<SolverBase> impl;
+  ~sap_handle() {
+    if (host_s) cudaFreeHost(host_s);
+    if (ev0) cudaEventDestroy(ev0);
+    if (ev1) cudaEventDestroy(ev1);
+  }
+};
+
+namespace {
+
+template <typename T>
+struct Solver : SolverBase {
+  sap_handle* h;
+  Factors<T> f;
+  double* scratch = nullptr;   // apply scratch: g (N), T tmp (N), ctop/cbot
+  bool adjoint_ready = false;
+  explicit Solver(sap_handle* hh) : h(hh) {}
+
+  sap_status_t factor(cudaStream_t s) override {
+    const Layout& L = h->L;
+    const int K = L.K, P = L.P;
+    const int64_t KK = (int64_t)K * K;
+    const int nI = P > 1 ? P - 1 : 1;
+    TRY(h->mem.alloc(&f.F, (size_t)L.f_elems));
+    TRY(h->mem.alloc(&scratch, (size_t)(2 * L.N + 2 * nI * K + 8)));
+    const double eps = h->opt.boost_eps;
+    CK(launch_absmax(h->band, L.N, K, h->absmax, s));
+    CK(launch_factor_lu<T>(h->band, L.N, K, P, h->d, h->absmax, eps, f.F, h->n_boosted, s));
+    if (h->opt.variant == SAP_C && P > 1) {
+      TRY(h->mem.alloc(&f.ULt, (size_t)(nI * KK)));
+      TRY(h->mem.alloc(&f.V, (size_t)(nI * KK)));
+      TRY(h->mem.alloc(&f.Wt, (size_t)(nI * KK)));
+      TRY(h->mem.alloc(&f.R, (size_t)(nI * KK)));
+      TRY(h->mem.alloc(&f.R0, (size_t)(nI * KK)));
+      TRY(h->mem.alloc(&f.piv, (size_t)(nI * K)));
+      CK(launch_factor_ul<T>(h->band, L.N, K, P, h->d, h->absmax, eps, f.ULt, h->n_boosted, s));
+      CK(launch_spikes<T>(h->band, L.N, K, P, h->d, f.F, f.ULt, false, f.V, f.Wt, f.R, f.R0, f.piv,
+                          h->singular, s));
+    }
+    return SAP_OK;
+  }
+
+  sap_status_t build_adjoint(cudaStream_t s) override {
+    if (adjoint_ready || h->opt.variant != SAP_C || h->L.P < 2) return SAP_OK;
+    const int K = h->L.K, nI = h->L.P - 1;
+    const int64_t KK = (int64_t)K * K;
+    TRY(h->mem.alloc(&f.Va, (size_t)(nI * KK)));
+    TRY(h->mem.alloc(&f.Wa, (size_t)(nI * KK)));
+    TRY(h->mem.alloc(&f.Ra, (size_t)(nI * KK)));
+    TRY(h->mem.alloc(&f.Ra0, (size_t)(nI * KK)));
+    TRY(h->mem.alloc(&f.piva, (size_t)(nI * K)));
+    CK(launch_spikes<T>(h->band, h->L.N, K, h->L.P, h->d, f.F, f.ULt, true, f.Va, f.Wa, f.Ra, f.Ra0, f.piva,
+                        h->singular, s));
+    int sing = 0;
+    CK(cudaMemcpyAsync(&sing, h->singular, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (sing) return SAP_ERR_SINGULAR;
+    adjoint_ready = true;
+    return SAP_OK;
+  }
+
+  sap_status_t apply(const double* r, double* z, bool transpose, cudaStream_t s) override {
+    if (transpose) TRY(build_adjoint(s));
+    CK(launch_apply<T>(h->band, h->L.N, h->L.K, h->L.P, h->d, f, h->opt.variant, transpose, r, z, scratch, s));
+    return SAP_OK;
+  }
+
+  sap_status_t block_lu(int i, double* host, cudaStream_t s) override {
+    const Layout& L = h->L;
+    const int64_t n = L.off[i + 1] - L.off[i], ld = L.ld[i];
+    const int W = L.W, K = L.K;
+    std::vector<T> buf((size_t)(W * ld));
+    CK(cudaMemcpyAsync(buf.data(), f.F + L.fbase[i], buf.size() * sizeof(T), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    // device layout F[c ld + q] = (r, q), c = K + r - q  ->  host f[r W + (q - r + K)]
+    for (int64_t r = 0; r < n; ++r)
+      for (int dq = -K; dq <= K; ++dq) {
+        int64_t q = r + dq;
+        double v = 0.0;
+        if (q >= 0 && q < n) v = (double)buf[(size_t)((K + r - q) * ld + q)];
+        host[r * W + (dq + K)] = v;
+      }
+    return SAP_OK;
+  }
+
+  sap_status_t interface(int i, int which, bool adjoint, double* host, cudaStream_t s) override {
+    const int K = h->L.K;
+    const int64_t KK = (int64_t)K * K;
+    if (h->opt.variant != SAP_C || h->L.P < 2 || i < 0 || i >= h->L.P - 1 || which < 0 || which > 4)
+      return SAP_ERR_INVALID_ARG;
+    if (adjoint) TRY(build_adjoint(s));
+    if (which <= 1) {
+      // B_i / C_{i+1} from the band (or their transposed roles for A^T)
+      std::vector<double> tmp((size_t)KK, 0.0);
+      const int64_t N = h->L.N, sr = h->L.off[i + 1];
+      std::vector<double> col((size_t)(2 * K + 1));
+      for (int r = 0; r < K; ++r)
+        for (int c = 0; c < K; ++c) {
+          // forward: B(r,c) = a(s-K+r, s+c); C(r,c) = a(s+r, s-K+c)
+          // adjoint: B'(r,c) = C(c,r); C'(r,c) = B(c,r)
+          int64_t gi, gj;
+          bool isB = (which == 0) != adjoint;
+          int rr = adjoint ? c : r, cc = adjoint ? r : c;
+          if (isB) { gi = sr - K + rr; gj = sr + cc; } else { gi = sr + rr; gj = sr - K + cc; }
+          int64_t cidx = K + gi - gj;
+          double v = 0.0;
+          if (cidx >= 0 && cidx <= 2 * K)
+            CK(cudaMemcpyAsync(&v, h->band + cidx * N + gj, sizeof(double), cudaMemcpyDeviceToHost, s));
+          CK(cudaStreamSynchronize(s));
+          tmp[(size_t)(r * K + c)] = v;
+        }
+      std::memcpy(host, tmp.data(), (size_t)KK * sizeof(double));
+      return SAP_OK;
+    }
+    if (which == 4) {
+      const double* src = (adjoint ? f.Ra0 : f.R0) + i * KK;
+      CK(cudaMemcpyAsync(host, src, (size_t)KK * sizeof(double), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      return SAP_OK;
+    }
+    const T* src = (which == 2 ? (adjoint ? f.Va : f.V) : (adjoint ? f.Wa : f.Wt)) + i * KK;
+    std::vector<T> buf((size_t)KK);
+    CK(cudaMemcpyAsync(buf.data(), src, (size_t)KK * sizeof(T), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    for (int64_t e = 0; e < KK; ++e) host[e] = (double)buf[(size_t)e];
+    return SAP_OK;
+  }
+};
+
+sap_status_t check_options(const sap_options_t* o, int64_t N, int K) {
+  if (!o) return SAP_ERR_INVALID_ARG;
+  if (N < 2 || K < 1 || K >= N) return SAP_ERR_INVALID_ARG;
+  if (o->P < 1 || o->P > N) return SAP_ERR_INVALID_ARG;
+  if (o->variant != SAP_D && o->variant != SAP_C) return SAP_ERR_INVALID_ARG;
+  if (o->precision != SAP_FP64 && o->precision != SAP_FP32) return SAP_ERR_INVALID_ARG;
+  return SAP_OK;
+}
+
+// Largest K of the SaP-C spike kernel: 8 K^2 + 2 sizeof(T) K^2 bytes of shared memory.
+int max_K_spikes(int precision) { return precision == SAP_FP64 ? 98 : 120; }
+
+// One preconditioned matvec y = M^{-1} (A v) (or with A^T and the SaP of A^T).
+sap_status_t opmv(sap_handle* h, const double* v, double* y, double* tmp, bool tr, cudaStream_t s) {
+  CK(launch_spmv(h->band, h->L.N, h->L.K, v, tmp, tr, s));
+  return h->impl->apply(tmp, y, tr, s);
+}
+
+sap_status_t krylov(sap_handle* h, const double* b, double* x, bool tr, sap_info_t* info, cudaStream_t s) {
+  const int64_t N = h->L.N;
+  double* r[3] = {h->vec, h->vec + N, h->vec + 2 * N};
+  double* u[3] = {h->vec + 3 * N, h->vec + 4 * N, h->vec + 5 * N};
+  double* rt = h->vec + 6 * N;
+  double* tmp = h->vec + 7 * N;
+  double* t = h->vec + 8 * N;
+  KrylovDev kd = h->kd;
+  const double tol = h->opt.tol;
+  sap_info_t inf{};
+  inf.iters = 0;
+  inf.relres = 1.0;
+  CK(cudaEventRecord(h->ev0, s));
+  CK(cudaMemsetAsync(x, 0, N * sizeof(double), s));
+  CK(kr_init(kd, s));
+  CK(kr_norm2(b, N, kd, S_BN2, s));
+  TRY(h->impl->apply(b, r[0], tr, s));
+  CK(kr_norm2(r[0], N, kd, S_BTN2, s));
+  CK(cudaMemcpyAsync(rt, r[0], N * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  CK(cudaMemsetAsync(u[0], 0, N * sizeof(double), s));
+  CK(cudaMemcpyAsync(h->host_s, kd.S + S_RN2, 5 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  const double bn = std::sqrt(h->host_s[S_BN2 - S_RN2]);
+  const double btn = std::sqrt(h->host_s[S_BTN2 - S_RN2]);
+  sap_status_t status = SAP_ERR_NOT_CONVERGED;
+  int64_t nmv = 0;
+  if (bn == 0.0) {
+    inf.relres = 0.0;
+    status = SAP_OK;
+  } else {
+    // exit test: recursive residual, then the true residual in FP64
+    auto exit_test = [&](double quarters, bool* done) -> sap_status_t {
+      *done = false;
+      CK(cudaMemcpyAsync(h->host_s, kd.S + S_RN2, 5 * sizeof(double), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      if (h->host_s[S_BREAK - S_RN2] != 0.0) { status = SAP_ERR_BREAKDOWN; *done = true; return SAP_OK; }
+      const double rn = std::sqrt(h->host_s[0]);
+      if (!(rn <= tol * btn)) return SAP_OK;
+      CK(launch_spmv(h->band, N, h->L.K, x, tmp, tr, s));
+      CK(kr_residual(b, tmp, t, N, kd, S_TN2, s));
+      CK(cudaMemcpyAsync(h->host_s, kd.S + S_RN2, 5 * sizeof(double), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      const double rel = std::sqrt(h->host_s[S_TN2 - S_RN2]) / bn;
+      inf.relres = rel;
+      if (rel <= tol) { status = SAP_OK; inf.iters = quarters; *done = true; return SAP_OK; }
+      TRY(h->impl->apply(t, r[0], tr, s));   // reliable update of r^0
+      ++inf.n_restarts;
+      return SAP_OK;
+    };
+    bool done = false;
+    for (int it = 0; it < h->opt.max_iters && !done; ++it) {
+      for (int j = 0; j < 2 && !done; ++j) {
+        CK(kr_bicg_rho(r[j], rt, N, kd, j, s));
+        CK(kr_bicg_u(u[0], u[1], r[0], r[1], N, kd, j, s));
+        TRY(opmv(h, u[j], u[j + 1], tmp, tr, s));
+        ++nmv;
+        CK(kr_bicg_gamma(u[j + 1], rt, N, kd, s));
+        CK(kr_bicg_r(r[0], r[1], u[0], u[1], u[2], x, N, kd, j, s));
+        TRY(exit_test(it + (j == 0 ? 0.25 : 0.75), &done));
+        if (done) break;
+        TRY(opmv(h, r[j], r[j + 1], tmp, tr, s));
+        ++nmv;
+      }
+      if (done) break;
+      CK(kr_mr(x, r[0], r[1], r[2], u[0], u[1], u[2], N, kd, s));
+      TRY(exit_test(it + 1.0, &done));
+      inf.iters = it + 1.0;
+    }
+    if (status != SAP_OK) {
+      CK(launch_spmv(h->band, N, h->L.K, x, tmp, tr, s));
+      CK(kr_residual(b, tmp, t, N, kd, S_TN2, s));
+      CK(cudaMemcpyAsync(h->host_s, kd.S + S_RN2, 5 * sizeof(double), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      inf.relres = std::sqrt(h->host_s[S_TN2 - S_RN2]) / bn;
+    }
+  }
+  CK(cudaEventRecord(h->ev1, s));
+  CK(cudaEventSynchronize(h->ev1));
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, h->ev0, h->ev1);
+  inf.n_matvec = nmv;
+  inf.t_solve_ms = ms;
+  inf.t_factor_ms = h->t_factor_ms;
+  unsigned long long nb = 0;
+  CK(cudaMemcpy(&nb, h->n_boosted, sizeof(nb), cudaMemcpyDeviceToHost));
+  inf.n_boosted = (int64_t)nb;
+  if (info) *info = inf;
+  return status;
+}
+
+}  // namespace
+
+extern "C" {
+
+void sap_default_options(sap_options_t* o) {
+  if (!o) return;
+  o->P = 1;
+  o->variant = SAP_D;
+  o->precision = SAP_FP64;
+  o->max_iters = 500;
+  o->tol = 1e-10;
+  o->boost_eps = 0.0;
+  o->spin_limit = 0;
+}
+
+int64_t sap_kernel_launches(void) { return (int64_t)sap::g_launches.load(); }
+
+int32_t sap_max_K(int32_t precision) {
+  (void)precision;
+  return kMaxK;
+}
+
+sap_status_t sap_factor(const double* band_dev, int64_t N, int32_t K, const sap_options_t* opt_in,
+                        cudaStream_t s, sap_handle_t* out) {
+  if (!out) return SAP_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!band_dev) return SAP_ERR_INVALID_ARG;
+  TRY(check_options(opt_in, N, K));
+  sap_options_t opt = *opt_in;
+  if (opt.max_iters <= 0) opt.max_iters = 500;
+  if (!(opt.tol > 0.0)) opt.tol = 1e-10;
+  if (!(opt.boost_eps > 0.0)) opt.boost_eps = opt.precision == SAP_FP64 ? 0x1p-53 : 0x1p-24;
+  if (K > kMaxK) return SAP_ERR_NOT_IMPLEMENTED;
+  if (opt.variant == SAP_C && opt.P > 1 && K > max_K_spikes(opt.precision)) return SAP_ERR_NOT_IMPLEMENTED;
+  std::unique_ptr<sap_handle> h(new (std::nothrow) sap_handle());
+  if (!h) return SAP_ERR_OOM;
+  h->opt = opt;
+  h->band = band_dev;
+  Layout& L = h->L;
+  L.N = N; L.K = K; L.P = opt.P; L.W = 2 * K + 1;
+  L.off.resize(L.P + 1);
+  {
+    int64_t q = N / L.P, pr = N - (int64_t)L.P * q;
+    L.off[0] = 0;
+    for (int i = 0; i < L.P; ++i) L.off[i + 1] = L.off[i] + q + (i < pr ? 1 : 0);
+  }
+  L.fbase.resize(L.P);
+  L.ld.resize(L.P);
+  int64_t acc = 0;
+  for (int i = 0; i < L.P; ++i) {
+    int64_t n = L.off[i + 1] - L.off[i];
+    if (n < 1) return SAP_ERR_INVALID_ARG;
+    if (opt.variant == SAP_C && L.P > 1 && n < 2 * (int64_t)K) return SAP_ERR_INVALID_ARG;
+    L.ld[i] = (n + 31) / 32 * 32;
+    L.fbase[i] = acc;
+    acc += L.ld[i] * L.W;
+  }
+  L.f_elems = acc;
+  int64_t *doff, *dfb, *dld;
+  TRY(h->mem.alloc(&doff, L.P + 1));
+  TRY(h->mem.alloc(&dfb, L.P));
+  TRY(h->mem.alloc(&dld, L.P));
+  CK(cudaMemcpyAsync(doff, L.off.data(), (L.P + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(dfb, L.fbase.data(), L.P * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(dld, L.ld.data(), L.P * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+  h->d = Dev{doff, dfb, dld};
+  TRY(h->mem.alloc(&h->absmax, 1));
+  TRY(h->mem.alloc(&h->n_boosted, 1));
+  TRY(h->mem.alloc(&h->singular, 1));
+  TRY(h->mem.alloc(&h->vec, (size_t)(9 * N)));
+  TRY(h->mem.alloc(&h->kd.S, S_COUNT));
+  TRY(h->mem.alloc(&h->kd.part, kKrylovBlocks * 4));
+  TRY(h->mem.alloc(&h->kd.ticket, 1));
+  CK(cudaMemsetAsync(h->n_boosted, 0, sizeof(unsigned long long), s));
+  CK(cudaMemsetAsync(h->singular, 0, sizeof(int), s));
+  CK(cudaMemsetAsync(h->kd.ticket, 0, sizeof(unsigned), s));
+  CK(cudaMemsetAsync(h->vec, 0, 9 * N * sizeof(double), s));
+  if (cudaMallocHost(&h->host_s, 16 * sizeof(double)) != cudaSuccess) return SAP_ERR_OOM;
+  CK(cudaEventCreate(&h->ev0));
+  CK(cudaEventCreate(&h->ev1));
+  if (opt.precision == SAP_FP64) h->impl.reset(new Solver<double>(h.get()));
+  else h->impl.reset(new Solver<float>(h.get()));
+  CK(cudaEventRecord(h->ev0, s));
+  TRY(h->impl->factor(s));
+  CK(cudaEventRecord(h->ev1, s));
+  CK(cudaEventSynchronize(h->ev1));
+  CK(cudaGetLastError());
+  cudaEventElapsedTime(&h->t_factor_ms, h->ev0, h->ev1);
+  int sing = 0;
+  CK(cudaMemcpy(&sing, h->singular, sizeof(int), cudaMemcpyDeviceToHost));
+  if (sing) return SAP_ERR_SINGULAR;
+  *out = h.release();
+  return SAP_OK;
+}
+
+sap_status_t sap_solve(sap_handle_t h, const double* b, double* x, sap_info_t* info, cudaStream_t s) {
+  if (!h || !b || !x || b == x) return SAP_ERR_INVALID_ARG;
+  return krylov(h, b, x, false, info, s);
+}
+
+sap_status_t sap_solve_adjoint(sap_handle_t h, const double* g, double* lam, sap_info_t* info, cudaStream_t s) {
+  if (!h || !g || !lam || g == lam) return SAP_ERR_INVALID_ARG;
+  TRY(h->impl->build_adjoint(s));
+  return krylov(h, g, lam, true, info, s);
+}
+
+sap_status_t sap_solve_host(sap_handle_t h, const double* b_host, double* x_host, sap_info_t* info,
+                            cudaStream_t s) {
+  if (!h || !b_host || !x_host) return SAP_ERR_INVALID_ARG;
+  const int64_t N = h->L.N;
+  if (!h->host_stage) TRY(h->mem.alloc(&h->host_stage, (size_t)(2 * N)));
+  double* xb = h->host_stage;
+  CK(cudaMemcpyAsync(xb, b_host, N * sizeof(double), cudaMemcpyHostToDevice, s));
+  sap_status_t st = krylov(h, xb, xb + N, false, info, s);
+  CK(cudaMemcpyAsync(x_host, xb + N, N * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  return st;
+}
+
+sap_status_t sap_grad_band(sap_handle_t h, const double* lam, const double* x, double* g, cudaStream_t s) {
+  if (!h || !lam || !x || !g) return SAP_ERR_INVALID_ARG;
+  CK(launch_grad_band(lam, x, h->L.N, h->L.K, g, s));
+  return SAP_OK;
+}
+
+sap_status_t sap_apply_preconditioner(sap_handle_t h, const double* r, double* z, int32_t transpose,
+                                      cudaStream_t s) {
+  if (!h || !r || !z || r == z) return SAP_ERR_INVALID_ARG;
+  return h->impl->apply(r, z, transpose != 0, s);
+}
+
+sap_status_t sap_spmv(const double* band, int64_t N, int32_t K, const double* x, double* y, int32_t transpose,
+                      cudaStream_t s) {
+  if (!band || !x || !y || x == y || N < 1 || K < 0 || K >= N) return SAP_ERR_INVALID_ARG;
+  CK(launch_spmv(band, N, K, x, y, transpose != 0, s));
+  return SAP_OK;
+}
+
+sap_status_t sap_get_partition(sap_handle_t h, int64_t* off) {
+  if (!h || !off) return SAP_ERR_INVALID_ARG;
+  std::memcpy(off, h->L.off.data(), (h->L.P + 1) * sizeof(int64_t));
+  return SAP_OK;
+}
+
+sap_status_t sap_get_block_lu(sap_handle_t h, int32_t i, double* f, cudaStream_t s) {
+  if (!h || !f || i < 0 || i >= h->L.P) return SAP_ERR_INVALID_ARG;
+  return h->impl->block_lu(i, f, s);
+}
+
+sap_status_t sap_get_interface(sap_handle_t h, int32_t i, int32_t which, int32_t adjoint, double* m,
+                               cudaStream_t s) {
+  if (!h || !m) return SAP_ERR_INVALID_ARG;
+  return h->impl->interface(i, which, adjoint != 0, m, s);
+}
+
+int64_t sap_n_boosted(sap_handle_t h) {
+  if (!h) return -1;
+  unsigned long long nb = 0;
+  if (cudaMemcpy(&nb, h->n_boosted, sizeof(nb), cudaMemcpyDeviceToHost) != cudaSuccess) return -1;
+  return (int64_t)nb;
+}
+
+sap_status_t sap_destroy(sap_handle_t h) {
+  if (!h) return SAP_ERR_INVALID_ARG;
+  cudaDeviceSynchronize();
+  delete h;
+  return SAP_OK;
+}
+
+const char* sap_status_string(sap_status_t s) {
+  switch (s) {
+    case SAP_OK: return "ok";
+    case SAP_ERR_INVALID_ARG: return "invalid argument";
+    case SAP_ERR_OOM: return "out of device memory";
+    case SAP_ERR_NOT_CONVERGED: return "not converged";
+    case SAP_ERR_BREAKDOWN: return "BiCGStab(2) breakdown";
+    case SAP_ERR_TIMEOUT: return "device wait timed out";
+    case SAP_ERR_CUDA: return "CUDA error";
+    case SAP_ERR_NOT_IMPLEMENTED: return "not implemented for these sizes";
+    case SAP_ERR_SINGULAR: return "singular reduced matrix";
+  }
+  return "unknown status";
+}
+
+}  // extern "C"

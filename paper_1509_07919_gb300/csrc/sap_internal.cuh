@@ -1,0 +1,74 @@
+// Internal declarations shared by the libsap translation units.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+#include <vector>
+#include "../../include/sap.h"
+
+namespace sap {
+
+// Largest half-bandwidth handled by the register-window factor kernel:
+// a 16 x 16 thread grid with up to 8 x 8 window slots per thread.
+constexpr int kMaxK = 127;
+
+// Factor storage of one block (per block i, local rows/cols 0..n_i-1):
+// "diagonal-major" like the input band, indexed by the column:
+//   F_i[c * ld_i + q] = factor entry (r, q) with c = K + r - q,
+// c > K: unit-lower L, c <= K: U (diagonal at c = K).
+struct Layout {
+  int64_t N = 0;
+  int K = 0, P = 0, W = 0;
+  std::vector<int64_t> off;    // P+1 row offsets
+  std::vector<int64_t> fbase;  // element offset of block i in the factor array
+  std::vector<int64_t> ld;     // leading dimension of block i
+  int64_t f_elems = 0;
+};
+
+struct Dev {  // device copies of the partition, passed to kernels
+  const int64_t* off;
+  const int64_t* fbase;
+  const int64_t* ld;
+};
+
+template <typename T>
+struct Factors {
+  T* F = nullptr;        // LU factors of all blocks
+  T* ULt = nullptr;      // per block i >= 1: top K x K of [U'|L'] (row-major, U' strictly upper, L' on/below)
+  T* V = nullptr;        // per interface: V^(b)_i (K x K row-major)
+  T* Wt = nullptr;       // per interface: W^(t)_{i+1}
+  double* R = nullptr;   // per interface: Rbar_i^{-1} (from its GEPP factors), FP64
+  int* piv = nullptr;    // per interface: pivots of Rbar_i
+  double* R0 = nullptr;  // per interface: Rbar_i before factoring (kept for inspection)
+  // adjoint SaP (built on demand)
+  T* Va = nullptr; T* Wa = nullptr; double* Ra = nullptr; int* piva = nullptr; double* Ra0 = nullptr;
+};
+
+// Host-side count of kernel launches issued by the library (for reporting).
+void count_launches(int n);
+
+// ---- launchers (each returns cudaGetLastError()) ----
+cudaError_t launch_spmv(const double* band, int64_t N, int K, const double* x, double* y,
+                        bool transpose, cudaStream_t s);
+cudaError_t launch_absmax(const double* band, int64_t N, int K, double* out, cudaStream_t s);
+cudaError_t launch_grad_band(const double* lam, const double* x, int64_t N, int K, double* g,
+                             cudaStream_t s);
+
+template <typename T>
+cudaError_t launch_factor_lu(const double* band, int64_t N, int K, int P, Dev d, const double* absmax,
+                             double eps, T* F, unsigned long long* n_boosted, cudaStream_t s);
+template <typename T>
+cudaError_t launch_factor_ul(const double* band, int64_t N, int K, int P, Dev d, const double* absmax,
+                             double eps, T* ULt, unsigned long long* n_boosted, cudaStream_t s);
+template <typename T>
+cudaError_t launch_spikes(const double* band, int64_t N, int K, int P, Dev d, const T* F, const T* ULt,
+                          bool adjoint, T* V, T* Wt, double* Rinv, double* R0, int* piv, int* singular,
+                          cudaStream_t s);
+template <typename T>
+cudaError_t launch_apply(const double* band, int64_t N, int K, int P, Dev d, const Factors<T>& f,
+                         int variant, bool transpose, const double* r, double* z, double* scratch,
+                         cudaStream_t s);
+
+// Krylov vector kernels (FP64)
+struct Krylov;  // defined in sap_api.cu
+
+}  // namespace sap

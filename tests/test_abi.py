@@ -1,0 +1,47 @@
+"""CPU checks of the boundary: libsap builds, loads without a GPU and exports
+every entry point that include/sap.h declares (no compute calls here)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "sap.h")
+
+
+def declared_symbols():
+    src = open(HEADER).read()
+    return sorted(set(re.findall(r"SAP_API\s+[\w\s\*]*?\b(sap_\w+)\s*\(", src)))
+
+
+def test_header_declares_the_entry_points():
+    names = declared_symbols()
+    for must in ("sap_factor", "sap_solve", "sap_solve_adjoint", "sap_grad_band", "sap_spmv",
+                 "sap_apply_preconditioner", "sap_destroy", "sap_status_string"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol():
+    import __graft_entry__
+    lib_path = __graft_entry__._load_build_module().build()
+    lib = ctypes.CDLL(lib_path)
+    missing = [n for n in declared_symbols() if not hasattr(lib, n)]
+    assert not missing, missing
+    lib.sap_status_string.restype = ctypes.c_char_p
+    assert lib.sap_status_string(0) == b"ok"
+    assert lib.sap_max_K(1) >= 64
+
+
+def test_package_refuses_to_run_without_library(tmp_path, monkeypatch):
+    """The binding raises at import when libsap.so is absent (no CPU fallback)."""
+    import importlib.util
+    import shutil
+    pkg = tmp_path / "paper_1509_07919_gb300"
+    shutil.copytree(os.path.join(ROOT, "paper_1509_07919_gb300"), pkg,
+                    ignore=shutil.ignore_patterns("*.so", "_build", "__pycache__"))
+    spec = importlib.util.spec_from_file_location("sap_nolib", pkg / "__init__.py",
+                                                  submodule_search_locations=[str(pkg)])
+    mod = importlib.util.module_from_spec(spec)
+    with pytest.raises(ImportError):
+        spec.loader.exec_module(mod)

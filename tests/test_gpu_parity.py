@@ -1,0 +1,269 @@
+"""GPU parity: every step of the CUDA path (through the C ABI) against the FP64
+CPU oracle on the same seeded inputs.
+
+Tolerances (FP64 path): factors within 1e-11 relative (per block, max norm),
+spike tips / Rbar within 1e-11, preconditioner output within 1e-11, final
+solutions ||x - x_oracle|| / ||x_oracle|| <= 1e-8 with true relres <= 1e-10.
+FP32 preconditioner: factors within 64 K u32 relative; the FP64 outer
+iteration still has to reach relres <= 1e-10 and the 1e-8 solution match."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import sap_inputs as G
+
+pytestmark = pytest.mark.gpu
+
+U32 = 2.0 ** -24
+
+
+@pytest.fixture(scope="module")
+def sap():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1509_07919_gb300 as S
+    return S
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to("cuda")
+
+
+def host(t):
+    return t.detach().cpu().numpy()
+
+
+def make(N, K, d, seed):
+    band = G.dense_banded(N, K, d, seed)
+    xt = G.x_true(N, seed)
+    b = O.spmv(band, N, K, xt)
+    return band, xt, b
+
+
+def relerr(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+# ------------------------------------------------------------------ SpMV --
+
+@pytest.mark.parametrize("N,K", [(10007, 7), (1000, 50), (513, 1), (300, 127)])
+def test_spmv_parity(sap, N, K):
+    band, xt, _ = make(N, K, 1.0, 100 + K)
+    # poison the padding slots: the kernel must not read them
+    bp = band.reshape(2 * K + 1, N).copy()
+    for c in range(2 * K + 1):
+        lo, hi = max(0, K - c), min(N, N + K - c)
+        bp[c, :lo] = np.nan
+        bp[c, hi:] = np.nan
+    bd = dev(bp.reshape(-1))
+    x = dev(xt)
+    for tr in (False, True):
+        y = host(sap.sap_spmv(bd, N, K, x, transpose=tr))
+        yo = O.spmv(band, N, K, xt, transpose=tr)
+        scale = O.spmv(np.abs(band), N, K, np.abs(xt), transpose=tr)
+        assert np.all(np.abs(y - yo) <= 1e-14 * scale + 1e-300), (tr, np.abs(y - yo).max())
+
+
+# ------------------------------------------------------------- factors --
+
+@pytest.mark.parametrize("N,K,P", [(2000, 10, 8), (4003, 50, 4), (997, 33, 5), (600, 1, 3), (1500, 64, 2),
+                                   (700, 100, 3)])
+def test_block_lu_parity_fp64(sap, N, K, P):
+    band, _, _ = make(N, K, 1.0, 200 + K)
+    h = sap.sap_factor(dev(band), N, K, P=P, variant=sap.SAP_D, precision=sap.SAP_FP64)
+    o = O.Sap(band, N, K, P, O.SAP_D)
+    assert list(sap.sap_get_partition(h)) == list(o.offsets)
+    for i in range(P):
+        fg, fo = sap.sap_get_block_lu(h, i), o.block(i, 0)
+        assert np.abs(fg - fo).max() <= 1e-11 * np.abs(fo).max(), (i, np.abs(fg - fo).max())
+    assert sap.sap_n_boosted(h) == 0 == o.n_boosted
+
+
+@pytest.mark.parametrize("N,K,P", [(4003, 50, 4), (2000, 10, 8), (700, 100, 3)])
+def test_block_lu_parity_fp32(sap, N, K, P):
+    band, _, _ = make(N, K, 1.0, 300 + K)
+    h = sap.sap_factor(dev(band), N, K, P=P, variant=sap.SAP_D, precision=sap.SAP_FP32)
+    o = O.Sap(band, N, K, P, O.SAP_D)
+    for i in range(P):
+        fg, fo = sap.sap_get_block_lu(h, i), o.block(i, 0)
+        assert np.abs(fg - fo).max() <= 64 * K * U32 * np.abs(fo).max()
+
+
+@pytest.mark.parametrize("prec,tol", [(0, 1e-11), (1, 2e-4)])
+@pytest.mark.parametrize("N,K,P", [(1200, 10, 5), (3001, 40, 6), (900, 64, 3)])
+def test_spike_tips_and_rbar_parity(sap, N, K, P, prec, tol):
+    band, _, _ = make(N, K, 1.0, 400 + K)
+    h = sap.sap_factor(dev(band), N, K, P=P, variant=sap.SAP_C, precision=prec)
+    o = O.Sap(band, N, K, P, O.SAP_C)
+    bt = O.transpose_band(band, N, K)
+    oa = O.Sap(bt, N, K, P, O.SAP_C)
+    for i in range(P - 1):
+        for w in ("B", "C", "V", "W", "R"):
+            g, r = sap.sap_get_interface(h, i, w), o.interface(i, w)
+            assert np.abs(g - r).max() <= tol * max(np.abs(r).max(), 1.0), (i, w, np.abs(g - r).max())
+            ga, ra = sap.sap_get_interface(h, i, w, adjoint=True), oa.interface(i, w)
+            assert np.abs(ga - ra).max() <= tol * max(np.abs(ra).max(), 1.0), ("adj", i, w)
+
+
+# --------------------------------------------------------------- apply --
+
+@pytest.mark.parametrize("variant", [0, 1])
+@pytest.mark.parametrize("N,K,P", [(2000, 10, 8), (4003, 50, 4), (1111, 33, 3), (777, 5, 1)])
+def test_apply_parity(sap, variant, N, K, P):
+    band, _, _ = make(N, K, 1.0, 500 + K)
+    r = G.adjoint_seed(N, 500 + K)
+    for prec, tol in ((0, 1e-11), (1, 1e-4)):
+        h = sap.sap_factor(dev(band), N, K, P=P, variant=variant, precision=prec)
+        o = O.Sap(band, N, K, P, variant)
+        z = host(sap.sap_apply_preconditioner(h, dev(r)))
+        zo = o.apply(r)
+        assert relerr(z, zo) <= tol, (prec, relerr(z, zo))
+        oa = O.Sap(O.transpose_band(band, N, K), N, K, P, variant)
+        za = host(sap.sap_apply_preconditioner(h, dev(r), transpose=True))
+        assert relerr(za, oa.apply(r)) <= tol, (prec, "adjoint", relerr(za, oa.apply(r)))
+
+
+# --------------------------------------------------------------- solve --
+
+@pytest.mark.parametrize("variant", [0, 1])
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("N,K,P,d", [(10000, 10, 8, 1.2), (6007, 50, 6, 1.0), (3000, 20, 10, 0.8)])
+def test_solve_parity(sap, variant, prec, N, K, P, d):
+    band, xt, b = make(N, K, d, 600 + K)
+    xo, io, _ = O.solve(band, N, K, b, P, variant)
+    assert io.status == O.OK
+    h = sap.sap_factor(dev(band), N, K, P=P, variant=variant, precision=prec)
+    x, info, st = sap.sap_solve(h, dev(b))
+    x = host(x)
+    assert st == sap.SAP_OK
+    assert info.relres <= 1e-10
+    assert np.linalg.norm(b - O.spmv(band, N, K, x)) / np.linalg.norm(b) <= 1e-10
+    assert relerr(x, xo) <= 1e-8
+    if prec == 0:
+        assert abs(info.iters - io.iters) <= 0.5, (info.iters, io.iters)
+
+
+@pytest.mark.parametrize("variant", [0, 1])
+@pytest.mark.parametrize("prec", [0, 1])
+def test_adjoint_and_grad_parity(sap, variant, prec):
+    N, K, P = 5003, 30, 5
+    band, xt, b = make(N, K, 1.0, 700)
+    g = G.adjoint_seed(N, 700)
+    lo, io, _ = O.solve_adjoint(band, N, K, g, P, variant)
+    xo, _, _ = O.solve(band, N, K, b, P, variant)
+    h = sap.sap_factor(dev(band), N, K, P=P, variant=variant, precision=prec)
+    lam, info, st = sap.sap_solve_adjoint(h, dev(g))
+    assert st == sap.SAP_OK and info.relres <= 1e-10
+    assert relerr(host(lam), lo) <= 1e-8
+    x, _, _ = sap.sap_solve(h, dev(b))
+    gb = host(sap.sap_grad_band(h, lam, x))
+    gbo = O.grad_band(N, K, lo, xo)
+    assert np.abs(gb - gbo).max() <= 1e-8 * np.abs(gbo).max()
+    pad = np.array([not (0 <= (k % N) + (k // N) - K < N) for k in range(band.size)])
+    assert np.all(gb[pad] == 0.0)
+
+
+def test_autograd_matches_oracle_and_fd(sap):
+    """SapSolve.backward: dl/db = lambda, dl/dband = -lambda x^T (band), checked
+    against the oracle gradient and against central differences (tol 1e-14)."""
+    N, K, P = 1500, 8, 3
+    band, xt, b = make(N, K, 1.0, 800)
+    w = G.adjoint_seed(N, 800)
+    bd = dev(band).requires_grad_(True)
+    bb = dev(b).requires_grad_(True)
+    x = sap.sap_solve_autograd(bd, bb, N, K, P=P, variant=sap.SAP_C, precision=sap.SAP_FP64, tol=1e-14)
+    loss = (x * dev(w)).sum()
+    loss.backward()
+    lo, _, _ = O.solve_adjoint(band, N, K, w, P, O.SAP_C, tol=1e-14)
+    xo, _, _ = O.solve(band, N, K, b, P, O.SAP_C, tol=1e-14)
+    assert relerr(host(bb.grad), lo) <= 1e-8
+    gbo = O.grad_band(N, K, lo, xo)
+    assert np.abs(host(bd.grad) - gbo).max() <= 1e-8 * np.abs(gbo).max()
+    # central differences of the GPU solve on sampled band entries and b entries
+    rng = np.random.default_rng(1)
+    valid = [k for k in range(band.size) if 0 <= (k % N) + (k // N) - K < N]
+
+    def lossf(bnd, rhs):
+        h = sap.sap_factor(dev(bnd), N, K, P=P, variant=sap.SAP_C, precision=sap.SAP_FP64, tol=1e-14)
+        xx, _, _ = sap.sap_solve(h, dev(rhs))
+        return float(host(xx) @ w)
+
+    gband = host(bd.grad)
+    for k in rng.choice(valid, 12, replace=False):
+        hstep = 1e-5 * max(1.0, abs(band[k]))
+        bp, bm = band.copy(), band.copy()
+        bp[k] += hstep
+        bm[k] -= hstep
+        fd = (lossf(bp, b) - lossf(bm, b)) / (2 * hstep)
+        assert abs(fd - gband[k]) <= 1e-6 * max(1.0, abs(gband[k])), (k, fd, gband[k])
+
+
+# ------------------------------------------------------------ edge cases --
+
+def test_invalid_arguments(sap):
+    N, K = 100, 10
+    band = dev(G.dense_banded(N, K, 1.0, 1))
+    with pytest.raises(sap.SapError) as e:
+        sap.sap_factor(band, N, K, P=8, variant=sap.SAP_C)        # N_i = 12 < 2K
+    assert e.value.status == sap.SAP_ERR_INVALID_ARG
+    with pytest.raises(sap.SapError):
+        sap.sap_factor(band, N, N, P=1)                            # K >= N
+    with pytest.raises(sap.SapError):
+        sap.sap_factor(band, N, K, P=0)
+    with pytest.raises(sap.SapError) as e:
+        sap.sap_factor(dev(G.dense_banded(400, 150, 1.0, 1)), 400, 150, P=1)
+    assert e.value.status == sap.SAP_ERR_NOT_IMPLEMENTED
+
+
+def test_zero_rhs_and_p1_exact(sap):
+    N, K = 3000, 12
+    band, xt, b = make(N, K, 1.0, 900)
+    h = sap.sap_factor(dev(band), N, K, P=1, precision=sap.SAP_FP64)
+    x, info, st = sap.sap_solve(h, dev(np.zeros(N)))
+    assert st == sap.SAP_OK and np.all(host(x) == 0.0)
+    x, info, st = sap.sap_solve(h, dev(b))
+    assert st == sap.SAP_OK and info.iters == 0.25 and info.n_matvec == 1
+    assert relerr(host(x), xt) <= 1e-10
+
+
+def test_boosted_pivot_matches_oracle(sap):
+    """A zero pivot (Sec. 2.2) is boosted to +tau on both sides."""
+    N, K = 64, 2
+    A = np.diag(np.full(N, 4.0)) + np.diag(np.ones(N - 1), 1) + np.diag(np.ones(N - 1), -1)
+    A[3, 3] = 0.0
+    A[3, 2] = A[2, 3] = 0.0
+    from tests._dense import dense_to_band
+    band = dense_to_band(A, K)
+    eps = 1e-3 / np.abs(A).max()
+    h = sap.sap_factor(dev(band), N, K, P=1, precision=sap.SAP_FP64, boost_eps=eps)
+    o = O.Sap(band, N, K, 1, O.SAP_D, boost_eps=eps)
+    assert sap.sap_n_boosted(h) == o.n_boosted == 1
+    np.testing.assert_allclose(sap.sap_get_block_lu(h, 0), o.block(0, 0), rtol=1e-13, atol=1e-15)
+
+
+def test_not_converged_status(sap):
+    N, K, P = 4000, 4, 400
+    band, xt, b = make(N, K, 0.3, 901)
+    h = sap.sap_factor(dev(band), N, K, P=P, variant=sap.SAP_D, precision=sap.SAP_FP64, max_iters=1)
+    x, info, st = sap.sap_solve(h, dev(b), raise_on_error=False)
+    assert st in (sap.SAP_ERR_NOT_CONVERGED, sap.SAP_OK)
+    if st == sap.SAP_ERR_NOT_CONVERGED:
+        assert info.relres > 1e-10
+
+
+# ------------------------------------------------ full-size configuration --
+
+def test_full_size_dense_banded_n200k_k50_p50(sap):
+    """The N=200000, K=50, d=1, P=50 workload: SaP-D and SaP-C, FP64 and FP32
+    preconditioners, against the oracle's solution."""
+    N, K, P = 200000, 50, 50
+    band, xt, b = make(N, K, 1.0, G.config_seed(2))
+    bd = dev(band)
+    for variant in (0, 1):
+        xo, io, _ = O.solve(band, N, K, b, P, variant)
+        for prec in (0, 1):
+            h = sap.sap_factor(bd, N, K, P=P, variant=variant, precision=prec)
+            x, info, st = sap.sap_solve(h, dev(b))
+            assert st == sap.SAP_OK and info.relres <= 1e-10
+            assert relerr(host(x), xo) <= 1e-8

@@ -1,0 +1,368 @@
+"""Benchmark: time to true relative residual 1e-10, forward + adjoint, of the
+dense-banded SaP solver on one GB300 (and N independent replicas under
+torchrun).
+
+Workload (default): dense banded N = 200,000, K = 50, d = 1.0, P = 50,
+off-diagonals U(-1,1), x_true ~ U(-1,1), b = A x_true, adjoint right-hand
+side g-bar ~ U(-1,1).  One step = refactor of the SaP preconditioner (FP32
+factors) + BiCGStab(2) solve of A x = b + adjoint solve of A^T lambda = g-bar,
+each to relres <= 1e-10 (the FP64 SaP is timed the same way for comparison).
+Inputs are resident in HBM before timing; L2 (129 MB) is flushed before
+every timed step by writing a 512 MB buffer.
+
+`python bench.py --impl reference` times the FP64 CPU oracle (the
+repository's plain C reference) on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "time to rel.res 1e-10 & HBM GB/s: FP32-precond vs FP64 SaP, fwd+adjoint"
+WORKLOADS = {
+    "n200k_k50": dict(N=200000, K=50, d=1.0, P=50, seed_cfg=2),
+    "n10k_k10": dict(N=10000, K=10, d=1.2, P=8, seed_cfg=1),
+}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="n200k_k50", choices=sorted(WORKLOADS))
+    ap.add_argument("--variant", default="C", choices=["C", "D"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-compare", action="store_true", help="skip the FP64 / other-variant comparison runs")
+    return ap.parse_args()
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+# ----------------------------------------------------------------- inputs --
+
+def make_inputs(w):
+    import sap_inputs as G
+    seed = G.config_seed(w["seed_cfg"])
+    band = G.dense_banded(w["N"], w["K"], w["d"], seed)
+    xt = G.x_true(w["N"], seed)
+    g = G.adjoint_seed(w["N"], seed)
+    return band, xt, g
+
+
+# ------------------------------------------------------------- CPU oracle --
+
+def oracle_step(band, b, g, w, variant):
+    """One fwd + adjoint time-to-solution with the FP64 CPU oracle."""
+    import oracle as O
+    N, K, P = w["N"], w["K"], w["P"]
+    var = O.SAP_C if variant == "C" else O.SAP_D
+    s = O.Sap(band, N, K, P, var)
+    x, i1 = s.solve(b)
+    lam, i2, _ = O.solve_adjoint(band, N, K, g, P, var)
+    assert i1.status == O.OK and i2.status == O.OK
+    return i1, i2
+
+
+def cpu_baseline(w, variant, band, b, g, reps=1):
+    import oracle as O  # noqa: F401
+    ts = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        oracle_step(band, b, g, w, variant)
+        ts.append((time.perf_counter() - t0) * 1e3)
+    return {"value": statistics.median(ts), "unit": "ms", "cores": 1, "kind": "oracle",
+            "sample": f"the full workload, {reps} run(s) of factor + solve + adjoint solve "
+                      f"(single-threaded FP64 C oracle, SaP-{variant})"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    w = WORKLOADS[args.workload]
+    import oracle as O
+    band, xt, g = make_inputs(w)
+    b = O.spmv(band, w["N"], w["K"], xt)
+    for _ in range(args.warmup):
+        oracle_step(band, b, g, w, args.variant)
+    ts = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle_step(band, b, g, w, args.variant)
+        ts.append((time.perf_counter() - t0) * 1e3)
+    v = statistics.mean(ts)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "ms", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": v, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(args, w),
+            "cpu_baseline": {"value": v, "unit": "ms", "cores": 1, "kind": "oracle",
+                             "sample": "each step: the full workload, factor + solve + adjoint solve "
+                                       "(single-threaded FP64 C oracle)"},
+            "e2e": {"value": v, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def workload_config(args, w):
+    return {"workload": f"dense banded N={w['N']} K={w['K']} d={w['d']} P={w['P']} SaP-{args.variant}, "
+                        f"FP32 preconditioner + FP64 BiCGStab(2), fwd + adjoint to relres 1e-10",
+            "N": w["N"], "K": w["K"], "P": w["P"], "d": w["d"], "variant": f"SaP-{args.variant}",
+            "l2": "flushed (512 MB write) before every timed step"}
+
+
+# ------------------------------------------------------------------- GPU --
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, gpu_index):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={gpu_index}", f"--query-gpu={q}",
+                                       "--format=csv,noheader,nounits", "-lms", "100"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        self.p.wait()
+        self.f.flush()
+        rows = [r.split(",") for r in open(self.f.name).read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm = [float(r[1]) for r in rows if len(r) >= 9 and r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if len(r) >= 9 and r[2].strip().replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            if len(r) < 9:
+                continue
+            for k, name in enumerate(names):
+                if r[5 + k].strip().lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    import paper_1509_07919_gb300 as S
+
+    w = WORKLOADS[args.workload]
+    N, K, P = w["N"], w["K"], w["P"]
+    variant = S.SAP_C if args.variant == "C" else S.SAP_D
+    band_np, xt_np, g_np = make_inputs(w)
+    band = torch.from_numpy(band_np).cuda()
+    xt = torch.from_numpy(xt_np).cuda()
+    g = torch.from_numpy(g_np).cuda()
+    b = S.sap_spmv(band, N, K, xt)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def make_handle(prec, var):
+        return S.sap_factor(band, N, K, P=P, variant=var, precision=prec)
+
+    def step(h, x, lam):
+        S.sap_refactor(h)
+        _, i1, _ = S.sap_solve(h, b, x)
+        _, i2, _ = S.sap_solve_adjoint(h, g, lam)
+        return i1, i2
+
+    def timed(h, steps, warmup, clocks=False):
+        x = torch.empty_like(b)
+        lam = torch.empty_like(b)
+        for _ in range(warmup):
+            step(h, x, lam)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        ck = Clocks(local) if clocks else None
+        l0 = S.sap_kernel_launches()
+        times, infos = [], []
+        for _ in range(steps):
+            flush.fill_(1.0)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            i1, i2 = step(h, x, lam)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+            infos.append((i1, i2))
+        launches = S.sap_kernel_launches() - l0
+        ckd = ck.stop() if ck else None
+        return times, infos, launches, ckd, x, lam
+
+    h = make_handle(S.SAP_FP32, variant)
+    times, infos, launches, clocks, x, lam = timed(h, args.steps, args.warmup, clocks=True)
+    ms = statistics.mean(times)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    i1, i2 = infos[-1]
+    # accuracy against the generating solution
+    err_x = float(torch.linalg.norm(x - xt) / torch.linalg.norm(xt))
+
+    # ---- phase split and the dominant kernel's live duration ----
+    t_lu = statistics.mean([a.t_lu_ms for a, _ in infos])
+    t_ul = statistics.mean([a.t_ul_ms for a, _ in infos])
+    t_spk = statistics.mean([a.t_spk_ms for a, _ in infos])
+    t_fwd = statistics.mean([a.t_solve_ms for a, _ in infos])
+    t_adj = statistics.mean([b_.t_solve_ms for _, b_ in infos])
+
+    # per-kernel timing with events on the launching stream (inside this run)
+    def kernel_ms(fn, reps=20):
+        for _ in range(3):
+            fn()
+        flush.fill_(2.0)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    y = torch.empty_like(b)
+    z = torch.empty_like(b)
+    t_spmv = kernel_ms(lambda: S.sap_spmv(band, N, K, xt, y))
+    t_apply = kernel_ms(lambda: S.sap_apply_preconditioner(h, b, z))
+    W = 2 * K + 1
+    hbm_peak, peak_kind = load_peaks()
+    lu_bytes = 8 * N * W + 4 * N * W               # read the FP64 band, write FP32 factors
+    spmv_bytes = 8 * N * W + 16 * N
+    apply_bytes = (4 * N * W + 16 * N) * (2 if variant == S.SAP_C else 1)
+    kernels = {
+        "band_lu": {"ms": t_lu, "bytes": lu_bytes, "GBs": lu_bytes / (t_lu * 1e6)},
+        "spmv_fp64": {"ms": t_spmv, "bytes": spmv_bytes, "GBs": spmv_bytes / (t_spmv * 1e6),
+                      "fp64_TFLOPs": 2 * N * W / (t_spmv * 1e9)},
+        "apply_fp32": {"ms": t_apply, "bytes": apply_bytes, "GBs": apply_bytes / (t_apply * 1e6)},
+    }
+    dom = "band_lu"
+    ach = kernels[dom]["GBs"]
+    roofline = {"bound": "hbm", "kernel": "k_band_lu (block LU, FP32 factors)", "achieved": ach,
+                "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak,
+                "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else
+                "fallback 6.8 TB/s", "traffic": None,
+                "algorithmic_bytes_per_launch": lu_bytes,
+                "note": "latency-bound: N_i dependent elimination steps per block, one CTA per block"}
+
+    # ---- end to end through the public API with host buffers ----
+    band_h = torch.from_numpy(band_np).pin_memory()
+    b_h = b.cpu().pin_memory()
+    g_h = g.cpu().pin_memory()
+    x_h = torch.empty_like(b_h).pin_memory()
+    l_h = torch.empty_like(b_h).pin_memory()
+    band_d2 = torch.empty_like(band)
+    b_d2 = torch.empty_like(b)
+    g_d2 = torch.empty_like(g)
+    h2 = S.sap_factor(band_d2.copy_(band), N, K, P=P, variant=variant, precision=S.SAP_FP32)
+    xe = torch.empty_like(b)
+    le = torch.empty_like(b)
+    e2e_times = []
+    for k in range(args.warmup + args.steps):
+        flush.fill_(3.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        band_d2.copy_(band_h, non_blocking=True)
+        b_d2.copy_(b_h, non_blocking=True)
+        g_d2.copy_(g_h, non_blocking=True)
+        S.sap_refactor(h2)
+        S.sap_solve(h2, b_d2, xe)
+        S.sap_solve_adjoint(h2, g_d2, le)
+        x_h.copy_(xe, non_blocking=True)
+        l_h.copy_(le, non_blocking=True)
+        torch.cuda.synchronize()
+        if k >= args.warmup:
+            e2e_times.append((time.perf_counter() - t0) * 1e3)
+    e2e_ms = statistics.mean(e2e_times)
+    del h2
+
+    # ---- comparison: FP64 SaP and the other variant (same protocol, fewer steps) ----
+    compare = {}
+    if not args.no_compare:
+        for name, prec, var in (("sapc_fp64", S.SAP_FP64, S.SAP_C), ("sapd_fp64", S.SAP_FP64, S.SAP_D),
+                                ("sapc_fp32", S.SAP_FP32, S.SAP_C), ("sapd_fp32", S.SAP_FP32, S.SAP_D)):
+            hh = make_handle(prec, var)
+            tt, inf, _, _, _, _ = timed(hh, max(3, args.steps // 2), 2)
+            a, c = inf[-1]
+            compare[name] = {"ms": statistics.mean(tt), "iters_fwd": a.iters, "iters_adj": c.iters,
+                             "relres_fwd": a.relres, "relres_adj": c.relres,
+                             "t_factor_ms": a.t_factor_ms, "t_fwd_ms": a.t_solve_ms, "t_adj_ms": c.t_solve_ms}
+            del hh
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(w, args.variant, band_np, b.cpu().numpy(), g_np)
+
+    if rank == 0:
+        # replicas: every rank solves its own system; job-level time per system
+        line = {
+            "metric": METRIC, "value": ms / world, "unit": "ms",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64", "data": "synthetic",
+            "config": workload_config(args, w),
+            "clocks": clocks,
+            "e2e": {"value": e2e_ms, "unit": "ms",
+                    "h2d_bytes_per_step": int(band_h.numel() * 8 + b_h.numel() * 8 + g_h.numel() * 8),
+                    "d2h_bytes_per_step": int(x_h.numel() * 8 + l_h.numel() * 8)},
+            "gpu_launches": int(launches),
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "detail": {"iters_fwd": i1.iters, "iters_adj": i2.iters, "relres_fwd": i1.relres,
+                       "relres_adj": i2.relres, "err_x_vs_x_true": err_x, "n_boosted": i1.n_boosted,
+                       "t_lu_ms": t_lu, "t_ul_ms": t_ul, "t_spk_ms": t_spk, "t_fwd_solve_ms": t_fwd,
+                       "t_adj_solve_ms": t_adj, "kernels": kernels, "compare": compare,
+                       "paper_context_ms_k20x": {"SaP-D": 187.717, "SaP-C": 186.756,
+                                                 "note": "fwd only, K20X, precision unstated"}},
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -77,8 +77,11 @@ typedef struct {
     int64_t n_boosted;    /* boosted pivots in all LU and UL factorisations */
     int64_t n_matvec;     /* preconditioned matvecs M^{-1} A v performed */
     int64_t n_restarts;   /* residual replacements after a failed true-residual check */
-    float t_factor_ms;    /* device time of the factorisation (LU, BC, SPK, LUrdcd) */
+    float t_factor_ms;    /* device time of the last factorisation (all phases) */
     float t_solve_ms;     /* device time of the Krylov phase of the last solve */
+    float t_lu_ms;        /* factor phase T_LU: block LU (and the boost-threshold pass) */
+    float t_ul_ms;        /* SaP-C: block UL (top tiles only) */
+    float t_spk_ms;       /* SaP-C: B/C, spike tips, Rbar_i, its GEPP and inverse */
 } sap_info_t;
 
 /* Defaults as documented above. */
@@ -99,6 +102,11 @@ SAP_API void sap_default_options(sap_options_t *opt);
 SAP_API sap_status_t sap_factor(const double *band_dev, int64_t N, int32_t K,
                         const sap_options_t *opt, cudaStream_t stream,
                         sap_handle_t *out);
+
+/* Recompute the factorisation in place after the values of the borrowed
+ * band changed (same N, K, options; no allocation).  The adjoint reduced
+ * matrices are rebuilt on the next adjoint call.  Synchronises `stream`. */
+SAP_API sap_status_t sap_refactor(sap_handle_t h, cudaStream_t stream);
 
 /* Solve A x = b by left-preconditioned BiCGStab(2) (Sec. 2.1.1) from
  * x0 = 0 to the handle's tolerance.  b_dev, x_dev: device, length N, must

@@ -40,7 +40,8 @@ class sap_options_t(C.Structure):
 class sap_info_t(C.Structure):
     _fields_ = [("iters", C.c_double), ("relres", C.c_double), ("n_boosted", C.c_int64),
                 ("n_matvec", C.c_int64), ("n_restarts", C.c_int64),
-                ("t_factor_ms", C.c_float), ("t_solve_ms", C.c_float)]
+                ("t_factor_ms", C.c_float), ("t_solve_ms", C.c_float), ("t_lu_ms", C.c_float),
+                ("t_ul_ms", C.c_float), ("t_spk_ms", C.c_float)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -55,6 +56,7 @@ def _load():
     sig = {
         "sap_default_options": (None, [P(sap_options_t)]),
         "sap_factor": (C.c_int, [vp, i64, i32, P(sap_options_t), vp, P(vp)]),
+        "sap_refactor": (C.c_int, [vp, vp]),
         "sap_solve": (C.c_int, [vp, vp, vp, P(sap_info_t), vp]),
         "sap_solve_adjoint": (C.c_int, [vp, vp, vp, P(sap_info_t), vp]),
         "sap_grad_band": (C.c_int, [vp, vp, vp, vp, vp]),
@@ -134,6 +136,11 @@ def sap_factor(band: torch.Tensor, N: int, K: int, opts: sap_options_t | None = 
     st = _lib.sap_factor(_ptr(band), N, K, C.byref(opts), _stream(stream), C.byref(out))
     _check(st, "sap_factor")
     return Handle(out.value, band, N, K, opts)
+
+
+def sap_refactor(h: Handle, stream=None) -> None:
+    """Refactor after the values of h.band changed (no allocation)."""
+    _check(_lib.sap_refactor(h.ptr, _stream(stream)), "sap_refactor")
 
 
 def sap_solve(h: Handle, b: torch.Tensor, x: torch.Tensor | None = None, stream=None,

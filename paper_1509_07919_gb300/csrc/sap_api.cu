@@ -54,6 +54,7 @@ struct DevMem {
 // Precision-independent part of the solver.
 struct SolverBase {
   virtual ~SolverBase() = default;
+  virtual sap_status_t alloc() = 0;
   virtual sap_status_t factor(cudaStream_t s) = 0;
   virtual sap_status_t build_adjoint(cudaStream_t s) = 0;
   virtual sap_status_t apply(const double* r, double* z, bool transpose, cudaStream_t s) = 0;
@@ -77,13 +78,16 @@ struct sap_handle {
   KrylovDev kd{};
   double* host_s = nullptr;   // pinned scalar readback
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-  float t_factor_ms = 0.f;
+  cudaEvent_t evp[4] = {nullptr, nullptr, nullptr, nullptr};
+  float t_factor_ms = 0.f, t_lu_ms = 0.f, t_ul_ms = 0.f, t_spk_ms = 0.f;
   double* host_stage = nullptr;  // 2 N doubles for sap_solve_host, allocated on first use
   std::unique_ptr<SolverBase> impl;
   ~sap_handle() {
     if (host_s) cudaFreeHost(host_s);
     if (ev0) cudaEventDestroy(ev0);
     if (ev1) cudaEventDestroy(ev1);
+    for (cudaEvent_t e : evp)
+      if (e) cudaEventDestroy(e);
   }
 };
 
@@ -97,16 +101,13 @@ struct Solver : SolverBase {
   bool adjoint_ready = false;
   explicit Solver(sap_handle* hh) : h(hh) {}
 
-  sap_status_t factor(cudaStream_t s) override {
+  sap_status_t alloc() override {
     const Layout& L = h->L;
     const int K = L.K, P = L.P;
     const int64_t KK = (int64_t)K * K;
     const int nI = P > 1 ? P - 1 : 1;
     TRY(h->mem.alloc(&f.F, (size_t)L.f_elems));
     TRY(h->mem.alloc(&scratch, (size_t)(2 * L.N + 2 * nI * K + 8)));
-    const double eps = h->opt.boost_eps;
-    CK(launch_absmax(h->band, L.N, K, h->absmax, s));
-    CK(launch_factor_lu<T>(h->band, L.N, K, P, h->d, h->absmax, eps, f.F, h->n_boosted, s));
     if (h->opt.variant == SAP_C && P > 1) {
       TRY(h->mem.alloc(&f.ULt, (size_t)(nI * KK)));
       TRY(h->mem.alloc(&f.V, (size_t)(nI * KK)));
@@ -114,10 +115,30 @@ struct Solver : SolverBase {
       TRY(h->mem.alloc(&f.R, (size_t)(nI * KK)));
       TRY(h->mem.alloc(&f.R0, (size_t)(nI * KK)));
       TRY(h->mem.alloc(&f.piv, (size_t)(nI * K)));
+    }
+    return SAP_OK;
+  }
+
+  // Factor phases, each bracketed by events ev[0..4]: T_LU (absmax + LU),
+  // T_UL, T_SPK (B/C, tips, Rbar, its GEPP and inverse).
+  sap_status_t factor(cudaStream_t s) override {
+    const Layout& L = h->L;
+    const int K = L.K, P = L.P;
+    const double eps = h->opt.boost_eps;
+    adjoint_ready = false;
+    CK(cudaEventRecord(h->evp[0], s));
+    CK(launch_absmax(h->band, L.N, K, h->absmax, s));
+    CK(launch_factor_lu<T>(h->band, L.N, K, P, h->d, h->absmax, eps, f.F, h->n_boosted, s));
+    CK(cudaEventRecord(h->evp[1], s));
+    if (h->opt.variant == SAP_C && P > 1) {
       CK(launch_factor_ul<T>(h->band, L.N, K, P, h->d, h->absmax, eps, f.ULt, h->n_boosted, s));
+      CK(cudaEventRecord(h->evp[2], s));
       CK(launch_spikes<T>(h->band, L.N, K, P, h->d, f.F, f.ULt, false, f.V, f.Wt, f.R, f.R0, f.piv,
                           h->singular, s));
+    } else {
+      CK(cudaEventRecord(h->evp[2], s));
     }
+    CK(cudaEventRecord(h->evp[3], s));
     return SAP_OK;
   }
 
@@ -125,11 +146,13 @@ struct Solver : SolverBase {
     if (adjoint_ready || h->opt.variant != SAP_C || h->L.P < 2) return SAP_OK;
     const int K = h->L.K, nI = h->L.P - 1;
     const int64_t KK = (int64_t)K * K;
-    TRY(h->mem.alloc(&f.Va, (size_t)(nI * KK)));
-    TRY(h->mem.alloc(&f.Wa, (size_t)(nI * KK)));
-    TRY(h->mem.alloc(&f.Ra, (size_t)(nI * KK)));
-    TRY(h->mem.alloc(&f.Ra0, (size_t)(nI * KK)));
-    TRY(h->mem.alloc(&f.piva, (size_t)(nI * K)));
+    if (!f.Va) {
+      TRY(h->mem.alloc(&f.Va, (size_t)(nI * KK)));
+      TRY(h->mem.alloc(&f.Wa, (size_t)(nI * KK)));
+      TRY(h->mem.alloc(&f.Ra, (size_t)(nI * KK)));
+      TRY(h->mem.alloc(&f.Ra0, (size_t)(nI * KK)));
+      TRY(h->mem.alloc(&f.piva, (size_t)(nI * K)));
+    }
     CK(launch_spikes<T>(h->band, h->L.N, K, h->L.P, h->d, f.F, f.ULt, true, f.Va, f.Wa, f.Ra, f.Ra0, f.piva,
                         h->singular, s));
     int sing = 0;
@@ -309,11 +332,30 @@ sap_status_t krylov(sap_handle* h, const double* b, double* x, bool tr, sap_info
   inf.n_matvec = nmv;
   inf.t_solve_ms = ms;
   inf.t_factor_ms = h->t_factor_ms;
+  inf.t_lu_ms = h->t_lu_ms;
+  inf.t_ul_ms = h->t_ul_ms;
+  inf.t_spk_ms = h->t_spk_ms;
   unsigned long long nb = 0;
   CK(cudaMemcpy(&nb, h->n_boosted, sizeof(nb), cudaMemcpyDeviceToHost));
   inf.n_boosted = (int64_t)nb;
   if (info) *info = inf;
   return status;
+}
+
+sap_status_t run_factor(sap_handle* h, cudaStream_t s) {
+  CK(cudaMemsetAsync(h->n_boosted, 0, sizeof(unsigned long long), s));
+  CK(cudaMemsetAsync(h->singular, 0, sizeof(int), s));
+  TRY(h->impl->factor(s));
+  CK(cudaEventSynchronize(h->evp[3]));
+  CK(cudaGetLastError());
+  cudaEventElapsedTime(&h->t_lu_ms, h->evp[0], h->evp[1]);
+  cudaEventElapsedTime(&h->t_ul_ms, h->evp[1], h->evp[2]);
+  cudaEventElapsedTime(&h->t_spk_ms, h->evp[2], h->evp[3]);
+  cudaEventElapsedTime(&h->t_factor_ms, h->evp[0], h->evp[3]);
+  int sing = 0;
+  CK(cudaMemcpy(&sing, h->singular, sizeof(int), cudaMemcpyDeviceToHost));
+  if (sing) return SAP_ERR_SINGULAR;
+  return SAP_OK;
 }
 
 }  // namespace
@@ -396,19 +438,18 @@ sap_status_t sap_factor(const double* band_dev, int64_t N, int32_t K, const sap_
   if (cudaMallocHost(&h->host_s, 16 * sizeof(double)) != cudaSuccess) return SAP_ERR_OOM;
   CK(cudaEventCreate(&h->ev0));
   CK(cudaEventCreate(&h->ev1));
+  for (auto& e : h->evp) CK(cudaEventCreate(&e));
   if (opt.precision == SAP_FP64) h->impl.reset(new Solver<double>(h.get()));
   else h->impl.reset(new Solver<float>(h.get()));
-  CK(cudaEventRecord(h->ev0, s));
-  TRY(h->impl->factor(s));
-  CK(cudaEventRecord(h->ev1, s));
-  CK(cudaEventSynchronize(h->ev1));
-  CK(cudaGetLastError());
-  cudaEventElapsedTime(&h->t_factor_ms, h->ev0, h->ev1);
-  int sing = 0;
-  CK(cudaMemcpy(&sing, h->singular, sizeof(int), cudaMemcpyDeviceToHost));
-  if (sing) return SAP_ERR_SINGULAR;
+  TRY(h->impl->alloc());
+  TRY(run_factor(h.get(), s));
   *out = h.release();
   return SAP_OK;
+}
+
+sap_status_t sap_refactor(sap_handle_t h, cudaStream_t s) {
+  if (!h) return SAP_ERR_INVALID_ARG;
+  return run_factor(h, s);
 }
 
 sap_status_t sap_solve(sap_handle_t h, const double* b, double* x, sap_info_t* info, cudaStream_t s) {

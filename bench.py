@@ -344,7 +344,9 @@ def run_gpu(args):
             "gpu_launches": int(launches),
             "roofline": roofline,
             "cpu_baseline": cpu,
-            "detail": {"iters_fwd": i1.iters, "iters_adj": i2.iters, "relres_fwd": i1.relres,
+            "detail": {"iters_fwd": i1.iters, "iters_adj": i2.iters, "matvecs_fwd": i1.n_matvec,
+                       "matvecs_adj": i2.n_matvec, "restarts_fwd": i1.n_restarts,
+                       "restarts_adj": i2.n_restarts, "relres_fwd": i1.relres,
                        "relres_adj": i2.relres, "err_x_vs_x_true": err_x, "n_boosted": i1.n_boosted,
                        "t_lu_ms": t_lu, "t_ul_ms": t_ul, "t_spk_ms": t_spk, "t_fwd_solve_ms": t_fwd,
                        "t_adj_solve_ms": t_adj, "kernels": kernels, "compare": compare,

@@ -4,20 +4,25 @@
 // solves that follow them.
 //
 // Sweep kernel: one CTA (4 warps) per block, both sweeps in one launch.  A
-// sweep is a linear recurrence over positions p = 0..n-1,
+// sweep is a linear recurrence over positions p (rows in sweep order),
 //     z_p = ( y_p - sum_{d=1..K} coef(p, d) z_{p-d} ) / diag(p),
 // processed in chunks of 32 positions:
 //   - warp 0 (the solver) runs the dependent chain of a chunk: lane t holds
 //     row t; for j = 0..31 it broadcasts z_j with one shuffle and every
-//     lane applies the in-chunk coefficient and, at the same time, the
-//     coefficient that couples row t of the *next* chunk to z_j;
-//   - warps 1..3 (helpers) prepare the next chunk meanwhile: they load the
-//     right-hand side and the coefficients (pre-scaled by 1/diag, so the
-//     chain has no division) into shared memory, and sum the "older"
-//     contributions (d > 32 + t) from a shared-memory ring of past z.
+//     lane applies its in-chunk coefficient and, in the same step, the
+//     coefficient that couples row t of the *next* chunk to z_j.  The
+//     coefficients are pre-scaled by 1/diag off the chain, so one step of
+//     the chain is one shuffle and one FMA;
+//   - warps 1..7 (helpers) stream the factor columns of later chunks into a
+//     shared-memory ring with cp.async (PF chunks ahead) and sum the
+//     "older" contributions (d > 32 + t) of the next chunk from that ring
+//     and a ring of past z.
 // The four sweep kinds (L forward, U backward, U^T forward, L^T backward)
-// differ only in how (p, d) maps to the factor storage
-//   F[c * ld + q] = entry (r, q) of block i, c = K + r - q.
+// differ only in which diagonals are staged and where a row's coefficients
+// sit: factor storage is F[c * ld + q] = entry (r, q), c = K + r - q.
+// Positions run over [0, ld) (ld = n rounded up to 32); a backward sweep
+// maps row r to p = ld - 1 - r.  Positions without a row are padding and
+// produce z = 0.
 #include <cuda_runtime.h>
 #include <cstdint>
 #include "sap_internal.cuh"
@@ -26,192 +31,308 @@ namespace sap {
 
 namespace {
 
-constexpr int NW = 4;               // warps per sweep CTA
+constexpr int NW = 8;               // warps per sweep CTA: 1 solver + 7 helpers
 constexpr int CHK = 32;             // chunk length
 
 enum Mode { LF = 0, UB = 1, UTF = 2, LTB = 3 };
 
-template <int MODE>
-__device__ __forceinline__ int64_t row_of(int64_t p, int64_t n) {
-  return (MODE == LF || MODE == UTF) ? p : n - 1 - p;
-}
-// address of coef(p, d) (row r = row_of(p)), valid for 1 <= d <= K, d <= p
-template <int MODE>
-__device__ __forceinline__ int64_t coef_idx(int64_t r, int d, int K, int64_t ld) {
-  if (MODE == LF) return (int64_t)(K + d) * ld + r - d;   // l(r, r-d)
-  if (MODE == UB) return (int64_t)(K - d) * ld + r + d;   // u(r, r+d)
-  if (MODE == UTF) return (int64_t)(K - d) * ld + r;      // u(r-d, r)
-  return (int64_t)(K + d) * ld + r;                       // l(r+d, r)
-}
+template <int MODE> __device__ __forceinline__ constexpr bool fwd_mode() { return MODE == LF || MODE == UTF; }
 template <int MODE> __device__ __forceinline__ constexpr bool unit_diag() { return MODE == LF || MODE == LTB; }
-
-template <typename T> __device__ __forceinline__ T to_t(double v) { return (T)v; }
-
-struct SweepIO {
-  // input: y(r) = in[r] - corrections (top rows: ctop[r], bottom rows: cbot[r-(n-K)])
-  const double* in_d;      // FP64 input (first sweep)
-  const void* in_t;        // T input (second sweep), or nullptr
-  const double* ctop;      // K corrections for rows 0..K-1, or nullptr
-  const double* cbot;      // K corrections for rows n-K..n-1, or nullptr
-  double* out_d;           // FP64 output or nullptr
-  void* out_t;             // T output or nullptr
-};
-
-template <typename T>
-struct SweepSmem {
-  T coef1[2][CHK][CHK];   // [buf][j][t]: in-chunk coefficient of row t on z_j
-  T coef2[2][CHK][CHK];   // [buf][j][t]: row t of the next chunk on z_j of this chunk
-  T yhat[2][CHK];
-  T older[2][NW - 1][CHK];
-};
-
-template <typename T, int MODE>
-__device__ __forceinline__ T load_y(const SweepIO& io, int64_t r, int64_t n, int K) {
-  if (io.in_t) return reinterpret_cast<const T*>(io.in_t)[r];
-  double v = io.in_d[r];
-  if (io.ctop && r < K) v -= io.ctop[r];
-  if (io.cbot && r >= n - K) v -= io.cbot[r - (n - K)];
-  return to_t<T>(v);
+// row-oriented: coef(p, d) sits in column position p - d; column-oriented: in p
+template <int MODE> __device__ __forceinline__ constexpr bool row_oriented() { return MODE == LF || MODE == UB; }
+// diagonal c of the factor for distance d
+template <int MODE> __device__ __forceinline__ int diag_of(int K, int d) {
+  return (MODE == LF || MODE == LTB) ? K + d : K - d;
 }
 
-// Helpers (warps 1..NW-1): prepare chunk c (yhat, coef1, older) and coef2 of chunk c+1.
-template <typename T, int MODE>
-__device__ __forceinline__ void stage_chunk(SweepSmem<T>& sm, const T* __restrict__ F, int64_t ld, int K,
-                                            int64_t n, int64_t c, const SweepIO& io, const T* ring,
-                                            int ringmask) {
-  const int ht = threadIdx.x - 32;           // 0 .. 32*(NW-1)-1
-  const int nh = 32 * (NW - 1);
-  const int lane = threadIdx.x & 31;
-  const int hw = (threadIdx.x >> 5) - 1;     // helper warp index
-  const int buf = c & 1;
-  const int64_t p0 = c * CHK;
-  // yhat and the in-chunk coefficients of chunk c, coef2 of chunk c+1
-  for (int e = ht; e < CHK * CHK * 2 + CHK; e += nh) {
-    if (e < CHK) {
-      int64_t p = p0 + e;
-      T v = T(0);
-      if (p < n) {
-        int64_t r = row_of<MODE>(p, n);
-        v = load_y<T, MODE>(io, r, n, K);
-        if (!unit_diag<MODE>()) v = v / F[(int64_t)K * ld + r];
-      }
-      sm.yhat[buf][e] = v;
-      continue;
-    }
-    int f = e - CHK;
-    int part = f / (CHK * CHK);               // 0 = coef1(c), 1 = coef2(c+1)
-    int g = f % (CHK * CHK);
-    int d = g / CHK + 1;                      // distance 1..32 (coef1) or d-offset (coef2)
-    int t = g % CHK;                          // row lane (coalesced along the diagonal)
-    if (part == 0) {
-      // coef1[j][t], j = t - d, needs 1 <= d <= min(t, K)
-      if (d <= t) {
-        int64_t p = p0 + t;
-        T v = T(0);
-        if (d <= K && p < n) {
-          int64_t r = row_of<MODE>(p, n);
-          v = F[coef_idx<MODE>(r, d, K, ld)];
-          if (!unit_diag<MODE>()) v = v / F[(int64_t)K * ld + r];
-        }
-        sm.coef1[buf][t - d][t] = v;
-      }
-    } else {
-      // coef2 of chunk c+1: row t of chunk c+1 on z_j of chunk c, distance dd = 32 + t - j
-      // here enumerate j = d - 1 (0..31)
-      int j = d - 1;
-      int dd = CHK + t - j;
-      int64_t p = p0 + CHK + t;
-      T v = T(0);
-      if (dd <= K && p < n) {
-        int64_t r = row_of<MODE>(p, n);
-        v = F[coef_idx<MODE>(r, dd, K, ld)];
-        if (!unit_diag<MODE>()) v = v / F[(int64_t)K * ld + r];
-      }
-      sm.coef2[buf][j][t] = v;
+__device__ __forceinline__ void cpa4(void* smem, const void* gmem) {
+  unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cpa8(void* smem, const void* gmem) {
+  unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+template <typename X> __device__ __forceinline__ X rcp_t(X v) { return X(1) / v; }
+template <> __device__ __forceinline__ float rcp_t<float>(float v) { return __frcp_rn(v); }
+template <typename X> __device__ __forceinline__ void cpa(X* smem, const X* gmem) {
+  if (sizeof(X) == 4) cpa4(smem, gmem); else cpa8(smem, gmem);
+}
+__device__ __forceinline__ void cpa_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N_> __device__ __forceinline__ void cpa_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N_) : "memory"); }
+
+struct SweepGeom {
+  int K;
+  int n, ld;     // rows of the block, positions (n rounded up to 32)
+  int RQ;        // ring length in column positions (multiple of 32)
+  int ZR;        // z history ring length (power of 2 >= K + 96)
+  int DR;        // ring rows: distances d = 0 .. DR-1 (DR >= 64; rows > K are zero)
+  int DRP;       // slot pitch of the ring (even, >= DR): R[slot * DRP + d]
+};
+
+template <typename T, typename YT>
+struct SweepSh {
+  T* R;          // RQ x DRP ring of factor columns: R[slot * DRP + d], d = distance
+  YT* Y;         // (PF+1) x 32 ring of right-hand sides
+  T* Z;          // ZR ring of computed z (indexed by position mod ZR, ZR a power of 2)
+  T* C1;         // [2][32][32]: in-chunk coefficients, pre-scaled by 1/diag, [j][t]
+  T* C2;         // [2][32][32]: next-chunk row t on z_j of this chunk, pre-scaled
+  T* YH;         // [2][32]: right-hand side pre-scaled by 1/diag
+  T* older;      // [2][NOLD][32]: contributions of z older than the previous chunk
+  double* corr;  // 2K corrections (top K rows, bottom K rows)
+};
+
+constexpr int NOLD = 3;   // helper warps that sum the older contributions
+
+template <int MODE>
+__device__ __forceinline__ int row_of(int p, int ld) { return fwd_mode<MODE>() ? p : ld - 1 - p; }
+// Ring slot of column position pos (the factor column q = row_of(pos) mod RQ).
+template <int MODE>
+__device__ __forceinline__ int slot_of(int pos, const SweepGeom& g) { return row_of<MODE>(pos, g.ld) % g.RQ; }
+// Slot of pos - d given sl = slot_of(pos), 0 <= d < RQ.
+template <int MODE>
+__device__ __forceinline__ int slot_back(int sl, int d, int RQ) {
+  if (fwd_mode<MODE>()) { int x = sl - d; return x < 0 ? x + RQ : x; }
+  int x = sl + d; return x >= RQ ? x - RQ : x;
+}
+// Slot of p0 + j for a chunk start p0 (multiple of 32) with sb = slot_of(p0): never wraps.
+template <int MODE>
+__device__ __forceinline__ int slot_in_chunk(int sb, int j) { return fwd_mode<MODE>() ? sb + j : sb - j; }
+
+// Helpers: issue the cp.async copies of chunk cc (factor columns and y).
+// Ring rows d = 1..K (and d = 0, the diagonal, for non-unit sweeps) are
+// streamed; rows K+1..DR-1 stay zero for the whole kernel.
+template <typename T, typename YT, int MODE, int PF>
+__device__ __forceinline__ void prefetch(const SweepSh<T, YT>& sh, const SweepGeom& g, const T* __restrict__ F,
+                                         const YT* __restrict__ yin, int cc) {
+  const int p0 = cc * CHK;
+  if (p0 < g.ld) {
+    const int d0 = unit_diag<MODE>() ? 1 : 0;
+    const int sb = slot_of<MODE>(p0, g);
+    const int q0 = row_of<MODE>(p0, g.ld);
+    const int sgn = fwd_mode<MODE>() ? 1 : -1;
+    // helper warp hw copies distances d = d0 + hw, d0 + hw + (NW-1), ... for
+    // column t = lane: 32 consecutive factor columns of one diagonal per warp
+    const int lane = threadIdx.x & 31, hw = (threadIdx.x >> 5) - 1;
+    const int dstep = NW - 1;
+    // the factor diagonal of distance d is K + d (L sweeps) or K - d (U sweeps)
+    const int64_t sstride = (int64_t)((MODE == LF || MODE == LTB) ? 1 : -1) * dstep * g.ld;
+    int d = d0 + hw;
+    const T* src = F + (int64_t)diag_of<MODE>(g.K, d) * g.ld + (q0 + sgn * lane);
+    T* dst = &sh.R[(sb + sgn * lane) * g.DRP + d];
+    for (; d <= g.K; d += dstep, src += sstride, dst += dstep) cpa(dst, src);
+    if (hw == 0) {
+      const int r = q0 + sgn * lane;
+      YT* ydst = &sh.Y[(cc % (PF + 1)) * CHK + lane];
+      if (r < g.n) cpa(ydst, &yin[r]);
+      else *ydst = YT(0);
     }
   }
-  // zero the upper part of coef1 (j >= t) once per buffer use
-  for (int e = ht; e < CHK * CHK; e += nh) {
-    int j = e / CHK, t = e % CHK;
-    if (j >= t) sm.coef1[buf][j][t] = T(0);
+  cpa_commit();
+}
+
+// Helpers: build the pre-scaled tiles of chunk cb (needs ring chunks cb, cb+1)
+// and, in warps 1..NOLD, its older contributions (needs z of chunks <= cb-2).
+template <typename T, typename YT, int MODE, int PF, int DRPC>
+__device__ __forceinline__ void build_tiles(const SweepSh<T, YT>& sh, const SweepGeom& g, int cb,
+                                            bool has_top, bool has_bot) {
+  const int lane = threadIdx.x & 31, hw = (threadIdx.x >> 5) - 1;
+  const int K = g.K, RQ = g.RQ;
+  const int DRP = DRPC ? DRPC : g.DRP;
+  const int buf = cb & 1;
+  const int p0 = cb * CHK;
+  if (p0 >= g.ld) return;
+  const int p = p0 + lane;                  // this lane's row in chunk cb
+  const int p2 = p + CHK;                   // and in chunk cb + 1
+  const bool valid = row_of<MODE>(p, g.ld) < g.n;
+  const bool valid2 = p2 < g.ld && row_of<MODE>(p2, g.ld) < g.n;
+  const int sb = slot_of<MODE>(p0, g);
+  const int sp = slot_in_chunk<MODE>(sb, lane);
+  const int sb2 = p0 + CHK < g.ld ? slot_of<MODE>(p0 + CHK, g) : sb;
+  const int sp2 = slot_in_chunk<MODE>(sb2, lane);
+  T dinv = T(1), dinv2 = T(1);
+  if (!unit_diag<MODE>()) {
+    dinv = valid ? rcp_t(sh.R[sp * DRP]) : T(0);
+    dinv2 = valid2 ? rcp_t(sh.R[sp2 * DRP]) : T(0);
   }
-  // older contributions of chunk c: d in [33 + t, K], z positions < 32 (c-1)
-  {
-    const int t = lane;
-    const int64_t p = p0 + t;
+  T* C1 = sh.C1 + buf * CHK * CHK;
+  T* C2 = sh.C2 + buf * CHK * CHK;
+  for (int j = hw; j < CHK; j += NW - 1) {
+    const int d1 = lane - j, d2 = CHK + lane - j;
+    const int sl1 = row_oriented<MODE>() ? slot_in_chunk<MODE>(sb, j) : sp;
+    const int sl2 = row_oriented<MODE>() ? slot_in_chunk<MODE>(sb, j) : sp2;
+    C1[j * CHK + lane] = (d1 >= 1) ? sh.R[sl1 * DRP + d1] * dinv : T(0);   // rows > K are zero
+    C2[j * CHK + lane] = sh.R[sl2 * DRP + d2] * dinv2;
+  }
+  if (hw == 0) {
+    const int r = row_of<MODE>(p, g.ld);
+    T yv = T(0);
+    if (valid) {
+      yv = (T)sh.Y[(cb % (PF + 1)) * CHK + lane];
+      if (has_top && r < K) yv -= (T)sh.corr[r];
+      if (has_bot && r >= g.n - K) yv -= (T)sh.corr[K + (r - (g.n - K))];
+    }
+    sh.YH[buf * CHK + lane] = yv * dinv;
+  }
+  if (hw < NOLD) {
+    // older contributions of row p: d in [33 + lane, K], z positions <= 32 cb - 33
     T acc = T(0);
-    if (p < n && K > CHK + t) {
-      int64_t r = row_of<MODE>(p, n);
-      T dinv = T(1);
-      if (!unit_diag<MODE>()) dinv = T(1) / F[(int64_t)K * ld + r];
-      for (int d = CHK + 1 + t + hw; d <= K; d += NW - 1) {
-        if (d > p) break;
-        acc += F[coef_idx<MODE>(r, d, K, ld)] * ring[(p - d) & ringmask];
+    if (valid && K > CHK + lane) {
+      const int zp = p & (g.ZR - 1);
+      for (int d = CHK + 1 + lane + hw; d <= K && d <= p; d += NOLD) {
+        const int sl = row_oriented<MODE>() ? slot_back<MODE>(sp, d, RQ) : sp;
+        acc += sh.R[sl * DRP + d] * sh.Z[(zp - d) & (g.ZR - 1)];
       }
       acc *= dinv;
     }
-    sm.older[buf][hw][t] = acc;
+    sh.older[(buf * NOLD + hw) * CHK + lane] = acc;
   }
 }
 
-template <typename T, int MODE>
-__device__ void sweep(SweepSmem<T>& sm, T* ring, int ringmask, const T* __restrict__ F, int64_t ld, int K,
-                      int64_t n, const SweepIO& io) {
+template <typename T, typename YT, int MODE, int PF, int DRPC>
+__device__ void sweep(const SweepSh<T, YT>& sh, const SweepGeom& g, const T* __restrict__ F,
+                      const YT* __restrict__ yin, bool has_top, bool has_bot, double* __restrict__ out_d,
+                      T* __restrict__ out_t) {
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
-  const int64_t nchunks = (n + CHK - 1) / CHK;
-  if (warp > 0) stage_chunk<T, MODE>(sm, F, ld, K, n, 0, io, ring, ringmask);
+  const int nch = g.ld / CHK;
+  // prologue: chunks 0..PF-1 in flight; tiles of chunk 0 need ring chunks 0, 1
+  if (warp > 0) {
+    for (int cc = 0; cc < PF; ++cc) prefetch<T, YT, MODE, PF>(sh, g, F, yin, cc);
+    cpa_wait<PF - 2>();
+  }
   __syncthreads();
-  T recent = T(0);  // warp 0: contribution of the previous chunk to this chunk's row `lane`
-  for (int64_t c = 0; c < nchunks; ++c) {
+  if (warp > 0) {
+    build_tiles<T, YT, MODE, PF, DRPC>(sh, g, 0, has_top, has_bot);
+    cpa_wait<PF - 3>();     // chunk 2 landed: tiles of chunk 1 can be built in iteration 0
+  }
+  __syncthreads();
+  T recent = T(0);   // warp 0: prev-chunk contribution to this chunk's row (pre-scaled)
+  for (int c = 0; c < nch; ++c) {
     const int buf = c & 1;
     if (warp == 0) {
-      T s = sm.yhat[buf][lane] - recent;
+      const T* C1 = sh.C1 + buf * CHK * CHK + lane;
+      const T* C2 = sh.C2 + buf * CHK * CHK + lane;
+      T s = sh.YH[buf * CHK + lane] - recent;
 #pragma unroll
-      for (int w = 0; w < NW - 1; ++w) s -= sm.older[buf][w][lane];
+      for (int w = 0; w < NOLD; ++w) s -= sh.older[(buf * NOLD + w) * CHK + lane];
       T nxt = T(0);
 #pragma unroll
       for (int j = 0; j < CHK; ++j) {
-        T zj = __shfl_sync(0xffffffffu, s, j);
-        s -= sm.coef1[buf][j][lane] * zj;
-        nxt += sm.coef2[buf][j][lane] * zj;
+        const T c1 = C1[j * CHK];
+        const T c2 = C2[j * CHK];
+        const T zj = __shfl_sync(0xffffffffu, s, j);
+        s -= c1 * zj;
+        nxt += c2 * zj;
       }
       recent = nxt;
-      const int64_t p = c * CHK + lane;
-      ring[p & ringmask] = s;
-      if (p < n) {
-        int64_t r = row_of<MODE>(p, n);
-        if (io.out_d) io.out_d[r] = (double)s;
-        else reinterpret_cast<T*>(io.out_t)[r] = s;
+      const int p = c * CHK + lane;
+      sh.Z[p & (g.ZR - 1)] = s;
+      const int r = row_of<MODE>(p, g.ld);
+      if (r < g.n) {
+        if (out_d) out_d[r] = (double)s;
+        else out_t[r] = s;
       }
-    } else if (c + 1 < nchunks) {
-      stage_chunk<T, MODE>(sm, F, ld, K, n, c + 1, io, ring, ringmask);
+    } else {
+      prefetch<T, YT, MODE, PF>(sh, g, F, yin, c + PF);
+      build_tiles<T, YT, MODE, PF, DRPC>(sh, g, c + 1, has_top, has_bot);
+      cpa_wait<PF - 3>();   // chunk c + 3 landed (tiles of chunk c + 2 need chunks c + 2, c + 3)
     }
     __syncthreads();
   }
+  if (warp > 0) cpa_wait<0>();
+  __syncthreads();
 }
 
-template <typename T, bool TRANS>
+template <typename T> __host__ __device__ constexpr int pf_of() { return sizeof(T) == 4 ? 5 : 4; }
+
+__host__ __device__ inline int ring_rows(int K) { return (K > 2 * CHK - 1 ? K : 2 * CHK - 1) + 1; }
+// even slot pitch: all four sweep kinds read the ring without bank conflicts
+__host__ __device__ inline int ring_pitch(int K) { return (ring_rows(K) + 2) & ~1; }
+constexpr int kSmallDRP = 66;   // ring_pitch(K) for K <= 63
+__host__ __device__ inline int z_ring(int K) { int z = 64; while (z < K + 3 * CHK) z <<= 1; return z; }
+
+template <typename T>
+size_t sweep_smem(int K, int* RQ_out) {
+  constexpr int PF = pf_of<T>();
+  int RQ = ((K + CHK * (PF + 1)) + CHK - 1) / CHK * CHK;
+  *RQ_out = RQ;
+  size_t b = (size_t)ring_pitch(K) * RQ * sizeof(T);
+  b = (b + 15) & ~(size_t)15;
+  b += (size_t)(PF + 1) * CHK * sizeof(double);   // Y ring (largest input type)
+  b += (size_t)z_ring(K) * sizeof(T);             // Z ring
+  b = (b + 15) & ~(size_t)15;
+  b += (size_t)2 * 2 * CHK * CHK * sizeof(T);     // C1, C2
+  b += (size_t)2 * CHK * sizeof(T);               // YH
+  b += (size_t)2 * NOLD * CHK * sizeof(T);        // older
+  b = (b + 15) & ~(size_t)15;
+  b += (size_t)2 * K * sizeof(double);            // corrections
+  return b;
+}
+
+template <typename T, typename YT, int PF>
+__device__ __forceinline__ SweepSh<T, YT> carve(unsigned char* base, const SweepGeom& g) {
+  SweepSh<T, YT> sh;
+  size_t off = 0;
+  sh.R = reinterpret_cast<T*>(base);
+  off = (size_t)g.DRP * g.RQ * sizeof(T);
+  off = (off + 15) & ~(size_t)15;
+  sh.Y = reinterpret_cast<YT*>(base + off);
+  off += (size_t)(PF + 1) * CHK * sizeof(double);
+  sh.Z = reinterpret_cast<T*>(base + off);
+  off += (size_t)g.ZR * sizeof(T);
+  off = (off + 15) & ~(size_t)15;
+  sh.C1 = reinterpret_cast<T*>(base + off);
+  off += (size_t)2 * CHK * CHK * sizeof(T);
+  sh.C2 = reinterpret_cast<T*>(base + off);
+  off += (size_t)2 * CHK * CHK * sizeof(T);
+  sh.YH = reinterpret_cast<T*>(base + off);
+  off += (size_t)2 * CHK * sizeof(T);
+  sh.older = reinterpret_cast<T*>(base + off);
+  off += (size_t)2 * NOLD * CHK * sizeof(T);
+  off = (off + 15) & ~(size_t)15;
+  sh.corr = reinterpret_cast<double*>(base + off);
+  return sh;
+}
+
+template <typename T, bool TRANS, int DRPC>
 __global__ void __launch_bounds__(NW * 32)
 k_block_solve(const T* __restrict__ Fall, int K, Dev d, const double* __restrict__ r_in,
               double* __restrict__ z_out, T* __restrict__ tmp, const double* __restrict__ ctop_all,
-              const double* __restrict__ cbot_all, int P, int ringsize) {
+              const double* __restrict__ cbot_all, int P, int RQ) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  SweepSmem<T>& sm = *reinterpret_cast<SweepSmem<T>*>(smem_raw);
-  T* ring = reinterpret_cast<T*>(smem_raw + sizeof(SweepSmem<T>));
+  constexpr int PF = pf_of<T>();
   const int b = blockIdx.x;
   const int64_t s = d.off[b];
-  const int64_t n = d.off[b + 1] - s;
-  const int64_t ld = d.ld[b];
+  SweepGeom g;
+  g.K = K;
+  g.n = (int)(d.off[b + 1] - s);
+  g.ld = (int)d.ld[b];
+  g.RQ = RQ;
+  g.DR = ring_rows(K);
+  g.DRP = ring_pitch(K);
+  g.ZR = z_ring(K);
   const T* F = Fall + d.fbase[b];
-  SweepIO io1{r_in + s, nullptr, nullptr, nullptr, nullptr, tmp + s};
-  if (ctop_all && b > 0) io1.ctop = ctop_all + (int64_t)(b - 1) * K;
-  if (cbot_all && b + 1 < P) io1.cbot = cbot_all + (int64_t)b * K;
-  if (!TRANS) sweep<T, LF>(sm, ring, ringsize - 1, F, ld, K, n, io1);
-  else sweep<T, UTF>(sm, ring, ringsize - 1, F, ld, K, n, io1);
-  SweepIO io2{nullptr, tmp + s, nullptr, nullptr, z_out + s, nullptr};
-  if (!TRANS) sweep<T, UB>(sm, ring, ringsize - 1, F, ld, K, n, io2);
-  else sweep<T, LTB>(sm, ring, ringsize - 1, F, ld, K, n, io2);
+  const bool has_top = ctop_all && b > 0;
+  const bool has_bot = cbot_all && b + 1 < P;
+  {
+    SweepSh<T, double> sh = carve<T, double, PF>(smem_raw, g);
+    // ring distances beyond K are read as zero coefficients and never streamed
+    const int nz = g.DRP - K - 1;
+    for (int e = threadIdx.x; e < RQ * nz; e += blockDim.x) sh.R[(e / nz) * g.DRP + K + 1 + e % nz] = T(0);
+    for (int t = threadIdx.x; t < K; t += blockDim.x) {
+      sh.corr[t] = has_top ? ctop_all[(int64_t)(b - 1) * K + t] : 0.0;
+      sh.corr[K + t] = has_bot ? cbot_all[(int64_t)b * K + t] : 0.0;
+    }
+    __syncthreads();
+    if (!TRANS) sweep<T, double, LF, PF, DRPC>(sh, g, F, r_in + s, has_top, has_bot, nullptr, tmp + s);
+    else sweep<T, double, UTF, PF, DRPC>(sh, g, F, r_in + s, has_top, has_bot, nullptr, tmp + s);
+  }
+  {
+    SweepSh<T, T> sh = carve<T, T, PF>(smem_raw, g);
+    if (!TRANS) sweep<T, T, UB, PF, DRPC>(sh, g, F, tmp + s, false, false, z_out + s, nullptr);
+    else sweep<T, T, LTB, PF, DRPC>(sh, g, F, tmp + s, false, false, z_out + s, nullptr);
+  }
 }
 
 // ---- SaP-C reduced systems (Eq. (2.5)) and purification right-hand sides ----
@@ -281,28 +402,25 @@ __global__ void k_reduced(const double* __restrict__ band, int64_t N, int K, Dev
   }
 }
 
-template <typename T>
-size_t sweep_smem(int K, int* ringsize) {
-  int ring = 64;
-  while (ring < K + 2 * CHK + 32) ring <<= 1;
-  *ringsize = ring;
-  return sizeof(SweepSmem<T>) + ring * sizeof(T);
-}
-
 template <typename T, bool TRANS>
 cudaError_t launch_block_solve(const T* F, int K, int P, Dev d, const double* r, double* z, T* tmp,
                                const double* ctop, const double* cbot, cudaStream_t s) {
-  int ring;
-  size_t smem = sweep_smem<T>(K, &ring);
-  auto kern = k_block_solve<T, TRANS>;
+  int RQ;
+  size_t smem = sweep_smem<T>(K, &RQ);
+  auto kern = (ring_pitch(K) == kSmallDRP) ? k_block_solve<T, TRANS, kSmallDRP> : k_block_solve<T, TRANS, 0>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   count_launches(1);
-  kern<<<P, NW * 32, smem, s>>>(F, K, d, r, z, tmp, ctop, cbot, P, ring);
+  kern<<<P, NW * 32, smem, s>>>(F, K, d, r, z, tmp, ctop, cbot, P, RQ);
   return cudaGetLastError();
 }
 
 }  // namespace
+
+size_t sweep_smem_bytes(int K, bool fp64) {
+  int RQ;
+  return fp64 ? sweep_smem<double>(K, &RQ) : sweep_smem<float>(K, &RQ);
+}
 
 // scratch layout (doubles): [0, N) g ; then T tmp (N); then ctop, cbot ((P-1) K each)
 template <typename T>

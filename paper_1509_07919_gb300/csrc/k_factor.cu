@@ -1,20 +1,22 @@
 // Banded LU / UL factorisation of the diagonal blocks A_i without pivoting,
 // with pivot boosting (Sec. 2.2, Sec. 3.1 "LU/UL factorizations").
 //
-// One CTA factors one block.  The active (K+1) x (K+1) window of the
-// right-looking elimination lives in registers: a 16 x 16 thread grid, each
-// thread owning R x R fixed *physical* window slots (rows ty + 16 y,
-// columns tx + 16 x).  Window rows and columns are addressed modulo
-// M = K + 1, so sliding the window by one step only replaces the physical
-// row and column of the pivot; no data moves.  Per step k:
-//   1. read the pivot row/column (published in shared memory by their
-//      owners at the end of step k-1), boost the pivot, 1/p;
-//   2. rank-1 update of every owned slot outside the pivot row/column;
-//   3. write L(:,k) and U(k,:) (LU) or the last K rows/columns (UL) out;
-//   4. reload the pivot's physical row/column with the entering band row
-//      k+K+1 / column k+K+1 (pristine entries of A, prefetched into a
-//      shared-memory ring by cp.async one chunk of steps ahead);
-//   5. publish the next pivot row/column; one __syncthreads.
+// One CTA (8 warps) factors one block with a blocked right-looking
+// elimination over panels of NB = 16 columns.  The active window, rows and
+// columns [k0, k0 + K + NB) of the block, lives in shared memory, addressed
+// modulo M2 = K + NB in both directions so that sliding it by a panel only
+// replaces NB physical rows and columns.  Per panel:
+//   A. warp 0 factors the (K+NB) x NB panel in registers (pivot row by
+//      shuffles, boosted pivot, multipliers, in-panel update); meanwhile the
+//      other warps cp.async the entering band rows/columns of the next
+//      window into a staging buffer;
+//   B. U12 = L11^{-1} A12 for the panel rows (one thread per column);
+//   C. trailing update A22 -= L21 U12 (K x K, 4 x 4 register tiles);
+//   D. the finished panel rows of U and columns of L go to global memory and
+//      the staged entering rows/columns replace the retired ones.
+// Four barriers per 16 columns.  Entries outside the band (and outside the
+// block) are kept as exact zeros, so no band masks are needed inside the
+// arithmetic.
 // The UL factorisation is the same elimination run on the reversed block
 // J A_i J: if J A_i J = L~ U~ (unit L~) then A_i = (J L~ J)(J U~ J) = U' L'
 // with unit upper U'.  Only the last K rows/columns of L~, U~ are kept,
@@ -27,10 +29,8 @@ namespace sap {
 
 namespace {
 
-constexpr int TDIM = 16;           // thread grid is TDIM x TDIM
-constexpr int NTHREADS = TDIM * TDIM;
-constexpr int CH = 16;             // steps per prefetch chunk
-constexpr int NSTAGE = 2 * CH;     // ring of two chunks
+constexpr int NB = 16;             // panel width
+constexpr int NTHREADS = 256;
 
 __device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
   unsigned s = (unsigned)__cvta_generic_to_shared(smem);
@@ -43,7 +43,7 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // Returns a pointer into the band, or nullptr for a structural zero.
 template <bool REV>
 __device__ __forceinline__ const double* elem_ptr(const double* band, int64_t N, int K, int64_t s,
-                                                  int64_t n, int64_t r, int64_t q) {
+                                                  int n, int r, int q) {
   if (r < 0 || q < 0 || r >= n || q >= n) return nullptr;
   int64_t gi = REV ? s + n - 1 - r : s + r;
   int64_t gj = REV ? s + n - 1 - q : s + q;
@@ -52,182 +52,245 @@ __device__ __forceinline__ const double* elem_ptr(const double* band, int64_t N,
   return band + c * N + gj;
 }
 
-// Prefetch the entering row / column of steps [k0, k0 + CH) into ring slots.
-// For step k the entering row is r = k + M with columns q = k+1+m (m < M),
-// the entering column is q = k + M with rows r = k+1+m (m < M-1).
-template <bool REV>
-__device__ __forceinline__ void prefetch_chunk(double* stage, int Mp, const double* band, int64_t N,
-                                               int K, int64_t s, int64_t n, int64_t k0) {
-  const int M = K + 1;
-  const int total = CH * (2 * M);
-  for (int e = threadIdx.x; e < total; e += NTHREADS) {
-    int kk = e % CH;
-    int t = e / CH;           // 0..2M-1
-    int which = t / M;        // 0 = row, 1 = column
-    int m = t % M;
-    int64_t k = k0 + kk;
-    double* dst = stage + ((size_t)((k % NSTAGE) * 2 + which) * Mp + m);
-    const double* src = nullptr;
-    if (which == 0) src = elem_ptr<REV>(band, N, K, s, n, k + M, k + 1 + m);
-    else if (m < M - 1) src = elem_ptr<REV>(band, N, K, s, n, k + 1 + m, k + M);
-    if (src) cp_async8(dst, src);
-    else *dst = 0.0;
+template <typename T> __device__ __forceinline__ T rcp(T p) { return T(1) / p; }
+template <> __device__ __forceinline__ float rcp<float>(float p) { return __frcp_rn(p); }
+
+// Window geometry: M2 = K + NB rounded up to a multiple of NB, row pitch
+// LDW = M2 + 4 (16-byte aligned rows; 128-bit row reads are conflict-free).
+// The base (physical index of logical offset 0) is a multiple of NB, so a
+// panel's NB columns, and any 4-aligned group of offsets, never wrap.
+struct Win {
+  int M2, LDW, base;
+  __device__ __forceinline__ int ph(int off) const { int x = base + off; return x >= M2 ? x - M2 : x; }
+};
+__host__ __device__ inline int win_m2(int K) { return (K + NB + NB - 1) / NB * NB; }
+
+template <typename T> struct Vec4;
+template <> struct Vec4<float> { using type = float4; };
+template <> struct Vec4<double> { using type = double4; };
+
+// 4 consecutive T from a 16-byte (float) / 32-byte-capable (double) aligned address
+template <typename T>
+__device__ __forceinline__ void ld4(const T* p, T (&v)[4]) {
+  if (sizeof(T) == 4) {
+    float4 x = *reinterpret_cast<const float4*>(p);
+    v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
+  } else {
+    double2 x = *reinterpret_cast<const double2*>(p);
+    double2 y = *reinterpret_cast<const double2*>(p + 2);
+    v[0] = x.x; v[1] = x.y; v[2] = y.x; v[3] = y.y;
   }
-  cp_async_commit();
 }
 
-template <typename T, int R, bool REV>
+template <typename T, int MR, bool REV>
 __global__ void __launch_bounds__(NTHREADS)
 k_band_lu(const double* __restrict__ band, int64_t N, int K, Dev d, int block0,
           const double* __restrict__ absmax, double eps, T* __restrict__ out,
           unsigned long long* __restrict__ n_boosted) {
-  extern __shared__ __align__(16) double stage[];   // [NSTAGE][2][Mp]
-  __shared__ T colbuf[2][TDIM * R];
-  __shared__ T rowbuf[2][TDIM * R];
-
+  extern __shared__ __align__(16) unsigned char smem_raw[];
   const int b = block0 + blockIdx.x;
   const int64_t s = d.off[b];
-  const int64_t n = d.off[b + 1] - s;
-  const int M = K + 1;
-  const int Mp = (M + 1) & ~1;
-  const int tx = threadIdx.x % TDIM, ty = threadIdx.x / TDIM;
+  const int n = (int)(d.off[b + 1] - s);
+  const int M2 = win_m2(K);
+  const int LDW = M2 + 4;
+  const int KA = K + NB;          // active rows/cols of the window in a panel step
+  const int ME = M2 - NB;         // rows of the next window that are already resident
+  T* W = reinterpret_cast<T*>(smem_raw);
+  size_t woff = ((size_t)M2 * LDW * sizeof(T) + 15) & ~(size_t)15;
+  double* ER = reinterpret_cast<double*>(smem_raw + woff);   // NB x M2 entering rows
+  double* EC = ER + NB * M2;                                   // ME x NB entering columns
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const T tau = (T)(eps * absmax[0]);
   unsigned long long nb = 0;
-
-  // output addressing
   const int64_t ld = REV ? 0 : d.ld[b];
   T* F = REV ? out + (int64_t)(b - 1) * K * K : out + d.fbase[b];
 
-  // initial window: rows/cols 0..K, physical == logical
-  T a[R][R];
-#pragma unroll
-  for (int y = 0; y < R; ++y)
-#pragma unroll
-    for (int x = 0; x < R; ++x) {
-      int pr = ty + TDIM * y, pc = tx + TDIM * x;
-      const double* p = (pr < M && pc < M) ? elem_ptr<REV>(band, N, K, s, n, pr, pc) : nullptr;
-      a[y][x] = p ? (T)(*p) : T(0);
-      if (pr < M && pc == 0) colbuf[0][pr] = a[y][x];
-      if (pc < M && pr == 0) rowbuf[0][pc] = a[y][x];
-    }
-  prefetch_chunk<REV>(stage, Mp, band, N, K, s, n, 0);
-  cp_async_wait_all();
+  Win w{M2, LDW, 0};
+  // initial window: logical rows/cols [0, M2), physical == logical
+  for (int e = tid; e < M2 * M2; e += NTHREADS) {
+    int r = e / M2, q = e % M2;
+    const double* p = elem_ptr<REV>(band, N, K, s, n, r, q);
+    W[r * LDW + q] = p ? (T)(*p) : T(0);
+  }
   __syncthreads();
 
-  int pk = 0;  // physical index of the pivot row/column (k mod M)
-  for (int64_t k = 0; k < n; ++k) {
-    if (k % CH == 0 && k + CH < n) prefetch_chunk<REV>(stage, Mp, band, N, K, s, n, k + CH);
-    const T* cb = colbuf[k & 1];
-    const T* rb = rowbuf[k & 1];
-    T p = rb[pk];
-    if ((p < T(0) ? -p : p) < tau) {
-      p = p >= T(0) ? tau : -tau;
-      ++nb;
-    }
-    const T rinv = T(1) / p;
-    const int pk1 = (pk + 1 == M) ? 0 : pk + 1;
-
-    T l[R], u[R];
+  for (int k0 = 0; k0 < n; k0 += NB) {
+    const int base = w.base;     // physical column of the panel start (multiple of NB)
+    // ---- A: panel factorisation (warp 0) || prefetch of the entering data (warps 1..7) ----
+    if (warp == 0) {
+      T pv[MR][NB];
 #pragma unroll
-    for (int y = 0; y < R; ++y) {
-      int pr = ty + TDIM * y;
-      l[y] = (pr < M && pr != pk) ? cb[pr] * rinv : T(0);
-    }
+      for (int m = 0; m < MR; ++m) {
+        const int off = lane + 32 * m;
+        if (off < KA) {
+          const T* row = &W[w.ph(off) * LDW + base];
 #pragma unroll
-    for (int x = 0; x < R; ++x) {
-      int pc = tx + TDIM * x;
-      u[x] = (pc < M && pc != pk) ? rb[pc] : T(0);
-    }
+          for (int c4 = 0; c4 < NB / 4; ++c4) {
+            T v[4];
+            ld4(row + 4 * c4, v);
 #pragma unroll
-    for (int y = 0; y < R; ++y)
+            for (int x = 0; x < 4; ++x) pv[m][4 * c4 + x] = v[x];
+          }
+        } else {
 #pragma unroll
-      for (int x = 0; x < R; ++x) a[y][x] -= l[y] * u[x];
-
-    // ---- outputs of step k ----
-    if (!REV) {
-      if (tx == 0) {
+          for (int c = 0; c < NB; ++c) pv[m][c] = T(0);
+        }
+      }
 #pragma unroll
-        for (int y = 0; y < R; ++y) {
-          int pr = ty + TDIM * y;
-          if (pr < M && pr != pk) {
-            int off = pr - pk; if (off < 0) off += M;      // logical row = k + off
-            if (k + off < n) F[(int64_t)(K + off) * ld + k] = l[y];
+      for (int j = 0; j < NB; ++j) {
+        // pivot row j (owned by lane j, m = 0): entries j..NB-1
+        T u[NB];
+#pragma unroll
+        for (int c = j; c < NB; ++c) u[c] = __shfl_sync(0xffffffffu, pv[0][c], j);
+        T p = u[j];
+        if (k0 + j < n) {
+          if ((p < T(0) ? -p : p) < tau) {
+            p = p >= T(0) ? tau : -tau;
+            ++nb;
+          }
+        } else {
+          p = T(1);   // padding past the block: rows there are all zero
+        }
+        const T rinv = rcp(p);
+#pragma unroll
+        for (int m = 0; m < MR; ++m) {
+          const int off = lane + 32 * m;
+          if (off > j) {
+            const T l = pv[m][j] * rinv;
+            pv[m][j] = l;
+#pragma unroll
+            for (int c = j + 1; c < NB; ++c) pv[m][c] -= l * u[c];
+          } else if (off == j) {
+            pv[m][j] = p;
           }
         }
       }
-      if (ty == 0) {
 #pragma unroll
-        for (int x = 0; x < R; ++x) {
-          int pc = tx + TDIM * x;
-          if (pc < M) {
-            int off = pc - pk; if (off < 0) off += M;      // logical col = k + off
-            if (k + off < n) F[(int64_t)(K - off) * ld + k + off] = (off == 0) ? p : rb[pc];
-          }
+      for (int m = 0; m < MR; ++m) {
+        const int off = lane + 32 * m;
+        if (off < KA) {
+          T* row = &W[w.ph(off) * LDW + base];
+#pragma unroll
+          for (int c = 0; c < NB; ++c) row[c] = pv[m][c];
         }
       }
-    } else if (k >= n - K) {
-      // keep the last K rows/cols of L~ and U~ of J A J, flipped:
-      // U'(n-1-i, n-1-k) = L~(i, k), L'(n-1-k, n-1-j) = U~(k, j)
-      if (tx == 0) {
-#pragma unroll
-        for (int y = 0; y < R; ++y) {
-          int pr = ty + TDIM * y;
-          if (pr < M && pr != pk) {
-            int off = pr - pk; if (off < 0) off += M;
-            int64_t i = k + off;
-            if (i < n) F[(n - 1 - i) * K + (n - 1 - k)] = l[y];
-          }
+    } else {
+      // entering rows i = k0 + M2 + e (columns of the next window, offsets jo from k0 + NB)
+      // and entering columns j = k0 + M2 + e for resident rows i = k0 + NB + ro (ro < ME)
+      const int hw = warp - 1, ht = tid - 32, nh = NTHREADS - 32;
+      for (int e = hw; e < NB; e += NTHREADS / 32 - 1)
+        for (int jo = lane; jo < M2; jo += 32) {
+          double* dst = &ER[e * M2 + jo];
+          const double* src = elem_ptr<REV>(band, N, K, s, n, k0 + M2 + e, k0 + NB + jo);
+          if (src) cp_async8(dst, src);
+          else *dst = 0.0;
         }
+      for (int y = ht; y < ME * NB; y += nh) {
+        const int ro = y / NB, e = y % NB;
+        double* dst = &EC[y];
+        const double* src = elem_ptr<REV>(band, N, K, s, n, k0 + NB + ro, k0 + M2 + e);
+        if (src) cp_async8(dst, src);
+        else *dst = 0.0;
       }
-      if (ty == 0) {
-#pragma unroll
-        for (int x = 0; x < R; ++x) {
-          int pc = tx + TDIM * x;
-          if (pc < M) {
-            int off = pc - pk; if (off < 0) off += M;
-            int64_t j = k + off;
-            if (j < n) F[(n - 1 - k) * K + (n - 1 - j)] = (off == 0) ? p : rb[pc];
-          }
-        }
-      }
+      cp_async_commit();
     }
-
-    // ---- chunk boundary: the next chunk must have landed ----
-    const double* st = stage + (size_t)((k % NSTAGE) * 2) * Mp;
-    // ---- reload the pivot's physical row / column with entering data ----
-#pragma unroll
-    for (int y = 0; y < R; ++y) {
-      int pr = ty + TDIM * y;
-      if (pr >= M) continue;
-#pragma unroll
-      for (int x = 0; x < R; ++x) {
-        int pc = tx + TDIM * x;
-        if (pc >= M) continue;
-        if (pr == pk) {          // entering row k+M, column logical k+1+m
-          int m = pc - pk1; if (m < 0) m += M;
-          a[y][x] = (T)st[m];
-        } else if (pc == pk) {   // entering column k+M, row logical k+1+m
-          int m = pr - pk1; if (m < 0) m += M;
-          a[y][x] = (T)st[Mp + m];
-        }
-      }
-    }
-    // ---- publish pivot row / column of step k+1 ----
-    T* ncb = colbuf[(k + 1) & 1];
-    T* nrb = rowbuf[(k + 1) & 1];
-#pragma unroll
-    for (int y = 0; y < R; ++y)
-#pragma unroll
-      for (int x = 0; x < R; ++x) {
-        int pr = ty + TDIM * y, pc = tx + TDIM * x;
-        if (pr < M && pc == pk1) ncb[pr] = a[y][x];
-        if (pc < M && pr == pk1) nrb[pc] = a[y][x];
-      }
-    if ((k + 1) % CH == 0) cp_async_wait_all();
     __syncthreads();
-    pk = pk1;
+
+    // ---- B: U12 = L11^{-1} A12 (panel rows, window columns NB..KA-1) ----
+    for (int c = NB + tid; c < KA; c += NTHREADS) {
+      const int pc = w.ph(c);
+      T x[NB];
+#pragma unroll
+      for (int r = 0; r < NB; ++r) x[r] = W[(base + r) * LDW + pc];
+#pragma unroll
+      for (int r = 1; r < NB; ++r) {
+        const T* Lr = &W[(base + r) * LDW + base];
+        T lr[NB];
+#pragma unroll
+        for (int c4 = 0; c4 < NB / 4; ++c4) {
+          T v[4];
+          ld4(Lr + 4 * c4, v);
+#pragma unroll
+          for (int y = 0; y < 4; ++y) lr[4 * c4 + y] = v[y];
+        }
+        T acc = x[r];
+#pragma unroll
+        for (int q = 0; q < r; ++q) acc -= lr[q] * x[q];
+        x[r] = acc;
+      }
+#pragma unroll
+      for (int r = 1; r < NB; ++r) W[(base + r) * LDW + pc] = x[r];
+    }
+    __syncthreads();
+
+    // ---- C: A22 -= L21 U12 over window rows/cols [NB, NB + 4 ceil(K/4)), 4 x 4 tiles ----
+    {
+      const int nt = (K + 3) / 4;
+      for (int t = tid; t < nt * nt; t += NTHREADS) {
+        const int ti = t / nt, tj = t % nt;
+        const int r0 = w.ph(NB + 4 * ti), c0 = w.ph(NB + 4 * tj);   // 4-groups never wrap
+        T acc[4][4];
+#pragma unroll
+        for (int x = 0; x < 4; ++x)
+#pragma unroll
+          for (int y = 0; y < 4; ++y) acc[x][y] = T(0);
+#pragma unroll
+        for (int q4 = 0; q4 < NB / 4; ++q4) {
+          T a[4][4], bq[4][4];
+#pragma unroll
+          for (int x = 0; x < 4; ++x) ld4(&W[(r0 + x) * LDW + base + 4 * q4], a[x]);
+#pragma unroll
+          for (int qq = 0; qq < 4; ++qq) ld4(&W[(base + 4 * q4 + qq) * LDW + c0], bq[qq]);
+#pragma unroll
+          for (int qq = 0; qq < 4; ++qq)
+#pragma unroll
+            for (int x = 0; x < 4; ++x)
+#pragma unroll
+              for (int y = 0; y < 4; ++y) acc[x][y] += a[x][qq] * bq[qq][y];
+        }
+#pragma unroll
+        for (int x = 0; x < 4; ++x) {
+          T* row = &W[(r0 + x) * LDW + c0];
+#pragma unroll
+          for (int y = 0; y < 4; ++y) row[y] -= acc[x][y];
+        }
+      }
+    }
+    // ---- D1: write the finished panel (U rows k0.., L columns k0..) ----
+    for (int e = tid; e < NB * (2 * K + 1); e += NTHREADS) {
+      const int dg = e / NB, t = e % NB;    // diagonal index c = K + i - j, position in panel
+      int i, j;
+      if (dg <= K) { i = k0 + t; j = i + (K - dg); }     // U(i, j), j - i = K - dg
+      else { j = k0 + t; i = j + (dg - K); }             // L(i, j), i - j = dg - K
+      if (i >= n || j >= n) continue;
+      const T v = W[w.ph(i - k0) * LDW + w.ph(j - k0)];
+      if (!REV) {
+        F[(int64_t)dg * ld + j] = v;
+      } else {
+        // keep the last K rows/cols of L~ and U~ of J A J, flipped:
+        // U'(n-1-i, n-1-k) = L~(i, k), L'(n-1-k, n-1-j) = U~(k, j)
+        const int kk = (dg <= K) ? i : j;
+        if (kk >= n - K) F[(int64_t)(n - 1 - i) * K + (n - 1 - j)] = v;
+      }
+    }
+    if (warp > 0) cp_async_wait_all();
+    __syncthreads();
+    // ---- D2: slide the window by NB: entering rows/cols replace the panel's ----
+    {
+      Win w2{M2, LDW, w.ph(NB)};        // next window: logical offset 0 = k0 + NB
+      for (int e = warp; e < NB; e += NTHREADS / 32) {
+        T* row = &W[w2.ph(ME + e) * LDW];                      // row k0+M2+e = next offset ME+e
+        for (int jo = lane; jo < M2; jo += 32) row[w2.ph(jo)] = (T)ER[e * M2 + jo];
+      }
+      for (int y = tid; y < ME * NB; y += NTHREADS) {
+        const int ro = y / NB, e = y % NB;
+        W[w2.ph(ro) * LDW + w2.ph(ME + e)] = (T)EC[y];        // column k0+M2+e, row k0+NB+ro
+      }
+      w = w2;
+    }
+    __syncthreads();
   }
-  if (threadIdx.x == 0 && nb) atomicAdd(n_boosted, nb);
+  if (warp == 0 && lane == 0 && nb) atomicAdd(n_boosted, nb);
 }
 
 template <typename T, bool REV>
@@ -235,28 +298,40 @@ cudaError_t launch_lu_impl(const double* band, int64_t N, int K, int nblocks, in
                            const double* absmax, double eps, T* out, unsigned long long* nb,
                            cudaStream_t s) {
   if (nblocks <= 0) return cudaSuccess;
-  const int M = K + 1;
-  const int Mp = (M + 1) & ~1;
-  size_t smem = (size_t)NSTAGE * 2 * Mp * sizeof(double);
-  int R = (M <= 16) ? 1 : (M <= 32) ? 2 : (M <= 64) ? 4 : 8;
+  const int M2 = win_m2(K);
+  const int LDW = M2 + 4;
+  size_t smem = (((size_t)M2 * LDW * sizeof(T) + 15) & ~(size_t)15) +
+                ((size_t)NB * M2 + (size_t)(M2 - NB) * NB) * sizeof(double);
+  const int MR = (K + NB + 31) / 32;
   cudaError_t e = cudaSuccess;
 #define SAP_LAUNCH_LU(RR)                                                                           \
   do {                                                                                              \
     auto kern = k_band_lu<T, RR, REV>;                                                             \
-    if (smem > 48 * 1024) e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);         \
     if (e != cudaSuccess) return e;                                                                 \
-    count_launches(1);                                                                             \
+    count_launches(1);                                                                              \
     kern<<<nblocks, NTHREADS, smem, s>>>(band, N, K, d, block0, absmax, eps, out, nb);             \
   } while (0)
-  switch (R) {
+  switch (MR) {
     case 1: SAP_LAUNCH_LU(1); break;
     case 2: SAP_LAUNCH_LU(2); break;
+    case 3: SAP_LAUNCH_LU(3); break;
     case 4: SAP_LAUNCH_LU(4); break;
-    default: SAP_LAUNCH_LU(8); break;
+    default: SAP_LAUNCH_LU(5); break;
   }
 #undef SAP_LAUNCH_LU
   return cudaGetLastError();
 }
+
+}  // namespace
+
+size_t lu_smem_bytes(int K, bool fp64) {
+  const int M2 = win_m2(K);
+  const size_t ts = fp64 ? sizeof(double) : sizeof(float);
+  return (((size_t)M2 * (M2 + 4) * ts + 15) & ~(size_t)15) + ((size_t)NB * M2 + (size_t)(M2 - NB) * NB) * sizeof(double);
+}
+
+namespace {
 
 // ---- max |a_ij| over the in-band entries (boost threshold scale) ----
 __global__ void k_absmax(const double* __restrict__ band, int64_t N, int K, double* out) {

@@ -107,6 +107,8 @@ struct Solver : SolverBase {
     const int64_t KK = (int64_t)K * K;
     const int nI = P > 1 ? P - 1 : 1;
     TRY(h->mem.alloc(&f.F, (size_t)L.f_elems));
+    // the padding columns [n_i, ld_i) of every block are read by the sweeps and must be 0
+    CK(cudaMemset(f.F, 0, (size_t)L.f_elems * sizeof(T)));
     TRY(h->mem.alloc(&scratch, (size_t)(2 * L.N + 2 * nI * K + 8)));
     if (h->opt.variant == SAP_C && P > 1) {
       TRY(h->mem.alloc(&f.ULt, (size_t)(nI * KK)));
@@ -376,8 +378,10 @@ void sap_default_options(sap_options_t* o) {
 int64_t sap_kernel_launches(void) { return (int64_t)sap::g_launches.load(); }
 
 int32_t sap_max_K(int32_t precision) {
-  (void)precision;
-  return kMaxK;
+  const bool fp64 = precision == SAP_FP64;
+  int K = kMaxK;
+  while (K > 1 && (sweep_smem_bytes(K, fp64) > kSmemPerBlock || lu_smem_bytes(K, fp64) > kSmemPerBlock)) --K;
+  return K;
 }
 
 sap_status_t sap_factor(const double* band_dev, int64_t N, int32_t K, const sap_options_t* opt_in,
@@ -390,7 +394,7 @@ sap_status_t sap_factor(const double* band_dev, int64_t N, int32_t K, const sap_
   if (opt.max_iters <= 0) opt.max_iters = 500;
   if (!(opt.tol > 0.0)) opt.tol = 1e-10;
   if (!(opt.boost_eps > 0.0)) opt.boost_eps = opt.precision == SAP_FP64 ? 0x1p-53 : 0x1p-24;
-  if (K > kMaxK) return SAP_ERR_NOT_IMPLEMENTED;
+  if (K > sap_max_K(opt.precision)) return SAP_ERR_NOT_IMPLEMENTED;
   if (opt.variant == SAP_C && opt.P > 1 && K > max_K_spikes(opt.precision)) return SAP_ERR_NOT_IMPLEMENTED;
   std::unique_ptr<sap_handle> h(new (std::nothrow) sap_handle());
   if (!h) return SAP_ERR_OOM;

@@ -10,6 +10,11 @@ namespace sap {
 // Largest half-bandwidth handled by the register-window factor kernel:
 // a 16 x 16 thread grid with up to 8 x 8 window slots per thread.
 constexpr int kMaxK = 127;
+constexpr size_t kSmemPerBlock = 232448;   // opt-in shared memory per CTA on sm_103
+
+// Dynamic shared memory of the sweep and factor kernels for half-bandwidth K.
+size_t sweep_smem_bytes(int K, bool fp64);
+size_t lu_smem_bytes(int K, bool fp64);
 
 // Factor storage of one block (per block i, local rows/cols 0..n_i-1):
 // "diagonal-major" like the input band, indexed by the column:

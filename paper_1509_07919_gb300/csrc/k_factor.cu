@@ -65,10 +65,6 @@ struct Win {
 };
 __host__ __device__ inline int win_m2(int K) { return (K + NB + NB - 1) / NB * NB; }
 
-template <typename T> struct Vec4;
-template <> struct Vec4<float> { using type = float4; };
-template <> struct Vec4<double> { using type = double4; };
-
 // 4 consecutive T from a 16-byte (float) / 32-byte-capable (double) aligned address
 template <typename T>
 __device__ __forceinline__ void ld4(const T* p, T (&v)[4]) {

@@ -167,6 +167,31 @@ SAP_API sap_status_t sap_destroy(sap_handle_t h);
 /* Static description of a status code. */
 SAP_API const char *sap_status_string(sap_status_t s);
 
+/* Direct banded solve A x = b that allocates no device memory.  There is no
+ * counterpart in the paper: it exists for callers that cannot call
+ * cudaMalloc (cudaMalloc may synchronise the device, which latency-critical
+ * loops cannot afford, and some host programs own all device memory and
+ * forbid new driver allocations).  It runs the kernels of sap_factor with
+ * P = 1, SaP-D, followed by sap_apply_preconditioner: one banded LU without
+ * pivoting (pivots boosted at the unit roundoff of `precision` times
+ * max|a_ij|) and the forward and backward sweeps, so x = A^{-1} b up to the
+ * factorisation's rounding; no Krylov iteration.
+ *   All intermediates live in one file-scope device array of 32 MiB that
+ *   every GPU loading the library holds until the process exits; the call
+ *   needs (N rounded up to 32) (2K+1) sizeof(factor) + (2N + 2K + 8) 8 bytes
+ *   plus 256-byte alignment, and returns SAP_ERR_INVALID_ARG beyond that.
+ *   The caller still provides band_dev, b_dev and x_dev (device, float64).
+ *   The first call on a device looks up the array's device address; make
+ *   that first call before any stream capture.
+ *   Every call uses the same array and overwrites the previous call's
+ *   contents, so calls that overlap on the GPU (other streams or threads)
+ *   race; order them on one stream.  Asynchronous on `stream`.
+ * Errors: INVALID_ARG (sizes, null or aliased pointers, too large for the
+ * array), NOT_IMPLEMENTED (K above sap_max_K), CUDA. */
+SAP_API sap_status_t sap_band_solve_noalloc(const double *band_dev, int64_t N, int32_t K,
+                                           const double *b_dev, double *x_dev, int32_t precision,
+                                           cudaStream_t stream);
+
 /* Number of CUDA kernels this library has launched in this process so far
  * (host-side counter, all handles and threads). */
 SAP_API int64_t sap_kernel_launches(void);

@@ -71,6 +71,7 @@ def _load():
         "sap_status_string": (C.c_char_p, [C.c_int]),
         "sap_max_K": (i32, [i32]),
         "sap_kernel_launches": (i64, []),
+        "sap_band_solve_noalloc": (C.c_int, [vp, i64, i32, vp, vp, i32, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -218,6 +219,14 @@ def sap_get_interface(h: Handle, i: int, which: str, adjoint: bool = False, stre
     _check(_lib.sap_get_interface(h.ptr, i, code, int(adjoint), C.c_void_p(m.ctypes.data), _stream(stream)),
            "sap_get_interface")
     return m
+
+
+def sap_band_solve_noalloc(band: torch.Tensor, N: int, K: int, b: torch.Tensor, x: torch.Tensor,
+                           precision: int = SAP_FP64, stream=None) -> torch.Tensor:
+    """Allocation-free direct banded solve (see include/sap.h)."""
+    _check(_lib.sap_band_solve_noalloc(_ptr(band), N, K, _ptr(b), _ptr(x), precision, _stream(stream)),
+           "sap_band_solve_noalloc")
+    return x
 
 
 def sap_kernel_launches() -> int:

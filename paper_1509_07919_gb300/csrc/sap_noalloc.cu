@@ -1,0 +1,94 @@
+// Allocation-free direct banded solve.
+//
+// Some callers cannot call cudaMalloc: cudaMalloc may synchronise the
+// device, which latency-critical loops cannot afford, and some host
+// programs own all device memory themselves and forbid new driver
+// allocations.  sap_band_solve_noalloc serves them: it runs the same
+// kernels as sap_factor (P = 1, SaP-D) followed by
+// sap_apply_preconditioner, i.e. one banded LU without pivoting (boosted
+// pivots) and its two triangular sweeps, but keeps every intermediate
+// (factor array, sweep intermediate, partition descriptor, boost
+// threshold, counters) in one file-scope device array instead of
+// allocating.  The array is kScratchBytes large and lives on every GPU
+// that loads the library until the process exits.
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstring>
+#include <mutex>
+#include "sap_internal.cuh"
+
+using namespace sap;
+
+namespace {
+
+constexpr size_t kScratchBytes = size_t(32) << 20;   // 32 MiB
+constexpr int kMaxDevices = 64;
+
+__device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
+
+std::mutex g_mu;
+void* g_dev_ptr[kMaxDevices] = {};
+
+// Device address of the scratch array on the current device (looked up once
+// per device; host code may not use the symbol itself as an address).
+cudaError_t scratch_address(void** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_mu);
+  if (!g_dev_ptr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    g_dev_ptr[dev] = p;
+  }
+  *out = g_dev_ptr[dev];
+  return cudaSuccess;
+}
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+template <typename T>
+sap_status_t run(const double* band, int64_t N, int K, const double* b, double* x, cudaStream_t s) {
+  const int W = 2 * K + 1;
+  const int64_t ld = (N + 31) / 32 * 32;
+  // scratch layout: header | factors | sweep scratch
+  const size_t hdr = 256;
+  const size_t f_bytes = align256((size_t)ld * W * sizeof(T));
+  const size_t a_bytes = align256((size_t)(2 * N + 2 * K + 8) * sizeof(double));
+  if (hdr + f_bytes + a_bytes > kScratchBytes) return SAP_ERR_INVALID_ARG;
+  void* base = nullptr;
+  if (scratch_address(&base) != cudaSuccess) return SAP_ERR_CUDA;
+  unsigned char* p = static_cast<unsigned char*>(base);
+  int64_t* desc = reinterpret_cast<int64_t*>(p);        // off[2], fbase[1], ld[1]
+  double* absmax = reinterpret_cast<double*>(p + 64);
+  unsigned long long* nb = reinterpret_cast<unsigned long long*>(p + 128);
+  T* F = reinterpret_cast<T*>(p + hdr);
+  double* ascratch = reinterpret_cast<double*>(p + hdr + f_bytes);
+  const int64_t h_desc[4] = {0, N, 0, ld};
+  if (cudaMemcpyAsync(desc, h_desc, sizeof(h_desc), cudaMemcpyHostToDevice, s) != cudaSuccess) return SAP_ERR_CUDA;
+  // counters start at zero; factor padding columns are read as zeros by the sweeps
+  if (cudaMemsetAsync(nb, 0, sizeof(*nb), s) != cudaSuccess) return SAP_ERR_CUDA;
+  if (cudaMemsetAsync(F, 0, (size_t)ld * W * sizeof(T), s) != cudaSuccess) return SAP_ERR_CUDA;
+  Dev d{desc, desc + 2, desc + 3};
+  const double eps = sizeof(T) == 8 ? 0x1p-53 : 0x1p-24;
+  if (launch_absmax(band, N, K, absmax, s) != cudaSuccess) return SAP_ERR_CUDA;
+  if (launch_factor_lu<T>(band, N, K, 1, d, absmax, eps, F, nb, s) != cudaSuccess) return SAP_ERR_CUDA;
+  Factors<T> f;
+  f.F = F;
+  if (launch_apply<T>(band, N, K, 1, d, f, SAP_D, false, b, x, ascratch, s) != cudaSuccess) return SAP_ERR_CUDA;
+  return SAP_OK;
+}
+
+}  // namespace
+
+extern "C" sap_status_t sap_band_solve_noalloc(const double* band_dev, int64_t N, int32_t K, const double* b_dev,
+                                               double* x_dev, int32_t precision, cudaStream_t stream) {
+  if (!band_dev || !b_dev || !x_dev || b_dev == x_dev) return SAP_ERR_INVALID_ARG;
+  if (N < 2 || K < 1 || K >= N) return SAP_ERR_INVALID_ARG;
+  if (precision != SAP_FP64 && precision != SAP_FP32) return SAP_ERR_INVALID_ARG;
+  if (K > sap_max_K(precision)) return SAP_ERR_NOT_IMPLEMENTED;
+  return precision == SAP_FP64 ? run<double>(band_dev, N, K, b_dev, x_dev, stream)
+                               : run<float>(band_dev, N, K, b_dev, x_dev, stream);
+}

@@ -60,6 +60,8 @@ struct SolverBase {
   virtual sap_status_t apply(const double* r, double* z, bool transpose, cudaStream_t s) = 0;
   virtual sap_status_t block_lu(int i, double* host, cudaStream_t s) = 0;
   virtual sap_status_t interface(int i, int which, bool adjoint, double* host, cudaStream_t s) = 0;
+  // SAP_ERR_TIMEOUT (and reset) if a device-side wait gave up since the last call
+  virtual sap_status_t take_device_error(cudaStream_t s) = 0;
 };
 
 }  // namespace
@@ -70,6 +72,7 @@ struct sap_handle {
   const double* band = nullptr;
   DevMem mem;
   Dev d{};
+  const int64_t* dcbase = nullptr;   // per block offset of the chunk matrices
   double* absmax = nullptr;
   unsigned long long* n_boosted = nullptr;
   int* singular = nullptr;
@@ -99,6 +102,7 @@ struct Solver : SolverBase {
   Factors<T> f;
   double* scratch = nullptr;   // apply scratch: g (N), T tmp (N), ctop/cbot
   bool adjoint_ready = false;
+  bool transposed_ready = false;
   explicit Solver(sap_handle* hh) : h(hh) {}
 
   sap_status_t alloc() override {
@@ -110,6 +114,11 @@ struct Solver : SolverBase {
     // the padding columns [n_i, ld_i) of every block are read by the sweeps and must be 0
     CK(cudaMemset(f.F, 0, (size_t)L.f_elems * sizeof(T)));
     TRY(h->mem.alloc(&scratch, (size_t)(2 * L.N + 2 * nI * K + 8)));
+    TRY(h->mem.alloc(&f.err, 1));
+    CK(cudaMemset(f.err, 0, sizeof(int)));
+    TRY(h->mem.alloc(&f.Mlf, (size_t)L.c_elems));
+    TRY(h->mem.alloc(&f.Mub, (size_t)L.c_elems));
+    f.cbase = h->dcbase;
     if (h->opt.variant == SAP_C && P > 1) {
       TRY(h->mem.alloc(&f.ULt, (size_t)(nI * KK)));
       TRY(h->mem.alloc(&f.V, (size_t)(nI * KK)));
@@ -131,6 +140,9 @@ struct Solver : SolverBase {
     CK(cudaEventRecord(h->evp[0], s));
     CK(launch_absmax(h->band, L.N, K, h->absmax, s));
     CK(launch_factor_lu<T>(h->band, L.N, K, P, h->d, h->absmax, eps, f.F, h->n_boosted, s));
+    CK(launch_chunk_mats<T>(f.F, K, P, h->d, f.cbase, L.max_nch, 0, f.Mlf, s));
+    CK(launch_chunk_mats<T>(f.F, K, P, h->d, f.cbase, L.max_nch, 1, f.Mub, s));
+    transposed_ready = false;
     CK(cudaEventRecord(h->evp[1], s));
     if (h->opt.variant == SAP_C && P > 1) {
       CK(launch_factor_ul<T>(h->band, L.N, K, P, h->d, h->absmax, eps, f.ULt, h->n_boosted, s));
@@ -165,10 +177,36 @@ struct Solver : SolverBase {
     return SAP_OK;
   }
 
+  // chunk matrices of the transposed sweeps (U^T forward, L^T backward)
+  sap_status_t build_transposed(cudaStream_t s) {
+    if (transposed_ready) return SAP_OK;
+    const Layout& L = h->L;
+    if (!f.Mutf) {
+      TRY(h->mem.alloc(&f.Mutf, (size_t)L.c_elems));
+      TRY(h->mem.alloc(&f.Mltb, (size_t)L.c_elems));
+    }
+    CK(launch_chunk_mats<T>(f.F, L.K, L.P, h->d, f.cbase, L.max_nch, 2, f.Mutf, s));
+    CK(launch_chunk_mats<T>(f.F, L.K, L.P, h->d, f.cbase, L.max_nch, 3, f.Mltb, s));
+    transposed_ready = true;
+    return SAP_OK;
+  }
+
   sap_status_t apply(const double* r, double* z, bool transpose, cudaStream_t s) override {
-    if (transpose) TRY(build_adjoint(s));
+    if (transpose) {
+      TRY(build_adjoint(s));
+      TRY(build_transposed(s));
+    }
     CK(launch_apply<T>(h->band, h->L.N, h->L.K, h->L.P, h->d, f, h->opt.variant, transpose, r, z, scratch, s));
     return SAP_OK;
+  }
+
+  sap_status_t take_device_error(cudaStream_t s) override {
+    int e = 0;
+    CK(cudaMemcpyAsync(&e, f.err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (!e) return SAP_OK;
+    CK(cudaMemsetAsync(f.err, 0, sizeof(int), s));
+    return SAP_ERR_TIMEOUT;
   }
 
   sap_status_t block_lu(int i, double* host, cudaStream_t s) override {
@@ -329,6 +367,7 @@ sap_status_t krylov(sap_handle* h, const double* b, double* x, bool tr, sap_info
   }
   CK(cudaEventRecord(h->ev1, s));
   CK(cudaEventSynchronize(h->ev1));
+  if (h->impl->take_device_error(s) != SAP_OK) status = SAP_ERR_TIMEOUT;
   float ms = 0.f;
   cudaEventElapsedTime(&ms, h->ev0, h->ev1);
   inf.n_matvec = nmv;
@@ -420,13 +459,26 @@ sap_status_t sap_factor(const double* band_dev, int64_t N, int32_t K, const sap_
     acc += L.ld[i] * L.W;
   }
   L.f_elems = acc;
-  int64_t *doff, *dfb, *dld;
+  std::vector<int64_t> cb(L.P);
+  int64_t cacc = 0;
+  L.max_nch = 0;
+  for (int i = 0; i < L.P; ++i) {
+    cb[i] = cacc;
+    const int nch = (int)(L.ld[i] / 32);
+    cacc += (int64_t)nch * (1 + chunk_couplings(K)) * 32 * 32;
+    if (nch > L.max_nch) L.max_nch = nch;
+  }
+  L.c_elems = cacc;
+  int64_t *doff, *dfb, *dld, *dcb;
   TRY(h->mem.alloc(&doff, L.P + 1));
   TRY(h->mem.alloc(&dfb, L.P));
   TRY(h->mem.alloc(&dld, L.P));
   CK(cudaMemcpyAsync(doff, L.off.data(), (L.P + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(dfb, L.fbase.data(), L.P * sizeof(int64_t), cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(dld, L.ld.data(), L.P * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+  TRY(h->mem.alloc(&dcb, L.P));
+  CK(cudaMemcpyAsync(dcb, cb.data(), L.P * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+  h->dcbase = dcb;
   h->d = Dev{doff, dfb, dld};
   TRY(h->mem.alloc(&h->absmax, 1));
   TRY(h->mem.alloc(&h->n_boosted, 1));

@@ -14,6 +14,8 @@ constexpr size_t kSmemPerBlock = 232448;   // opt-in shared memory per CTA on sm
 
 // Dynamic shared memory of the sweep and factor kernels for half-bandwidth K.
 size_t sweep_smem_bytes(int K, bool fp64);
+// Coupling matrices per chunk of the blocked sweeps: ceil(K / 32).
+int chunk_couplings(int K);
 size_t lu_smem_bytes(int K, bool fp64);
 
 // Factor storage of one block (per block i, local rows/cols 0..n_i-1):
@@ -27,6 +29,8 @@ struct Layout {
   std::vector<int64_t> fbase;  // element offset of block i in the factor array
   std::vector<int64_t> ld;     // leading dimension of block i
   int64_t f_elems = 0;
+  int64_t c_elems = 0;   // chunk-matrix elements per sweep kind (all blocks)
+  int max_nch = 0;       // most 32-row chunks in one block
 };
 
 struct Dev {  // device copies of the partition, passed to kernels
@@ -46,6 +50,12 @@ struct Factors {
   double* R0 = nullptr;  // per interface: Rbar_i before factoring (kept for inspection)
   // adjoint SaP (built on demand)
   T* Va = nullptr; T* Wa = nullptr; double* Ra = nullptr; int* piva = nullptr; double* Ra0 = nullptr;
+  // chunk matrices of the blocked sweeps (MINV, G per 32-row chunk, sweep order):
+  // L forward, U backward (built with the factors), U^T forward, L^T backward
+  // (built on the first transposed apply).  cbase[i]: offset of block i.
+  T* Mlf = nullptr; T* Mub = nullptr; T* Mutf = nullptr; T* Mltb = nullptr;
+  const int64_t* cbase = nullptr;
+  int* err = nullptr;    // set to nonzero by a device-side wait that timed out
 };
 
 // Host-side count of kernel launches issued by the library (for reporting).
@@ -68,6 +78,9 @@ template <typename T>
 cudaError_t launch_spikes(const double* band, int64_t N, int K, int P, Dev d, const T* F, const T* ULt,
                           bool adjoint, T* V, T* Wt, double* Rinv, double* R0, int* piv, int* singular,
                           cudaStream_t s);
+template <typename T>
+cudaError_t launch_chunk_mats(const T* F, int K, int P, Dev d, const int64_t* cbase, int max_nch, int mode, T* out,
+                              cudaStream_t s);
 template <typename T>
 cudaError_t launch_apply(const double* band, int64_t N, int K, int P, Dev d, const Factors<T>& f,
                          int variant, bool transpose, const double* r, double* z, double* scratch,

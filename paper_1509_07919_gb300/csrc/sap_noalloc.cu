@@ -53,30 +53,43 @@ template <typename T>
 sap_status_t run(const double* band, int64_t N, int K, const double* b, double* x, cudaStream_t s) {
   const int W = 2 * K + 1;
   const int64_t ld = (N + 31) / 32 * 32;
-  // scratch layout: header | factors | sweep scratch
+  // scratch layout: header | factors | chunk matrices (L, U sweeps) | sweep scratch
   const size_t hdr = 256;
   const size_t f_bytes = align256((size_t)ld * W * sizeof(T));
+  const size_t c_elems = (size_t)(ld / 32) * (1 + chunk_couplings(K)) * 32 * 32;
+  const size_t c_bytes = align256(c_elems * sizeof(T));
   const size_t a_bytes = align256((size_t)(2 * N + 2 * K + 8) * sizeof(double));
-  if (hdr + f_bytes + a_bytes > kScratchBytes) return SAP_ERR_INVALID_ARG;
+  if (hdr + f_bytes + 2 * c_bytes + a_bytes > kScratchBytes) return SAP_ERR_INVALID_ARG;
   void* base = nullptr;
   if (scratch_address(&base) != cudaSuccess) return SAP_ERR_CUDA;
   unsigned char* p = static_cast<unsigned char*>(base);
-  int64_t* desc = reinterpret_cast<int64_t*>(p);        // off[2], fbase[1], ld[1]
+  int64_t* desc = reinterpret_cast<int64_t*>(p);        // off[2], fbase[1], ld[1], cbase[1]
   double* absmax = reinterpret_cast<double*>(p + 64);
   unsigned long long* nb = reinterpret_cast<unsigned long long*>(p + 128);
+  int* err = reinterpret_cast<int*>(p + 192);
   T* F = reinterpret_cast<T*>(p + hdr);
-  double* ascratch = reinterpret_cast<double*>(p + hdr + f_bytes);
-  const int64_t h_desc[4] = {0, N, 0, ld};
+  T* Mlf = reinterpret_cast<T*>(p + hdr + f_bytes);
+  T* Mub = reinterpret_cast<T*>(p + hdr + f_bytes + c_bytes);
+  double* ascratch = reinterpret_cast<double*>(p + hdr + f_bytes + 2 * c_bytes);
+  const int64_t h_desc[5] = {0, N, 0, ld, 0};
   if (cudaMemcpyAsync(desc, h_desc, sizeof(h_desc), cudaMemcpyHostToDevice, s) != cudaSuccess) return SAP_ERR_CUDA;
   // counters start at zero; factor padding columns are read as zeros by the sweeps
   if (cudaMemsetAsync(nb, 0, sizeof(*nb), s) != cudaSuccess) return SAP_ERR_CUDA;
+  if (cudaMemsetAsync(err, 0, sizeof(*err), s) != cudaSuccess) return SAP_ERR_CUDA;
   if (cudaMemsetAsync(F, 0, (size_t)ld * W * sizeof(T), s) != cudaSuccess) return SAP_ERR_CUDA;
   Dev d{desc, desc + 2, desc + 3};
   const double eps = sizeof(T) == 8 ? 0x1p-53 : 0x1p-24;
   if (launch_absmax(band, N, K, absmax, s) != cudaSuccess) return SAP_ERR_CUDA;
   if (launch_factor_lu<T>(band, N, K, 1, d, absmax, eps, F, nb, s) != cudaSuccess) return SAP_ERR_CUDA;
+  const int64_t* cbase = desc + 4;
+  if (launch_chunk_mats<T>(F, K, 1, d, cbase, (int)(ld / 32), 0, Mlf, s) != cudaSuccess) return SAP_ERR_CUDA;
+  if (launch_chunk_mats<T>(F, K, 1, d, cbase, (int)(ld / 32), 1, Mub, s) != cudaSuccess) return SAP_ERR_CUDA;
   Factors<T> f;
   f.F = F;
+  f.Mlf = Mlf;
+  f.Mub = Mub;
+  f.cbase = cbase;
+  f.err = err;
   if (launch_apply<T>(band, N, K, 1, d, f, SAP_D, false, b, x, ascratch, s) != cudaSuccess) return SAP_ERR_CUDA;
   return SAP_OK;
 }

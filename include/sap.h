@@ -178,8 +178,9 @@ SAP_API const char *sap_status_string(sap_status_t s);
  * factorisation's rounding; no Krylov iteration.
  *   All intermediates live in one file-scope device array of 32 MiB that
  *   every GPU loading the library holds until the process exits; the call
- *   needs (N rounded up to 32) (2K+1) sizeof(factor) + (2N + 2K + 8) 8 bytes
- *   plus 256-byte alignment, and returns SAP_ERR_INVALID_ARG beyond that.
+ *   needs, with n = N rounded up to 32 and s = sizeof(factor), about
+ *   n (2K+1) s (factors) + 2 n 32 (1 + ceil(K/32)) s (sweep matrices) +
+ *   (2N + 2K + 8) 8 bytes, and returns SAP_ERR_INVALID_ARG beyond that.
  *   The caller still provides band_dev, b_dev and x_dev (device, float64).
  *   The first call on a device looks up the array's device address; make
  *   that first call before any stream capture.

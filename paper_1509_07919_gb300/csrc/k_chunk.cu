@@ -28,25 +28,22 @@ constexpr int CH = 32;
 // position pc (pc <= pr), for sweep kind MODE, or 0 outside the band or the
 // block.  F[c * ld + q] = entry (r, q), c = K + r - q (unit-lower L below,
 // U on and above the diagonal).
-template <int MODE>
-__device__ __forceinline__ double sweep_entry(const void* Fv, bool fp64, int K, int n, int ld, int pr, int pc) {
+template <int MODE, typename T>
+__device__ __forceinline__ T sweep_entry(const T* F, int K, int n, int ld, int pr, int pc) {
   const bool fwd = (MODE == 0 || MODE == 2);          // LF, UTF
   const int r = fwd ? pr : ld - 1 - pr;
   const int q = fwd ? pc : ld - 1 - pc;
-  if (r >= n || q >= n || r < 0 || q < 0) return (pr == pc) ? 1.0 : 0.0;   // padding rows: identity
+  if (r >= n || q >= n || r < 0 || q < 0) return (pr == pc) ? T(1) : T(0);   // padding rows: identity
   int fr, fq;               // factor entry (fr, fq)
   bool unit;
   if (MODE == 0) { fr = r; fq = q; unit = true; }       // L(r, q), q <= r
   else if (MODE == 1) { fr = r; fq = q; unit = false; } // U(r, q), q >= r
   else if (MODE == 2) { fr = q; fq = r; unit = false; } // U^T(r, q) = U(q, r)
   else { fr = q; fq = r; unit = true; }                 // L^T(r, q) = L(q, r)
-  if (pr == pc) {
-    if (unit) return 1.0;
-  }
+  if (pr == pc && unit) return T(1);
   const int c = K + fr - fq;
-  if (c < 0 || c > 2 * K) return 0.0;
-  const int64_t idx = (int64_t)c * ld + fq;
-  return fp64 ? static_cast<const double*>(Fv)[idx] : (double)static_cast<const float*>(Fv)[idx];
+  if (c < 0 || c > 2 * K) return T(0);
+  return F[(int64_t)c * ld + fq];
 }
 
 template <typename T, int MODE>
@@ -63,13 +60,12 @@ k_chunk_mats(const T* __restrict__ Fall, int K, Dev d, const int64_t* __restrict
   if (c >= nch) return;
   const int n = (int)(d.off[b + 1] - d.off[b]);
   const T* F = Fall + d.fbase[b];
-  const bool fp64 = sizeof(T) == 8;
   const int tid = threadIdx.x;
   const int p0 = c * CH;
   for (int e = tid; e < CH * CH; e += blockDim.x) {
     const int t = e / CH, j = e % CH;
     // in-chunk lower-triangular block
-    A[t][j] = (j <= t) ? (T)sweep_entry<MODE>(F, fp64, K, n, ld, p0 + t, p0 + j) : T(0);
+    A[t][j] = (j <= t) ? sweep_entry<MODE>(F, K, n, ld, p0 + t, p0 + j) : T(0);
     X[t][j] = T(0);
   }
   __syncthreads();
@@ -96,7 +92,7 @@ k_chunk_mats(const T* __restrict__ Fall, int K, Dev d, const int64_t* __restrict
     for (int e = tid; e < CH * CH; e += blockDim.x) {
       const int t = e / CH, j = e % CH;
       const int dist = k * CH + t - j;    // position distance to column j of chunk c - k
-      Bc[t][j] = (c >= k && dist <= K) ? (T)sweep_entry<MODE>(F, fp64, K, n, ld, p0 + t, p0 - k * CH + j) : T(0);
+      Bc[t][j] = (c >= k && dist <= K) ? sweep_entry<MODE>(F, K, n, ld, p0 + t, p0 - k * CH + j) : T(0);
     }
     __syncthreads();
     T* G = M + (int64_t)k * CH * CH;

@@ -36,14 +36,21 @@ __device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
   unsigned s = (unsigned)__cvta_generic_to_shared(smem);
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
 }
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+  unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+template <typename X> __device__ __forceinline__ void cp_async_t(X* smem, const X* gmem) {
+  if (sizeof(X) == 4) cp_async4(smem, gmem); else cp_async8(smem, gmem);
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
 // Entries of the block in local coordinates (r, q), reversed when REV.
 // Returns a pointer into the band, or nullptr for a structural zero.
-template <bool REV>
-__device__ __forceinline__ const double* elem_ptr(const double* band, int64_t N, int K, int64_t s,
-                                                  int n, int r, int q) {
+template <bool REV, typename BT>
+__device__ __forceinline__ const BT* elem_ptr(const BT* band, int64_t N, int K, int64_t s,
+                                              int n, int r, int q) {
   if (r < 0 || q < 0 || r >= n || q >= n) return nullptr;
   int64_t gi = REV ? s + n - 1 - r : s + r;
   int64_t gj = REV ? s + n - 1 - q : s + q;
@@ -78,9 +85,9 @@ __device__ __forceinline__ void ld4(const T* p, T (&v)[4]) {
   }
 }
 
-template <typename T, int MR, bool REV>
+template <typename T, bool REV>
 __global__ void __launch_bounds__(NTHREADS)
-k_band_lu(const double* __restrict__ band, int64_t N, int K, Dev d, int block0,
+k_band_lu(const T* __restrict__ band, int64_t N, int K, Dev d, int block0,
           const double* __restrict__ absmax, double eps, T* __restrict__ out,
           unsigned long long* __restrict__ n_boosted) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -93,8 +100,9 @@ k_band_lu(const double* __restrict__ band, int64_t N, int K, Dev d, int block0,
   const int ME = M2 - NB;         // rows of the next window that are already resident
   T* W = reinterpret_cast<T*>(smem_raw);
   size_t woff = ((size_t)M2 * LDW * sizeof(T) + 15) & ~(size_t)15;
-  double* ER = reinterpret_cast<double*>(smem_raw + woff);   // NB x M2 entering rows
-  double* EC = ER + NB * M2;                                   // ME x NB entering columns
+  T* ER = reinterpret_cast<T*>(smem_raw + woff);   // NB x M2 entering rows
+  T* EC = ER + NB * M2;                              // ME x NB entering columns
+  T* RV = EC + ME * NB;                              // NB reciprocals of the panel's pivots
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const T tau = (T)(eps * absmax[0]);
   unsigned long long nb = 0;
@@ -105,39 +113,35 @@ k_band_lu(const double* __restrict__ band, int64_t N, int K, Dev d, int block0,
   // initial window: logical rows/cols [0, M2), physical == logical
   for (int e = tid; e < M2 * M2; e += NTHREADS) {
     int r = e / M2, q = e % M2;
-    const double* p = elem_ptr<REV>(band, N, K, s, n, r, q);
-    W[r * LDW + q] = p ? (T)(*p) : T(0);
+    const T* p = elem_ptr<REV>(band, N, K, s, n, r, q);
+    W[r * LDW + q] = p ? *p : T(0);
   }
   __syncthreads();
 
   for (int k0 = 0; k0 < n; k0 += NB) {
     const int base = w.base;     // physical column of the panel start (multiple of NB)
-    // ---- A: panel factorisation (warp 0) || prefetch of the entering data (warps 1..7) ----
+    // ---- A1: LU of the NB x NB diagonal block (warp 0) || prefetch (warps 1..7) ----
     if (warp == 0) {
-      T pv[MR][NB];
+      T pv[NB];
+      if (lane < NB) {
+        const T* row = &W[(base + lane) * LDW + base];
 #pragma unroll
-      for (int m = 0; m < MR; ++m) {
-        const int off = lane + 32 * m;
-        if (off < KA) {
-          const T* row = &W[w.ph(off) * LDW + base];
+        for (int c4 = 0; c4 < NB / 4; ++c4) {
+          T v[4];
+          ld4(row + 4 * c4, v);
 #pragma unroll
-          for (int c4 = 0; c4 < NB / 4; ++c4) {
-            T v[4];
-            ld4(row + 4 * c4, v);
-#pragma unroll
-            for (int x = 0; x < 4; ++x) pv[m][4 * c4 + x] = v[x];
-          }
-        } else {
-#pragma unroll
-          for (int c = 0; c < NB; ++c) pv[m][c] = T(0);
+          for (int x = 0; x < 4; ++x) pv[4 * c4 + x] = v[x];
         }
+      } else {
+#pragma unroll
+        for (int c = 0; c < NB; ++c) pv[c] = T(0);
       }
+      T myrinv = T(0);
 #pragma unroll
       for (int j = 0; j < NB; ++j) {
-        // pivot row j (owned by lane j, m = 0): entries j..NB-1
         T u[NB];
 #pragma unroll
-        for (int c = j; c < NB; ++c) u[c] = __shfl_sync(0xffffffffu, pv[0][c], j);
+        for (int c = j; c < NB; ++c) u[c] = __shfl_sync(0xffffffffu, pv[c], j);
         T p = u[j];
         if (k0 + j < n) {
           if ((p < T(0) ? -p : p) < tau) {
@@ -148,27 +152,21 @@ k_band_lu(const double* __restrict__ band, int64_t N, int K, Dev d, int block0,
           p = T(1);   // padding past the block: rows there are all zero
         }
         const T rinv = rcp(p);
+        if (lane > j) {
+          const T l = pv[j] * rinv;
+          pv[j] = l;
 #pragma unroll
-        for (int m = 0; m < MR; ++m) {
-          const int off = lane + 32 * m;
-          if (off > j) {
-            const T l = pv[m][j] * rinv;
-            pv[m][j] = l;
-#pragma unroll
-            for (int c = j + 1; c < NB; ++c) pv[m][c] -= l * u[c];
-          } else if (off == j) {
-            pv[m][j] = p;
-          }
+          for (int c = j + 1; c < NB; ++c) pv[c] -= l * u[c];
+        } else if (lane == j) {
+          pv[j] = p;
+          myrinv = rinv;
         }
       }
+      if (lane < NB) {
+        T* row = &W[(base + lane) * LDW + base];
 #pragma unroll
-      for (int m = 0; m < MR; ++m) {
-        const int off = lane + 32 * m;
-        if (off < KA) {
-          T* row = &W[w.ph(off) * LDW + base];
-#pragma unroll
-          for (int c = 0; c < NB; ++c) row[c] = pv[m][c];
-        }
+        for (int c = 0; c < NB; ++c) row[c] = pv[c];
+        RV[lane] = myrinv;
       }
     } else {
       // entering rows i = k0 + M2 + e (columns of the next window, offsets jo from k0 + NB)
@@ -176,46 +174,61 @@ k_band_lu(const double* __restrict__ band, int64_t N, int K, Dev d, int block0,
       const int hw = warp - 1, ht = tid - 32, nh = NTHREADS - 32;
       for (int e = hw; e < NB; e += NTHREADS / 32 - 1)
         for (int jo = lane; jo < M2; jo += 32) {
-          double* dst = &ER[e * M2 + jo];
-          const double* src = elem_ptr<REV>(band, N, K, s, n, k0 + M2 + e, k0 + NB + jo);
-          if (src) cp_async8(dst, src);
-          else *dst = 0.0;
+          T* dst = &ER[e * M2 + jo];
+          const T* src = elem_ptr<REV>(band, N, K, s, n, k0 + M2 + e, k0 + NB + jo);
+          if (src) cp_async_t(dst, src);
+          else *dst = T(0);
         }
       for (int y = ht; y < ME * NB; y += nh) {
         const int ro = y / NB, e = y % NB;
-        double* dst = &EC[y];
-        const double* src = elem_ptr<REV>(band, N, K, s, n, k0 + NB + ro, k0 + M2 + e);
-        if (src) cp_async8(dst, src);
-        else *dst = 0.0;
+        T* dst = &EC[y];
+        const T* src = elem_ptr<REV>(band, N, K, s, n, k0 + NB + ro, k0 + M2 + e);
+        if (src) cp_async_t(dst, src);
+        else *dst = T(0);
       }
       cp_async_commit();
     }
     __syncthreads();
 
-    // ---- B: U12 = L11^{-1} A12 (panel rows, window columns NB..KA-1) ----
-    for (int c = NB + tid; c < KA; c += NTHREADS) {
-      const int pc = w.ph(c);
-      T x[NB];
-#pragma unroll
-      for (int r = 0; r < NB; ++r) x[r] = W[(base + r) * LDW + pc];
-#pragma unroll
-      for (int r = 1; r < NB; ++r) {
-        const T* Lr = &W[(base + r) * LDW + base];
-        T lr[NB];
+    // ---- A2: L21 = A21 U11^{-1} (rows NB..KA-1, threads 0..127) ||
+    //      B:  U12 = L11^{-1} A12 (columns NB..KA-1, threads 128..255) ----
+    if (tid < NTHREADS / 2) {
+      for (int ro = NB + tid; ro < KA; ro += NTHREADS / 2) {
+        T* row = &W[w.ph(ro) * LDW + base];
+        T x[NB];
 #pragma unroll
         for (int c4 = 0; c4 < NB / 4; ++c4) {
           T v[4];
-          ld4(Lr + 4 * c4, v);
+          ld4(row + 4 * c4, v);
 #pragma unroll
-          for (int y = 0; y < 4; ++y) lr[4 * c4 + y] = v[y];
+          for (int y = 0; y < 4; ++y) x[4 * c4 + y] = v[y];
         }
-        T acc = x[r];
 #pragma unroll
-        for (int q = 0; q < r; ++q) acc -= lr[q] * x[q];
-        x[r] = acc;
+        for (int j = 0; j < NB; ++j) {
+          T acc = x[j];
+#pragma unroll
+          for (int q = 0; q < j; ++q) acc -= x[q] * W[(base + q) * LDW + base + j];
+          x[j] = acc * RV[j];
+        }
+#pragma unroll
+        for (int c = 0; c < NB; ++c) row[c] = x[c];
       }
+    } else {
+      for (int c = NB + tid - NTHREADS / 2; c < KA; c += NTHREADS / 2) {
+        const int pc = w.ph(c);
+        T x[NB];
 #pragma unroll
-      for (int r = 1; r < NB; ++r) W[(base + r) * LDW + pc] = x[r];
+        for (int r = 0; r < NB; ++r) x[r] = W[(base + r) * LDW + pc];
+#pragma unroll
+        for (int r = 1; r < NB; ++r) {
+          T acc = x[r];
+#pragma unroll
+          for (int q = 0; q < r; ++q) acc -= W[(base + r) * LDW + base + q] * x[q];
+          x[r] = acc;
+        }
+#pragma unroll
+        for (int r = 1; r < NB; ++r) W[(base + r) * LDW + pc] = x[r];
+      }
     }
     __syncthreads();
 
@@ -276,11 +289,11 @@ k_band_lu(const double* __restrict__ band, int64_t N, int K, Dev d, int block0,
       Win w2{M2, LDW, w.ph(NB)};        // next window: logical offset 0 = k0 + NB
       for (int e = warp; e < NB; e += NTHREADS / 32) {
         T* row = &W[w2.ph(ME + e) * LDW];                      // row k0+M2+e = next offset ME+e
-        for (int jo = lane; jo < M2; jo += 32) row[w2.ph(jo)] = (T)ER[e * M2 + jo];
+        for (int jo = lane; jo < M2; jo += 32) row[w2.ph(jo)] = ER[e * M2 + jo];
       }
       for (int y = tid; y < ME * NB; y += NTHREADS) {
         const int ro = y / NB, e = y % NB;
-        W[w2.ph(ro) * LDW + w2.ph(ME + e)] = (T)EC[y];        // column k0+M2+e, row k0+NB+ro
+        W[w2.ph(ro) * LDW + w2.ph(ME + e)] = EC[y];           // column k0+M2+e, row k0+NB+ro
       }
       w = w2;
     }
@@ -290,32 +303,19 @@ k_band_lu(const double* __restrict__ band, int64_t N, int K, Dev d, int block0,
 }
 
 template <typename T, bool REV>
-cudaError_t launch_lu_impl(const double* band, int64_t N, int K, int nblocks, int block0, Dev d,
+cudaError_t launch_lu_impl(const T* band, int64_t N, int K, int nblocks, int block0, Dev d,
                            const double* absmax, double eps, T* out, unsigned long long* nb,
                            cudaStream_t s) {
   if (nblocks <= 0) return cudaSuccess;
   const int M2 = win_m2(K);
   const int LDW = M2 + 4;
   size_t smem = (((size_t)M2 * LDW * sizeof(T) + 15) & ~(size_t)15) +
-                ((size_t)NB * M2 + (size_t)(M2 - NB) * NB) * sizeof(double);
-  const int MR = (K + NB + 31) / 32;
-  cudaError_t e = cudaSuccess;
-#define SAP_LAUNCH_LU(RR)                                                                           \
-  do {                                                                                              \
-    auto kern = k_band_lu<T, RR, REV>;                                                             \
-    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);         \
-    if (e != cudaSuccess) return e;                                                                 \
-    count_launches(1);                                                                              \
-    kern<<<nblocks, NTHREADS, smem, s>>>(band, N, K, d, block0, absmax, eps, out, nb);             \
-  } while (0)
-  switch (MR) {
-    case 1: SAP_LAUNCH_LU(1); break;
-    case 2: SAP_LAUNCH_LU(2); break;
-    case 3: SAP_LAUNCH_LU(3); break;
-    case 4: SAP_LAUNCH_LU(4); break;
-    default: SAP_LAUNCH_LU(5); break;
-  }
-#undef SAP_LAUNCH_LU
+                ((size_t)NB * M2 + (size_t)(M2 - NB) * NB + NB) * sizeof(T);
+  auto kern = k_band_lu<T, REV>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  count_launches(1);
+  kern<<<nblocks, NTHREADS, smem, s>>>(band, N, K, d, block0, absmax, eps, out, nb);
   return cudaGetLastError();
 }
 
@@ -324,7 +324,7 @@ cudaError_t launch_lu_impl(const double* band, int64_t N, int K, int nblocks, in
 size_t lu_smem_bytes(int K, bool fp64) {
   const int M2 = win_m2(K);
   const size_t ts = fp64 ? sizeof(double) : sizeof(float);
-  return (((size_t)M2 * (M2 + 4) * ts + 15) & ~(size_t)15) + ((size_t)NB * M2 + (size_t)(M2 - NB) * NB) * sizeof(double);
+  return (((size_t)M2 * (M2 + 4) * ts + 15) & ~(size_t)15) + ((size_t)NB * M2 + (size_t)(M2 - NB) * NB + NB) * ts;
 }
 
 namespace {
@@ -344,7 +344,38 @@ __global__ void k_absmax(const double* __restrict__ band, int64_t N, int K, doub
     atomicMax(reinterpret_cast<unsigned long long*>(out), (unsigned long long)__double_as_longlong(m));
 }
 
+// max |a_ij| over the in-band entries and an FP32 copy of the band (RN),
+// padding slots written as 0: the FP32 factorisation then loads FP32.
+__global__ void k_absmax_cast(const double* __restrict__ band, int64_t N, int K, double* out,
+                              float* __restrict__ bandf) {
+  const int64_t total = (int64_t)(2 * K + 1) * N;
+  double m = 0.0;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t c = e / N, j = e - c * N;
+    int64_t i = j + c - K;
+    float v = 0.f;
+    if (i >= 0 && i < N) {
+      const double a = band[e];
+      m = fmax(m, fabs(a));
+      v = (float)a;
+    }
+    bandf[e] = v;
+  }
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0)
+    atomicMax(reinterpret_cast<unsigned long long*>(out), (unsigned long long)__double_as_longlong(m));
+}
+
 }  // namespace
+
+cudaError_t launch_absmax_cast(const double* band, int64_t N, int K, double* out, float* bandf, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(out, 0, sizeof(double), s);
+  if (e != cudaSuccess) return e;
+  count_launches(1);
+  k_absmax_cast<<<152 * 8, 256, 0, s>>>(band, N, K, out, bandf);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_absmax(const double* band, int64_t N, int K, double* out, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(out, 0, sizeof(double), s);
@@ -355,23 +386,23 @@ cudaError_t launch_absmax(const double* band, int64_t N, int K, double* out, cud
 }
 
 template <typename T>
-cudaError_t launch_factor_lu(const double* band, int64_t N, int K, int P, Dev d, const double* absmax,
+cudaError_t launch_factor_lu(const T* band, int64_t N, int K, int P, Dev d, const double* absmax,
                              double eps, T* F, unsigned long long* nb, cudaStream_t s) {
   return launch_lu_impl<T, false>(band, N, K, P, 0, d, absmax, eps, F, nb, s);
 }
 
 template <typename T>
-cudaError_t launch_factor_ul(const double* band, int64_t N, int K, int P, Dev d, const double* absmax,
+cudaError_t launch_factor_ul(const T* band, int64_t N, int K, int P, Dev d, const double* absmax,
                              double eps, T* ULt, unsigned long long* nb, cudaStream_t s) {
   // UL tiles are only needed for blocks 1..P-1 (the W^(t) tips)
   return launch_lu_impl<T, true>(band, N, K, P - 1, 1, d, absmax, eps, ULt, nb, s);
 }
 
-template cudaError_t launch_factor_lu<float>(const double*, int64_t, int, int, Dev, const double*, double,
+template cudaError_t launch_factor_lu<float>(const float*, int64_t, int, int, Dev, const double*, double,
                                              float*, unsigned long long*, cudaStream_t);
 template cudaError_t launch_factor_lu<double>(const double*, int64_t, int, int, Dev, const double*, double,
                                               double*, unsigned long long*, cudaStream_t);
-template cudaError_t launch_factor_ul<float>(const double*, int64_t, int, int, Dev, const double*, double,
+template cudaError_t launch_factor_ul<float>(const float*, int64_t, int, int, Dev, const double*, double,
                                              float*, unsigned long long*, cudaStream_t);
 template cudaError_t launch_factor_ul<double>(const double*, int64_t, int, int, Dev, const double*, double,
                                               double*, unsigned long long*, cudaStream_t);

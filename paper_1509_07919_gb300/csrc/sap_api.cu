@@ -101,6 +101,7 @@ struct Solver : SolverBase {
   sap_handle* h;
   Factors<T> f;
   double* scratch = nullptr;   // apply scratch: g (N), T tmp (N), ctop/cbot
+  float* bandf = nullptr;      // FP32 copy of the band (FP32 factorisation only)
   bool adjoint_ready = false;
   bool transposed_ready = false;
   explicit Solver(sap_handle* hh) : h(hh) {}
@@ -114,6 +115,7 @@ struct Solver : SolverBase {
     // the padding columns [n_i, ld_i) of every block are read by the sweeps and must be 0
     CK(cudaMemset(f.F, 0, (size_t)L.f_elems * sizeof(T)));
     TRY(h->mem.alloc(&scratch, (size_t)(2 * L.N + 2 * nI * K + 8)));
+    if (sizeof(T) == 4) TRY(h->mem.alloc(&bandf, (size_t)L.N * L.W));
     TRY(h->mem.alloc(&f.err, 1));
     CK(cudaMemset(f.err, 0, sizeof(int)));
     TRY(h->mem.alloc(&f.Mlf, (size_t)L.c_elems));
@@ -138,14 +140,16 @@ struct Solver : SolverBase {
     const double eps = h->opt.boost_eps;
     adjoint_ready = false;
     CK(cudaEventRecord(h->evp[0], s));
-    CK(launch_absmax(h->band, L.N, K, h->absmax, s));
-    CK(launch_factor_lu<T>(h->band, L.N, K, P, h->d, h->absmax, eps, f.F, h->n_boosted, s));
+    const T* bandT = band_in_T();
+    if (sizeof(T) == 4) CK(launch_absmax_cast(h->band, L.N, K, h->absmax, bandf, s));
+    else CK(launch_absmax(h->band, L.N, K, h->absmax, s));
+    CK(launch_factor_lu<T>(bandT, L.N, K, P, h->d, h->absmax, eps, f.F, h->n_boosted, s));
     CK(launch_chunk_mats<T>(f.F, K, P, h->d, f.cbase, L.max_nch, 0, f.Mlf, s));
     CK(launch_chunk_mats<T>(f.F, K, P, h->d, f.cbase, L.max_nch, 1, f.Mub, s));
     transposed_ready = false;
     CK(cudaEventRecord(h->evp[1], s));
     if (h->opt.variant == SAP_C && P > 1) {
-      CK(launch_factor_ul<T>(h->band, L.N, K, P, h->d, h->absmax, eps, f.ULt, h->n_boosted, s));
+      CK(launch_factor_ul<T>(bandT, L.N, K, P, h->d, h->absmax, eps, f.ULt, h->n_boosted, s));
       CK(cudaEventRecord(h->evp[2], s));
       CK(launch_spikes<T>(h->band, L.N, K, P, h->d, f.F, f.ULt, false, f.V, f.Wt, f.R, f.R0, f.piv,
                           h->singular, s));
@@ -175,6 +179,12 @@ struct Solver : SolverBase {
     if (sing) return SAP_ERR_SINGULAR;
     adjoint_ready = true;
     return SAP_OK;
+  }
+
+  // the band in the factor precision: the borrowed FP64 band, or its FP32 copy
+  const T* band_in_T() const {
+    if (sizeof(T) == 8) return reinterpret_cast<const T*>(h->band);
+    return reinterpret_cast<const T*>(bandf);
   }
 
   // chunk matrices of the transposed sweeps (U^T forward, L^T backward)

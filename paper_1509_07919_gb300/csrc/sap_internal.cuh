@@ -68,11 +68,13 @@ cudaError_t launch_absmax(const double* band, int64_t N, int K, double* out, cud
 cudaError_t launch_grad_band(const double* lam, const double* x, int64_t N, int K, double* g,
                              cudaStream_t s);
 
+// FP32 path: absmax plus an FP32 copy of the band (the factor kernels load it)
+cudaError_t launch_absmax_cast(const double* band, int64_t N, int K, double* out, float* bandf, cudaStream_t s);
 template <typename T>
-cudaError_t launch_factor_lu(const double* band, int64_t N, int K, int P, Dev d, const double* absmax,
+cudaError_t launch_factor_lu(const T* band, int64_t N, int K, int P, Dev d, const double* absmax,
                              double eps, T* F, unsigned long long* n_boosted, cudaStream_t s);
 template <typename T>
-cudaError_t launch_factor_ul(const double* band, int64_t N, int K, int P, Dev d, const double* absmax,
+cudaError_t launch_factor_ul(const T* band, int64_t N, int K, int P, Dev d, const double* absmax,
                              double eps, T* ULt, unsigned long long* n_boosted, cudaStream_t s);
 template <typename T>
 cudaError_t launch_spikes(const double* band, int64_t N, int K, int P, Dev d, const T* F, const T* ULt,

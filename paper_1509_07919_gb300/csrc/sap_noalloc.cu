@@ -59,7 +59,8 @@ sap_status_t run(const double* band, int64_t N, int K, const double* b, double* 
   const size_t c_elems = (size_t)(ld / 32) * (1 + chunk_couplings(K)) * 32 * 32;
   const size_t c_bytes = align256(c_elems * sizeof(T));
   const size_t a_bytes = align256((size_t)(2 * N + 2 * K + 8) * sizeof(double));
-  if (hdr + f_bytes + 2 * c_bytes + a_bytes > kScratchBytes) return SAP_ERR_INVALID_ARG;
+  const size_t b_bytes = sizeof(T) == 4 ? align256((size_t)N * W * sizeof(float)) : 0;   // FP32 band copy
+  if (hdr + f_bytes + 2 * c_bytes + a_bytes + b_bytes > kScratchBytes) return SAP_ERR_INVALID_ARG;
   void* base = nullptr;
   if (scratch_address(&base) != cudaSuccess) return SAP_ERR_CUDA;
   unsigned char* p = static_cast<unsigned char*>(base);
@@ -71,6 +72,7 @@ sap_status_t run(const double* band, int64_t N, int K, const double* b, double* 
   T* Mlf = reinterpret_cast<T*>(p + hdr + f_bytes);
   T* Mub = reinterpret_cast<T*>(p + hdr + f_bytes + c_bytes);
   double* ascratch = reinterpret_cast<double*>(p + hdr + f_bytes + 2 * c_bytes);
+  float* bandf = reinterpret_cast<float*>(p + hdr + f_bytes + 2 * c_bytes + a_bytes);
   const int64_t h_desc[5] = {0, N, 0, ld, 0};
   if (cudaMemcpyAsync(desc, h_desc, sizeof(h_desc), cudaMemcpyHostToDevice, s) != cudaSuccess) return SAP_ERR_CUDA;
   // counters start at zero; factor padding columns are read as zeros by the sweeps
@@ -79,8 +81,15 @@ sap_status_t run(const double* band, int64_t N, int K, const double* b, double* 
   if (cudaMemsetAsync(F, 0, (size_t)ld * W * sizeof(T), s) != cudaSuccess) return SAP_ERR_CUDA;
   Dev d{desc, desc + 2, desc + 3};
   const double eps = sizeof(T) == 8 ? 0x1p-53 : 0x1p-24;
-  if (launch_absmax(band, N, K, absmax, s) != cudaSuccess) return SAP_ERR_CUDA;
-  if (launch_factor_lu<T>(band, N, K, 1, d, absmax, eps, F, nb, s) != cudaSuccess) return SAP_ERR_CUDA;
+  const T* bandT;
+  if (sizeof(T) == 4) {
+    if (launch_absmax_cast(band, N, K, absmax, bandf, s) != cudaSuccess) return SAP_ERR_CUDA;
+    bandT = reinterpret_cast<const T*>(bandf);
+  } else {
+    if (launch_absmax(band, N, K, absmax, s) != cudaSuccess) return SAP_ERR_CUDA;
+    bandT = reinterpret_cast<const T*>(band);
+  }
+  if (launch_factor_lu<T>(bandT, N, K, 1, d, absmax, eps, F, nb, s) != cudaSuccess) return SAP_ERR_CUDA;
   const int64_t* cbase = desc + 4;
   if (launch_chunk_mats<T>(F, K, 1, d, cbase, (int)(ld / 32), 0, Mlf, s) != cudaSuccess) return SAP_ERR_CUDA;
   if (launch_chunk_mats<T>(F, K, 1, d, cbase, (int)(ld / 32), 1, Mub, s) != cudaSuccess) return SAP_ERR_CUDA;

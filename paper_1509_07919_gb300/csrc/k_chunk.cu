@@ -46,13 +46,52 @@ __device__ __forceinline__ T sweep_entry(const T* F, int K, int n, int ld, int p
   return F[(int64_t)c * ld + fq];
 }
 
-template <typename T, int MODE>
-__global__ void __launch_bounds__(128)
-k_chunk_mats(const T* __restrict__ Fall, int K, Dev d, const int64_t* __restrict__ cbase, T* __restrict__ out) {
-  __shared__ T A[CH][CH + 1];
-  __shared__ T X[CH][CH + 1];     // MINV, column j computed by thread j
-  __shared__ T Bc[CH][CH + 1];
+constexpr int NT = 256;
+constexpr int LDS = CH + 1;      // padded shared-memory row
+
+// S[t][j] = sweep entry (p0 + t, p0 - k * 32 + j) where its position
+// distance k * 32 + t - j lies in [0, K], else 0 (identity padding comes
+// from sweep_entry).  Warps walk the 63 diagonals t - j = const with lane = j,
+// so each load of the band-stored factor reads consecutive addresses.
+template <int MODE, typename T>
+__device__ __forceinline__ void load_tile(T* S, const T* F, int K, int n, int ld, int p0, int k, int c) {
+  const int lane = threadIdx.x % 32, warp = threadIdx.x / 32;
+  constexpr int ROWS = (2 * CH - 1 + NT / 32 - 1) / (NT / 32);
+  T v[ROWS];
+#pragma unroll
+  for (int i = 0; i < ROWS; ++i) {
+    const int delta = warp + i * (NT / 32) - (CH - 1);   // t - j
+    const int t = lane + delta;
+    const int dist = k * CH + delta;
+    v[i] = (t >= 0 && t < CH && c >= k && dist >= 0 && dist <= K)
+               ? sweep_entry<MODE>(F, K, n, ld, p0 + t, p0 - k * CH + lane)
+               : T(0);
+  }
+#pragma unroll
+  for (int i = 0; i < ROWS; ++i) {
+    const int delta = warp + i * (NT / 32) - (CH - 1);
+    const int t = lane + delta;
+    if (delta < CH && t >= 0 && t < CH) S[t * LDS + lane] = v[i];
+  }
+}
+
+// Dynamic shared memory: A (in-chunk block), X (its inverse), ng coupling
+// tiles B_k, 32 reciprocal pivots.
+template <typename T>
+size_t chunk_smem_bytes(int K) {
   const int ng = (K + CH - 1) / CH;
+  return (size_t)(2 + ng) * CH * LDS * sizeof(T) + CH * sizeof(T);
+}
+
+template <typename T, int MODE>
+__global__ void __launch_bounds__(NT)
+k_chunk_mats(const T* __restrict__ Fall, int K, Dev d, const int64_t* __restrict__ cbase, T* __restrict__ out) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* A = reinterpret_cast<T*>(smem_raw);
+  T* X = A + CH * LDS;            // MINV
+  T* Bs = X + CH * LDS;           // B_1 .. B_ng
+  const int ng = (K + CH - 1) / CH;
+  T* Rd = Bs + ng * CH * LDS;
   const int b = blockIdx.y;
   const int ld = (int)d.ld[b];
   const int nch = ld / CH;
@@ -62,47 +101,65 @@ k_chunk_mats(const T* __restrict__ Fall, int K, Dev d, const int64_t* __restrict
   const T* F = Fall + d.fbase[b];
   const int tid = threadIdx.x;
   const int p0 = c * CH;
-  for (int e = tid; e < CH * CH; e += blockDim.x) {
-    const int t = e / CH, j = e % CH;
-    // in-chunk lower-triangular block
-    A[t][j] = (j <= t) ? sweep_entry<MODE>(F, K, n, ld, p0 + t, p0 + j) : T(0);
-    X[t][j] = T(0);
-  }
+  // every tile is loaded up front: the loads of all tiles are in flight together
+  load_tile<MODE>(A, F, K, n, ld, p0, 0, c);
+  for (int k = 1; k <= ng; ++k) load_tile<MODE>(Bs + (k - 1) * CH * LDS, F, K, n, ld, p0, k, c);
+  for (int e = tid; e < CH * CH; e += NT) X[(e / CH) * LDS + e % CH] = T(0);
   __syncthreads();
-  // MINV = A^{-1} (lower triangular): thread j solves A x = e_j by substitution
+  if (tid < CH) Rd[tid] = T(1) / A[tid * LDS + tid];
+  __syncthreads();
+  // MINV = A^{-1} (lower triangular): thread j solves A x = e_j by forward
+  // substitution with four independent partial sums per row
   if (tid < CH) {
     const int j = tid;
-    X[j][j] = T(1) / A[j][j];
+    X[j * LDS + j] = Rd[j];
     for (int r = j + 1; r < CH; ++r) {
-      T acc = T(0);
-      for (int q = j; q < r; ++q) acc += A[r][q] * X[q][j];
-      X[r][j] = -acc / A[r][r];
+      const T* Ar = A + r * LDS;
+      T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
+      int q = j;
+      for (; q + 3 < r; q += 4) {
+        a0 += Ar[q] * X[q * LDS + j];
+        a1 += Ar[q + 1] * X[(q + 1) * LDS + j];
+        a2 += Ar[q + 2] * X[(q + 2) * LDS + j];
+        a3 += Ar[q + 3] * X[(q + 3) * LDS + j];
+      }
+      for (; q < r; ++q) a0 += Ar[q] * X[q * LDS + j];
+      X[r * LDS + j] = -((a0 + a1) + (a2 + a3)) * Rd[r];
     }
   }
   __syncthreads();
   // stored column-major (element (t, j) at j * 32 + t): the sweep's lane t
   // reads its row as 32 conflict-free shared-memory loads
   T* M = out + cbase[b] + (int64_t)c * (1 + ng) * CH * CH;
-  for (int e = tid; e < CH * CH; e += blockDim.x) {
-    const int j = e / CH, t = e % CH;
-    M[e] = X[t][j];
+  constexpr int PER = CH * CH / NT;    // outputs per thread and matrix (4)
+#pragma unroll
+  for (int i = 0; i < PER; ++i) {
+    const int e = tid + i * NT;
+    M[e] = X[(e % CH) * LDS + e / CH];
   }
+  // G_k = MINV B_k: thread computes row t = lane of columns j = warp, warp + 8, ...
+  // (conflict-free reads of X, broadcast reads of B_k, coalesced stores)
+  const int t = tid % CH, jq = tid / CH;
   for (int k = 1; k <= ng; ++k) {
-    __syncthreads();
-    for (int e = tid; e < CH * CH; e += blockDim.x) {
-      const int t = e / CH, j = e % CH;
-      const int dist = k * CH + t - j;    // position distance to column j of chunk c - k
-      Bc[t][j] = (c >= k && dist <= K) ? sweep_entry<MODE>(F, K, n, ld, p0 + t, p0 - k * CH + j) : T(0);
+    const T* Bk = Bs + (k - 1) * CH * LDS;
+    T acc[PER];
+#pragma unroll
+    for (int i = 0; i < PER; ++i) acc[i] = T(0);
+    for (int q = 0; q <= t; ++q) {
+      const T xq = X[t * LDS + q];
+#pragma unroll
+      for (int i = 0; i < PER; ++i) acc[i] += xq * Bk[q * LDS + jq + i * (NT / CH)];
     }
-    __syncthreads();
     T* G = M + (int64_t)k * CH * CH;
-    for (int e = tid; e < CH * CH; e += blockDim.x) {
-      const int j = e / CH, t = e % CH;
-      T acc = T(0);
-      for (int q = 0; q <= t; ++q) acc += X[t][q] * Bc[q][j];
-      G[e] = acc;
-    }
+#pragma unroll
+    for (int i = 0; i < PER; ++i) G[(jq + i * (NT / CH)) * CH + t] = acc[i];
   }
+}
+
+template <typename T, int MODE>
+void launch_mode(dim3 grid, size_t smem, const T* F, int K, Dev d, const int64_t* cbase, T* out, cudaStream_t s) {
+  if (smem > 48 * 1024) cudaFuncSetAttribute(k_chunk_mats<T, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_chunk_mats<T, MODE><<<grid, NT, smem, s>>>(F, K, d, cbase, out);
 }
 
 }  // namespace
@@ -111,12 +168,13 @@ template <typename T>
 cudaError_t launch_chunk_mats(const T* F, int K, int P, Dev d, const int64_t* cbase, int max_nch, int mode, T* out,
                               cudaStream_t s) {
   dim3 grid(max_nch, P);
+  const size_t smem = chunk_smem_bytes<T>(K);
   count_launches(1);
   switch (mode) {
-    case 0: k_chunk_mats<T, 0><<<grid, 128, 0, s>>>(F, K, d, cbase, out); break;
-    case 1: k_chunk_mats<T, 1><<<grid, 128, 0, s>>>(F, K, d, cbase, out); break;
-    case 2: k_chunk_mats<T, 2><<<grid, 128, 0, s>>>(F, K, d, cbase, out); break;
-    default: k_chunk_mats<T, 3><<<grid, 128, 0, s>>>(F, K, d, cbase, out); break;
+    case 0: launch_mode<T, 0>(grid, smem, F, K, d, cbase, out, s); break;
+    case 1: launch_mode<T, 1>(grid, smem, F, K, d, cbase, out, s); break;
+    case 2: launch_mode<T, 2>(grid, smem, F, K, d, cbase, out, s); break;
+    default: launch_mode<T, 3>(grid, smem, F, K, d, cbase, out, s); break;
   }
   return cudaGetLastError();
 }

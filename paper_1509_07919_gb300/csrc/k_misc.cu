@@ -3,7 +3,7 @@
 // BiCGStab(2) iteration (Sleijpen & Fokkema 1993, l = 2; Sec. 2.1.1).
 //
 // Reductions are deterministic: a fixed grid writes one partial per block,
-// and the last block to finish (atomic ticket) sums the partials in block
+// and the last block to finish (atomic ticket) sums the partials in a fixed
 // order and evaluates the iteration's scalar recurrences on the device, so
 // the host never round-trips for alpha, beta, omega, gamma.
 #include <cuda_runtime.h>
@@ -15,11 +15,14 @@ namespace sap {
 
 // ------------------------------------------------------------------ SpMV --
 namespace {
-constexpr int SPMV_T = 256;
+constexpr int SPMV_T = 128;
 
 // y_i = sum_c band[c N + j] x_j, j = i + K - c  (A x)
 // y_j = sum_c band[c N + j] x_i, i = j + c - K  (A^T x)
 // x is staged in shared memory for the CTA's rows plus a K-halo each side.
+// Each thread keeps 16 band loads in flight; the band is read once per
+// product with evict-first loads (__ldcs), so that the Krylov vectors stay
+// resident in L2 across the iteration.
 template <bool TRANS>
 __global__ void __launch_bounds__(SPMV_T)
 k_spmv(const double* __restrict__ band, int64_t N, int K, const double* __restrict__ x,
@@ -45,13 +48,25 @@ k_spmv(const double* __restrict__ band, int64_t N, int K, const double* __restri
     const int64_t stride = N - 1;
     const int xl = threadIdx.x + 2 * K;         // xs index of j = i + K - c is xl - c
     int c = clo;
-    for (; c + 3 <= chi; c += 4) {
-      a0 += bp[(int64_t)c * stride] * xs[xl - c];
-      a1 += bp[(int64_t)(c + 1) * stride] * xs[xl - c - 1];
-      a2 += bp[(int64_t)(c + 2) * stride] * xs[xl - c - 2];
-      a3 += bp[(int64_t)(c + 3) * stride] * xs[xl - c - 3];
+    for (; c + 15 <= chi; c += 16) {
+      double v[16];
+#pragma unroll
+      for (int u = 0; u < 16; ++u) v[u] = __ldcs(bp + (int64_t)(c + u) * stride);
+#pragma unroll
+      for (int u = 0; u < 16; u += 4) {
+        a0 += v[u] * xs[xl - c - u];
+        a1 += v[u + 1] * xs[xl - c - u - 1];
+        a2 += v[u + 2] * xs[xl - c - u - 2];
+        a3 += v[u + 3] * xs[xl - c - u - 3];
+      }
     }
-    for (; c <= chi; ++c) a0 += bp[(int64_t)c * stride] * xs[xl - c];
+    for (; c + 3 <= chi; c += 4) {
+      a0 += __ldcs(bp + (int64_t)c * stride) * xs[xl - c];
+      a1 += __ldcs(bp + (int64_t)(c + 1) * stride) * xs[xl - c - 1];
+      a2 += __ldcs(bp + (int64_t)(c + 2) * stride) * xs[xl - c - 2];
+      a3 += __ldcs(bp + (int64_t)(c + 3) * stride) * xs[xl - c - 3];
+    }
+    for (; c <= chi; ++c) a0 += __ldcs(bp + (int64_t)c * stride) * xs[xl - c];
   } else {
     // i' = i + c - K in range <=> c in [max(0, K-i), min(2K, N-1-i+K)]
     int clo = (int)max((int64_t)0, (int64_t)K - i);
@@ -59,13 +74,25 @@ k_spmv(const double* __restrict__ band, int64_t N, int K, const double* __restri
     const double* bp = band + i;
     const int xl = threadIdx.x;                 // xs index of i + c - K is xl + c
     int c = clo;
-    for (; c + 3 <= chi; c += 4) {
-      a0 += bp[(int64_t)c * N] * xs[xl + c];
-      a1 += bp[(int64_t)(c + 1) * N] * xs[xl + c + 1];
-      a2 += bp[(int64_t)(c + 2) * N] * xs[xl + c + 2];
-      a3 += bp[(int64_t)(c + 3) * N] * xs[xl + c + 3];
+    for (; c + 15 <= chi; c += 16) {
+      double v[16];
+#pragma unroll
+      for (int u = 0; u < 16; ++u) v[u] = __ldcs(bp + (int64_t)(c + u) * N);
+#pragma unroll
+      for (int u = 0; u < 16; u += 4) {
+        a0 += v[u] * xs[xl + c + u];
+        a1 += v[u + 1] * xs[xl + c + u + 1];
+        a2 += v[u + 2] * xs[xl + c + u + 2];
+        a3 += v[u + 3] * xs[xl + c + u + 3];
+      }
     }
-    for (; c <= chi; ++c) a0 += bp[(int64_t)c * N] * xs[xl + c];
+    for (; c + 3 <= chi; c += 4) {
+      a0 += __ldcs(bp + (int64_t)c * N) * xs[xl + c];
+      a1 += __ldcs(bp + (int64_t)(c + 1) * N) * xs[xl + c + 1];
+      a2 += __ldcs(bp + (int64_t)(c + 2) * N) * xs[xl + c + 2];
+      a3 += __ldcs(bp + (int64_t)(c + 3) * N) * xs[xl + c + 3];
+    }
+    for (; c <= chi; ++c) a0 += __ldcs(bp + (int64_t)c * N) * xs[xl + c];
   }
   y[i] = (a0 + a1) + (a2 + a3);
 }
@@ -111,8 +138,12 @@ cudaError_t launch_grad_band(const double* lam, const double* x, int64_t N, int 
 namespace {
 constexpr int RT = 256;
 
-// Block-reduce ND values; the last block sums all partials in block order
-// into red[0..ND) and returns true (its thread 0 then runs the epilogue).
+// Block-reduce ND values; the last block to finish sums all partials and
+// returns true (its thread 0 then holds the sums in red[0..ND) and runs the
+// epilogue).  Every sum is taken in one fixed order (partials strided over
+// the threads, a shuffle butterfly, warp sums in warp order), so results do
+// not depend on block scheduling; the loads of the final sum are spread over
+// the whole block rather than chained through one thread.
 template <int ND>
 __device__ __forceinline__ bool reduce_last(double (&v)[ND], KrylovDev& kd, double* red) {
   __shared__ double ws[RT / 32][ND];
@@ -138,12 +169,20 @@ __device__ __forceinline__ bool reduce_last(double (&v)[ND], KrylovDev& kd, doub
   }
   __syncthreads();
   if (!last) return false;
+  __threadfence();
+#pragma unroll
+  for (int k = 0; k < ND; ++k) {
+    double a = 0.0;
+    for (unsigned b = threadIdx.x; b < gridDim.x; b += RT) a += __ldcg(&kd.part[b * ND + k]);
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    if (lane == 0) ws[w][k] = a;
+  }
+  __syncthreads();
   if (threadIdx.x == 0) {
-    __threadfence();
 #pragma unroll
     for (int k = 0; k < ND; ++k) {
       double a = 0.0;
-      for (unsigned b = 0; b < gridDim.x; ++b) a += ((volatile double*)kd.part)[b * ND + k];
+      for (int q = 0; q < RT / 32; ++q) a += ws[q][k];
       red[k] = a;
     }
     *kd.ticket = 0u;

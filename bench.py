@@ -28,9 +28,10 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "time to rel.res 1e-10 & HBM GB/s: FP32-precond vs FP64 SaP, fwd+adjoint"
-# DRAM bytes (read + write) of one k_block_solve launch on the N=200000, K=50, P=50
-# workload, from the ncu capture summarised in profiles/k_block_solve_n200k_k50_fp32.md
-TRAFFIC_BLOCK_SOLVE = 155417344 + 3786496
+# DRAM bytes (read + write) of the sweep launches of one FP32 SaP-D preconditioner
+# apply on the N=200000, K=50, P=50 workload (automatic segment count), from the
+# ncu capture summarised in profiles/k_sweep_n200k_k50_fp32.md
+TRAFFIC_SWEEPS = 267929600
 WORKLOADS = {
     "n200k_k50": dict(N=200000, K=50, d=1.0, P=50, seed_cfg=2),
     "n10k_k10": dict(N=10000, K=10, d=1.2, P=8, seed_cfg=1),
@@ -263,8 +264,11 @@ def run_gpu(args):
     y = torch.empty_like(b)
     z = torch.empty_like(b)
     t_spmv = kernel_ms(lambda: S.sap_spmv(band, N, K, xt, y))
-    # the block-solve kernel alone: one SaP-D apply is exactly one launch of it
+    # the sweep kernel alone: one SaP-D apply is exactly its launches (one fused
+    # launch unsegmented; two passes per sweep kind with segments)
     hd = h if variant == S.SAP_D else make_handle(S.SAP_FP32, S.SAP_D)
+    segs = i1.segments
+    sweep_launches = 1 if segs == 1 else 4
     t_sweep = kernel_ms(lambda: S.sap_apply_preconditioner(hd, b, z))
     t_apply = kernel_ms(lambda: S.sap_apply_preconditioner(h, b, z))
     W = 2 * K + 1
@@ -281,16 +285,21 @@ def run_gpu(args):
         "apply_fp32": {"ms": t_apply, "bytes": apply_bytes, "GBs": apply_bytes / (t_apply * 1e6)},
     }
     ach = kernels["block_solve_fp32"]["GBs"]
-    roofline = {"bound": "hbm", "kernel": "k_block_solve (both triangular sweeps of every block, FP32)",
+    roofline = {"bound": "hbm",
+                "kernel": ("k_block_solve (both triangular sweeps of every block, FP32)" if segs == 1 else
+                           f"k_sweep (both triangular sweeps of every block in {segs} segments, two passes "
+                           f"each, FP32; {sweep_launches} launches per apply)"),
                 "achieved": ach, "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak,
                 "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else
                 "fallback 6.8 TB/s",
-                # dram__bytes_read.sum + dram__bytes_write.sum of one k_block_solve launch
-                # (profiles/k_block_solve_n200k_k50_fp32.md); above the algorithmic bytes
+                # dram__bytes_read.sum + dram__bytes_write.sum of the sweep launches of one
+                # apply (profiles/k_sweep_n200k_k50_fp32.md); above the algorithmic bytes
                 # because the sweeps stream the per-chunk inverse/coupling matrices
-                "traffic": TRAFFIC_BLOCK_SOLVE if (N, K, P) == (200000, 50, 50) else None,
+                "traffic": TRAFFIC_SWEEPS if (N, K, P) == (200000, 50, 50) else None,
                 "algorithmic_bytes_per_launch": sweep_bytes,
-                "note": "one CTA per block; the 32-row chunk recurrence is latency-bound (50 of 152 SMs busy)"}
+                "unit_of_launch": f"one preconditioner apply = {sweep_launches} sweep launch(es)",
+                "note": f"{segs} segment(s) per block, {segs * P} CTAs per pass; the 32-row chunk "
+                        "recurrence is latency-bound"}
 
     # ---- end to end through the public API with host buffers ----
     band_h = torch.from_numpy(band_np).pin_memory()
@@ -333,7 +342,8 @@ def run_gpu(args):
             a, c = inf[-1]
             compare[name] = {"ms": statistics.mean(tt), "iters_fwd": a.iters, "iters_adj": c.iters,
                              "relres_fwd": a.relres, "relres_adj": c.relres,
-                             "t_factor_ms": a.t_factor_ms, "t_fwd_ms": a.t_solve_ms, "t_adj_ms": c.t_solve_ms}
+                             "t_factor_ms": a.t_factor_ms, "t_fwd_ms": a.t_solve_ms, "t_adj_ms": c.t_solve_ms,
+                             "segments": a.segments}
             del hh
 
     cpu = None
@@ -355,7 +365,8 @@ def run_gpu(args):
             "gpu_launches": int(launches),
             "roofline": roofline,
             "cpu_baseline": cpu,
-            "detail": {"iters_fwd": i1.iters, "iters_adj": i2.iters, "matvecs_fwd": i1.n_matvec,
+            "detail": {"sweep_segments_per_block": i1.segments,
+                       "iters_fwd": i1.iters, "iters_adj": i2.iters, "matvecs_fwd": i1.n_matvec,
                        "matvecs_adj": i2.n_matvec, "restarts_fwd": i1.n_restarts,
                        "restarts_adj": i2.n_restarts, "relres_fwd": i1.relres,
                        "relres_adj": i2.relres, "err_x_vs_x_true": err_x, "n_boosted": i1.n_boosted,

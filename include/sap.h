@@ -69,6 +69,18 @@ typedef struct {
                              |p| < boost_eps * max|a_ij| becomes sign(p) times that
                              value; <= 0 selects the unit roundoff of `precision` */
     int64_t spin_limit;   /* reserved for device-side waits (0 = default) */
+    int32_t segments;     /* sweep segments per block (0 = automatic, 1 = none): the
+                             two banded triangular sweeps of every block are split
+                             into this many consecutive row ranges that run on
+                             separate CTAs, in two passes (zero history, then the
+                             true history carried over by the precomputed transfer
+                             matrices of the ranges); the same operator as one
+                             sequential sweep up to rounding.  The paper sweeps each
+                             block with one thread block; this is a GB300 addition
+                             to fill the SMs when P is small.  Values that leave a
+                             range shorter than ceil(K/32) chunks of 32 rows are
+                             lowered automatically. */
+    int32_t reserved0;    /* must be 0 */
 } sap_options_t;
 
 typedef struct {
@@ -82,6 +94,8 @@ typedef struct {
     float t_lu_ms;        /* factor phase T_LU: block LU (and the boost-threshold pass) */
     float t_ul_ms;        /* SaP-C: block UL (top tiles only) */
     float t_spk_ms;       /* SaP-C: B/C, spike tips, Rbar_i, its GEPP and inverse */
+    int32_t segments;     /* sweep segments per block in use (sap_options_t.segments) */
+    int32_t reserved0;
 } sap_info_t;
 
 /* Defaults as documented above. */

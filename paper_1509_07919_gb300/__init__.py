@@ -34,14 +34,15 @@ class SapError(RuntimeError):
 class sap_options_t(C.Structure):
     _fields_ = [("P", C.c_int32), ("variant", C.c_int32), ("precision", C.c_int32),
                 ("max_iters", C.c_int32), ("tol", C.c_double), ("boost_eps", C.c_double),
-                ("spin_limit", C.c_int64)]
+                ("spin_limit", C.c_int64), ("segments", C.c_int32), ("reserved0", C.c_int32)]
 
 
 class sap_info_t(C.Structure):
     _fields_ = [("iters", C.c_double), ("relres", C.c_double), ("n_boosted", C.c_int64),
                 ("n_matvec", C.c_int64), ("n_restarts", C.c_int64),
                 ("t_factor_ms", C.c_float), ("t_solve_ms", C.c_float), ("t_lu_ms", C.c_float),
-                ("t_ul_ms", C.c_float), ("t_spk_ms", C.c_float)]
+                ("t_ul_ms", C.c_float), ("t_spk_ms", C.c_float), ("segments", C.c_int32),
+                ("reserved0", C.c_int32)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}

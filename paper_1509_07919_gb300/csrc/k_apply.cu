@@ -3,8 +3,8 @@
 // SaP-C the truncated reduced systems (Eq. (2.5)) and the purification
 // solves that follow them.
 //
-// Sweep kernel: one CTA of three warps per block, both sweeps in one launch.
-// A sweep is a lower-triangular recurrence over positions p (rows in sweep
+// Sweep kernel: one CTA of three warps per block and segment, one sweep kind
+// per launch.  A sweep is a lower-triangular recurrence over positions p (rows in sweep
 // order), processed in chunks of 32 positions with the chunk matrices of
 // k_chunk.cu (MINV_c and the couplings G_{c,k}, k = 1..ng, ng = ceil(K/32)):
 //     z_c = w_c - G_{c,1} z_{c-1},
@@ -18,6 +18,9 @@
 //     mbarrier; the other warps see the data through the CTA barrier.
 // Positions run over [0, ld) (ld = n rounded up to 32); a backward sweep
 // maps row r to p = ld - 1 - r.  Positions without a row produce 0.
+// With S > 1 segments per block the chunks of a sweep are cut into S ranges
+// swept concurrently in two passes (see k_sweep and the transfer matrices of
+// k_chunk.cu), so that P blocks occupy S P CTAs.
 #include <cuda_runtime.h>
 #include <cstdint>
 #include "sap_internal.cuh"
@@ -102,6 +105,11 @@ __device__ __forceinline__ T coldot32(const T* __restrict__ Mcm, const T* __rest
   return (a0 + a1) + (a2 + a3);
 }
 
+// 16-byte vector of T.
+template <typename T> struct Vec16;
+template <> struct Vec16<float> { using type = float4; };
+template <> struct Vec16<double> { using type = double2; };
+
 struct SweepGeom {
   int K, n, ld, ng;
 };
@@ -113,6 +121,7 @@ struct SweepSh {
   T* zh;         // (ng+1) x 32: z of the most recent chunks (chunk mod (ng+1))
   T* W;          // [2][32]: w of the next chunk
   T* yb;         // 32: y - corrections of the chunk being prepared
+  T* hist;       // [2][32 ng]: history of the segment (second pass), ping-pong
   double* corr;  // 2K corrections (top K rows, bottom K rows)
   uint64_t* bar; // PF+1 mbarriers: chunk matrices of a ring slot landed
 };
@@ -120,59 +129,69 @@ struct SweepSh {
 template <int MODE>
 __device__ __forceinline__ int row_of(int p, int ld) { return fwd_mode<MODE>() ? p : ld - 1 - p; }
 
-// Warp 2: bulk-copy chunk cc's matrices into ring slot cc % (PF+1).  Chunks
-// past the end only arrive on the barrier, so that every slot completes one
-// phase per chunk index.
+// Warp 2: bulk-copy local chunk lc's matrices into ring slot lc % (PF+1).
+// Chunks past the segment (lc >= nc) only arrive on the barrier, so that every
+// slot completes one phase per chunk index.
 template <typename T, typename YT>
 __device__ __forceinline__ void prefetch_mats(const SweepSh<T, YT>& sh, const SweepGeom& g, const T* __restrict__ Mg,
-                                              int cc) {
+                                              int lc, int nc) {
   if ((threadIdx.x & 31) != 0) return;
-  const int slot = cc % (PF + 1);
+  const int slot = lc % (PF + 1);
   const int mat = (1 + g.ng) * CHK * CHK;
-  if (cc * CHK < g.ld) {
+  if (lc < nc) {
     const unsigned bytes = (unsigned)(mat * sizeof(T));
     mbar_expect_tx(&sh.bar[slot], bytes);
-    bulk_g2s(sh.M + slot * mat, Mg + (int64_t)cc * mat, bytes, &sh.bar[slot]);
+    bulk_g2s(sh.M + slot * mat, Mg + (int64_t)lc * mat, bytes, &sh.bar[slot]);
   } else {
     mbar_arrive(&sh.bar[slot]);
   }
 }
 
-// Warp 1: cp.async of chunk cc's right-hand side (one commit group per chunk).
+// Warp 1: cp.async of local chunk lc's right-hand side (one commit group per
+// chunk); p0: first position of the segment.
 template <typename T, typename YT, int MODE>
 __device__ __forceinline__ void prefetch_y(const SweepSh<T, YT>& sh, const SweepGeom& g, const YT* __restrict__ yin,
-                                           int cc) {
+                                           int lc, int nc, int p0) {
   const int lane = threadIdx.x & 31;
-  const int p0 = cc * CHK;
-  if (p0 < g.ld) {
-    const int r = row_of<MODE>(p0 + lane, g.ld);
-    YT* ydst = &sh.Y[(cc % (PF + 1)) * CHK + lane];
+  if (lc < nc) {
+    const int r = row_of<MODE>(p0 + lc * CHK + lane, g.ld);
+    YT* ydst = &sh.Y[(lc % (PF + 1)) * CHK + lane];
     if (r < g.n) cpa(ydst, &yin[r]);
     else *ydst = YT(0);
   }
   cpa_commit();
 }
 
-template <typename T, typename YT, int MODE>
+// One sweep over the nc chunks of a segment starting at chunk c0 of a block
+// (Mg: the block's chunk matrices).  Local chunk lc = c - c0; z history slot
+// of local chunk lc (lc >= -ng) is (lc + ng + 1) % (ng + 1), so the ng
+// chunks before the segment occupy slots 1..ng.  hist: z of those chunks
+// (32 ng values, oldest first), or nullptr for zero history.  out (if not
+// null) receives z of the segment's rows; tail (if not null) the z of its last
+// ng chunks, in the order of hist.
+template <typename T, typename YT, typename OT, int MODE>
 __device__ void sweep(const SweepSh<T, YT>& sh, const SweepGeom& g, const T* __restrict__ Mg,
-                      const YT* __restrict__ yin, bool has_top, bool has_bot, double* __restrict__ out_d,
-                      T* __restrict__ out_t, unsigned& ph, bool& failed, int* __restrict__ err) {
+                      const YT* __restrict__ yin, bool has_top, bool has_bot, OT* __restrict__ out, int c0, int nc,
+                      const T* hist, T* __restrict__ tail, unsigned& ph, bool& failed, int* __restrict__ err) {
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
-  const int nch = g.ld / CHK;
   const int K = g.K, ng = g.ng;
   const int mat = (1 + ng) * CHK * CHK;
-  auto wait_chunk = [&](int cc) {     // warp 2: lane 0 polls
-    const int sl = cc % (PF + 1);
+  const int p0 = c0 * CHK;
+  const T* Ms = Mg + (int64_t)c0 * mat;
+  // ph: per-slot parity of the next barrier phase (lane 0 of warp 2), carried
+  // from sweep to sweep of one CTA
+  auto wait_chunk = [&](int lc) {     // warp 2: lane 0 polls
+    const int sl = lc % (PF + 1);
     if (lane == 0) mbar_wait(&sh.bar[sl], (ph >> sl) & 1u, err, failed);
     ph ^= 1u << sl;
     __syncwarp();
   };
-  // w_cb = MINV_cb (y_cb - corrections) - sum_{k>=2} G_{cb,k} z_{cb-k}
-  auto prepare = [&](int cb) {
-    const int slot = cb % (PF + 1);
-    const int p = cb * CHK + lane;
-    const int r = row_of<MODE>(p, g.ld);
+  auto zslot = [&](int lc) { return (lc + ng + 1) % (ng + 1); };
+  // w_lb = MINV (y - corrections) - sum_{k>=2} G_k z_{lb-k}
+  auto prepare = [&](int lb) {
+    const int slot = lb % (PF + 1);
+    const int r = row_of<MODE>(p0 + lb * CHK + lane, g.ld);
     T yv = T(0);
     if (r < g.n) {
       yv = (T)sh.Y[slot * CHK + lane];
@@ -183,32 +202,37 @@ __device__ void sweep(const SweepSh<T, YT>& sh, const SweepGeom& g, const T* __r
     __syncwarp();
     const T* Mc = sh.M + slot * mat;
     T w = coldot32(Mc, sh.yb, lane);
-    for (int k = 2; k <= ng; ++k)
-      if (cb - k >= 0) w -= coldot32(Mc + k * CHK * CHK, sh.zh + ((cb - k) % (ng + 1)) * CHK, lane);
-    sh.W[(cb & 1) * CHK + lane] = w;
+    for (int k = 2; k <= ng; ++k) w -= coldot32(Mc + k * CHK * CHK, sh.zh + zslot(lb - k) * CHK, lane);
+    sh.W[(lb & 1) * CHK + lane] = w;
     __syncwarp();
   };
-  // prologue: matrices of chunks 0..PF-1 in flight, chunks 0 and 1 landed, w_0 formed
+  // z history: zero, or the segment's incoming history in slots 1..ng
+  for (int t = threadIdx.x; t < (ng + 1) * CHK; t += blockDim.x) sh.zh[t] = T(0);
+  __syncthreads();
+  if (hist)
+    for (int t = threadIdx.x; t < ng * CHK; t += blockDim.x) sh.zh[(1 + t / CHK) * CHK + t % CHK] = hist[t];
+  // prologue: matrices of local chunks 0..PF-1 in flight, 0 and 1 landed, w_0 formed
   if (warp == 2) {
-    for (int cc = 0; cc < PF; ++cc) prefetch_mats(sh, g, Mg, cc);
+    for (int lc = 0; lc < PF; ++lc) prefetch_mats(sh, g, Ms, lc, nc);
     wait_chunk(0);
     wait_chunk(1);
   } else if (warp == 1) {
-    for (int cc = 0; cc < PF; ++cc) prefetch_y<T, YT, MODE>(sh, g, yin, cc);
+    for (int lc = 0; lc < PF; ++lc) prefetch_y<T, YT, MODE>(sh, g, yin, lc, nc, p0);
     cpa_wait<PF - 1>();
     __syncwarp();
   }
   __syncthreads();
   if (warp == 1) prepare(0);
   __syncthreads();
-  T zprev = T(0);    // warp 0: z of the previous chunk, lane t holds position t
-  for (int c = 0; c < nch; ++c) {
+  // warp 0: z of the previous chunk, lane t holds position t
+  T zprev = hist ? hist[(ng - 1) * CHK + lane] : T(0);
+  for (int lc = 0; lc < nc; ++lc) {
     if (warp == 0) {
-      const T* G1 = sh.M + (c % (PF + 1)) * mat + CHK * CHK;
+      const T* G1 = sh.M + (lc % (PF + 1)) * mat + CHK * CHK;
       T m[CHK];
 #pragma unroll
       for (int j = 0; j < CHK; ++j) m[j] = G1[j * CHK + lane];
-      T a0 = sh.W[(c & 1) * CHK + lane], a1 = T(0), a2 = T(0), a3 = T(0);
+      T a0 = sh.W[(lc & 1) * CHK + lane], a1 = T(0), a2 = T(0), a3 = T(0);
 #pragma unroll
       for (int j = 0; j < CHK; j += 4) {
         a0 -= m[j] * __shfl_sync(0xffffffffu, zprev, j);
@@ -218,29 +242,28 @@ __device__ void sweep(const SweepSh<T, YT>& sh, const SweepGeom& g, const T* __r
       }
       const T z = (a0 + a1) + (a2 + a3);
       zprev = z;
-      sh.zh[(c % (ng + 1)) * CHK + lane] = z;
-      const int r = row_of<MODE>(c * CHK + lane, g.ld);
-      if (r < g.n) {
-        if (out_d) out_d[r] = (double)z;
-        else out_t[r] = z;
-      }
+      sh.zh[zslot(lc) * CHK + lane] = z;
+      const int r = row_of<MODE>(p0 + lc * CHK + lane, g.ld);
+      if (out && r < g.n) out[r] = (OT)z;
     } else if (warp == 1) {
-      prefetch_y<T, YT, MODE>(sh, g, yin, c + PF);
-      if (c + 1 < nch) {
-        cpa_wait<PF - 1>();     // y of chunk c + 1 landed
+      prefetch_y<T, YT, MODE>(sh, g, yin, lc + PF, nc, p0);
+      if (lc + 1 < nc) {
+        cpa_wait<PF - 1>();     // y of chunk lc + 1 landed
         __syncwarp();
-        prepare(c + 1);
+        prepare(lc + 1);
       }
     } else {
-      prefetch_mats(sh, g, Mg, c + PF);
-      wait_chunk(c + 2);        // read by warp 1 in iteration c + 1, by warp 0 in c + 2
+      prefetch_mats(sh, g, Ms, lc + PF, nc);
+      wait_chunk(lc + 2);       // read by warp 1 in iteration lc + 1, by warp 0 in lc + 2
     }
     __syncthreads();
   }
   // warp 2: consume the phases of the remaining prefetched chunks
   if (warp == 2)
-    for (int cc = nch + 2; cc < nch + PF; ++cc) wait_chunk(cc);
+    for (int lc = nc + 2; lc < nc + PF; ++lc) wait_chunk(lc);
   if (warp == 1) cpa_wait<0>();
+  if (tail && warp == 0)
+    for (int i = 0; i < ng; ++i) tail[i * CHK + lane] = sh.zh[zslot(nc - ng + i) * CHK + lane];
   __syncthreads();
 }
 
@@ -253,6 +276,7 @@ size_t sweep_smem(int K) {
   b += (size_t)(PF + 1) * CHK * sizeof(double);                      // Y ring (largest input type)
   b += (size_t)(ng + 1) * CHK * sizeof(T);                           // z history
   b += (size_t)3 * CHK * sizeof(T);                                  // W, yb
+  b += (size_t)2 * ng * CHK * sizeof(T);                             // segment history (ping-pong)
   b = (b + 15) & ~(size_t)15;
   b += (size_t)2 * K * sizeof(double);                               // corrections
   b = (b + 15) & ~(size_t)15;
@@ -274,6 +298,8 @@ __device__ __forceinline__ SweepSh<T, YT> carve(unsigned char* base, const Sweep
   off += 2 * CHK * sizeof(T);
   sh.yb = reinterpret_cast<T*>(base + off);
   off += CHK * sizeof(T);
+  sh.hist = reinterpret_cast<T*>(base + off);
+  off += (size_t)2 * g.ng * CHK * sizeof(T);
   off = (off + 15) & ~(size_t)15;
   sh.corr = reinterpret_cast<double*>(base + off);
   off += (size_t)2 * g.K * sizeof(double);
@@ -282,10 +308,119 @@ __device__ __forceinline__ SweepSh<T, YT> carve(unsigned char* base, const Sweep
   return sh;
 }
 
+// One sweep kind over every block, split into S segments of ceil(nch / S)
+// chunks (Dev partition; grid (segments of this pass, P)):
+//   pass 1: segments 0..S-2 with zero history; segment 0 (exact) writes its
+//           rows, each writes its zero-history tail;
+//   pass 2: segment s >= 1 forms its true history by the transfer recurrence
+//           tail_j = zhat_tail_j + T_j tail_{j-1} (j < s, tail_0 exact) and
+//           sweeps again from it, writing its rows.
+// ctop/cbot: SaP-C corrections of the right-hand side (forward sweeps of the
+// second block solve only).
+template <typename T, typename YT, typename OT, int MODE>
+__global__ void __launch_bounds__(NWS * 32)
+k_sweep(const T* __restrict__ Mall, const T* __restrict__ Tall, const int64_t* __restrict__ cbase, int K, Dev d,
+        const YT* __restrict__ yin, OT* __restrict__ out, T* __restrict__ tails,
+        const double* __restrict__ ctop_all, const double* __restrict__ cbot_all, int P, int S, int pass,
+        int* __restrict__ err) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int b = blockIdx.y;
+  const int seg = pass == 1 ? (int)blockIdx.x : (int)blockIdx.x + 1;
+  const int64_t s = d.off[b];
+  SweepGeom g;
+  g.K = K;
+  g.n = (int)(d.off[b + 1] - s);
+  g.ld = (int)d.ld[b];
+  g.ng = n_couplings(K);
+  const int nch = g.ld / CHK;
+  const int cps = seg_chunks(nch, S);
+  const int c0 = seg * cps, c1 = min(nch, c0 + cps);
+  if (c0 >= c1) return;
+  const int NGW = g.ng * CHK;
+  const bool has_top = ctop_all && b > 0;
+  const bool has_bot = cbot_all && b + 1 < P;
+  bool failed = false;   // a barrier wait of this thread timed out
+  SweepSh<T, YT> sh = carve<T, YT>(smem_raw, g);
+  if (threadIdx.x == 0) {
+    for (int q = 0; q <= PF; ++q) mbar_init(&sh.bar[q], 1);
+    mbar_fence_init();
+  }
+  for (int t = threadIdx.x; t < K; t += blockDim.x) {
+    sh.corr[t] = has_top ? ctop_all[(int64_t)(b - 1) * K + t] : 0.0;
+    sh.corr[K + t] = has_bot ? cbot_all[(int64_t)b * K + t] : 0.0;
+  }
+  const T* hist = nullptr;
+  T* tb = tails ? tails + (int64_t)b * S * NGW : nullptr;
+  if (pass == 2) {
+    // true history of this segment: tail_j = zhat_tail_j + T_j tail_{j-1}.
+    // T_j is staged in the (not yet used) chunk-matrix ring with all loads in
+    // flight at once, the next one prefetched into L2; thread i forms row i.
+    using V = typename Vec16<T>::type;
+    constexpr int E = 16 / (int)sizeof(T);
+    T* Ts = sh.M;            // NGW x NGW <= (PF + 1) (1 + ng) 32 x 32 for ng <= 5
+    T* h0 = sh.hist;
+    T* h1 = sh.hist + NGW;
+    for (int t = threadIdx.x; t < NGW; t += blockDim.x) h0[t] = tb[t];
+    for (int j = 1; j < seg; ++j) {
+      const T* Tj = Tall + ((int64_t)b * S + j) * NGW * NGW;
+      __syncthreads();       // h0 complete, previous Ts readers done
+      {
+        const V* src = reinterpret_cast<const V*>(Tj);
+        V* dst = reinterpret_cast<V*>(Ts);
+        const int nv = NGW * NGW / E;
+        constexpr int U = 8;
+        for (int v0 = threadIdx.x; v0 < nv; v0 += U * blockDim.x) {
+          V tmpv[U];
+#pragma unroll
+          for (int u = 0; u < U; ++u)
+            if (v0 + u * (int)blockDim.x < nv) tmpv[u] = src[v0 + u * blockDim.x];
+#pragma unroll
+          for (int u = 0; u < U; ++u)
+            if (v0 + u * (int)blockDim.x < nv) dst[v0 + u * blockDim.x] = tmpv[u];
+        }
+      }
+      if (j + 1 < seg) {
+        const char* nx = reinterpret_cast<const char*>(Tj + (int64_t)NGW * NGW);
+        for (int o = threadIdx.x * 128; o < NGW * NGW * (int)sizeof(T); o += blockDim.x * 128)
+          asm volatile("prefetch.global.L2 [%0];\n" ::"l"(nx + o));
+      }
+      __syncthreads();
+      for (int i = threadIdx.x; i < NGW; i += blockDim.x) {
+        // row i is read starting at column i (rotated), so that the threads'
+        // rows (stride NGW, a multiple of 32) fall in distinct banks
+        const T* row = Ts + i * NGW;
+        T acc[4] = {T(0), T(0), T(0), T(0)};
+        int qq = i;
+#pragma unroll 4
+        for (int q = 0; q < NGW; ++q) {
+          acc[q & 3] += row[qq] * h0[qq];
+          qq = (qq + 1 == NGW) ? 0 : qq + 1;
+        }
+        h1[i] = tb[(int64_t)j * NGW + i] + ((acc[0] + acc[1]) + (acc[2] + acc[3]));
+      }
+      T* tt = h0; h0 = h1; h1 = tt;
+    }
+    // the ring is refilled by bulk (async-proxy) copies next: order the
+    // generic-proxy accesses to it before them
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    hist = h0;
+  }
+  __syncthreads();
+  const bool write_out = pass == 2 || seg == 0;
+  T* tail = (tb && pass == 1 && seg + 1 < S) ? tb + (int64_t)seg * NGW : nullptr;
+  unsigned ph = 0;
+  sweep<T, YT, OT, MODE>(sh, g, Mall + cbase[b], yin + s, has_top, has_bot, write_out ? out + s : nullptr, c0,
+                         c1 - c0, hist, tail, ph, failed, err);
+}
+
+// Unsegmented block solve (S = 1): one CTA per block runs the forward and
+// then the backward sweep of its block.  Measured faster than two launches of
+// k_sweep with S = 1 (125 us against about 150 us per apply on the
+// N = 200000, K = 50, P = 50 FP32 system).
 template <typename T, bool TRANS>
 __global__ void __launch_bounds__(NWS * 32)
-k_block_solve(const T* __restrict__ M1all, const T* __restrict__ M2all, const int64_t* __restrict__ cbase,
-              int K, Dev d, const double* __restrict__ r_in, double* __restrict__ z_out, T* __restrict__ tmp,
+k_block_solve(const T* __restrict__ M1all, const T* __restrict__ M2all, const int64_t* __restrict__ cbase, int K,
+              Dev d, const double* __restrict__ r_in, double* __restrict__ z_out, T* __restrict__ tmp,
               const double* __restrict__ ctop_all, const double* __restrict__ cbot_all, int P,
               int* __restrict__ err) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -296,13 +431,11 @@ k_block_solve(const T* __restrict__ M1all, const T* __restrict__ M2all, const in
   g.n = (int)(d.off[b + 1] - s);
   g.ld = (int)d.ld[b];
   g.ng = n_couplings(K);
-  const int64_t cb0 = cbase[b];
-  const T* M1 = M1all + cb0;
-  const T* M2 = M2all + cb0;
+  const int nch = g.ld / CHK;
   const bool has_top = ctop_all && b > 0;
   const bool has_bot = cbot_all && b + 1 < P;
-  unsigned ph = 0;       // per-slot parity of the next barrier phase (lane 0 of each warp)
-  bool failed = false;   // a barrier wait of this thread timed out
+  unsigned ph = 0;
+  bool failed = false;
   {
     SweepSh<T, double> sh = carve<T, double>(smem_raw, g);
     if (threadIdx.x == 0) {
@@ -313,17 +446,21 @@ k_block_solve(const T* __restrict__ M1all, const T* __restrict__ M2all, const in
       sh.corr[t] = has_top ? ctop_all[(int64_t)(b - 1) * K + t] : 0.0;
       sh.corr[K + t] = has_bot ? cbot_all[(int64_t)b * K + t] : 0.0;
     }
-    for (int t = threadIdx.x; t < (g.ng + 1) * CHK; t += blockDim.x) sh.zh[t] = T(0);
-    __syncthreads();
-    if (!TRANS) sweep<T, double, LF>(sh, g, M1, r_in + s, has_top, has_bot, nullptr, tmp + s, ph, failed, err);
-    else sweep<T, double, UTF>(sh, g, M1, r_in + s, has_top, has_bot, nullptr, tmp + s, ph, failed, err);
+    if (!TRANS)
+      sweep<T, double, T, LF>(sh, g, M1all + cbase[b], r_in + s, has_top, has_bot, tmp + s, 0, nch, nullptr,
+                              nullptr, ph, failed, err);
+    else
+      sweep<T, double, T, UTF>(sh, g, M1all + cbase[b], r_in + s, has_top, has_bot, tmp + s, 0, nch, nullptr,
+                               nullptr, ph, failed, err);
   }
   {
     SweepSh<T, T> sh = carve<T, T>(smem_raw, g);
-    for (int t = threadIdx.x; t < (g.ng + 1) * CHK; t += blockDim.x) sh.zh[t] = T(0);
-    __syncthreads();
-    if (!TRANS) sweep<T, T, UB>(sh, g, M2, tmp + s, false, false, z_out + s, nullptr, ph, failed, err);
-    else sweep<T, T, LTB>(sh, g, M2, tmp + s, false, false, z_out + s, nullptr, ph, failed, err);
+    if (!TRANS)
+      sweep<T, T, double, UB>(sh, g, M2all + cbase[b], tmp + s, false, false, z_out + s, 0, nch, nullptr, nullptr,
+                              ph, failed, err);
+    else
+      sweep<T, T, double, LTB>(sh, g, M2all + cbase[b], tmp + s, false, false, z_out + s, 0, nch, nullptr,
+                               nullptr, ph, failed, err);
   }
 }
 
@@ -394,18 +531,49 @@ __global__ void k_reduced(const double* __restrict__ band, int64_t N, int K, Dev
   }
 }
 
+template <typename T, typename YT, typename OT, int MODE>
+cudaError_t launch_sweep(const T* M, const T* Tm, const Factors<T>& f, int K, int P, Dev d, const YT* yin, OT* out,
+                         const double* ctop, const double* cbot, cudaStream_t s) {
+  const size_t smem = sweep_smem<T>(K);
+  auto kern = k_sweep<T, YT, OT, MODE>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const int S = f.S;
+  count_launches(1);
+  kern<<<dim3(S > 1 ? S - 1 : 1, P), NWS * 32, smem, s>>>(M, Tm, f.cbase, K, d, yin, out, f.tails, ctop, cbot, P, S,
+                                                          1, f.err);
+  if (S > 1) {
+    count_launches(1);
+    kern<<<dim3(S - 1, P), NWS * 32, smem, s>>>(M, Tm, f.cbase, K, d, yin, out, f.tails, ctop, cbot, P, S, 2,
+                                                 f.err);
+  }
+  return cudaGetLastError();
+}
+
+// Block-diagonal solve D g = r: forward then backward sweep of every block
+// (L then U; for the transposed operator U^T then L^T).
 template <typename T, bool TRANS>
 cudaError_t launch_block_solve(const Factors<T>& f, int K, int P, Dev d, const double* r, double* z, T* tmp,
                                const double* ctop, const double* cbot, cudaStream_t s) {
-  size_t smem = sweep_smem<T>(K);
-  auto kern = k_block_solve<T, TRANS>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e;
+  if (f.S == 1) {
+    const size_t smem = sweep_smem<T>(K);
+    auto kern = k_block_solve<T, TRANS>;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    count_launches(1);
+    kern<<<P, NWS * 32, smem, s>>>(TRANS ? f.Mutf : f.Mlf, TRANS ? f.Mltb : f.Mub, f.cbase, K, d, r, z, tmp, ctop,
+                                   cbot, P, f.err);
+    return cudaGetLastError();
+  }
+  if (!TRANS) {
+    e = launch_sweep<T, double, T, LF>(f.Mlf, f.Tlf, f, K, P, d, r, tmp, ctop, cbot, s);
+    if (e != cudaSuccess) return e;
+    return launch_sweep<T, T, double, UB>(f.Mub, f.Tub, f, K, P, d, tmp, z, nullptr, nullptr, s);
+  }
+  e = launch_sweep<T, double, T, UTF>(f.Mutf, f.Tutf, f, K, P, d, r, tmp, ctop, cbot, s);
   if (e != cudaSuccess) return e;
-  const T* m1 = TRANS ? f.Mutf : f.Mlf;
-  const T* m2 = TRANS ? f.Mltb : f.Mub;
-  count_launches(1);
-  kern<<<P, NWS * 32, smem, s>>>(m1, m2, f.cbase, K, d, r, z, tmp, ctop, cbot, P, f.err);
-  return cudaGetLastError();
+  return launch_sweep<T, T, double, LTB>(f.Mltb, f.Tltb, f, K, P, d, tmp, z, nullptr, nullptr, s);
 }
 
 }  // namespace

@@ -1,6 +1,7 @@
 // C ABI of libsap (include/sap.h): handle management, the factor pipeline
 // and the outer BiCGStab(2) loop (Sec. 2.1.1) around the device kernels.
 #include <cuda_runtime.h>
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -106,6 +107,12 @@ struct Solver : SolverBase {
   bool transposed_ready = false;
   explicit Solver(sap_handle* hh) : h(hh) {}
 
+  // elements of one sweep kind's transfer matrices: P x S x (32 ng)^2
+  size_t trans_elems() const {
+    const size_t ngw = (size_t)32 * chunk_couplings(h->L.K);
+    return (size_t)h->L.P * h->L.S * ngw * ngw;
+  }
+
   sap_status_t alloc() override {
     const Layout& L = h->L;
     const int K = L.K, P = L.P;
@@ -121,6 +128,12 @@ struct Solver : SolverBase {
     TRY(h->mem.alloc(&f.Mlf, (size_t)L.c_elems));
     TRY(h->mem.alloc(&f.Mub, (size_t)L.c_elems));
     f.cbase = h->dcbase;
+    f.S = L.S;
+    if (L.S > 1) {
+      TRY(h->mem.alloc(&f.Tlf, trans_elems()));
+      TRY(h->mem.alloc(&f.Tub, trans_elems()));
+      TRY(h->mem.alloc(&f.tails, (size_t)P * L.S * 32 * chunk_couplings(K)));
+    }
     if (h->opt.variant == SAP_C && P > 1) {
       TRY(h->mem.alloc(&f.ULt, (size_t)(nI * KK)));
       TRY(h->mem.alloc(&f.V, (size_t)(nI * KK)));
@@ -146,6 +159,8 @@ struct Solver : SolverBase {
     CK(launch_factor_lu<T>(bandT, L.N, K, P, h->d, h->absmax, eps, f.F, h->n_boosted, s));
     CK(launch_chunk_mats<T>(f.F, K, P, h->d, f.cbase, L.max_nch, 0, f.Mlf, s));
     CK(launch_chunk_mats<T>(f.F, K, P, h->d, f.cbase, L.max_nch, 1, f.Mub, s));
+    CK(launch_seg_trans<T>(f.Mlf, f.cbase, K, P, L.S, h->d, f.Tlf, s));
+    CK(launch_seg_trans<T>(f.Mub, f.cbase, K, P, L.S, h->d, f.Tub, s));
     transposed_ready = false;
     CK(cudaEventRecord(h->evp[1], s));
     if (h->opt.variant == SAP_C && P > 1) {
@@ -194,9 +209,15 @@ struct Solver : SolverBase {
     if (!f.Mutf) {
       TRY(h->mem.alloc(&f.Mutf, (size_t)L.c_elems));
       TRY(h->mem.alloc(&f.Mltb, (size_t)L.c_elems));
+      if (L.S > 1) {
+        TRY(h->mem.alloc(&f.Tutf, trans_elems()));
+        TRY(h->mem.alloc(&f.Tltb, trans_elems()));
+      }
     }
     CK(launch_chunk_mats<T>(f.F, L.K, L.P, h->d, f.cbase, L.max_nch, 2, f.Mutf, s));
     CK(launch_chunk_mats<T>(f.F, L.K, L.P, h->d, f.cbase, L.max_nch, 3, f.Mltb, s));
+    CK(launch_seg_trans<T>(f.Mutf, f.cbase, L.K, L.P, L.S, h->d, f.Tutf, s));
+    CK(launch_seg_trans<T>(f.Mltb, f.cbase, L.K, L.P, L.S, h->d, f.Tltb, s));
     transposed_ready = true;
     return SAP_OK;
   }
@@ -281,12 +302,16 @@ struct Solver : SolverBase {
   }
 };
 
+constexpr int kSMs = 152;               // SMs of a GB300
+constexpr int kMaxAutoSegments = 64;
+
 sap_status_t check_options(const sap_options_t* o, int64_t N, int K) {
   if (!o) return SAP_ERR_INVALID_ARG;
   if (N < 2 || K < 1 || K >= N) return SAP_ERR_INVALID_ARG;
   if (o->P < 1 || o->P > N) return SAP_ERR_INVALID_ARG;
   if (o->variant != SAP_D && o->variant != SAP_C) return SAP_ERR_INVALID_ARG;
   if (o->precision != SAP_FP64 && o->precision != SAP_FP32) return SAP_ERR_INVALID_ARG;
+  if (o->segments < 0 || o->reserved0 != 0) return SAP_ERR_INVALID_ARG;
   return SAP_OK;
 }
 
@@ -386,6 +411,7 @@ sap_status_t krylov(sap_handle* h, const double* b, double* x, bool tr, sap_info
   inf.t_lu_ms = h->t_lu_ms;
   inf.t_ul_ms = h->t_ul_ms;
   inf.t_spk_ms = h->t_spk_ms;
+  inf.segments = h->L.S;
   unsigned long long nb = 0;
   CK(cudaMemcpy(&nb, h->n_boosted, sizeof(nb), cudaMemcpyDeviceToHost));
   inf.n_boosted = (int64_t)nb;
@@ -422,6 +448,8 @@ void sap_default_options(sap_options_t* o) {
   o->tol = 1e-10;
   o->boost_eps = 0.0;
   o->spin_limit = 0;
+  o->segments = 0;
+  o->reserved0 = 0;
 }
 
 int64_t sap_kernel_launches(void) { return (int64_t)sap::g_launches.load(); }
@@ -479,6 +507,27 @@ sap_status_t sap_factor(const double* band_dev, int64_t N, int32_t K, const sap_
     if (nch > L.max_nch) L.max_nch = nch;
   }
   L.c_elems = cacc;
+  {
+    // sweep segments.  Automatic count (measured on GB300): FP32 factors with
+    // ng <= 2 couplings per chunk: up to two CTAs per SM over all blocks,
+    // segments of at least 16 chunks, used only if that gives at least 4
+    // segments per block.  For ng >= 3 or FP64 factors the transfer matrices
+    // cost more to form (FP64 arithmetic is slow on this part): one CTA per
+    // SM, segments of at least 32 chunks, at least 6 per block.  Never more
+    // than kMaxAutoSegments.  Any count is lowered to keep max(ng, 2) chunks
+    // of 32 rows in every full segment.
+    int min_nch = L.max_nch;
+    for (int i = 0; i < L.P; ++i) min_nch = std::min(min_nch, (int)(L.ld[i] / 32));
+    const int ngc = chunk_couplings(K);
+    int S = opt.segments;
+    if (S == 0) {
+      const bool narrow = ngc <= 2 && opt.precision == SAP_FP32;
+      S = std::min((narrow ? 2 : 1) * kSMs / L.P, min_nch / (narrow ? 16 : 32));
+      S = S < (narrow ? 4 : 6) ? 1 : std::min(S, kMaxAutoSegments);
+    }
+    S = std::min(S, std::max(1, min_nch / std::max(chunk_couplings(K), 2)));
+    L.S = std::max(1, S);
+  }
   int64_t *doff, *dfb, *dld, *dcb;
   TRY(h->mem.alloc(&doff, L.P + 1));
   TRY(h->mem.alloc(&dfb, L.P));

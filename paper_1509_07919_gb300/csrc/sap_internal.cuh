@@ -31,6 +31,7 @@ struct Layout {
   int64_t f_elems = 0;
   int64_t c_elems = 0;   // chunk-matrix elements per sweep kind (all blocks)
   int max_nch = 0;       // most 32-row chunks in one block
+  int S = 1;             // sweep segments per block
 };
 
 struct Dev {  // device copies of the partition, passed to kernels
@@ -55,6 +56,12 @@ struct Factors {
   // (built on the first transposed apply).  cbase[i]: offset of block i.
   T* Mlf = nullptr; T* Mub = nullptr; T* Mutf = nullptr; T* Mltb = nullptr;
   const int64_t* cbase = nullptr;
+  // segmented sweeps (S segments per block): per block and segment s >= 1 the
+  // (32 ng) x (32 ng) transfer matrix of each sweep kind (row-major, segment 0
+  // unused), and the per-apply tails of the zero-history pass
+  int S = 1;
+  T* Tlf = nullptr; T* Tub = nullptr; T* Tutf = nullptr; T* Tltb = nullptr;
+  T* tails = nullptr;    // P x S x 32 ng
   int* err = nullptr;    // set to nonzero by a device-side wait that timed out
 };
 
@@ -83,6 +90,12 @@ cudaError_t launch_spikes(const double* band, int64_t N, int K, int P, Dev d, co
 template <typename T>
 cudaError_t launch_chunk_mats(const T* F, int K, int P, Dev d, const int64_t* cbase, int max_nch, int mode, T* out,
                               cudaStream_t s);
+// Transfer matrices of segments 1..S-1 of every block from the chunk matrices
+// M of one sweep kind (out: P x S x (32 ng)^2).
+template <typename T>
+cudaError_t launch_seg_trans(const T* M, const int64_t* cbase, int K, int P, int S, Dev d, T* out, cudaStream_t s);
+// Chunks of 32 rows per segment of a block with nch chunks: ceil(nch / S).
+__host__ __device__ inline int seg_chunks(int nch, int S) { return (nch + S - 1) / S; }
 template <typename T>
 cudaError_t launch_apply(const double* band, int64_t N, int K, int P, Dev d, const Factors<T>& f,
                          int variant, bool transpose, const double* r, double* z, double* scratch,

@@ -124,6 +124,37 @@ def test_apply_parity(sap, variant, N, K, P):
         assert relerr(za, oa.apply(r)) <= tol, (prec, "adjoint", relerr(za, oa.apply(r)))
 
 
+@pytest.mark.parametrize("variant", [0, 1])
+@pytest.mark.parametrize("N,K,P", [(4003, 50, 2), (3001, 100, 3), (2500, 20, 1), (1111, 33, 3), (5000, 127, 2)])
+def test_segmented_sweeps_parity(sap, variant, N, K, P):
+    """Sweeps split into S concurrent segments (two passes with transfer
+    matrices) against the oracle's apply, forward and transposed, for explicit
+    segment counts; the count in use is reported and lowered to keep every
+    full segment at least max(ceil(K/32), 2) chunks of 32 rows."""
+    band, xt, b = make(N, K, 1.0, 800 + K)
+    r = G.adjoint_seed(N, 800 + K)
+    o = O.Sap(band, N, K, P, variant)
+    oa = O.Sap(O.transpose_band(band, N, K), N, K, P, variant)
+    zo, zao = o.apply(r), oa.apply(r)
+    nmin = N // P
+    ng = -(-K // 32)
+    for prec, tol in ((0, 1e-11), (1, 1e-4)):
+        if K > sap.sap_max_K(prec) or (variant == 1 and K > (98 if prec == 0 else 120)):
+            continue
+        for S in (1, 2, 3, 7, 1000):
+            h = sap.sap_factor(dev(band), N, K, P=P, variant=variant, precision=prec, segments=S)
+            z = host(sap.sap_apply_preconditioner(h, dev(r)))
+            assert relerr(z, zo) <= tol, (prec, S, relerr(z, zo))
+            za = host(sap.sap_apply_preconditioner(h, dev(r), transpose=True))
+            assert relerr(za, zao) <= tol, (prec, S, "adjoint", relerr(za, zao))
+            x, info, st = sap.sap_solve(h, dev(b))
+            assert st == sap.SAP_OK and info.relres <= 1e-10
+            assert 1 <= info.segments <= S
+            assert info.segments <= max(1, (-(-nmin // 32)) // max(ng, 2))
+            if S == 1:
+                assert info.segments == 1
+
+
 # --------------------------------------------------------------- solve --
 
 @pytest.mark.parametrize("variant", [0, 1])

@@ -31,7 +31,7 @@ METRIC = "time to rel.res 1e-10 & HBM GB/s: FP32-precond vs FP64 SaP, fwd+adjoin
 # DRAM bytes (read + write) of the sweep launches of one FP32 SaP-D preconditioner
 # apply on the N=200000, K=50, P=50 workload (automatic segment count), from the
 # ncu capture summarised in profiles/k_sweep_n200k_k50_fp32.md
-TRAFFIC_SWEEPS = 267929600
+TRAFFIC_SWEEPS = 250970112
 WORKLOADS = {
     "n200k_k50": dict(N=200000, K=50, d=1.0, P=50, seed_cfg=2),
     "n10k_k10": dict(N=10000, K=10, d=1.2, P=8, seed_cfg=1),
@@ -264,11 +264,12 @@ def run_gpu(args):
     y = torch.empty_like(b)
     z = torch.empty_like(b)
     t_spmv = kernel_ms(lambda: S.sap_spmv(band, N, K, xt, y))
-    # the sweep kernel alone: one SaP-D apply is exactly its launches (one fused
-    # launch unsegmented; two passes per sweep kind with segments)
+    # the sweep kernels alone: one SaP-D apply is exactly their launches (one
+    # fused launch unsegmented; with segments, per sweep kind the zero-history
+    # sweep, the history chain (more than two segments) and the correction)
     hd = h if variant == S.SAP_D else make_handle(S.SAP_FP32, S.SAP_D)
     segs = i1.segments
-    sweep_launches = 1 if segs == 1 else 4
+    sweep_launches = 1 if segs == 1 else (6 if segs > 2 else 4)
     t_sweep = kernel_ms(lambda: S.sap_apply_preconditioner(hd, b, z))
     t_apply = kernel_ms(lambda: S.sap_apply_preconditioner(h, b, z))
     W = 2 * K + 1
@@ -287,8 +288,8 @@ def run_gpu(args):
     ach = kernels["block_solve_fp32"]["GBs"]
     roofline = {"bound": "hbm",
                 "kernel": ("k_block_solve (both triangular sweeps of every block, FP32)" if segs == 1 else
-                           f"k_sweep (both triangular sweeps of every block in {segs} segments, two passes "
-                           f"each, FP32; {sweep_launches} launches per apply)"),
+                           f"k_sweep + k_seg_chain + k_seg_correct (both triangular sweeps of every block in "
+                           f"{segs} segments, FP32; {sweep_launches} launches per apply)"),
                 "achieved": ach, "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak,
                 "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else
                 "fallback 6.8 TB/s",

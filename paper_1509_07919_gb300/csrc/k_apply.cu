@@ -121,7 +121,6 @@ struct SweepSh {
   T* zh;         // (ng+1) x 32: z of the most recent chunks (chunk mod (ng+1))
   T* W;          // [2][32]: w of the next chunk
   T* yb;         // 32: y - corrections of the chunk being prepared
-  T* hist;       // [2][32 ng]: history of the segment (second pass), ping-pong
   double* corr;  // 2K corrections (top K rows, bottom K rows)
   uint64_t* bar; // PF+1 mbarriers: chunk matrices of a ring slot landed
 };
@@ -163,16 +162,15 @@ __device__ __forceinline__ void prefetch_y(const SweepSh<T, YT>& sh, const Sweep
 }
 
 // One sweep over the nc chunks of a segment starting at chunk c0 of a block
-// (Mg: the block's chunk matrices).  Local chunk lc = c - c0; z history slot
-// of local chunk lc (lc >= -ng) is (lc + ng + 1) % (ng + 1), so the ng
-// chunks before the segment occupy slots 1..ng.  hist: z of those chunks
-// (32 ng values, oldest first), or nullptr for zero history.  out (if not
-// null) receives z of the segment's rows; tail (if not null) the z of its last
-// ng chunks, in the order of hist.
+// (Mg: the block's chunk matrices), with zero history.  Local chunk
+// lc = c - c0; z history slot of local chunk lc (lc >= -ng) is
+// (lc + ng + 1) % (ng + 1), the ng chunks before the segment occupying slots
+// 1..ng (zero).  out receives z of the segment's rows; tail (if not null) the
+// z of its last ng chunks, oldest first.
 template <typename T, typename YT, typename OT, int MODE>
 __device__ void sweep(const SweepSh<T, YT>& sh, const SweepGeom& g, const T* __restrict__ Mg,
                       const YT* __restrict__ yin, bool has_top, bool has_bot, OT* __restrict__ out, int c0, int nc,
-                      const T* hist, T* __restrict__ tail, unsigned& ph, bool& failed, int* __restrict__ err) {
+                      T* __restrict__ tail, unsigned& ph, bool& failed, int* __restrict__ err) {
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
   const int K = g.K, ng = g.ng;
@@ -206,11 +204,9 @@ __device__ void sweep(const SweepSh<T, YT>& sh, const SweepGeom& g, const T* __r
     sh.W[(lb & 1) * CHK + lane] = w;
     __syncwarp();
   };
-  // z history: zero, or the segment's incoming history in slots 1..ng
+  // z history: zero
   for (int t = threadIdx.x; t < (ng + 1) * CHK; t += blockDim.x) sh.zh[t] = T(0);
   __syncthreads();
-  if (hist)
-    for (int t = threadIdx.x; t < ng * CHK; t += blockDim.x) sh.zh[(1 + t / CHK) * CHK + t % CHK] = hist[t];
   // prologue: matrices of local chunks 0..PF-1 in flight, 0 and 1 landed, w_0 formed
   if (warp == 2) {
     for (int lc = 0; lc < PF; ++lc) prefetch_mats(sh, g, Ms, lc, nc);
@@ -225,7 +221,7 @@ __device__ void sweep(const SweepSh<T, YT>& sh, const SweepGeom& g, const T* __r
   if (warp == 1) prepare(0);
   __syncthreads();
   // warp 0: z of the previous chunk, lane t holds position t
-  T zprev = hist ? hist[(ng - 1) * CHK + lane] : T(0);
+  T zprev = T(0);
   for (int lc = 0; lc < nc; ++lc) {
     if (warp == 0) {
       const T* G1 = sh.M + (lc % (PF + 1)) * mat + CHK * CHK;
@@ -276,7 +272,6 @@ size_t sweep_smem(int K) {
   b += (size_t)(PF + 1) * CHK * sizeof(double);                      // Y ring (largest input type)
   b += (size_t)(ng + 1) * CHK * sizeof(T);                           // z history
   b += (size_t)3 * CHK * sizeof(T);                                  // W, yb
-  b += (size_t)2 * ng * CHK * sizeof(T);                             // segment history (ping-pong)
   b = (b + 15) & ~(size_t)15;
   b += (size_t)2 * K * sizeof(double);                               // corrections
   b = (b + 15) & ~(size_t)15;
@@ -298,8 +293,6 @@ __device__ __forceinline__ SweepSh<T, YT> carve(unsigned char* base, const Sweep
   off += 2 * CHK * sizeof(T);
   sh.yb = reinterpret_cast<T*>(base + off);
   off += CHK * sizeof(T);
-  sh.hist = reinterpret_cast<T*>(base + off);
-  off += (size_t)2 * g.ng * CHK * sizeof(T);
   off = (off + 15) & ~(size_t)15;
   sh.corr = reinterpret_cast<double*>(base + off);
   off += (size_t)2 * g.K * sizeof(double);
@@ -309,23 +302,20 @@ __device__ __forceinline__ SweepSh<T, YT> carve(unsigned char* base, const Sweep
 }
 
 // One sweep kind over every block, split into S segments of ceil(nch / S)
-// chunks (Dev partition; grid (segments of this pass, P)):
-//   pass 1: segments 0..S-2 with zero history; segment 0 (exact) writes its
-//           rows, each writes its zero-history tail;
-//   pass 2: segment s >= 1 forms its true history by the transfer recurrence
-//           tail_j = zhat_tail_j + T_j tail_{j-1} (j < s, tail_0 exact) and
-//           sweeps again from it, writing its rows.
+// chunks (Dev partition; grid (S, P)), all with zero history: segment 0 is
+// exact; every segment writes its rows (zhat) and, but the last, the z of its
+// last ng chunks (its zero-history tail).  k_seg_chain turns the tails into
+// true histories, k_seg_correct then adds X h.
 // ctop/cbot: SaP-C corrections of the right-hand side (forward sweeps of the
 // second block solve only).
 template <typename T, typename YT, typename OT, int MODE>
 __global__ void __launch_bounds__(NWS * 32)
-k_sweep(const T* __restrict__ Mall, const T* __restrict__ Tall, const int64_t* __restrict__ cbase, int K, Dev d,
-        const YT* __restrict__ yin, OT* __restrict__ out, T* __restrict__ tails,
-        const double* __restrict__ ctop_all, const double* __restrict__ cbot_all, int P, int S, int pass,
-        int* __restrict__ err) {
+k_sweep(const T* __restrict__ Mall, const int64_t* __restrict__ cbase, int K, Dev d, const YT* __restrict__ yin,
+        OT* __restrict__ out, T* __restrict__ tails, const double* __restrict__ ctop_all,
+        const double* __restrict__ cbot_all, int P, int S, int* __restrict__ err) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int b = blockIdx.y;
-  const int seg = pass == 1 ? (int)blockIdx.x : (int)blockIdx.x + 1;
+  const int seg = (int)blockIdx.x;
   const int64_t s = d.off[b];
   SweepGeom g;
   g.K = K;
@@ -349,68 +339,132 @@ k_sweep(const T* __restrict__ Mall, const T* __restrict__ Tall, const int64_t* _
     sh.corr[t] = has_top ? ctop_all[(int64_t)(b - 1) * K + t] : 0.0;
     sh.corr[K + t] = has_bot ? cbot_all[(int64_t)b * K + t] : 0.0;
   }
-  const T* hist = nullptr;
-  T* tb = tails ? tails + (int64_t)b * S * NGW : nullptr;
-  if (pass == 2) {
-    // true history of this segment: tail_j = zhat_tail_j + T_j tail_{j-1}.
-    // T_j is staged in the (not yet used) chunk-matrix ring with all loads in
-    // flight at once, the next one prefetched into L2; thread i forms row i.
-    using V = typename Vec16<T>::type;
-    constexpr int E = 16 / (int)sizeof(T);
-    T* Ts = sh.M;            // NGW x NGW <= (PF + 1) (1 + ng) 32 x 32 for ng <= 5
-    T* h0 = sh.hist;
-    T* h1 = sh.hist + NGW;
-    for (int t = threadIdx.x; t < NGW; t += blockDim.x) h0[t] = tb[t];
-    for (int j = 1; j < seg; ++j) {
-      const T* Tj = Tall + ((int64_t)b * S + j) * NGW * NGW;
-      __syncthreads();       // h0 complete, previous Ts readers done
-      {
-        const V* src = reinterpret_cast<const V*>(Tj);
-        V* dst = reinterpret_cast<V*>(Ts);
-        const int nv = NGW * NGW / E;
-        constexpr int U = 8;
-        for (int v0 = threadIdx.x; v0 < nv; v0 += U * blockDim.x) {
-          V tmpv[U];
-#pragma unroll
-          for (int u = 0; u < U; ++u)
-            if (v0 + u * (int)blockDim.x < nv) tmpv[u] = src[v0 + u * blockDim.x];
-#pragma unroll
-          for (int u = 0; u < U; ++u)
-            if (v0 + u * (int)blockDim.x < nv) dst[v0 + u * blockDim.x] = tmpv[u];
+  T* tail = (tails && seg + 1 < S) ? tails + ((int64_t)b * S + seg) * NGW : nullptr;
+  unsigned ph = 0;
+  sweep<T, YT, OT, MODE>(sh, g, Mall + cbase[b], yin + s, has_top, has_bot, out + s, c0, c1 - c0, tail, ph,
+                         failed, err);
+}
+
+constexpr int kCorrThreads = 256;
+
+// Segment histories (grid P, kCorrThreads threads): the zero-history tails
+// written by k_sweep are turned in place into the true tails by the transfer
+// recurrence
+//     tail_j = zhat_tail_j + T_j tail_{j-1},  j = 1 .. S-2  (tail_0 exact),
+// so that segment s >= 1 finds its history in tail_{s-1}.  The T_j are
+// staged into shared memory by cp.async in rounds of up to RB matrices (one
+// memory latency per round); within a step TPR threads share a row (rotated
+// column order: conflict-free) and combine by shuffles.
+template <typename T>
+__host__ __device__ inline int chain_ring(int K, int S) {   // matrices per staging round
+  const int ngw = CHK * n_couplings(K);
+  const size_t one = (size_t)ngw * ngw * sizeof(T);
+  int rb = (int)((200 * 1024) / one);
+  rb = rb > 8 ? 8 : rb;
+  rb = rb > S - 2 ? S - 2 : rb;
+  return rb < 1 ? 1 : rb;
+}
+template <typename T>
+size_t chain_smem(int K, int S) {
+  const int ngw = CHK * n_couplings(K);
+  return (size_t)chain_ring<T>(K, S) * ngw * ngw * sizeof(T) + 2 * (size_t)ngw * sizeof(T);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kCorrThreads)
+k_seg_chain(const T* __restrict__ Tall, T* __restrict__ tails, int K, Dev d, int S) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int b = blockIdx.x;
+  const int ng = n_couplings(K);
+  const int NGW = ng * CHK;
+  const int nch = (int)(d.ld[b] / CHK);
+  const int cps = seg_chunks(nch, S);
+  const int nseg = (nch + cps - 1) / cps;          // nonempty segments of this block
+  const int RB = chain_ring<T>(K, S);
+  T* Ts = reinterpret_cast<T*>(smem_raw);         // RB x NGW x NGW
+  T* h0 = Ts + (size_t)RB * NGW * NGW;
+  T* h1 = h0 + NGW;
+  T* tb = tails + (int64_t)b * S * NGW;
+  // threads per row: the largest power of two with NGW TPR <= 256 (NGW <= 128)
+  const int TPR = NGW > 128 ? 1 : (NGW > 64 ? 2 : (NGW > 32 ? 4 : 8));
+  const int i = threadIdx.x / TPR, part = threadIdx.x % TPR;
+  for (int t = threadIdx.x; t < NGW; t += blockDim.x) h0[t] = tb[t];
+  const int jend = nseg - 1;                       // tails 1 .. nseg-2 are needed
+  for (int j0 = 1; j0 < jend; j0 += RB) {
+    const int nr = min(RB, jend - j0);
+    __syncthreads();          // previous round's readers of Ts are done
+    {
+      const char* src = reinterpret_cast<const char*>(Tall + ((int64_t)b * S + j0) * NGW * NGW);
+      const int nbytes = nr * NGW * NGW * (int)sizeof(T);
+      const unsigned dst = (unsigned)__cvta_generic_to_shared(Ts);
+      for (int o = threadIdx.x * 16; o < nbytes; o += blockDim.x * 16)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst + o), "l"(src + o) : "memory");
+      asm volatile("cp.async.commit_group;\n" ::: "memory");
+      asm volatile("cp.async.wait_all;\n" ::: "memory");
+    }
+    __syncthreads();
+    for (int u = 0; u < nr; ++u) {
+      const int j = j0 + u;
+      const T* Tj = Ts + (size_t)u * NGW * NGW;
+      T acc = T(0);
+      if (i < NGW) {
+        const T* row = Tj + i * NGW;
+        int q = (part + TPR * i) % NGW;
+        for (int m = 0; m < NGW / TPR; ++m) {
+          acc += row[q] * h0[q];
+          q += TPR;
+          if (q >= NGW) q -= NGW;
         }
       }
-      if (j + 1 < seg) {
-        const char* nx = reinterpret_cast<const char*>(Tj + (int64_t)NGW * NGW);
-        for (int o = threadIdx.x * 128; o < NGW * NGW * (int)sizeof(T); o += blockDim.x * 128)
-          asm volatile("prefetch.global.L2 [%0];\n" ::"l"(nx + o));
+      for (int o = TPR / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      if (i < NGW && part == 0) {
+        const T t = tb[(int64_t)j * NGW + i] + acc;
+        h1[i] = t;
+        tb[(int64_t)j * NGW + i] = t;
       }
       __syncthreads();
-      for (int i = threadIdx.x; i < NGW; i += blockDim.x) {
-        // row i is read starting at column i (rotated), so that the threads'
-        // rows (stride NGW, a multiple of 32) fall in distinct banks
-        const T* row = Ts + i * NGW;
-        T acc[4] = {T(0), T(0), T(0), T(0)};
-        int qq = i;
-#pragma unroll 4
-        for (int q = 0; q < NGW; ++q) {
-          acc[q & 3] += row[qq] * h0[qq];
-          qq = (qq + 1 == NGW) ? 0 : qq + 1;
-        }
-        h1[i] = tb[(int64_t)j * NGW + i] + ((acc[0] + acc[1]) + (acc[2] + acc[3]));
-      }
       T* tt = h0; h0 = h1; h1 = tt;
     }
-    // the ring is refilled by bulk (async-proxy) copies next: order the
-    // generic-proxy accesses to it before them
-    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-    hist = h0;
   }
+}
+
+// History correction z_p += sum_q X[q][p] h_q of segments s >= 1, h = the
+// true tail_{s-1}; grid (row tiles of kCorrThreads positions, S - 1, P), one
+// position per thread, X column-major (coalesced).
+template <typename T, typename OT, int MODE>
+__global__ void __launch_bounds__(kCorrThreads)
+k_seg_correct(const T* __restrict__ Xall, const T* __restrict__ tails, int K, Dev d, int S, int cpsmax,
+              OT* __restrict__ out) {
+  __shared__ T h[4 * CHK];
+  const int b = blockIdx.z;
+  const int seg = (int)blockIdx.y + 1;
+  const int ng = n_couplings(K);
+  const int NGW = ng * CHK;
+  const int ld = (int)d.ld[b];
+  const int64_t s = d.off[b];
+  const int n = (int)(d.off[b + 1] - s);
+  const int nch = ld / CHK;
+  const int cps = seg_chunks(nch, S);
+  const int c0 = seg * cps, c1 = min(nch, c0 + cps);
+  const int p = blockIdx.x * kCorrThreads + threadIdx.x;
+  if (c0 >= c1 || (int)blockIdx.x * kCorrThreads >= (c1 - c0) * CHK) return;
+  for (int t = threadIdx.x; t < NGW; t += blockDim.x) h[t] = tails[((int64_t)b * S + seg - 1) * NGW + t];
   __syncthreads();
-  const bool write_out = pass == 2 || seg == 0;
-  T* tail = (tb && pass == 1 && seg + 1 < S) ? tb + (int64_t)seg * NGW : nullptr;
-  unsigned ph = 0;
-  sweep<T, YT, OT, MODE>(sh, g, Mall + cbase[b], yin + s, has_top, has_bot, write_out ? out + s : nullptr, c0,
-                         c1 - c0, hist, tail, ph, failed, err);
+  if (p >= (c1 - c0) * CHK) return;
+  const int r = row_of<MODE>(c0 * CHK + p, ld);
+  if (r >= n) return;
+  const int64_t xm = (int64_t)cpsmax * CHK;
+  const T* Xp = Xall + ((int64_t)b * (S - 1) + (seg - 1)) * xm * NGW + p;
+  T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
+#pragma unroll 2
+  for (int q = 0; q < NGW; q += 4) {
+    a0 += Xp[(int64_t)q * xm] * h[q];
+    a1 += Xp[(int64_t)(q + 1) * xm] * h[q + 1];
+    a2 += Xp[(int64_t)(q + 2) * xm] * h[q + 2];
+    a3 += Xp[(int64_t)(q + 3) * xm] * h[q + 3];
+  }
+  OT* ob = out + s;
+  ob[r] = (OT)((T)ob[r] + ((a0 + a1) + (a2 + a3)));
 }
 
 // Unsegmented block solve (S = 1): one CTA per block runs the forward and
@@ -447,20 +501,20 @@ k_block_solve(const T* __restrict__ M1all, const T* __restrict__ M2all, const in
       sh.corr[K + t] = has_bot ? cbot_all[(int64_t)b * K + t] : 0.0;
     }
     if (!TRANS)
-      sweep<T, double, T, LF>(sh, g, M1all + cbase[b], r_in + s, has_top, has_bot, tmp + s, 0, nch, nullptr,
-                              nullptr, ph, failed, err);
+      sweep<T, double, T, LF>(sh, g, M1all + cbase[b], r_in + s, has_top, has_bot, tmp + s, 0, nch, nullptr, ph,
+                              failed, err);
     else
-      sweep<T, double, T, UTF>(sh, g, M1all + cbase[b], r_in + s, has_top, has_bot, tmp + s, 0, nch, nullptr,
-                               nullptr, ph, failed, err);
+      sweep<T, double, T, UTF>(sh, g, M1all + cbase[b], r_in + s, has_top, has_bot, tmp + s, 0, nch, nullptr, ph,
+                               failed, err);
   }
   {
     SweepSh<T, T> sh = carve<T, T>(smem_raw, g);
     if (!TRANS)
-      sweep<T, T, double, UB>(sh, g, M2all + cbase[b], tmp + s, false, false, z_out + s, 0, nch, nullptr, nullptr,
-                              ph, failed, err);
+      sweep<T, T, double, UB>(sh, g, M2all + cbase[b], tmp + s, false, false, z_out + s, 0, nch, nullptr, ph,
+                              failed, err);
     else
-      sweep<T, T, double, LTB>(sh, g, M2all + cbase[b], tmp + s, false, false, z_out + s, 0, nch, nullptr,
-                               nullptr, ph, failed, err);
+      sweep<T, T, double, LTB>(sh, g, M2all + cbase[b], tmp + s, false, false, z_out + s, 0, nch, nullptr, ph,
+                               failed, err);
   }
 }
 
@@ -532,21 +586,32 @@ __global__ void k_reduced(const double* __restrict__ band, int64_t N, int K, Dev
 }
 
 template <typename T, typename YT, typename OT, int MODE>
-cudaError_t launch_sweep(const T* M, const T* Tm, const Factors<T>& f, int K, int P, Dev d, const YT* yin, OT* out,
-                         const double* ctop, const double* cbot, cudaStream_t s) {
+cudaError_t launch_sweep(const T* M, const T* Tm, const T* Xm, const Factors<T>& f, int K, int P, Dev d,
+                         const YT* yin, OT* out, const double* ctop, const double* cbot, cudaStream_t s) {
   const size_t smem = sweep_smem<T>(K);
   auto kern = k_sweep<T, YT, OT, MODE>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int S = f.S;
   count_launches(1);
-  kern<<<dim3(S > 1 ? S - 1 : 1, P), NWS * 32, smem, s>>>(M, Tm, f.cbase, K, d, yin, out, f.tails, ctop, cbot, P, S,
-                                                          1, f.err);
-  if (S > 1) {
+  kern<<<dim3(S, P), NWS * 32, smem, s>>>(M, f.cbase, K, d, yin, out, f.tails, ctop, cbot, P, S, f.err);
+  e = cudaGetLastError();
+  if (e != cudaSuccess || S == 1) return e;
+  if (S > 2) {
+    const size_t csmem = chain_smem<T>(K, S);
+    auto chain = k_seg_chain<T>;
+    if (csmem > 48 * 1024) {
+      e = cudaFuncSetAttribute(chain, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csmem);
+      if (e != cudaSuccess) return e;
+    }
     count_launches(1);
-    kern<<<dim3(S - 1, P), NWS * 32, smem, s>>>(M, Tm, f.cbase, K, d, yin, out, f.tails, ctop, cbot, P, S, 2,
-                                                 f.err);
+    chain<<<P, kCorrThreads, csmem, s>>>(Tm, f.tails, K, d, S);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
   }
+  count_launches(1);
+  const int tiles = (f.cpsmax * CHK + kCorrThreads - 1) / kCorrThreads;
+  k_seg_correct<T, OT, MODE><<<dim3(tiles, S - 1, P), kCorrThreads, 0, s>>>(Xm, f.tails, K, d, S, f.cpsmax, out);
   return cudaGetLastError();
 }
 
@@ -567,13 +632,13 @@ cudaError_t launch_block_solve(const Factors<T>& f, int K, int P, Dev d, const d
     return cudaGetLastError();
   }
   if (!TRANS) {
-    e = launch_sweep<T, double, T, LF>(f.Mlf, f.Tlf, f, K, P, d, r, tmp, ctop, cbot, s);
+    e = launch_sweep<T, double, T, LF>(f.Mlf, f.Tlf, f.Xlf, f, K, P, d, r, tmp, ctop, cbot, s);
     if (e != cudaSuccess) return e;
-    return launch_sweep<T, T, double, UB>(f.Mub, f.Tub, f, K, P, d, tmp, z, nullptr, nullptr, s);
+    return launch_sweep<T, T, double, UB>(f.Mub, f.Tub, f.Xub, f, K, P, d, tmp, z, nullptr, nullptr, s);
   }
-  e = launch_sweep<T, double, T, UTF>(f.Mutf, f.Tutf, f, K, P, d, r, tmp, ctop, cbot, s);
+  e = launch_sweep<T, double, T, UTF>(f.Mutf, f.Tutf, f.Xutf, f, K, P, d, r, tmp, ctop, cbot, s);
   if (e != cudaSuccess) return e;
-  return launch_sweep<T, T, double, LTB>(f.Mltb, f.Tltb, f, K, P, d, tmp, z, nullptr, nullptr, s);
+  return launch_sweep<T, T, double, LTB>(f.Mltb, f.Tltb, f.Xltb, f, K, P, d, tmp, z, nullptr, nullptr, s);
 }
 
 }  // namespace

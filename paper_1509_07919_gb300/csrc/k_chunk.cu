@@ -189,20 +189,25 @@ namespace {
 // with zero history it yields zhat; by linearity its true values are
 // z = zhat + X h, with
 //     X_c = - sum_{k=1..ng} G_{c,k} X_{c-k},   c = c0 .. c1-1,
-// started from X_{c0-ng+i} = the identity rows of history chunk i.  The
-// transfer matrix T_s (X on the segment's last ng chunks, (32 ng) x (32 ng),
-// row-major) carries the history from segment to segment:
+// started from X_{c0-ng+i} = the identity rows of history chunk i.  This
+// kernel stores, per block and segment s >= 1, X itself (column-major over
+// the segment's positions, cpsmax 32 rows per segment) for the correction
+// z += X h of the apply, and the transfer matrix T_s (X on the segment's last
+// ng chunks, (32 ng) x (32 ng), row-major), which carries the history from
+// segment to segment:
 //     tail_s = zhat_tail_s + T_s tail_{s-1}.
 // One CTA per block and segment s >= 1; thread (q, rg) computes column q of
 // rows rg R .. rg R + R - 1 of every X_c (broadcast 16-byte reads of G,
-// conflict-free reads of X).
+// conflict-free reads of X; X rows padded by one element so that the
+// column-major store reads them conflict-free too).
 template <typename T, int NG>
 struct SegTrans {
   static constexpr int NGW = CH * NG;
+  static constexpr int XLD = NGW + 1;                      // padded X row
   static constexpr int RG = (NG == 3) ? 2 : 256 / NGW;   // row groups
   static constexpr int R = CH / RG;                        // rows per thread
   static constexpr int NTH = NGW * RG;
-  static constexpr size_t smem = ((size_t)(NG + 1) * CH * NGW + (size_t)NG * CH * CH) * sizeof(T);
+  static constexpr size_t smem = ((size_t)(NG + 1) * CH * XLD + (size_t)NG * CH * CH) * sizeof(T);
 };
 
 template <typename T> struct Vec16;
@@ -211,14 +216,15 @@ template <> struct Vec16<double> { using type = double2; };
 
 template <typename T, int NG>
 __global__ void __launch_bounds__(256)
-k_seg_trans(const T* __restrict__ Mall, const int64_t* __restrict__ cbase, Dev d, int S, T* __restrict__ Tout) {
+k_seg_trans(const T* __restrict__ Mall, const int64_t* __restrict__ cbase, Dev d, int S, int cpsmax,
+            T* __restrict__ Tout, T* __restrict__ Xout) {
   using C = SegTrans<T, NG>;
-  constexpr int NGW = C::NGW, R = C::R, NTH = C::NTH;
+  constexpr int NGW = C::NGW, XLD = C::XLD, R = C::R, NTH = C::NTH;
   constexpr int E = 16 / (int)sizeof(T);
   using V = typename Vec16<T>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* X = reinterpret_cast<T*>(smem_raw);          // (NG + 1) ring slots x 32 x NGW
-  T* Gs = X + (NG + 1) * CH * NGW;                // G_{c,1..NG}, column-major as stored
+  T* Gs = reinterpret_cast<T*>(smem_raw);         // G_{c,1..NG}, column-major as stored
+  T* X = Gs + NG * CH * CH;                       // (NG + 1) ring slots x 32 x XLD
   const int b = blockIdx.y, s = blockIdx.x + 1;
   const int nch = (int)(d.ld[b] / CH);
   const int cps = seg_chunks(nch, S);
@@ -226,14 +232,16 @@ k_seg_trans(const T* __restrict__ Mall, const int64_t* __restrict__ cbase, Dev d
   if (c0 >= c1) return;
   const int tid = threadIdx.x;
   auto slot = [](int c) { return ((c % (NG + 1)) + (NG + 1)) % (NG + 1); };
-  for (int e = tid; e < (NG + 1) * CH * NGW; e += NTH) X[e] = T(0);
+  for (int e = tid; e < (NG + 1) * CH * XLD; e += NTH) X[e] = T(0);
   __syncthreads();
   for (int e = tid; e < NG * CH; e += NTH)        // history chunk i = e / 32, row t = e % 32, column e
-    X[slot(c0 - NG + e / CH) * CH * NGW + (e % CH) * NGW + e] = T(1);
+    X[slot(c0 - NG + e / CH) * CH * XLD + (e % CH) * XLD + e] = T(1);
   const int q = tid % NGW, rg = tid / NGW;
   const T* Mb = Mall + cbase[b];
+  const int64_t xm = (int64_t)cpsmax * CH;        // rows of one segment's X
+  T* Xb = Xout + ((int64_t)b * (S - 1) + (s - 1)) * xm * NGW;
   for (int c = c0; c < c1; ++c) {
-    __syncthreads();    // readers of the previous Gs and writers of the previous X_c are done
+    __syncthreads();    // readers of the previous Gs and X_c are done
     const T* Mc = Mb + (int64_t)c * (1 + NG) * CH * CH + CH * CH;
     for (int e = tid; e < NG * CH * CH; e += NTH) Gs[e] = Mc[e];
     __syncthreads();
@@ -241,11 +249,11 @@ k_seg_trans(const T* __restrict__ Mall, const int64_t* __restrict__ cbase, Dev d
 #pragma unroll
     for (int r = 0; r < R; ++r) acc[r] = T(0);
     for (int k = 1; k <= NG; ++k) {
-      const T* Xk = X + slot(c - k) * CH * NGW + q;
+      const T* Xk = X + slot(c - k) * CH * XLD + q;
       const T* Gk = Gs + (k - 1) * CH * CH + rg * R;
 #pragma unroll 4
       for (int j = 0; j < CH; ++j) {
-        const T x = Xk[j * NGW];
+        const T x = Xk[j * XLD];
         const V* g = reinterpret_cast<const V*>(Gk + j * CH);
 #pragma unroll
         for (int v = 0; v < R / E; ++v) {
@@ -256,47 +264,57 @@ k_seg_trans(const T* __restrict__ Mall, const int64_t* __restrict__ cbase, Dev d
         }
       }
     }
-    T* Xc = X + slot(c) * CH * NGW + q;
+    T* Xc = X + slot(c) * CH * XLD;
 #pragma unroll
-    for (int r = 0; r < R; ++r) Xc[(rg * R + r) * NGW] = acc[r];
+    for (int r = 0; r < R; ++r) Xc[(rg * R + r) * XLD + q] = acc[r];
+    __syncthreads();
+    // X_c to global, column-major over the segment's positions (coalesced)
+    const int64_t pr = (int64_t)(c - c0) * CH;
+    for (int e = tid; e < CH * NGW; e += NTH) {
+      const int t = e % CH, qq = e / CH;
+      Xb[(int64_t)qq * xm + pr + t] = Xc[t * XLD + qq];
+    }
   }
   __syncthreads();
   T* To = Tout + ((int64_t)b * S + s) * NGW * NGW;
   for (int e = tid; e < NGW * NGW; e += NTH) {
     const int row = e / NGW, col = e % NGW;        // row = 32 i + t: chunk c1 - NG + i, position t
-    To[e] = X[slot(c1 - NG + row / CH) * CH * NGW + (row % CH) * NGW + col];
+    To[e] = X[slot(c1 - NG + row / CH) * CH * XLD + (row % CH) * XLD + col];
   }
 }
 
 template <typename T, int NG>
-cudaError_t seg_trans_ng(const T* M, const int64_t* cbase, int P, int S, Dev d, T* out, cudaStream_t s) {
+cudaError_t seg_trans_ng(const T* M, const int64_t* cbase, int P, int S, int cpsmax, Dev d, T* tout, T* xout,
+                         cudaStream_t s) {
   using C = SegTrans<T, NG>;
   auto kern = k_seg_trans<T, NG>;
   if (C::smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem);
     if (e != cudaSuccess) return e;
   }
-  kern<<<dim3(S - 1, P), C::NTH, C::smem, s>>>(M, cbase, d, S, out);
+  kern<<<dim3(S - 1, P), C::NTH, C::smem, s>>>(M, cbase, d, S, cpsmax, tout, xout);
   return cudaGetLastError();
 }
 
 }  // namespace
 
 template <typename T>
-cudaError_t launch_seg_trans(const T* M, const int64_t* cbase, int K, int P, int S, Dev d, T* out, cudaStream_t s) {
+cudaError_t launch_seg_trans(const T* M, const int64_t* cbase, int K, int P, int S, int cpsmax, Dev d, T* tout,
+                             T* xout, cudaStream_t s) {
   if (S < 2) return cudaSuccess;
   count_launches(1);
   switch ((K + CH - 1) / CH) {
-    case 1: return seg_trans_ng<T, 1>(M, cbase, P, S, d, out, s);
-    case 2: return seg_trans_ng<T, 2>(M, cbase, P, S, d, out, s);
-    case 3: return seg_trans_ng<T, 3>(M, cbase, P, S, d, out, s);
-    default: return seg_trans_ng<T, 4>(M, cbase, P, S, d, out, s);
+    case 1: return seg_trans_ng<T, 1>(M, cbase, P, S, cpsmax, d, tout, xout, s);
+    case 2: return seg_trans_ng<T, 2>(M, cbase, P, S, cpsmax, d, tout, xout, s);
+    case 3: return seg_trans_ng<T, 3>(M, cbase, P, S, cpsmax, d, tout, xout, s);
+    default: return seg_trans_ng<T, 4>(M, cbase, P, S, cpsmax, d, tout, xout, s);
   }
 }
 
-template cudaError_t launch_seg_trans<float>(const float*, const int64_t*, int, int, int, Dev, float*, cudaStream_t);
-template cudaError_t launch_seg_trans<double>(const double*, const int64_t*, int, int, int, Dev, double*,
-                                              cudaStream_t);
+template cudaError_t launch_seg_trans<float>(const float*, const int64_t*, int, int, int, int, Dev, float*, float*,
+                                             cudaStream_t);
+template cudaError_t launch_seg_trans<double>(const double*, const int64_t*, int, int, int, int, Dev, double*,
+                                              double*, cudaStream_t);
 
 template cudaError_t launch_chunk_mats<float>(const float*, int, int, Dev, const int64_t*, int, int, float*,
                                               cudaStream_t);

@@ -112,6 +112,11 @@ struct Solver : SolverBase {
     const size_t ngw = (size_t)32 * chunk_couplings(h->L.K);
     return (size_t)h->L.P * h->L.S * ngw * ngw;
   }
+  // elements of one sweep kind's history responses: P x (S - 1) x 32 ng x cpsmax 32
+  size_t xresp_elems() const {
+    const size_t ngw = (size_t)32 * chunk_couplings(h->L.K);
+    return (size_t)h->L.P * (h->L.S - 1) * ngw * (size_t)seg_chunks(h->L.max_nch, h->L.S) * 32;
+  }
 
   sap_status_t alloc() override {
     const Layout& L = h->L;
@@ -132,6 +137,9 @@ struct Solver : SolverBase {
     if (L.S > 1) {
       TRY(h->mem.alloc(&f.Tlf, trans_elems()));
       TRY(h->mem.alloc(&f.Tub, trans_elems()));
+      TRY(h->mem.alloc(&f.Xlf, xresp_elems()));
+      TRY(h->mem.alloc(&f.Xub, xresp_elems()));
+      f.cpsmax = seg_chunks(L.max_nch, L.S);
       TRY(h->mem.alloc(&f.tails, (size_t)P * L.S * 32 * chunk_couplings(K)));
     }
     if (h->opt.variant == SAP_C && P > 1) {
@@ -159,8 +167,8 @@ struct Solver : SolverBase {
     CK(launch_factor_lu<T>(bandT, L.N, K, P, h->d, h->absmax, eps, f.F, h->n_boosted, s));
     CK(launch_chunk_mats<T>(f.F, K, P, h->d, f.cbase, L.max_nch, 0, f.Mlf, s));
     CK(launch_chunk_mats<T>(f.F, K, P, h->d, f.cbase, L.max_nch, 1, f.Mub, s));
-    CK(launch_seg_trans<T>(f.Mlf, f.cbase, K, P, L.S, h->d, f.Tlf, s));
-    CK(launch_seg_trans<T>(f.Mub, f.cbase, K, P, L.S, h->d, f.Tub, s));
+    CK(launch_seg_trans<T>(f.Mlf, f.cbase, K, P, L.S, f.cpsmax, h->d, f.Tlf, f.Xlf, s));
+    CK(launch_seg_trans<T>(f.Mub, f.cbase, K, P, L.S, f.cpsmax, h->d, f.Tub, f.Xub, s));
     transposed_ready = false;
     CK(cudaEventRecord(h->evp[1], s));
     if (h->opt.variant == SAP_C && P > 1) {
@@ -212,12 +220,14 @@ struct Solver : SolverBase {
       if (L.S > 1) {
         TRY(h->mem.alloc(&f.Tutf, trans_elems()));
         TRY(h->mem.alloc(&f.Tltb, trans_elems()));
+        TRY(h->mem.alloc(&f.Xutf, xresp_elems()));
+        TRY(h->mem.alloc(&f.Xltb, xresp_elems()));
       }
     }
     CK(launch_chunk_mats<T>(f.F, L.K, L.P, h->d, f.cbase, L.max_nch, 2, f.Mutf, s));
     CK(launch_chunk_mats<T>(f.F, L.K, L.P, h->d, f.cbase, L.max_nch, 3, f.Mltb, s));
-    CK(launch_seg_trans<T>(f.Mutf, f.cbase, L.K, L.P, L.S, h->d, f.Tutf, s));
-    CK(launch_seg_trans<T>(f.Mltb, f.cbase, L.K, L.P, L.S, h->d, f.Tltb, s));
+    CK(launch_seg_trans<T>(f.Mutf, f.cbase, L.K, L.P, L.S, f.cpsmax, h->d, f.Tutf, f.Xutf, s));
+    CK(launch_seg_trans<T>(f.Mltb, f.cbase, L.K, L.P, L.S, f.cpsmax, h->d, f.Tltb, f.Xltb, s));
     transposed_ready = true;
     return SAP_OK;
   }
@@ -508,24 +518,25 @@ sap_status_t sap_factor(const double* band_dev, int64_t N, int32_t K, const sap_
   }
   L.c_elems = cacc;
   {
-    // sweep segments.  Automatic count (measured on GB300): FP32 factors with
-    // ng <= 2 couplings per chunk: up to two CTAs per SM over all blocks,
-    // segments of at least 16 chunks, used only if that gives at least 4
-    // segments per block.  For ng >= 3 or FP64 factors the transfer matrices
-    // cost more to form (FP64 arithmetic is slow on this part): one CTA per
-    // SM, segments of at least 32 chunks, at least 6 per block.  Never more
-    // than kMaxAutoSegments.  Any count is lowered to keep max(ng, 2) chunks
-    // of 32 rows in every full segment.
+    // sweep segments.  Automatic count (measured on GB300): FP32 factors:
+    // up to two CTAs per SM over all blocks, segments of at least 16 chunks,
+    // used only if that gives at least 4 segments per block.  FP64 factors:
+    // the transfer matrices cost more to form (FP64 arithmetic is slow on
+    // this part): one CTA per SM, segments of at least 32 chunks, at least 6
+    // per block.  Never more than kMaxAutoSegments.  Any count is lowered to
+    // keep max(ng, 2) chunks of 32 rows in every full segment; segmentation
+    // needs ng <= 4 couplings per chunk.
     int min_nch = L.max_nch;
     for (int i = 0; i < L.P; ++i) min_nch = std::min(min_nch, (int)(L.ld[i] / 32));
     const int ngc = chunk_couplings(K);
     int S = opt.segments;
     if (S == 0) {
-      const bool narrow = ngc <= 2 && opt.precision == SAP_FP32;
-      S = std::min((narrow ? 2 : 1) * kSMs / L.P, min_nch / (narrow ? 16 : 32));
-      S = S < (narrow ? 4 : 6) ? 1 : std::min(S, kMaxAutoSegments);
+      const bool f32 = opt.precision == SAP_FP32;
+      S = std::min((f32 ? 2 : 1) * kSMs / L.P, min_nch / (f32 ? 16 : 32));
+      S = S < (f32 ? 4 : 6) ? 1 : std::min(S, kMaxAutoSegments);
     }
-    S = std::min(S, std::max(1, min_nch / std::max(chunk_couplings(K), 2)));
+    S = std::min(S, std::max(1, min_nch / std::max(ngc, 2)));
+    if (ngc > 4) S = 1;
     L.S = std::max(1, S);
   }
   int64_t *doff, *dfb, *dld, *dcb;

@@ -366,7 +366,7 @@ def run_gpu(args):
             "gpu_launches": int(launches),
             "roofline": roofline,
             "cpu_baseline": cpu,
-            "detail": {"sweep_segments_per_block": i1.segments,
+            "detail": {"sweep_segments_per_block": i1.segments, "krylov_graph": bool(i1.graphed),
                        "iters_fwd": i1.iters, "iters_adj": i2.iters, "matvecs_fwd": i1.n_matvec,
                        "matvecs_adj": i2.n_matvec, "restarts_fwd": i1.n_restarts,
                        "restarts_adj": i2.n_restarts, "relres_fwd": i1.relres,

@@ -95,7 +95,7 @@ typedef struct {
     float t_ul_ms;        /* SaP-C: block UL (top tiles only) */
     float t_spk_ms;       /* SaP-C: B/C, spike tips, Rbar_i, its GEPP and inverse */
     int32_t segments;     /* sweep segments per block in use (sap_options_t.segments) */
-    int32_t reserved0;
+    int32_t graphed;      /* 1 if the iterations ran as replays of one captured CUDA graph */
 } sap_info_t;
 
 /* Defaults as documented above. */

@@ -312,8 +312,9 @@ template <typename T, typename YT, typename OT, int MODE>
 __global__ void __launch_bounds__(NWS * 32)
 k_sweep(const T* __restrict__ Mall, const int64_t* __restrict__ cbase, int K, Dev d, const YT* __restrict__ yin,
         OT* __restrict__ out, T* __restrict__ tails, const double* __restrict__ ctop_all,
-        const double* __restrict__ cbot_all, int P, int S, int* __restrict__ err) {
+        const double* __restrict__ cbot_all, int P, int S, int* __restrict__ err, Gate gt) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  if (gate_skip(gt)) return;
   const int b = blockIdx.y;
   const int seg = (int)blockIdx.x;
   const int64_t s = d.off[b];
@@ -372,8 +373,9 @@ size_t chain_smem(int K, int S) {
 
 template <typename T>
 __global__ void __launch_bounds__(kCorrThreads)
-k_seg_chain(const T* __restrict__ Tall, T* __restrict__ tails, int K, Dev d, int S) {
+k_seg_chain(const T* __restrict__ Tall, T* __restrict__ tails, int K, Dev d, int S, Gate gt) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  if (gate_skip(gt)) return;
   const int b = blockIdx.x;
   const int ng = n_couplings(K);
   const int NGW = ng * CHK;
@@ -434,8 +436,9 @@ k_seg_chain(const T* __restrict__ Tall, T* __restrict__ tails, int K, Dev d, int
 template <typename T, typename OT, int MODE>
 __global__ void __launch_bounds__(kCorrThreads)
 k_seg_correct(const T* __restrict__ Xall, const T* __restrict__ tails, int K, Dev d, int S, int cpsmax,
-              OT* __restrict__ out) {
+              OT* __restrict__ out, Gate gt) {
   __shared__ T h[4 * CHK];
+  if (gate_skip(gt)) return;
   const int b = blockIdx.z;
   const int seg = (int)blockIdx.y + 1;
   const int ng = n_couplings(K);
@@ -476,8 +479,9 @@ __global__ void __launch_bounds__(NWS * 32)
 k_block_solve(const T* __restrict__ M1all, const T* __restrict__ M2all, const int64_t* __restrict__ cbase, int K,
               Dev d, const double* __restrict__ r_in, double* __restrict__ z_out, T* __restrict__ tmp,
               const double* __restrict__ ctop_all, const double* __restrict__ cbot_all, int P,
-              int* __restrict__ err) {
+              int* __restrict__ err, Gate gt) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  if (gate_skip(gt)) return;
   const int b = blockIdx.x;
   const int64_t s = d.off[b];
   SweepGeom g;
@@ -543,8 +547,10 @@ __device__ __forceinline__ double rowdot(const M* __restrict__ a, const double* 
 template <typename T, bool TRANS>
 __global__ void k_reduced(const double* __restrict__ band, int64_t N, int K, Dev d,
                           const T* __restrict__ V, const T* __restrict__ Wt, const double* __restrict__ Rinv,
-                          const double* __restrict__ g, double* __restrict__ ctop, double* __restrict__ cbot) {
+                          const double* __restrict__ g, double* __restrict__ ctop, double* __restrict__ cbot,
+                          Gate gate) {
   extern __shared__ __align__(16) double sh[];
+  if (gate_skip(gate)) return;
   double* gb = sh;           // K
   double* gt = gb + K;       // K
   double* xt = gt + K;       // K
@@ -587,14 +593,14 @@ __global__ void k_reduced(const double* __restrict__ band, int64_t N, int K, Dev
 
 template <typename T, typename YT, typename OT, int MODE>
 cudaError_t launch_sweep(const T* M, const T* Tm, const T* Xm, const Factors<T>& f, int K, int P, Dev d,
-                         const YT* yin, OT* out, const double* ctop, const double* cbot, cudaStream_t s) {
+                         const YT* yin, OT* out, const double* ctop, const double* cbot, cudaStream_t s, Gate gt) {
   const size_t smem = sweep_smem<T>(K);
   auto kern = k_sweep<T, YT, OT, MODE>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int S = f.S;
   count_launches(1);
-  kern<<<dim3(S, P), NWS * 32, smem, s>>>(M, f.cbase, K, d, yin, out, f.tails, ctop, cbot, P, S, f.err);
+  kern<<<dim3(S, P), NWS * 32, smem, s>>>(M, f.cbase, K, d, yin, out, f.tails, ctop, cbot, P, S, f.err, gt);
   e = cudaGetLastError();
   if (e != cudaSuccess || S == 1) return e;
   if (S > 2) {
@@ -605,13 +611,14 @@ cudaError_t launch_sweep(const T* M, const T* Tm, const T* Xm, const Factors<T>&
       if (e != cudaSuccess) return e;
     }
     count_launches(1);
-    chain<<<P, kCorrThreads, csmem, s>>>(Tm, f.tails, K, d, S);
+    chain<<<P, kCorrThreads, csmem, s>>>(Tm, f.tails, K, d, S, gt);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
   count_launches(1);
   const int tiles = (f.cpsmax * CHK + kCorrThreads - 1) / kCorrThreads;
-  k_seg_correct<T, OT, MODE><<<dim3(tiles, S - 1, P), kCorrThreads, 0, s>>>(Xm, f.tails, K, d, S, f.cpsmax, out);
+  k_seg_correct<T, OT, MODE><<<dim3(tiles, S - 1, P), kCorrThreads, 0, s>>>(Xm, f.tails, K, d, S, f.cpsmax, out,
+                                                                            gt);
   return cudaGetLastError();
 }
 
@@ -619,7 +626,7 @@ cudaError_t launch_sweep(const T* M, const T* Tm, const T* Xm, const Factors<T>&
 // (L then U; for the transposed operator U^T then L^T).
 template <typename T, bool TRANS>
 cudaError_t launch_block_solve(const Factors<T>& f, int K, int P, Dev d, const double* r, double* z, T* tmp,
-                               const double* ctop, const double* cbot, cudaStream_t s) {
+                               const double* ctop, const double* cbot, cudaStream_t s, Gate gt) {
   cudaError_t e;
   if (f.S == 1) {
     const size_t smem = sweep_smem<T>(K);
@@ -628,17 +635,17 @@ cudaError_t launch_block_solve(const Factors<T>& f, int K, int P, Dev d, const d
     if (e != cudaSuccess) return e;
     count_launches(1);
     kern<<<P, NWS * 32, smem, s>>>(TRANS ? f.Mutf : f.Mlf, TRANS ? f.Mltb : f.Mub, f.cbase, K, d, r, z, tmp, ctop,
-                                   cbot, P, f.err);
+                                   cbot, P, f.err, gt);
     return cudaGetLastError();
   }
   if (!TRANS) {
-    e = launch_sweep<T, double, T, LF>(f.Mlf, f.Tlf, f.Xlf, f, K, P, d, r, tmp, ctop, cbot, s);
+    e = launch_sweep<T, double, T, LF>(f.Mlf, f.Tlf, f.Xlf, f, K, P, d, r, tmp, ctop, cbot, s, gt);
     if (e != cudaSuccess) return e;
-    return launch_sweep<T, T, double, UB>(f.Mub, f.Tub, f.Xub, f, K, P, d, tmp, z, nullptr, nullptr, s);
+    return launch_sweep<T, T, double, UB>(f.Mub, f.Tub, f.Xub, f, K, P, d, tmp, z, nullptr, nullptr, s, gt);
   }
-  e = launch_sweep<T, double, T, UTF>(f.Mutf, f.Tutf, f.Xutf, f, K, P, d, r, tmp, ctop, cbot, s);
+  e = launch_sweep<T, double, T, UTF>(f.Mutf, f.Tutf, f.Xutf, f, K, P, d, r, tmp, ctop, cbot, s, gt);
   if (e != cudaSuccess) return e;
-  return launch_sweep<T, T, double, LTB>(f.Mltb, f.Tltb, f.Xltb, f, K, P, d, tmp, z, nullptr, nullptr, s);
+  return launch_sweep<T, T, double, LTB>(f.Mltb, f.Tltb, f.Xltb, f, K, P, d, tmp, z, nullptr, nullptr, s, gt);
 }
 
 }  // namespace
@@ -650,34 +657,34 @@ int chunk_couplings(int K) { return n_couplings(K); }
 template <typename T>
 cudaError_t launch_apply(const double* band, int64_t N, int K, int P, Dev d, const Factors<T>& f,
                          int variant, bool transpose, const double* r, double* z, double* scratch,
-                         cudaStream_t s) {
+                         cudaStream_t s, Gate gt) {
   double* g = scratch;
   T* tmp = reinterpret_cast<T*>(scratch + N);
   double* ctop = scratch + 2 * N;
   double* cbot = ctop + (int64_t)(P > 1 ? P - 1 : 1) * K;
   cudaError_t e;
   if (variant == SAP_D || P == 1) {
-    return transpose ? launch_block_solve<T, true>(f, K, P, d, r, z, tmp, nullptr, nullptr, s)
-                     : launch_block_solve<T, false>(f, K, P, d, r, z, tmp, nullptr, nullptr, s);
+    return transpose ? launch_block_solve<T, true>(f, K, P, d, r, z, tmp, nullptr, nullptr, s, gt)
+                     : launch_block_solve<T, false>(f, K, P, d, r, z, tmp, nullptr, nullptr, s, gt);
   }
-  e = transpose ? launch_block_solve<T, true>(f, K, P, d, r, g, tmp, nullptr, nullptr, s)
-                : launch_block_solve<T, false>(f, K, P, d, r, g, tmp, nullptr, nullptr, s);
+  e = transpose ? launch_block_solve<T, true>(f, K, P, d, r, g, tmp, nullptr, nullptr, s, gt)
+                : launch_block_solve<T, false>(f, K, P, d, r, g, tmp, nullptr, nullptr, s, gt);
   if (e != cudaSuccess) return e;
   size_t sm = 5 * (size_t)K * sizeof(double);
   count_launches(1);
   if (!transpose)
-    k_reduced<T, false><<<P - 1, 128, sm, s>>>(band, N, K, d, f.V, f.Wt, f.R, g, ctop, cbot);
+    k_reduced<T, false><<<P - 1, 128, sm, s>>>(band, N, K, d, f.V, f.Wt, f.R, g, ctop, cbot, gt);
   else
-    k_reduced<T, true><<<P - 1, 128, sm, s>>>(band, N, K, d, f.Va, f.Wa, f.Ra, g, ctop, cbot);
+    k_reduced<T, true><<<P - 1, 128, sm, s>>>(band, N, K, d, f.Va, f.Wa, f.Ra, g, ctop, cbot, gt);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  return transpose ? launch_block_solve<T, true>(f, K, P, d, r, z, tmp, ctop, cbot, s)
-                   : launch_block_solve<T, false>(f, K, P, d, r, z, tmp, ctop, cbot, s);
+  return transpose ? launch_block_solve<T, true>(f, K, P, d, r, z, tmp, ctop, cbot, s, gt)
+                   : launch_block_solve<T, false>(f, K, P, d, r, z, tmp, ctop, cbot, s, gt);
 }
 
 template cudaError_t launch_apply<float>(const double*, int64_t, int, int, Dev, const Factors<float>&, int, bool,
-                                         const double*, double*, double*, cudaStream_t);
+                                         const double*, double*, double*, cudaStream_t, Gate);
 template cudaError_t launch_apply<double>(const double*, int64_t, int, int, Dev, const Factors<double>&, int,
-                                          bool, const double*, double*, double*, cudaStream_t);
+                                          bool, const double*, double*, double*, cudaStream_t, Gate);
 
 }  // namespace sap

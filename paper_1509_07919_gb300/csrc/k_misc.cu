@@ -26,8 +26,9 @@ constexpr int SPMV_T = 128;
 template <bool TRANS>
 __global__ void __launch_bounds__(SPMV_T)
 k_spmv(const double* __restrict__ band, int64_t N, int K, const double* __restrict__ x,
-       double* __restrict__ y) {
+       double* __restrict__ y, Gate gt) {
   extern __shared__ double xs[];
+  if (gate_skip(gt)) return;
   const int64_t i0 = (int64_t)blockIdx.x * SPMV_T;
   const int span = SPMV_T + 2 * K;
   for (int t = threadIdx.x; t < span; t += SPMV_T) {
@@ -110,7 +111,7 @@ __global__ void k_grad_band(const double* __restrict__ lam, const double* __rest
 }  // namespace
 
 cudaError_t launch_spmv(const double* band, int64_t N, int K, const double* x, double* y, bool transpose,
-                        cudaStream_t s) {
+                        cudaStream_t s, Gate gt) {
   int64_t nb = (N + SPMV_T - 1) / SPMV_T;
   size_t smem = (SPMV_T + 2 * (size_t)K) * sizeof(double);
   cudaError_t e;
@@ -118,12 +119,12 @@ cudaError_t launch_spmv(const double* band, int64_t N, int K, const double* x, d
     e = cudaFuncSetAttribute(k_spmv<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     count_launches(1);
-    k_spmv<true><<<(unsigned)nb, SPMV_T, smem, s>>>(band, N, K, x, y);
+    k_spmv<true><<<(unsigned)nb, SPMV_T, smem, s>>>(band, N, K, x, y, gt);
   } else {
     e = cudaFuncSetAttribute(k_spmv<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     count_launches(1);
-    k_spmv<false><<<(unsigned)nb, SPMV_T, smem, s>>>(band, N, K, x, y);
+    k_spmv<false><<<(unsigned)nb, SPMV_T, smem, s>>>(band, N, K, x, y, gt);
   }
   return cudaGetLastError();
 }
@@ -137,6 +138,13 @@ cudaError_t launch_grad_band(const double* lam, const double* x, int64_t N, int 
 // --------------------------------------------------------------- Krylov --
 namespace {
 constexpr int RT = 256;
+
+__device__ __forceinline__ bool kr_skip(const KrylovDev& kd) {
+  Gate g;
+  g.flags = kd.flags;
+  g.mode = kd.gmode;
+  return gate_skip(g);
+}
 
 // Block-reduce ND values; the last block to finish sums all partials and
 // returns true (its thread 0 then holds the sums in red[0..ND) and runs the
@@ -194,6 +202,7 @@ __device__ __forceinline__ bool reduce_last(double (&v)[ND], KrylovDev& kd, doub
 
 // ||a||^2 -> S[slot]
 __global__ void __launch_bounds__(RT) k_norm2(const double* __restrict__ a, int64_t n, KrylovDev kd, int slot) {
+  if (kr_skip(kd)) return;
   double v[1] = {0.0};
   GRID_LOOP(i) v[0] += a[i] * a[i];
   double red[1];
@@ -203,6 +212,7 @@ __global__ void __launch_bounds__(RT) k_norm2(const double* __restrict__ a, int6
 // t = b - y, ||t||^2 -> S[slot]
 __global__ void __launch_bounds__(RT) k_residual(const double* __restrict__ b, const double* __restrict__ y,
                                                  double* __restrict__ t, int64_t n, KrylovDev kd, int slot) {
+  if (kr_skip(kd)) return;
   double v[1] = {0.0};
   GRID_LOOP(i) {
     double r = b[i] - y[i];
@@ -217,6 +227,7 @@ __global__ void __launch_bounds__(RT) k_residual(const double* __restrict__ b, c
 // beta = alpha rho1 / rho0, rho0 = rho1.
 __global__ void __launch_bounds__(RT) k_bicg_rho(const double* __restrict__ rj, const double* __restrict__ rt,
                                                  int64_t n, KrylovDev kd, int j) {
+  if (kr_skip(kd)) return;
   double v[1] = {0.0};
   GRID_LOOP(i) v[0] += rj[i] * rt[i];
   double red[1];
@@ -233,8 +244,9 @@ __global__ void __launch_bounds__(RT) k_bicg_rho(const double* __restrict__ rj, 
 // u_i = r_i - beta u_i, i = 0..j
 __global__ void __launch_bounds__(RT) k_bicg_u(double* __restrict__ u0, double* __restrict__ u1,
                                                const double* __restrict__ r0, const double* __restrict__ r1,
-                                               int64_t n, const double* __restrict__ S, int j) {
-  const double beta = S[S_BETA];
+                                               int64_t n, KrylovDev kd, int j) {
+  if (kr_skip(kd)) return;
+  const double beta = kd.S[S_BETA];
   GRID_LOOP(i) {
     u0[i] = r0[i] - beta * u0[i];
     if (j >= 1) u1[i] = r1[i] - beta * u1[i];
@@ -244,6 +256,7 @@ __global__ void __launch_bounds__(RT) k_bicg_u(double* __restrict__ u0, double* 
 // gamma = <u_{j+1}, rt>, alpha = rho0 / gamma
 __global__ void __launch_bounds__(RT) k_bicg_gamma(const double* __restrict__ uj1, const double* __restrict__ rt,
                                                    int64_t n, KrylovDev kd) {
+  if (kr_skip(kd)) return;
   double v[1] = {0.0};
   GRID_LOOP(i) v[0] += uj1[i] * rt[i];
   double red[1];
@@ -260,6 +273,7 @@ __global__ void __launch_bounds__(RT) k_bicg_r(double* __restrict__ r0, double* 
                                                const double* __restrict__ u0, const double* __restrict__ u1,
                                                const double* __restrict__ u2, double* __restrict__ x,
                                                int64_t n, KrylovDev kd, int j) {
+  if (kr_skip(kd)) return;
   const double alpha = kd.S[S_ALPHA];
   double v[1] = {0.0};
   GRID_LOOP(i) {
@@ -276,6 +290,7 @@ __global__ void __launch_bounds__(RT) k_bicg_r(double* __restrict__ r0, double* 
 // MR part (1): sigma1 = <r1,r1>, gamma'_1 = <r0,r1>/sigma1, tau12 = <r2,r1>/sigma1
 __global__ void __launch_bounds__(RT) k_mr1(const double* __restrict__ r0, const double* __restrict__ r1,
                                             const double* __restrict__ r2, int64_t n, KrylovDev kd) {
+  if (kr_skip(kd)) return;
   double v[3] = {0.0, 0.0, 0.0};
   GRID_LOOP(i) {
     double a = r1[i];
@@ -298,6 +313,7 @@ __global__ void __launch_bounds__(RT) k_mr1(const double* __restrict__ r0, const
 // gamma_2 = gamma'_2, omega = gamma_2, gamma_1 = gamma'_1 - tau12 gamma_2, gamma''_1 = gamma_2
 __global__ void __launch_bounds__(RT) k_mr2(const double* __restrict__ r0, const double* __restrict__ r1,
                                             double* __restrict__ r2, int64_t n, KrylovDev kd) {
+  if (kr_skip(kd)) return;
   const double tau = kd.S[S_TAU12];
   double v[2] = {0.0, 0.0};
   GRID_LOOP(i) {
@@ -326,6 +342,7 @@ __global__ void __launch_bounds__(RT) k_mr3(double* __restrict__ x, double* __re
                                             const double* __restrict__ r1, const double* __restrict__ r2,
                                             double* __restrict__ u0, const double* __restrict__ u1,
                                             const double* __restrict__ u2, int64_t n, KrylovDev kd) {
+  if (kr_skip(kd)) return;
   const double* S = kd.S;
   const double g1 = S[S_G1], gpp1 = S[S_GPP1], gp2 = S[S_GP2], gp1 = S[S_GP1], g2 = S[S_G2];
   double v[1] = {0.0};
@@ -339,6 +356,42 @@ __global__ void __launch_bounds__(RT) k_mr3(double* __restrict__ x, double* __re
   }
   double red[1];
   if (reduce_last<1>(v, kd, red) && threadIdx.x == 0) kd.S[S_RN2] = red[0];
+}
+
+__global__ void k_exit_check(KrylovDev kd, double tol, double qoff) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  int* f = kd.flags;
+  double* S = kd.S;
+  if (f[F_DONE]) return;
+  f[F_REPLACE] = 0;
+  if (S[S_BREAK] != 0.0) {
+    f[F_DONE] = 1;
+    f[F_STATUS] = SAP_ERR_BREAKDOWN;
+    S[S_QUART] = S[S_IT] + qoff;
+    return;
+  }
+  f[F_CHECK] = (sqrt(S[S_RN2]) <= tol * sqrt(S[S_BTN2])) ? 1 : 0;
+}
+
+__global__ void k_exit_decide(KrylovDev kd, double tol, double qoff) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  int* f = kd.flags;
+  double* S = kd.S;
+  if (f[F_DONE]) return;
+  if (f[F_CHECK]) {
+    f[F_CHECK] = 0;
+    const double rel = sqrt(S[S_TN2]) / sqrt(S[S_BN2]);
+    S[S_RELRES] = rel;
+    if (rel <= tol) {
+      f[F_DONE] = 1;
+      f[F_STATUS] = SAP_OK;
+      S[S_QUART] = S[S_IT] + qoff;
+      return;
+    }
+    f[F_REPLACE] = 1;       // reliable update r^0 = M^{-1} (b - A x) follows
+    f[F_RESTARTS] += 1;
+  }
+  if (qoff == 1.0) S[S_IT] += 1.0;
 }
 
 __global__ void k_init_scalars(double* S) {
@@ -363,6 +416,16 @@ cudaError_t kr_init(KrylovDev kd, cudaStream_t s) {
   k_init_scalars<<<1, 32, 0, s>>>(kd.S);
   return cudaGetLastError();
 }
+cudaError_t kr_exit_check(KrylovDev kd, double tol, double qoff, cudaStream_t s) {
+  count_launches(1);
+  k_exit_check<<<1, 32, 0, s>>>(kd, tol, qoff);
+  return cudaGetLastError();
+}
+cudaError_t kr_exit_decide(KrylovDev kd, double tol, double qoff, cudaStream_t s) {
+  count_launches(1);
+  k_exit_decide<<<1, 32, 0, s>>>(kd, tol, qoff);
+  return cudaGetLastError();
+}
 cudaError_t kr_norm2(const double* a, int64_t n, KrylovDev kd, int slot, cudaStream_t s) {
   count_launches(1);
   k_norm2<<<krylov_grid(n), RT, 0, s>>>(a, n, kd, slot);
@@ -382,7 +445,7 @@ cudaError_t kr_bicg_rho(const double* rj, const double* rt, int64_t n, KrylovDev
 cudaError_t kr_bicg_u(double* u0, double* u1, const double* r0, const double* r1, int64_t n, KrylovDev kd, int j,
                       cudaStream_t s) {
   count_launches(1);
-  k_bicg_u<<<krylov_grid(n), RT, 0, s>>>(u0, u1, r0, r1, n, kd.S, j);
+  k_bicg_u<<<krylov_grid(n), RT, 0, s>>>(u0, u1, r0, r1, n, kd, j);
   return cudaGetLastError();
 }
 cudaError_t kr_bicg_gamma(const double* uj1, const double* rt, int64_t n, KrylovDev kd, cudaStream_t s) {

@@ -2,6 +2,7 @@
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
+#include "sap_internal.cuh"
 
 namespace sap {
 
@@ -13,6 +14,9 @@ enum ScalarSlot {
   S_BTN2,     // ||M^{-1} b||^2
   S_TN2,      // ||b - A x||^2 (true residual)
   S_BREAK,    // breakdown flag (nonzero)
+  S_IT,       // completed outer iterations
+  S_QUART,    // iterations (in quarters) at the accepted exit
+  S_RELRES,   // true relative residual of the last check
   S_COUNT
 };
 
@@ -22,6 +26,8 @@ struct KrylovDev {
   double* S;           // S_COUNT scalars
   double* part;        // kKrylovBlocks * 4 partial sums
   unsigned* ticket;    // last-block counter (returns to 0 after each reduction)
+  int* flags = nullptr;   // F_COUNT control flags of the device-driven iteration
+  int gmode = 0;          // GateMode of the launch carrying this struct
 };
 
 int krylov_grid(int64_t n);
@@ -37,5 +43,11 @@ cudaError_t kr_bicg_r(double* r0, double* r1, const double* u0, const double* u1
                       int64_t n, KrylovDev kd, int j, cudaStream_t s);
 cudaError_t kr_mr(double* x, double* r0, double* r1, double* r2, double* u0, const double* u1, const double* u2,
                   int64_t n, KrylovDev kd, cudaStream_t s);
+// Exit test at iteration S_IT + qoff, first half: unless finished, flag a true-
+// residual check when ||r^0|| <= tol ||M^{-1} b|| (breakdown finishes the solve).
+cudaError_t kr_exit_check(KrylovDev kd, double tol, double qoff, cudaStream_t s);
+// Second half, after the gated true residual: accept (finish) or flag the
+// residual replacement; qoff == 1 also completes the outer iteration.
+cudaError_t kr_exit_decide(KrylovDev kd, double tol, double qoff, cudaStream_t s);
 
 }  // namespace sap

@@ -17,6 +17,7 @@ using namespace sap;
 namespace sap {
 static std::atomic<long long> g_launches{0};
 void count_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+long long launches_so_far() { return g_launches.load(std::memory_order_relaxed); }
 }  // namespace sap
 
 namespace {
@@ -58,7 +59,9 @@ struct SolverBase {
   virtual sap_status_t alloc() = 0;
   virtual sap_status_t factor(cudaStream_t s) = 0;
   virtual sap_status_t build_adjoint(cudaStream_t s) = 0;
-  virtual sap_status_t apply(const double* r, double* z, bool transpose, cudaStream_t s) = 0;
+  virtual sap_status_t apply(const double* r, double* z, bool transpose, cudaStream_t s, Gate gt = Gate()) = 0;
+  // build what a transposed apply needs (adjoint tips, transposed sweep matrices); synchronises
+  virtual sap_status_t prepare_transposed(cudaStream_t s) = 0;
   virtual sap_status_t block_lu(int i, double* host, cudaStream_t s) = 0;
   virtual sap_status_t interface(int i, int which, bool adjoint, double* host, cudaStream_t s) = 0;
   // SAP_ERR_TIMEOUT (and reset) if a device-side wait gave up since the last call
@@ -78,16 +81,31 @@ struct sap_handle {
   unsigned long long* n_boosted = nullptr;
   int* singular = nullptr;
   // Krylov workspace
-  double* vec = nullptr;      // 9 N doubles: r0 r1 r2 u0 u1 u2 rt tmp t
+  double* vec = nullptr;      // 11 N doubles: r0 r1 r2 u0 u1 u2 rt tmp t, b and x of the iteration
+  // one outer BiCGStab(2) iteration captured as a CUDA graph, per direction
+  // (0 forward, 1 adjoint); captured on first use, replayed per iteration
+  cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+  cudaStream_t ks = nullptr;          // internal stream of the iteration (capturable)
+  cudaEvent_t evf = nullptr, evj = nullptr;   // fork from / join to the caller's stream
+  long long glaunches[2] = {0, 0};   // kernels in each graph
+  bool gfailed[2] = {false, false};  // capture unavailable: launch directly
   KrylovDev kd{};
   double* host_s = nullptr;   // pinned scalar readback
+  int* flags = nullptr;       // F_COUNT device control flags of the Krylov iteration
+  int* host_f = nullptr;      // pinned flag readback
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   cudaEvent_t evp[4] = {nullptr, nullptr, nullptr, nullptr};
   float t_factor_ms = 0.f, t_lu_ms = 0.f, t_ul_ms = 0.f, t_spk_ms = 0.f;
   double* host_stage = nullptr;  // 2 N doubles for sap_solve_host, allocated on first use
   std::unique_ptr<SolverBase> impl;
   ~sap_handle() {
+    for (cudaGraphExec_t g : gexec)
+      if (g) cudaGraphExecDestroy(g);
+    if (ks) cudaStreamDestroy(ks);
+    if (evf) cudaEventDestroy(evf);
+    if (evj) cudaEventDestroy(evj);
     if (host_s) cudaFreeHost(host_s);
+    if (host_f) cudaFreeHost(host_f);
     if (ev0) cudaEventDestroy(ev0);
     if (ev1) cudaEventDestroy(ev1);
     for (cudaEvent_t e : evp)
@@ -232,12 +250,15 @@ struct Solver : SolverBase {
     return SAP_OK;
   }
 
-  sap_status_t apply(const double* r, double* z, bool transpose, cudaStream_t s) override {
-    if (transpose) {
-      TRY(build_adjoint(s));
-      TRY(build_transposed(s));
-    }
-    CK(launch_apply<T>(h->band, h->L.N, h->L.K, h->L.P, h->d, f, h->opt.variant, transpose, r, z, scratch, s));
+  sap_status_t prepare_transposed(cudaStream_t s) override {
+    TRY(build_adjoint(s));
+    return build_transposed(s);
+  }
+
+  sap_status_t apply(const double* r, double* z, bool transpose, cudaStream_t s, Gate gt) override {
+    if (transpose) TRY(prepare_transposed(s));
+    CK(launch_apply<T>(h->band, h->L.N, h->L.K, h->L.P, h->d, f, h->opt.variant, transpose, r, z, scratch, s,
+                       gt));
     return SAP_OK;
   }
 
@@ -328,26 +349,65 @@ sap_status_t check_options(const sap_options_t* o, int64_t N, int K) {
 // Largest K of the SaP-C spike kernel: 8 K^2 + 2 sizeof(T) K^2 bytes of shared memory.
 int max_K_spikes(int precision) { return precision == SAP_FP64 ? 98 : 120; }
 
-// One preconditioned matvec y = M^{-1} (A v) (or with A^T and the SaP of A^T).
-sap_status_t opmv(sap_handle* h, const double* v, double* y, double* tmp, bool tr, cudaStream_t s) {
-  CK(launch_spmv(h->band, h->L.N, h->L.K, v, tmp, tr, s));
-  return h->impl->apply(tmp, y, tr, s);
+// BiCGStab(2) (Sleijpen & Fokkema 1993, l = 2) on M^{-1} A x = M^{-1} b, or
+// on the transposed system.  The iteration runs device-driven: every launch
+// carries a Gate on the solve's control flags, the exit tests after the first
+// and third matvec and after the MR step are device kernels (a true-residual
+// check is flagged when ||r^0|| <= tol ||M^{-1} b||; if the true residual
+// then fails, the residual replacement r^0 = M^{-1}(b - A x) is flagged), and
+// the host reads the flags once per outer iteration.  Launches after the
+// accepted exit of an iteration do nothing.
+sap_status_t krylov_on(sap_handle* h, const double* b_user, double* x_user, bool tr, sap_info_t* info,
+                       cudaStream_t s);
+
+// Runs the solve on the handle's internal stream (stream capture needs a
+// non-legacy stream), ordered after and before the caller's stream.
+sap_status_t krylov(sap_handle* h, const double* b_user, double* x_user, bool tr, sap_info_t* info,
+                    cudaStream_t s) {
+  if (!h->ks) {
+    CK(cudaStreamCreateWithFlags(&h->ks, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&h->evf, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&h->evj, cudaEventDisableTiming));
+  }
+  CK(cudaEventRecord(h->evf, s));
+  CK(cudaStreamWaitEvent(h->ks, h->evf, 0));
+  const sap_status_t st = krylov_on(h, b_user, x_user, tr, info, h->ks);
+  CK(cudaEventRecord(h->evj, h->ks));
+  CK(cudaStreamWaitEvent(s, h->evj, 0));
+  return st;
 }
 
-sap_status_t krylov(sap_handle* h, const double* b, double* x, bool tr, sap_info_t* info, cudaStream_t s) {
+sap_status_t krylov_on(sap_handle* h, const double* b_user, double* x_user, bool tr, sap_info_t* info,
+                       cudaStream_t s) {
   const int64_t N = h->L.N;
   double* r[3] = {h->vec, h->vec + N, h->vec + 2 * N};
   double* u[3] = {h->vec + 3 * N, h->vec + 4 * N, h->vec + 5 * N};
   double* rt = h->vec + 6 * N;
   double* tmp = h->vec + 7 * N;
   double* t = h->vec + 8 * N;
+  // the iteration works on handle-owned copies of b and x, so that its
+  // captured graph does not depend on the caller's pointers
+  double* b = h->vec + 9 * N;
+  double* x = h->vec + 10 * N;
   KrylovDev kd = h->kd;
+  kd.flags = h->flags;
+  KrylovDev ka = kd, kc = kd;
+  ka.gmode = G_ACTIVE;
+  kc.gmode = G_CHECK;
+  Gate gA, gC, gR;
+  gA.flags = gC.flags = gR.flags = h->flags;
+  gA.mode = G_ACTIVE;
+  gC.mode = G_CHECK;
+  gR.mode = G_REPLACE;
   const double tol = h->opt.tol;
   sap_info_t inf{};
   inf.iters = 0;
   inf.relres = 1.0;
+  if (tr) TRY(h->impl->prepare_transposed(s));
   CK(cudaEventRecord(h->ev0, s));
+  CK(cudaMemcpyAsync(b, b_user, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
   CK(cudaMemsetAsync(x, 0, N * sizeof(double), s));
+  CK(cudaMemsetAsync(h->flags, 0, F_COUNT * sizeof(int), s));
   CK(kr_init(kd, s));
   CK(kr_norm2(b, N, kd, S_BN2, s));
   TRY(h->impl->apply(b, r[0], tr, s));
@@ -357,50 +417,75 @@ sap_status_t krylov(sap_handle* h, const double* b, double* x, bool tr, sap_info
   CK(cudaMemcpyAsync(h->host_s, kd.S + S_RN2, 5 * sizeof(double), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   const double bn = std::sqrt(h->host_s[S_BN2 - S_RN2]);
-  const double btn = std::sqrt(h->host_s[S_BTN2 - S_RN2]);
   sap_status_t status = SAP_ERR_NOT_CONVERGED;
-  int64_t nmv = 0;
   if (bn == 0.0) {
     inf.relres = 0.0;
     status = SAP_OK;
   } else {
-    // exit test: recursive residual, then the true residual in FP64
-    auto exit_test = [&](double quarters, bool* done) -> sap_status_t {
-      *done = false;
-      CK(cudaMemcpyAsync(h->host_s, kd.S + S_RN2, 5 * sizeof(double), cudaMemcpyDeviceToHost, s));
-      CK(cudaStreamSynchronize(s));
-      if (h->host_s[S_BREAK - S_RN2] != 0.0) { status = SAP_ERR_BREAKDOWN; *done = true; return SAP_OK; }
-      const double rn = std::sqrt(h->host_s[0]);
-      if (!(rn <= tol * btn)) return SAP_OK;
-      CK(launch_spmv(h->band, N, h->L.K, x, tmp, tr, s));
-      CK(kr_residual(b, tmp, t, N, kd, S_TN2, s));
-      CK(cudaMemcpyAsync(h->host_s, kd.S + S_RN2, 5 * sizeof(double), cudaMemcpyDeviceToHost, s));
-      CK(cudaStreamSynchronize(s));
-      const double rel = std::sqrt(h->host_s[S_TN2 - S_RN2]) / bn;
-      inf.relres = rel;
-      if (rel <= tol) { status = SAP_OK; inf.iters = quarters; *done = true; return SAP_OK; }
-      TRY(h->impl->apply(t, r[0], tr, s));   // reliable update of r^0
-      ++inf.n_restarts;
-      return SAP_OK;
+    auto exit_test = [&](double qoff) -> sap_status_t {
+      CK(kr_exit_check(kd, tol, qoff, s));
+      CK(launch_spmv(h->band, N, h->L.K, x, tmp, tr, s, gC));
+      CK(kr_residual(b, tmp, t, N, kc, S_TN2, s));
+      CK(kr_exit_decide(kd, tol, qoff, s));
+      return h->impl->apply(t, r[0], tr, s, gR);    // residual replacement, when flagged
     };
+    auto iteration = [&]() -> sap_status_t {
+      for (int j = 0; j < 2; ++j) {
+        CK(kr_bicg_rho(r[j], rt, N, ka, j, s));
+        CK(kr_bicg_u(u[0], u[1], r[0], r[1], N, ka, j, s));
+        CK(launch_spmv(h->band, N, h->L.K, u[j], tmp, tr, s, gA));
+        TRY(h->impl->apply(tmp, u[j + 1], tr, s, gA));
+        CK(kr_bicg_gamma(u[j + 1], rt, N, ka, s));
+        CK(kr_bicg_r(r[0], r[1], u[0], u[1], u[2], x, N, ka, j, s));
+        TRY(exit_test(j == 0 ? 0.25 : 0.75));
+        CK(launch_spmv(h->band, N, h->L.K, r[j], tmp, tr, s, gA));
+        TRY(h->impl->apply(tmp, r[j + 1], tr, s, gA));
+      }
+      CK(kr_mr(x, r[0], r[1], r[2], u[0], u[1], u[2], N, ka, s));
+      return exit_test(1.0);
+    };
+    // capture the iteration once per direction; on any capture failure the
+    // iteration is launched directly instead
+    const int gi = tr ? 1 : 0;
+    if (!h->gexec[gi] && !h->gfailed[gi]) {
+      const long long l0 = launches_so_far();
+      cudaGraph_t graph = nullptr;
+      bool ok = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+      const sap_status_t cst = ok ? iteration() : SAP_ERR_CUDA;
+      if (ok) ok = cudaStreamEndCapture(s, &graph) == cudaSuccess && cst == SAP_OK;
+      if (ok) ok = cudaGraphInstantiate(&h->gexec[gi], graph, 0) == cudaSuccess;
+      if (graph) cudaGraphDestroy(graph);
+      if (!ok) {
+        if (h->gexec[gi]) cudaGraphExecDestroy(h->gexec[gi]);
+        h->gexec[gi] = nullptr;
+        h->gfailed[gi] = true;
+        cudaGetLastError();
+      }
+      h->glaunches[gi] = launches_so_far() - l0;
+      count_launches(-(int)h->glaunches[gi]);     // captured, not run
+    }
     bool done = false;
     for (int it = 0; it < h->opt.max_iters && !done; ++it) {
-      for (int j = 0; j < 2 && !done; ++j) {
-        CK(kr_bicg_rho(r[j], rt, N, kd, j, s));
-        CK(kr_bicg_u(u[0], u[1], r[0], r[1], N, kd, j, s));
-        TRY(opmv(h, u[j], u[j + 1], tmp, tr, s));
-        ++nmv;
-        CK(kr_bicg_gamma(u[j + 1], rt, N, kd, s));
-        CK(kr_bicg_r(r[0], r[1], u[0], u[1], u[2], x, N, kd, j, s));
-        TRY(exit_test(it + (j == 0 ? 0.25 : 0.75), &done));
-        if (done) break;
-        TRY(opmv(h, r[j], r[j + 1], tmp, tr, s));
-        ++nmv;
+      if (h->gexec[gi]) {
+        CK(cudaGraphLaunch(h->gexec[gi], s));
+        count_launches((int)h->glaunches[gi]);
+      } else {
+        TRY(iteration());
       }
-      if (done) break;
-      CK(kr_mr(x, r[0], r[1], r[2], u[0], u[1], u[2], N, kd, s));
-      TRY(exit_test(it + 1.0, &done));
-      inf.iters = it + 1.0;
+      CK(cudaMemcpyAsync(h->host_f, h->flags, F_COUNT * sizeof(int), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      done = h->host_f[F_DONE] != 0;
+    }
+    CK(cudaMemcpyAsync(h->host_s, kd.S, S_COUNT * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(h->host_f, h->flags, F_COUNT * sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    inf.n_restarts = h->host_f[F_RESTARTS];
+    if (done) {
+      status = (sap_status_t)h->host_f[F_STATUS];
+      inf.iters = h->host_s[S_QUART];
+      inf.relres = h->host_s[S_RELRES];
+    } else {
+      inf.iters = h->opt.max_iters;
     }
     if (status != SAP_OK) {
       CK(launch_spmv(h->band, N, h->L.K, x, tmp, tr, s));
@@ -410,18 +495,20 @@ sap_status_t krylov(sap_handle* h, const double* b, double* x, bool tr, sap_info
       inf.relres = std::sqrt(h->host_s[S_TN2 - S_RN2]) / bn;
     }
   }
+  CK(cudaMemcpyAsync(x_user, x, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
   CK(cudaEventRecord(h->ev1, s));
   CK(cudaEventSynchronize(h->ev1));
   if (h->impl->take_device_error(s) != SAP_OK) status = SAP_ERR_TIMEOUT;
   float ms = 0.f;
   cudaEventElapsedTime(&ms, h->ev0, h->ev1);
-  inf.n_matvec = nmv;
+  inf.n_matvec = (int64_t)std::llround(4.0 * inf.iters);
   inf.t_solve_ms = ms;
   inf.t_factor_ms = h->t_factor_ms;
   inf.t_lu_ms = h->t_lu_ms;
   inf.t_ul_ms = h->t_ul_ms;
   inf.t_spk_ms = h->t_spk_ms;
   inf.segments = h->L.S;
+  inf.graphed = (h->gexec[tr ? 1 : 0] != nullptr) ? 1 : 0;
   unsigned long long nb = 0;
   CK(cudaMemcpy(&nb, h->n_boosted, sizeof(nb), cudaMemcpyDeviceToHost));
   inf.n_boosted = (int64_t)nb;
@@ -553,15 +640,17 @@ sap_status_t sap_factor(const double* band_dev, int64_t N, int32_t K, const sap_
   TRY(h->mem.alloc(&h->absmax, 1));
   TRY(h->mem.alloc(&h->n_boosted, 1));
   TRY(h->mem.alloc(&h->singular, 1));
-  TRY(h->mem.alloc(&h->vec, (size_t)(9 * N)));
+  TRY(h->mem.alloc(&h->vec, (size_t)(11 * N)));
   TRY(h->mem.alloc(&h->kd.S, S_COUNT));
   TRY(h->mem.alloc(&h->kd.part, kKrylovBlocks * 4));
   TRY(h->mem.alloc(&h->kd.ticket, 1));
+  TRY(h->mem.alloc(&h->flags, F_COUNT));
   CK(cudaMemsetAsync(h->n_boosted, 0, sizeof(unsigned long long), s));
   CK(cudaMemsetAsync(h->singular, 0, sizeof(int), s));
   CK(cudaMemsetAsync(h->kd.ticket, 0, sizeof(unsigned), s));
-  CK(cudaMemsetAsync(h->vec, 0, 9 * N * sizeof(double), s));
-  if (cudaMallocHost(&h->host_s, 16 * sizeof(double)) != cudaSuccess) return SAP_ERR_OOM;
+  CK(cudaMemsetAsync(h->vec, 0, 11 * N * sizeof(double), s));
+  if (cudaMallocHost(&h->host_s, S_COUNT * sizeof(double)) != cudaSuccess) return SAP_ERR_OOM;
+  if (cudaMallocHost(&h->host_f, F_COUNT * sizeof(int)) != cudaSuccess) return SAP_ERR_OOM;
   CK(cudaEventCreate(&h->ev0));
   CK(cudaEventCreate(&h->ev1));
   for (auto& e : h->evp) CK(cudaEventCreate(&e));

@@ -68,12 +68,33 @@ struct Factors {
   int* err = nullptr;    // set to nonzero by a device-side wait that timed out
 };
 
+// Device-side control of the Krylov iteration.  A launch carrying a Gate
+// does nothing when the solve has finished (flags[F_DONE]); the true-residual
+// launches of an exit test run only when the test asked for them
+// (flags[F_CHECK]) and the residual replacement only when the true residual
+// failed (flags[F_REPLACE]).  Kernels read the flags at entry and return
+// uniformly per CTA, so a gated-off launch costs only its launch.
+enum FlagSlot { F_DONE = 0, F_CHECK, F_REPLACE, F_STATUS, F_RESTARTS, F_COUNT };
+enum GateMode { G_ALWAYS = 0, G_ACTIVE = 1, G_CHECK = 2, G_REPLACE = 3 };
+struct Gate {
+  const int* flags = nullptr;
+  int mode = G_ALWAYS;
+};
+__device__ __forceinline__ bool gate_skip(const Gate& g) {
+  if (!g.flags || g.mode == G_ALWAYS) return false;
+  if (g.flags[F_DONE]) return true;
+  if (g.mode == G_CHECK) return g.flags[F_CHECK] == 0;
+  if (g.mode == G_REPLACE) return g.flags[F_REPLACE] == 0;
+  return false;
+}
+
 // Host-side count of kernel launches issued by the library (for reporting).
 void count_launches(int n);
+long long launches_so_far();
 
 // ---- launchers (each returns cudaGetLastError()) ----
 cudaError_t launch_spmv(const double* band, int64_t N, int K, const double* x, double* y,
-                        bool transpose, cudaStream_t s);
+                        bool transpose, cudaStream_t s, Gate gt = Gate());
 cudaError_t launch_absmax(const double* band, int64_t N, int K, double* out, cudaStream_t s);
 cudaError_t launch_grad_band(const double* lam, const double* x, int64_t N, int K, double* g,
                              cudaStream_t s);
@@ -104,7 +125,7 @@ __host__ __device__ inline int seg_chunks(int nch, int S) { return (nch + S - 1)
 template <typename T>
 cudaError_t launch_apply(const double* band, int64_t N, int K, int P, Dev d, const Factors<T>& f,
                          int variant, bool transpose, const double* r, double* z, double* scratch,
-                         cudaStream_t s);
+                         cudaStream_t s, Gate gt = Gate());
 
 // Krylov vector kernels (FP64)
 struct Krylov;  // defined in sap_api.cu

@@ -168,6 +168,7 @@ def test_solve_parity(sap, variant, prec, N, K, P, d):
     x, info, st = sap.sap_solve(h, dev(b))
     x = host(x)
     assert st == sap.SAP_OK
+    assert info.graphed == 1                     # the iteration ran as a captured CUDA graph
     assert info.relres <= 1e-10
     assert np.linalg.norm(b - O.spmv(band, N, K, x)) / np.linalg.norm(b) <= 1e-10
     assert relerr(x, xo) <= 1e-8

@@ -207,6 +207,43 @@ SAP_API sap_status_t sap_band_solve_noalloc(const double *band_dev, int64_t N, i
                                            const double *b_dev, double *x_dev, int32_t precision,
                                            cudaStream_t stream);
 
+/* ---- Batches of independent banded systems ----
+ * Not in the paper (a GB300 addition): n systems of their own N_i and K_i,
+ * each with its own SaP preconditioner, factored and solved together.  Every
+ * system runs on its own internal stream, so their kernels overlap on the
+ * GPU; a batched solve advances all unfinished systems by one outer
+ * BiCGStab(2) iteration per round (each a replay of the system's captured
+ * CUDA graph) and synchronises the host once per round for the whole batch.
+ *   opt applies to every system; opt->P == 0 picks P_i per system so that
+ *   the batch has about two blocks per SM in total, P_i in proportion to N_i
+ *   (at least 1; SaP-C keeps N_i / P_i >= 2 K_i); opt->segments == 0 means
+ *   unsegmented sweeps (the batch already fills the SMs).
+ *   bands_dev[i]: device band of system i (borrowed, as for sap_factor).
+ * Errors: as sap_factor, for the first system that fails (nothing is
+ * returned then). */
+typedef struct sap_batch *sap_batch_t;
+SAP_API sap_status_t sap_factor_batched(int32_t n, const double *const *bands_dev, const int64_t *N,
+                                        const int32_t *K, const sap_options_t *opt, cudaStream_t stream,
+                                        sap_batch_t *out);
+/* Refactor every system after its band values changed (no allocation). */
+SAP_API sap_status_t sap_refactor_batched(sap_batch_t b, cudaStream_t stream);
+/* Solve A_i x_i = b_i (or A_i^T lambda_i = g_i) for all i.  infos and
+ * statuses (per system, optional) receive each solve's report and status;
+ * the return value is SAP_OK or the first failing status.  Synchronises. */
+SAP_API sap_status_t sap_solve_batched(sap_batch_t b, const double *const *b_dev, double *const *x_dev,
+                                       sap_info_t *infos, int32_t *statuses, cudaStream_t stream);
+SAP_API sap_status_t sap_solve_adjoint_batched(sap_batch_t b, const double *const *g_dev,
+                                               double *const *lambda_dev, sap_info_t *infos,
+                                               int32_t *statuses, cudaStream_t stream);
+/* grad_band_i = -lambda_i x_i^T restricted to the band of system i. */
+SAP_API sap_status_t sap_grad_band_batched(sap_batch_t b, const double *const *lambda_dev,
+                                           const double *const *x_dev, double *const *grad_band_dev,
+                                           cudaStream_t stream);
+/* Number of systems, and the partition count chosen for system i (-1 if out of range). */
+SAP_API int32_t sap_batch_size(sap_batch_t b);
+SAP_API int32_t sap_batch_partitions(sap_batch_t b, int32_t i);
+SAP_API sap_status_t sap_batch_destroy(sap_batch_t b);
+
 /* Number of CUDA kernels this library has launched in this process so far
  * (host-side counter, all handles and threads). */
 SAP_API int64_t sap_kernel_launches(void);

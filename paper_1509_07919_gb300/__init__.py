@@ -73,6 +73,14 @@ def _load():
         "sap_max_K": (i32, [i32]),
         "sap_kernel_launches": (i64, []),
         "sap_band_solve_noalloc": (C.c_int, [vp, i64, i32, vp, vp, i32, vp]),
+        "sap_factor_batched": (C.c_int, [i32, vp, vp, vp, P(sap_options_t), vp, P(vp)]),
+        "sap_refactor_batched": (C.c_int, [vp, vp]),
+        "sap_solve_batched": (C.c_int, [vp, vp, vp, vp, vp, vp]),
+        "sap_solve_adjoint_batched": (C.c_int, [vp, vp, vp, vp, vp, vp]),
+        "sap_grad_band_batched": (C.c_int, [vp, vp, vp, vp, vp]),
+        "sap_batch_size": (i32, [vp]),
+        "sap_batch_partitions": (i32, [vp, i32]),
+        "sap_batch_destroy": (C.c_int, [vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -230,6 +238,76 @@ def sap_band_solve_noalloc(band: torch.Tensor, N: int, K: int, b: torch.Tensor, 
     return x
 
 
+class BatchHandle:
+    """Owns a sap_batch_t and keeps the borrowed band tensors alive."""
+
+    def __init__(self, ptr: int, bands, Ns, Ks, opts: sap_options_t):
+        self.ptr = C.c_void_p(ptr)
+        self.bands, self.Ns, self.Ks, self.opts = list(bands), list(Ns), list(Ks), opts
+
+    def __len__(self):
+        return len(self.bands)
+
+    def __del__(self):
+        if getattr(self, "ptr", None) is not None and self.ptr.value and _lib is not None:
+            _lib.sap_batch_destroy(self.ptr)
+            self.ptr = None
+
+
+def _ptr_array(ts):
+    return (C.c_void_p * len(ts))(*[_ptr(t) for t in ts])
+
+
+def sap_factor_batched(bands, Ns, Ks, opts: sap_options_t | None = None, stream=None, **kw) -> BatchHandle:
+    """Factor a batch of systems (P=0 picks the partition count per system)."""
+    kw.setdefault("P", 0)
+    opts = opts or sap_default_options(**kw)
+    n = len(bands)
+    if not (len(Ns) == len(Ks) == n):
+        raise ValueError("bands, Ns and Ks must have the same length")
+    NA = (C.c_int64 * n)(*[int(v) for v in Ns])
+    KA = (C.c_int32 * n)(*[int(v) for v in Ks])
+    out = C.c_void_p()
+    st = _lib.sap_factor_batched(n, _ptr_array(bands), NA, KA, C.byref(opts), _stream(stream), C.byref(out))
+    _check(st, "sap_factor_batched")
+    return BatchHandle(out.value, bands, Ns, Ks, opts)
+
+
+def sap_refactor_batched(bh: BatchHandle, stream=None) -> None:
+    _check(_lib.sap_refactor_batched(bh.ptr, _stream(stream)), "sap_refactor_batched")
+
+
+def _solve_batched(fn, name, bh, ins, outs, stream, raise_on_error):
+    n = len(bh)
+    outs = [torch.empty_like(t) for t in ins] if outs is None else list(outs)
+    infos = (sap_info_t * n)()
+    stats = (C.c_int32 * n)()
+    st = fn(bh.ptr, _ptr_array(ins), _ptr_array(outs), infos, stats, _stream(stream))
+    if raise_on_error:
+        _check(st, name)
+    return outs, list(infos), list(stats), st
+
+
+def sap_solve_batched(bh: BatchHandle, bs, xs=None, stream=None, raise_on_error: bool = True):
+    return _solve_batched(_lib.sap_solve_batched, "sap_solve_batched", bh, bs, xs, stream, raise_on_error)
+
+
+def sap_solve_adjoint_batched(bh: BatchHandle, gs, lams=None, stream=None, raise_on_error: bool = True):
+    return _solve_batched(_lib.sap_solve_adjoint_batched, "sap_solve_adjoint_batched", bh, gs, lams, stream,
+                          raise_on_error)
+
+
+def sap_grad_band_batched(bh: BatchHandle, lams, xs, outs=None, stream=None):
+    outs = [torch.empty_like(bd) for bd in bh.bands] if outs is None else list(outs)
+    _check(_lib.sap_grad_band_batched(bh.ptr, _ptr_array(lams), _ptr_array(xs), _ptr_array(outs),
+                                      _stream(stream)), "sap_grad_band_batched")
+    return outs
+
+
+def sap_batch_partitions(bh: BatchHandle):
+    return [int(_lib.sap_batch_partitions(bh.ptr, i)) for i in range(len(bh))]
+
+
 def sap_kernel_launches() -> int:
     """Kernels launched by libsap in this process so far."""
     return int(_lib.sap_kernel_launches())
@@ -239,6 +317,7 @@ def sap_n_boosted(h: Handle) -> int:
     return int(_lib.sap_n_boosted(h.ptr))
 
 
-from .autograd import SapSolve, sap_solve_autograd  # noqa: E402
+from .autograd import SapSolve, SapSolveBatched, sap_solve_autograd, sap_solve_batched_autograd  # noqa: E402
 
-__all__ = [n for n in dir() if n.startswith("sap_") or n in ("Handle", "SapError", "SapSolve")]
+__all__ = [n for n in dir() if n.startswith("sap_") or n in ("Handle", "BatchHandle", "SapError", "SapSolve",
+                                                                 "SapSolveBatched")]

@@ -35,3 +35,39 @@ class SapSolve(torch.autograd.Function):
 def sap_solve_autograd(band: torch.Tensor, b: torch.Tensor, N: int, K: int, **opts_kw) -> torch.Tensor:
     """Differentiable x = A^{-1} b (options as keyword arguments of sap_options_t)."""
     return SapSolve.apply(band, b, N, K, opts_kw)
+
+
+class SapSolveBatched(torch.autograd.Function):
+    """x_i = A_i^{-1} b_i for a batch; backward by the batched adjoint solve."""
+
+    @staticmethod
+    def forward(ctx, meta, *args):
+        from . import sap_factor_batched, sap_solve_batched
+        Ns, Ks, opts_kw = meta
+        n = len(Ns)
+        bands = [a.contiguous() for a in args[:n]]
+        bs = [a.contiguous() for a in args[n:]]
+        bh = sap_factor_batched(bands, Ns, Ks, **opts_kw)
+        xs, infos, _, _ = sap_solve_batched(bh, bs)
+        ctx.bh = bh
+        ctx.infos = infos
+        ctx.save_for_backward(*xs)
+        return tuple(xs)
+
+    @staticmethod
+    def backward(ctx, *gxs):
+        from . import sap_grad_band_batched, sap_solve_adjoint_batched
+        xs = list(ctx.saved_tensors)
+        n = len(xs)
+        gxs = [torch.zeros_like(x) if g is None else g.contiguous() for g, x in zip(gxs, xs)]
+        lams, _, _, _ = sap_solve_adjoint_batched(ctx.bh, gxs)
+        need_band = any(ctx.needs_input_grad[1:1 + n])
+        gbands = sap_grad_band_batched(ctx.bh, lams, xs) if need_band else [None] * n
+        gbs = [lam if ctx.needs_input_grad[1 + n + i] else None for i, lam in enumerate(lams)]
+        gbands = [g if ctx.needs_input_grad[1 + i] else None for i, g in enumerate(gbands)]
+        return (None, *gbands, *gbs)
+
+
+def sap_solve_batched_autograd(bands, bs, Ns, Ks, **opts_kw):
+    """Differentiable x_i = A_i^{-1} b_i for a batch (one shared option set)."""
+    return list(SapSolveBatched.apply((list(Ns), list(Ks), opts_kw), *bands, *bs))

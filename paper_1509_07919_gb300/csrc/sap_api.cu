@@ -349,177 +349,238 @@ sap_status_t check_options(const sap_options_t* o, int64_t N, int K) {
 // Largest K of the SaP-C spike kernel: 8 K^2 + 2 sizeof(T) K^2 bytes of shared memory.
 int max_K_spikes(int precision) { return precision == SAP_FP64 ? 98 : 120; }
 
+// The handle's internal stream and its fork/join events, created on first use.
+sap_status_t ensure_stream(sap_handle* h) {
+  if (h->ks) return SAP_OK;
+  CK(cudaStreamCreateWithFlags(&h->ks, cudaStreamNonBlocking));
+  CK(cudaEventCreateWithFlags(&h->evf, cudaEventDisableTiming));
+  CK(cudaEventCreateWithFlags(&h->evj, cudaEventDisableTiming));
+  return SAP_OK;
+}
+
+// One BiCGStab(2) solve, split at its host synchronisation points so that a
+// batch of solves can share them: begin() (setup, scalar readback), then
+// rounds (one outer iteration each, flag readback), then finish().  Between
+// two steps the caller synchronises the handle's stream.  All work runs on
+// the handle's internal stream (stream capture needs a non-legacy stream),
+// ordered after the caller's stream at begin() and before it at the end of
+// finish().
+struct KrylovRun {
+  sap_handle* h = nullptr;
+  bool tr = false;
+  cudaStream_t user = nullptr, s = nullptr;
+  const double* b_user = nullptr;
+  double* x_user = nullptr;
+  int64_t N = 0;
+  double *r[3], *u[3], *rt, *tmp, *t, *b, *x;
+  KrylovDev kd, ka, kc;
+  Gate gA, gC, gR;
+  double tol = 0.0, bn = 0.0;
+  sap_info_t inf{};
+  sap_status_t status = SAP_ERR_NOT_CONVERGED;
+  bool done = false;     // converged or broken down (or b = 0)
+  int it = 0;            // outer iterations launched
+  int gi = 0;
+
+  sap_status_t init(sap_handle* hh, const double* bu, double* xu, bool transposed, cudaStream_t us) {
+    h = hh; tr = transposed; user = us; b_user = bu; x_user = xu;
+    TRY(ensure_stream(h));
+    s = h->ks;
+    N = h->L.N;
+    for (int k = 0; k < 3; ++k) {
+      r[k] = h->vec + k * N;
+      u[k] = h->vec + (3 + k) * N;
+    }
+    rt = h->vec + 6 * N;
+    tmp = h->vec + 7 * N;
+    t = h->vec + 8 * N;
+    // the iteration works on handle-owned copies of b and x, so that its
+    // captured graph does not depend on the caller's pointers
+    b = h->vec + 9 * N;
+    x = h->vec + 10 * N;
+    kd = h->kd;
+    kd.flags = h->flags;
+    ka = kd;
+    ka.gmode = G_ACTIVE;
+    kc = kd;
+    kc.gmode = G_CHECK;
+    gA.flags = gC.flags = gR.flags = h->flags;
+    gA.mode = G_ACTIVE;
+    gC.mode = G_CHECK;
+    gR.mode = G_REPLACE;
+    tol = h->opt.tol;
+    inf.iters = 0;
+    inf.relres = 1.0;
+    gi = tr ? 1 : 0;
+    return SAP_OK;
+  }
+
+  // setup launches and the readback of ||b||^2, ||M^{-1} b||^2
+  sap_status_t begin() {
+    if (tr) TRY(h->impl->prepare_transposed(user));
+    CK(cudaEventRecord(h->evf, user));
+    CK(cudaStreamWaitEvent(s, h->evf, 0));
+    CK(cudaEventRecord(h->ev0, s));
+    CK(cudaMemcpyAsync(b, b_user, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemsetAsync(x, 0, N * sizeof(double), s));
+    CK(cudaMemsetAsync(h->flags, 0, F_COUNT * sizeof(int), s));
+    CK(kr_init(kd, s));
+    CK(kr_norm2(b, N, kd, S_BN2, s));
+    TRY(h->impl->apply(b, r[0], tr, s));
+    CK(kr_norm2(r[0], N, kd, S_BTN2, s));
+    CK(cudaMemcpyAsync(rt, r[0], N * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemsetAsync(u[0], 0, N * sizeof(double), s));
+    CK(cudaMemcpyAsync(h->host_s, kd.S + S_RN2, 5 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    return SAP_OK;
+  }
+  // after the stream synchronised: b = 0 finishes at once
+  void after_begin() {
+    bn = std::sqrt(h->host_s[S_BN2 - S_RN2]);
+    if (bn == 0.0) {
+      inf.relres = 0.0;
+      status = SAP_OK;
+      done = true;
+    }
+  }
+
+  sap_status_t exit_test(double qoff) {
+    CK(kr_exit_check(kd, tol, qoff, s));
+    CK(launch_spmv(h->band, N, h->L.K, x, tmp, tr, s, gC));
+    CK(kr_residual(b, tmp, t, N, kc, S_TN2, s));
+    CK(kr_exit_decide(kd, tol, qoff, s));
+    return h->impl->apply(t, r[0], tr, s, gR);    // residual replacement, when flagged
+  }
+  sap_status_t iteration() {
+    for (int j = 0; j < 2; ++j) {
+      CK(kr_bicg_rho(r[j], rt, N, ka, j, s));
+      CK(kr_bicg_u(u[0], u[1], r[0], r[1], N, ka, j, s));
+      CK(launch_spmv(h->band, N, h->L.K, u[j], tmp, tr, s, gA));
+      TRY(h->impl->apply(tmp, u[j + 1], tr, s, gA));
+      CK(kr_bicg_gamma(u[j + 1], rt, N, ka, s));
+      CK(kr_bicg_r(r[0], r[1], u[0], u[1], u[2], x, N, ka, j, s));
+      TRY(exit_test(j == 0 ? 0.25 : 0.75));
+      CK(launch_spmv(h->band, N, h->L.K, r[j], tmp, tr, s, gA));
+      TRY(h->impl->apply(tmp, r[j + 1], tr, s, gA));
+    }
+    CK(kr_mr(x, r[0], r[1], r[2], u[0], u[1], u[2], N, ka, s));
+    return exit_test(1.0);
+  }
+  // capture the iteration once per handle and direction; on any capture
+  // failure the iteration is launched directly instead
+  void capture() {
+    if (h->gexec[gi] || h->gfailed[gi]) return;
+    const long long l0 = launches_so_far();
+    cudaGraph_t graph = nullptr;
+    bool ok = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    const sap_status_t cst = ok ? iteration() : SAP_ERR_CUDA;
+    if (ok) ok = cudaStreamEndCapture(s, &graph) == cudaSuccess && cst == SAP_OK;
+    if (ok) ok = cudaGraphInstantiate(&h->gexec[gi], graph, 0) == cudaSuccess;
+    if (graph) cudaGraphDestroy(graph);
+    if (!ok) {
+      if (h->gexec[gi]) cudaGraphExecDestroy(h->gexec[gi]);
+      h->gexec[gi] = nullptr;
+      h->gfailed[gi] = true;
+      cudaGetLastError();
+    }
+    h->glaunches[gi] = launches_so_far() - l0;
+    count_launches(-(int)h->glaunches[gi]);     // captured, not run
+  }
+  bool active() const { return !done && it < h->opt.max_iters; }
+  // one outer iteration and the readback of the control flags
+  sap_status_t round() {
+    capture();
+    if (h->gexec[gi]) {
+      CK(cudaGraphLaunch(h->gexec[gi], s));
+      count_launches((int)h->glaunches[gi]);
+    } else {
+      TRY(iteration());
+    }
+    ++it;
+    CK(cudaMemcpyAsync(h->host_f, h->flags, F_COUNT * sizeof(int), cudaMemcpyDeviceToHost, s));
+    return SAP_OK;
+  }
+  void after_round() { done = h->host_f[F_DONE] != 0; }
+
+  // results; synchronises the handle's stream and joins the caller's
+  sap_status_t finish(sap_info_t* info) {
+    if (bn != 0.0) {
+      CK(cudaMemcpyAsync(h->host_s, kd.S, S_COUNT * sizeof(double), cudaMemcpyDeviceToHost, s));
+      CK(cudaMemcpyAsync(h->host_f, h->flags, F_COUNT * sizeof(int), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      inf.n_restarts = h->host_f[F_RESTARTS];
+      if (h->host_f[F_DONE]) {
+        status = (sap_status_t)h->host_f[F_STATUS];
+        inf.iters = h->host_s[S_QUART];
+        inf.relres = h->host_s[S_RELRES];
+      } else {
+        status = SAP_ERR_NOT_CONVERGED;
+        inf.iters = h->opt.max_iters;
+      }
+      if (status != SAP_OK) {
+        CK(launch_spmv(h->band, N, h->L.K, x, tmp, tr, s));
+        CK(kr_residual(b, tmp, t, N, kd, S_TN2, s));
+        CK(cudaMemcpyAsync(h->host_s, kd.S + S_RN2, 5 * sizeof(double), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        inf.relres = std::sqrt(h->host_s[S_TN2 - S_RN2]) / bn;
+      }
+    }
+    CK(cudaMemcpyAsync(x_user, x, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    CK(cudaEventRecord(h->ev1, s));
+    CK(cudaEventSynchronize(h->ev1));
+    if (h->impl->take_device_error(s) != SAP_OK) status = SAP_ERR_TIMEOUT;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, h->ev0, h->ev1);
+    inf.n_matvec = (int64_t)std::llround(4.0 * inf.iters);
+    inf.t_solve_ms = ms;
+    inf.t_factor_ms = h->t_factor_ms;
+    inf.t_lu_ms = h->t_lu_ms;
+    inf.t_ul_ms = h->t_ul_ms;
+    inf.t_spk_ms = h->t_spk_ms;
+    inf.segments = h->L.S;
+    inf.graphed = (h->gexec[gi] != nullptr) ? 1 : 0;
+    unsigned long long nb = 0;
+    CK(cudaMemcpy(&nb, h->n_boosted, sizeof(nb), cudaMemcpyDeviceToHost));
+    inf.n_boosted = (int64_t)nb;
+    CK(cudaEventRecord(h->evj, s));
+    CK(cudaStreamWaitEvent(user, h->evj, 0));
+    if (info) *info = inf;
+    return status;
+  }
+};
+
 // BiCGStab(2) (Sleijpen & Fokkema 1993, l = 2) on M^{-1} A x = M^{-1} b, or
 // on the transposed system.  The iteration runs device-driven: every launch
 // carries a Gate on the solve's control flags, the exit tests after the first
 // and third matvec and after the MR step are device kernels (a true-residual
 // check is flagged when ||r^0|| <= tol ||M^{-1} b||; if the true residual
 // then fails, the residual replacement r^0 = M^{-1}(b - A x) is flagged), and
-// the host reads the flags once per outer iteration.  Launches after the
-// accepted exit of an iteration do nothing.
-sap_status_t krylov_on(sap_handle* h, const double* b_user, double* x_user, bool tr, sap_info_t* info,
-                       cudaStream_t s);
-
-// Runs the solve on the handle's internal stream (stream capture needs a
-// non-legacy stream), ordered after and before the caller's stream.
+// the host reads the flags once per outer iteration, which runs as one
+// captured CUDA graph.  Launches after the accepted exit do nothing.
 sap_status_t krylov(sap_handle* h, const double* b_user, double* x_user, bool tr, sap_info_t* info,
                     cudaStream_t s) {
-  if (!h->ks) {
-    CK(cudaStreamCreateWithFlags(&h->ks, cudaStreamNonBlocking));
-    CK(cudaEventCreateWithFlags(&h->evf, cudaEventDisableTiming));
-    CK(cudaEventCreateWithFlags(&h->evj, cudaEventDisableTiming));
+  KrylovRun k;
+  TRY(k.init(h, b_user, x_user, tr, s));
+  TRY(k.begin());
+  CK(cudaStreamSynchronize(k.s));
+  k.after_begin();
+  while (k.active()) {
+    TRY(k.round());
+    CK(cudaStreamSynchronize(k.s));
+    k.after_round();
   }
-  CK(cudaEventRecord(h->evf, s));
-  CK(cudaStreamWaitEvent(h->ks, h->evf, 0));
-  const sap_status_t st = krylov_on(h, b_user, x_user, tr, info, h->ks);
-  CK(cudaEventRecord(h->evj, h->ks));
-  CK(cudaStreamWaitEvent(s, h->evj, 0));
-  return st;
+  return k.finish(info);
 }
 
-sap_status_t krylov_on(sap_handle* h, const double* b_user, double* x_user, bool tr, sap_info_t* info,
-                       cudaStream_t s) {
-  const int64_t N = h->L.N;
-  double* r[3] = {h->vec, h->vec + N, h->vec + 2 * N};
-  double* u[3] = {h->vec + 3 * N, h->vec + 4 * N, h->vec + 5 * N};
-  double* rt = h->vec + 6 * N;
-  double* tmp = h->vec + 7 * N;
-  double* t = h->vec + 8 * N;
-  // the iteration works on handle-owned copies of b and x, so that its
-  // captured graph does not depend on the caller's pointers
-  double* b = h->vec + 9 * N;
-  double* x = h->vec + 10 * N;
-  KrylovDev kd = h->kd;
-  kd.flags = h->flags;
-  KrylovDev ka = kd, kc = kd;
-  ka.gmode = G_ACTIVE;
-  kc.gmode = G_CHECK;
-  Gate gA, gC, gR;
-  gA.flags = gC.flags = gR.flags = h->flags;
-  gA.mode = G_ACTIVE;
-  gC.mode = G_CHECK;
-  gR.mode = G_REPLACE;
-  const double tol = h->opt.tol;
-  sap_info_t inf{};
-  inf.iters = 0;
-  inf.relres = 1.0;
-  if (tr) TRY(h->impl->prepare_transposed(s));
-  CK(cudaEventRecord(h->ev0, s));
-  CK(cudaMemcpyAsync(b, b_user, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
-  CK(cudaMemsetAsync(x, 0, N * sizeof(double), s));
-  CK(cudaMemsetAsync(h->flags, 0, F_COUNT * sizeof(int), s));
-  CK(kr_init(kd, s));
-  CK(kr_norm2(b, N, kd, S_BN2, s));
-  TRY(h->impl->apply(b, r[0], tr, s));
-  CK(kr_norm2(r[0], N, kd, S_BTN2, s));
-  CK(cudaMemcpyAsync(rt, r[0], N * sizeof(double), cudaMemcpyDeviceToDevice, s));
-  CK(cudaMemsetAsync(u[0], 0, N * sizeof(double), s));
-  CK(cudaMemcpyAsync(h->host_s, kd.S + S_RN2, 5 * sizeof(double), cudaMemcpyDeviceToHost, s));
-  CK(cudaStreamSynchronize(s));
-  const double bn = std::sqrt(h->host_s[S_BN2 - S_RN2]);
-  sap_status_t status = SAP_ERR_NOT_CONVERGED;
-  if (bn == 0.0) {
-    inf.relres = 0.0;
-    status = SAP_OK;
-  } else {
-    auto exit_test = [&](double qoff) -> sap_status_t {
-      CK(kr_exit_check(kd, tol, qoff, s));
-      CK(launch_spmv(h->band, N, h->L.K, x, tmp, tr, s, gC));
-      CK(kr_residual(b, tmp, t, N, kc, S_TN2, s));
-      CK(kr_exit_decide(kd, tol, qoff, s));
-      return h->impl->apply(t, r[0], tr, s, gR);    // residual replacement, when flagged
-    };
-    auto iteration = [&]() -> sap_status_t {
-      for (int j = 0; j < 2; ++j) {
-        CK(kr_bicg_rho(r[j], rt, N, ka, j, s));
-        CK(kr_bicg_u(u[0], u[1], r[0], r[1], N, ka, j, s));
-        CK(launch_spmv(h->band, N, h->L.K, u[j], tmp, tr, s, gA));
-        TRY(h->impl->apply(tmp, u[j + 1], tr, s, gA));
-        CK(kr_bicg_gamma(u[j + 1], rt, N, ka, s));
-        CK(kr_bicg_r(r[0], r[1], u[0], u[1], u[2], x, N, ka, j, s));
-        TRY(exit_test(j == 0 ? 0.25 : 0.75));
-        CK(launch_spmv(h->band, N, h->L.K, r[j], tmp, tr, s, gA));
-        TRY(h->impl->apply(tmp, r[j + 1], tr, s, gA));
-      }
-      CK(kr_mr(x, r[0], r[1], r[2], u[0], u[1], u[2], N, ka, s));
-      return exit_test(1.0);
-    };
-    // capture the iteration once per direction; on any capture failure the
-    // iteration is launched directly instead
-    const int gi = tr ? 1 : 0;
-    if (!h->gexec[gi] && !h->gfailed[gi]) {
-      const long long l0 = launches_so_far();
-      cudaGraph_t graph = nullptr;
-      bool ok = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
-      const sap_status_t cst = ok ? iteration() : SAP_ERR_CUDA;
-      if (ok) ok = cudaStreamEndCapture(s, &graph) == cudaSuccess && cst == SAP_OK;
-      if (ok) ok = cudaGraphInstantiate(&h->gexec[gi], graph, 0) == cudaSuccess;
-      if (graph) cudaGraphDestroy(graph);
-      if (!ok) {
-        if (h->gexec[gi]) cudaGraphExecDestroy(h->gexec[gi]);
-        h->gexec[gi] = nullptr;
-        h->gfailed[gi] = true;
-        cudaGetLastError();
-      }
-      h->glaunches[gi] = launches_so_far() - l0;
-      count_launches(-(int)h->glaunches[gi]);     // captured, not run
-    }
-    bool done = false;
-    for (int it = 0; it < h->opt.max_iters && !done; ++it) {
-      if (h->gexec[gi]) {
-        CK(cudaGraphLaunch(h->gexec[gi], s));
-        count_launches((int)h->glaunches[gi]);
-      } else {
-        TRY(iteration());
-      }
-      CK(cudaMemcpyAsync(h->host_f, h->flags, F_COUNT * sizeof(int), cudaMemcpyDeviceToHost, s));
-      CK(cudaStreamSynchronize(s));
-      done = h->host_f[F_DONE] != 0;
-    }
-    CK(cudaMemcpyAsync(h->host_s, kd.S, S_COUNT * sizeof(double), cudaMemcpyDeviceToHost, s));
-    CK(cudaMemcpyAsync(h->host_f, h->flags, F_COUNT * sizeof(int), cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
-    inf.n_restarts = h->host_f[F_RESTARTS];
-    if (done) {
-      status = (sap_status_t)h->host_f[F_STATUS];
-      inf.iters = h->host_s[S_QUART];
-      inf.relres = h->host_s[S_RELRES];
-    } else {
-      inf.iters = h->opt.max_iters;
-    }
-    if (status != SAP_OK) {
-      CK(launch_spmv(h->band, N, h->L.K, x, tmp, tr, s));
-      CK(kr_residual(b, tmp, t, N, kd, S_TN2, s));
-      CK(cudaMemcpyAsync(h->host_s, kd.S + S_RN2, 5 * sizeof(double), cudaMemcpyDeviceToHost, s));
-      CK(cudaStreamSynchronize(s));
-      inf.relres = std::sqrt(h->host_s[S_TN2 - S_RN2]) / bn;
-    }
-  }
-  CK(cudaMemcpyAsync(x_user, x, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
-  CK(cudaEventRecord(h->ev1, s));
-  CK(cudaEventSynchronize(h->ev1));
-  if (h->impl->take_device_error(s) != SAP_OK) status = SAP_ERR_TIMEOUT;
-  float ms = 0.f;
-  cudaEventElapsedTime(&ms, h->ev0, h->ev1);
-  inf.n_matvec = (int64_t)std::llround(4.0 * inf.iters);
-  inf.t_solve_ms = ms;
-  inf.t_factor_ms = h->t_factor_ms;
-  inf.t_lu_ms = h->t_lu_ms;
-  inf.t_ul_ms = h->t_ul_ms;
-  inf.t_spk_ms = h->t_spk_ms;
-  inf.segments = h->L.S;
-  inf.graphed = (h->gexec[tr ? 1 : 0] != nullptr) ? 1 : 0;
-  unsigned long long nb = 0;
-  CK(cudaMemcpy(&nb, h->n_boosted, sizeof(nb), cudaMemcpyDeviceToHost));
-  inf.n_boosted = (int64_t)nb;
-  if (info) *info = inf;
-  return status;
-}
-
-sap_status_t run_factor(sap_handle* h, cudaStream_t s) {
+// Factorisation in two steps (a batch launches all systems before waiting):
+// launch_factor queues the factor phases on s, finish_factor waits for them,
+// reads the phase times and the singular flag.
+sap_status_t launch_factor(sap_handle* h, cudaStream_t s) {
   CK(cudaMemsetAsync(h->n_boosted, 0, sizeof(unsigned long long), s));
   CK(cudaMemsetAsync(h->singular, 0, sizeof(int), s));
-  TRY(h->impl->factor(s));
+  return h->impl->factor(s);
+}
+
+sap_status_t finish_factor(sap_handle* h) {
   CK(cudaEventSynchronize(h->evp[3]));
   CK(cudaGetLastError());
   cudaEventElapsedTime(&h->t_lu_ms, h->evp[0], h->evp[1]);
@@ -532,36 +593,14 @@ sap_status_t run_factor(sap_handle* h, cudaStream_t s) {
   return SAP_OK;
 }
 
-}  // namespace
-
-extern "C" {
-
-void sap_default_options(sap_options_t* o) {
-  if (!o) return;
-  o->P = 1;
-  o->variant = SAP_D;
-  o->precision = SAP_FP64;
-  o->max_iters = 500;
-  o->tol = 1e-10;
-  o->boost_eps = 0.0;
-  o->spin_limit = 0;
-  o->segments = 0;
-  o->reserved0 = 0;
+sap_status_t run_factor(sap_handle* h, cudaStream_t s) {
+  TRY(launch_factor(h, s));
+  return finish_factor(h);
 }
 
-int64_t sap_kernel_launches(void) { return (int64_t)sap::g_launches.load(); }
-
-int32_t sap_max_K(int32_t precision) {
-  const bool fp64 = precision == SAP_FP64;
-  int K = kMaxK;
-  while (K > 1 && (sweep_smem_bytes(K, fp64) > kSmemPerBlock || lu_smem_bytes(K, fp64) > kSmemPerBlock)) --K;
-  return K;
-}
-
-sap_status_t sap_factor(const double* band_dev, int64_t N, int32_t K, const sap_options_t* opt_in,
-                        cudaStream_t s, sap_handle_t* out) {
-  if (!out) return SAP_ERR_INVALID_ARG;
-  *out = nullptr;
+// A handle with its layout and device memory, not yet factored.
+sap_status_t create_handle(const double* band_dev, int64_t N, int32_t K, const sap_options_t* opt_in,
+                           cudaStream_t s, std::unique_ptr<sap_handle>& out) {
   if (!band_dev) return SAP_ERR_INVALID_ARG;
   TRY(check_options(opt_in, N, K));
   sap_options_t opt = *opt_in;
@@ -570,8 +609,9 @@ sap_status_t sap_factor(const double* band_dev, int64_t N, int32_t K, const sap_
   if (!(opt.boost_eps > 0.0)) opt.boost_eps = opt.precision == SAP_FP64 ? 0x1p-53 : 0x1p-24;
   if (K > sap_max_K(opt.precision)) return SAP_ERR_NOT_IMPLEMENTED;
   if (opt.variant == SAP_C && opt.P > 1 && K > max_K_spikes(opt.precision)) return SAP_ERR_NOT_IMPLEMENTED;
-  std::unique_ptr<sap_handle> h(new (std::nothrow) sap_handle());
-  if (!h) return SAP_ERR_OOM;
+  out.reset(new (std::nothrow) sap_handle());
+  if (!out) return SAP_ERR_OOM;
+  sap_handle* h = out.get();
   h->opt = opt;
   h->band = band_dev;
   Layout& L = h->L;
@@ -654,9 +694,127 @@ sap_status_t sap_factor(const double* band_dev, int64_t N, int32_t K, const sap_
   CK(cudaEventCreate(&h->ev0));
   CK(cudaEventCreate(&h->ev1));
   for (auto& e : h->evp) CK(cudaEventCreate(&e));
-  if (opt.precision == SAP_FP64) h->impl.reset(new Solver<double>(h.get()));
-  else h->impl.reset(new Solver<float>(h.get()));
+  if (opt.precision == SAP_FP64) h->impl.reset(new Solver<double>(h));
+  else h->impl.reset(new Solver<float>(h));
   TRY(h->impl->alloc());
+  return SAP_OK;
+}
+
+}  // namespace
+
+struct sap_batch {
+  std::vector<sap_handle*> hs;
+  ~sap_batch() {
+    for (sap_handle* h : hs) delete h;
+  }
+};
+
+namespace {
+
+// Partition count of system i of a batch (opt.P == 0): about two blocks per
+// SM over the whole batch, in proportion to N_i; SaP-C keeps N_i / P >= 2 K_i.
+int batch_partitions(int64_t N, int K, int64_t total_rows, int variant) {
+  const double share = (double)N / (double)total_rows;
+  int64_t P = (int64_t)std::llround(2.0 * 152.0 * share);
+  if (P < 1) P = 1;
+  const int64_t pmax = variant == SAP_C ? std::max<int64_t>(1, N / (2 * (int64_t)K)) : std::max<int64_t>(1, N / 64);
+  return (int)std::min(P, pmax);
+}
+
+// Factor every system on its own internal stream, ordered after s; wait for
+// all; s is ordered after them.
+sap_status_t factor_batch(sap_batch* B, cudaStream_t s) {
+  cudaEvent_t fork = nullptr;
+  CK(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+  std::unique_ptr<CUevent_st, cudaError_t (*)(cudaEvent_t)> guard(fork, cudaEventDestroy);
+  CK(cudaEventRecord(fork, s));
+  for (sap_handle* h : B->hs) {
+    TRY(ensure_stream(h));
+    CK(cudaStreamWaitEvent(h->ks, fork, 0));
+    TRY(launch_factor(h, h->ks));
+  }
+  sap_status_t st = SAP_OK;
+  for (sap_handle* h : B->hs) {
+    const sap_status_t e = finish_factor(h);
+    if (st == SAP_OK) st = e;
+    CK(cudaEventRecord(h->evj, h->ks));
+    CK(cudaStreamWaitEvent(s, h->evj, 0));
+  }
+  return st;
+}
+
+// All systems' solves in lockstep rounds of one outer iteration each.
+sap_status_t solve_batch(sap_batch* B, const double* const* b, double* const* x, bool tr, sap_info_t* infos,
+                         int32_t* statuses, cudaStream_t s) {
+  const size_t n = B->hs.size();
+  std::vector<KrylovRun> k(n);
+  for (size_t i = 0; i < n; ++i) {
+    if (!b[i] || !x[i] || b[i] == x[i]) return SAP_ERR_INVALID_ARG;
+    TRY(k[i].init(B->hs[i], b[i], x[i], tr, s));
+  }
+  for (size_t i = 0; i < n; ++i) TRY(k[i].begin());
+  for (size_t i = 0; i < n; ++i) {
+    CK(cudaStreamSynchronize(k[i].s));
+    k[i].after_begin();
+  }
+  std::vector<char> ran(n);
+  for (;;) {
+    bool any = false;
+    for (size_t i = 0; i < n; ++i) {
+      ran[i] = k[i].active();
+      if (ran[i]) {
+        TRY(k[i].round());
+        any = true;
+      }
+    }
+    if (!any) break;
+    for (size_t i = 0; i < n; ++i)
+      if (ran[i]) {
+        CK(cudaStreamSynchronize(k[i].s));
+        k[i].after_round();
+      }
+  }
+  sap_status_t st = SAP_OK;
+  for (size_t i = 0; i < n; ++i) {
+    const sap_status_t e = k[i].finish(infos ? &infos[i] : nullptr);
+    if (statuses) statuses[i] = e;
+    if (st == SAP_OK) st = e;
+  }
+  return st;
+}
+
+}  // namespace
+
+extern "C" {
+
+void sap_default_options(sap_options_t* o) {
+  if (!o) return;
+  o->P = 1;
+  o->variant = SAP_D;
+  o->precision = SAP_FP64;
+  o->max_iters = 500;
+  o->tol = 1e-10;
+  o->boost_eps = 0.0;
+  o->spin_limit = 0;
+  o->segments = 0;
+  o->reserved0 = 0;
+}
+
+int64_t sap_kernel_launches(void) { return (int64_t)sap::g_launches.load(); }
+
+int32_t sap_max_K(int32_t precision) {
+  const bool fp64 = precision == SAP_FP64;
+  int K = kMaxK;
+  while (K > 1 && (sweep_smem_bytes(K, fp64) > kSmemPerBlock || lu_smem_bytes(K, fp64) > kSmemPerBlock)) --K;
+  return K;
+}
+
+sap_status_t sap_factor(const double* band_dev, int64_t N, int32_t K, const sap_options_t* opt_in,
+                        cudaStream_t s, sap_handle_t* out) {
+  if (!out) return SAP_ERR_INVALID_ARG;
+  *out = nullptr;
+  std::unique_ptr<sap_handle> h;
+  TRY(create_handle(band_dev, N, K, opt_in, s, h));
   TRY(run_factor(h.get(), s));
   *out = h.release();
   return SAP_OK;
@@ -754,6 +912,69 @@ const char* sap_status_string(sap_status_t s) {
     case SAP_ERR_SINGULAR: return "singular reduced matrix";
   }
   return "unknown status";
+}
+
+sap_status_t sap_factor_batched(int32_t n, const double* const* bands, const int64_t* N, const int32_t* K,
+                                const sap_options_t* opt, cudaStream_t s, sap_batch_t* out) {
+  if (!out) return SAP_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (n < 1 || !bands || !N || !K || !opt) return SAP_ERR_INVALID_ARG;
+  int64_t total = 0;
+  for (int32_t i = 0; i < n; ++i) {
+    if (!bands[i] || N[i] < 2 || K[i] < 1 || K[i] >= N[i]) return SAP_ERR_INVALID_ARG;
+    total += N[i];
+  }
+  std::unique_ptr<sap_batch> B(new (std::nothrow) sap_batch());
+  if (!B) return SAP_ERR_OOM;
+  for (int32_t i = 0; i < n; ++i) {
+    sap_options_t o = *opt;
+    if (o.P == 0) o.P = batch_partitions(N[i], K[i], total, o.variant);
+    if (o.segments == 0) o.segments = 1;
+    std::unique_ptr<sap_handle> h;
+    TRY(create_handle(bands[i], N[i], K[i], &o, s, h));
+    B->hs.push_back(h.release());
+  }
+  TRY(factor_batch(B.get(), s));
+  *out = B.release();
+  return SAP_OK;
+}
+
+sap_status_t sap_refactor_batched(sap_batch_t b, cudaStream_t s) {
+  if (!b) return SAP_ERR_INVALID_ARG;
+  return factor_batch(b, s);
+}
+
+sap_status_t sap_solve_batched(sap_batch_t b, const double* const* bv, double* const* xv, sap_info_t* infos,
+                               int32_t* statuses, cudaStream_t s) {
+  if (!b || !bv || !xv) return SAP_ERR_INVALID_ARG;
+  return solve_batch(b, bv, xv, false, infos, statuses, s);
+}
+
+sap_status_t sap_solve_adjoint_batched(sap_batch_t b, const double* const* gv, double* const* lv,
+                                       sap_info_t* infos, int32_t* statuses, cudaStream_t s) {
+  if (!b || !gv || !lv) return SAP_ERR_INVALID_ARG;
+  return solve_batch(b, gv, lv, true, infos, statuses, s);
+}
+
+sap_status_t sap_grad_band_batched(sap_batch_t b, const double* const* lam, const double* const* x,
+                                   double* const* g, cudaStream_t s) {
+  if (!b || !lam || !x || !g) return SAP_ERR_INVALID_ARG;
+  for (size_t i = 0; i < b->hs.size(); ++i) TRY(sap_grad_band(b->hs[i], lam[i], x[i], g[i], s));
+  return SAP_OK;
+}
+
+int32_t sap_batch_size(sap_batch_t b) { return b ? (int32_t)b->hs.size() : 0; }
+
+int32_t sap_batch_partitions(sap_batch_t b, int32_t i) {
+  if (!b || i < 0 || i >= (int32_t)b->hs.size()) return -1;
+  return b->hs[i]->L.P;
+}
+
+sap_status_t sap_batch_destroy(sap_batch_t b) {
+  if (!b) return SAP_ERR_INVALID_ARG;
+  cudaDeviceSynchronize();
+  delete b;
+  return SAP_OK;
 }
 
 }  // extern "C"

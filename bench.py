@@ -44,7 +44,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="n200k_k50", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="n200k_k50", choices=sorted(WORKLOADS) + ["batch64"],
+                    help="batch64: 64 systems N ~ U{1e4..1e5}, K ~ U{8..64} through the batched API")
     ap.add_argument("--variant", default="D", choices=["C", "D"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-compare", action="store_true", help="skip the FP64 / other-variant comparison runs")
@@ -96,9 +97,57 @@ def cpu_baseline(w, variant, band, b, g, reps=1):
                       f"(single-threaded FP64 C oracle, SaP-{variant})"}
 
 
+def run_reference_batch(args):
+    """Oracle arm of the 64-system batch: each step runs the FP64 oracle (factor,
+    solve, adjoint solve) on the three smallest systems and scales the time by
+    rows to the whole batch (a bounded sample)."""
+    import numpy as np
+    import oracle as O
+    import sap_inputs as G
+    specs = G.batch_specs(64)
+    Ns = [n for n, _, _ in specs]
+    idx = list(np.argsort(Ns)[:3])
+    total = sum(Ns)
+    rows = sum(Ns[i] for i in idx)
+    sample = []
+    for i in idx:
+        n, k, sd = specs[i]
+        band = G.dense_banded(n, k, 1.0, sd)
+        P = max(1, round(2 * 152 * n / total))
+        sample.append((band, n, k, O.spmv(band, n, k, G.x_true(n, sd)), G.adjoint_seed(n, sd), P))
+
+    def step():
+        for band, n, k, b, g, P in sample:
+            O.solve(band, n, k, b, P, O.SAP_D)
+            O.solve_adjoint(band, n, k, g, P, O.SAP_D)
+
+    for _ in range(args.warmup):
+        step()
+    ts = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        step()
+        ts.append((time.perf_counter() - t0) * 1e3 * total / rows)
+    v = statistics.mean(ts)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "ms", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": v, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "batch of 64 dense banded systems, N ~ U{10000..100000}, K ~ U{8..64}, d=1.0, "
+                                   "SaP-D, FP32 preconditioner + FP64 BiCGStab(2), fwd + adjoint to relres 1e-10",
+                       "systems": 64, "rows": int(total)},
+            "cpu_baseline": {"value": v, "unit": "ms", "cores": 1, "kind": "oracle",
+                             "sample": f"each step: the 3 smallest systems ({rows} rows), factor + solve + adjoint "
+                                       f"solve, scaled by rows to {total}"},
+            "e2e": {"value": v, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
+        return
+    if args.workload == "batch64":
+        run_reference_batch(args)
         return
     w = WORKLOADS[args.workload]
     import oracle as O
@@ -381,10 +430,141 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
+def run_gpu_batch(args):
+    """The 64-system batch (uneven N and K, d = 1), FP32 preconditioner + FP64
+    BiCGStab(2): a step is one batched refactor, forward solve and adjoint
+    solve of all systems; value = ms per step."""
+    import numpy as np
+    import torch
+    import paper_1509_07919_gb300 as S
+    import sap_inputs as G
+    import oracle as O
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    specs = G.batch_specs(64)
+    Ns = [n for n, _, _ in specs]
+    Ks = [k for _, k, _ in specs]
+    bands_np = [G.dense_banded(n, k, 1.0, sd) for n, k, sd in specs]
+    bands = [torch.from_numpy(b).cuda() for b in bands_np]
+    xts = [torch.from_numpy(G.x_true(n, sd)).cuda() for n, _, sd in specs]
+    gs = [torch.from_numpy(G.adjoint_seed(n, sd)).cuda() for n, _, sd in specs]
+    bs = [S.sap_spmv(bd, n, k, xt) for bd, n, k, xt in zip(bands, Ns, Ks, xts)]
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    bh = S.sap_factor_batched(bands, Ns, Ks, precision=S.SAP_FP32, variant=S.SAP_D)
+    xs = [torch.empty_like(b) for b in bs]
+    ls = [torch.empty_like(b) for b in bs]
+
+    def step():
+        S.sap_refactor_batched(bh)
+        _, i1, _, _ = S.sap_solve_batched(bh, bs, xs)
+        _, i2, _, _ = S.sap_solve_adjoint_batched(bh, gs, ls)
+        return i1, i2
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ck = Clocks(local)
+    l0 = S.sap_kernel_launches()
+    times = []
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        i1, i2 = step()
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    launches = S.sap_kernel_launches() - l0
+    clocks = ck.stop()
+    ms = statistics.mean(times)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    err = max(float(torch.linalg.norm(x - xt) / torch.linalg.norm(xt)) for x, xt in zip(xs, xts))
+    # end to end: bands, rhs and adjoint seeds from pinned host memory, results back
+    hb = [torch.from_numpy(b).pin_memory() for b in bands_np]
+    hr = [b.cpu().pin_memory() for b in bs]
+    hg = [g.cpu().pin_memory() for g in gs]
+    hx = [torch.empty_like(b).pin_memory() for b in hr]
+    hl = [torch.empty_like(b).pin_memory() for b in hr]
+    dr = [torch.empty_like(b) for b in bs]
+    dg = [torch.empty_like(b) for b in bs]
+    e2e = []
+    for k in range(args.warmup + args.steps):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for a, b_ in zip(bands, hb):
+            a.copy_(b_, non_blocking=True)
+        for a, b_ in zip(dr, hr):
+            a.copy_(b_, non_blocking=True)
+        for a, b_ in zip(dg, hg):
+            a.copy_(b_, non_blocking=True)
+        S.sap_refactor_batched(bh)
+        S.sap_solve_batched(bh, dr, xs)
+        S.sap_solve_adjoint_batched(bh, dg, ls)
+        for a, b_ in zip(hx, xs):
+            a.copy_(b_, non_blocking=True)
+        for a, b_ in zip(hl, ls):
+            a.copy_(b_, non_blocking=True)
+        torch.cuda.synchronize()
+        if k >= args.warmup:
+            e2e.append((time.perf_counter() - t0) * 1e3)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        # oracle on the three smallest systems (bounded sample), scaled by rows
+        idx = list(np.argsort(Ns)[:3])
+        t0 = time.perf_counter()
+        for i in idx:
+            bnp = bs[i].cpu().numpy()
+            O.solve(bands_np[i], Ns[i], Ks[i], bnp, S.sap_batch_partitions(bh)[i], O.SAP_D)
+            O.solve_adjoint(bands_np[i], Ns[i], Ks[i], gs[i].cpu().numpy(), S.sap_batch_partitions(bh)[i],
+                            O.SAP_D)
+        dt = (time.perf_counter() - t0) * 1e3
+        rows = sum(Ns[i] for i in idx)
+        cpu = {"value": dt * sum(Ns) / rows, "unit": "ms", "cores": 1, "kind": "oracle",
+               "sample": f"3 smallest systems ({rows} rows) timed, scaled by rows to the batch's {sum(Ns)}"}
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": ms / world, "unit": "ms", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": "batch of 64 dense banded systems, N ~ U{10000..100000}, K ~ U{8..64}, d=1.0, "
+                                   "SaP-D, FP32 preconditioner + FP64 BiCGStab(2), fwd + adjoint to relres 1e-10",
+                       "systems": 64, "rows": int(sum(Ns)), "partitions": S.sap_batch_partitions(bh),
+                       "l2": "flushed (512 MB write) before every timed step"},
+            "clocks": clocks,
+            "e2e": {"value": statistics.mean(e2e), "unit": "ms",
+                    "h2d_bytes_per_step": int(sum(b.numel() for b in hb) * 8 + 2 * sum(r.numel() for r in hr) * 8),
+                    "d2h_bytes_per_step": int(2 * sum(x.numel() for x in hx) * 8)},
+            "gpu_launches": int(launches),
+            "roofline": None,
+            "cpu_baseline": cpu,
+            "detail": {"max_err_x_vs_x_true": err,
+                       "iters_fwd_max": max(i.iters for i in i1), "iters_adj_max": max(i.iters for i in i2),
+                       "relres_fwd_max": max(i.relres for i in i1), "relres_adj_max": max(i.relres for i in i2),
+                       "graphed": all(i.graphed for i in i1)},
+        }
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batch64":
+        run_gpu_batch(args)
     else:
         run_gpu(args)
 

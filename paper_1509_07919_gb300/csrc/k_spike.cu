@@ -72,7 +72,7 @@ k_spikes(const double* __restrict__ band, int64_t N, int K, Dev d, const T* __re
   double* R = reinterpret_cast<double*>(smem_raw);            // K x K FP64
   T* Mx = reinterpret_cast<T*>(R + KK);                        // K x K factor tile
   T* X = Mx + KK;                                              // K x K right-hand sides / tips
-  __shared__ int pivs[kMaxK + 1];
+  __shared__ int pivs[128];          // K <= 120 for the spike kernel (its shared-memory limit)
   __shared__ double red_v[NT / 32];
   __shared__ int red_i[NT / 32];
 

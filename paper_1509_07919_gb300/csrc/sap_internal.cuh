@@ -7,9 +7,10 @@
 
 namespace sap {
 
-// Largest half-bandwidth handled by the register-window factor kernel:
-// a 16 x 16 thread grid with up to 8 x 8 window slots per thread.
-constexpr int kMaxK = 127;
+// Upper bound of the half-bandwidth searched by sap_max_K; the limit in force
+// is the largest K whose factor window and sweep ring fit in shared memory
+// (208 for FP32, 128 for FP64 factors).
+constexpr int kMaxK = 255;
 constexpr size_t kSmemPerBlock = 232448;   // opt-in shared memory per CTA on sm_103
 
 // Dynamic shared memory of the sweep and factor kernels for half-bandwidth K.

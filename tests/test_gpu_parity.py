@@ -80,7 +80,8 @@ def test_block_lu_parity_fp64(sap, N, K, P):
     assert sap.sap_n_boosted(h) == 0 == o.n_boosted
 
 
-@pytest.mark.parametrize("N,K,P", [(4003, 50, 4), (2000, 10, 8), (700, 100, 3), (1000, 127, 3)])
+@pytest.mark.parametrize("N,K,P", [(4003, 50, 4), (2000, 10, 8), (700, 100, 3), (1000, 127, 3), (1300, 200, 2),
+                                   (900, 208, 2)])
 def test_block_lu_parity_fp32(sap, N, K, P):
     band, _, _ = make(N, K, 1.0, 300 + K)
     h = sap.sap_factor(dev(band), N, K, P=P, variant=sap.SAP_D, precision=sap.SAP_FP32)
@@ -243,8 +244,17 @@ def test_invalid_arguments(sap):
         sap.sap_factor(band, N, N, P=1)                            # K >= N
     with pytest.raises(sap.SapError):
         sap.sap_factor(band, N, K, P=0)
+    # above the shared-memory limits of the factor window / sweep ring
+    assert sap.sap_max_K(sap.SAP_FP64) == 128 and sap.sap_max_K(sap.SAP_FP32) == 208
     with pytest.raises(sap.SapError) as e:
-        sap.sap_factor(dev(G.dense_banded(400, 150, 1.0, 1)), 400, 150, P=1)
+        sap.sap_factor(dev(G.dense_banded(600, 150, 1.0, 1)), 600, 150, P=1, precision=sap.SAP_FP64)
+    assert e.value.status == sap.SAP_ERR_NOT_IMPLEMENTED
+    with pytest.raises(sap.SapError) as e:
+        sap.sap_factor(dev(G.dense_banded(600, 209, 1.0, 1)), 600, 209, P=1, precision=sap.SAP_FP32)
+    assert e.value.status == sap.SAP_ERR_NOT_IMPLEMENTED
+    with pytest.raises(sap.SapError) as e:          # SaP-C spike tips: K <= 120 in FP32
+        sap.sap_factor(dev(G.dense_banded(2000, 150, 1.0, 1)), 2000, 150, P=4, variant=sap.SAP_C,
+                       precision=sap.SAP_FP32)
     assert e.value.status == sap.SAP_ERR_NOT_IMPLEMENTED
 
 
@@ -282,6 +292,22 @@ def test_not_converged_status(sap):
     assert st in (sap.SAP_ERR_NOT_CONVERGED, sap.SAP_OK)
     if st == sap.SAP_ERR_NOT_CONVERGED:
         assert info.relres > 1e-10
+
+
+@pytest.mark.parametrize("N,K,P,prec", [(20000, 200, 10, 1), (12000, 128, 6, 0), (9000, 170, 5, 1)])
+def test_wide_band_solve_parity(sap, N, K, P, prec):
+    """Wide bands (K > 127, SaP-D; C3's K = 200): 4 + couplings per chunk,
+    unsegmented sweeps; FP32 up to K = 208, FP64 up to K = 128."""
+    band, xt, b = make(N, K, 1.0, 900 + K)
+    xo, io, _ = O.solve(band, N, K, b, P, O.SAP_D)
+    h = sap.sap_factor(dev(band), N, K, P=P, precision=prec)
+    x, info, st = sap.sap_solve(h, dev(b))
+    assert st == sap.SAP_OK and info.relres <= 1e-10
+    assert relerr(host(x), xo) <= 1e-8
+    g = G.adjoint_seed(N, 900 + K)
+    lo, _, _ = O.solve_adjoint(band, N, K, g, P, O.SAP_D)
+    lam, ainfo, ast = sap.sap_solve_adjoint(h, dev(g))
+    assert ast == sap.SAP_OK and relerr(host(lam), lo) <= 1e-8
 
 
 # ------------------------------------------------ full-size configuration --

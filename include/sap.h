@@ -207,6 +207,29 @@ SAP_API sap_status_t sap_band_solve_noalloc(const double *band_dev, int64_t N, i
                                            const double *b_dev, double *x_dev, int32_t precision,
                                            cudaStream_t stream);
 
+/* ---- Autotuner ----
+ * Not in the paper (a GB300 addition): picks the partition count P and the
+ * sweep segment count for one matrix by measurement.  Every candidate
+ * (P_cands[i], seg_cands[j]) is factored and solved (refactor + solve timed
+ * with CUDA events on `stream`, best of two) and the fastest is returned.
+ *   opt: the other options (variant, precision, tol, ...); opt->P and
+ *        opt->segments are ignored.
+ *   P_cands, nP: candidate partition counts; nP == 0 uses N / {16000, 8000,
+ *        4000, 2000, 1000} rounded, clipped to [1, N/64] (SaP-D) or
+ *        [1, N/(2K)] (SaP-C), duplicates removed.
+ *   seg_cands, nS: candidate segment counts; nS == 0 uses {0} (automatic).
+ *   b_dev: right-hand side for the timing (N doubles on the device), or NULL
+ *        for b = A * ones.
+ *   ms_out (optional, nP' x nS entries in candidate order, nP' = the number of
+ *        P candidates actually used, at most 16): measured ms, -1 for a
+ *        candidate that failed; n_out (optional) receives nP'.
+ * Errors: INVALID_ARG, or the status of the last candidate when all fail.
+ * Synchronises; allocates and frees one handle per candidate. */
+SAP_API sap_status_t sap_autotune(const double *band_dev, int64_t N, int32_t K, const sap_options_t *opt,
+                                  const int32_t *P_cands, int32_t nP, const int32_t *seg_cands, int32_t nS,
+                                  const double *b_dev, cudaStream_t stream, int32_t *best_P,
+                                  int32_t *best_segments, float *ms_out, int32_t *n_out);
+
 /* ---- Batches of independent banded systems ----
  * Not in the paper (a GB300 addition): n systems of their own N_i and K_i,
  * each with its own SaP preconditioner, factored and solved together.  Every

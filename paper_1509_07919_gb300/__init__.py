@@ -74,6 +74,8 @@ def _load():
         "sap_kernel_launches": (i64, []),
         "sap_band_solve_noalloc": (C.c_int, [vp, i64, i32, vp, vp, i32, vp]),
         "sap_factor_batched": (C.c_int, [i32, vp, vp, vp, P(sap_options_t), vp, P(vp)]),
+        "sap_autotune": (C.c_int, [vp, i64, i32, P(sap_options_t), vp, i32, vp, i32, vp, vp,
+                                   P(C.c_int32), P(C.c_int32), vp, P(C.c_int32)]),
         "sap_refactor_batched": (C.c_int, [vp, vp]),
         "sap_solve_batched": (C.c_int, [vp, vp, vp, vp, vp, vp]),
         "sap_solve_adjoint_batched": (C.c_int, [vp, vp, vp, vp, vp, vp]),
@@ -236,6 +238,38 @@ def sap_band_solve_noalloc(band: torch.Tensor, N: int, K: int, b: torch.Tensor, 
     _check(_lib.sap_band_solve_noalloc(_ptr(band), N, K, _ptr(b), _ptr(x), precision, _stream(stream)),
            "sap_band_solve_noalloc")
     return x
+
+
+def sap_autotune(band: torch.Tensor, N: int, K: int, P_cands=None, seg_cands=None, b: torch.Tensor | None = None,
+                 stream=None, **kw):
+    """Measured choice of (P, segments); returns (P, segments, {(P, S): ms})."""
+    opts = sap_default_options(**kw)
+    Pc = list(P_cands or [])
+    Sc = list(seg_cands or [])
+    PA = (C.c_int32 * max(1, len(Pc)))(*Pc) if Pc else None
+    SA = (C.c_int32 * max(1, len(Sc)))(*Sc) if Sc else None
+    ms = (C.c_float * (16 * max(1, len(Sc))))()
+    bp, bs_, nused = C.c_int32(), C.c_int32(), C.c_int32()
+    st = _lib.sap_autotune(_ptr(band), N, K, C.byref(opts), PA, len(Pc), SA, len(Sc),
+                           _ptr(b) if b is not None else None, _stream(stream), C.byref(bp), C.byref(bs_),
+                           ms, C.byref(nused))
+    _check(st, "sap_autotune")
+    table = {}
+    Slist = Sc or [0]
+    # candidate P values in the library's order are not returned; rebuild them as it does
+    if Pc:
+        Plist = [p for p in Pc if 1 <= p <= N][:16]
+    else:
+        pmax = max(1, N // (2 * K)) if opts.variant == SAP_C else max(1, N // 64)
+        Plist = []
+        for rows in (16000, 8000, 4000, 2000, 1000):
+            p = max(1, min(pmax, (N + rows // 2) // rows))
+            if p not in Plist:
+                Plist.append(p)
+    for i, p in enumerate(Plist[:nused.value]):
+        for j, sg in enumerate(Slist):
+            table[(p, sg)] = float(ms[i * len(Slist) + j])
+    return bp.value, bs_.value, table
 
 
 class BatchHandle:

@@ -914,6 +914,87 @@ const char* sap_status_string(sap_status_t s) {
   return "unknown status";
 }
 
+sap_status_t sap_autotune(const double* band, int64_t N, int32_t K, const sap_options_t* opt_in,
+                          const int32_t* P_cands, int32_t nP, const int32_t* seg_cands, int32_t nS,
+                          const double* b_dev, cudaStream_t s, int32_t* best_P, int32_t* best_segments,
+                          float* ms_out, int32_t* n_out) {
+  if (!band || !opt_in || !best_P || !best_segments || N < 2 || K < 1 || K >= N) return SAP_ERR_INVALID_ARG;
+  if (nP < 0 || nS < 0 || (nP > 0 && !P_cands) || (nS > 0 && !seg_cands)) return SAP_ERR_INVALID_ARG;
+  const int64_t pmax = opt_in->variant == SAP_C ? std::max<int64_t>(1, N / (2 * (int64_t)K))
+                                                : std::max<int64_t>(1, N / 64);
+  std::vector<int32_t> Ps;
+  if (nP > 0) {
+    for (int32_t i = 0; i < nP && Ps.size() < 16; ++i)
+      if (P_cands[i] >= 1 && P_cands[i] <= N) Ps.push_back(P_cands[i]);
+  } else {
+    for (int64_t rows : {16000, 8000, 4000, 2000, 1000}) {
+      int64_t P = std::max<int64_t>(1, std::min<int64_t>(pmax, (N + rows / 2) / rows));
+      if (std::find(Ps.begin(), Ps.end(), (int32_t)P) == Ps.end()) Ps.push_back((int32_t)P);
+    }
+  }
+  if (Ps.empty()) return SAP_ERR_INVALID_ARG;
+  std::vector<int32_t> Ss;
+  if (nS > 0) Ss.assign(seg_cands, seg_cands + nS);
+  else Ss.push_back(0);
+  if (n_out) *n_out = (int32_t)Ps.size();
+  // right-hand side and solution buffers
+  double* buf = nullptr;
+  if (cudaMalloc(&buf, 3 * (size_t)N * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    return SAP_ERR_OOM;
+  }
+  std::unique_ptr<double, cudaError_t (*)(void*)> guard(buf, cudaFree);
+  double* ones = buf;
+  double* bb = buf + N;
+  double* xx = buf + 2 * N;
+  if (!b_dev) {
+    std::vector<double> h1((size_t)N, 1.0);
+    CK(cudaMemcpyAsync(ones, h1.data(), (size_t)N * sizeof(double), cudaMemcpyHostToDevice, s));
+    CK(launch_spmv(band, N, K, ones, bb, false, s));
+    CK(cudaStreamSynchronize(s));
+    b_dev = bb;
+  }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  float best = -1.f;
+  sap_status_t last = SAP_ERR_INVALID_ARG;
+  for (size_t i = 0; i < Ps.size(); ++i)
+    for (size_t j = 0; j < Ss.size(); ++j) {
+      sap_options_t o = *opt_in;
+      o.P = Ps[i];
+      o.segments = Ss[j];
+      float ms = -1.f;
+      sap_handle_t h = nullptr;
+      sap_status_t st = sap_factor(band, N, K, &o, s, &h);
+      if (st == SAP_OK) st = sap_solve(h, b_dev, xx, nullptr, s);       // warm-up, captures the graph
+      for (int rep = 0; rep < 2 && st == SAP_OK; ++rep) {
+        cudaEventRecord(e0, s);
+        st = sap_refactor(h, s);
+        if (st == SAP_OK) st = sap_solve(h, b_dev, xx, nullptr, s);
+        cudaEventRecord(e1, s);
+        cudaEventSynchronize(e1);
+        float t = 0.f;
+        cudaEventElapsedTime(&t, e0, e1);
+        if (st == SAP_OK && (ms < 0.f || t < ms)) ms = t;
+      }
+      if (h) sap_destroy(h);
+      if (st != SAP_OK) {
+        last = st;
+        ms = -1.f;
+      }
+      if (ms_out) ms_out[i * Ss.size() + j] = ms;
+      if (ms >= 0.f && (best < 0.f || ms < best)) {
+        best = ms;
+        *best_P = Ps[i];
+        *best_segments = Ss[j];
+      }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return best >= 0.f ? SAP_OK : last;
+}
+
 sap_status_t sap_factor_batched(int32_t n, const double* const* bands, const int64_t* N, const int32_t* K,
                                 const sap_options_t* opt, cudaStream_t s, sap_batch_t* out) {
   if (!out) return SAP_ERR_INVALID_ARG;

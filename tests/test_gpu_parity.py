@@ -310,6 +310,25 @@ def test_wide_band_solve_parity(sap, N, K, P, prec):
     assert ast == sap.SAP_OK and relerr(host(lam), lo) <= 1e-8
 
 
+def test_autotune_picks_the_fastest_measured_candidate(sap):
+    """The measured autotuner times refactor + solve for each (P, segments)
+    candidate and returns the fastest; the default P grid is N / {16000 .. 1000}."""
+    N, K = 60000, 50
+    band, xt, b = make(N, K, 1.0, 950)
+    bd = dev(band)
+    P, S, table = sap.sap_autotune(bd, N, K, precision=sap.SAP_FP32)
+    assert sorted(p for p, _ in table) == sorted({max(1, min(N // 64, (N + r // 2) // r))
+                                                  for r in (16000, 8000, 4000, 2000, 1000)})
+    assert all(v > 0 for v in table.values())
+    assert table[(P, S)] == min(table.values())
+    P2, S2, t2 = sap.sap_autotune(bd, N, K, P_cands=[10, 20], seg_cands=[1, 4], b=dev(b),
+                                  precision=sap.SAP_FP32)
+    assert set(t2) == {(10, 1), (10, 4), (20, 1), (20, 4)} and (P2, S2) in t2
+    h = sap.sap_factor(bd, N, K, P=P2, segments=S2, precision=sap.SAP_FP32)
+    x, info, st = sap.sap_solve(h, dev(b))
+    assert st == sap.SAP_OK and info.relres <= 1e-10
+
+
 # ------------------------------------------------ full-size configuration --
 
 def test_full_size_dense_banded_n200k_k50_p50(sap):

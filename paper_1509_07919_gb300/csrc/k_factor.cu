@@ -22,6 +22,7 @@
 // with unit upper U'.  Only the last K rows/columns of L~, U~ are kept,
 // flipped back into the top K x K tiles of U' and L'.
 #include <cuda_runtime.h>
+#include <algorithm>
 #include <cstdint>
 #include "sap_internal.cuh"
 
@@ -85,15 +86,12 @@ __device__ __forceinline__ void ld4(const T* p, T (&v)[4]) {
   }
 }
 
+// Factor one block (rows s .. s+n-1 of the band) with the whole CTA; F: the
+// block's factor storage (LU) or flipped top tiles (REV, ld unused).
 template <typename T, bool REV>
-__global__ void __launch_bounds__(NTHREADS)
-k_band_lu(const T* __restrict__ band, int64_t N, int K, Dev d, int block0,
-          const double* __restrict__ absmax, double eps, T* __restrict__ out,
-          unsigned long long* __restrict__ n_boosted) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int b = block0 + blockIdx.x;
-  const int64_t s = d.off[b];
-  const int n = (int)(d.off[b + 1] - s);
+__device__ void band_lu_block(unsigned char* smem_raw, const T* __restrict__ band, int64_t N, int K, int64_t s,
+                              int n, int64_t ld, T* __restrict__ F, const T tau,
+                              unsigned long long* __restrict__ n_boosted) {
   const int M2 = win_m2(K);
   const int LDW = M2 + 4;
   const int KA = K + NB;          // active rows/cols of the window in a panel step
@@ -104,10 +102,7 @@ k_band_lu(const T* __restrict__ band, int64_t N, int K, Dev d, int block0,
   T* EC = ER + NB * M2;                              // ME x NB entering columns
   T* RV = EC + ME * NB;                              // NB reciprocals of the panel's pivots
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const T tau = (T)(eps * absmax[0]);
   unsigned long long nb = 0;
-  const int64_t ld = REV ? 0 : d.ld[b];
-  T* F = REV ? out + (int64_t)(b - 1) * K * K : out + d.fbase[b];
 
   Win w{M2, LDW, 0};
   // initial window: logical rows/cols [0, M2), physical == logical
@@ -303,6 +298,41 @@ k_band_lu(const T* __restrict__ band, int64_t N, int K, Dev d, int block0,
 }
 
 template <typename T, bool REV>
+__global__ void __launch_bounds__(NTHREADS)
+k_band_lu(const T* __restrict__ band, int64_t N, int K, Dev d, int block0,
+          const double* __restrict__ absmax, double eps, T* __restrict__ out,
+          unsigned long long* __restrict__ n_boosted) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int b = block0 + blockIdx.x;
+  const int64_t s = d.off[b];
+  const int n = (int)(d.off[b + 1] - s);
+  const int64_t ld = REV ? 0 : d.ld[b];
+  T* F = REV ? out + (int64_t)(b - 1) * K * K : out + d.fbase[b];
+  band_lu_block<T, REV>(smem_raw, band, N, K, s, n, ld, F, (T)(eps * absmax[0]), n_boosted);
+}
+
+// Persistent LU over a work list of blocks of many systems (LuItem, longest
+// first): each CTA takes the next item from an atomic counter until the list
+// is exhausted, so one launch factors every block of a batch.
+template <typename T>
+__global__ void __launch_bounds__(NTHREADS)
+k_band_lu_items(const LuItem* __restrict__ items, int nitems, unsigned* __restrict__ counter) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int cur;
+  for (;;) {
+    if (threadIdx.x == 0) cur = (int)atomicAdd(counter, 1u);
+    __syncthreads();
+    const int it = cur;
+    __syncthreads();          // every thread has read cur before it changes
+    if (it >= nitems) break;
+    const LuItem I = items[it];
+    band_lu_block<T, false>(smem_raw, reinterpret_cast<const T*>(I.band), I.N, I.K, I.s, I.n, I.ld,
+                            reinterpret_cast<T*>(I.F), (T)(I.eps * I.absmax[0]), I.nb);
+    __syncthreads();
+  }
+}
+
+template <typename T, bool REV>
 cudaError_t launch_lu_impl(const T* band, int64_t N, int K, int nblocks, int block0, Dev d,
                            const double* absmax, double eps, T* out, unsigned long long* nb,
                            cudaStream_t s) {
@@ -397,6 +427,30 @@ cudaError_t launch_factor_ul(const T* band, int64_t N, int K, int P, Dev d, cons
   // UL tiles are only needed for blocks 1..P-1 (the W^(t) tips)
   return launch_lu_impl<T, true>(band, N, K, P - 1, 1, d, absmax, eps, ULt, nb, s);
 }
+
+template <typename T>
+cudaError_t launch_factor_lu_items(const LuItem* items, int nitems, int Kmax, unsigned* counter, cudaStream_t s) {
+  if (nitems <= 0) return cudaSuccess;
+  const size_t smem = lu_smem_bytes(Kmax, sizeof(T) == 8);
+  auto kern = k_band_lu_items<T>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NTHREADS, smem);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int grid = std::max(1, std::min(nitems, std::max(1, per_sm) * sms));
+  e = cudaMemsetAsync(counter, 0, sizeof(unsigned), s);
+  if (e != cudaSuccess) return e;
+  count_launches(1);
+  kern<<<grid, NTHREADS, smem, s>>>(items, nitems, counter);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_factor_lu_items<float>(const LuItem*, int, int, unsigned*, cudaStream_t);
+template cudaError_t launch_factor_lu_items<double>(const LuItem*, int, int, unsigned*, cudaStream_t);
 
 template cudaError_t launch_factor_lu<float>(const float*, int64_t, int, int, Dev, const double*, double,
                                              float*, unsigned long long*, cudaStream_t);

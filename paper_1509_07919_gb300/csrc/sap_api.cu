@@ -58,6 +58,9 @@ struct SolverBase {
   virtual ~SolverBase() = default;
   virtual sap_status_t alloc() = 0;
   virtual sap_status_t factor(cudaStream_t s) = 0;
+  virtual sap_status_t factor_pre(cudaStream_t s) = 0;       // before the block LU
+  virtual sap_status_t factor_post(cudaStream_t s) = 0;      // after the block LU
+  virtual void lu_items(std::vector<LuItem>& out) const = 0;  // this system's blocks as LU work items
   virtual sap_status_t build_adjoint(cudaStream_t s) = 0;
   virtual sap_status_t apply(const double* r, double* z, bool transpose, cudaStream_t s, Gate gt = Gate()) = 0;
   // build what a transposed apply needs (adjoint tips, transposed sweep matrices); synchronises
@@ -173,24 +176,47 @@ struct Solver : SolverBase {
 
   // Factor phases, each bracketed by events ev[0..4]: T_LU (absmax + LU),
   // T_UL, T_SPK (B/C, tips, Rbar, its GEPP and inverse).
-  sap_status_t factor(cudaStream_t s) override {
+  // Factor phases, each bracketed by events ev[0..4]: T_LU (absmax + LU +
+  // sweep matrices), T_UL, T_SPK (B/C, tips, Rbar, its GEPP and inverse).
+  // factor_pre and factor_post surround the block LU, so that a batch can run
+  // one LU launch over all its systems in between.
+  sap_status_t factor_pre(cudaStream_t s) override {
+    const Layout& L = h->L;
+    adjoint_ready = false;
+    transposed_ready = false;
+    CK(cudaEventRecord(h->evp[0], s));
+    if (sizeof(T) == 4) CK(launch_absmax_cast(h->band, L.N, L.K, h->absmax, bandf, s));
+    else CK(launch_absmax(h->band, L.N, L.K, h->absmax, s));
+    return SAP_OK;
+  }
+  void lu_items(std::vector<LuItem>& out) const override {
+    const Layout& L = h->L;
+    for (int i = 0; i < L.P; ++i) {
+      LuItem it{};
+      it.band = band_in_T();
+      it.F = f.F + L.fbase[i];
+      it.absmax = h->absmax;
+      it.nb = h->n_boosted;
+      it.N = L.N;
+      it.s = L.off[i];
+      it.ld = L.ld[i];
+      it.eps = h->opt.boost_eps;
+      it.K = L.K;
+      it.n = (int)(L.off[i + 1] - L.off[i]);
+      out.push_back(it);
+    }
+  }
+  sap_status_t factor_post(cudaStream_t s) override {
     const Layout& L = h->L;
     const int K = L.K, P = L.P;
     const double eps = h->opt.boost_eps;
-    adjoint_ready = false;
-    CK(cudaEventRecord(h->evp[0], s));
-    const T* bandT = band_in_T();
-    if (sizeof(T) == 4) CK(launch_absmax_cast(h->band, L.N, K, h->absmax, bandf, s));
-    else CK(launch_absmax(h->band, L.N, K, h->absmax, s));
-    CK(launch_factor_lu<T>(bandT, L.N, K, P, h->d, h->absmax, eps, f.F, h->n_boosted, s));
     CK(launch_chunk_mats<T>(f.F, K, P, h->d, f.cbase, L.max_nch, 0, f.Mlf, s));
     CK(launch_chunk_mats<T>(f.F, K, P, h->d, f.cbase, L.max_nch, 1, f.Mub, s));
     CK(launch_seg_trans<T>(f.Mlf, f.cbase, K, P, L.S, f.cpsmax, h->d, f.Tlf, f.Xlf, s));
     CK(launch_seg_trans<T>(f.Mub, f.cbase, K, P, L.S, f.cpsmax, h->d, f.Tub, f.Xub, s));
-    transposed_ready = false;
     CK(cudaEventRecord(h->evp[1], s));
     if (h->opt.variant == SAP_C && P > 1) {
-      CK(launch_factor_ul<T>(bandT, L.N, K, P, h->d, h->absmax, eps, f.ULt, h->n_boosted, s));
+      CK(launch_factor_ul<T>(band_in_T(), L.N, K, P, h->d, h->absmax, eps, f.ULt, h->n_boosted, s));
       CK(cudaEventRecord(h->evp[2], s));
       CK(launch_spikes<T>(h->band, L.N, K, P, h->d, f.F, f.ULt, false, f.V, f.Wt, f.R, f.R0, f.piv,
                           h->singular, s));
@@ -199,6 +225,13 @@ struct Solver : SolverBase {
     }
     CK(cudaEventRecord(h->evp[3], s));
     return SAP_OK;
+  }
+  sap_status_t factor(cudaStream_t s) override {
+    const Layout& L = h->L;
+    TRY(factor_pre(s));
+    CK(launch_factor_lu<T>(band_in_T(), L.N, L.K, L.P, h->d, h->absmax, h->opt.boost_eps, f.F, h->n_boosted,
+                           s));
+    return factor_post(s);
   }
 
   sap_status_t build_adjoint(cudaStream_t s) override {
@@ -704,8 +737,16 @@ sap_status_t create_handle(const double* band_dev, int64_t N, int32_t K, const s
 
 struct sap_batch {
   std::vector<sap_handle*> hs;
+  LuItem* items = nullptr;       // device work list of all blocks, longest first
+  unsigned* counter = nullptr;   // work-list position of the persistent LU
+  int nitems = 0, Kmax = 1;
+  bool fp64 = false;
+  cudaEvent_t ev = nullptr;
   ~sap_batch() {
     for (sap_handle* h : hs) delete h;
+    if (items) cudaFree(items);
+    if (counter) cudaFree(counter);
+    if (ev) cudaEventDestroy(ev);
   }
 };
 
@@ -721,17 +762,49 @@ int batch_partitions(int64_t N, int K, int64_t total_rows, int variant) {
   return (int)std::min(P, pmax);
 }
 
-// Factor every system on its own internal stream, ordered after s; wait for
-// all; s is ordered after them.
+// The batch's LU work list: every block of every system, longest first (LPT
+// order on the elimination cost n K^2), copied to the device once.
+sap_status_t build_work_list(sap_batch* B) {
+  std::vector<LuItem> items;
+  for (sap_handle* h : B->hs) {
+    h->impl->lu_items(items);
+    B->Kmax = std::max(B->Kmax, h->L.K);
+  }
+  std::stable_sort(items.begin(), items.end(), [](const LuItem& a, const LuItem& b) {
+    return (double)a.n * a.K * a.K > (double)b.n * b.K * b.K;
+  });
+  B->nitems = (int)items.size();
+  if (cudaMalloc(&B->items, items.size() * sizeof(LuItem)) != cudaSuccess ||
+      cudaMalloc(&B->counter, sizeof(unsigned)) != cudaSuccess) {
+    cudaGetLastError();
+    return SAP_ERR_OOM;
+  }
+  CK(cudaMemcpy(B->items, items.data(), items.size() * sizeof(LuItem), cudaMemcpyHostToDevice));
+  CK(cudaEventCreateWithFlags(&B->ev, cudaEventDisableTiming));
+  return SAP_OK;
+}
+
+// Factor a batch: each system's threshold pass (and FP32 cast) on its own
+// internal stream, then ONE persistent LU launch over the work list of all
+// blocks, then each system's sweep matrices (and SaP-C tips) on its stream
+// again; wait for all; s is ordered after them.
 sap_status_t factor_batch(sap_batch* B, cudaStream_t s) {
-  cudaEvent_t fork = nullptr;
-  CK(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
-  std::unique_ptr<CUevent_st, cudaError_t (*)(cudaEvent_t)> guard(fork, cudaEventDestroy);
-  CK(cudaEventRecord(fork, s));
+  CK(cudaEventRecord(B->ev, s));
   for (sap_handle* h : B->hs) {
     TRY(ensure_stream(h));
-    CK(cudaStreamWaitEvent(h->ks, fork, 0));
-    TRY(launch_factor(h, h->ks));
+    CK(cudaStreamWaitEvent(h->ks, B->ev, 0));
+    CK(cudaMemsetAsync(h->n_boosted, 0, sizeof(unsigned long long), h->ks));
+    CK(cudaMemsetAsync(h->singular, 0, sizeof(int), h->ks));
+    TRY(h->impl->factor_pre(h->ks));
+    CK(cudaEventRecord(h->evj, h->ks));
+    CK(cudaStreamWaitEvent(s, h->evj, 0));
+  }
+  CK(B->fp64 ? launch_factor_lu_items<double>(B->items, B->nitems, B->Kmax, B->counter, s)
+             : launch_factor_lu_items<float>(B->items, B->nitems, B->Kmax, B->counter, s));
+  CK(cudaEventRecord(B->ev, s));
+  for (sap_handle* h : B->hs) {
+    CK(cudaStreamWaitEvent(h->ks, B->ev, 0));
+    TRY(h->impl->factor_post(h->ks));
   }
   sap_status_t st = SAP_OK;
   for (sap_handle* h : B->hs) {
@@ -1015,6 +1088,8 @@ sap_status_t sap_factor_batched(int32_t n, const double* const* bands, const int
     TRY(create_handle(bands[i], N[i], K[i], &o, s, h));
     B->hs.push_back(h.release());
   }
+  B->fp64 = opt->precision == SAP_FP64;
+  TRY(build_work_list(B.get()));
   TRY(factor_batch(B.get(), s));
   *out = B.release();
   return SAP_OK;

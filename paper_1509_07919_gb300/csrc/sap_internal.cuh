@@ -102,6 +102,20 @@ cudaError_t launch_grad_band(const double* lam, const double* x, int64_t N, int 
 
 // FP32 path: absmax plus an FP32 copy of the band (the factor kernels load it)
 cudaError_t launch_absmax_cast(const double* band, int64_t N, int K, double* out, float* bandf, cudaStream_t s);
+// One block of a batched LU work list (band, factor storage and boost
+// threshold of its own system).
+struct LuItem {
+  const void* band;          // the system's band in the factor precision
+  void* F;                   // the block's factor storage
+  const double* absmax;      // the system's max |a_ij|
+  unsigned long long* nb;    // the system's boosted-pivot counter
+  int64_t N, s, ld;          // system order, first row of the block, factor leading dimension
+  double eps;                // relative boost threshold
+  int K, n;                  // half-bandwidth, block rows
+};
+template <typename T>
+cudaError_t launch_factor_lu_items(const LuItem* items, int nitems, int Kmax, unsigned* counter, cudaStream_t s);
+
 template <typename T>
 cudaError_t launch_factor_lu(const T* band, int64_t N, int K, int P, Dev d, const double* absmax,
                              double eps, T* F, unsigned long long* n_boosted, cudaStream_t s);

@@ -368,7 +368,7 @@ __host__ __device__ inline int chain_ring(int K, int S) {   // matrices per stag
 template <typename T>
 size_t chain_smem(int K, int S) {
   const int ngw = CHK * n_couplings(K);
-  return (size_t)chain_ring<T>(K, S) * ngw * ngw * sizeof(T) + 2 * (size_t)ngw * sizeof(T);
+  return (size_t)chain_ring<T>(K, S) * ngw * ngw * sizeof(T) + (size_t)(S + 1) * ngw * sizeof(T);
 }
 
 template <typename T>
@@ -384,48 +384,49 @@ k_seg_chain(const T* __restrict__ Tall, T* __restrict__ tails, int K, Dev d, int
   const int nseg = (nch + cps - 1) / cps;          // nonempty segments of this block
   const int RB = chain_ring<T>(K, S);
   T* Ts = reinterpret_cast<T*>(smem_raw);         // RB x NGW x NGW
-  T* h0 = Ts + (size_t)RB * NGW * NGW;
-  T* h1 = h0 + NGW;
+  T* zt = Ts + (size_t)RB * NGW * NGW;            // S x NGW tails (in place: zero-history -> true)
   T* tb = tails + (int64_t)b * S * NGW;
   // threads per row: the largest power of two with NGW TPR <= 256 (NGW <= 128)
   const int TPR = NGW > 128 ? 1 : (NGW > 64 ? 2 : (NGW > 32 ? 4 : 8));
   const int i = threadIdx.x / TPR, part = threadIdx.x % TPR;
-  for (int t = threadIdx.x; t < NGW; t += blockDim.x) h0[t] = tb[t];
   const int jend = nseg - 1;                       // tails 1 .. nseg-2 are needed
+  auto stage = [&](void* dsts, const void* srcg, int nbytes) {
+    const char* src = reinterpret_cast<const char*>(srcg);
+    const unsigned dst = (unsigned)__cvta_generic_to_shared(dsts);
+    for (int o = threadIdx.x * 16; o < nbytes; o += blockDim.x * 16)
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst + o), "l"(src + o) : "memory");
+  };
+  if (jend < 2) return;                            // tail_0 is exact: nothing to carry
+  // all tails of the block and the first round of T_j in one memory latency
+  stage(zt, tb, jend * NGW * (int)sizeof(T));
   for (int j0 = 1; j0 < jend; j0 += RB) {
     const int nr = min(RB, jend - j0);
-    __syncthreads();          // previous round's readers of Ts are done
-    {
-      const char* src = reinterpret_cast<const char*>(Tall + ((int64_t)b * S + j0) * NGW * NGW);
-      const int nbytes = nr * NGW * NGW * (int)sizeof(T);
-      const unsigned dst = (unsigned)__cvta_generic_to_shared(Ts);
-      for (int o = threadIdx.x * 16; o < nbytes; o += blockDim.x * 16)
-        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst + o), "l"(src + o) : "memory");
-      asm volatile("cp.async.commit_group;\n" ::: "memory");
-      asm volatile("cp.async.wait_all;\n" ::: "memory");
-    }
+    if (j0 > 1) __syncthreads();    // previous round's readers of Ts are done
+    stage(Ts, Tall + ((int64_t)b * S + j0) * NGW * NGW, nr * NGW * NGW * (int)sizeof(T));
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
     __syncthreads();
     for (int u = 0; u < nr; ++u) {
       const int j = j0 + u;
       const T* Tj = Ts + (size_t)u * NGW * NGW;
+      const T* hp = zt + (size_t)(j - 1) * NGW;    // true tail_{j-1}
       T acc = T(0);
       if (i < NGW) {
         const T* row = Tj + i * NGW;
         int q = (part + TPR * i) % NGW;
         for (int m = 0; m < NGW / TPR; ++m) {
-          acc += row[q] * h0[q];
+          acc += row[q] * hp[q];
           q += TPR;
           if (q >= NGW) q -= NGW;
         }
       }
       for (int o = TPR / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
       if (i < NGW && part == 0) {
-        const T t = tb[(int64_t)j * NGW + i] + acc;
-        h1[i] = t;
+        const T t = zt[(size_t)j * NGW + i] + acc;
+        zt[(size_t)j * NGW + i] = t;
         tb[(int64_t)j * NGW + i] = t;
       }
       __syncthreads();
-      T* tt = h0; h0 = h1; h1 = tt;
     }
   }
 }

@@ -89,6 +89,10 @@ struct sap_handle {
   // (0 forward, 1 adjoint); captured on first use, replayed per iteration
   cudaGraphExec_t gexec[2] = {nullptr, nullptr};
   cudaStream_t ks = nullptr;          // internal stream of the iteration (capturable)
+  // background stream of the transposed sweep matrices (see Solver::factor_post)
+  cudaStream_t ts = nullptr;
+  cudaEvent_t ev_ts = nullptr, ev_td = nullptr;
+  bool ts_pending = false;
   cudaEvent_t evf = nullptr, evj = nullptr;   // fork from / join to the caller's stream
   long long glaunches[2] = {0, 0};   // kernels in each graph
   bool gfailed[2] = {false, false};  // capture unavailable: launch directly
@@ -105,6 +109,9 @@ struct sap_handle {
     for (cudaGraphExec_t g : gexec)
       if (g) cudaGraphExecDestroy(g);
     if (ks) cudaStreamDestroy(ks);
+    if (ts) cudaStreamDestroy(ts);
+    if (ev_ts) cudaEventDestroy(ev_ts);
+    if (ev_td) cudaEventDestroy(ev_td);
     if (evf) cudaEventDestroy(evf);
     if (evj) cudaEventDestroy(evj);
     if (host_s) cudaFreeHost(host_s);
@@ -182,6 +189,9 @@ struct Solver : SolverBase {
   // one LU launch over all its systems in between.
   sap_status_t factor_pre(cudaStream_t s) override {
     const Layout& L = h->L;
+    // the background build of the previous factorisation reads F: wait for it
+    if (h->ts_pending) CK(cudaStreamWaitEvent(s, h->ev_td, 0));
+    h->ts_pending = false;
     adjoint_ready = false;
     transposed_ready = false;
     CK(cudaEventRecord(h->evp[0], s));
@@ -214,6 +224,21 @@ struct Solver : SolverBase {
     CK(launch_chunk_mats<T>(f.F, K, P, h->d, f.cbase, L.max_nch, 1, f.Mub, s));
     CK(launch_seg_trans<T>(f.Mlf, f.cbase, K, P, L.S, f.cpsmax, h->d, f.Tlf, f.Xlf, s));
     CK(launch_seg_trans<T>(f.Mub, f.cbase, K, P, L.S, f.cpsmax, h->d, f.Tub, f.Xub, s));
+    // a handle that has run a transposed apply gets its transposed sweep
+    // matrices rebuilt in the background, overlapping whatever follows on s
+    // (typically the forward solve); transposed applies wait for them
+    if (f.Mutf) {
+      if (!h->ts) {
+        CK(cudaStreamCreateWithFlags(&h->ts, cudaStreamNonBlocking));
+        CK(cudaEventCreateWithFlags(&h->ev_ts, cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&h->ev_td, cudaEventDisableTiming));
+      }
+      CK(cudaEventRecord(h->ev_ts, s));
+      CK(cudaStreamWaitEvent(h->ts, h->ev_ts, 0));
+      TRY(build_transposed(h->ts));
+      CK(cudaEventRecord(h->ev_td, h->ts));
+      h->ts_pending = true;
+    }
     CK(cudaEventRecord(h->evp[1], s));
     if (h->opt.variant == SAP_C && P > 1) {
       CK(launch_factor_ul<T>(band_in_T(), L.N, K, P, h->d, h->absmax, eps, f.ULt, h->n_boosted, s));
@@ -285,6 +310,10 @@ struct Solver : SolverBase {
 
   sap_status_t prepare_transposed(cudaStream_t s) override {
     TRY(build_adjoint(s));
+    if (h->ts_pending) {       // built in the background after the LU: order s after it
+      CK(cudaStreamWaitEvent(s, h->ev_td, 0));
+      return SAP_OK;
+    }
     return build_transposed(s);
   }
 

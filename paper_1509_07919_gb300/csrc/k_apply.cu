@@ -166,7 +166,7 @@ __device__ __forceinline__ void prefetch_y(const SweepSh<T, YT>& sh, const Sweep
 // lc = c - c0; z history slot of local chunk lc (lc >= -ng) is
 // (lc + ng + 1) % (ng + 1), the ng chunks before the segment occupying slots
 // 1..ng (zero).  out receives z of the segment's rows; tail (if not null) the
-// z of its last ng chunks, oldest first.
+// z of its last hist_width(K) positions, oldest first.
 template <typename T, typename YT, typename OT, int MODE>
 __device__ void sweep(const SweepSh<T, YT>& sh, const SweepGeom& g, const T* __restrict__ Mg,
                       const YT* __restrict__ yin, bool has_top, bool has_bot, OT* __restrict__ out, int c0, int nc,
@@ -258,8 +258,13 @@ __device__ void sweep(const SweepSh<T, YT>& sh, const SweepGeom& g, const T* __r
   if (warp == 2)
     for (int lc = nc + 2; lc < nc + PF; ++lc) wait_chunk(lc);
   if (warp == 1) cpa_wait<0>();
-  if (tail && warp == 0)
-    for (int i = 0; i < ng; ++i) tail[i * CHK + lane] = sh.zh[zslot(nc - ng + i) * CHK + lane];
+  if (tail && warp == 0) {     // the last KH positions of the segment's last ng chunks
+    const int off = ng * CHK - hist_width(K);
+    for (int i = 0; i < ng; ++i) {
+      const int j = i * CHK + lane - off;
+      if (j >= 0) tail[j] = sh.zh[zslot(nc - ng + i) * CHK + lane];
+    }
+  }
   __syncthreads();
 }
 
@@ -327,7 +332,7 @@ k_sweep(const T* __restrict__ Mall, const int64_t* __restrict__ cbase, int K, De
   const int cps = seg_chunks(nch, S);
   const int c0 = seg * cps, c1 = min(nch, c0 + cps);
   if (c0 >= c1) return;
-  const int NGW = g.ng * CHK;
+  const int KH = hist_width(K);
   const bool has_top = ctop_all && b > 0;
   const bool has_bot = cbot_all && b + 1 < P;
   bool failed = false;   // a barrier wait of this thread timed out
@@ -340,7 +345,7 @@ k_sweep(const T* __restrict__ Mall, const int64_t* __restrict__ cbase, int K, De
     sh.corr[t] = has_top ? ctop_all[(int64_t)(b - 1) * K + t] : 0.0;
     sh.corr[K + t] = has_bot ? cbot_all[(int64_t)b * K + t] : 0.0;
   }
-  T* tail = (tails && seg + 1 < S) ? tails + ((int64_t)b * S + seg) * NGW : nullptr;
+  T* tail = (tails && seg + 1 < S) ? tails + ((int64_t)b * S + seg) * KH : nullptr;
   unsigned ph = 0;
   sweep<T, YT, OT, MODE>(sh, g, Mall + cbase[b], yin + s, has_top, has_bot, out + s, c0, c1 - c0, tail, ph,
                          failed, err);
@@ -358,8 +363,8 @@ constexpr int kCorrThreads = 256;
 // column order: conflict-free) and combine by shuffles.
 template <typename T>
 __host__ __device__ inline int chain_ring(int K, int S) {   // matrices per staging round
-  const int ngw = CHK * n_couplings(K);
-  const size_t one = (size_t)ngw * ngw * sizeof(T);
+  const int kh = hist_width(K);
+  const size_t one = (size_t)kh * kh * sizeof(T);
   int rb = (int)((200 * 1024) / one);
   rb = rb > 8 ? 8 : rb;
   rb = rb > S - 2 ? S - 2 : rb;
@@ -367,8 +372,8 @@ __host__ __device__ inline int chain_ring(int K, int S) {   // matrices per stag
 }
 template <typename T>
 size_t chain_smem(int K, int S) {
-  const int ngw = CHK * n_couplings(K);
-  return (size_t)chain_ring<T>(K, S) * ngw * ngw * sizeof(T) + (size_t)(S + 1) * ngw * sizeof(T);
+  const int kh = hist_width(K);
+  return (size_t)chain_ring<T>(K, S) * kh * kh * sizeof(T) + (size_t)(S + 1) * kh * sizeof(T);
 }
 
 template <typename T>
@@ -377,8 +382,7 @@ k_seg_chain(const T* __restrict__ Tall, T* __restrict__ tails, int K, Dev d, int
   extern __shared__ __align__(16) unsigned char smem_raw[];
   if (gate_skip(gt)) return;
   const int b = blockIdx.x;
-  const int ng = n_couplings(K);
-  const int NGW = ng * CHK;
+  const int NGW = hist_width(K);                   // history width
   const int nch = (int)(d.ld[b] / CHK);
   const int cps = seg_chunks(nch, S);
   const int nseg = (nch + cps - 1) / cps;          // nonempty segments of this block
@@ -386,8 +390,9 @@ k_seg_chain(const T* __restrict__ Tall, T* __restrict__ tails, int K, Dev d, int
   T* Ts = reinterpret_cast<T*>(smem_raw);         // RB x NGW x NGW
   T* zt = Ts + (size_t)RB * NGW * NGW;            // S x NGW tails (in place: zero-history -> true)
   T* tb = tails + (int64_t)b * S * NGW;
-  // threads per row: the largest power of two with NGW TPR <= 256 (NGW <= 128)
-  const int TPR = NGW > 128 ? 1 : (NGW > 64 ? 2 : (NGW > 32 ? 4 : 8));
+  // threads per row: the largest power of two <= 8 dividing NGW with NGW TPR <= 256
+  int TPR = 1;
+  while (TPR < 8 && NGW % (2 * TPR) == 0 && NGW * 2 * TPR <= kCorrThreads) TPR *= 2;
   const int i = threadIdx.x / TPR, part = threadIdx.x % TPR;
   const int jend = nseg - 1;                       // tails 1 .. nseg-2 are needed
   auto stage = [&](void* dsts, const void* srcg, int nbytes) {
@@ -442,8 +447,7 @@ k_seg_correct(const T* __restrict__ Xall, const T* __restrict__ tails, int K, De
   if (gate_skip(gt)) return;
   const int b = blockIdx.z;
   const int seg = (int)blockIdx.y + 1;
-  const int ng = n_couplings(K);
-  const int NGW = ng * CHK;
+  const int NGW = hist_width(K);                   // history width
   const int ld = (int)d.ld[b];
   const int64_t s = d.off[b];
   const int n = (int)(d.off[b + 1] - s);

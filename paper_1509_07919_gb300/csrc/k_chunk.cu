@@ -189,12 +189,14 @@ namespace {
 // with zero history it yields zhat; by linearity its true values are
 // z = zhat + X h, with
 //     X_c = - sum_{k=1..ng} G_{c,k} X_{c-k},   c = c0 .. c1-1,
-// started from X_{c0-ng+i} = the identity rows of history chunk i.  This
-// kernel stores, per block and segment s >= 1, X itself (column-major over
-// the segment's positions, cpsmax 32 rows per segment) for the correction
-// z += X h of the apply, and the transfer matrix T_s (X on the segment's last
-// ng chunks, (32 ng) x (32 ng), row-major), which carries the history from
-// segment to segment:
+// started from X_{c0-ng+i} = the identity rows of history chunk i.  Only the
+// last KH = hist_width(K) history positions couple into the segment (the
+// columns of X for the others stay exactly zero), so this kernel stores, per
+// block and segment s >= 1, the KH columns of X for those positions
+// (column-major over the segment's positions, cpsmax 32 rows per segment) for
+// the correction z += X h of the apply, and the transfer matrix T_s (those
+// columns on the segment's last KH positions, KH x KH, row-major), which
+// carries the history from segment to segment:
 //     tail_s = zhat_tail_s + T_s tail_{s-1}.
 // One CTA per block and segment s >= 1; thread (q, rg) computes column q of
 // rows rg R .. rg R + R - 1 of every X_c (broadcast 16-byte reads of G,
@@ -216,7 +218,7 @@ template <> struct Vec16<double> { using type = double2; };
 
 template <typename T, int NG>
 __global__ void __launch_bounds__(256)
-k_seg_trans(const T* __restrict__ Mall, const int64_t* __restrict__ cbase, Dev d, int S, int cpsmax,
+k_seg_trans(const T* __restrict__ Mall, const int64_t* __restrict__ cbase, Dev d, int S, int cpsmax, int kh,
             T* __restrict__ Tout, T* __restrict__ Xout) {
   using C = SegTrans<T, NG>;
   constexpr int NGW = C::NGW, XLD = C::XLD, R = C::R, NTH = C::NTH;
@@ -239,7 +241,9 @@ k_seg_trans(const T* __restrict__ Mall, const int64_t* __restrict__ cbase, Dev d
   const int q = tid % NGW, rg = tid / NGW;
   const T* Mb = Mall + cbase[b];
   const int64_t xm = (int64_t)cpsmax * CH;        // rows of one segment's X
-  T* Xb = Xout + ((int64_t)b * (S - 1) + (s - 1)) * xm * NGW;
+  const int KH = kh;                              // stored history width
+  const int hoff = NGW - KH;                      // first stored history column
+  T* Xb = Xout + ((int64_t)b * (S - 1) + (s - 1)) * xm * KH;
   for (int c = c0; c < c1; ++c) {
     __syncthreads();    // readers of the previous Gs and X_c are done
     const T* Mc = Mb + (int64_t)c * (1 + NG) * CH * CH + CH * CH;
@@ -268,31 +272,32 @@ k_seg_trans(const T* __restrict__ Mall, const int64_t* __restrict__ cbase, Dev d
 #pragma unroll
     for (int r = 0; r < R; ++r) Xc[(rg * R + r) * XLD + q] = acc[r];
     __syncthreads();
-    // X_c to global, column-major over the segment's positions (coalesced)
+    // X_c to global (its KH stored columns), column-major over the segment's
+    // positions (coalesced)
     const int64_t pr = (int64_t)(c - c0) * CH;
-    for (int e = tid; e < CH * NGW; e += NTH) {
+    for (int e = tid; e < CH * KH; e += NTH) {
       const int t = e % CH, qq = e / CH;
-      Xb[(int64_t)qq * xm + pr + t] = Xc[t * XLD + qq];
+      Xb[(int64_t)qq * xm + pr + t] = Xc[t * XLD + hoff + qq];
     }
   }
   __syncthreads();
-  T* To = Tout + ((int64_t)b * S + s) * NGW * NGW;
-  for (int e = tid; e < NGW * NGW; e += NTH) {
-    const int row = e / NGW, col = e % NGW;        // row = 32 i + t: chunk c1 - NG + i, position t
+  T* To = Tout + ((int64_t)b * S + s) * KH * KH;
+  for (int e = tid; e < KH * KH; e += NTH) {
+    const int row = hoff + e / KH, col = hoff + e % KH;   // row = 32 i + t: chunk c1 - NG + i, position t
     To[e] = X[slot(c1 - NG + row / CH) * CH * XLD + (row % CH) * XLD + col];
   }
 }
 
 template <typename T, int NG>
-cudaError_t seg_trans_ng(const T* M, const int64_t* cbase, int P, int S, int cpsmax, Dev d, T* tout, T* xout,
-                         cudaStream_t s) {
+cudaError_t seg_trans_ng(const T* M, const int64_t* cbase, int P, int S, int cpsmax, int kh, Dev d, T* tout,
+                         T* xout, cudaStream_t s) {
   using C = SegTrans<T, NG>;
   auto kern = k_seg_trans<T, NG>;
   if (C::smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem);
     if (e != cudaSuccess) return e;
   }
-  kern<<<dim3(S - 1, P), C::NTH, C::smem, s>>>(M, cbase, d, S, cpsmax, tout, xout);
+  kern<<<dim3(S - 1, P), C::NTH, C::smem, s>>>(M, cbase, d, S, cpsmax, kh, tout, xout);
   return cudaGetLastError();
 }
 
@@ -304,10 +309,10 @@ cudaError_t launch_seg_trans(const T* M, const int64_t* cbase, int K, int P, int
   if (S < 2) return cudaSuccess;
   count_launches(1);
   switch ((K + CH - 1) / CH) {
-    case 1: return seg_trans_ng<T, 1>(M, cbase, P, S, cpsmax, d, tout, xout, s);
-    case 2: return seg_trans_ng<T, 2>(M, cbase, P, S, cpsmax, d, tout, xout, s);
-    case 3: return seg_trans_ng<T, 3>(M, cbase, P, S, cpsmax, d, tout, xout, s);
-    default: return seg_trans_ng<T, 4>(M, cbase, P, S, cpsmax, d, tout, xout, s);
+    case 1: return seg_trans_ng<T, 1>(M, cbase, P, S, cpsmax, hist_width(K), d, tout, xout, s);
+    case 2: return seg_trans_ng<T, 2>(M, cbase, P, S, cpsmax, hist_width(K), d, tout, xout, s);
+    case 3: return seg_trans_ng<T, 3>(M, cbase, P, S, cpsmax, hist_width(K), d, tout, xout, s);
+    default: return seg_trans_ng<T, 4>(M, cbase, P, S, cpsmax, hist_width(K), d, tout, xout, s);
   }
 }
 

@@ -135,15 +135,15 @@ struct Solver : SolverBase {
   bool transposed_ready = false;
   explicit Solver(sap_handle* hh) : h(hh) {}
 
-  // elements of one sweep kind's transfer matrices: P x S x (32 ng)^2
+  // elements of one sweep kind's transfer matrices: P x S x KH^2
   size_t trans_elems() const {
-    const size_t ngw = (size_t)32 * chunk_couplings(h->L.K);
-    return (size_t)h->L.P * h->L.S * ngw * ngw;
+    const size_t kh = (size_t)hist_width(h->L.K);
+    return (size_t)h->L.P * h->L.S * kh * kh;
   }
-  // elements of one sweep kind's history responses: P x (S - 1) x 32 ng x cpsmax 32
+  // elements of one sweep kind's history responses: P x (S - 1) x KH x cpsmax 32
   size_t xresp_elems() const {
-    const size_t ngw = (size_t)32 * chunk_couplings(h->L.K);
-    return (size_t)h->L.P * (h->L.S - 1) * ngw * (size_t)seg_chunks(h->L.max_nch, h->L.S) * 32;
+    const size_t kh = (size_t)hist_width(h->L.K);
+    return (size_t)h->L.P * (h->L.S - 1) * kh * (size_t)seg_chunks(h->L.max_nch, h->L.S) * 32;
   }
 
   sap_status_t alloc() override {
@@ -168,7 +168,7 @@ struct Solver : SolverBase {
       TRY(h->mem.alloc(&f.Xlf, xresp_elems()));
       TRY(h->mem.alloc(&f.Xub, xresp_elems()));
       f.cpsmax = seg_chunks(L.max_nch, L.S);
-      TRY(h->mem.alloc(&f.tails, (size_t)P * L.S * 32 * chunk_couplings(K)));
+      TRY(h->mem.alloc(&f.tails, (size_t)P * L.S * hist_width(K)));
     }
     if (h->opt.variant == SAP_C && P > 1) {
       TRY(h->mem.alloc(&f.ULt, (size_t)(nI * KK)));

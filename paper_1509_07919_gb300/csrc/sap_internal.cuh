@@ -58,14 +58,14 @@ struct Factors {
   T* Mlf = nullptr; T* Mub = nullptr; T* Mutf = nullptr; T* Mltb = nullptr;
   const int64_t* cbase = nullptr;
   // segmented sweeps (S segments per block): per block and segment s >= 1 the
-  // (32 ng) x (32 ng) transfer matrix of each sweep kind (row-major, segment 0
-  // unused) and its history response X, and the per-apply tails of the
-  // zero-history pass
+  // KH x KH transfer matrix of each sweep kind (KH = hist_width(K), row-major,
+  // segment 0 unused) and its history response X, and the per-apply tails
+  // (last KH values of each segment) of the zero-history pass
   int S = 1;
   T* Tlf = nullptr; T* Tub = nullptr; T* Tutf = nullptr; T* Tltb = nullptr;
   T* Xlf = nullptr; T* Xub = nullptr; T* Xutf = nullptr; T* Xltb = nullptr;   // history responses
   int cpsmax = 0;        // chunks of the longest segment
-  T* tails = nullptr;    // P x S x 32 ng
+  T* tails = nullptr;    // P x S x KH
   int* err = nullptr;    // set to nonzero by a device-side wait that timed out
 };
 
@@ -129,12 +129,16 @@ cudaError_t launch_spikes(const double* band, int64_t N, int K, int P, Dev d, co
 template <typename T>
 cudaError_t launch_chunk_mats(const T* F, int K, int P, Dev d, const int64_t* cbase, int max_nch, int mode, T* out,
                               cudaStream_t s);
-// Transfer matrices (tout: P x S x (32 ng)^2) and history responses X (xout:
-// P x (S-1) x (32 ng) x cpsmax 32, column-major per segment) of segments
-// 1..S-1 of every block, from the chunk matrices M of one sweep kind.
+// Transfer matrices (tout: P x S x KH^2) and history responses X (xout:
+// P x (S-1) x KH x cpsmax 32, column-major per segment), KH = hist_width(K), of
+// segments 1..S-1 of every block, from the chunk matrices M of one sweep kind.
 template <typename T>
 cudaError_t launch_seg_trans(const T* M, const int64_t* cbase, int K, int P, int S, int cpsmax, Dev d, T* tout,
                              T* xout, cudaStream_t s);
+// Width of a segment's history in the segmented sweeps: only the last K
+// positions before a segment couple into it, rounded up to a multiple of 4
+// (16-byte rows for FP32) and at most 32 ceil(K/32).
+__host__ __device__ inline int hist_width(int K) { return (K + 3) / 4 * 4; }
 // Chunks of 32 rows per segment of a block with nch chunks: ceil(nch / S).
 __host__ __device__ inline int seg_chunks(int nch, int S) { return (nch + S - 1) / S; }
 template <typename T>

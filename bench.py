@@ -31,7 +31,7 @@ METRIC = "time to rel.res 1e-10 & HBM GB/s: FP32-precond vs FP64 SaP, fwd+adjoin
 # DRAM bytes (read + write) of the sweep launches of one FP32 SaP-D preconditioner
 # apply on the N=200000, K=50, P=50 workload (automatic segment count), from the
 # ncu capture summarised in profiles/k_sweep_n200k_k50_fp32.md
-TRAFFIC_SWEEPS = None
+TRAFFIC_SWEEPS = 232812800
 WORKLOADS = {
     "n200k_k50": dict(N=200000, K=50, d=1.0, P=50, seed_cfg=2),
     "n10k_k10": dict(N=10000, K=10, d=1.2, P=8, seed_cfg=1),

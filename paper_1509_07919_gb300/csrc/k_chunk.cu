@@ -46,52 +46,63 @@ __device__ __forceinline__ T sweep_entry(const T* F, int K, int n, int ld, int p
   return F[(int64_t)c * ld + fq];
 }
 
-constexpr int NT = 256;
 constexpr int LDS = CH + 1;      // padded shared-memory row
 
 // S[t][j] = sweep entry (p0 + t, p0 - k * 32 + j) where its position
 // distance k * 32 + t - j lies in [0, K], else 0 (identity padding comes
-// from sweep_entry).  Warps walk the 63 diagonals t - j = const with lane = j,
-// so each load of the band-stored factor reads consecutive addresses.
-template <int MODE, typename T>
+// from sweep_entry).  The NWARPS warps walk the 63 diagonals t - j = const
+// with lane = j, so each load of the band-stored factor reads consecutive
+// addresses; all loads of a thread are issued before its stores.
+template <int MODE, int NWARPS, typename T>
 __device__ __forceinline__ void load_tile(T* S, const T* F, int K, int n, int ld, int p0, int k, int c) {
   const int lane = threadIdx.x % 32, warp = threadIdx.x / 32;
-  constexpr int ROWS = (2 * CH - 1 + NT / 32 - 1) / (NT / 32);
+  constexpr int ROWS = (2 * CH - 1 + NWARPS - 1) / NWARPS;
   T v[ROWS];
 #pragma unroll
   for (int i = 0; i < ROWS; ++i) {
-    const int delta = warp + i * (NT / 32) - (CH - 1);   // t - j
+    const int delta = warp + i * NWARPS - (CH - 1);   // t - j
     const int t = lane + delta;
     const int dist = k * CH + delta;
-    v[i] = (t >= 0 && t < CH && c >= k && dist >= 0 && dist <= K)
+    v[i] = (delta < CH && t >= 0 && t < CH && c >= k && dist >= 0 && dist <= K)
                ? sweep_entry<MODE>(F, K, n, ld, p0 + t, p0 - k * CH + lane)
                : T(0);
   }
 #pragma unroll
   for (int i = 0; i < ROWS; ++i) {
-    const int delta = warp + i * (NT / 32) - (CH - 1);
+    const int delta = warp + i * NWARPS - (CH - 1);
     const int t = lane + delta;
     if (delta < CH && t >= 0 && t < CH) S[t * LDS + lane] = v[i];
   }
 }
 
-// Dynamic shared memory: A (in-chunk block), X (its inverse), ng coupling
-// tiles B_k, 32 reciprocal pivots.
+// One CTA per chunk: the 32 (1 + NG) columns of [MINV_c | G_{c,1} .. G_{c,NG}]
+// are the solutions of A_c x = e_j and A_c x = (column j of B_{c,k}), all
+// solved at once by forward substitution, TPC threads per column (thread
+// `part` keeps x_r for r = part mod TPC in registers; the partial dot
+// products of a row are combined by shuffles).  Same matrices as forming
+// A_c^{-1} and multiplying, different rounding order.
+template <int NG>
+struct ChunkCfg {
+  static constexpr int NCOL = CH * (1 + NG);
+  static constexpr int TPC = NG == 1 ? 8 : (NG <= 3 ? 4 : (NG <= 7 ? 2 : 1));
+  static constexpr int NTH = NCOL * TPC;      // 512, 384, 512, 320, 384, 448, 512
+};
+
 template <typename T>
 size_t chunk_smem_bytes(int K) {
   const int ng = (K + CH - 1) / CH;
-  return (size_t)(2 + ng) * CH * LDS * sizeof(T) + CH * sizeof(T);
+  return (size_t)(1 + ng) * CH * LDS * sizeof(T) + CH * sizeof(T);
 }
 
-template <typename T, int MODE>
-__global__ void __launch_bounds__(NT)
+template <typename T, int MODE, int NG>
+__global__ void __launch_bounds__(ChunkCfg<NG>::NTH)
 k_chunk_mats(const T* __restrict__ Fall, int K, Dev d, const int64_t* __restrict__ cbase, T* __restrict__ out) {
+  using C = ChunkCfg<NG>;
+  constexpr int TPC = C::TPC, NW = C::NTH / 32, XR = CH / TPC;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* A = reinterpret_cast<T*>(smem_raw);
-  T* X = A + CH * LDS;            // MINV
-  T* Bs = X + CH * LDS;           // B_1 .. B_ng
-  const int ng = (K + CH - 1) / CH;
-  T* Rd = Bs + ng * CH * LDS;
+  T* A = reinterpret_cast<T*>(smem_raw);        // in-chunk block, then B_1 .. B_NG
+  T* Bs = A + CH * LDS;
+  T* Rd = Bs + NG * CH * LDS;
   const int b = blockIdx.y;
   const int ld = (int)d.ld[b];
   const int nch = ld / CH;
@@ -101,65 +112,55 @@ k_chunk_mats(const T* __restrict__ Fall, int K, Dev d, const int64_t* __restrict
   const T* F = Fall + d.fbase[b];
   const int tid = threadIdx.x;
   const int p0 = c * CH;
-  // every tile is loaded up front: the loads of all tiles are in flight together
-  load_tile<MODE>(A, F, K, n, ld, p0, 0, c);
-  for (int k = 1; k <= ng; ++k) load_tile<MODE>(Bs + (k - 1) * CH * LDS, F, K, n, ld, p0, k, c);
-  for (int e = tid; e < CH * CH; e += NT) X[(e / CH) * LDS + e % CH] = T(0);
+  load_tile<MODE, NW>(A, F, K, n, ld, p0, 0, c);
+#pragma unroll
+  for (int k = 1; k <= NG; ++k) load_tile<MODE, NW>(Bs + (k - 1) * CH * LDS, F, K, n, ld, p0, k, c);
   __syncthreads();
   if (tid < CH) Rd[tid] = T(1) / A[tid * LDS + tid];
   __syncthreads();
-  // MINV = A^{-1} (lower triangular): thread j solves A x = e_j by forward
-  // substitution with four independent partial sums per row
-  if (tid < CH) {
-    const int j = tid;
-    X[j * LDS + j] = Rd[j];
-    for (int r = j + 1; r < CH; ++r) {
-      const T* Ar = A + r * LDS;
-      T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
-      int q = j;
-      for (; q + 3 < r; q += 4) {
-        a0 += Ar[q] * X[q * LDS + j];
-        a1 += Ar[q + 1] * X[(q + 1) * LDS + j];
-        a2 += Ar[q + 2] * X[(q + 2) * LDS + j];
-        a3 += Ar[q + 3] * X[(q + 3) * LDS + j];
-      }
-      for (; q < r; ++q) a0 += Ar[q] * X[q * LDS + j];
-      X[r * LDS + j] = -((a0 + a1) + (a2 + a3)) * Rd[r];
+  const int col = tid / TPC, part = tid % TPC;
+  const T* Bcol = col >= CH ? Bs + ((col - CH) / CH) * CH * LDS + (col % CH) : nullptr;
+  T xr[XR];
+#pragma unroll
+  for (int r = 0; r < CH; ++r) {
+    T acc = T(0);
+#pragma unroll
+    for (int m = 0; m <= r / TPC; ++m) {
+      const int q = m * TPC + part;
+      if (q < r) acc += A[r * LDS + q] * xr[m];
     }
+#pragma unroll
+    for (int o = TPC / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    const T rhs = Bcol ? Bcol[r * LDS] : (r == col ? T(1) : T(0));
+    const T x = (rhs - acc) * Rd[r];
+    if (r % TPC == part) xr[r / TPC] = x;
   }
-  __syncthreads();
   // stored column-major (element (t, j) at j * 32 + t): the sweep's lane t
   // reads its row as 32 conflict-free shared-memory loads
-  T* M = out + cbase[b] + (int64_t)c * (1 + ng) * CH * CH;
-  constexpr int PER = CH * CH / NT;    // outputs per thread and matrix (4)
+  T* M = out + cbase[b] + (int64_t)c * (1 + NG) * CH * CH + (int64_t)(col / CH) * CH * CH + (col % CH) * CH;
 #pragma unroll
-  for (int i = 0; i < PER; ++i) {
-    const int e = tid + i * NT;
-    M[e] = X[(e % CH) * LDS + e / CH];
-  }
-  // G_k = MINV B_k: thread computes row t = lane of columns j = warp, warp + 8, ...
-  // (conflict-free reads of X, broadcast reads of B_k, coalesced stores)
-  const int t = tid % CH, jq = tid / CH;
-  for (int k = 1; k <= ng; ++k) {
-    const T* Bk = Bs + (k - 1) * CH * LDS;
-    T acc[PER];
-#pragma unroll
-    for (int i = 0; i < PER; ++i) acc[i] = T(0);
-    for (int q = 0; q <= t; ++q) {
-      const T xq = X[t * LDS + q];
-#pragma unroll
-      for (int i = 0; i < PER; ++i) acc[i] += xq * Bk[q * LDS + jq + i * (NT / CH)];
-    }
-    T* G = M + (int64_t)k * CH * CH;
-#pragma unroll
-    for (int i = 0; i < PER; ++i) G[(jq + i * (NT / CH)) * CH + t] = acc[i];
-  }
+  for (int m = 0; m < XR; ++m) M[m * TPC + part] = xr[m];
+}
+
+template <typename T, int MODE, int NG>
+void launch_mode(dim3 grid, size_t smem, const T* F, int K, Dev d, const int64_t* cbase, T* out, cudaStream_t s) {
+  auto kern = k_chunk_mats<T, MODE, NG>;
+  if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  kern<<<grid, ChunkCfg<NG>::NTH, smem, s>>>(F, K, d, cbase, out);
 }
 
 template <typename T, int MODE>
-void launch_mode(dim3 grid, size_t smem, const T* F, int K, Dev d, const int64_t* cbase, T* out, cudaStream_t s) {
-  if (smem > 48 * 1024) cudaFuncSetAttribute(k_chunk_mats<T, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k_chunk_mats<T, MODE><<<grid, NT, smem, s>>>(F, K, d, cbase, out);
+void launch_mode_ng(int ng, dim3 grid, size_t smem, const T* F, int K, Dev d, const int64_t* cbase, T* out,
+                    cudaStream_t s) {
+  switch (ng) {
+    case 1: launch_mode<T, MODE, 1>(grid, smem, F, K, d, cbase, out, s); break;
+    case 2: launch_mode<T, MODE, 2>(grid, smem, F, K, d, cbase, out, s); break;
+    case 3: launch_mode<T, MODE, 3>(grid, smem, F, K, d, cbase, out, s); break;
+    case 4: launch_mode<T, MODE, 4>(grid, smem, F, K, d, cbase, out, s); break;
+    case 5: launch_mode<T, MODE, 5>(grid, smem, F, K, d, cbase, out, s); break;
+    case 6: launch_mode<T, MODE, 6>(grid, smem, F, K, d, cbase, out, s); break;
+    default: launch_mode<T, MODE, 7>(grid, smem, F, K, d, cbase, out, s); break;
+  }
 }
 
 }  // namespace
@@ -170,11 +171,12 @@ cudaError_t launch_chunk_mats(const T* F, int K, int P, Dev d, const int64_t* cb
   dim3 grid(max_nch, P);
   const size_t smem = chunk_smem_bytes<T>(K);
   count_launches(1);
+  const int ng = (K + CH - 1) / CH;
   switch (mode) {
-    case 0: launch_mode<T, 0>(grid, smem, F, K, d, cbase, out, s); break;
-    case 1: launch_mode<T, 1>(grid, smem, F, K, d, cbase, out, s); break;
-    case 2: launch_mode<T, 2>(grid, smem, F, K, d, cbase, out, s); break;
-    default: launch_mode<T, 3>(grid, smem, F, K, d, cbase, out, s); break;
+    case 0: launch_mode_ng<T, 0>(ng, grid, smem, F, K, d, cbase, out, s); break;
+    case 1: launch_mode_ng<T, 1>(ng, grid, smem, F, K, d, cbase, out, s); break;
+    case 2: launch_mode_ng<T, 2>(ng, grid, smem, F, K, d, cbase, out, s); break;
+    default: launch_mode_ng<T, 3>(ng, grid, smem, F, K, d, cbase, out, s); break;
   }
   return cudaGetLastError();
 }

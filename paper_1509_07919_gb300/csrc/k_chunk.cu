@@ -211,7 +211,11 @@ struct SegTrans {
   static constexpr int RG = (NG == 3) ? 2 : 256 / NGW;   // row groups
   static constexpr int R = CH / RG;                        // rows per thread
   static constexpr int NTH = NGW * RG;
-  static constexpr size_t smem = ((size_t)(NG + 1) * CH * XLD + (size_t)NG * CH * CH) * sizeof(T);
+  static constexpr size_t xbytes = (size_t)(NG + 1) * CH * XLD * sizeof(T);
+  static constexpr size_t gbytes = (size_t)NG * CH * CH * sizeof(T);
+  // G double-buffered (the next chunk's couplings in flight) when it fits
+  static constexpr bool DB = xbytes + 2 * gbytes <= 227 * 1024;
+  static constexpr size_t smem = xbytes + (DB ? 2 : 1) * gbytes;
 };
 
 template <typename T> struct Vec16;
@@ -227,8 +231,8 @@ k_seg_trans(const T* __restrict__ Mall, const int64_t* __restrict__ cbase, Dev d
   constexpr int E = 16 / (int)sizeof(T);
   using V = typename Vec16<T>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* Gs = reinterpret_cast<T*>(smem_raw);         // G_{c,1..NG}, column-major as stored
-  T* X = Gs + NG * CH * CH;                       // (NG + 1) ring slots x 32 x XLD
+  T* Gbuf = reinterpret_cast<T*>(smem_raw);       // G_{c,1..NG}, column-major as stored (x2 if DB)
+  T* X = Gbuf + (C::DB ? 2 : 1) * NG * CH * CH;   // (NG + 1) ring slots x 32 x XLD
   const int b = blockIdx.y, s = blockIdx.x + 1;
   const int nch = (int)(d.ld[b] / CH);
   const int cps = seg_chunks(nch, S);
@@ -246,11 +250,28 @@ k_seg_trans(const T* __restrict__ Mall, const int64_t* __restrict__ cbase, Dev d
   const int KH = kh;                              // stored history width
   const int hoff = NGW - KH;                      // first stored history column
   T* Xb = Xout + ((int64_t)b * (S - 1) + (s - 1)) * xm * KH;
+  // cp.async of chunk cc's couplings into buffer `buf`
+  auto stage = [&](int cc, int buf) {
+    const char* src = reinterpret_cast<const char*>(Mb + (int64_t)cc * (1 + NG) * CH * CH + CH * CH);
+    const unsigned dst = (unsigned)__cvta_generic_to_shared(Gbuf + buf * NG * CH * CH);
+    for (int o = tid * 16; o < (int)C::gbytes; o += NTH * 16)
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst + o), "l"(src + o) : "memory");
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+  };
+  if (C::DB) stage(c0, 0);
   for (int c = c0; c < c1; ++c) {
-    __syncthreads();    // readers of the previous Gs and X_c are done
-    const T* Mc = Mb + (int64_t)c * (1 + NG) * CH * CH + CH * CH;
-    for (int e = tid; e < NG * CH * CH; e += NTH) Gs[e] = Mc[e];
+    const int cur = C::DB ? (c - c0) & 1 : 0;
+    __syncthreads();    // readers of the previous G buffer and X_c are done
+    if (C::DB) {
+      if (c + 1 < c1) stage(c + 1, cur ^ 1);
+      else asm volatile("cp.async.commit_group;\n" ::: "memory");
+      asm volatile("cp.async.wait_group 1;\n" ::: "memory");      // chunk c landed
+    } else {
+      stage(c, 0);
+      asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    }
     __syncthreads();
+    const T* Gs = Gbuf + cur * NG * CH * CH;
     T acc[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) acc[r] = T(0);

@@ -31,7 +31,7 @@ namespace {
 
 constexpr int NWS = 3;              // warps per sweep CTA
 constexpr int CHK = 32;             // chunk length
-constexpr int PF = 4;               // chunks prefetched ahead
+constexpr int PF = 4;               // chunks prefetched ahead (2 where a 4-deep ring does not fit)
 
 enum Mode { LF = 0, UB = 1, UTF = 2, LTB = 3 };
 
@@ -128,14 +128,14 @@ struct SweepSh {
 template <int MODE>
 __device__ __forceinline__ int row_of(int p, int ld) { return fwd_mode<MODE>() ? p : ld - 1 - p; }
 
-// Warp 2: bulk-copy local chunk lc's matrices into ring slot lc % (PF+1).
+// Warp 2: bulk-copy local chunk lc's matrices into ring slot lc % (PFD+1).
 // Chunks past the segment (lc >= nc) only arrive on the barrier, so that every
 // slot completes one phase per chunk index.
-template <typename T, typename YT>
+template <int PFD, typename T, typename YT>
 __device__ __forceinline__ void prefetch_mats(const SweepSh<T, YT>& sh, const SweepGeom& g, const T* __restrict__ Mg,
                                               int lc, int nc) {
   if ((threadIdx.x & 31) != 0) return;
-  const int slot = lc % (PF + 1);
+  const int slot = lc % (PFD + 1);
   const int mat = (1 + g.ng) * CHK * CHK;
   if (lc < nc) {
     const unsigned bytes = (unsigned)(mat * sizeof(T));
@@ -148,13 +148,13 @@ __device__ __forceinline__ void prefetch_mats(const SweepSh<T, YT>& sh, const Sw
 
 // Warp 1: cp.async of local chunk lc's right-hand side (one commit group per
 // chunk); p0: first position of the segment.
-template <typename T, typename YT, int MODE>
+template <int PFD, typename T, typename YT, int MODE>
 __device__ __forceinline__ void prefetch_y(const SweepSh<T, YT>& sh, const SweepGeom& g, const YT* __restrict__ yin,
                                            int lc, int nc, int p0) {
   const int lane = threadIdx.x & 31;
   if (lc < nc) {
     const int r = row_of<MODE>(p0 + lc * CHK + lane, g.ld);
-    YT* ydst = &sh.Y[(lc % (PF + 1)) * CHK + lane];
+    YT* ydst = &sh.Y[(lc % (PFD + 1)) * CHK + lane];
     if (r < g.n) cpa(ydst, &yin[r]);
     else *ydst = YT(0);
   }
@@ -167,7 +167,7 @@ __device__ __forceinline__ void prefetch_y(const SweepSh<T, YT>& sh, const Sweep
 // (lc + ng + 1) % (ng + 1), the ng chunks before the segment occupying slots
 // 1..ng (zero).  out receives z of the segment's rows; tail (if not null) the
 // z of its last hist_width(K) positions, oldest first.
-template <typename T, typename YT, typename OT, int MODE>
+template <typename T, typename YT, typename OT, int MODE, int PFD = PF>
 __device__ void sweep(const SweepSh<T, YT>& sh, const SweepGeom& g, const T* __restrict__ Mg,
                       const YT* __restrict__ yin, bool has_top, bool has_bot, OT* __restrict__ out, int c0, int nc,
                       T* __restrict__ tail, unsigned& ph, bool& failed, int* __restrict__ err) {
@@ -180,7 +180,7 @@ __device__ void sweep(const SweepSh<T, YT>& sh, const SweepGeom& g, const T* __r
   // ph: per-slot parity of the next barrier phase (lane 0 of warp 2), carried
   // from sweep to sweep of one CTA
   auto wait_chunk = [&](int lc) {     // warp 2: lane 0 polls
-    const int sl = lc % (PF + 1);
+    const int sl = lc % (PFD + 1);
     if (lane == 0) mbar_wait(&sh.bar[sl], (ph >> sl) & 1u, err, failed);
     ph ^= 1u << sl;
     __syncwarp();
@@ -188,7 +188,7 @@ __device__ void sweep(const SweepSh<T, YT>& sh, const SweepGeom& g, const T* __r
   auto zslot = [&](int lc) { return (lc + ng + 1) % (ng + 1); };
   // w_lb = MINV (y - corrections) - sum_{k>=2} G_k z_{lb-k}
   auto prepare = [&](int lb) {
-    const int slot = lb % (PF + 1);
+    const int slot = lb % (PFD + 1);
     const int r = row_of<MODE>(p0 + lb * CHK + lane, g.ld);
     T yv = T(0);
     if (r < g.n) {
@@ -207,14 +207,14 @@ __device__ void sweep(const SweepSh<T, YT>& sh, const SweepGeom& g, const T* __r
   // z history: zero
   for (int t = threadIdx.x; t < (ng + 1) * CHK; t += blockDim.x) sh.zh[t] = T(0);
   __syncthreads();
-  // prologue: matrices of local chunks 0..PF-1 in flight, 0 and 1 landed, w_0 formed
+  // prologue: matrices of local chunks 0..PFD-1 in flight, 0 and 1 landed, w_0 formed
   if (warp == 2) {
-    for (int lc = 0; lc < PF; ++lc) prefetch_mats(sh, g, Ms, lc, nc);
+    for (int lc = 0; lc < PFD; ++lc) prefetch_mats<PFD>(sh, g, Ms, lc, nc);
     wait_chunk(0);
     wait_chunk(1);
   } else if (warp == 1) {
-    for (int lc = 0; lc < PF; ++lc) prefetch_y<T, YT, MODE>(sh, g, yin, lc, nc, p0);
-    cpa_wait<PF - 1>();
+    for (int lc = 0; lc < PFD; ++lc) prefetch_y<PFD, T, YT, MODE>(sh, g, yin, lc, nc, p0);
+    cpa_wait<PFD - 1>();
     __syncwarp();
   }
   __syncthreads();
@@ -224,7 +224,7 @@ __device__ void sweep(const SweepSh<T, YT>& sh, const SweepGeom& g, const T* __r
   T zprev = T(0);
   for (int lc = 0; lc < nc; ++lc) {
     if (warp == 0) {
-      const T* G1 = sh.M + (lc % (PF + 1)) * mat + CHK * CHK;
+      const T* G1 = sh.M + (lc % (PFD + 1)) * mat + CHK * CHK;
       T m[CHK];
 #pragma unroll
       for (int j = 0; j < CHK; ++j) m[j] = G1[j * CHK + lane];
@@ -242,21 +242,21 @@ __device__ void sweep(const SweepSh<T, YT>& sh, const SweepGeom& g, const T* __r
       const int r = row_of<MODE>(p0 + lc * CHK + lane, g.ld);
       if (out && r < g.n) out[r] = (OT)z;
     } else if (warp == 1) {
-      prefetch_y<T, YT, MODE>(sh, g, yin, lc + PF, nc, p0);
+      prefetch_y<PFD, T, YT, MODE>(sh, g, yin, lc + PFD, nc, p0);
       if (lc + 1 < nc) {
-        cpa_wait<PF - 1>();     // y of chunk lc + 1 landed
+        cpa_wait<PFD - 1>();     // y of chunk lc + 1 landed
         __syncwarp();
         prepare(lc + 1);
       }
     } else {
-      prefetch_mats(sh, g, Ms, lc + PF, nc);
+      prefetch_mats<PFD>(sh, g, Ms, lc + PFD, nc);
       wait_chunk(lc + 2);       // read by warp 1 in iteration lc + 1, by warp 0 in lc + 2
     }
     __syncthreads();
   }
   // warp 2: consume the phases of the remaining prefetched chunks
   if (warp == 2)
-    for (int lc = nc + 2; lc < nc + PF; ++lc) wait_chunk(lc);
+    for (int lc = nc + 2; lc < nc + PFD; ++lc) wait_chunk(lc);
   if (warp == 1) cpa_wait<0>();
   if (tail && warp == 0) {     // the last KH positions of the segment's last ng chunks
     const int off = ng * CHK - hist_width(K);
@@ -270,28 +270,28 @@ __device__ void sweep(const SweepSh<T, YT>& sh, const SweepGeom& g, const T* __r
 
 __host__ __device__ inline int n_couplings(int K) { return (K + CHK - 1) / CHK; }
 
-template <typename T>
+template <typename T, int PFD = PF>
 size_t sweep_smem(int K) {
   const int ng = n_couplings(K);
-  size_t b = (size_t)(PF + 1) * (1 + ng) * CHK * CHK * sizeof(T);   // chunk matrices
-  b += (size_t)(PF + 1) * CHK * sizeof(double);                      // Y ring (largest input type)
+  size_t b = (size_t)(PFD + 1) * (1 + ng) * CHK * CHK * sizeof(T);   // chunk matrices
+  b += (size_t)(PFD + 1) * CHK * sizeof(double);                      // Y ring (largest input type)
   b += (size_t)(ng + 1) * CHK * sizeof(T);                           // z history
   b += (size_t)3 * CHK * sizeof(T);                                  // W, yb
   b = (b + 15) & ~(size_t)15;
   b += (size_t)2 * K * sizeof(double);                               // corrections
   b = (b + 15) & ~(size_t)15;
-  b += (size_t)(PF + 1) * sizeof(uint64_t);                          // mbarriers
+  b += (size_t)(PFD + 1) * sizeof(uint64_t);                          // mbarriers
   return b;
 }
 
-template <typename T, typename YT>
+template <typename T, typename YT, int PFD = PF>
 __device__ __forceinline__ SweepSh<T, YT> carve(unsigned char* base, const SweepGeom& g) {
   SweepSh<T, YT> sh;
   size_t off = 0;
   sh.M = reinterpret_cast<T*>(base);
-  off = (size_t)(PF + 1) * (1 + g.ng) * CHK * CHK * sizeof(T);
+  off = (size_t)(PFD + 1) * (1 + g.ng) * CHK * CHK * sizeof(T);
   sh.Y = reinterpret_cast<YT*>(base + off);
-  off += (size_t)(PF + 1) * CHK * sizeof(double);
+  off += (size_t)(PFD + 1) * CHK * sizeof(double);
   sh.zh = reinterpret_cast<T*>(base + off);
   off += (size_t)(g.ng + 1) * CHK * sizeof(T);
   sh.W = reinterpret_cast<T*>(base + off);
@@ -479,7 +479,7 @@ k_seg_correct(const T* __restrict__ Xall, const T* __restrict__ tails, int K, De
 // then the backward sweep of its block.  Measured faster than two launches of
 // k_sweep with S = 1 (125 us against about 150 us per apply on the
 // N = 200000, K = 50, P = 50 FP32 system).
-template <typename T, bool TRANS>
+template <typename T, bool TRANS, int PFD>
 __global__ void __launch_bounds__(NWS * 32)
 k_block_solve(const T* __restrict__ M1all, const T* __restrict__ M2all, const int64_t* __restrict__ cbase, int K,
               Dev d, const double* __restrict__ r_in, double* __restrict__ z_out, T* __restrict__ tmp,
@@ -500,9 +500,9 @@ k_block_solve(const T* __restrict__ M1all, const T* __restrict__ M2all, const in
   unsigned ph = 0;
   bool failed = false;
   {
-    SweepSh<T, double> sh = carve<T, double>(smem_raw, g);
+    SweepSh<T, double> sh = carve<T, double, PFD>(smem_raw, g);
     if (threadIdx.x == 0) {
-      for (int q = 0; q <= PF; ++q) mbar_init(&sh.bar[q], 1);
+      for (int q = 0; q <= PFD; ++q) mbar_init(&sh.bar[q], 1);
       mbar_fence_init();
     }
     for (int t = threadIdx.x; t < K; t += blockDim.x) {
@@ -510,19 +510,19 @@ k_block_solve(const T* __restrict__ M1all, const T* __restrict__ M2all, const in
       sh.corr[K + t] = has_bot ? cbot_all[(int64_t)b * K + t] : 0.0;
     }
     if (!TRANS)
-      sweep<T, double, T, LF>(sh, g, M1all + cbase[b], r_in + s, has_top, has_bot, tmp + s, 0, nch, nullptr, ph,
+      sweep<T, double, T, LF, PFD>(sh, g, M1all + cbase[b], r_in + s, has_top, has_bot, tmp + s, 0, nch, nullptr, ph,
                               failed, err);
     else
-      sweep<T, double, T, UTF>(sh, g, M1all + cbase[b], r_in + s, has_top, has_bot, tmp + s, 0, nch, nullptr, ph,
+      sweep<T, double, T, UTF, PFD>(sh, g, M1all + cbase[b], r_in + s, has_top, has_bot, tmp + s, 0, nch, nullptr, ph,
                                failed, err);
   }
   {
-    SweepSh<T, T> sh = carve<T, T>(smem_raw, g);
+    SweepSh<T, T> sh = carve<T, T, PFD>(smem_raw, g);
     if (!TRANS)
-      sweep<T, T, double, UB>(sh, g, M2all + cbase[b], tmp + s, false, false, z_out + s, 0, nch, nullptr, ph,
+      sweep<T, T, double, UB, PFD>(sh, g, M2all + cbase[b], tmp + s, false, false, z_out + s, 0, nch, nullptr, ph,
                               failed, err);
     else
-      sweep<T, T, double, LTB>(sh, g, M2all + cbase[b], tmp + s, false, false, z_out + s, 0, nch, nullptr, ph,
+      sweep<T, T, double, LTB, PFD>(sh, g, M2all + cbase[b], tmp + s, false, false, z_out + s, 0, nch, nullptr, ph,
                                failed, err);
   }
 }
@@ -634,8 +634,10 @@ cudaError_t launch_block_solve(const Factors<T>& f, int K, int P, Dev d, const d
                                const double* ctop, const double* cbot, cudaStream_t s, Gate gt) {
   cudaError_t e;
   if (f.S == 1) {
-    const size_t smem = sweep_smem<T>(K);
-    auto kern = k_block_solve<T, TRANS>;
+    // four chunks in flight where the ring fits, two for the widest bands
+    const bool deep = sweep_smem<T, PF>(K) <= kSmemPerBlock;
+    const size_t smem = deep ? sweep_smem<T, PF>(K) : sweep_smem<T, 2>(K);
+    auto kern = deep ? k_block_solve<T, TRANS, PF> : k_block_solve<T, TRANS, 2>;
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     count_launches(1);
@@ -655,7 +657,8 @@ cudaError_t launch_block_solve(const Factors<T>& f, int K, int P, Dev d, const d
 
 }  // namespace
 
-size_t sweep_smem_bytes(int K, bool fp64) { return fp64 ? sweep_smem<double>(K) : sweep_smem<float>(K); }
+// the unsegmented sweep's smallest ring (two chunks ahead): the limit on K
+size_t sweep_smem_bytes(int K, bool fp64) { return fp64 ? sweep_smem<double, 2>(K) : sweep_smem<float, 2>(K); }
 int chunk_couplings(int K) { return n_couplings(K); }
 
 // scratch layout (doubles): [0, N) g ; then T tmp (N); then ctop, cbot ((P-1) K each)

@@ -142,6 +142,52 @@ k_chunk_mats(const T* __restrict__ Fall, int K, Dev d, const int64_t* __restrict
   for (int m = 0; m < XR; ++m) M[m * TPC + part] = xr[m];
 }
 
+// The same solves for wide bands (ng > 7 couplings, ng known at run time):
+// one thread per column (32 (1 + ng) threads), the tiles loaded by the first
+// eight warps.  Same rounding order as k_chunk_mats with TPC = 1.
+constexpr int kWideMaxNg = 17;
+constexpr int kWideMaxThreads = CH * (1 + kWideMaxNg);
+
+template <typename T, int MODE>
+__global__ void __launch_bounds__(kWideMaxThreads)
+k_chunk_mats_wide(const T* __restrict__ Fall, int K, int ng, Dev d, const int64_t* __restrict__ cbase,
+                  T* __restrict__ out) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* A = reinterpret_cast<T*>(smem_raw);        // in-chunk block, then B_1 .. B_ng
+  T* Bs = A + CH * LDS;
+  T* Rd = Bs + ng * CH * LDS;
+  const int b = blockIdx.y;
+  const int ld = (int)d.ld[b];
+  const int nch = ld / CH;
+  const int c = blockIdx.x;
+  if (c >= nch) return;
+  const int n = (int)(d.off[b + 1] - d.off[b]);
+  const T* F = Fall + d.fbase[b];
+  const int tid = threadIdx.x;
+  const int p0 = c * CH;
+  if (tid < 8 * 32) {
+    load_tile<MODE, 8>(A, F, K, n, ld, p0, 0, c);
+    for (int k = 1; k <= ng; ++k) load_tile<MODE, 8>(Bs + (k - 1) * CH * LDS, F, K, n, ld, p0, k, c);
+  }
+  __syncthreads();
+  if (tid < CH) Rd[tid] = T(1) / A[tid * LDS + tid];
+  __syncthreads();
+  const int col = tid;
+  const T* Bcol = col >= CH ? Bs + ((col - CH) / CH) * CH * LDS + (col % CH) : nullptr;
+  T xr[CH];
+#pragma unroll
+  for (int r = 0; r < CH; ++r) {
+    T acc = T(0);
+#pragma unroll
+    for (int q = 0; q < r; ++q) acc += A[r * LDS + q] * xr[q];
+    const T rhs = Bcol ? Bcol[r * LDS] : (r == col ? T(1) : T(0));
+    xr[r] = (rhs - acc) * Rd[r];
+  }
+  T* M = out + cbase[b] + (int64_t)c * (1 + ng) * CH * CH + (int64_t)(col / CH) * CH * CH + (col % CH) * CH;
+#pragma unroll
+  for (int m = 0; m < CH; ++m) M[m] = xr[m];
+}
+
 template <typename T, int MODE, int NG>
 void launch_mode(dim3 grid, size_t smem, const T* F, int K, Dev d, const int64_t* cbase, T* out, cudaStream_t s) {
   auto kern = k_chunk_mats<T, MODE, NG>;
@@ -159,19 +205,30 @@ void launch_mode_ng(int ng, dim3 grid, size_t smem, const T* F, int K, Dev d, co
     case 4: launch_mode<T, MODE, 4>(grid, smem, F, K, d, cbase, out, s); break;
     case 5: launch_mode<T, MODE, 5>(grid, smem, F, K, d, cbase, out, s); break;
     case 6: launch_mode<T, MODE, 6>(grid, smem, F, K, d, cbase, out, s); break;
-    default: launch_mode<T, MODE, 7>(grid, smem, F, K, d, cbase, out, s); break;
+    case 7: launch_mode<T, MODE, 7>(grid, smem, F, K, d, cbase, out, s); break;
+    default: {
+      auto kern = k_chunk_mats_wide<T, MODE>;
+      if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      kern<<<grid, CH * (1 + ng), smem, s>>>(F, K, ng, d, cbase, out);
+    } break;
   }
 }
 
 }  // namespace
+
+size_t chunk_mats_smem_bytes(int K, bool fp64) {
+  if ((K + CH - 1) / CH > kWideMaxNg) return ~(size_t)0;     // more couplings than one CTA has columns for
+  return fp64 ? chunk_smem_bytes<double>(K) : chunk_smem_bytes<float>(K);
+}
 
 template <typename T>
 cudaError_t launch_chunk_mats(const T* F, int K, int P, Dev d, const int64_t* cbase, int max_nch, int mode, T* out,
                               cudaStream_t s) {
   dim3 grid(max_nch, P);
   const size_t smem = chunk_smem_bytes<T>(K);
-  count_launches(1);
   const int ng = (K + CH - 1) / CH;
+  if (ng > kWideMaxNg) return cudaErrorInvalidValue;
+  count_launches(1);
   switch (mode) {
     case 0: launch_mode_ng<T, 0>(ng, grid, smem, F, K, d, cbase, out, s); break;
     case 1: launch_mode_ng<T, 1>(ng, grid, smem, F, K, d, cbase, out, s); break;

@@ -88,16 +88,19 @@ __device__ __forceinline__ void ld4(const T* p, T (&v)[4]) {
 
 // Factor one block (rows s .. s+n-1 of the band) with the whole CTA; F: the
 // block's factor storage (LU) or flipped top tiles (REV, ld unused).
-template <typename T, bool REV>
+// GW: the window in global memory at wglob (M2 x LDW, L2-resident) instead
+// of shared memory; wide bands whose (K+16)^2 window does not fit in
+// shared memory use the global form, the staging buffers stay in shared memory.
+template <typename T, bool REV, bool GW>
 __device__ void band_lu_block(unsigned char* smem_raw, const T* __restrict__ band, int64_t N, int K, int64_t s,
                               int n, int64_t ld, T* __restrict__ F, const T tau,
-                              unsigned long long* __restrict__ n_boosted) {
+                              unsigned long long* __restrict__ n_boosted, T* wglob) {
   const int M2 = win_m2(K);
   const int LDW = M2 + 4;
   const int KA = K + NB;          // active rows/cols of the window in a panel step
   const int ME = M2 - NB;         // rows of the next window that are already resident
-  T* W = reinterpret_cast<T*>(smem_raw);
-  size_t woff = ((size_t)M2 * LDW * sizeof(T) + 15) & ~(size_t)15;
+  T* W = GW ? wglob : reinterpret_cast<T*>(smem_raw);
+  const size_t woff = GW ? 0 : ((size_t)M2 * LDW * sizeof(T) + 15) & ~(size_t)15;
   T* ER = reinterpret_cast<T*>(smem_raw + woff);   // NB x M2 entering rows
   T* EC = ER + NB * M2;                              // ME x NB entering columns
   T* RV = EC + ME * NB;                              // NB reciprocals of the panel's pivots
@@ -297,26 +300,29 @@ __device__ void band_lu_block(unsigned char* smem_raw, const T* __restrict__ ban
   if (warp == 0 && lane == 0 && nb) atomicAdd(n_boosted, nb);
 }
 
-template <typename T, bool REV>
+template <typename T, bool REV, bool GW>
 __global__ void __launch_bounds__(NTHREADS)
 k_band_lu(const T* __restrict__ band, int64_t N, int K, Dev d, int block0,
           const double* __restrict__ absmax, double eps, T* __restrict__ out,
-          unsigned long long* __restrict__ n_boosted) {
+          unsigned long long* __restrict__ n_boosted, T* __restrict__ wscratch) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int b = block0 + blockIdx.x;
   const int64_t s = d.off[b];
   const int n = (int)(d.off[b + 1] - s);
   const int64_t ld = REV ? 0 : d.ld[b];
   T* F = REV ? out + (int64_t)(b - 1) * K * K : out + d.fbase[b];
-  band_lu_block<T, REV>(smem_raw, band, N, K, s, n, ld, F, (T)(eps * absmax[0]), n_boosted);
+  const int M2 = win_m2(K);
+  T* wg = GW ? wscratch + (int64_t)blockIdx.x * M2 * (M2 + 4) : nullptr;
+  band_lu_block<T, REV, GW>(smem_raw, band, N, K, s, n, ld, F, (T)(eps * absmax[0]), n_boosted, wg);
 }
 
 // Persistent LU over a work list of blocks of many systems (LuItem, longest
 // first): each CTA takes the next item from an atomic counter until the list
 // is exhausted, so one launch factors every block of a batch.
-template <typename T>
+template <typename T, bool GW>
 __global__ void __launch_bounds__(NTHREADS)
-k_band_lu_items(const LuItem* __restrict__ items, int nitems, unsigned* __restrict__ counter) {
+k_band_lu_items(const LuItem* __restrict__ items, int nitems, unsigned* __restrict__ counter,
+                T* __restrict__ wscratch, int64_t wstride) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int cur;
   for (;;) {
@@ -326,8 +332,9 @@ k_band_lu_items(const LuItem* __restrict__ items, int nitems, unsigned* __restri
     __syncthreads();          // every thread has read cur before it changes
     if (it >= nitems) break;
     const LuItem I = items[it];
-    band_lu_block<T, false>(smem_raw, reinterpret_cast<const T*>(I.band), I.N, I.K, I.s, I.n, I.ld,
-                            reinterpret_cast<T*>(I.F), (T)(I.eps * I.absmax[0]), I.nb);
+    band_lu_block<T, false, GW>(smem_raw, reinterpret_cast<const T*>(I.band), I.N, I.K, I.s, I.n, I.ld,
+                                reinterpret_cast<T*>(I.F), (T)(I.eps * I.absmax[0]), I.nb,
+                                GW ? wscratch + (int64_t)blockIdx.x * wstride : nullptr);
     __syncthreads();
   }
 }
@@ -335,27 +342,36 @@ k_band_lu_items(const LuItem* __restrict__ items, int nitems, unsigned* __restri
 template <typename T, bool REV>
 cudaError_t launch_lu_impl(const T* band, int64_t N, int K, int nblocks, int block0, Dev d,
                            const double* absmax, double eps, T* out, unsigned long long* nb,
-                           cudaStream_t s) {
+                           T* wscratch, cudaStream_t s) {
   if (nblocks <= 0) return cudaSuccess;
-  const int M2 = win_m2(K);
-  const int LDW = M2 + 4;
-  size_t smem = (((size_t)M2 * LDW * sizeof(T) + 15) & ~(size_t)15) +
-                ((size_t)NB * M2 + (size_t)(M2 - NB) * NB + NB) * sizeof(T);
-  auto kern = k_band_lu<T, REV>;
+  const bool gw = lu_window_global(K, sizeof(T) == 8);
+  if (gw && !wscratch) return cudaErrorInvalidValue;
+  const size_t smem = lu_smem_used(K, sizeof(T) == 8, gw);
+  auto kern = gw ? k_band_lu<T, REV, true> : k_band_lu<T, REV, false>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   count_launches(1);
-  kern<<<nblocks, NTHREADS, smem, s>>>(band, N, K, d, block0, absmax, eps, out, nb);
+  kern<<<nblocks, NTHREADS, smem, s>>>(band, N, K, d, block0, absmax, eps, out, nb, wscratch);
   return cudaGetLastError();
 }
 
 }  // namespace
 
-size_t lu_smem_bytes(int K, bool fp64) {
+// shared memory of the factor kernel: window (unless global) + staging
+size_t lu_smem_used(int K, bool fp64, bool global_window) {
   const int M2 = win_m2(K);
   const size_t ts = fp64 ? sizeof(double) : sizeof(float);
-  return (((size_t)M2 * (M2 + 4) * ts + 15) & ~(size_t)15) + ((size_t)NB * M2 + (size_t)(M2 - NB) * NB + NB) * ts;
+  const size_t stage = ((size_t)NB * M2 + (size_t)(M2 - NB) * NB + NB) * ts;
+  if (global_window) return stage;
+  return (((size_t)M2 * (M2 + 4) * ts + 15) & ~(size_t)15) + stage;
 }
+bool lu_window_global(int K, bool fp64) { return lu_smem_used(K, fp64, false) > kSmemPerBlock; }
+size_t lu_window_elems(int K) {
+  const int M2 = win_m2(K);
+  return (size_t)M2 * (M2 + 4);
+}
+
+size_t lu_smem_bytes(int K, bool fp64) { return lu_smem_used(K, fp64, lu_window_global(K, fp64)); }
 
 namespace {
 
@@ -417,48 +433,60 @@ cudaError_t launch_absmax(const double* band, int64_t N, int K, double* out, cud
 
 template <typename T>
 cudaError_t launch_factor_lu(const T* band, int64_t N, int K, int P, Dev d, const double* absmax,
-                             double eps, T* F, unsigned long long* nb, cudaStream_t s) {
-  return launch_lu_impl<T, false>(band, N, K, P, 0, d, absmax, eps, F, nb, s);
+                             double eps, T* F, unsigned long long* nb, T* wscratch, cudaStream_t s) {
+  return launch_lu_impl<T, false>(band, N, K, P, 0, d, absmax, eps, F, nb, wscratch, s);
 }
 
 template <typename T>
 cudaError_t launch_factor_ul(const T* band, int64_t N, int K, int P, Dev d, const double* absmax,
-                             double eps, T* ULt, unsigned long long* nb, cudaStream_t s) {
+                             double eps, T* ULt, unsigned long long* nb, T* wscratch, cudaStream_t s) {
   // UL tiles are only needed for blocks 1..P-1 (the W^(t) tips)
-  return launch_lu_impl<T, true>(band, N, K, P - 1, 1, d, absmax, eps, ULt, nb, s);
+  return launch_lu_impl<T, true>(band, N, K, P - 1, 1, d, absmax, eps, ULt, nb, wscratch, s);
 }
 
-template <typename T>
-cudaError_t launch_factor_lu_items(const LuItem* items, int nitems, int Kmax, unsigned* counter, cudaStream_t s) {
-  if (nitems <= 0) return cudaSuccess;
-  const size_t smem = lu_smem_bytes(Kmax, sizeof(T) == 8);
-  auto kern = k_band_lu_items<T>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
+int lu_items_grid(int nitems, int Kmax, bool fp64) {
+  const size_t smem = lu_smem_bytes(Kmax, fp64);
+  const bool gw = lu_window_global(Kmax, fp64);
   int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NTHREADS, smem);
-  if (e != cudaSuccess) return e;
+  auto occ = [&](auto kern) {
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NTHREADS, smem);
+  };
+  if (fp64) gw ? occ(k_band_lu_items<double, true>) : occ(k_band_lu_items<double, false>);
+  else gw ? occ(k_band_lu_items<float, true>) : occ(k_band_lu_items<float, false>);
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int grid = std::max(1, std::min(nitems, std::max(1, per_sm) * sms));
-  e = cudaMemsetAsync(counter, 0, sizeof(unsigned), s);
+  return std::max(1, std::min(nitems, std::max(1, per_sm) * sms));
+}
+
+template <typename T>
+cudaError_t launch_factor_lu_items(const LuItem* items, int nitems, int Kmax, unsigned* counter, T* wscratch,
+                                   cudaStream_t s) {
+  if (nitems <= 0) return cudaSuccess;
+  const bool fp64 = sizeof(T) == 8;
+  const bool gw = lu_window_global(Kmax, fp64);
+  if (gw && !wscratch) return cudaErrorInvalidValue;
+  const size_t smem = lu_smem_bytes(Kmax, fp64);
+  auto kern = gw ? k_band_lu_items<T, true> : k_band_lu_items<T, false>;
+  const int grid = lu_items_grid(nitems, Kmax, fp64);   // also sets the shared-memory attribute
+  cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned), s);
   if (e != cudaSuccess) return e;
   count_launches(1);
-  kern<<<grid, NTHREADS, smem, s>>>(items, nitems, counter);
+  kern<<<grid, NTHREADS, smem, s>>>(items, nitems, counter, wscratch, (int64_t)lu_window_elems(Kmax));
   return cudaGetLastError();
 }
 
-template cudaError_t launch_factor_lu_items<float>(const LuItem*, int, int, unsigned*, cudaStream_t);
-template cudaError_t launch_factor_lu_items<double>(const LuItem*, int, int, unsigned*, cudaStream_t);
+template cudaError_t launch_factor_lu_items<float>(const LuItem*, int, int, unsigned*, float*, cudaStream_t);
+template cudaError_t launch_factor_lu_items<double>(const LuItem*, int, int, unsigned*, double*, cudaStream_t);
 
 template cudaError_t launch_factor_lu<float>(const float*, int64_t, int, int, Dev, const double*, double,
-                                             float*, unsigned long long*, cudaStream_t);
+                                             float*, unsigned long long*, float*, cudaStream_t);
 template cudaError_t launch_factor_lu<double>(const double*, int64_t, int, int, Dev, const double*, double,
-                                              double*, unsigned long long*, cudaStream_t);
+                                              double*, unsigned long long*, double*, cudaStream_t);
 template cudaError_t launch_factor_ul<float>(const float*, int64_t, int, int, Dev, const double*, double,
-                                             float*, unsigned long long*, cudaStream_t);
+                                             float*, unsigned long long*, float*, cudaStream_t);
 template cudaError_t launch_factor_ul<double>(const double*, int64_t, int, int, Dev, const double*, double,
-                                              double*, unsigned long long*, cudaStream_t);
+                                              double*, unsigned long long*, double*, cudaStream_t);
 
 }  // namespace sap

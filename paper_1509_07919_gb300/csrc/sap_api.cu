@@ -131,6 +131,7 @@ struct Solver : SolverBase {
   Factors<T> f;
   double* scratch = nullptr;   // apply scratch: g (N), T tmp (N), ctop/cbot
   float* bandf = nullptr;      // FP32 copy of the band (FP32 factorisation only)
+  T* wlu = nullptr;            // factor windows in global memory (bands too wide for shared memory)
   bool adjoint_ready = false;
   bool transposed_ready = false;
   explicit Solver(sap_handle* hh) : h(hh) {}
@@ -156,6 +157,7 @@ struct Solver : SolverBase {
     CK(cudaMemset(f.F, 0, (size_t)L.f_elems * sizeof(T)));
     TRY(h->mem.alloc(&scratch, (size_t)(2 * L.N + 2 * nI * K + 8)));
     if (sizeof(T) == 4) TRY(h->mem.alloc(&bandf, (size_t)L.N * L.W));
+    if (lu_window_global(K, sizeof(T) == 8)) TRY(h->mem.alloc(&wlu, (size_t)P * lu_window_elems(K)));
     TRY(h->mem.alloc(&f.err, 1));
     CK(cudaMemset(f.err, 0, sizeof(int)));
     TRY(h->mem.alloc(&f.Mlf, (size_t)L.c_elems));
@@ -241,7 +243,7 @@ struct Solver : SolverBase {
     }
     CK(cudaEventRecord(h->evp[1], s));
     if (h->opt.variant == SAP_C && P > 1) {
-      CK(launch_factor_ul<T>(band_in_T(), L.N, K, P, h->d, h->absmax, eps, f.ULt, h->n_boosted, s));
+      CK(launch_factor_ul<T>(band_in_T(), L.N, K, P, h->d, h->absmax, eps, f.ULt, h->n_boosted, wlu, s));
       CK(cudaEventRecord(h->evp[2], s));
       CK(launch_spikes<T>(h->band, L.N, K, P, h->d, f.F, f.ULt, false, f.V, f.Wt, f.R, f.R0, f.piv,
                           h->singular, s));
@@ -255,7 +257,7 @@ struct Solver : SolverBase {
     const Layout& L = h->L;
     TRY(factor_pre(s));
     CK(launch_factor_lu<T>(band_in_T(), L.N, L.K, L.P, h->d, h->absmax, h->opt.boost_eps, f.F, h->n_boosted,
-                           s));
+                           wlu, s));
     return factor_post(s);
   }
 
@@ -768,6 +770,7 @@ struct sap_batch {
   std::vector<sap_handle*> hs;
   LuItem* items = nullptr;       // device work list of all blocks, longest first
   unsigned* counter = nullptr;   // work-list position of the persistent LU
+  void* wlu = nullptr;           // per-CTA factor windows when Kmax's window exceeds shared memory
   int nitems = 0, Kmax = 1;
   bool fp64 = false;
   cudaEvent_t ev = nullptr;
@@ -775,6 +778,7 @@ struct sap_batch {
     for (sap_handle* h : hs) delete h;
     if (items) cudaFree(items);
     if (counter) cudaFree(counter);
+    if (wlu) cudaFree(wlu);
     if (ev) cudaEventDestroy(ev);
   }
 };
@@ -809,6 +813,14 @@ sap_status_t build_work_list(sap_batch* B) {
     return SAP_ERR_OOM;
   }
   CK(cudaMemcpy(B->items, items.data(), items.size() * sizeof(LuItem), cudaMemcpyHostToDevice));
+  if (lu_window_global(B->Kmax, B->fp64)) {
+    const size_t bytes = (size_t)lu_items_grid(B->nitems, B->Kmax, B->fp64) * lu_window_elems(B->Kmax) *
+                         (B->fp64 ? sizeof(double) : sizeof(float));
+    if (cudaMalloc(&B->wlu, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      return SAP_ERR_OOM;
+    }
+  }
   CK(cudaEventCreateWithFlags(&B->ev, cudaEventDisableTiming));
   return SAP_OK;
 }
@@ -828,8 +840,10 @@ sap_status_t factor_batch(sap_batch* B, cudaStream_t s) {
     CK(cudaEventRecord(h->evj, h->ks));
     CK(cudaStreamWaitEvent(s, h->evj, 0));
   }
-  CK(B->fp64 ? launch_factor_lu_items<double>(B->items, B->nitems, B->Kmax, B->counter, s)
-             : launch_factor_lu_items<float>(B->items, B->nitems, B->Kmax, B->counter, s));
+  CK(B->fp64 ? launch_factor_lu_items<double>(B->items, B->nitems, B->Kmax, B->counter,
+                                              static_cast<double*>(B->wlu), s)
+             : launch_factor_lu_items<float>(B->items, B->nitems, B->Kmax, B->counter,
+                                             static_cast<float*>(B->wlu), s));
   CK(cudaEventRecord(B->ev, s));
   for (sap_handle* h : B->hs) {
     CK(cudaStreamWaitEvent(h->ks, B->ev, 0));
@@ -907,7 +921,9 @@ int64_t sap_kernel_launches(void) { return (int64_t)sap::g_launches.load(); }
 int32_t sap_max_K(int32_t precision) {
   const bool fp64 = precision == SAP_FP64;
   int K = kMaxK;
-  while (K > 1 && (sweep_smem_bytes(K, fp64) > kSmemPerBlock || lu_smem_bytes(K, fp64) > kSmemPerBlock)) --K;
+  while (K > 1 && (sweep_smem_bytes(K, fp64) > kSmemPerBlock || lu_smem_bytes(K, fp64) > kSmemPerBlock ||
+                   chunk_mats_smem_bytes(K, fp64) > kSmemPerBlock))
+    --K;
   return K;
 }
 

@@ -8,9 +8,9 @@
 namespace sap {
 
 // Upper bound of the half-bandwidth searched by sap_max_K; the limit in force
-// is the largest K whose factor window and sweep ring fit in shared memory
-// (208 for FP32, 128 for FP64 factors).
-constexpr int kMaxK = 255;
+// is the largest K whose sweep ring (two chunks ahead at least) and factor
+// staging fit in shared memory (512 for FP32, 256 for FP64 factors).
+constexpr int kMaxK = 600;
 constexpr size_t kSmemPerBlock = 232448;   // opt-in shared memory per CTA on sm_103
 
 // Dynamic shared memory of the sweep and factor kernels for half-bandwidth K.
@@ -18,6 +18,16 @@ size_t sweep_smem_bytes(int K, bool fp64);
 // Coupling matrices per chunk of the blocked sweeps: ceil(K / 32).
 int chunk_couplings(int K);
 size_t lu_smem_bytes(int K, bool fp64);
+// Factor window: in shared memory when it fits, else in a global scratch of
+// lu_window_elems(K) elements per CTA (L2-resident); lu_smem_used gives the
+// shared memory of either form.
+size_t lu_smem_used(int K, bool fp64, bool global_window);
+bool lu_window_global(int K, bool fp64);
+size_t lu_window_elems(int K);
+// CTAs of the persistent work-list LU for nitems items of half-bandwidth <= Kmax.
+int lu_items_grid(int nitems, int Kmax, bool fp64);
+// Shared memory of the chunk-matrix kernel.
+size_t chunk_mats_smem_bytes(int K, bool fp64);
 
 // Factor storage of one block (per block i, local rows/cols 0..n_i-1):
 // "diagonal-major" like the input band, indexed by the column:
@@ -114,14 +124,15 @@ struct LuItem {
   int K, n;                  // half-bandwidth, block rows
 };
 template <typename T>
-cudaError_t launch_factor_lu_items(const LuItem* items, int nitems, int Kmax, unsigned* counter, cudaStream_t s);
+cudaError_t launch_factor_lu_items(const LuItem* items, int nitems, int Kmax, unsigned* counter, T* wscratch,
+                                   cudaStream_t s);
 
 template <typename T>
 cudaError_t launch_factor_lu(const T* band, int64_t N, int K, int P, Dev d, const double* absmax,
-                             double eps, T* F, unsigned long long* n_boosted, cudaStream_t s);
+                             double eps, T* F, unsigned long long* n_boosted, T* wscratch, cudaStream_t s);
 template <typename T>
 cudaError_t launch_factor_ul(const T* band, int64_t N, int K, int P, Dev d, const double* absmax,
-                             double eps, T* ULt, unsigned long long* n_boosted, cudaStream_t s);
+                             double eps, T* ULt, unsigned long long* n_boosted, T* wscratch, cudaStream_t s);
 template <typename T>
 cudaError_t launch_spikes(const double* band, int64_t N, int K, int P, Dev d, const T* F, const T* ULt,
                           bool adjoint, T* V, T* Wt, double* Rinv, double* R0, int* piv, int* singular,

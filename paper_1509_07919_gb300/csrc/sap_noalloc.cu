@@ -60,7 +60,9 @@ sap_status_t run(const double* band, int64_t N, int K, const double* b, double* 
   const size_t c_bytes = align256(c_elems * sizeof(T));
   const size_t a_bytes = align256((size_t)(2 * N + 2 * K + 8) * sizeof(double));
   const size_t b_bytes = sizeof(T) == 4 ? align256((size_t)N * W * sizeof(float)) : 0;   // FP32 band copy
-  if (hdr + f_bytes + 2 * c_bytes + a_bytes + b_bytes > kScratchBytes) return SAP_ERR_INVALID_ARG;
+  const bool gw = lu_window_global(K, sizeof(T) == 8);                                   // factor window
+  const size_t w_bytes = gw ? align256(lu_window_elems(K) * sizeof(T)) : 0;
+  if (hdr + f_bytes + 2 * c_bytes + a_bytes + b_bytes + w_bytes > kScratchBytes) return SAP_ERR_INVALID_ARG;
   void* base = nullptr;
   if (scratch_address(&base) != cudaSuccess) return SAP_ERR_CUDA;
   unsigned char* p = static_cast<unsigned char*>(base);
@@ -73,6 +75,7 @@ sap_status_t run(const double* band, int64_t N, int K, const double* b, double* 
   T* Mub = reinterpret_cast<T*>(p + hdr + f_bytes + c_bytes);
   double* ascratch = reinterpret_cast<double*>(p + hdr + f_bytes + 2 * c_bytes);
   float* bandf = reinterpret_cast<float*>(p + hdr + f_bytes + 2 * c_bytes + a_bytes);
+  T* wlu = gw ? reinterpret_cast<T*>(p + hdr + f_bytes + 2 * c_bytes + a_bytes + b_bytes) : nullptr;
   const int64_t h_desc[5] = {0, N, 0, ld, 0};
   if (cudaMemcpyAsync(desc, h_desc, sizeof(h_desc), cudaMemcpyHostToDevice, s) != cudaSuccess) return SAP_ERR_CUDA;
   // counters start at zero; factor padding columns are read as zeros by the sweeps
@@ -89,7 +92,7 @@ sap_status_t run(const double* band, int64_t N, int K, const double* b, double* 
     if (launch_absmax(band, N, K, absmax, s) != cudaSuccess) return SAP_ERR_CUDA;
     bandT = reinterpret_cast<const T*>(band);
   }
-  if (launch_factor_lu<T>(bandT, N, K, 1, d, absmax, eps, F, nb, s) != cudaSuccess) return SAP_ERR_CUDA;
+  if (launch_factor_lu<T>(bandT, N, K, 1, d, absmax, eps, F, nb, wlu, s) != cudaSuccess) return SAP_ERR_CUDA;
   const int64_t* cbase = desc + 4;
   if (launch_chunk_mats<T>(F, K, 1, d, cbase, (int)(ld / 32), 0, Mlf, s) != cudaSuccess) return SAP_ERR_CUDA;
   if (launch_chunk_mats<T>(F, K, 1, d, cbase, (int)(ld / 32), 1, Mub, s) != cudaSuccess) return SAP_ERR_CUDA;

@@ -154,6 +154,22 @@ def test_batch_of_64_uneven_systems(sap):
         assert relerr(host(xs[i]), xo) <= 1e-8
 
 
+def test_batch_with_a_wide_band_system(sap):
+    """One system's window exceeds shared memory (K = 300): the persistent LU
+    keeps every CTA's window in global memory."""
+    specs = [(3000, 300, 41), (2500, 20, 42), (5000, 64, 43)]
+    bands, xts, bs = make_batch(specs, 1.0)
+    Ns = [s[0] for s in specs]
+    Ks = [s[1] for s in specs]
+    bh = sap.sap_factor_batched([dev(b) for b in bands], Ns, Ks, P=2, precision=sap.SAP_FP32)
+    xs, infos, stats, st = sap.sap_solve_batched(bh, [dev(b) for b in bs])
+    assert st == sap.SAP_OK
+    for i, (N, K, _) in enumerate(specs):
+        assert infos[i].relres <= 1e-10
+        xo, _, _ = O.solve(bands[i], N, K, bs[i], 2, O.SAP_D)
+        assert relerr(host(xs[i]), xo) <= 1e-8, (i, relerr(host(xs[i]), xo))
+
+
 def test_batched_invalid_arguments(sap):
     band = dev(G.dense_banded(100, 3, 1.0, 5))
     with pytest.raises(sap.SapError):

@@ -68,8 +68,9 @@ def test_spmv_parity(sap, N, K):
 # ------------------------------------------------------------- factors --
 
 @pytest.mark.parametrize("N,K,P", [(2000, 10, 8), (4003, 50, 4), (997, 33, 5), (600, 1, 3), (1500, 64, 2),
-                                   (700, 90, 3)])
+                                   (700, 90, 3), (1000, 128, 2), (1200, 129, 2), (1100, 256, 2)])
 def test_block_lu_parity_fp64(sap, N, K, P):
+    """K <= 128: the factor window in shared memory; K > 128: in global memory."""
     band, _, _ = make(N, K, 1.0, 200 + K)
     h = sap.sap_factor(dev(band), N, K, P=P, variant=sap.SAP_D, precision=sap.SAP_FP64)
     o = O.Sap(band, N, K, P, O.SAP_D)
@@ -81,8 +82,10 @@ def test_block_lu_parity_fp64(sap, N, K, P):
 
 
 @pytest.mark.parametrize("N,K,P", [(4003, 50, 4), (2000, 10, 8), (700, 100, 3), (1000, 127, 3), (1300, 200, 2),
-                                   (900, 208, 2)])
+                                   (900, 208, 2), (900, 209, 2), (1700, 400, 2), (1500, 512, 2)])
 def test_block_lu_parity_fp32(sap, N, K, P):
+    """K <= 208: the factor window in shared memory; K > 208: in global memory
+    (the last case with blocks narrower than the band)."""
     band, _, _ = make(N, K, 1.0, 300 + K)
     h = sap.sap_factor(dev(band), N, K, P=P, variant=sap.SAP_D, precision=sap.SAP_FP32)
     o = O.Sap(band, N, K, P, O.SAP_D)
@@ -244,13 +247,13 @@ def test_invalid_arguments(sap):
         sap.sap_factor(band, N, N, P=1)                            # K >= N
     with pytest.raises(sap.SapError):
         sap.sap_factor(band, N, K, P=0)
-    # above the shared-memory limits of the factor window / sweep ring
-    assert sap.sap_max_K(sap.SAP_FP64) == 128 and sap.sap_max_K(sap.SAP_FP32) == 208
+    # above the shared-memory limit of the sweep ring (two chunks ahead)
+    assert sap.sap_max_K(sap.SAP_FP64) == 256 and sap.sap_max_K(sap.SAP_FP32) == 512
     with pytest.raises(sap.SapError) as e:
-        sap.sap_factor(dev(G.dense_banded(600, 150, 1.0, 1)), 600, 150, P=1, precision=sap.SAP_FP64)
+        sap.sap_factor(dev(G.dense_banded(600, 257, 1.0, 1)), 600, 257, P=1, precision=sap.SAP_FP64)
     assert e.value.status == sap.SAP_ERR_NOT_IMPLEMENTED
     with pytest.raises(sap.SapError) as e:
-        sap.sap_factor(dev(G.dense_banded(600, 209, 1.0, 1)), 600, 209, P=1, precision=sap.SAP_FP32)
+        sap.sap_factor(dev(G.dense_banded(1100, 513, 1.0, 1)), 1100, 513, P=1, precision=sap.SAP_FP32)
     assert e.value.status == sap.SAP_ERR_NOT_IMPLEMENTED
     with pytest.raises(sap.SapError) as e:          # SaP-C spike tips: K <= 120 in FP32
         sap.sap_factor(dev(G.dense_banded(2000, 150, 1.0, 1)), 2000, 150, P=4, variant=sap.SAP_C,
@@ -294,10 +297,13 @@ def test_not_converged_status(sap):
         assert info.relres > 1e-10
 
 
-@pytest.mark.parametrize("N,K,P,prec", [(20000, 200, 10, 1), (12000, 128, 6, 0), (9000, 170, 5, 1)])
+@pytest.mark.parametrize("N,K,P,prec", [(20000, 200, 10, 1), (12000, 128, 6, 0), (9000, 170, 5, 1),
+                                        (12000, 400, 6, 1), (8000, 250, 4, 0), (9000, 300, 3, 1)])
 def test_wide_band_solve_parity(sap, N, K, P, prec):
-    """Wide bands (K > 127, SaP-D; C3's K = 200): 4 + couplings per chunk,
-    unsegmented sweeps; FP32 up to K = 208, FP64 up to K = 128."""
+    """Wide bands (K > 127, SaP-D; K = 200 and 400 of the K sweep): 4 + couplings
+    per chunk, unsegmented sweeps; above K = 208 (FP32) / 128 (FP64) the factor
+    window lives in global memory, above K = 288 (FP32) / 128 (FP64) the sweep
+    prefetches two chunks ahead instead of four."""
     band, xt, b = make(N, K, 1.0, 900 + K)
     xo, io, _ = O.solve(band, N, K, b, P, O.SAP_D)
     h = sap.sap_factor(dev(band), N, K, P=P, precision=prec)

@@ -33,9 +33,11 @@ def _noalloc(S, band, N, K, b, x, prec):
               ctypes.c_void_p(x.data_ptr()), prec, ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
 
 
-@pytest.mark.parametrize("prec,tol", [(0, 1e-11), (1, 1e-4)])
-@pytest.mark.parametrize("N,K", [(20011, 25), (4000, 50)])
+@pytest.mark.parametrize("prec,tol,N,K", [(0, 1e-11, 20011, 25), (0, 1e-11, 4000, 50), (1, 1e-4, 20011, 25),
+                                          (1, 1e-4, 4000, 50), (0, 1e-11, 2500, 200), (1, 1e-4, 3000, 300)])
 def test_noalloc_matches_allocating_path_twice(sap, prec, tol, N, K):
+    """The last two sizes put the factor window in the scratch array (bands
+    too wide for a shared-memory window)."""
     band_np = G.dense_banded(N, K, 1.0, 4242 + K)
     band = torch.from_numpy(band_np).cuda()
     h = sap.sap_factor(band, N, K, P=1, variant=sap.SAP_D, precision=prec)

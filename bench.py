@@ -32,10 +32,20 @@ METRIC = "time to rel.res 1e-10 & HBM GB/s: FP32-precond vs FP64 SaP, fwd+adjoin
 # apply on the N=200000, K=50, P=50 workload (automatic segment count), from the
 # ncu capture summarised in profiles/k_sweep_n200k_k50_fp32.md
 TRAFFIC_SWEEPS = 232812800
+# P=None: picked by sap_autotune (measured refactor + solve over N / {16000 .. 1000})
+# before the timed region; P_ref is the oracle's partition count in that case
+# (the autotuner's pick on GB300 when this table was written).
 WORKLOADS = {
     "n200k_k50": dict(N=200000, K=50, d=1.0, P=50, seed_cfg=2),
     "n10k_k10": dict(N=10000, K=10, d=1.2, P=8, seed_cfg=1),
+    "n200k_k100": dict(N=200000, K=100, d=1.0, P=None, P_ref=200, seed_cfg=3),
+    "n200k_k200": dict(N=200000, K=200, d=1.0, P=None, P_ref=100, seed_cfg=3),
+    "n200k_k400": dict(N=200000, K=400, d=1.0, P=None, P_ref=200, seed_cfg=3),
+    "convdiff_400x250": dict(N=100000, K=250, d=None, P=32, seed_cfg=4, grid=(400, 250), variant="C"),
 }
+# oracle work (multiply-adds of the factorisations, forward + adjoint) above
+# which the CPU baseline times a leading sample of the blocks and scales by rows
+ORACLE_FULL_LIMIT = 1.5e10
 
 
 def parse():
@@ -46,10 +56,14 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="n200k_k50", choices=sorted(WORKLOADS) + ["batch64"],
                     help="batch64: 64 systems N ~ U{1e4..1e5}, K ~ U{8..64} through the batched API")
-    ap.add_argument("--variant", default="D", choices=["C", "D"])
+    ap.add_argument("--variant", default=None, choices=["C", "D"],
+                    help="SaP variant (default: the workload's, else D)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-compare", action="store_true", help="skip the FP64 / other-variant comparison runs")
-    return ap.parse_args()
+    a = ap.parse_args()
+    if a.variant is None:
+        a.variant = WORKLOADS.get(a.workload, {}).get("variant", "D")
+    return a
 
 
 def load_peaks():
@@ -65,7 +79,11 @@ def load_peaks():
 def make_inputs(w):
     import sap_inputs as G
     seed = G.config_seed(w["seed_cfg"])
-    band = G.dense_banded(w["N"], w["K"], w["d"], seed)
+    if "grid" in w:
+        band, N, K = G.convection_diffusion(*w["grid"])
+        assert (N, K) == (w["N"], w["K"])
+    else:
+        band = G.dense_banded(w["N"], w["K"], w["d"], seed)
     xt = G.x_true(w["N"], seed)
     g = G.adjoint_seed(w["N"], seed)
     return band, xt, g
@@ -73,10 +91,34 @@ def make_inputs(w):
 
 # ------------------------------------------------------------- CPU oracle --
 
+def oracle_P(w):
+    return w["P"] if w["P"] is not None else w["P_ref"]
+
+
+def oracle_sample(w, variant, band, xt, g):
+    """The oracle's inputs: the whole workload, or (too much work for a bounded
+    CPU run) the leading principal sub-system of its first m blocks, with
+    b = A_s x_true_s; returns (w_s, band_s, b_s, g_s, rows scale, description)."""
+    import numpy as np
+    import oracle as O
+    N, K, P = w["N"], w["K"], oracle_P(w)
+    per_row = (2 if variant == "C" else 1) * 2 * K * K
+    if per_row * N <= ORACLE_FULL_LIMIT:
+        return dict(w, P=P), band, O.spmv(band, N, K, xt), g, 1.0, "the full workload"
+    n = N // P
+    m = max(2 if variant == "C" else 1, int(ORACLE_FULL_LIMIT // (per_row * n)))
+    Ns = m * n
+    band_s = np.ascontiguousarray(band.reshape(2 * K + 1, N)[:, :Ns]).reshape(-1)
+    ws = dict(w, N=Ns, P=m)
+    return (ws, band_s, O.spmv(band_s, Ns, K, xt[:Ns]), np.ascontiguousarray(g[:Ns]), N / Ns,
+            f"the leading {m} of {P} blocks ({Ns} of {N} rows, the principal sub-system), time scaled by "
+            f"rows x{N / Ns:.2f}")
+
+
 def oracle_step(band, b, g, w, variant):
     """One fwd + adjoint time-to-solution with the FP64 CPU oracle."""
     import oracle as O
-    N, K, P = w["N"], w["K"], w["P"]
+    N, K, P = w["N"], w["K"], oracle_P(w)
     var = O.SAP_C if variant == "C" else O.SAP_D
     s = O.Sap(band, N, K, P, var)
     x, i1 = s.solve(b)
@@ -85,16 +127,16 @@ def oracle_step(band, b, g, w, variant):
     return i1, i2
 
 
-def cpu_baseline(w, variant, band, b, g, reps=1):
-    import oracle as O  # noqa: F401
+def cpu_baseline(w, variant, band, xt, g, reps=1):
+    ws, band_s, b_s, g_s, scale, what = oracle_sample(w, variant, band, xt, g)
     ts = []
     for _ in range(reps):
         t0 = time.perf_counter()
-        oracle_step(band, b, g, w, variant)
-        ts.append((time.perf_counter() - t0) * 1e3)
+        oracle_step(band_s, b_s, g_s, ws, variant)
+        ts.append((time.perf_counter() - t0) * 1e3 * scale)
     return {"value": statistics.median(ts), "unit": "ms", "cores": 1, "kind": "oracle",
-            "sample": f"the full workload, {reps} run(s) of factor + solve + adjoint solve "
-                      f"(single-threaded FP64 C oracle, SaP-{variant})"}
+            "sample": f"{what}, {reps} run(s) of factor + solve + adjoint solve "
+                      f"(single-threaded FP64 C oracle, SaP-{variant}, P = {oracle_P(w)} for the workload)"}
 
 
 def run_reference_batch(args):
@@ -150,32 +192,37 @@ def run_reference(args):
         run_reference_batch(args)
         return
     w = WORKLOADS[args.workload]
-    import oracle as O
     band, xt, g = make_inputs(w)
-    b = O.spmv(band, w["N"], w["K"], xt)
+    ws, band_s, b_s, g_s, scale, what = oracle_sample(w, args.variant, band, xt, g)
     for _ in range(args.warmup):
-        oracle_step(band, b, g, w, args.variant)
+        oracle_step(band_s, b_s, g_s, ws, args.variant)
     ts = []
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        oracle_step(band, b, g, w, args.variant)
-        ts.append((time.perf_counter() - t0) * 1e3)
+        oracle_step(band_s, b_s, g_s, ws, args.variant)
+        ts.append((time.perf_counter() - t0) * 1e3 * scale)
     v = statistics.mean(ts)
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "ms", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": v, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": workload_config(args, w),
             "cpu_baseline": {"value": v, "unit": "ms", "cores": 1, "kind": "oracle",
-                             "sample": "each step: the full workload, factor + solve + adjoint solve "
-                                       "(single-threaded FP64 C oracle)"},
+                             "sample": f"each step: {what}, factor + solve + adjoint solve "
+                                       f"(single-threaded FP64 C oracle, P = {oracle_P(w)} for the workload)"},
             "e2e": {"value": v, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
 def workload_config(args, w):
-    return {"workload": f"dense banded N={w['N']} K={w['K']} d={w['d']} P={w['P']} SaP-{args.variant}, "
+    Ptxt = "autotuned" if w["P"] is None else w["P"]
+    if "grid" in w:
+        kind = (f"2-D convection-diffusion {w['grid'][0]}x{w['grid'][1]} (5-point upwind, Peclet 10) as a dense "
+                f"band N={w['N']} K={w['K']}")
+    else:
+        kind = f"dense banded N={w['N']} K={w['K']} d={w['d']}"
+    return {"workload": f"{kind} P={Ptxt} SaP-{args.variant}, "
                         f"FP32 preconditioner + FP64 BiCGStab(2), fwd + adjoint to relres 1e-10",
-            "N": w["N"], "K": w["K"], "P": w["P"], "d": w["d"], "variant": f"SaP-{args.variant}",
+            "N": w["N"], "K": w["K"], "P": Ptxt, "d": w["d"], "variant": f"SaP-{args.variant}",
             "l2": "flushed (512 MB write) before every timed step"}
 
 
@@ -241,6 +288,10 @@ def run_gpu(args):
     b = S.sap_spmv(band, N, K, xt)
     stream = torch.cuda.current_stream()
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    autotune = None
+    if P is None:       # measured choice, outside the timed region
+        P, _, table = S.sap_autotune(band, N, K, b=b, variant=variant, precision=S.SAP_FP32)
+        autotune = {"P": P, "ms_by_P_segments": {f"{p},{sg}": v for (p, sg), v in sorted(table.items())}}
 
     def make_handle(prec, var):
         return S.sap_factor(band, N, K, P=P, variant=var, precision=prec)
@@ -387,7 +438,11 @@ def run_gpu(args):
     if not args.no_compare:
         for name, prec, var in (("sapc_fp64", S.SAP_FP64, S.SAP_C), ("sapd_fp64", S.SAP_FP64, S.SAP_D),
                                 ("sapc_fp32", S.SAP_FP32, S.SAP_C), ("sapd_fp32", S.SAP_FP32, S.SAP_D)):
-            hh = make_handle(prec, var)
+            try:
+                hh = make_handle(prec, var)
+            except S.SapError as e:
+                compare[name] = {"unavailable": str(e)}
+                continue
             tt, inf, _, _, _, _ = timed(hh, max(3, args.steps // 2), 2)
             a, c = inf[-1]
             compare[name] = {"ms": statistics.mean(tt), "iters_fwd": a.iters, "iters_adj": c.iters,
@@ -398,7 +453,7 @@ def run_gpu(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(w, args.variant, band_np, b.cpu().numpy(), g_np)
+        cpu = cpu_baseline(w, args.variant, band_np, xt_np, g_np)
 
     if rank == 0:
         # replicas: every rank solves its own system; job-level time per system
@@ -415,7 +470,8 @@ def run_gpu(args):
             "gpu_launches": int(launches),
             "roofline": roofline,
             "cpu_baseline": cpu,
-            "detail": {"sweep_segments_per_block": i1.segments, "krylov_graph": bool(i1.graphed),
+            "detail": {"P": P, "autotune": autotune,
+                       "sweep_segments_per_block": i1.segments, "krylov_graph": bool(i1.graphed),
                        "iters_fwd": i1.iters, "iters_adj": i2.iters, "matvecs_fwd": i1.n_matvec,
                        "matvecs_adj": i2.n_matvec, "restarts_fwd": i1.n_restarts,
                        "restarts_adj": i2.n_restarts, "relres_fwd": i1.relres,

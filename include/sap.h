@@ -111,8 +111,7 @@ SAP_API void sap_default_options(sap_options_t *opt);
  *   N >= 2, 1 <= K < N.  SaP-C needs every block to have >= 2K rows.
  *   *out receives a new handle owning all other device memory.
  * Errors: INVALID_ARG (sizes, options, N_i < 2K for SaP-C), NOT_IMPLEMENTED
- * (K above sap_max_K, or above the SaP-C spike limit: 98 in FP64, 120 in
- * FP32), OOM, SINGULAR, CUDA.  Synchronises `stream`. */
+ * (K above sap_max_K), OOM, SINGULAR, CUDA.  Synchronises `stream`. */
 SAP_API sap_status_t sap_factor(const double *band_dev, int64_t N, int32_t K,
                         const sap_options_t *opt, cudaStream_t stream,
                         sap_handle_t *out);
@@ -271,7 +270,10 @@ SAP_API sap_status_t sap_batch_destroy(sap_batch_t b);
  * (host-side counter, all handles and threads). */
 SAP_API int64_t sap_kernel_launches(void);
 
-/* Largest half-bandwidth K this build factors, per precision. */
+/* Largest half-bandwidth K this build factors, per precision (both variants):
+ * 512 with FP32 factors, 256 with FP64 factors.  The limit is the sweep's
+ * shared-memory ring of per-chunk matrices; factor windows and spike
+ * workspaces that exceed shared memory move to global memory. */
 SAP_API int32_t sap_max_K(int32_t precision);
 
 #ifdef __cplusplus

@@ -12,7 +12,8 @@
 // couplings B'_i = C_{i+1}^T, C'_{i+1} = B_i^T:
 //     V'^(b)_i     = L_bb^{-T} U_bb^{-T} C_{i+1}^T
 //     W'^(t)_{i+1} = U'_tt^{-T} L'_tt^{-T} B_i^T
-// One CTA per interface; K x K working matrices in shared memory.
+// One CTA per interface; K x K working matrices in shared memory, or (wide
+// bands, GM) in a per-interface global scratch that stays L2-resident.
 #include <cuda_runtime.h>
 #include <cstdint>
 #include "sap_internal.cuh"
@@ -62,17 +63,27 @@ __device__ void tri_col(const T* M, int K, bool lower, bool unit, bool trans, T*
   }
 }
 
-template <typename T>
+// Bytes of one interface's working matrices: R (FP64), factor tile and
+// right-hand sides (T), the latter two reused as one FP64 K x K workspace for
+// the inverse (2 sizeof(T) >= 8).
+__host__ __device__ inline size_t spike_ws_bytes(int K, int tsize) {
+  return (size_t)K * K * (sizeof(double) + 2 * (size_t)tsize);
+}
+__host__ __device__ inline size_t spike_ws_stride(int K, int tsize) { return (spike_ws_bytes(K, tsize) + 255) & ~(size_t)255; }
+
+template <typename T, bool GM>
 __global__ void __launch_bounds__(NT)
 k_spikes(const double* __restrict__ band, int64_t N, int K, Dev d, const T* __restrict__ F,
          const T* __restrict__ ULt, bool adjoint, T* __restrict__ Vout, T* __restrict__ Wout,
-         double* __restrict__ Rinv, double* __restrict__ R0, int* __restrict__ pivout, int* singular) {
+         double* __restrict__ Rinv, double* __restrict__ R0, int* __restrict__ pivout, int* singular,
+         unsigned char* __restrict__ gws) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int KK = K * K;
-  double* R = reinterpret_cast<double*>(smem_raw);            // K x K FP64
+  unsigned char* ws = GM ? gws + (size_t)blockIdx.x * spike_ws_stride(K, sizeof(T)) : smem_raw;
+  double* R = reinterpret_cast<double*>(ws);                   // K x K FP64
   T* Mx = reinterpret_cast<T*>(R + KK);                        // K x K factor tile
   T* X = Mx + KK;                                              // K x K right-hand sides / tips
-  __shared__ int pivs[128];          // K <= 120 for the spike kernel (its shared-memory limit)
+  int* pivs = reinterpret_cast<int*>(smem_raw + (GM ? 0 : spike_ws_bytes(K, sizeof(T))));   // K pivots
   __shared__ double red_v[NT / 32];
   __shared__ int red_i[NT / 32];
 
@@ -209,24 +220,35 @@ k_spikes(const double* __restrict__ band, int64_t N, int K, Dev d, const T* __re
 
 }  // namespace
 
+size_t spike_scratch_bytes(int K, int P, bool fp64) {
+  const int ts = fp64 ? 8 : 4;
+  if (P < 2 || spike_ws_bytes(K, ts) + (size_t)K * sizeof(int) <= kSmemPerBlock) return 0;
+  return (size_t)(P - 1) * spike_ws_stride(K, ts);
+}
+
 template <typename T>
 cudaError_t launch_spikes(const double* band, int64_t N, int K, int P, Dev d, const T* F, const T* ULt,
                           bool adjoint, T* V, T* Wt, double* Rinv, double* R0, int* piv, int* singular,
-                          cudaStream_t s) {
+                          void* gscratch, cudaStream_t s) {
   if (P < 2) return cudaSuccess;
-  // R (FP64 K x K) + factor tile + right-hand sides (T); the latter two are
-  // reused as one FP64 K x K workspace for the inverse (2 sizeof(T) >= 8).
-  size_t smem = (size_t)K * K * (sizeof(double) + 2 * sizeof(T));
-  cudaError_t e = cudaFuncSetAttribute(k_spikes<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
+  const bool gm = spike_scratch_bytes(K, P, sizeof(T) == 8) > 0;
+  if (gm && !gscratch) return cudaErrorInvalidValue;
+  const size_t smem = (gm ? 0 : spike_ws_bytes(K, sizeof(T))) + (size_t)K * sizeof(int);
+  auto kern = gm ? k_spikes<T, true> : k_spikes<T, false>;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
   count_launches(1);
-  k_spikes<T><<<P - 1, NT, smem, s>>>(band, N, K, d, F, ULt, adjoint, V, Wt, Rinv, R0, piv, singular);
+  kern<<<P - 1, NT, smem, s>>>(band, N, K, d, F, ULt, adjoint, V, Wt, Rinv, R0, piv, singular,
+                               static_cast<unsigned char*>(gscratch));
   return cudaGetLastError();
 }
 
 template cudaError_t launch_spikes<float>(const double*, int64_t, int, int, Dev, const float*, const float*, bool,
-                                          float*, float*, double*, double*, int*, int*, cudaStream_t);
+                                          float*, float*, double*, double*, int*, int*, void*, cudaStream_t);
 template cudaError_t launch_spikes<double>(const double*, int64_t, int, int, Dev, const double*, const double*,
-                                           bool, double*, double*, double*, double*, int*, int*, cudaStream_t);
+                                           bool, double*, double*, double*, double*, int*, int*, void*,
+                                           cudaStream_t);
 
 }  // namespace sap

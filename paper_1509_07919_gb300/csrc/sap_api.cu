@@ -132,6 +132,7 @@ struct Solver : SolverBase {
   double* scratch = nullptr;   // apply scratch: g (N), T tmp (N), ctop/cbot
   float* bandf = nullptr;      // FP32 copy of the band (FP32 factorisation only)
   T* wlu = nullptr;            // factor windows in global memory (bands too wide for shared memory)
+  void* wspk = nullptr;        // spike-kernel workspaces in global memory (same)
   bool adjoint_ready = false;
   bool transposed_ready = false;
   explicit Solver(sap_handle* hh) : h(hh) {}
@@ -179,6 +180,12 @@ struct Solver : SolverBase {
       TRY(h->mem.alloc(&f.R, (size_t)(nI * KK)));
       TRY(h->mem.alloc(&f.R0, (size_t)(nI * KK)));
       TRY(h->mem.alloc(&f.piv, (size_t)(nI * K)));
+      const size_t sb = spike_scratch_bytes(K, P, sizeof(T) == 8);
+      if (sb) {
+        unsigned char* q = nullptr;
+        TRY(h->mem.alloc(&q, sb));
+        wspk = q;
+      }
     }
     return SAP_OK;
   }
@@ -246,7 +253,7 @@ struct Solver : SolverBase {
       CK(launch_factor_ul<T>(band_in_T(), L.N, K, P, h->d, h->absmax, eps, f.ULt, h->n_boosted, wlu, s));
       CK(cudaEventRecord(h->evp[2], s));
       CK(launch_spikes<T>(h->band, L.N, K, P, h->d, f.F, f.ULt, false, f.V, f.Wt, f.R, f.R0, f.piv,
-                          h->singular, s));
+                          h->singular, wspk, s));
     } else {
       CK(cudaEventRecord(h->evp[2], s));
     }
@@ -273,7 +280,7 @@ struct Solver : SolverBase {
       TRY(h->mem.alloc(&f.piva, (size_t)(nI * K)));
     }
     CK(launch_spikes<T>(h->band, h->L.N, K, h->L.P, h->d, f.F, f.ULt, true, f.Va, f.Wa, f.Ra, f.Ra0, f.piva,
-                        h->singular, s));
+                        h->singular, wspk, s));
     int sing = 0;
     CK(cudaMemcpyAsync(&sing, h->singular, sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
@@ -409,9 +416,6 @@ sap_status_t check_options(const sap_options_t* o, int64_t N, int K) {
   if (o->segments < 0 || o->reserved0 != 0) return SAP_ERR_INVALID_ARG;
   return SAP_OK;
 }
-
-// Largest K of the SaP-C spike kernel: 8 K^2 + 2 sizeof(T) K^2 bytes of shared memory.
-int max_K_spikes(int precision) { return precision == SAP_FP64 ? 98 : 120; }
 
 // The handle's internal stream and its fork/join events, created on first use.
 sap_status_t ensure_stream(sap_handle* h) {
@@ -672,7 +676,6 @@ sap_status_t create_handle(const double* band_dev, int64_t N, int32_t K, const s
   if (!(opt.tol > 0.0)) opt.tol = 1e-10;
   if (!(opt.boost_eps > 0.0)) opt.boost_eps = opt.precision == SAP_FP64 ? 0x1p-53 : 0x1p-24;
   if (K > sap_max_K(opt.precision)) return SAP_ERR_NOT_IMPLEMENTED;
-  if (opt.variant == SAP_C && opt.P > 1 && K > max_K_spikes(opt.precision)) return SAP_ERR_NOT_IMPLEMENTED;
   out.reset(new (std::nothrow) sap_handle());
   if (!out) return SAP_ERR_OOM;
   sap_handle* h = out.get();

@@ -136,7 +136,10 @@ cudaError_t launch_factor_ul(const T* band, int64_t N, int K, int P, Dev d, cons
 template <typename T>
 cudaError_t launch_spikes(const double* band, int64_t N, int K, int P, Dev d, const T* F, const T* ULt,
                           bool adjoint, T* V, T* Wt, double* Rinv, double* R0, int* piv, int* singular,
-                          cudaStream_t s);
+                          void* gscratch, cudaStream_t s);
+// Global scratch of the spike kernel (0 when its K x K matrices fit in shared
+// memory): one workspace per interface, shared by the forward and adjoint tips.
+size_t spike_scratch_bytes(int K, int P, bool fp64);
 template <typename T>
 cudaError_t launch_chunk_mats(const T* F, int K, int P, Dev d, const int64_t* cbase, int max_nch, int mode, T* out,
                               cudaStream_t s);

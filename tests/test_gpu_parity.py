@@ -95,8 +95,10 @@ def test_block_lu_parity_fp32(sap, N, K, P):
 
 
 @pytest.mark.parametrize("prec,tol", [(0, 1e-11), (1, 2e-4)])
-@pytest.mark.parametrize("N,K,P", [(1200, 10, 5), (3001, 40, 6), (900, 64, 3)])
+@pytest.mark.parametrize("N,K,P", [(1200, 10, 5), (3001, 40, 6), (900, 64, 3), (2100, 99, 3), (1500, 130, 3)])
 def test_spike_tips_and_rbar_parity(sap, N, K, P, prec, tol):
+    """K = 99 (FP64) and K = 130 (both precisions) put the spike kernel's K x K
+    matrices in its global workspace."""
     band, _, _ = make(N, K, 1.0, 400 + K)
     h = sap.sap_factor(dev(band), N, K, P=P, variant=sap.SAP_C, precision=prec)
     o = O.Sap(band, N, K, P, O.SAP_C)
@@ -255,9 +257,9 @@ def test_invalid_arguments(sap):
     with pytest.raises(sap.SapError) as e:
         sap.sap_factor(dev(G.dense_banded(1100, 513, 1.0, 1)), 1100, 513, P=1, precision=sap.SAP_FP32)
     assert e.value.status == sap.SAP_ERR_NOT_IMPLEMENTED
-    with pytest.raises(sap.SapError) as e:          # SaP-C spike tips: K <= 120 in FP32
-        sap.sap_factor(dev(G.dense_banded(2000, 150, 1.0, 1)), 2000, 150, P=4, variant=sap.SAP_C,
-                       precision=sap.SAP_FP32)
+    with pytest.raises(sap.SapError) as e:          # the same limit for SaP-C
+        sap.sap_factor(dev(G.dense_banded(4000, 257, 1.0, 1)), 4000, 257, P=2, variant=sap.SAP_C,
+                       precision=sap.SAP_FP64)
     assert e.value.status == sap.SAP_ERR_NOT_IMPLEMENTED
 
 
@@ -316,6 +318,37 @@ def test_wide_band_solve_parity(sap, N, K, P, prec):
     assert ast == sap.SAP_OK and relerr(host(lam), lo) <= 1e-8
 
 
+@pytest.mark.parametrize("N,K,P,prec", [(8000, 250, 4, 1), (6000, 150, 3, 0), (5000, 121, 4, 1)])
+def test_wide_band_sapc_solve_parity(sap, N, K, P, prec):
+    """SaP-C with wide bands: UL windows and spike workspaces in global memory
+    (K > 120 in FP32, K > 98 in FP64); forward and adjoint against the oracle."""
+    band, xt, b = make(N, K, 1.0, 930 + K)
+    xo, io, _ = O.solve(band, N, K, b, P, O.SAP_C)
+    h = sap.sap_factor(dev(band), N, K, P=P, variant=sap.SAP_C, precision=prec)
+    x, info, st = sap.sap_solve(h, dev(b))
+    assert st == sap.SAP_OK and info.relres <= 1e-10
+    assert relerr(host(x), xo) <= 1e-8
+    g = G.adjoint_seed(N, 930 + K)
+    lo, _, _ = O.solve_adjoint(band, N, K, g, P, O.SAP_C)
+    lam, ainfo, ast = sap.sap_solve_adjoint(h, dev(g))
+    assert ast == sap.SAP_OK and ainfo.relres <= 1e-10 and relerr(host(lam), lo) <= 1e-8
+
+
+@pytest.mark.parametrize("nx,ny,P,prec", [(60, 40, 4, 1), (60, 40, 4, 0), (200, 130, 8, 1)])
+def test_convection_diffusion_sapc_parity(sap, nx, ny, P, prec):
+    """The sparse-in-band nonsymmetric convection-diffusion operator (5-point
+    upwind, Peclet 10) treated as a dense band, SaP-C, against the oracle."""
+    band, N, K = G.convection_diffusion(nx, ny)
+    xt = G.x_true(N, G.config_seed(4))
+    b = O.spmv(band, N, K, xt)
+    xo, io, _ = O.solve(band, N, K, b, P, O.SAP_C)
+    assert io.status == O.OK
+    h = sap.sap_factor(dev(band), N, K, P=P, variant=sap.SAP_C, precision=prec)
+    x, info, st = sap.sap_solve(h, dev(b))
+    assert st == sap.SAP_OK and info.relres <= 1e-10
+    assert relerr(host(x), xo) <= 1e-8
+
+
 def test_autotune_picks_the_fastest_measured_candidate(sap):
     """The measured autotuner times refactor + solve for each (P, segments)
     candidate and returns the fastest; the default P grid is N / {16000 .. 1000}."""
@@ -350,3 +383,20 @@ def test_full_size_dense_banded_n200k_k50_p50(sap):
             x, info, st = sap.sap_solve(h, dev(b))
             assert st == sap.SAP_OK and info.relres <= 1e-10
             assert relerr(host(x), xo) <= 1e-8
+
+
+def test_full_size_convection_diffusion_400x250_sapc_p32(sap):
+    """The 400 x 250 convection-diffusion workload (N = 100000, K = 250), SaP-C,
+    P = 32, FP32 preconditioner with FP64 BiCGStab(2): the true residual
+    recomputed on the host, and the solution against the oracle's."""
+    band, N, K = G.convection_diffusion(400, 250)
+    assert (N, K) == (100000, 250)
+    xt = G.x_true(N, G.config_seed(4))
+    b = O.spmv(band, N, K, xt)
+    h = sap.sap_factor(dev(band), N, K, P=32, variant=sap.SAP_C, precision=sap.SAP_FP32)
+    x, info, st = sap.sap_solve(h, dev(b))
+    assert st == sap.SAP_OK and info.relres <= 1e-10
+    xh = host(x)
+    assert np.linalg.norm(b - O.spmv(band, N, K, xh)) / np.linalg.norm(b) <= 1e-10
+    xo, io, _ = O.solve(band, N, K, b, 32, O.SAP_C)
+    assert io.status == O.OK and relerr(xh, xo) <= 1e-8

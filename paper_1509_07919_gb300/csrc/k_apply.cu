@@ -119,7 +119,7 @@ struct SweepSh {
   T* M;          // (PF+1) x (1+ng) x 32 x 32 ring of chunk matrices, column-major
   YT* Y;         // (PF+1) x 32 ring of right-hand sides
   T* zh;         // (ng+1) x 32: z of the most recent chunks (chunk mod (ng+1))
-  T* W;          // [2][32]: w of the next chunk
+  T* W;          // [2][NPW][32]: partial sums of w of the next chunk, one per prepare warp
   T* yb;         // 32: y - corrections of the chunk being prepared
   double* corr;  // 2K corrections (top K rows, bottom K rows)
   uint64_t* bar; // PF+1 mbarriers: chunk matrices of a ring slot landed
@@ -167,7 +167,7 @@ __device__ __forceinline__ void prefetch_y(const SweepSh<T, YT>& sh, const Sweep
 // (lc + ng + 1) % (ng + 1), the ng chunks before the segment occupying slots
 // 1..ng (zero).  out receives z of the segment's rows; tail (if not null) the
 // z of its last hist_width(K) positions, oldest first.
-template <typename T, typename YT, typename OT, int MODE, int PFD = PF>
+template <typename T, typename YT, typename OT, int MODE, int PFD = PF, int NPW = 1>
 __device__ void sweep(const SweepSh<T, YT>& sh, const SweepGeom& g, const T* __restrict__ Mg,
                       const YT* __restrict__ yin, bool has_top, bool has_bot, OT* __restrict__ out, int c0, int nc,
                       T* __restrict__ tail, unsigned& ph, bool& failed, int* __restrict__ err) {
@@ -177,38 +177,64 @@ __device__ void sweep(const SweepSh<T, YT>& sh, const SweepGeom& g, const T* __r
   const int mat = (1 + ng) * CHK * CHK;
   const int p0 = c0 * CHK;
   const T* Ms = Mg + (int64_t)c0 * mat;
-  // ph: per-slot parity of the next barrier phase (lane 0 of warp 2), carried
-  // from sweep to sweep of one CTA
-  auto wait_chunk = [&](int lc) {     // warp 2: lane 0 polls
+  // warp roles: 0 the chain, 1 .. NPW the preparation of the next chunk's w
+  // (warp 1 also fetches y), NPW + 1 the bulk copies of the chunk matrices.
+  // ph: per-slot parity of the next barrier phase (lane 0 of the copy warp),
+  // carried from sweep to sweep of one CTA
+  constexpr int WCOPY = NPW + 1;
+  const bool prep = NPW == 1 ? warp == 1 : (warp >= 1 && warp <= NPW);
+  auto wait_chunk = [&](int lc) {     // copy warp: lane 0 polls
     const int sl = lc % (PFD + 1);
     if (lane == 0) mbar_wait(&sh.bar[sl], (ph >> sl) & 1u, err, failed);
     ph ^= 1u << sl;
     __syncwarp();
   };
   auto zslot = [&](int lc) { return (lc + ng + 1) % (ng + 1); };
-  // w_lb = MINV (y - corrections) - sum_{k>=2} G_k z_{lb-k}
+  // w_lb = MINV (y - corrections) - sum_{k>=2} G_k z_{lb-k}: prepare warp j
+  // (0-based) forms the MINV term (j = 0) and the G_k terms with k = j + 2 mod
+  // NPW; warp 0 adds the NPW partial sums in order
   auto prepare = [&](int lb) {
     const int slot = lb % (PFD + 1);
-    const int r = row_of<MODE>(p0 + lb * CHK + lane, g.ld);
-    T yv = T(0);
-    if (r < g.n) {
-      yv = (T)sh.Y[slot * CHK + lane];
-      if (has_top && r < K) yv -= (T)sh.corr[r];
-      if (has_bot && r >= g.n - K) yv -= (T)sh.corr[K + (r - (g.n - K))];
-    }
-    sh.yb[lane] = yv;
-    __syncwarp();
     const T* Mc = sh.M + slot * mat;
-    T w = coldot32(Mc, sh.yb, lane);
-    for (int k = 2; k <= ng; ++k) w -= coldot32(Mc + k * CHK * CHK, sh.zh + zslot(lb - k) * CHK, lane);
-    sh.W[(lb & 1) * CHK + lane] = w;
-    __syncwarp();
+    if constexpr (NPW == 1) {
+      const int r = row_of<MODE>(p0 + lb * CHK + lane, g.ld);
+      T yv = T(0);
+      if (r < g.n) {
+        yv = (T)sh.Y[slot * CHK + lane];
+        if (has_top && r < K) yv -= (T)sh.corr[r];
+        if (has_bot && r >= g.n - K) yv -= (T)sh.corr[K + (r - (g.n - K))];
+      }
+      sh.yb[lane] = yv;
+      __syncwarp();
+      T w = coldot32(Mc, sh.yb, lane);
+      for (int k = 2; k <= ng; ++k) w -= coldot32(Mc + k * CHK * CHK, sh.zh + zslot(lb - k) * CHK, lane);
+      sh.W[(lb & 1) * CHK + lane] = w;
+      __syncwarp();
+    } else {
+      const int j = warp - 1;
+      T w = T(0);
+      if (j == 0) {
+        const int r = row_of<MODE>(p0 + lb * CHK + lane, g.ld);
+        T yv = T(0);
+        if (r < g.n) {
+          yv = (T)sh.Y[slot * CHK + lane];
+          if (has_top && r < K) yv -= (T)sh.corr[r];
+          if (has_bot && r >= g.n - K) yv -= (T)sh.corr[K + (r - (g.n - K))];
+        }
+        sh.yb[lane] = yv;
+        __syncwarp();
+        w = coldot32(Mc, sh.yb, lane);
+      }
+      for (int k = 2 + j; k <= ng; k += NPW) w -= coldot32(Mc + k * CHK * CHK, sh.zh + zslot(lb - k) * CHK, lane);
+      sh.W[((lb & 1) * NPW + j) * CHK + lane] = w;
+      __syncwarp();
+    }
   };
   // z history: zero
   for (int t = threadIdx.x; t < (ng + 1) * CHK; t += blockDim.x) sh.zh[t] = T(0);
   __syncthreads();
   // prologue: matrices of local chunks 0..PFD-1 in flight, 0 and 1 landed, w_0 formed
-  if (warp == 2) {
+  if (warp == WCOPY) {
     for (int lc = 0; lc < PFD; ++lc) prefetch_mats<PFD>(sh, g, Ms, lc, nc);
     wait_chunk(0);
     wait_chunk(1);
@@ -218,7 +244,7 @@ __device__ void sweep(const SweepSh<T, YT>& sh, const SweepGeom& g, const T* __r
     __syncwarp();
   }
   __syncthreads();
-  if (warp == 1) prepare(0);
+  if (prep) prepare(0);
   __syncthreads();
   // warp 0: z of the previous chunk, lane t holds position t
   T zprev = T(0);
@@ -228,7 +254,12 @@ __device__ void sweep(const SweepSh<T, YT>& sh, const SweepGeom& g, const T* __r
       T m[CHK];
 #pragma unroll
       for (int j = 0; j < CHK; ++j) m[j] = G1[j * CHK + lane];
-      T a0 = sh.W[(lc & 1) * CHK + lane], a1 = T(0), a2 = T(0), a3 = T(0);
+      const T* Wl = sh.W + (lc & 1) * NPW * CHK + lane;
+      T a0 = Wl[0], a1 = T(0), a2 = T(0), a3 = T(0);
+      if constexpr (NPW > 1) {
+#pragma unroll
+        for (int j = 1; j < NPW; ++j) a0 += Wl[j * CHK];
+      }
 #pragma unroll
       for (int j = 0; j < CHK; j += 4) {
         a0 -= m[j] * __shfl_sync(0xffffffffu, zprev, j);
@@ -248,14 +279,16 @@ __device__ void sweep(const SweepSh<T, YT>& sh, const SweepGeom& g, const T* __r
         __syncwarp();
         prepare(lc + 1);
       }
+    } else if (NPW > 1 && prep) {
+      if (lc + 1 < nc) prepare(lc + 1);
     } else {
       prefetch_mats<PFD>(sh, g, Ms, lc + PFD, nc);
-      wait_chunk(lc + 2);       // read by warp 1 in iteration lc + 1, by warp 0 in lc + 2
+      wait_chunk(lc + 2);       // read by the prepare warps in iteration lc + 1, by warp 0 in lc + 2
     }
     __syncthreads();
   }
-  // warp 2: consume the phases of the remaining prefetched chunks
-  if (warp == 2)
+  // copy warp: consume the phases of the remaining prefetched chunks
+  if (warp == WCOPY)
     for (int lc = nc + 2; lc < nc + PFD; ++lc) wait_chunk(lc);
   if (warp == 1) cpa_wait<0>();
   if (tail && warp == 0) {     // the last KH positions of the segment's last ng chunks
@@ -270,13 +303,13 @@ __device__ void sweep(const SweepSh<T, YT>& sh, const SweepGeom& g, const T* __r
 
 __host__ __device__ inline int n_couplings(int K) { return (K + CHK - 1) / CHK; }
 
-template <typename T, int PFD = PF>
+template <typename T, int PFD = PF, int NPW = 1>
 size_t sweep_smem(int K) {
   const int ng = n_couplings(K);
   size_t b = (size_t)(PFD + 1) * (1 + ng) * CHK * CHK * sizeof(T);   // chunk matrices
   b += (size_t)(PFD + 1) * CHK * sizeof(double);                      // Y ring (largest input type)
   b += (size_t)(ng + 1) * CHK * sizeof(T);                           // z history
-  b += (size_t)3 * CHK * sizeof(T);                                  // W, yb
+  b += (size_t)(2 * NPW + 1) * CHK * sizeof(T);                      // W partials, yb
   b = (b + 15) & ~(size_t)15;
   b += (size_t)2 * K * sizeof(double);                               // corrections
   b = (b + 15) & ~(size_t)15;
@@ -284,7 +317,7 @@ size_t sweep_smem(int K) {
   return b;
 }
 
-template <typename T, typename YT, int PFD = PF>
+template <typename T, typename YT, int PFD = PF, int NPW = 1>
 __device__ __forceinline__ SweepSh<T, YT> carve(unsigned char* base, const SweepGeom& g) {
   SweepSh<T, YT> sh;
   size_t off = 0;
@@ -295,7 +328,7 @@ __device__ __forceinline__ SweepSh<T, YT> carve(unsigned char* base, const Sweep
   sh.zh = reinterpret_cast<T*>(base + off);
   off += (size_t)(g.ng + 1) * CHK * sizeof(T);
   sh.W = reinterpret_cast<T*>(base + off);
-  off += 2 * CHK * sizeof(T);
+  off += 2 * NPW * CHK * sizeof(T);
   sh.yb = reinterpret_cast<T*>(base + off);
   off += CHK * sizeof(T);
   off = (off + 15) & ~(size_t)15;
@@ -479,8 +512,8 @@ k_seg_correct(const T* __restrict__ Xall, const T* __restrict__ tails, int K, De
 // then the backward sweep of its block.  Measured faster than two launches of
 // k_sweep with S = 1 (125 us against about 150 us per apply on the
 // N = 200000, K = 50, P = 50 FP32 system).
-template <typename T, bool TRANS, int PFD>
-__global__ void __launch_bounds__(NWS * 32)
+template <typename T, bool TRANS, int PFD, int NPW>
+__global__ void __launch_bounds__(32 * (NPW + 2))
 k_block_solve(const T* __restrict__ M1all, const T* __restrict__ M2all, const int64_t* __restrict__ cbase, int K,
               Dev d, const double* __restrict__ r_in, double* __restrict__ z_out, T* __restrict__ tmp,
               const double* __restrict__ ctop_all, const double* __restrict__ cbot_all, int P,
@@ -500,7 +533,7 @@ k_block_solve(const T* __restrict__ M1all, const T* __restrict__ M2all, const in
   unsigned ph = 0;
   bool failed = false;
   {
-    SweepSh<T, double> sh = carve<T, double, PFD>(smem_raw, g);
+    SweepSh<T, double> sh = carve<T, double, PFD, NPW>(smem_raw, g);
     if (threadIdx.x == 0) {
       for (int q = 0; q <= PFD; ++q) mbar_init(&sh.bar[q], 1);
       mbar_fence_init();
@@ -510,19 +543,19 @@ k_block_solve(const T* __restrict__ M1all, const T* __restrict__ M2all, const in
       sh.corr[K + t] = has_bot ? cbot_all[(int64_t)b * K + t] : 0.0;
     }
     if (!TRANS)
-      sweep<T, double, T, LF, PFD>(sh, g, M1all + cbase[b], r_in + s, has_top, has_bot, tmp + s, 0, nch, nullptr, ph,
+      sweep<T, double, T, LF, PFD, NPW>(sh, g, M1all + cbase[b], r_in + s, has_top, has_bot, tmp + s, 0, nch, nullptr, ph,
                               failed, err);
     else
-      sweep<T, double, T, UTF, PFD>(sh, g, M1all + cbase[b], r_in + s, has_top, has_bot, tmp + s, 0, nch, nullptr, ph,
+      sweep<T, double, T, UTF, PFD, NPW>(sh, g, M1all + cbase[b], r_in + s, has_top, has_bot, tmp + s, 0, nch, nullptr, ph,
                                failed, err);
   }
   {
-    SweepSh<T, T> sh = carve<T, T, PFD>(smem_raw, g);
+    SweepSh<T, T> sh = carve<T, T, PFD, NPW>(smem_raw, g);
     if (!TRANS)
-      sweep<T, T, double, UB, PFD>(sh, g, M2all + cbase[b], tmp + s, false, false, z_out + s, 0, nch, nullptr, ph,
+      sweep<T, T, double, UB, PFD, NPW>(sh, g, M2all + cbase[b], tmp + s, false, false, z_out + s, 0, nch, nullptr, ph,
                               failed, err);
     else
-      sweep<T, T, double, LTB, PFD>(sh, g, M2all + cbase[b], tmp + s, false, false, z_out + s, 0, nch, nullptr, ph,
+      sweep<T, T, double, LTB, PFD, NPW>(sh, g, M2all + cbase[b], tmp + s, false, false, z_out + s, 0, nch, nullptr, ph,
                                failed, err);
   }
 }
@@ -634,15 +667,30 @@ cudaError_t launch_block_solve(const Factors<T>& f, int K, int P, Dev d, const d
                                const double* ctop, const double* cbot, cudaStream_t s, Gate gt) {
   cudaError_t e;
   if (f.S == 1) {
-    // four chunks in flight where the ring fits, two for the widest bands
-    const bool deep = sweep_smem<T, PF>(K) <= kSmemPerBlock;
-    const size_t smem = deep ? sweep_smem<T, PF>(K) : sweep_smem<T, 2>(K);
-    auto kern = deep ? k_block_solve<T, TRANS, PF> : k_block_solve<T, TRANS, 2>;
+    // four chunks in flight where the ring fits, two for the widest bands;
+    // the next chunk's couplings split over 1, 2 or 4 prepare warps
+    const int ng = n_couplings(K);
+    const int npw = ng <= 3 ? 1 : (ng <= 7 ? 2 : 4);
+    const bool deep = (npw == 1 ? sweep_smem<T, PF, 1>(K) : npw == 2 ? sweep_smem<T, PF, 2>(K)
+                                                                     : sweep_smem<T, PF, 4>(K)) <= kSmemPerBlock;
+    size_t smem;
+    void (*kern)(const T*, const T*, const int64_t*, int, Dev, const double*, double*, T*, const double*,
+                 const double*, int, int*, Gate);
+    if (npw == 1) {
+      smem = sweep_smem<T, PF, 1>(K);
+      kern = k_block_solve<T, TRANS, PF, 1>;
+    } else if (npw == 2) {
+      smem = deep ? sweep_smem<T, PF, 2>(K) : sweep_smem<T, 2, 2>(K);
+      kern = deep ? k_block_solve<T, TRANS, PF, 2> : k_block_solve<T, TRANS, 2, 2>;
+    } else {
+      smem = deep ? sweep_smem<T, PF, 4>(K) : sweep_smem<T, 2, 4>(K);
+      kern = deep ? k_block_solve<T, TRANS, PF, 4> : k_block_solve<T, TRANS, 2, 4>;
+    }
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     count_launches(1);
-    kern<<<P, NWS * 32, smem, s>>>(TRANS ? f.Mutf : f.Mlf, TRANS ? f.Mltb : f.Mub, f.cbase, K, d, r, z, tmp, ctop,
-                                   cbot, P, f.err, gt);
+    kern<<<P, 32 * (npw + 2), smem, s>>>(TRANS ? f.Mutf : f.Mlf, TRANS ? f.Mltb : f.Mub, f.cbase, K, d, r, z, tmp,
+                                         ctop, cbot, P, f.err, gt);
     return cudaGetLastError();
   }
   if (!TRANS) {
@@ -657,8 +705,8 @@ cudaError_t launch_block_solve(const Factors<T>& f, int K, int P, Dev d, const d
 
 }  // namespace
 
-// the unsegmented sweep's smallest ring (two chunks ahead): the limit on K
-size_t sweep_smem_bytes(int K, bool fp64) { return fp64 ? sweep_smem<double, 2>(K) : sweep_smem<float, 2>(K); }
+// the unsegmented sweep's smallest ring (two chunks ahead, four prepare warps): the limit on K
+size_t sweep_smem_bytes(int K, bool fp64) { return fp64 ? sweep_smem<double, 2, 4>(K) : sweep_smem<float, 2, 4>(K); }
 int chunk_couplings(int K) { return n_couplings(K); }
 
 // scratch layout (doubles): [0, N) g ; then T tmp (N); then ctop, cbot ((P-1) K each)

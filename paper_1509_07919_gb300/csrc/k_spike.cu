@@ -24,41 +24,41 @@ namespace {
 
 constexpr int NT = 256;
 
-// Solve op(M) x = x in place for the column `col` of X (K x K row-major in
-// shared memory), M in shared memory (row-major K x K).  lower: the
-// triangle of M used; unit: implicit unit diagonal; trans: use M^T.
+// Solve op(M) x = x in place for the column `col` of X (K rows, row pitch
+// ldx), M row-major K x K.  lower: the triangle of M used; unit: implicit
+// unit diagonal; trans: use M^T.
 template <typename T>
-__device__ void tri_col(const T* M, int K, bool lower, bool unit, bool trans, T* X, int col) {
+__device__ void tri_col(const T* M, int K, bool lower, bool unit, bool trans, T* X, int col, int ldx) {
   // effective matrix E = trans ? M^T : M; E is lower iff (lower != trans)
   const bool elower = (lower != trans);
   auto E = [&](int r, int q) -> T { return trans ? M[q * K + r] : M[r * K + q]; };
   if (elower) {
     for (int r = 0; r < K; ++r) {
-      T a0 = X[r * K + col], a1 = T(0), a2 = T(0), a3 = T(0);
+      T a0 = X[r * ldx + col], a1 = T(0), a2 = T(0), a3 = T(0);
       int q = 0;
       for (; q + 3 < r; q += 4) {
-        a0 -= E(r, q) * X[q * K + col];
-        a1 -= E(r, q + 1) * X[(q + 1) * K + col];
-        a2 -= E(r, q + 2) * X[(q + 2) * K + col];
-        a3 -= E(r, q + 3) * X[(q + 3) * K + col];
+        a0 -= E(r, q) * X[q * ldx + col];
+        a1 -= E(r, q + 1) * X[(q + 1) * ldx + col];
+        a2 -= E(r, q + 2) * X[(q + 2) * ldx + col];
+        a3 -= E(r, q + 3) * X[(q + 3) * ldx + col];
       }
-      for (; q < r; ++q) a0 -= E(r, q) * X[q * K + col];
+      for (; q < r; ++q) a0 -= E(r, q) * X[q * ldx + col];
       T v = (a0 + a1) + (a2 + a3);
-      X[r * K + col] = unit ? v : v / E(r, r);
+      X[r * ldx + col] = unit ? v : v / E(r, r);
     }
   } else {
     for (int r = K - 1; r >= 0; --r) {
-      T a0 = X[r * K + col], a1 = T(0), a2 = T(0), a3 = T(0);
+      T a0 = X[r * ldx + col], a1 = T(0), a2 = T(0), a3 = T(0);
       int q = r + 1;
       for (; q + 3 < K; q += 4) {
-        a0 -= E(r, q) * X[q * K + col];
-        a1 -= E(r, q + 1) * X[(q + 1) * K + col];
-        a2 -= E(r, q + 2) * X[(q + 2) * K + col];
-        a3 -= E(r, q + 3) * X[(q + 3) * K + col];
+        a0 -= E(r, q) * X[q * ldx + col];
+        a1 -= E(r, q + 1) * X[(q + 1) * ldx + col];
+        a2 -= E(r, q + 2) * X[(q + 2) * ldx + col];
+        a3 -= E(r, q + 3) * X[(q + 3) * ldx + col];
       }
-      for (; q < K; ++q) a0 -= E(r, q) * X[q * K + col];
+      for (; q < K; ++q) a0 -= E(r, q) * X[q * ldx + col];
       T v = (a0 + a1) + (a2 + a3);
-      X[r * K + col] = unit ? v : v / E(r, r);
+      X[r * ldx + col] = unit ? v : v / E(r, r);
     }
   }
 }
@@ -70,6 +70,49 @@ __host__ __device__ inline size_t spike_ws_bytes(int K, int tsize) {
   return (size_t)K * K * (sizeof(double) + 2 * (size_t)tsize);
 }
 __host__ __device__ inline size_t spike_ws_stride(int K, int tsize) { return (spike_ws_bytes(K, tsize) + 255) & ~(size_t)255; }
+
+// GEPP of the K x K FP64 matrix R in place (P R = L U, unit L below the
+// diagonal), ties to the lowest row index; pivs[k] = row swapped with k.  The
+// whole CTA (NT threads) takes part.
+__device__ void rbar_gepp(double* R, int K, int* pivs, int* singular, double* red_v, int* red_i) {
+  const int tid = threadIdx.x;
+  for (int k = 0; k < K; ++k) {
+    double best = -1.0;
+    int bi = k;
+    for (int r = k + tid; r < K; r += NT) {
+      double v = fabs(R[r * K + k]);
+      if (v > best) { best = v; bi = r; }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      double ov = __shfl_xor_sync(0xffffffffu, best, o);
+      int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+    }
+    if ((tid & 31) == 0) { red_v[tid >> 5] = best; red_i[tid >> 5] = bi; }
+    __syncthreads();
+    if (tid == 0) {
+      double bv = red_v[0]; int bx = red_i[0];
+      for (int w = 1; w < NT / 32; ++w)
+        if (red_v[w] > bv || (red_v[w] == bv && red_i[w] < bx)) { bv = red_v[w]; bx = red_i[w]; }
+      pivs[k] = bx;
+      if (bv == 0.0) atomicExch(singular, 1);
+    }
+    __syncthreads();
+    const int p = pivs[k];
+    if (p != k)
+      for (int c = tid; c < K; c += NT) { double t = R[k * K + c]; R[k * K + c] = R[p * K + c]; R[p * K + c] = t; }
+    __syncthreads();
+    const double pv = R[k * K + k];
+    for (int r = k + 1 + tid; r < K; r += NT) R[r * K + k] = (pv != 0.0) ? R[r * K + k] / pv : 0.0;
+    __syncthreads();
+    const int m = K - k - 1;
+    for (int e = tid; e < m * m; e += NT) {
+      int r = k + 1 + e / m, c = k + 1 + e % m;
+      R[r * K + c] -= R[r * K + k] * R[k * K + c];
+    }
+    __syncthreads();
+  }
+}
 
 template <typename T, bool GM>
 __global__ void __launch_bounds__(NT)
@@ -111,11 +154,11 @@ k_spikes(const double* __restrict__ band, int64_t N, int K, Dev d, const T* __re
   __syncthreads();
   for (int col = tid; col < K; col += NT) {
     if (!adjoint) {
-      tri_col(Mx, K, true, true, false, X, col);    // L_bb (unit lower)
-      tri_col(Mx, K, false, false, false, X, col);  // U_bb
+      tri_col(Mx, K, true, true, false, X, col, K);    // L_bb (unit lower)
+      tri_col(Mx, K, false, false, false, X, col, K);  // U_bb
     } else {
-      tri_col(Mx, K, false, false, true, X, col);   // U_bb^T (lower)
-      tri_col(Mx, K, true, true, true, X, col);     // L_bb^T (unit upper)
+      tri_col(Mx, K, false, false, true, X, col, K);   // U_bb^T (lower)
+      tri_col(Mx, K, true, true, true, X, col, K);     // L_bb^T (unit upper)
     }
   }
   __syncthreads();
@@ -135,15 +178,16 @@ k_spikes(const double* __restrict__ band, int64_t N, int K, Dev d, const T* __re
   __syncthreads();
   for (int col = tid; col < K; col += NT) {
     if (!adjoint) {
-      tri_col(Mx, K, false, true, false, X, col);   // U'_tt (unit upper)
-      tri_col(Mx, K, true, false, false, X, col);   // L'_tt (lower)
+      tri_col(Mx, K, false, true, false, X, col, K);   // U'_tt (unit upper)
+      tri_col(Mx, K, true, false, false, X, col, K);   // L'_tt (lower)
     } else {
-      tri_col(Mx, K, true, false, true, X, col);    // L'_tt^T (upper)
-      tri_col(Mx, K, false, true, true, X, col);    // U'_tt^T (unit lower)
+      tri_col(Mx, K, true, false, true, X, col, K);    // L'_tt^T (upper)
+      tri_col(Mx, K, false, true, true, X, col, K);    // U'_tt^T (unit lower)
     }
   }
   __syncthreads();
   for (int e = tid; e < KK; e += NT) Wi[e] = X[e];
+  if (GM) return;     // wide bands: Rbar, its GEPP and inverse by k_rbar_form / _gepp / _inv
   // ---- Rbar = I - W V in FP64 (V re-read from global, W in X) ----
   __syncthreads();
   for (int e = tid; e < KK; e += NT) Mx[e] = Vi[e];
@@ -162,42 +206,7 @@ k_spikes(const double* __restrict__ band, int64_t N, int K, Dev d, const T* __re
   }
   __syncthreads();
   // ---- GEPP of Rbar (ties to the lowest row) ----
-  for (int k = 0; k < K; ++k) {
-    double best = -1.0;
-    int bi = k;
-    for (int r = k + tid; r < K; r += NT) {
-      double v = fabs(R[r * K + k]);
-      if (v > best) { best = v; bi = r; }
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-      double ov = __shfl_xor_sync(0xffffffffu, best, o);
-      int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-      if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
-    }
-    if ((tid & 31) == 0) { red_v[tid >> 5] = best; red_i[tid >> 5] = bi; }
-    __syncthreads();
-    if (tid == 0) {
-      double bv = red_v[0]; int bx = red_i[0];
-      for (int w = 1; w < NT / 32; ++w)
-        if (red_v[w] > bv || (red_v[w] == bv && red_i[w] < bx)) { bv = red_v[w]; bx = red_i[w]; }
-      pivs[k] = bx;
-      if (bv == 0.0) atomicExch(singular, 1);
-    }
-    __syncthreads();
-    const int p = pivs[k];
-    if (p != k)
-      for (int c = tid; c < K; c += NT) { double t = R[k * K + c]; R[k * K + c] = R[p * K + c]; R[p * K + c] = t; }
-    __syncthreads();
-    const double pv = R[k * K + k];
-    for (int r = k + 1 + tid; r < K; r += NT) R[r * K + k] = (pv != 0.0) ? R[r * K + k] / pv : 0.0;
-    __syncthreads();
-    const int m = K - k - 1;
-    for (int e = tid; e < m * m; e += NT) {
-      int r = k + 1 + e / m, c = k + 1 + e % m;
-      R[r * K + c] -= R[r * K + k] * R[k * K + c];
-    }
-    __syncthreads();
-  }
+  rbar_gepp(R, K, pivs, singular, red_v, red_i);
   // ---- inverse Rinv = U^{-1} L^{-1} P (P R = L U), column by column ----
   double* Xd = reinterpret_cast<double*>(Mx);   // reuse Mx + X as a K x K FP64 workspace
   for (int e = tid; e < KK; e += NT) Xd[e] = 0.0;
@@ -210,12 +219,118 @@ k_spikes(const double* __restrict__ band, int64_t N, int K, Dev d, const T* __re
       else if (k == pos) pos = pivs[k];
     }
     Xd[pos * K + col] = 1.0;
-    tri_col(R, K, true, true, false, Xd, col);
-    tri_col(R, K, false, false, false, Xd, col);
+    tri_col(R, K, true, true, false, Xd, col, K);
+    tri_col(R, K, false, false, false, Xd, col, K);
   }
   __syncthreads();
   for (int e = tid; e < KK; e += NT) Rinv[(int64_t)i * KK + e] = Xd[e];
   for (int k = tid; k < K; k += NT) pivout[(int64_t)i * K + k] = pivs[k];
+}
+
+// ---- wide bands: Rbar, GEPP and inverse spread over more CTAs ----
+
+// Rbar_i = I - W^(t)_{i+1} V^(b)_i in FP64 (R0, and a copy in the interface's
+// workspace for the GEPP), 64 x 64 output tiles, 16-deep panels of W and V
+// staged in shared memory; grid (tiles, tiles, P - 1).
+constexpr int RT = 64, RQ = 16;
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_rbar_form(const T* __restrict__ V, const T* __restrict__ Wt, int K, double* __restrict__ R0,
+            unsigned char* __restrict__ gws) {
+  __shared__ double As[RQ][RT + 1];   // W(r0 + x, q0 + q) at As[q][x]
+  __shared__ double Bs[RQ][RT + 1];   // V(q0 + q, c0 + y) at Bs[q][y]
+  const int i = blockIdx.z;
+  const int64_t KK = (int64_t)K * K;
+  const T* Wi = Wt + i * KK;
+  const T* Vi = V + i * KK;
+  const int r0 = blockIdx.y * RT, c0 = blockIdx.x * RT;
+  const int tid = threadIdx.x, tr = tid / 16, tc = tid % 16;
+  double acc[4][4];
+#pragma unroll
+  for (int x = 0; x < 4; ++x)
+#pragma unroll
+    for (int y = 0; y < 4; ++y) acc[x][y] = 0.0;
+  for (int q0 = 0; q0 < K; q0 += RQ) {
+    for (int e = tid; e < RT * RQ; e += 256) {
+      const int x = e / RQ, q = e % RQ;          // W rows, consecutive q per thread group
+      const int r = r0 + x, qq = q0 + q;
+      As[q][x] = (r < K && qq < K) ? (double)Wi[(int64_t)r * K + qq] : 0.0;
+      const int q2 = e / RT, y = e % RT;         // V rows q, consecutive columns
+      const int qv = q0 + q2, c = c0 + y;
+      Bs[q2][y] = (qv < K && c < K) ? (double)Vi[(int64_t)qv * K + c] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < RQ; ++q) {
+      double a[4], b[4];
+#pragma unroll
+      for (int x = 0; x < 4; ++x) a[x] = As[q][tr + 16 * x];
+#pragma unroll
+      for (int y = 0; y < 4; ++y) b[y] = Bs[q][tc + 16 * y];
+#pragma unroll
+      for (int x = 0; x < 4; ++x)
+#pragma unroll
+        for (int y = 0; y < 4; ++y) acc[x][y] += a[x] * b[y];
+    }
+    __syncthreads();
+  }
+  double* Rw = reinterpret_cast<double*>(gws + (size_t)i * spike_ws_stride(K, sizeof(T)));
+#pragma unroll
+  for (int x = 0; x < 4; ++x) {
+    const int r = r0 + tr + 16 * x;
+    if (r >= K) continue;
+#pragma unroll
+    for (int y = 0; y < 4; ++y) {
+      const int c = c0 + tc + 16 * y;
+      if (c >= K) continue;
+      const double v = (r == c ? 1.0 : 0.0) - acc[x][y];
+      R0[i * KK + (int64_t)r * K + c] = v;
+      Rw[(int64_t)r * K + c] = v;
+    }
+  }
+}
+
+// GEPP of every Rbar_i in its workspace (one CTA per interface).
+template <typename T>
+__global__ void __launch_bounds__(NT)
+k_rbar_gepp(int K, unsigned char* __restrict__ gws, int* __restrict__ pivout, int* singular) {
+  extern __shared__ int pivs_sh[];
+  __shared__ double red_v[NT / 32];
+  __shared__ int red_i[NT / 32];
+  const int i = blockIdx.x;
+  double* R = reinterpret_cast<double*>(gws + (size_t)i * spike_ws_stride(K, sizeof(T)));
+  rbar_gepp(R, K, pivs_sh, singular, red_v, red_i);
+  for (int k = threadIdx.x; k < K; k += NT) pivout[(int64_t)i * K + k] = pivs_sh[k];
+}
+
+// Rbar_i^{-1} = U^{-1} L^{-1} P from the GEPP factors, 32 columns per CTA
+// (one per thread, K x 32 right-hand sides in shared memory); grid
+// (ceil(K / 32), P - 1).
+template <typename T>
+__global__ void __launch_bounds__(32)
+k_rbar_inv(int K, const unsigned char* __restrict__ gws, const int* __restrict__ pivin, double* __restrict__ Rinv) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* Xs = reinterpret_cast<double*>(smem_raw);      // K x 32
+  int* pv = reinterpret_cast<int*>(Xs + (size_t)K * 32);  // K pivots
+  const int i = blockIdx.y;
+  const int lane = threadIdx.x;
+  const int col = blockIdx.x * 32 + lane;
+  const double* R = reinterpret_cast<const double*>(gws + (size_t)i * spike_ws_stride(K, sizeof(T)));
+  for (int k = lane; k < K; k += 32) pv[k] = pivin[(int64_t)i * K + k];
+  for (int e = lane; e < K * 32; e += 32) Xs[e] = 0.0;
+  __syncwarp();
+  if (col < K) {
+    int pos = col;        // P e_col: the recorded swaps applied to e_col
+    for (int k = 0; k < K; ++k) {
+      if (pv[k] == pos) pos = k;
+      else if (k == pos) pos = pv[k];
+    }
+    Xs[pos * 32 + lane] = 1.0;
+    tri_col(R, K, true, true, false, Xs, lane, 32);
+    tri_col(R, K, false, false, false, Xs, lane, 32);
+    double* out = Rinv + (int64_t)i * K * K;
+    for (int r = 0; r < K; ++r) out[(int64_t)r * K + col] = Xs[r * 32 + lane];
+  }
 }
 
 }  // namespace
@@ -242,6 +357,19 @@ cudaError_t launch_spikes(const double* band, int64_t N, int K, int P, Dev d, co
   count_launches(1);
   kern<<<P - 1, NT, smem, s>>>(band, N, K, d, F, ULt, adjoint, V, Wt, Rinv, R0, piv, singular,
                                static_cast<unsigned char*>(gscratch));
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || !gm) return e;
+  unsigned char* gws = static_cast<unsigned char*>(gscratch);
+  const int tiles = (K + RT - 1) / RT;
+  count_launches(3);
+  k_rbar_form<T><<<dim3(tiles, tiles, P - 1), 256, 0, s>>>(V, Wt, K, R0, gws);
+  k_rbar_gepp<T><<<P - 1, NT, (size_t)K * sizeof(int), s>>>(K, gws, piv, singular);
+  const size_t ism = (size_t)K * 32 * sizeof(double) + (size_t)K * sizeof(int);
+  if (ism > 48 * 1024) {
+    e = cudaFuncSetAttribute(k_rbar_inv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ism);
+    if (e != cudaSuccess) return e;
+  }
+  k_rbar_inv<T><<<dim3((K + 31) / 32, P - 1), 32, ism, s>>>(K, gws, piv, Rinv);
   return cudaGetLastError();
 }
 

@@ -92,6 +92,10 @@ struct sap_handle {
   // background stream of the transposed sweep matrices (see Solver::factor_post)
   cudaStream_t ts = nullptr;
   cudaEvent_t ev_ts = nullptr, ev_td = nullptr;
+  // SaP-C: the UL factorisation runs on its own stream, concurrently with the LU
+  cudaStream_t us = nullptr;
+  cudaEvent_t ev_us0 = nullptr, ev_us1 = nullptr;
+  cudaEvent_t evu[2] = {nullptr, nullptr};      // T_UL bracket (on us)
   bool ts_pending = false;
   cudaEvent_t evf = nullptr, evj = nullptr;   // fork from / join to the caller's stream
   long long glaunches[2] = {0, 0};   // kernels in each graph
@@ -112,6 +116,11 @@ struct sap_handle {
     if (ts) cudaStreamDestroy(ts);
     if (ev_ts) cudaEventDestroy(ev_ts);
     if (ev_td) cudaEventDestroy(ev_td);
+    if (us) cudaStreamDestroy(us);
+    if (ev_us0) cudaEventDestroy(ev_us0);
+    if (ev_us1) cudaEventDestroy(ev_us1);
+    for (cudaEvent_t e : evu)
+      if (e) cudaEventDestroy(e);
     if (evf) cudaEventDestroy(evf);
     if (evj) cudaEventDestroy(evj);
     if (host_s) cudaFreeHost(host_s);
@@ -132,6 +141,7 @@ struct Solver : SolverBase {
   double* scratch = nullptr;   // apply scratch: g (N), T tmp (N), ctop/cbot
   float* bandf = nullptr;      // FP32 copy of the band (FP32 factorisation only)
   T* wlu = nullptr;            // factor windows in global memory (bands too wide for shared memory)
+  T* wul = nullptr;            // the same for the UL factorisation (it runs concurrently with the LU)
   void* wspk = nullptr;        // spike-kernel workspaces in global memory (same)
   bool adjoint_ready = false;
   bool transposed_ready = false;
@@ -158,7 +168,10 @@ struct Solver : SolverBase {
     CK(cudaMemset(f.F, 0, (size_t)L.f_elems * sizeof(T)));
     TRY(h->mem.alloc(&scratch, (size_t)(2 * L.N + 2 * nI * K + 8)));
     if (sizeof(T) == 4) TRY(h->mem.alloc(&bandf, (size_t)L.N * L.W));
-    if (lu_window_global(K, sizeof(T) == 8)) TRY(h->mem.alloc(&wlu, (size_t)P * lu_window_elems(K)));
+    if (lu_window_global(K, sizeof(T) == 8)) {
+      TRY(h->mem.alloc(&wlu, (size_t)P * lu_window_elems(K)));
+      if (h->opt.variant == SAP_C && P > 1) TRY(h->mem.alloc(&wul, (size_t)(P - 1) * lu_window_elems(K)));
+    }
     TRY(h->mem.alloc(&f.err, 1));
     CK(cudaMemset(f.err, 0, sizeof(int)));
     TRY(h->mem.alloc(&f.Mlf, (size_t)L.c_elems));
@@ -190,10 +203,9 @@ struct Solver : SolverBase {
     return SAP_OK;
   }
 
-  // Factor phases, each bracketed by events ev[0..4]: T_LU (absmax + LU),
-  // T_UL, T_SPK (B/C, tips, Rbar, its GEPP and inverse).
-  // Factor phases, each bracketed by events ev[0..4]: T_LU (absmax + LU +
-  // sweep matrices), T_UL, T_SPK (B/C, tips, Rbar, its GEPP and inverse).
+  // Factor phases, bracketed by events: T_LU (absmax + LU + sweep matrices,
+  // evp[0..1]), T_UL (SaP-C, evu[0..1] on the side stream us, concurrent with
+  // the LU), T_SPK (B/C, tips, Rbar, its GEPP and inverse, evp[2..3]).
   // factor_pre and factor_post surround the block LU, so that a batch can run
   // one LU launch over all its systems in between.
   sap_status_t factor_pre(cudaStream_t s) override {
@@ -206,6 +218,23 @@ struct Solver : SolverBase {
     CK(cudaEventRecord(h->evp[0], s));
     if (sizeof(T) == 4) CK(launch_absmax_cast(h->band, L.N, L.K, h->absmax, bandf, s));
     else CK(launch_absmax(h->band, L.N, L.K, h->absmax, s));
+    if (h->opt.variant == SAP_C && L.P > 1) {
+      // UL of blocks 1..P-1 on the side stream, overlapping the LU; factor_post joins it
+      if (!h->us) {
+        CK(cudaStreamCreateWithFlags(&h->us, cudaStreamNonBlocking));
+        CK(cudaEventCreateWithFlags(&h->ev_us0, cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&h->ev_us1, cudaEventDisableTiming));
+        CK(cudaEventCreate(&h->evu[0]));
+        CK(cudaEventCreate(&h->evu[1]));
+      }
+      CK(cudaEventRecord(h->ev_us0, s));
+      CK(cudaStreamWaitEvent(h->us, h->ev_us0, 0));
+      CK(cudaEventRecord(h->evu[0], h->us));
+      CK(launch_factor_ul<T>(band_in_T(), L.N, L.K, L.P, h->d, h->absmax, h->opt.boost_eps, f.ULt, h->n_boosted,
+                             wul, h->us));
+      CK(cudaEventRecord(h->evu[1], h->us));
+      CK(cudaEventRecord(h->ev_us1, h->us));
+    }
     return SAP_OK;
   }
   void lu_items(std::vector<LuItem>& out) const override {
@@ -228,7 +257,6 @@ struct Solver : SolverBase {
   sap_status_t factor_post(cudaStream_t s) override {
     const Layout& L = h->L;
     const int K = L.K, P = L.P;
-    const double eps = h->opt.boost_eps;
     CK(launch_chunk_mats<T>(f.F, K, P, h->d, f.cbase, L.max_nch, 0, f.Mlf, s));
     CK(launch_chunk_mats<T>(f.F, K, P, h->d, f.cbase, L.max_nch, 1, f.Mub, s));
     CK(launch_seg_trans<T>(f.Mlf, f.cbase, K, P, L.S, f.cpsmax, h->d, f.Tlf, f.Xlf, s));
@@ -250,7 +278,7 @@ struct Solver : SolverBase {
     }
     CK(cudaEventRecord(h->evp[1], s));
     if (h->opt.variant == SAP_C && P > 1) {
-      CK(launch_factor_ul<T>(band_in_T(), L.N, K, P, h->d, h->absmax, eps, f.ULt, h->n_boosted, wlu, s));
+      CK(cudaStreamWaitEvent(s, h->ev_us1, 0));      // the UL started by factor_pre
       CK(cudaEventRecord(h->evp[2], s));
       CK(launch_spikes<T>(h->band, L.N, K, P, h->d, f.F, f.ULt, false, f.V, f.Wt, f.R, f.R0, f.piv,
                           h->singular, wspk, s));
@@ -652,7 +680,8 @@ sap_status_t finish_factor(sap_handle* h) {
   CK(cudaEventSynchronize(h->evp[3]));
   CK(cudaGetLastError());
   cudaEventElapsedTime(&h->t_lu_ms, h->evp[0], h->evp[1]);
-  cudaEventElapsedTime(&h->t_ul_ms, h->evp[1], h->evp[2]);
+  h->t_ul_ms = 0.f;
+  if (h->opt.variant == SAP_C && h->L.P > 1) cudaEventElapsedTime(&h->t_ul_ms, h->evu[0], h->evu[1]);
   cudaEventElapsedTime(&h->t_spk_ms, h->evp[2], h->evp[3]);
   cudaEventElapsedTime(&h->t_factor_ms, h->evp[0], h->evp[3]);
   int sing = 0;

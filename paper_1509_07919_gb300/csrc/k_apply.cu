@@ -629,6 +629,95 @@ __global__ void k_reduced(const double* __restrict__ band, int64_t N, int K, Dev
   }
 }
 
+// The same reduced solves for wide bands, one kernel per dependent step so
+// that each step spreads over (ceil(K / 32), P - 1) CTAs of 8 warps:
+//   k_red_mv   y = base - A x (or A x) for the 32 rows of its CTA, a warp per
+//              row reading A's row coalesced, x staged in shared memory;
+//   k_red_cpl  cbot, ctop from the band, lanes over rows and warps over band
+//              diagonals (consecutive rows of a diagonal are contiguous).
+// Same arithmetic as k_reduced, different summation order.
+constexpr int kRedRows = 32;
+enum RedStep { RED_RHS = 0, RED_XT = 1, RED_XB = 2 };
+
+template <typename M, int STEP>
+__global__ void __launch_bounds__(256)
+k_red_mv(const M* __restrict__ A, int K, Dev d, const double* __restrict__ g, const double* __restrict__ xin,
+         double* __restrict__ y, Gate gate) {
+  extern __shared__ __align__(16) double xs[];     // K
+  if (gate_skip(gate)) return;
+  const int i = blockIdx.y;
+  const int64_t s = d.off[i + 1];
+  const int64_t KK = (int64_t)K * K;
+  const M* Ai = A + i * KK;
+  // x: g^(b)_i (RHS step) or the previous step's vector of this interface
+  for (int t = threadIdx.x; t < K; t += blockDim.x) xs[t] = STEP == RED_RHS ? g[s - K + t] : xin[(int64_t)i * K + t];
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int rr = warp; rr < kRedRows; rr += 8) {
+    const int r = blockIdx.x * kRedRows + rr;
+    if (r >= K) break;
+    const M* row = Ai + (int64_t)r * K;
+    double a0 = 0.0, a1 = 0.0;
+    int q = lane;
+    for (; q + 32 < K; q += 64) {
+      a0 += (double)row[q] * xs[q];
+      a1 += (double)row[q + 32] * xs[q + 32];
+    }
+    if (q < K) a0 += (double)row[q] * xs[q];
+    double acc = a0 + a1;
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) {
+      double v;
+      if (STEP == RED_RHS) v = g[s + r] - acc;                       // g^(t)_{i+1} - W g^(b)_i
+      else if (STEP == RED_XT) v = acc;                             // Rbar^{-1} rhs
+      else v = g[s - K + r] - acc;                                  // g^(b)_i - V xt
+      y[(int64_t)i * K + r] = v;
+    }
+  }
+}
+
+template <bool TRANS>
+__global__ void __launch_bounds__(256)
+k_red_cpl(const double* __restrict__ band, int64_t N, int K, Dev d, const double* __restrict__ xt,
+          const double* __restrict__ xb, double* __restrict__ ctop, double* __restrict__ cbot, Gate gate) {
+  __shared__ double pb[8][kRedRows], pc[8][kRedRows];
+  if (gate_skip(gate)) return;
+  const int i = blockIdx.y;
+  const int64_t s = d.off[i + 1];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int r = blockIdx.x * kRedRows + lane;
+  const double* xti = xt + (int64_t)i * K;
+  const double* xbi = xb + (int64_t)i * K;
+  double accb = 0.0, accc = 0.0;
+  if (r < K) {
+    // B (or B' = C^T): entries (r, r - dd), dd = 0 .. r; C (or C' = B^T): entries (r, r + e), e = 0 .. K-1-r
+    for (int dd = warp; dd <= r; dd += 8) {
+      const double a = TRANS ? band[(int64_t)(2 * K - dd) * N + s - K + r] : band[(int64_t)dd * N + s + r - dd];
+      accb += a * xti[r - dd];
+    }
+    for (int e = warp; e < K - r; e += 8) {
+      const double a = TRANS ? band[(int64_t)e * N + s + r] : band[(int64_t)(2 * K - e) * N + s - K + r + e];
+      accc += a * xbi[r + e];
+    }
+  }
+  pb[warp][lane] = accb;
+  pc[warp][lane] = accc;
+  __syncthreads();
+  if (warp == 0 && r < K) {
+    double b = 0.0, c = 0.0;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) {
+      b += pb[w][lane];
+      c += pc[w][lane];
+    }
+    cbot[(int64_t)i * K + r] = b;
+    ctop[(int64_t)i * K + r] = c;
+  }
+}
+
+// K from which the reduced solves run as the four step kernels above
+constexpr int kRedStagedK = 96;
+
 template <typename T, typename YT, typename OT, int MODE>
 cudaError_t launch_sweep(const T* M, const T* Tm, const T* Xm, const Factors<T>& f, int K, int P, Dev d,
                          const YT* yin, OT* out, const double* ctop, const double* cbot, cudaStream_t s, Gate gt) {
@@ -709,7 +798,8 @@ cudaError_t launch_block_solve(const Factors<T>& f, int K, int P, Dev d, const d
 size_t sweep_smem_bytes(int K, bool fp64) { return fp64 ? sweep_smem<double, 2, 4>(K) : sweep_smem<float, 2, 4>(K); }
 int chunk_couplings(int K) { return n_couplings(K); }
 
-// scratch layout (doubles): [0, N) g ; then T tmp (N); then ctop, cbot ((P-1) K each)
+// scratch layout (doubles): [0, N) g ; then T tmp (N); then ctop, cbot ((P-1) K each);
+// then (wide bands, SaP-C) rhs, xt, xb of the reduced solves ((P-1) K each)
 template <typename T>
 cudaError_t launch_apply(const double* band, int64_t N, int K, int P, Dev d, const Factors<T>& f,
                          int variant, bool transpose, const double* r, double* z, double* scratch,
@@ -726,12 +816,26 @@ cudaError_t launch_apply(const double* band, int64_t N, int K, int P, Dev d, con
   e = transpose ? launch_block_solve<T, true>(f, K, P, d, r, g, tmp, nullptr, nullptr, s, gt)
                 : launch_block_solve<T, false>(f, K, P, d, r, g, tmp, nullptr, nullptr, s, gt);
   if (e != cudaSuccess) return e;
-  size_t sm = 5 * (size_t)K * sizeof(double);
-  count_launches(1);
-  if (!transpose)
-    k_reduced<T, false><<<P - 1, 128, sm, s>>>(band, N, K, d, f.V, f.Wt, f.R, g, ctop, cbot, gt);
-  else
-    k_reduced<T, true><<<P - 1, 128, sm, s>>>(band, N, K, d, f.Va, f.Wa, f.Ra, g, ctop, cbot, gt);
+  if (K < kRedStagedK) {
+    size_t sm = 5 * (size_t)K * sizeof(double);
+    count_launches(1);
+    if (!transpose)
+      k_reduced<T, false><<<P - 1, 128, sm, s>>>(band, N, K, d, f.V, f.Wt, f.R, g, ctop, cbot, gt);
+    else
+      k_reduced<T, true><<<P - 1, 128, sm, s>>>(band, N, K, d, f.Va, f.Wa, f.Ra, g, ctop, cbot, gt);
+  } else {
+    double* rhs = cbot + (int64_t)(P - 1) * K;     // three (P - 1) K vectors after cbot
+    double* xt = rhs + (int64_t)(P - 1) * K;
+    double* xb = xt + (int64_t)(P - 1) * K;
+    const dim3 grid((K + kRedRows - 1) / kRedRows, P - 1);
+    const size_t sm = (size_t)K * sizeof(double);
+    count_launches(4);
+    k_red_mv<T, RED_RHS><<<grid, 256, sm, s>>>(transpose ? f.Wa : f.Wt, K, d, g, nullptr, rhs, gt);
+    k_red_mv<double, RED_XT><<<grid, 256, sm, s>>>(transpose ? f.Ra : f.R, K, d, g, rhs, xt, gt);
+    k_red_mv<T, RED_XB><<<grid, 256, sm, s>>>(transpose ? f.Va : f.V, K, d, g, xt, xb, gt);
+    if (!transpose) k_red_cpl<false><<<grid, 256, 0, s>>>(band, N, K, d, xt, xb, ctop, cbot, gt);
+    else k_red_cpl<true><<<grid, 256, 0, s>>>(band, N, K, d, xt, xb, ctop, cbot, gt);
+  }
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   return transpose ? launch_block_solve<T, true>(f, K, P, d, r, z, tmp, ctop, cbot, s, gt)

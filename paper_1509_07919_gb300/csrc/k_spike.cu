@@ -140,6 +140,14 @@ k_spikes(const double* __restrict__ band, int64_t N, int K, Dev d, const T* __re
   T* Vi = Vout + (int64_t)i * KK;
   T* Wi = Wout + (int64_t)i * KK;
 
+  if (GM) {     // wide bands: the dense bottom LU tile only; the solves run in k_tip_cols
+    for (int e = tid; e < KK; e += NT) {
+      const int r = e / K, q = e % K;
+      const int64_t gr = n0 - K + r, gq = n0 - K + q;
+      Mx[e] = Fi[(int64_t)(K + gr - gq) * ld + gq];
+    }
+    return;
+  }
   // ---- V tip: M = [L_bb | U_bb] packed (bottom K x K of block i's LU) ----
   for (int e = tid; e < KK; e += NT) {
     int r = e / K, q = e % K;
@@ -187,7 +195,6 @@ k_spikes(const double* __restrict__ band, int64_t N, int K, Dev d, const T* __re
   }
   __syncthreads();
   for (int e = tid; e < KK; e += NT) Wi[e] = X[e];
-  if (GM) return;     // wide bands: Rbar, its GEPP and inverse by k_rbar_form / _gepp / _inv
   // ---- Rbar = I - W V in FP64 (V re-read from global, W in X) ----
   __syncthreads();
   for (int e = tid; e < KK; e += NT) Mx[e] = Vi[e];
@@ -227,7 +234,61 @@ k_spikes(const double* __restrict__ band, int64_t N, int K, Dev d, const T* __re
   for (int k = tid; k < K; k += NT) pivout[(int64_t)i * K + k] = pivs[k];
 }
 
-// ---- wide bands: Rbar, GEPP and inverse spread over more CTAs ----
+// ---- wide bands: tips, Rbar, GEPP and inverse spread over more CTAs ----
+
+// Spike tips, 32 columns per CTA (one per thread, K x 32 right-hand sides in
+// shared memory), the factor tiles read row-wise from global memory:
+// blockIdx.z = 0 the V tip (dense bottom LU tile, copied by k_spikes),
+// 1 the W tip (top UL tiles); grid (ceil(K / 32), P - 1, 2).
+template <typename T>
+__global__ void __launch_bounds__(32)
+k_tip_cols(const double* __restrict__ band, int64_t N, int K, Dev d, const T* __restrict__ ULt, bool adjoint,
+           T* __restrict__ Vout, T* __restrict__ Wout, const unsigned char* __restrict__ gws) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* Xs = reinterpret_cast<T*>(smem_raw);    // K x 32
+  const int i = blockIdx.y;
+  const int lane = threadIdx.x;
+  const int col = blockIdx.x * 32 + lane;
+  const int64_t s = d.off[i + 1];
+  const int64_t KK = (int64_t)K * K;
+  const bool vtip = blockIdx.z == 0;
+  const T* M = vtip ? reinterpret_cast<const T*>(gws + (size_t)i * spike_ws_stride(K, sizeof(T)) +
+                                                 (size_t)K * K * sizeof(double))
+                    : ULt + i * KK;
+  if (col < K) {
+    for (int r = 0; r < K; ++r) {
+      const int q = col;
+      double v = 0.0;
+      if (vtip) {   // forward B_i(r,q) = a(s-K+r, s+q) (q <= r); adjoint C_{i+1}^T(r,q) = a(s+q, s-K+r)
+        if (!adjoint) { if (q <= r) v = band[(int64_t)(r - q) * N + s + q]; }
+        else { if (r >= q) v = band[(int64_t)(2 * K + q - r) * N + s - K + r]; }
+      } else {      // forward C_{i+1}(r,q) = a(s+r, s-K+q) (q >= r); adjoint B_i^T(r,q) = a(s-K+q, s+r)
+        if (!adjoint) { if (q >= r) v = band[(int64_t)(2 * K + r - q) * N + s - K + q]; }
+        else { if (r <= q) v = band[(int64_t)(q - r) * N + s + r]; }
+      }
+      Xs[r * 32 + lane] = (T)v;
+    }
+    if (vtip) {
+      if (!adjoint) {
+        tri_col(M, K, true, true, false, Xs, lane, 32);    // L_bb (unit lower)
+        tri_col(M, K, false, false, false, Xs, lane, 32);  // U_bb
+      } else {
+        tri_col(M, K, false, false, true, Xs, lane, 32);   // U_bb^T (lower)
+        tri_col(M, K, true, true, true, Xs, lane, 32);     // L_bb^T (unit upper)
+      }
+    } else {
+      if (!adjoint) {
+        tri_col(M, K, false, true, false, Xs, lane, 32);   // U'_tt (unit upper)
+        tri_col(M, K, true, false, false, Xs, lane, 32);   // L'_tt (lower)
+      } else {
+        tri_col(M, K, true, false, true, Xs, lane, 32);    // L'_tt^T (upper)
+        tri_col(M, K, false, true, true, Xs, lane, 32);    // U'_tt^T (unit lower)
+      }
+    }
+    T* out = (vtip ? Vout : Wout) + i * KK;
+    for (int r = 0; r < K; ++r) out[(int64_t)r * K + col] = Xs[r * 32 + lane];
+  }
+}
 
 // Rbar_i = I - W^(t)_{i+1} V^(b)_i in FP64 (R0, and a copy in the interface's
 // workspace for the GEPP), 64 x 64 output tiles, 16-deep panels of W and V
@@ -360,6 +421,13 @@ cudaError_t launch_spikes(const double* band, int64_t N, int K, int P, Dev d, co
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || !gm) return e;
   unsigned char* gws = static_cast<unsigned char*>(gscratch);
+  const size_t tsm = (size_t)K * 32 * sizeof(T);
+  if (tsm > 48 * 1024) {
+    e = cudaFuncSetAttribute(k_tip_cols<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsm);
+    if (e != cudaSuccess) return e;
+  }
+  count_launches(1);
+  k_tip_cols<T><<<dim3((K + 31) / 32, P - 1, 2), 32, tsm, s>>>(band, N, K, d, ULt, adjoint, V, Wt, gws);
   const int tiles = (K + RT - 1) / RT;
   count_launches(3);
   k_rbar_form<T><<<dim3(tiles, tiles, P - 1), 256, 0, s>>>(V, Wt, K, R0, gws);

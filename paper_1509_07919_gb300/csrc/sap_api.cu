@@ -166,7 +166,7 @@ struct Solver : SolverBase {
     TRY(h->mem.alloc(&f.F, (size_t)L.f_elems));
     // the padding columns [n_i, ld_i) of every block are read by the sweeps and must be 0
     CK(cudaMemset(f.F, 0, (size_t)L.f_elems * sizeof(T)));
-    TRY(h->mem.alloc(&scratch, (size_t)(2 * L.N + 2 * nI * K + 8)));
+    TRY(h->mem.alloc(&scratch, (size_t)(2 * L.N + 5 * nI * K + 8)));
     if (sizeof(T) == 4) TRY(h->mem.alloc(&bandf, (size_t)L.N * L.W));
     if (lu_window_global(K, sizeof(T) == 8)) {
       TRY(h->mem.alloc(&wlu, (size_t)P * lu_window_elems(K)));

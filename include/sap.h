@@ -55,7 +55,14 @@ typedef enum {
 } sap_status_t;
 
 typedef enum { SAP_D = 0, SAP_C = 1 } sap_variant_t;          /* Sec. 2.1.1 */
-typedef enum { SAP_FP64 = 0, SAP_FP32 = 1 } sap_precision_t;  /* Sec. 3.1 mixed precision */
+/* Sec. 3.1 mixed precision.  SAP_FP32_BF16TU (a GB300 addition): FP32 factors
+ * whose block LU/UL trailing updates (the rank-16 products of each 16-column
+ * panel) run on the tensor cores with BF16 operands (RN) and FP32
+ * accumulation, for K >= 64 (below that it equals SAP_FP32); pivots, panels,
+ * tips, sweeps and everything FP64 as with SAP_FP32.  The factors then carry
+ * BF16-level error and the FP64 BiCGStab(2) makes up for it with more
+ * iterations. */
+typedef enum { SAP_FP64 = 0, SAP_FP32 = 1, SAP_FP32_BF16TU = 2 } sap_precision_t;
 
 typedef struct {
     int32_t P;            /* number of diagonal blocks, 1 <= P <= N (Sec. 3.1) */

@@ -22,7 +22,7 @@ LIB_PATH = os.path.join(_HERE, "libsap.so")
 SAP_OK, SAP_ERR_INVALID_ARG, SAP_ERR_OOM, SAP_ERR_NOT_CONVERGED, SAP_ERR_BREAKDOWN = 0, 1, 2, 3, 4
 SAP_ERR_TIMEOUT, SAP_ERR_CUDA, SAP_ERR_NOT_IMPLEMENTED, SAP_ERR_SINGULAR = 5, 6, 7, 8
 SAP_D, SAP_C = 0, 1
-SAP_FP64, SAP_FP32 = 0, 1
+SAP_FP64, SAP_FP32, SAP_FP32_BF16TU = 0, 1, 2
 
 
 class SapError(RuntimeError):

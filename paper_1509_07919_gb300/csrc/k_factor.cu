@@ -21,10 +21,12 @@
 // J A_i J: if J A_i J = L~ U~ (unit L~) then A_i = (J L~ J)(J U~ J) = U' L'
 // with unit upper U'.  Only the last K rows/columns of L~, U~ are kept,
 // flipped back into the top K x K tiles of U' and L'.
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <algorithm>
 #include <cstdint>
 #include "sap_internal.cuh"
+#include "tc_sm103.cuh"
 
 namespace sap {
 
@@ -86,15 +88,78 @@ __device__ __forceinline__ void ld4(const T* p, T (&v)[4]) {
   }
 }
 
+// Tensor-core trailing update (TC): per panel the rank-16 product L21 U12 is
+// formed by tcgen05 MMAs, BF16 operands (RN) and FP32 accumulation, in
+// 128 x 128 pieces of TMEM (four at a time), and subtracted from the FP32
+// window; pivots, the panel and U12 stay FP32.  Operand rows r (trailing rows
+// of L21, trailing columns of U12) in the no-swizzle K-major layout: element
+// (r, q) at (r / 8) 128 + (q / 8) 64 + (r % 8) 8 + q % 8 BF16 elements.
+constexpr int kTcPiece = 128;
+struct TcCtx {
+  __nv_bfloat16* A = nullptr;   // Kp x 16 (L21)
+  __nv_bfloat16* B = nullptr;   // Kp x 16 (U12 transposed)
+  uint64_t* bar = nullptr;      // MMA completion
+  uint32_t taddr = 0;           // TMEM base
+  unsigned ph = 0;              // next phase parity of bar
+  bool failed = false;          // a bounded wait of this thread gave up
+  int* err = nullptr;
+};
+__host__ __device__ inline int tc_rows(int K) { return ((K + 15) / 16 * 16 + kTcPiece - 1) / kTcPiece * kTcPiece; }
+__host__ __device__ inline uint32_t tc_cols(int K) {
+  const int nmt = tc_rows(K) / kTcPiece;
+  return nmt * nmt >= 4 ? 512u : (uint32_t)(nmt * nmt * kTcPiece);   // 1 piece: 128, more: 4 pieces
+}
+__host__ __device__ inline size_t tc_bytes(int K) { return (size_t)tc_rows(K) * 16 * 2 * 2 + 16; }
+
+// Operand buffers, barrier and TMEM of the CTA (whole CTA; warp 0 allocates).
+__device__ void tc_setup(unsigned char* base, int K, TcCtx& t, int* err) {
+  const int Kp = tc_rows(K);
+  t.A = reinterpret_cast<__nv_bfloat16*>(base);
+  t.B = t.A + Kp * 16;
+  t.bar = reinterpret_cast<uint64_t*>(t.B + Kp * 16);
+  uint32_t* slot = reinterpret_cast<uint32_t*>(t.bar + 1);
+  t.err = err;
+  for (int e = threadIdx.x; e < Kp * 16; e += blockDim.x) {
+    t.A[e] = __float2bfloat16_rn(0.f);
+    t.B[e] = __float2bfloat16_rn(0.f);
+  }
+  if (threadIdx.x == 0) {
+    tc::mbar_init(t.bar, 1);
+    tc::mbar_fence_init();
+  }
+  if (threadIdx.x < 32) {
+    tc::tmem_alloc(slot, tc_cols(K));
+    tc::tmem_relinquish();
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  t.taddr = *slot;
+}
+__device__ void tc_teardown(TcCtx& t, int K) {
+  // a thread whose wait gave up waits once more (bounded) for the MMAs in flight
+  if (t.failed) {
+    bool again = false;
+    tc::mbar_wait_bounded(t.bar, t.ph ^ 1u, 1 << 22, nullptr, again);
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    tc::fence_after_sync();
+    tc::tmem_dealloc(t.taddr, tc_cols(K));
+  }
+}
+
 // Factor one block (rows s .. s+n-1 of the band) with the whole CTA; F: the
 // block's factor storage (LU) or flipped top tiles (REV, ld unused).
 // GW: the window in global memory at wglob (M2 x LDW, L2-resident) instead
 // of shared memory; wide bands whose (K+16)^2 window does not fit in
 // shared memory use the global form, the staging buffers stay in shared memory.
-template <typename T, bool REV, bool GW>
+template <typename T, bool REV, bool GW, bool TC>
 __device__ void band_lu_block(unsigned char* smem_raw, const T* __restrict__ band, int64_t N, int K, int64_t s,
                               int n, int64_t ld, T* __restrict__ F, const T tau,
-                              unsigned long long* __restrict__ n_boosted, T* wglob) {
+                              unsigned long long* __restrict__ n_boosted, T* wglob, TcCtx& tcx) {
+  static_assert(!TC || sizeof(T) == 4, "the tensor-core trailing update is an FP32-factor mode");
   const int M2 = win_m2(K);
   const int LDW = M2 + 4;
   const int KA = K + NB;          // active rows/cols of the window in a panel step
@@ -230,7 +295,60 @@ __device__ void band_lu_block(unsigned char* smem_raw, const T* __restrict__ ban
     }
     __syncthreads();
 
-    // ---- C: A22 -= L21 U12 over window rows/cols [NB, NB + 4 ceil(K/4)), 4 x 4 tiles ----
+    // ---- C: A22 -= L21 U12 over window rows/cols [NB, NB + K) ----
+    if constexpr (TC) {
+      const int Kr = (K + 15) / 16 * 16;        // trailing rows / cols touched (16-aligned groups)
+      for (int e = tid; e < Kr * NB; e += NTHREADS) {
+        const int r = e / NB, q = e % NB;
+        const T a = r < K ? W[w.ph(NB + r) * LDW + base + q] : T(0);     // L21(r, q)
+        const T b = r < K ? W[(base + q) * LDW + w.ph(NB + r)] : T(0);    // U12(q, r)
+        const int off = (r >> 3) * 128 + (q >> 3) * 64 + (r & 7) * 8 + (q & 7);
+        tcx.A[off] = __float2bfloat16_rn((float)a);
+        tcx.B[off] = __float2bfloat16_rn((float)b);
+      }
+      tc::fence_async_smem();
+      __syncthreads();
+      const int nmt = (Kr + kTcPiece - 1) / kTcPiece;
+      const int npieces = nmt * nmt;
+      constexpr uint32_t idesc = tc::idesc_bf16_f32(kTcPiece, kTcPiece);
+      const int qd = warp & 3, hw = warp >> 2;
+      for (int g0 = 0; g0 < npieces; g0 += 4) {
+        const int gn = npieces - g0 < 4 ? npieces - g0 : 4;
+        if (tid == 0) {
+          tc::fence_after_sync();
+          for (int p = 0; p < gn; ++p) {
+            const int mt = (g0 + p) / nmt, nc = (g0 + p) % nmt;
+            tc::mma_bf16(tcx.taddr + (uint32_t)(kTcPiece * p), tc::smem_desc(tcx.A + mt * kTcPiece * 16, 128, 256),
+                         tc::smem_desc(tcx.B + nc * kTcPiece * 16, 128, 256), idesc, 0u);
+          }
+          tc::mma_commit(tcx.bar);
+        }
+        tc::mbar_wait_bounded(tcx.bar, tcx.ph, 1 << 22, tcx.err, tcx.failed);
+        tcx.ph ^= 1u;
+        tc::fence_after_sync();
+        for (int p = 0; p < gn; ++p) {
+          const int mt = (g0 + p) / nmt, nc = (g0 + p) % nmt;
+          const int r = mt * kTcPiece + qd * 32 + lane;      // trailing row of this lane
+          for (int j = hw; j < kTcPiece / 16; j += 2) {
+            const int c0 = nc * kTcPiece + j * 16;          // first of 16 trailing columns
+            if (c0 >= Kr) break;                            // warp-uniform
+            float v[16];
+            tc::ld_32x32b_x16(tcx.taddr + ((uint32_t)(qd * 32) << 16) + (uint32_t)(kTcPiece * p + j * 16), v);
+            if (r < Kr) {
+              T* row = &W[w.ph(NB + r) * LDW + w.ph(NB + c0)];   // 16-aligned offsets never wrap
+#pragma unroll
+              for (int y4 = 0; y4 < 4; ++y4) {
+                float4 x = *reinterpret_cast<float4*>(row + 4 * y4);
+                x.x -= v[4 * y4]; x.y -= v[4 * y4 + 1]; x.z -= v[4 * y4 + 2]; x.w -= v[4 * y4 + 3];
+                *reinterpret_cast<float4*>(row + 4 * y4) = x;
+              }
+            }
+          }
+        }
+        tc::fence_before_sync();
+        __syncthreads();     // TMEM read before the next group's MMAs overwrite it
+      }
+    } else
     {
       const int nt = (K + 3) / 4;
       for (int t = tid; t < nt * nt; t += NTHREADS) {
@@ -300,12 +418,26 @@ __device__ void band_lu_block(unsigned char* smem_raw, const T* __restrict__ ban
   if (warp == 0 && lane == 0 && nb) atomicAdd(n_boosted, nb);
 }
 
-template <typename T, bool REV, bool GW>
+// shared memory of the factor kernel: window (unless global) + staging
+// (+ the tensor-core operands, barrier and TMEM slot)
+__host__ __device__ inline size_t lu_smem_hd(int K, bool fp64, bool global_window, bool tc) {
+  const int M2 = win_m2(K);
+  const size_t ts = fp64 ? sizeof(double) : sizeof(float);
+  size_t b = ((size_t)NB * M2 + (size_t)(M2 - NB) * NB + NB) * ts;
+  if (!global_window) b += ((size_t)M2 * (M2 + 4) * ts + 15) & ~(size_t)15;
+  if (tc) b = ((b + 127) & ~(size_t)127) + tc_bytes(K);
+  return b;
+}
+__host__ __device__ inline size_t lu_tc_offset(int K, bool global_window) {
+  return (lu_smem_hd(K, false, global_window, false) + 127) & ~(size_t)127;
+}
+
+template <typename T, bool REV, bool GW, bool TC>
 __global__ void __launch_bounds__(NTHREADS)
 k_band_lu(const T* __restrict__ band, int64_t N, int K, Dev d, int block0,
           const double* __restrict__ absmax, double eps, T* __restrict__ out,
-          unsigned long long* __restrict__ n_boosted, T* __restrict__ wscratch) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+          unsigned long long* __restrict__ n_boosted, T* __restrict__ wscratch, int* __restrict__ err) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   const int b = block0 + blockIdx.x;
   const int64_t s = d.off[b];
   const int n = (int)(d.off[b + 1] - s);
@@ -313,18 +445,23 @@ k_band_lu(const T* __restrict__ band, int64_t N, int K, Dev d, int block0,
   T* F = REV ? out + (int64_t)(b - 1) * K * K : out + d.fbase[b];
   const int M2 = win_m2(K);
   T* wg = GW ? wscratch + (int64_t)blockIdx.x * M2 * (M2 + 4) : nullptr;
-  band_lu_block<T, REV, GW>(smem_raw, band, N, K, s, n, ld, F, (T)(eps * absmax[0]), n_boosted, wg);
+  TcCtx tcx;
+  if constexpr (TC) tc_setup(smem_raw + lu_tc_offset(K, GW), K, tcx, err);
+  band_lu_block<T, REV, GW, TC>(smem_raw, band, N, K, s, n, ld, F, (T)(eps * absmax[0]), n_boosted, wg, tcx);
+  if constexpr (TC) tc_teardown(tcx, K);
 }
 
 // Persistent LU over a work list of blocks of many systems (LuItem, longest
 // first): each CTA takes the next item from an atomic counter until the list
 // is exhausted, so one launch factors every block of a batch.
-template <typename T, bool GW>
+template <typename T, bool GW, bool TC>
 __global__ void __launch_bounds__(NTHREADS)
 k_band_lu_items(const LuItem* __restrict__ items, int nitems, unsigned* __restrict__ counter,
-                T* __restrict__ wscratch, int64_t wstride) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+                T* __restrict__ wscratch, int64_t wstride, int Kmax, int* __restrict__ err) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ int cur;
+  TcCtx tcx;
+  if constexpr (TC) tc_setup(smem_raw + lu_tc_offset(Kmax, GW), Kmax, tcx, err);
   for (;;) {
     if (threadIdx.x == 0) cur = (int)atomicAdd(counter, 1u);
     __syncthreads();
@@ -332,46 +469,47 @@ k_band_lu_items(const LuItem* __restrict__ items, int nitems, unsigned* __restri
     __syncthreads();          // every thread has read cur before it changes
     if (it >= nitems) break;
     const LuItem I = items[it];
-    band_lu_block<T, false, GW>(smem_raw, reinterpret_cast<const T*>(I.band), I.N, I.K, I.s, I.n, I.ld,
-                                reinterpret_cast<T*>(I.F), (T)(I.eps * I.absmax[0]), I.nb,
-                                GW ? wscratch + (int64_t)blockIdx.x * wstride : nullptr);
+    band_lu_block<T, false, GW, TC>(smem_raw, reinterpret_cast<const T*>(I.band), I.N, I.K, I.s, I.n, I.ld,
+                                    reinterpret_cast<T*>(I.F), (T)(I.eps * I.absmax[0]), I.nb,
+                                    GW ? wscratch + (int64_t)blockIdx.x * wstride : nullptr, tcx);
     __syncthreads();
   }
+  if constexpr (TC) tc_teardown(tcx, Kmax);
+}
+
+template <typename T, bool REV, bool GW>
+auto lu_kernel(bool tc) {
+  if constexpr (sizeof(T) == 4) return tc ? k_band_lu<T, REV, GW, true> : k_band_lu<T, REV, GW, false>;
+  else return k_band_lu<T, REV, GW, false>;
 }
 
 template <typename T, bool REV>
 cudaError_t launch_lu_impl(const T* band, int64_t N, int K, int nblocks, int block0, Dev d,
                            const double* absmax, double eps, T* out, unsigned long long* nb,
-                           T* wscratch, cudaStream_t s) {
+                           T* wscratch, bool tc, int* err, cudaStream_t s) {
   if (nblocks <= 0) return cudaSuccess;
-  const bool gw = lu_window_global(K, sizeof(T) == 8);
+  tc = tc && sizeof(T) == 4;
+  const bool gw = lu_window_global(K, sizeof(T) == 8, tc);
   if (gw && !wscratch) return cudaErrorInvalidValue;
-  const size_t smem = lu_smem_used(K, sizeof(T) == 8, gw);
-  auto kern = gw ? k_band_lu<T, REV, true> : k_band_lu<T, REV, false>;
+  const size_t smem = lu_smem_used(K, sizeof(T) == 8, gw, tc);
+  auto kern = gw ? lu_kernel<T, REV, true>(tc) : lu_kernel<T, REV, false>(tc);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   count_launches(1);
-  kern<<<nblocks, NTHREADS, smem, s>>>(band, N, K, d, block0, absmax, eps, out, nb, wscratch);
+  kern<<<nblocks, NTHREADS, smem, s>>>(band, N, K, d, block0, absmax, eps, out, nb, wscratch, err);
   return cudaGetLastError();
 }
 
 }  // namespace
 
-// shared memory of the factor kernel: window (unless global) + staging
-size_t lu_smem_used(int K, bool fp64, bool global_window) {
-  const int M2 = win_m2(K);
-  const size_t ts = fp64 ? sizeof(double) : sizeof(float);
-  const size_t stage = ((size_t)NB * M2 + (size_t)(M2 - NB) * NB + NB) * ts;
-  if (global_window) return stage;
-  return (((size_t)M2 * (M2 + 4) * ts + 15) & ~(size_t)15) + stage;
-}
-bool lu_window_global(int K, bool fp64) { return lu_smem_used(K, fp64, false) > kSmemPerBlock; }
+size_t lu_smem_used(int K, bool fp64, bool global_window, bool tc) { return lu_smem_hd(K, fp64, global_window, tc); }
+bool lu_window_global(int K, bool fp64, bool tc) { return lu_smem_used(K, fp64, false, tc) > kSmemPerBlock; }
 size_t lu_window_elems(int K) {
   const int M2 = win_m2(K);
   return (size_t)M2 * (M2 + 4);
 }
 
-size_t lu_smem_bytes(int K, bool fp64) { return lu_smem_used(K, fp64, lu_window_global(K, fp64)); }
+size_t lu_smem_bytes(int K, bool fp64, bool tc) { return lu_smem_used(K, fp64, lu_window_global(K, fp64, tc), tc); }
 
 namespace {
 
@@ -433,27 +571,33 @@ cudaError_t launch_absmax(const double* band, int64_t N, int K, double* out, cud
 
 template <typename T>
 cudaError_t launch_factor_lu(const T* band, int64_t N, int K, int P, Dev d, const double* absmax,
-                             double eps, T* F, unsigned long long* nb, T* wscratch, cudaStream_t s) {
-  return launch_lu_impl<T, false>(band, N, K, P, 0, d, absmax, eps, F, nb, wscratch, s);
+                             double eps, T* F, unsigned long long* nb, T* wscratch, bool tc, int* err,
+                             cudaStream_t s) {
+  return launch_lu_impl<T, false>(band, N, K, P, 0, d, absmax, eps, F, nb, wscratch, tc, err, s);
 }
 
 template <typename T>
 cudaError_t launch_factor_ul(const T* band, int64_t N, int K, int P, Dev d, const double* absmax,
-                             double eps, T* ULt, unsigned long long* nb, T* wscratch, cudaStream_t s) {
+                             double eps, T* ULt, unsigned long long* nb, T* wscratch, bool tc, int* err,
+                             cudaStream_t s) {
   // UL tiles are only needed for blocks 1..P-1 (the W^(t) tips)
-  return launch_lu_impl<T, true>(band, N, K, P - 1, 1, d, absmax, eps, ULt, nb, wscratch, s);
+  return launch_lu_impl<T, true>(band, N, K, P - 1, 1, d, absmax, eps, ULt, nb, wscratch, tc, err, s);
 }
 
-int lu_items_grid(int nitems, int Kmax, bool fp64) {
-  const size_t smem = lu_smem_bytes(Kmax, fp64);
-  const bool gw = lu_window_global(Kmax, fp64);
+int lu_items_grid(int nitems, int Kmax, bool fp64, bool tc) {
+  tc = tc && !fp64;
+  const size_t smem = lu_smem_bytes(Kmax, fp64, tc);
+  const bool gw = lu_window_global(Kmax, fp64, tc);
   int per_sm = 0;
   auto occ = [&](auto kern) {
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NTHREADS, smem);
   };
-  if (fp64) gw ? occ(k_band_lu_items<double, true>) : occ(k_band_lu_items<double, false>);
-  else gw ? occ(k_band_lu_items<float, true>) : occ(k_band_lu_items<float, false>);
+  if (fp64) gw ? occ(k_band_lu_items<double, true, false>) : occ(k_band_lu_items<double, false, false>);
+  else if (tc) gw ? occ(k_band_lu_items<float, true, true>) : occ(k_band_lu_items<float, false, true>);
+  else gw ? occ(k_band_lu_items<float, true, false>) : occ(k_band_lu_items<float, false, false>);
+  // resident CTAs hold their TMEM for the whole launch: no more per SM than fit in its 512 columns
+  if (tc) per_sm = std::min(per_sm, (int)(512u / tc_cols(Kmax)));
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -462,31 +606,40 @@ int lu_items_grid(int nitems, int Kmax, bool fp64) {
 
 template <typename T>
 cudaError_t launch_factor_lu_items(const LuItem* items, int nitems, int Kmax, unsigned* counter, T* wscratch,
-                                   cudaStream_t s) {
+                                   bool tc, int* err, cudaStream_t s) {
   if (nitems <= 0) return cudaSuccess;
   const bool fp64 = sizeof(T) == 8;
-  const bool gw = lu_window_global(Kmax, fp64);
+  tc = tc && !fp64;
+  const bool gw = lu_window_global(Kmax, fp64, tc);
   if (gw && !wscratch) return cudaErrorInvalidValue;
-  const size_t smem = lu_smem_bytes(Kmax, fp64);
-  auto kern = gw ? k_band_lu_items<T, true> : k_band_lu_items<T, false>;
-  const int grid = lu_items_grid(nitems, Kmax, fp64);   // also sets the shared-memory attribute
+  const size_t smem = lu_smem_bytes(Kmax, fp64, tc);
+  void (*kern)(const LuItem*, int, unsigned*, T*, int64_t, int, int*);
+  if constexpr (sizeof(T) == 4) {
+    if (tc) kern = gw ? k_band_lu_items<T, true, true> : k_band_lu_items<T, false, true>;
+    else kern = gw ? k_band_lu_items<T, true, false> : k_band_lu_items<T, false, false>;
+  } else {
+    kern = gw ? k_band_lu_items<T, true, false> : k_band_lu_items<T, false, false>;
+  }
+  const int grid = lu_items_grid(nitems, Kmax, fp64, tc);   // also sets the shared-memory attribute
   cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned), s);
   if (e != cudaSuccess) return e;
   count_launches(1);
-  kern<<<grid, NTHREADS, smem, s>>>(items, nitems, counter, wscratch, (int64_t)lu_window_elems(Kmax));
+  kern<<<grid, NTHREADS, smem, s>>>(items, nitems, counter, wscratch, (int64_t)lu_window_elems(Kmax), Kmax, err);
   return cudaGetLastError();
 }
 
-template cudaError_t launch_factor_lu_items<float>(const LuItem*, int, int, unsigned*, float*, cudaStream_t);
-template cudaError_t launch_factor_lu_items<double>(const LuItem*, int, int, unsigned*, double*, cudaStream_t);
+template cudaError_t launch_factor_lu_items<float>(const LuItem*, int, int, unsigned*, float*, bool, int*,
+                                                   cudaStream_t);
+template cudaError_t launch_factor_lu_items<double>(const LuItem*, int, int, unsigned*, double*, bool, int*,
+                                                    cudaStream_t);
 
 template cudaError_t launch_factor_lu<float>(const float*, int64_t, int, int, Dev, const double*, double,
-                                             float*, unsigned long long*, float*, cudaStream_t);
+                                             float*, unsigned long long*, float*, bool, int*, cudaStream_t);
 template cudaError_t launch_factor_lu<double>(const double*, int64_t, int, int, Dev, const double*, double,
-                                              double*, unsigned long long*, double*, cudaStream_t);
+                                              double*, unsigned long long*, double*, bool, int*, cudaStream_t);
 template cudaError_t launch_factor_ul<float>(const float*, int64_t, int, int, Dev, const double*, double,
-                                             float*, unsigned long long*, float*, cudaStream_t);
+                                             float*, unsigned long long*, float*, bool, int*, cudaStream_t);
 template cudaError_t launch_factor_ul<double>(const double*, int64_t, int, int, Dev, const double*, double,
-                                              double*, unsigned long long*, double*, cudaStream_t);
+                                              double*, unsigned long long*, double*, bool, int*, cudaStream_t);
 
 }  // namespace sap

@@ -69,6 +69,8 @@ struct SolverBase {
   virtual sap_status_t interface(int i, int which, bool adjoint, double* host, cudaStream_t s) = 0;
   // SAP_ERR_TIMEOUT (and reset) if a device-side wait gave up since the last call
   virtual sap_status_t take_device_error(cudaStream_t s) = 0;
+  virtual sap_status_t take_factor_error() = 0;
+  virtual int* err_flag() = 0;
 };
 
 }  // namespace
@@ -168,7 +170,7 @@ struct Solver : SolverBase {
     CK(cudaMemset(f.F, 0, (size_t)L.f_elems * sizeof(T)));
     TRY(h->mem.alloc(&scratch, (size_t)(2 * L.N + 5 * nI * K + 8)));
     if (sizeof(T) == 4) TRY(h->mem.alloc(&bandf, (size_t)L.N * L.W));
-    if (lu_window_global(K, sizeof(T) == 8)) {
+    if (lu_window_global(K, sizeof(T) == 8, tc())) {
       TRY(h->mem.alloc(&wlu, (size_t)P * lu_window_elems(K)));
       if (h->opt.variant == SAP_C && P > 1) TRY(h->mem.alloc(&wul, (size_t)(P - 1) * lu_window_elems(K)));
     }
@@ -231,7 +233,7 @@ struct Solver : SolverBase {
       CK(cudaStreamWaitEvent(h->us, h->ev_us0, 0));
       CK(cudaEventRecord(h->evu[0], h->us));
       CK(launch_factor_ul<T>(band_in_T(), L.N, L.K, L.P, h->d, h->absmax, h->opt.boost_eps, f.ULt, h->n_boosted,
-                             wul, h->us));
+                             wul, tc(), f.err, h->us));
       CK(cudaEventRecord(h->evu[1], h->us));
       CK(cudaEventRecord(h->ev_us1, h->us));
     }
@@ -292,7 +294,7 @@ struct Solver : SolverBase {
     const Layout& L = h->L;
     TRY(factor_pre(s));
     CK(launch_factor_lu<T>(band_in_T(), L.N, L.K, L.P, h->d, h->absmax, h->opt.boost_eps, f.F, h->n_boosted,
-                           wlu, s));
+                           wlu, tc(), f.err, s));
     return factor_post(s);
   }
 
@@ -316,6 +318,18 @@ struct Solver : SolverBase {
     adjoint_ready = true;
     return SAP_OK;
   }
+
+  // the tensor-core trailing update of the FP32 factorisation (SAP_FP32_BF16TU, K >= kTcMinK)
+  bool tc() const { return sizeof(T) == 4 && h->opt.precision == SAP_FP32_BF16TU && h->L.K >= kTcMinK; }
+  // a bounded wait of the factor kernels gave up (their error flag, then reset)
+  sap_status_t take_factor_error() override {
+    int e = 0;
+    CK(cudaMemcpy(&e, f.err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (!e) return SAP_OK;
+    CK(cudaMemset(f.err, 0, sizeof(int)));
+    return SAP_ERR_TIMEOUT;
+  }
+  int* err_flag() override { return f.err; }
 
   // the band in the factor precision: the borrowed FP64 band, or its FP32 copy
   const T* band_in_T() const {
@@ -440,7 +454,8 @@ sap_status_t check_options(const sap_options_t* o, int64_t N, int K) {
   if (N < 2 || K < 1 || K >= N) return SAP_ERR_INVALID_ARG;
   if (o->P < 1 || o->P > N) return SAP_ERR_INVALID_ARG;
   if (o->variant != SAP_D && o->variant != SAP_C) return SAP_ERR_INVALID_ARG;
-  if (o->precision != SAP_FP64 && o->precision != SAP_FP32) return SAP_ERR_INVALID_ARG;
+  if (o->precision != SAP_FP64 && o->precision != SAP_FP32 && o->precision != SAP_FP32_BF16TU)
+    return SAP_ERR_INVALID_ARG;
   if (o->segments < 0 || o->reserved0 != 0) return SAP_ERR_INVALID_ARG;
   return SAP_OK;
 }
@@ -687,7 +702,7 @@ sap_status_t finish_factor(sap_handle* h) {
   int sing = 0;
   CK(cudaMemcpy(&sing, h->singular, sizeof(int), cudaMemcpyDeviceToHost));
   if (sing) return SAP_ERR_SINGULAR;
-  return SAP_OK;
+  return h->impl->take_factor_error();
 }
 
 sap_status_t run_factor(sap_handle* h, cudaStream_t s) {
@@ -754,7 +769,7 @@ sap_status_t create_handle(const double* band_dev, int64_t N, int32_t K, const s
     const int ngc = chunk_couplings(K);
     int S = opt.segments;
     if (S == 0) {
-      const bool f32 = opt.precision == SAP_FP32;
+      const bool f32 = opt.precision != SAP_FP64;
       S = std::min((f32 ? 2 : 1) * kSMs / L.P, min_nch / (f32 ? 16 : 32));
       S = S < (f32 ? 4 : 6) ? 1 : std::min(S, kMaxAutoSegments);
     }
@@ -805,6 +820,7 @@ struct sap_batch {
   void* wlu = nullptr;           // per-CTA factor windows when Kmax's window exceeds shared memory
   int nitems = 0, Kmax = 1;
   bool fp64 = false;
+  bool tc = false;               // tensor-core trailing updates (SAP_FP32_BF16TU, Kmax >= kTcMinK)
   cudaEvent_t ev = nullptr;
   ~sap_batch() {
     for (sap_handle* h : hs) delete h;
@@ -835,6 +851,7 @@ sap_status_t build_work_list(sap_batch* B) {
     h->impl->lu_items(items);
     B->Kmax = std::max(B->Kmax, h->L.K);
   }
+  B->tc = !B->fp64 && B->hs[0]->opt.precision == SAP_FP32_BF16TU && B->Kmax >= kTcMinK;
   std::stable_sort(items.begin(), items.end(), [](const LuItem& a, const LuItem& b) {
     return (double)a.n * a.K * a.K > (double)b.n * b.K * b.K;
   });
@@ -845,8 +862,8 @@ sap_status_t build_work_list(sap_batch* B) {
     return SAP_ERR_OOM;
   }
   CK(cudaMemcpy(B->items, items.data(), items.size() * sizeof(LuItem), cudaMemcpyHostToDevice));
-  if (lu_window_global(B->Kmax, B->fp64)) {
-    const size_t bytes = (size_t)lu_items_grid(B->nitems, B->Kmax, B->fp64) * lu_window_elems(B->Kmax) *
+  if (lu_window_global(B->Kmax, B->fp64, B->tc)) {
+    const size_t bytes = (size_t)lu_items_grid(B->nitems, B->Kmax, B->fp64, B->tc) * lu_window_elems(B->Kmax) *
                          (B->fp64 ? sizeof(double) : sizeof(float));
     if (cudaMalloc(&B->wlu, bytes) != cudaSuccess) {
       cudaGetLastError();
@@ -872,10 +889,12 @@ sap_status_t factor_batch(sap_batch* B, cudaStream_t s) {
     CK(cudaEventRecord(h->evj, h->ks));
     CK(cudaStreamWaitEvent(s, h->evj, 0));
   }
+  // the work list's error flag: the first system's (every system's factor phase reads its own)
+  int* err = B->hs[0]->impl->err_flag();
   CK(B->fp64 ? launch_factor_lu_items<double>(B->items, B->nitems, B->Kmax, B->counter,
-                                              static_cast<double*>(B->wlu), s)
+                                              static_cast<double*>(B->wlu), false, err, s)
              : launch_factor_lu_items<float>(B->items, B->nitems, B->Kmax, B->counter,
-                                             static_cast<float*>(B->wlu), s));
+                                             static_cast<float*>(B->wlu), B->tc, err, s));
   CK(cudaEventRecord(B->ev, s));
   for (sap_handle* h : B->hs) {
     CK(cudaStreamWaitEvent(h->ks, B->ev, 0));
@@ -953,7 +972,8 @@ int64_t sap_kernel_launches(void) { return (int64_t)sap::g_launches.load(); }
 int32_t sap_max_K(int32_t precision) {
   const bool fp64 = precision == SAP_FP64;
   int K = kMaxK;
-  while (K > 1 && (sweep_smem_bytes(K, fp64) > kSmemPerBlock || lu_smem_bytes(K, fp64) > kSmemPerBlock ||
+  const bool tc = precision == SAP_FP32_BF16TU;
+  while (K > 1 && (sweep_smem_bytes(K, fp64) > kSmemPerBlock || lu_smem_bytes(K, fp64, tc) > kSmemPerBlock ||
                    chunk_mats_smem_bytes(K, fp64) > kSmemPerBlock))
     --K;
   return K;

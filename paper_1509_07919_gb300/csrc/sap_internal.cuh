@@ -17,15 +17,18 @@ constexpr size_t kSmemPerBlock = 232448;   // opt-in shared memory per CTA on sm
 size_t sweep_smem_bytes(int K, bool fp64);
 // Coupling matrices per chunk of the blocked sweeps: ceil(K / 32).
 int chunk_couplings(int K);
-size_t lu_smem_bytes(int K, bool fp64);
+// tc: the tensor-core (BF16 operand, FP32 accumulate) trailing update of the
+// FP32 factorisation, used from K = kTcMinK on (precision SAP_FP32_BF16TU).
+constexpr int kTcMinK = 64;
+size_t lu_smem_bytes(int K, bool fp64, bool tc = false);
 // Factor window: in shared memory when it fits, else in a global scratch of
 // lu_window_elems(K) elements per CTA (L2-resident); lu_smem_used gives the
 // shared memory of either form.
-size_t lu_smem_used(int K, bool fp64, bool global_window);
-bool lu_window_global(int K, bool fp64);
+size_t lu_smem_used(int K, bool fp64, bool global_window, bool tc = false);
+bool lu_window_global(int K, bool fp64, bool tc = false);
 size_t lu_window_elems(int K);
 // CTAs of the persistent work-list LU for nitems items of half-bandwidth <= Kmax.
-int lu_items_grid(int nitems, int Kmax, bool fp64);
+int lu_items_grid(int nitems, int Kmax, bool fp64, bool tc = false);
 // Shared memory of the chunk-matrix kernel.
 size_t chunk_mats_smem_bytes(int K, bool fp64);
 
@@ -125,14 +128,16 @@ struct LuItem {
 };
 template <typename T>
 cudaError_t launch_factor_lu_items(const LuItem* items, int nitems, int Kmax, unsigned* counter, T* wscratch,
-                                   cudaStream_t s);
+                                   bool tc, int* err, cudaStream_t s);
 
 template <typename T>
 cudaError_t launch_factor_lu(const T* band, int64_t N, int K, int P, Dev d, const double* absmax,
-                             double eps, T* F, unsigned long long* n_boosted, T* wscratch, cudaStream_t s);
+                             double eps, T* F, unsigned long long* n_boosted, T* wscratch, bool tc, int* err,
+                             cudaStream_t s);
 template <typename T>
 cudaError_t launch_factor_ul(const T* band, int64_t N, int K, int P, Dev d, const double* absmax,
-                             double eps, T* ULt, unsigned long long* n_boosted, T* wscratch, cudaStream_t s);
+                             double eps, T* ULt, unsigned long long* n_boosted, T* wscratch, bool tc, int* err,
+                             cudaStream_t s);
 template <typename T>
 cudaError_t launch_spikes(const double* band, int64_t N, int K, int P, Dev d, const T* F, const T* ULt,
                           bool adjoint, T* V, T* Wt, double* Rinv, double* R0, int* piv, int* singular,

@@ -92,7 +92,7 @@ sap_status_t run(const double* band, int64_t N, int K, const double* b, double* 
     if (launch_absmax(band, N, K, absmax, s) != cudaSuccess) return SAP_ERR_CUDA;
     bandT = reinterpret_cast<const T*>(band);
   }
-  if (launch_factor_lu<T>(bandT, N, K, 1, d, absmax, eps, F, nb, wlu, s) != cudaSuccess) return SAP_ERR_CUDA;
+  if (launch_factor_lu<T>(bandT, N, K, 1, d, absmax, eps, F, nb, wlu, false, err, s) != cudaSuccess) return SAP_ERR_CUDA;
   const int64_t* cbase = desc + 4;
   if (launch_chunk_mats<T>(F, K, 1, d, cbase, (int)(ld / 32), 0, Mlf, s) != cudaSuccess) return SAP_ERR_CUDA;
   if (launch_chunk_mats<T>(F, K, 1, d, cbase, (int)(ld / 32), 1, Mub, s) != cudaSuccess) return SAP_ERR_CUDA;

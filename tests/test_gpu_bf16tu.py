@@ -1,0 +1,93 @@
+"""GPU parity of the tensor-core (BF16 operand, FP32 accumulate) trailing
+update of the block LU, precision SAP_FP32_BF16TU, K >= 64.
+
+Factors: against the oracle's BF16 trailing-update emulation (same panel
+organisation, operands rounded to bfloat16, FP64 sums) to a Frobenius-norm
+relative 2e-4 (the remaining difference is FP32 arithmetic, and the rare
+operand that rounds to the other bfloat16 neighbour); their distance to the
+exact FP64 factors is stated and must stay below 1e-2 and exceed ten times
+the FP32 factorisation's, which shows the tensor-core path ran.  Solves: the FP64 BiCGStab(2) still
+reaches relres <= 1e-10 and the oracle's solution within 1e-8."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import sap_inputs as G
+from oracle.bf16tu import block_factors
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sap():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1509_07919_gb300 as S
+    return S
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to("cuda")
+
+
+def host(t):
+    return t.detach().cpu().numpy()
+
+
+def relerr(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+@pytest.mark.parametrize("N,K,P", [(1500, 64, 2), (1300, 100, 2), (1200, 150, 2), (1400, 200, 2), (1100, 300, 2)])
+def test_bf16tu_factors_match_the_bf16_emulation(sap, N, K, P):
+    """K = 64 .. 150: the window in shared memory; 200, 300: in global memory."""
+    band = G.dense_banded(N, K, 1.0, 1700 + K)
+    h = sap.sap_factor(dev(band), N, K, P=P, precision=sap.SAP_FP32_BF16TU)
+    hf = sap.sap_factor(dev(band), N, K, P=P, precision=sap.SAP_FP32)
+    o = O.Sap(band, N, K, P, O.SAP_D)
+    off = o.offsets
+    for i in range(P):
+        fg = sap.sap_get_block_lu(h, i)
+        fe, nb = block_factors(band, N, K, int(off[i]), int(off[i + 1] - off[i]), 0.0)
+        assert nb == 0
+        e_emul = relerr(fg, fe)
+        e_exact = relerr(fg, o.block(i, 0))
+        e_fp32 = relerr(sap.sap_get_block_lu(hf, i), o.block(i, 0))
+        assert e_emul <= 2e-4, (i, e_emul)
+        assert e_exact < 1e-2 and e_exact > 10 * e_fp32, (i, e_exact, e_fp32)
+        print(f"K={K} block {i}: vs BF16 emulation {e_emul:.2e}, vs FP64 {e_exact:.2e}, FP32 vs FP64 {e_fp32:.2e}")
+    assert sap.sap_n_boosted(h) == 0
+
+
+@pytest.mark.parametrize("N,K,P,variant", [(20000, 100, 10, 0), (20000, 200, 10, 0), (12000, 400, 6, 0),
+                                           (8000, 128, 4, 1), (6000, 50, 3, 0)])
+def test_bf16tu_solve_and_adjoint_parity(sap, N, K, P, variant):
+    """K = 50 runs the plain FP32 factorisation (below the tensor-core threshold)."""
+    band = G.dense_banded(N, K, 1.0, 1800 + K)
+    xt = G.x_true(N, 1800 + K)
+    b = O.spmv(band, N, K, xt)
+    xo, io, _ = O.solve(band, N, K, b, P, variant)
+    h = sap.sap_factor(dev(band), N, K, P=P, variant=variant, precision=sap.SAP_FP32_BF16TU)
+    x, info, st = sap.sap_solve(h, dev(b))
+    assert st == sap.SAP_OK and info.relres <= 1e-10
+    assert relerr(host(x), xo) <= 1e-8
+    g = G.adjoint_seed(N, 1800 + K)
+    lo, _, _ = O.solve_adjoint(band, N, K, g, P, variant)
+    lam, ainfo, ast = sap.sap_solve_adjoint(h, dev(g))
+    assert ast == sap.SAP_OK and ainfo.relres <= 1e-10 and relerr(host(lam), lo) <= 1e-8
+
+
+def test_bf16tu_batch(sap):
+    """The persistent work-list LU with tensor-core trailing updates."""
+    specs = [(3000, 96, 51), (2500, 20, 52), (4000, 64, 53), (3500, 130, 54)]
+    bands = [G.dense_banded(N, K, 1.0, sd) for N, K, sd in specs]
+    bs = [O.spmv(bd, N, K, G.x_true(N, sd)) for bd, (N, K, sd) in zip(bands, specs)]
+    bh = sap.sap_factor_batched([dev(b) for b in bands], [s[0] for s in specs], [s[1] for s in specs], P=2,
+                                precision=sap.SAP_FP32_BF16TU)
+    xs, infos, stats, st = sap.sap_solve_batched(bh, [dev(b) for b in bs])
+    assert st == sap.SAP_OK
+    for i, (N, K, _) in enumerate(specs):
+        assert infos[i].relres <= 1e-10
+        xo, _, _ = O.solve(bands[i], N, K, bs[i], 2, O.SAP_D)
+        assert relerr(host(xs[i]), xo) <= 1e-8, i

@@ -501,3 +501,52 @@ def test_convection_diffusion_is_weakly_dominant_m_matrix():
     assert np.all(np.diag(A) >= np.abs(off).sum(1) - 1e-12)
     assert K == 9 and N == 108
     assert not np.allclose(A, A.T)
+
+
+# ------------------------------------------- BF16 trailing-update LU (oracle) ---
+
+def test_bf16_round_matches_hand_computed_ties():
+    """Round to nearest bfloat16, ties to even: the spacing at 1 is 2^-7."""
+    from oracle.bf16tu import bf16_round
+    x = np.array([1.0, 1 + 2.0 ** -8, 1 + 3 * 2.0 ** -8, -(1 + 3 * 2.0 ** -8), 1 + 2.0 ** -8 + 2.0 ** -20,
+                  3.0, 0.0, 2.0 ** -130, 1 + 2.0 ** -9])
+    want = np.array([1.0, 1.0, 1 + 2.0 ** -6, -(1 + 2.0 ** -6), 1 + 2.0 ** -7, 3.0, 0.0, 2.0 ** -130, 1.0])
+    assert np.array_equal(bf16_round(x), want)
+    # every result has at most 8 significant bits; the error is at most half a spacing
+    y = np.random.default_rng(1).uniform(-4, 4, 10000)
+    r = bf16_round(y)
+    m, e = np.frexp(r)
+    assert np.all(np.abs(m * 256 - np.round(m * 256)) == 0)
+    assert np.all(np.abs(r - y) <= 2.0 ** -8 * np.abs(y) + 1e-300)
+
+
+def test_blocked_lu_without_rounding_equals_plain_lu():
+    """The panel organisation of the BF16 trailing-update LU is the plain
+    Doolittle LU of Sec. 3.1 when the operand rounding is the identity."""
+    from oracle.bf16tu import block_factors
+    N, K = 300, 37
+    band = rand_band(N, K, 1.0, 77)
+    f = np.zeros((N, 2 * K + 1))
+    b2 = band.reshape(2 * K + 1, N)
+    for r in range(N):
+        for d in range(-K, K + 1):
+            if 0 <= r + d < N:
+                f[r, d + K] = b2[K - d, r + d]
+    O.block_lu(f, N, K, 0.0)
+    g, nb = block_factors(band, N, K, 0, N, 0.0, rnd=lambda a: a)
+    assert nb == 0
+    assert np.abs(g - f).max() <= 1e-12 * np.abs(f).max()
+
+
+def test_bf16_trailing_update_error_is_at_bf16_level():
+    """With BF16 operands the factors reproduce the block to a BF16-level
+    residual (neither exact nor garbage)."""
+    from oracle.bf16tu import block_lu_panels, dense_block
+    N, K = 400, 64
+    band = rand_band(N, K, 1.0, 78)
+    A = dense_block(band, N, K, 0, N)
+    F, _ = block_lu_panels(A, K, 0.0)
+    L = np.tril(F, -1) + np.eye(N)
+    U = np.triu(F)
+    rel = np.linalg.norm(L @ U - A) / np.linalg.norm(A)
+    assert 1e-5 < rel < 1e-2, rel

@@ -3,11 +3,13 @@ update of the block LU, precision SAP_FP32_BF16TU, K >= 64.
 
 Factors: against the oracle's BF16 trailing-update emulation (same panel
 organisation, operands rounded to bfloat16, FP64 sums) to a Frobenius-norm
-relative 2e-4 (the remaining difference is FP32 arithmetic, and the rare
-operand that rounds to the other bfloat16 neighbour); their distance to the
-exact FP64 factors is stated and must stay below 1e-2 and exceed ten times
-the FP32 factorisation's, which shows the tensor-core path ran.  Solves: the FP64 BiCGStab(2) still
-reaches relres <= 1e-10 and the oracle's solution within 1e-8."""
+relative 2e-6 (measured 0.9e-7 .. 1.5e-7 for K = 64 .. 300: the remaining
+difference is FP32 arithmetic, and the rare operand that rounds to the other
+bfloat16 neighbour); their distance to the exact FP64 factors is stated
+(1.6e-6 .. 7.5e-6 measured) and must stay below 1e-2 and exceed ten times the
+FP32 factorisation's, which shows the tensor-core path ran.  Solves: the FP64
+BiCGStab(2) still reaches relres <= 1e-10 and the oracle's solution within
+1e-8."""
 import numpy as np
 import pytest
 import torch
@@ -54,7 +56,7 @@ def test_bf16tu_factors_match_the_bf16_emulation(sap, N, K, P):
         e_emul = relerr(fg, fe)
         e_exact = relerr(fg, o.block(i, 0))
         e_fp32 = relerr(sap.sap_get_block_lu(hf, i), o.block(i, 0))
-        assert e_emul <= 2e-4, (i, e_emul)
+        assert e_emul <= 2e-6, (i, e_emul)
         assert e_exact < 1e-2 and e_exact > 10 * e_fp32, (i, e_exact, e_fp32)
         print(f"K={K} block {i}: vs BF16 emulation {e_emul:.2e}, vs FP64 {e_exact:.2e}, FP32 vs FP64 {e_fp32:.2e}")
     assert sap.sap_n_boosted(h) == 0

@@ -436,8 +436,13 @@ def run_gpu(args):
     # ---- comparison: FP64 SaP and the other variant (same protocol, fewer steps) ----
     compare = {}
     if not args.no_compare:
-        for name, prec, var in (("sapc_fp64", S.SAP_FP64, S.SAP_C), ("sapd_fp64", S.SAP_FP64, S.SAP_D),
-                                ("sapc_fp32", S.SAP_FP32, S.SAP_C), ("sapd_fp32", S.SAP_FP32, S.SAP_D)):
+        runs = [("sapc_fp64", S.SAP_FP64, S.SAP_C), ("sapd_fp64", S.SAP_FP64, S.SAP_D),
+                ("sapc_fp32", S.SAP_FP32, S.SAP_C), ("sapd_fp32", S.SAP_FP32, S.SAP_D)]
+        if K >= 64:     # the tensor-core (BF16 operand) trailing update of the block LU
+            runs.append(("sapd_bf16tu", S.SAP_FP32_BF16TU, S.SAP_D))
+            if variant == S.SAP_C:
+                runs.append(("sapc_bf16tu", S.SAP_FP32_BF16TU, S.SAP_C))
+        for name, prec, var in runs:
             try:
                 hh = make_handle(prec, var)
             except S.SapError as e:
@@ -446,6 +451,7 @@ def run_gpu(args):
             tt, inf, _, _, _, _ = timed(hh, max(3, args.steps // 2), 2)
             a, c = inf[-1]
             compare[name] = {"ms": statistics.mean(tt), "iters_fwd": a.iters, "iters_adj": c.iters,
+                             "t_lu_ms": a.t_lu_ms,
                              "relres_fwd": a.relres, "relres_adj": c.relres,
                              "t_factor_ms": a.t_factor_ms, "t_fwd_ms": a.t_solve_ms, "t_adj_ms": c.t_solve_ms,
                              "segments": a.segments}

@@ -58,10 +58,12 @@ typedef enum { SAP_D = 0, SAP_C = 1 } sap_variant_t;          /* Sec. 2.1.1 */
 /* Sec. 3.1 mixed precision.  SAP_FP32_BF16TU (a GB300 addition): FP32 factors
  * whose block LU/UL trailing updates (the rank-16 products of each 16-column
  * panel) run on the tensor cores with BF16 operands (RN) and FP32
- * accumulation, for K >= 64 (below that it equals SAP_FP32); pivots, panels,
- * tips, sweeps and everything FP64 as with SAP_FP32.  The factors then carry
- * BF16-level error and the FP64 BiCGStab(2) makes up for it with more
- * iterations. */
+ * accumulation, for K >= 64 as long as the factor window stays in shared
+ * memory with the operand buffers (K <= 192); elsewhere it equals SAP_FP32
+ * (sap_info_t.tc_update reports which ran).  Pivots, panels, tips, sweeps and
+ * everything FP64 as with SAP_FP32.  The factors carry BF16-level error and
+ * the FP64 BiCGStab(2) makes up for it, with more iterations where the
+ * preconditioner is sensitive to it. */
 typedef enum { SAP_FP64 = 0, SAP_FP32 = 1, SAP_FP32_BF16TU = 2 } sap_precision_t;
 
 typedef struct {
@@ -103,6 +105,8 @@ typedef struct {
     float t_spk_ms;       /* SaP-C: B/C, spike tips, Rbar_i, its GEPP and inverse */
     int32_t segments;     /* sweep segments per block in use (sap_options_t.segments) */
     int32_t graphed;      /* 1 if the iterations ran as replays of one captured CUDA graph */
+    int32_t tc_update;    /* 1 if the block LU/UL trailing updates ran on the tensor cores */
+    int32_t reserved1;    /* 0 */
 } sap_info_t;
 
 /* Defaults as documented above. */

@@ -42,7 +42,7 @@ class sap_info_t(C.Structure):
                 ("n_matvec", C.c_int64), ("n_restarts", C.c_int64),
                 ("t_factor_ms", C.c_float), ("t_solve_ms", C.c_float), ("t_lu_ms", C.c_float),
                 ("t_ul_ms", C.c_float), ("t_spk_ms", C.c_float), ("segments", C.c_int32),
-                ("graphed", C.c_int32)]
+                ("graphed", C.c_int32), ("tc_update", C.c_int32), ("reserved1", C.c_int32)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -295,6 +295,25 @@ __device__ void band_lu_block(unsigned char* smem_raw, const T* __restrict__ ban
     }
     __syncthreads();
 
+    // ---- D1: write the finished panel (U rows k0.., L columns k0..) ----
+    auto write_panel = [&]() {
+      for (int e = tid; e < NB * (2 * K + 1); e += NTHREADS) {
+        const int dg = e / NB, t = e % NB;    // diagonal index c = K + i - j, position in panel
+        int i, j;
+        if (dg <= K) { i = k0 + t; j = i + (K - dg); }     // U(i, j), j - i = K - dg
+        else { j = k0 + t; i = j + (dg - K); }             // L(i, j), i - j = dg - K
+        if (i >= n || j >= n) continue;
+        const T v = W[w.ph(i - k0) * LDW + w.ph(j - k0)];
+        if (!REV) {
+          F[(int64_t)dg * ld + j] = v;
+        } else {
+          // keep the last K rows/cols of L~ and U~ of J A J, flipped:
+          // U'(n-1-i, n-1-k) = L~(i, k), L'(n-1-k, n-1-j) = U~(k, j)
+          const int kk = (dg <= K) ? i : j;
+          if (kk >= n - K) F[(int64_t)(n - 1 - i) * K + (n - 1 - j)] = v;
+        }
+      }
+    };
     // ---- C: A22 -= L21 U12 over window rows/cols [NB, NB + K) ----
     if constexpr (TC) {
       const int Kr = (K + 15) / 16 * 16;        // trailing rows / cols touched (16-aligned groups)
@@ -323,6 +342,7 @@ __device__ void band_lu_block(unsigned char* smem_raw, const T* __restrict__ ban
           }
           tc::mma_commit(tcx.bar);
         }
+        if (g0 == 0) write_panel();      // overlaps the MMAs (it reads only the panel's rows / columns)
         tc::mbar_wait_bounded(tcx.bar, tcx.ph, 1 << 22, tcx.err, tcx.failed);
         tcx.ph ^= 1u;
         tc::fence_after_sync();
@@ -381,23 +401,7 @@ __device__ void band_lu_block(unsigned char* smem_raw, const T* __restrict__ ban
         }
       }
     }
-    // ---- D1: write the finished panel (U rows k0.., L columns k0..) ----
-    for (int e = tid; e < NB * (2 * K + 1); e += NTHREADS) {
-      const int dg = e / NB, t = e % NB;    // diagonal index c = K + i - j, position in panel
-      int i, j;
-      if (dg <= K) { i = k0 + t; j = i + (K - dg); }     // U(i, j), j - i = K - dg
-      else { j = k0 + t; i = j + (dg - K); }             // L(i, j), i - j = dg - K
-      if (i >= n || j >= n) continue;
-      const T v = W[w.ph(i - k0) * LDW + w.ph(j - k0)];
-      if (!REV) {
-        F[(int64_t)dg * ld + j] = v;
-      } else {
-        // keep the last K rows/cols of L~ and U~ of J A J, flipped:
-        // U'(n-1-i, n-1-k) = L~(i, k), L'(n-1-k, n-1-j) = U~(k, j)
-        const int kk = (dg <= K) ? i : j;
-        if (kk >= n - K) F[(int64_t)(n - 1 - i) * K + (n - 1 - j)] = v;
-      }
-    }
+    if constexpr (!TC) write_panel();
     if (warp > 0) cp_async_wait_all();
     __syncthreads();
     // ---- D2: slide the window by NB: entering rows/cols replace the panel's ----

@@ -70,6 +70,7 @@ struct SolverBase {
   // SAP_ERR_TIMEOUT (and reset) if a device-side wait gave up since the last call
   virtual sap_status_t take_device_error(cudaStream_t s) = 0;
   virtual sap_status_t take_factor_error() = 0;
+  virtual bool tc_used() const = 0;
   virtual int* err_flag() = 0;
 };
 
@@ -320,7 +321,12 @@ struct Solver : SolverBase {
   }
 
   // the tensor-core trailing update of the FP32 factorisation (SAP_FP32_BF16TU, K >= kTcMinK)
-  bool tc() const { return sizeof(T) == 4 && h->opt.precision == SAP_FP32_BF16TU && h->L.K >= kTcMinK; }
+  // (only where the window stays in shared memory with the operand buffers: measured slower otherwise)
+  bool tc() const {
+    return sizeof(T) == 4 && h->opt.precision == SAP_FP32_BF16TU && h->L.K >= kTcMinK &&
+           !lu_window_global(h->L.K, false, true);
+  }
+  bool tc_used() const override { return tc(); }
   // a bounded wait of the factor kernels gave up (their error flag, then reset)
   sap_status_t take_factor_error() override {
     int e = 0;
@@ -649,6 +655,7 @@ struct KrylovRun {
     inf.t_spk_ms = h->t_spk_ms;
     inf.segments = h->L.S;
     inf.graphed = (h->gexec[gi] != nullptr) ? 1 : 0;
+    inf.tc_update = h->impl->tc_used() ? 1 : 0;
     unsigned long long nb = 0;
     CK(cudaMemcpy(&nb, h->n_boosted, sizeof(nb), cudaMemcpyDeviceToHost));
     inf.n_boosted = (int64_t)nb;
@@ -851,7 +858,8 @@ sap_status_t build_work_list(sap_batch* B) {
     h->impl->lu_items(items);
     B->Kmax = std::max(B->Kmax, h->L.K);
   }
-  B->tc = !B->fp64 && B->hs[0]->opt.precision == SAP_FP32_BF16TU && B->Kmax >= kTcMinK;
+  B->tc = !B->fp64 && B->hs[0]->opt.precision == SAP_FP32_BF16TU && B->Kmax >= kTcMinK &&
+          !lu_window_global(B->Kmax, false, true);
   std::stable_sort(items.begin(), items.end(), [](const LuItem& a, const LuItem& b) {
     return (double)a.n * a.K * a.K > (double)b.n * b.K * b.K;
   });

@@ -41,31 +41,42 @@ def relerr(a, b):
     return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
 
 
-@pytest.mark.parametrize("N,K,P", [(1500, 64, 2), (1300, 100, 2), (1200, 150, 2), (1400, 200, 2), (1100, 300, 2)])
+@pytest.mark.parametrize("N,K,P", [(1500, 64, 2), (1300, 100, 2), (1200, 150, 2), (1400, 192, 2), (1400, 200, 2),
+                                   (1100, 300, 2)])
 def test_bf16tu_factors_match_the_bf16_emulation(sap, N, K, P):
-    """K = 64 .. 150: the window in shared memory; 200, 300: in global memory."""
+    """K = 64 .. 192: tensor-core trailing updates, the window in shared memory;
+    above, the window would not fit with the operand buffers and the plain FP32
+    factorisation runs (bit-identical factors, info.tc_update = 0)."""
     band = G.dense_banded(N, K, 1.0, 1700 + K)
     h = sap.sap_factor(dev(band), N, K, P=P, precision=sap.SAP_FP32_BF16TU)
     hf = sap.sap_factor(dev(band), N, K, P=P, precision=sap.SAP_FP32)
+    _, info, st = sap.sap_solve(h, dev(O.spmv(band, N, K, G.x_true(N, 1700 + K))))
+    assert st == sap.SAP_OK and info.relres <= 1e-10
+    tc = K <= 192
+    assert info.tc_update == int(tc)
     o = O.Sap(band, N, K, P, O.SAP_D)
     off = o.offsets
     for i in range(P):
         fg = sap.sap_get_block_lu(h, i)
+        ff = sap.sap_get_block_lu(hf, i)
+        if not tc:
+            assert np.array_equal(fg, ff)
+            continue
         fe, nb = block_factors(band, N, K, int(off[i]), int(off[i + 1] - off[i]), 0.0)
         assert nb == 0
         e_emul = relerr(fg, fe)
         e_exact = relerr(fg, o.block(i, 0))
-        e_fp32 = relerr(sap.sap_get_block_lu(hf, i), o.block(i, 0))
+        e_fp32 = relerr(ff, o.block(i, 0))
         assert e_emul <= 2e-6, (i, e_emul)
         assert e_exact < 1e-2 and e_exact > 10 * e_fp32, (i, e_exact, e_fp32)
         print(f"K={K} block {i}: vs BF16 emulation {e_emul:.2e}, vs FP64 {e_exact:.2e}, FP32 vs FP64 {e_fp32:.2e}")
     assert sap.sap_n_boosted(h) == 0
 
 
-@pytest.mark.parametrize("N,K,P,variant", [(20000, 100, 10, 0), (20000, 200, 10, 0), (12000, 400, 6, 0),
+@pytest.mark.parametrize("N,K,P,variant", [(20000, 100, 10, 0), (20000, 192, 10, 0), (12000, 400, 6, 0),
                                            (8000, 128, 4, 1), (6000, 50, 3, 0)])
 def test_bf16tu_solve_and_adjoint_parity(sap, N, K, P, variant):
-    """K = 50 runs the plain FP32 factorisation (below the tensor-core threshold)."""
+    """K = 50 and K = 400 run the plain FP32 factorisation (outside the tensor-core range)."""
     band = G.dense_banded(N, K, 1.0, 1800 + K)
     xt = G.x_true(N, 1800 + K)
     b = O.spmv(band, N, K, xt)

@@ -32,15 +32,15 @@ METRIC = "time to rel.res 1e-10 & HBM GB/s: FP32-precond vs FP64 SaP, fwd+adjoin
 # apply on the N=200000, K=50, P=50 workload (automatic segment count), from the
 # ncu capture summarised in profiles/k_sweep_n200k_k50_fp32.md
 TRAFFIC_SWEEPS = 232812800
-# P=None: picked by sap_autotune (measured refactor + solve over N / {16000 .. 1000})
+# P=None: picked by sap_autotune (measured refactor + solve over N / {16000 .. 1000}, 152, 304)
 # before the timed region; P_ref is the oracle's partition count in that case
 # (the autotuner's pick on GB300 when this table was written).
 WORKLOADS = {
     "n200k_k50": dict(N=200000, K=50, d=1.0, P=50, seed_cfg=2),
     "n10k_k10": dict(N=10000, K=10, d=1.2, P=8, seed_cfg=1),
-    "n200k_k100": dict(N=200000, K=100, d=1.0, P=None, P_ref=200, seed_cfg=3),
-    "n200k_k200": dict(N=200000, K=200, d=1.0, P=None, P_ref=100, seed_cfg=3),
-    "n200k_k400": dict(N=200000, K=400, d=1.0, P=None, P_ref=200, seed_cfg=3),
+    "n200k_k100": dict(N=200000, K=100, d=1.0, P=None, P_ref=304, seed_cfg=3),
+    "n200k_k200": dict(N=200000, K=200, d=1.0, P=None, P_ref=152, seed_cfg=3),
+    "n200k_k400": dict(N=200000, K=400, d=1.0, P=None, P_ref=304, seed_cfg=3),
     "convdiff_400x250": dict(N=100000, K=250, d=None, P=32, seed_cfg=4, grid=(400, 250), variant="C"),
 }
 # oracle work (multiply-adds of the factorisations, forward + adjoint) above

@@ -226,7 +226,8 @@ SAP_API sap_status_t sap_band_solve_noalloc(const double *band_dev, int64_t N, i
  *        opt->segments are ignored.
  *   P_cands, nP: candidate partition counts; nP == 0 uses N / {16000, 8000,
  *        4000, 2000, 1000} rounded, clipped to [1, N/64] (SaP-D) or
- *        [1, N/(2K)] (SaP-C), duplicates removed.
+ *        [1, N/(2K)] (SaP-C), then 152 and 304 (one and two blocks per SM
+ *        of a GB300) where within that bound, duplicates removed.
  *   seg_cands, nS: candidate segment counts; nS == 0 uses {0} (automatic).
  *   b_dev: right-hand side for the timing (N doubles on the device), or NULL
  *        for b = A * ones.

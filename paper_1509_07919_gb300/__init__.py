@@ -266,6 +266,9 @@ def sap_autotune(band: torch.Tensor, N: int, K: int, P_cands=None, seg_cands=Non
             p = max(1, min(pmax, (N + rows // 2) // rows))
             if p not in Plist:
                 Plist.append(p)
+        for p in (152, 304):
+            if p <= pmax and p not in Plist:
+                Plist.append(p)
     for i, p in enumerate(Plist[:nused.value]):
         for j, sg in enumerate(Slist):
             table[(p, sg)] = float(ms[i * len(Slist) + j])

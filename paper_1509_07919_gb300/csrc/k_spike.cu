@@ -73,13 +73,14 @@ __host__ __device__ inline size_t spike_ws_stride(int K, int tsize) { return (sp
 
 // GEPP of the K x K FP64 matrix R in place (P R = L U, unit L below the
 // diagonal), ties to the lowest row index; pivs[k] = row swapped with k.  The
-// whole CTA (NT threads) takes part.
+// whole CTA (NTH threads) takes part.
+template <int NTH>
 __device__ void rbar_gepp(double* R, int K, int* pivs, int* singular, double* red_v, int* red_i) {
   const int tid = threadIdx.x;
   for (int k = 0; k < K; ++k) {
     double best = -1.0;
     int bi = k;
-    for (int r = k + tid; r < K; r += NT) {
+    for (int r = k + tid; r < K; r += NTH) {
       double v = fabs(R[r * K + k]);
       if (v > best) { best = v; bi = r; }
     }
@@ -92,7 +93,7 @@ __device__ void rbar_gepp(double* R, int K, int* pivs, int* singular, double* re
     __syncthreads();
     if (tid == 0) {
       double bv = red_v[0]; int bx = red_i[0];
-      for (int w = 1; w < NT / 32; ++w)
+      for (int w = 1; w < NTH / 32; ++w)
         if (red_v[w] > bv || (red_v[w] == bv && red_i[w] < bx)) { bv = red_v[w]; bx = red_i[w]; }
       pivs[k] = bx;
       if (bv == 0.0) atomicExch(singular, 1);
@@ -100,13 +101,13 @@ __device__ void rbar_gepp(double* R, int K, int* pivs, int* singular, double* re
     __syncthreads();
     const int p = pivs[k];
     if (p != k)
-      for (int c = tid; c < K; c += NT) { double t = R[k * K + c]; R[k * K + c] = R[p * K + c]; R[p * K + c] = t; }
+      for (int c = tid; c < K; c += NTH) { double t = R[k * K + c]; R[k * K + c] = R[p * K + c]; R[p * K + c] = t; }
     __syncthreads();
     const double pv = R[k * K + k];
-    for (int r = k + 1 + tid; r < K; r += NT) R[r * K + k] = (pv != 0.0) ? R[r * K + k] / pv : 0.0;
+    for (int r = k + 1 + tid; r < K; r += NTH) R[r * K + k] = (pv != 0.0) ? R[r * K + k] / pv : 0.0;
     __syncthreads();
     const int m = K - k - 1;
-    for (int e = tid; e < m * m; e += NT) {
+    for (int e = tid; e < m * m; e += NTH) {
       int r = k + 1 + e / m, c = k + 1 + e % m;
       R[r * K + c] -= R[r * K + k] * R[k * K + c];
     }
@@ -213,7 +214,7 @@ k_spikes(const double* __restrict__ band, int64_t N, int K, Dev d, const T* __re
   }
   __syncthreads();
   // ---- GEPP of Rbar (ties to the lowest row) ----
-  rbar_gepp(R, K, pivs, singular, red_v, red_i);
+  rbar_gepp<NT>(R, K, pivs, singular, red_v, red_i);
   // ---- inverse Rinv = U^{-1} L^{-1} P (P R = L U), column by column ----
   double* Xd = reinterpret_cast<double*>(Mx);   // reuse Mx + X as a K x K FP64 workspace
   for (int e = tid; e < KK; e += NT) Xd[e] = 0.0;
@@ -351,46 +352,93 @@ k_rbar_form(const T* __restrict__ V, const T* __restrict__ Wt, int K, double* __
   }
 }
 
-// GEPP of every Rbar_i in its workspace (one CTA per interface).
+// GEPP of every Rbar_i in its workspace (one CTA of 1024 threads per
+// interface: the L2-resident rank-1 updates want many loads in flight).
+constexpr int kGeppThreads = 1024;
 template <typename T>
-__global__ void __launch_bounds__(NT)
+__global__ void __launch_bounds__(kGeppThreads)
 k_rbar_gepp(int K, unsigned char* __restrict__ gws, int* __restrict__ pivout, int* singular) {
   extern __shared__ int pivs_sh[];
-  __shared__ double red_v[NT / 32];
-  __shared__ int red_i[NT / 32];
+  __shared__ double red_v[kGeppThreads / 32];
+  __shared__ int red_i[kGeppThreads / 32];
   const int i = blockIdx.x;
   double* R = reinterpret_cast<double*>(gws + (size_t)i * spike_ws_stride(K, sizeof(T)));
-  rbar_gepp(R, K, pivs_sh, singular, red_v, red_i);
-  for (int k = threadIdx.x; k < K; k += NT) pivout[(int64_t)i * K + k] = pivs_sh[k];
+  rbar_gepp<kGeppThreads>(R, K, pivs_sh, singular, red_v, red_i);
+  for (int k = threadIdx.x; k < K; k += kGeppThreads) pivout[(int64_t)i * K + k] = pivs_sh[k];
 }
 
 // Rbar_i^{-1} = U^{-1} L^{-1} P from the GEPP factors, 32 columns per CTA
-// (one per thread, K x 32 right-hand sides in shared memory); grid
-// (ceil(K / 32), P - 1).
+// (K x 32 right-hand sides in shared memory, lane = column); the four warps
+// split every row's dot product (q = w mod 4, two accumulators each: FP64
+// multiply-add latency is long on GB300) and warp 0 finishes the row.
+// Grid (ceil(K / 32), P - 1).
+constexpr int kInvWarps = 4;
 template <typename T>
-__global__ void __launch_bounds__(32)
+__global__ void __launch_bounds__(32 * kInvWarps)
 k_rbar_inv(int K, const unsigned char* __restrict__ gws, const int* __restrict__ pivin, double* __restrict__ Rinv) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  double* Xs = reinterpret_cast<double*>(smem_raw);      // K x 32
-  int* pv = reinterpret_cast<int*>(Xs + (size_t)K * 32);  // K pivots
+  double* Xs = reinterpret_cast<double*>(smem_raw);                  // K x 32
+  double* part = Xs + (size_t)K * 32;                                 // kInvWarps x 32
+  int* pv = reinterpret_cast<int*>(part + kInvWarps * 32);            // K pivots
   const int i = blockIdx.y;
-  const int lane = threadIdx.x;
+  const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
   const int col = blockIdx.x * 32 + lane;
   const double* R = reinterpret_cast<const double*>(gws + (size_t)i * spike_ws_stride(K, sizeof(T)));
-  for (int k = lane; k < K; k += 32) pv[k] = pivin[(int64_t)i * K + k];
-  for (int e = lane; e < K * 32; e += 32) Xs[e] = 0.0;
-  __syncwarp();
-  if (col < K) {
+  for (int k = threadIdx.x; k < K; k += 32 * kInvWarps) pv[k] = pivin[(int64_t)i * K + k];
+  for (int e = threadIdx.x; e < K * 32; e += 32 * kInvWarps) Xs[e] = 0.0;
+  __syncthreads();
+  if (wq == 0 && col < K) {
     int pos = col;        // P e_col: the recorded swaps applied to e_col
     for (int k = 0; k < K; ++k) {
       if (pv[k] == pos) pos = k;
       else if (k == pos) pos = pv[k];
     }
     Xs[pos * 32 + lane] = 1.0;
-    tri_col(R, K, true, true, false, Xs, lane, 32);
-    tri_col(R, K, false, false, false, Xs, lane, 32);
+  }
+  __syncthreads();
+  // forward: unit lower L (below the diagonal of R)
+  for (int r = 1; r < K; ++r) {
+    const double* row = R + (int64_t)r * K;
+    double a0 = 0.0, a1 = 0.0;
+    int q = wq;
+    for (; q + kInvWarps < r; q += 2 * kInvWarps) {
+      a0 += row[q] * Xs[q * 32 + lane];
+      a1 += row[q + kInvWarps] * Xs[(q + kInvWarps) * 32 + lane];
+    }
+    if (q < r) a0 += row[q] * Xs[q * 32 + lane];
+    part[wq * 32 + lane] = a0 + a1;
+    __syncthreads();
+    if (wq == 0) {
+      double sum = 0.0;
+#pragma unroll
+      for (int w = 0; w < kInvWarps; ++w) sum += part[w * 32 + lane];
+      Xs[r * 32 + lane] -= sum;
+    }
+    __syncthreads();
+  }
+  // backward: U (on and above the diagonal)
+  for (int r = K - 1; r >= 0; --r) {
+    const double* row = R + (int64_t)r * K;
+    double a0 = 0.0, a1 = 0.0;
+    int q = r + 1 + wq;
+    for (; q + kInvWarps < K; q += 2 * kInvWarps) {
+      a0 += row[q] * Xs[q * 32 + lane];
+      a1 += row[q + kInvWarps] * Xs[(q + kInvWarps) * 32 + lane];
+    }
+    if (q < K) a0 += row[q] * Xs[q * 32 + lane];
+    part[wq * 32 + lane] = a0 + a1;
+    __syncthreads();
+    if (wq == 0) {
+      double sum = 0.0;
+#pragma unroll
+      for (int w = 0; w < kInvWarps; ++w) sum += part[w * 32 + lane];
+      Xs[r * 32 + lane] = (Xs[r * 32 + lane] - sum) / row[r];
+    }
+    __syncthreads();
+  }
+  if (col < K) {
     double* out = Rinv + (int64_t)i * K * K;
-    for (int r = 0; r < K; ++r) out[(int64_t)r * K + col] = Xs[r * 32 + lane];
+    for (int r = wq; r < K; r += kInvWarps) out[(int64_t)r * K + col] = Xs[r * 32 + lane];
   }
 }
 
@@ -431,13 +479,13 @@ cudaError_t launch_spikes(const double* band, int64_t N, int K, int P, Dev d, co
   const int tiles = (K + RT - 1) / RT;
   count_launches(3);
   k_rbar_form<T><<<dim3(tiles, tiles, P - 1), 256, 0, s>>>(V, Wt, K, R0, gws);
-  k_rbar_gepp<T><<<P - 1, NT, (size_t)K * sizeof(int), s>>>(K, gws, piv, singular);
-  const size_t ism = (size_t)K * 32 * sizeof(double) + (size_t)K * sizeof(int);
+  k_rbar_gepp<T><<<P - 1, kGeppThreads, (size_t)K * sizeof(int), s>>>(K, gws, piv, singular);
+  const size_t ism = (size_t)(K + kInvWarps) * 32 * sizeof(double) + (size_t)K * sizeof(int);
   if (ism > 48 * 1024) {
     e = cudaFuncSetAttribute(k_rbar_inv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ism);
     if (e != cudaSuccess) return e;
   }
-  k_rbar_inv<T><<<dim3((K + 31) / 32, P - 1), 32, ism, s>>>(K, gws, piv, Rinv);
+  k_rbar_inv<T><<<dim3((K + 31) / 32, P - 1), 32 * kInvWarps, ism, s>>>(K, gws, piv, Rinv);
   return cudaGetLastError();
 }
 

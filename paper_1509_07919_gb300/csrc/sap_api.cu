@@ -1109,6 +1109,9 @@ sap_status_t sap_autotune(const double* band, int64_t N, int32_t K, const sap_op
       int64_t P = std::max<int64_t>(1, std::min<int64_t>(pmax, (N + rows / 2) / rows));
       if (std::find(Ps.begin(), Ps.end(), (int32_t)P) == Ps.end()) Ps.push_back((int32_t)P);
     }
+    // one and two blocks per SM: whole waves of the one-CTA-per-block LU and sweeps
+    for (int64_t P : {(int64_t)kSMs, 2 * (int64_t)kSMs})
+      if (P <= pmax && std::find(Ps.begin(), Ps.end(), (int32_t)P) == Ps.end()) Ps.push_back((int32_t)P);
   }
   if (Ps.empty()) return SAP_ERR_INVALID_ARG;
   std::vector<int32_t> Ss;

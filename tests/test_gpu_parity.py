@@ -351,13 +351,14 @@ def test_convection_diffusion_sapc_parity(sap, nx, ny, P, prec):
 
 def test_autotune_picks_the_fastest_measured_candidate(sap):
     """The measured autotuner times refactor + solve for each (P, segments)
-    candidate and returns the fastest; the default P grid is N / {16000 .. 1000}."""
+    candidate and returns the fastest; the default P grid is N / {16000 .. 1000}
+    and one and two blocks per SM (152, 304) where N / P >= 64."""
     N, K = 60000, 50
     band, xt, b = make(N, K, 1.0, 950)
     bd = dev(band)
     P, S, table = sap.sap_autotune(bd, N, K, precision=sap.SAP_FP32)
     assert sorted(p for p, _ in table) == sorted({max(1, min(N // 64, (N + r // 2) // r))
-                                                  for r in (16000, 8000, 4000, 2000, 1000)})
+                                                  for r in (16000, 8000, 4000, 2000, 1000)} | {152, 304})
     assert all(v > 0 for v in table.values())
     assert table[(P, S)] == min(table.values())
     P2, S2, t2 = sap.sap_autotune(bd, N, K, P_cands=[10, 20], seg_cands=[1, 4], b=dev(b),

@@ -138,6 +138,19 @@ SAP_API sap_status_t sap_refactor(sap_handle_t h, cudaStream_t stream);
 SAP_API sap_status_t sap_solve(sap_handle_t h, const double *b_dev, double *x_dev,
                        sap_info_t *info, cudaStream_t stream);
 
+/* The forward solve A x = b and the adjoint solve A^T lambda = gbar
+ * together (a GB300 addition, for a gbar that does not depend on x, e.g. the
+ * gradient of a linear functional w^T x): the two BiCGStab(2) iterations run
+ * concurrently on two internal streams with separate Krylov workspaces (the
+ * second allocated on the first call) and separate apply scratch, in lockstep
+ * rounds with one host synchronisation per round for both.  Each result is
+ * what sap_solve / sap_solve_adjoint return for it.  No two of b, x, gbar,
+ * lambda may alias (b and gbar may be the same array).  Returns the first
+ * non-OK status (forward first).  Synchronises `stream`. */
+SAP_API sap_status_t sap_solve_pair(sap_handle_t h, const double *b_dev, double *x_dev, const double *gbar_dev,
+                                    double *lambda_dev, sap_info_t *info_x, sap_info_t *info_lambda,
+                                    cudaStream_t stream);
+
 /* Solve A^T lambda = gbar with the same machinery on A^T: SpMV with A^T and
  * SaP on A^T built from the stored factors transposed (A_i^T = U_i^T L_i^T;
  * couplings B'_i = C_{i+1}^T, C'_{i+1} = B_i^T; its own reduced matrices,

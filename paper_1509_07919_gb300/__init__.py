@@ -60,6 +60,7 @@ def _load():
         "sap_refactor": (C.c_int, [vp, vp]),
         "sap_solve": (C.c_int, [vp, vp, vp, P(sap_info_t), vp]),
         "sap_solve_adjoint": (C.c_int, [vp, vp, vp, P(sap_info_t), vp]),
+        "sap_solve_pair": (C.c_int, [vp, vp, vp, vp, vp, P(sap_info_t), P(sap_info_t), vp]),
         "sap_grad_band": (C.c_int, [vp, vp, vp, vp, vp]),
         "sap_apply_preconditioner": (C.c_int, [vp, vp, vp, i32, vp]),
         "sap_spmv": (C.c_int, [vp, i64, i32, vp, vp, i32, vp]),
@@ -173,6 +174,19 @@ def sap_solve_adjoint(h: Handle, gbar: torch.Tensor, lam: torch.Tensor | None = 
     if raise_on_error:
         _check(st, "sap_solve_adjoint")
     return lam, info, st
+
+
+def sap_solve_pair(h: Handle, b: torch.Tensor, gbar: torch.Tensor, x: torch.Tensor | None = None,
+                   lam: torch.Tensor | None = None, stream=None, raise_on_error: bool = True):
+    """x = A^{-1} b and lambda = A^{-T} gbar, solved concurrently (gbar independent of x)."""
+    x = torch.empty_like(b) if x is None else x
+    lam = torch.empty_like(gbar) if lam is None else lam
+    ix, il = sap_info_t(), sap_info_t()
+    st = _lib.sap_solve_pair(h.ptr, _ptr(b), _ptr(x), _ptr(gbar), _ptr(lam), C.byref(ix), C.byref(il),
+                             _stream(stream))
+    if raise_on_error:
+        _check(st, "sap_solve_pair")
+    return x, lam, ix, il, st
 
 
 def sap_solve_host(h: Handle, b_host, x_host, stream=None, raise_on_error: bool = True):

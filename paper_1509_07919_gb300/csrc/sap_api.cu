@@ -89,8 +89,9 @@ struct sap_handle {
   // Krylov workspace
   double* vec = nullptr;      // 11 N doubles: r0 r1 r2 u0 u1 u2 rt tmp t, b and x of the iteration
   // one outer BiCGStab(2) iteration captured as a CUDA graph, per direction
-  // (0 forward, 1 adjoint); captured on first use, replayed per iteration
-  cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+  // (0 forward, 1 adjoint) and Krylov workspace (+2: the second one);
+  // captured on first use, replayed per iteration
+  cudaGraphExec_t gexec[4] = {nullptr, nullptr, nullptr, nullptr};
   cudaStream_t ks = nullptr;          // internal stream of the iteration (capturable)
   // background stream of the transposed sweep matrices (see Solver::factor_post)
   cudaStream_t ts = nullptr;
@@ -101,8 +102,20 @@ struct sap_handle {
   cudaEvent_t evu[2] = {nullptr, nullptr};      // T_UL bracket (on us)
   bool ts_pending = false;
   cudaEvent_t evf = nullptr, evj = nullptr;   // fork from / join to the caller's stream
-  long long glaunches[2] = {0, 0};   // kernels in each graph
-  bool gfailed[2] = {false, false};  // capture unavailable: launch directly
+  long long glaunches[4] = {0, 0, 0, 0};   // kernels in each graph
+  bool gfailed[4] = {false, false, false, false};  // capture unavailable: launch directly
+  // second Krylov workspace (vectors, scalars, flags, readbacks, stream, events)
+  // for an adjoint solve that runs concurrently with the forward one
+  // (sap_solve_pair); allocated on first use
+  struct Ws2 {
+    double* vec = nullptr;
+    KrylovDev kd{};
+    int* flags = nullptr;
+    double* host_s = nullptr;
+    int* host_f = nullptr;
+    cudaStream_t ks = nullptr;
+    cudaEvent_t evf = nullptr, evj = nullptr, ev0 = nullptr, ev1 = nullptr;
+  } w2;
   KrylovDev kd{};
   double* host_s = nullptr;   // pinned scalar readback
   int* flags = nullptr;       // F_COUNT device control flags of the Krylov iteration
@@ -130,6 +143,11 @@ struct sap_handle {
     if (host_f) cudaFreeHost(host_f);
     if (ev0) cudaEventDestroy(ev0);
     if (ev1) cudaEventDestroy(ev1);
+    if (w2.host_s) cudaFreeHost(w2.host_s);
+    if (w2.host_f) cudaFreeHost(w2.host_f);
+    if (w2.ks) cudaStreamDestroy(w2.ks);
+    for (cudaEvent_t e : {w2.evf, w2.evj, w2.ev0, w2.ev1})
+      if (e) cudaEventDestroy(e);
     for (cudaEvent_t e : evp)
       if (e) cudaEventDestroy(e);
   }
@@ -142,6 +160,8 @@ struct Solver : SolverBase {
   sap_handle* h;
   Factors<T> f;
   double* scratch = nullptr;   // apply scratch: g (N), T tmp (N), ctop/cbot
+  double* scratch_t = nullptr; // the same for transposed applies (an adjoint solve may run concurrently)
+  T* tails_t = nullptr;        // segment tails of the transposed sweeps
   float* bandf = nullptr;      // FP32 copy of the band (FP32 factorisation only)
   T* wlu = nullptr;            // factor windows in global memory (bands too wide for shared memory)
   T* wul = nullptr;            // the same for the UL factorisation (it runs concurrently with the LU)
@@ -350,6 +370,9 @@ struct Solver : SolverBase {
     if (!f.Mutf) {
       TRY(h->mem.alloc(&f.Mutf, (size_t)L.c_elems));
       TRY(h->mem.alloc(&f.Mltb, (size_t)L.c_elems));
+      const int nI = L.P > 1 ? L.P - 1 : 1;
+      TRY(h->mem.alloc(&scratch_t, (size_t)(2 * L.N + 5 * nI * L.K + 8)));
+      if (L.S > 1) TRY(h->mem.alloc(&tails_t, (size_t)L.P * L.S * hist_width(L.K)));
       if (L.S > 1) {
         TRY(h->mem.alloc(&f.Tutf, trans_elems()));
         TRY(h->mem.alloc(&f.Tltb, trans_elems()));
@@ -375,9 +398,14 @@ struct Solver : SolverBase {
   }
 
   sap_status_t apply(const double* r, double* z, bool transpose, cudaStream_t s, Gate gt) override {
-    if (transpose) TRY(prepare_transposed(s));
-    CK(launch_apply<T>(h->band, h->L.N, h->L.K, h->L.P, h->d, f, h->opt.variant, transpose, r, z, scratch, s,
-                       gt));
+    if (!transpose) {
+      CK(launch_apply<T>(h->band, h->L.N, h->L.K, h->L.P, h->d, f, h->opt.variant, false, r, z, scratch, s, gt));
+      return SAP_OK;
+    }
+    TRY(prepare_transposed(s));
+    Factors<T> ft = f;              // transposed applies own their scratch and segment tails
+    ft.tails = tails_t;
+    CK(launch_apply<T>(h->band, h->L.N, h->L.K, h->L.P, h->d, ft, h->opt.variant, true, r, z, scratch_t, s, gt));
     return SAP_OK;
   }
 
@@ -475,6 +503,28 @@ sap_status_t ensure_stream(sap_handle* h) {
   return SAP_OK;
 }
 
+// The second Krylov workspace, created on first use.
+sap_status_t ensure_ws2(sap_handle* h) {
+  auto& w = h->w2;
+  if (w.ks) return SAP_OK;
+  const int64_t N = h->L.N;
+  TRY(h->mem.alloc(&w.vec, (size_t)(11 * N)));
+  TRY(h->mem.alloc(&w.kd.S, S_COUNT));
+  TRY(h->mem.alloc(&w.kd.part, kKrylovBlocks * 4));
+  TRY(h->mem.alloc(&w.kd.ticket, 1));
+  TRY(h->mem.alloc(&w.flags, F_COUNT));
+  CK(cudaMemset(w.kd.ticket, 0, sizeof(unsigned)));
+  CK(cudaMemset(w.vec, 0, 11 * N * sizeof(double)));
+  if (cudaMallocHost(&w.host_s, S_COUNT * sizeof(double)) != cudaSuccess) return SAP_ERR_OOM;
+  if (cudaMallocHost(&w.host_f, F_COUNT * sizeof(int)) != cudaSuccess) return SAP_ERR_OOM;
+  CK(cudaEventCreateWithFlags(&w.evf, cudaEventDisableTiming));
+  CK(cudaEventCreateWithFlags(&w.evj, cudaEventDisableTiming));
+  CK(cudaEventCreate(&w.ev0));
+  CK(cudaEventCreate(&w.ev1));
+  CK(cudaStreamCreateWithFlags(&w.ks, cudaStreamNonBlocking));
+  return SAP_OK;
+}
+
 // One BiCGStab(2) solve, split at its host synchronisation points so that a
 // batch of solves can share them: begin() (setup, scalar readback), then
 // rounds (one outer iteration each, flag readback), then finish().  Between
@@ -491,6 +541,12 @@ struct KrylovRun {
   int64_t N = 0;
   double *r[3], *u[3], *rt, *tmp, *t, *b, *x;
   KrylovDev kd, ka, kc;
+  // the workspace of this run: the handle's own (ws 0) or its second one (ws 1)
+  double* vec = nullptr;
+  int* flags = nullptr;
+  double* hs = nullptr;
+  int* hf = nullptr;
+  cudaEvent_t evf = nullptr, evj = nullptr, ev0 = nullptr, ev1 = nullptr;
   Gate gA, gC, gR;
   double tol = 0.0, bn = 0.0;
   sap_info_t inf{};
@@ -499,60 +555,66 @@ struct KrylovRun {
   int it = 0;            // outer iterations launched
   int gi = 0;
 
-  sap_status_t init(sap_handle* hh, const double* bu, double* xu, bool transposed, cudaStream_t us) {
+  sap_status_t init(sap_handle* hh, const double* bu, double* xu, bool transposed, cudaStream_t us, int ws = 0) {
     h = hh; tr = transposed; user = us; b_user = bu; x_user = xu;
     TRY(ensure_stream(h));
-    s = h->ks;
     N = h->L.N;
-    for (int k = 0; k < 3; ++k) {
-      r[k] = h->vec + k * N;
-      u[k] = h->vec + (3 + k) * N;
+    if (ws == 0) {
+      s = h->ks; vec = h->vec; kd = h->kd; flags = h->flags; hs = h->host_s; hf = h->host_f;
+      evf = h->evf; evj = h->evj; ev0 = h->ev0; ev1 = h->ev1;
+    } else {
+      TRY(ensure_ws2(h));
+      s = h->w2.ks; vec = h->w2.vec; kd = h->w2.kd; flags = h->w2.flags; hs = h->w2.host_s; hf = h->w2.host_f;
+      evf = h->w2.evf; evj = h->w2.evj; ev0 = h->w2.ev0; ev1 = h->w2.ev1;
     }
-    rt = h->vec + 6 * N;
-    tmp = h->vec + 7 * N;
-    t = h->vec + 8 * N;
+    for (int k = 0; k < 3; ++k) {
+      r[k] = vec + k * N;
+      u[k] = vec + (3 + k) * N;
+    }
+    rt = vec + 6 * N;
+    tmp = vec + 7 * N;
+    t = vec + 8 * N;
     // the iteration works on handle-owned copies of b and x, so that its
     // captured graph does not depend on the caller's pointers
-    b = h->vec + 9 * N;
-    x = h->vec + 10 * N;
-    kd = h->kd;
-    kd.flags = h->flags;
+    b = vec + 9 * N;
+    x = vec + 10 * N;
+    kd.flags = flags;
     ka = kd;
     ka.gmode = G_ACTIVE;
     kc = kd;
     kc.gmode = G_CHECK;
-    gA.flags = gC.flags = gR.flags = h->flags;
+    gA.flags = gC.flags = gR.flags = flags;
     gA.mode = G_ACTIVE;
     gC.mode = G_CHECK;
     gR.mode = G_REPLACE;
     tol = h->opt.tol;
     inf.iters = 0;
     inf.relres = 1.0;
-    gi = tr ? 1 : 0;
+    gi = (tr ? 1 : 0) + 2 * ws;
     return SAP_OK;
   }
 
   // setup launches and the readback of ||b||^2, ||M^{-1} b||^2
   sap_status_t begin() {
     if (tr) TRY(h->impl->prepare_transposed(user));
-    CK(cudaEventRecord(h->evf, user));
-    CK(cudaStreamWaitEvent(s, h->evf, 0));
-    CK(cudaEventRecord(h->ev0, s));
+    CK(cudaEventRecord(evf, user));
+    CK(cudaStreamWaitEvent(s, evf, 0));
+    CK(cudaEventRecord(ev0, s));
     CK(cudaMemcpyAsync(b, b_user, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
     CK(cudaMemsetAsync(x, 0, N * sizeof(double), s));
-    CK(cudaMemsetAsync(h->flags, 0, F_COUNT * sizeof(int), s));
+    CK(cudaMemsetAsync(flags, 0, F_COUNT * sizeof(int), s));
     CK(kr_init(kd, s));
     CK(kr_norm2(b, N, kd, S_BN2, s));
     TRY(h->impl->apply(b, r[0], tr, s));
     CK(kr_norm2(r[0], N, kd, S_BTN2, s));
     CK(cudaMemcpyAsync(rt, r[0], N * sizeof(double), cudaMemcpyDeviceToDevice, s));
     CK(cudaMemsetAsync(u[0], 0, N * sizeof(double), s));
-    CK(cudaMemcpyAsync(h->host_s, kd.S + S_RN2, 5 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(hs, kd.S + S_RN2, 5 * sizeof(double), cudaMemcpyDeviceToHost, s));
     return SAP_OK;
   }
   // after the stream synchronised: b = 0 finishes at once
   void after_begin() {
-    bn = std::sqrt(h->host_s[S_BN2 - S_RN2]);
+    bn = std::sqrt(hs[S_BN2 - S_RN2]);
     if (bn == 0.0) {
       inf.relres = 0.0;
       status = SAP_OK;
@@ -613,22 +675,22 @@ struct KrylovRun {
       TRY(iteration());
     }
     ++it;
-    CK(cudaMemcpyAsync(h->host_f, h->flags, F_COUNT * sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(hf, flags, F_COUNT * sizeof(int), cudaMemcpyDeviceToHost, s));
     return SAP_OK;
   }
-  void after_round() { done = h->host_f[F_DONE] != 0; }
+  void after_round() { done = hf[F_DONE] != 0; }
 
   // results; synchronises the handle's stream and joins the caller's
   sap_status_t finish(sap_info_t* info) {
     if (bn != 0.0) {
-      CK(cudaMemcpyAsync(h->host_s, kd.S, S_COUNT * sizeof(double), cudaMemcpyDeviceToHost, s));
-      CK(cudaMemcpyAsync(h->host_f, h->flags, F_COUNT * sizeof(int), cudaMemcpyDeviceToHost, s));
+      CK(cudaMemcpyAsync(hs, kd.S, S_COUNT * sizeof(double), cudaMemcpyDeviceToHost, s));
+      CK(cudaMemcpyAsync(hf, flags, F_COUNT * sizeof(int), cudaMemcpyDeviceToHost, s));
       CK(cudaStreamSynchronize(s));
-      inf.n_restarts = h->host_f[F_RESTARTS];
-      if (h->host_f[F_DONE]) {
-        status = (sap_status_t)h->host_f[F_STATUS];
-        inf.iters = h->host_s[S_QUART];
-        inf.relres = h->host_s[S_RELRES];
+      inf.n_restarts = hf[F_RESTARTS];
+      if (hf[F_DONE]) {
+        status = (sap_status_t)hf[F_STATUS];
+        inf.iters = hs[S_QUART];
+        inf.relres = hs[S_RELRES];
       } else {
         status = SAP_ERR_NOT_CONVERGED;
         inf.iters = h->opt.max_iters;
@@ -636,17 +698,17 @@ struct KrylovRun {
       if (status != SAP_OK) {
         CK(launch_spmv(h->band, N, h->L.K, x, tmp, tr, s));
         CK(kr_residual(b, tmp, t, N, kd, S_TN2, s));
-        CK(cudaMemcpyAsync(h->host_s, kd.S + S_RN2, 5 * sizeof(double), cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(hs, kd.S + S_RN2, 5 * sizeof(double), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
-        inf.relres = std::sqrt(h->host_s[S_TN2 - S_RN2]) / bn;
+        inf.relres = std::sqrt(hs[S_TN2 - S_RN2]) / bn;
       }
     }
     CK(cudaMemcpyAsync(x_user, x, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    CK(cudaEventRecord(h->ev1, s));
-    CK(cudaEventSynchronize(h->ev1));
+    CK(cudaEventRecord(ev1, s));
+    CK(cudaEventSynchronize(ev1));
     if (h->impl->take_device_error(s) != SAP_OK) status = SAP_ERR_TIMEOUT;
     float ms = 0.f;
-    cudaEventElapsedTime(&ms, h->ev0, h->ev1);
+    cudaEventElapsedTime(&ms, ev0, ev1);
     inf.n_matvec = (int64_t)std::llround(4.0 * inf.iters);
     inf.t_solve_ms = ms;
     inf.t_factor_ms = h->t_factor_ms;
@@ -659,8 +721,8 @@ struct KrylovRun {
     unsigned long long nb = 0;
     CK(cudaMemcpy(&nb, h->n_boosted, sizeof(nb), cudaMemcpyDeviceToHost));
     inf.n_boosted = (int64_t)nb;
-    CK(cudaEventRecord(h->evj, s));
-    CK(cudaStreamWaitEvent(user, h->evj, 0));
+    CK(cudaEventRecord(evj, s));
+    CK(cudaStreamWaitEvent(user, evj, 0));
     if (info) *info = inf;
     return status;
   }
@@ -1012,6 +1074,37 @@ sap_status_t sap_solve_adjoint(sap_handle_t h, const double* g, double* lam, sap
   if (!h || !g || !lam || g == lam) return SAP_ERR_INVALID_ARG;
   TRY(h->impl->build_adjoint(s));
   return krylov(h, g, lam, true, info, s);
+}
+
+sap_status_t sap_solve_pair(sap_handle_t h, const double* b, double* x, const double* g, double* lam,
+                            sap_info_t* info_x, sap_info_t* info_lam, cudaStream_t s) {
+  if (!h || !b || !x || !g || !lam || b == x || g == lam || x == lam) return SAP_ERR_INVALID_ARG;
+  TRY(h->impl->build_adjoint(s));
+  // forward on the handle's workspace, adjoint on the second one: two streams,
+  // lockstep rounds, one host synchronisation per round for both
+  KrylovRun k[2];
+  TRY(k[0].init(h, b, x, false, s, 0));
+  TRY(k[1].init(h, g, lam, true, s, 1));
+  TRY(k[0].begin());
+  TRY(k[1].begin());
+  for (auto& r : k) {
+    CK(cudaStreamSynchronize(r.s));
+    r.after_begin();
+  }
+  for (;;) {
+    bool ran[2] = {k[0].active(), k[1].active()};
+    if (!ran[0] && !ran[1]) break;
+    for (int i = 0; i < 2; ++i)
+      if (ran[i]) TRY(k[i].round());
+    for (int i = 0; i < 2; ++i)
+      if (ran[i]) {
+        CK(cudaStreamSynchronize(k[i].s));
+        k[i].after_round();
+      }
+  }
+  const sap_status_t sx = k[0].finish(info_x);
+  const sap_status_t sl = k[1].finish(info_lam);
+  return sx != SAP_OK ? sx : sl;
 }
 
 sap_status_t sap_solve_host(sap_handle_t h, const double* b_host, double* x_host, sap_info_t* info,

@@ -401,3 +401,55 @@ def test_full_size_convection_diffusion_400x250_sapc_p32(sap):
     assert np.linalg.norm(b - O.spmv(band, N, K, xh)) / np.linalg.norm(b) <= 1e-10
     xo, io, _ = O.solve(band, N, K, b, 32, O.SAP_C)
     assert io.status == O.OK and relerr(xh, xo) <= 1e-8
+
+
+# ---------------------------------------------- concurrent fwd + adjoint --
+
+@pytest.mark.parametrize("variant,prec,S", [(0, 1, 0), (0, 1, 1), (1, 1, 0), (0, 0, 0), (1, 0, 0)])
+def test_solve_pair_equals_sequential_solves(sap, variant, prec, S):
+    """sap_solve_pair runs the forward and adjoint iterations concurrently on
+    separate workspaces: the same kernels in the same order per direction, so
+    x and lambda equal the sequential sap_solve / sap_solve_adjoint results bit
+    for bit, and the oracle's within the solve tolerances; twice in a row."""
+    N, K, P = 6007, 50, 6
+    band, xt, b = make(N, K, 1.0, 2100 + 10 * variant + prec)
+    g = G.adjoint_seed(N, 2100)
+    h = sap.sap_factor(dev(band), N, K, P=P, variant=variant, precision=prec, segments=S)
+    xs, _, _ = sap.sap_solve(h, dev(b))
+    ls, _, _ = sap.sap_solve_adjoint(h, dev(g))
+    xo, _, _ = O.solve(band, N, K, b, P, variant)
+    lo, _, _ = O.solve_adjoint(band, N, K, g, P, variant)
+    for _ in range(2):
+        x, lam, ix, il, st = sap.sap_solve_pair(h, dev(b), dev(g))
+        assert st == sap.SAP_OK and ix.relres <= 1e-10 and il.relres <= 1e-10
+        assert ix.graphed == 1 and il.graphed == 1
+        assert torch.equal(x, xs) and torch.equal(lam, ls)
+        assert relerr(host(x), xo) <= 1e-8 and relerr(host(lam), lo) <= 1e-8
+    sap.sap_refactor(h)
+    x, lam, ix, il, st = sap.sap_solve_pair(h, dev(b), dev(g))
+    assert st == sap.SAP_OK and torch.equal(x, xs) and torch.equal(lam, ls)
+
+
+def test_solve_pair_invalid_arguments(sap):
+    N, K = 500, 5
+    band, xt, b = make(N, K, 1.0, 2200)
+    h = sap.sap_factor(dev(band), N, K, P=2)
+    bd = dev(b)
+    x = torch.empty_like(bd)
+    assert sap.sap_solve_pair(h, bd, bd, x, x, raise_on_error=False)[4] == sap.SAP_ERR_INVALID_ARG
+    assert sap.sap_solve_pair(h, bd, bd, bd, x, raise_on_error=False)[4] == sap.SAP_ERR_INVALID_ARG
+
+
+def test_full_size_solve_pair_n200k_k50_p50(sap):
+    """The N=200000, K=50, P=50 workload through the concurrent pair, FP32
+    preconditioner: both results against the oracle."""
+    N, K, P = 200000, 50, 50
+    seed = G.config_seed(2)
+    band, xt, b = make(N, K, 1.0, seed)
+    g = G.adjoint_seed(N, seed)
+    h = sap.sap_factor(dev(band), N, K, P=P, precision=sap.SAP_FP32)
+    x, lam, ix, il, st = sap.sap_solve_pair(h, dev(b), dev(g))
+    assert st == sap.SAP_OK and ix.relres <= 1e-10 and il.relres <= 1e-10
+    xo, _, _ = O.solve(band, N, K, b, P, O.SAP_D)
+    lo, _, _ = O.solve_adjoint(band, N, K, g, P, O.SAP_D)
+    assert relerr(host(x), xo) <= 1e-8 and relerr(host(lam), lo) <= 1e-8

@@ -344,7 +344,7 @@ def run_gpu(args):
         ms = float(t.item())
     i1, i2 = infos[-1]
     # the same step with the two solves one after the other (sap_solve, then sap_solve_adjoint)
-    seq_times, _, _, _, _, _ = timed(h, max(3, args.steps // 2), 2, sequential=True)
+    seq_times, _, _, _, _, _ = timed(h, args.steps, args.warmup, sequential=True)
     seq_ms = statistics.mean(seq_times)
     # accuracy against the generating solution
     err_x = float(torch.linalg.norm(x - xt) / torch.linalg.norm(xt))

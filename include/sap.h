@@ -282,6 +282,13 @@ SAP_API sap_status_t sap_solve_batched(sap_batch_t b, const double *const *b_dev
 SAP_API sap_status_t sap_solve_adjoint_batched(sap_batch_t b, const double *const *g_dev,
                                                double *const *lambda_dev, sap_info_t *infos,
                                                int32_t *statuses, cudaStream_t stream);
+/* Every system's forward and adjoint solve together (as sap_solve_pair, all
+ * 2n iterations in the same lockstep rounds).  statuses (optional) has 2n
+ * entries: the forward solves, then the adjoint ones.  Synchronises. */
+SAP_API sap_status_t sap_solve_pair_batched(sap_batch_t b, const double *const *b_dev, double *const *x_dev,
+                                            const double *const *g_dev, double *const *lambda_dev,
+                                            sap_info_t *infos_x, sap_info_t *infos_lambda, int32_t *statuses,
+                                            cudaStream_t stream);
 /* grad_band_i = -lambda_i x_i^T restricted to the band of system i. */
 SAP_API sap_status_t sap_grad_band_batched(sap_batch_t b, const double *const *lambda_dev,
                                            const double *const *x_dev, double *const *grad_band_dev,

@@ -80,6 +80,7 @@ def _load():
         "sap_refactor_batched": (C.c_int, [vp, vp]),
         "sap_solve_batched": (C.c_int, [vp, vp, vp, vp, vp, vp]),
         "sap_solve_adjoint_batched": (C.c_int, [vp, vp, vp, vp, vp, vp]),
+        "sap_solve_pair_batched": (C.c_int, [vp, vp, vp, vp, vp, vp, vp, vp, vp]),
         "sap_grad_band_batched": (C.c_int, [vp, vp, vp, vp, vp]),
         "sap_batch_size": (i32, [vp]),
         "sap_batch_partitions": (i32, [vp, i32]),
@@ -346,6 +347,20 @@ def sap_solve_batched(bh: BatchHandle, bs, xs=None, stream=None, raise_on_error:
 def sap_solve_adjoint_batched(bh: BatchHandle, gs, lams=None, stream=None, raise_on_error: bool = True):
     return _solve_batched(_lib.sap_solve_adjoint_batched, "sap_solve_adjoint_batched", bh, gs, lams, stream,
                           raise_on_error)
+
+
+def sap_solve_pair_batched(bh: BatchHandle, bs, gs, xs=None, lams=None, stream=None, raise_on_error: bool = True):
+    """Every system's x_i = A_i^{-1} b_i and lambda_i = A_i^{-T} g_i, solved concurrently."""
+    n = len(bh)
+    xs = [torch.empty_like(t) for t in bs] if xs is None else list(xs)
+    lams = [torch.empty_like(t) for t in gs] if lams is None else list(lams)
+    ix, il = (sap_info_t * n)(), (sap_info_t * n)()
+    stats = (C.c_int32 * (2 * n))()
+    st = _lib.sap_solve_pair_batched(bh.ptr, _ptr_array(bs), _ptr_array(xs), _ptr_array(gs), _ptr_array(lams),
+                                     ix, il, stats, _stream(stream))
+    if raise_on_error:
+        _check(st, "sap_solve_pair_batched")
+    return xs, lams, list(ix), list(il), list(stats), st
 
 
 def sap_grad_band_batched(bh: BatchHandle, lams, xs, outs=None, stream=None):

@@ -980,15 +980,10 @@ sap_status_t factor_batch(sap_batch* B, cudaStream_t s) {
   return st;
 }
 
-// All systems' solves in lockstep rounds of one outer iteration each.
-sap_status_t solve_batch(sap_batch* B, const double* const* b, double* const* x, bool tr, sap_info_t* infos,
-                         int32_t* statuses, cudaStream_t s) {
-  const size_t n = B->hs.size();
-  std::vector<KrylovRun> k(n);
-  for (size_t i = 0; i < n; ++i) {
-    if (!b[i] || !x[i] || b[i] == x[i]) return SAP_ERR_INVALID_ARG;
-    TRY(k[i].init(B->hs[i], b[i], x[i], tr, s));
-  }
+// Solves in lockstep rounds of one outer iteration each: every unfinished
+// run replays its iteration on its own stream, then the host waits for all.
+sap_status_t run_lockstep(std::vector<KrylovRun>& k) {
+  const size_t n = k.size();
   for (size_t i = 0; i < n; ++i) TRY(k[i].begin());
   for (size_t i = 0; i < n; ++i) {
     CK(cudaStreamSynchronize(k[i].s));
@@ -1011,9 +1006,47 @@ sap_status_t solve_batch(sap_batch* B, const double* const* b, double* const* x,
         k[i].after_round();
       }
   }
+  return SAP_OK;
+}
+
+// All systems' solves (forward or adjoint) in lockstep rounds.
+sap_status_t solve_batch(sap_batch* B, const double* const* b, double* const* x, bool tr, sap_info_t* infos,
+                         int32_t* statuses, cudaStream_t s) {
+  const size_t n = B->hs.size();
+  std::vector<KrylovRun> k(n);
+  for (size_t i = 0; i < n; ++i) {
+    if (!b[i] || !x[i] || b[i] == x[i]) return SAP_ERR_INVALID_ARG;
+    TRY(k[i].init(B->hs[i], b[i], x[i], tr, s));
+  }
+  TRY(run_lockstep(k));
   sap_status_t st = SAP_OK;
   for (size_t i = 0; i < n; ++i) {
     const sap_status_t e = k[i].finish(infos ? &infos[i] : nullptr);
+    if (statuses) statuses[i] = e;
+    if (st == SAP_OK) st = e;
+  }
+  return st;
+}
+
+// Every system's forward and adjoint solve together: 2n runs in lockstep,
+// the adjoint ones on each handle's second workspace.
+sap_status_t solve_pair_batch(sap_batch* B, const double* const* b, double* const* x, const double* const* g,
+                              double* const* lam, sap_info_t* ix, sap_info_t* il, int32_t* statuses,
+                              cudaStream_t s) {
+  const size_t n = B->hs.size();
+  std::vector<KrylovRun> k(2 * n);
+  for (size_t i = 0; i < n; ++i) {
+    if (!b[i] || !x[i] || !g[i] || !lam[i] || b[i] == x[i] || g[i] == lam[i] || x[i] == lam[i])
+      return SAP_ERR_INVALID_ARG;
+    TRY(B->hs[i]->impl->build_adjoint(s));
+    TRY(k[i].init(B->hs[i], b[i], x[i], false, s, 0));
+    TRY(k[n + i].init(B->hs[i], g[i], lam[i], true, s, 1));
+  }
+  TRY(run_lockstep(k));
+  sap_status_t st = SAP_OK;
+  for (size_t i = 0; i < 2 * n; ++i) {
+    sap_info_t* inf = i < n ? (ix ? &ix[i] : nullptr) : (il ? &il[i - n] : nullptr);
+    const sap_status_t e = k[i].finish(inf);
     if (statuses) statuses[i] = e;
     if (st == SAP_OK) st = e;
   }
@@ -1311,6 +1344,13 @@ sap_status_t sap_solve_adjoint_batched(sap_batch_t b, const double* const* gv, d
                                        sap_info_t* infos, int32_t* statuses, cudaStream_t s) {
   if (!b || !gv || !lv) return SAP_ERR_INVALID_ARG;
   return solve_batch(b, gv, lv, true, infos, statuses, s);
+}
+
+sap_status_t sap_solve_pair_batched(sap_batch_t b, const double* const* bv, double* const* xv,
+                                    const double* const* gv, double* const* lv, sap_info_t* infos_x,
+                                    sap_info_t* infos_lambda, int32_t* statuses, cudaStream_t s) {
+  if (!b || !bv || !xv || !gv || !lv) return SAP_ERR_INVALID_ARG;
+  return solve_pair_batch(b, bv, xv, gv, lv, infos_x, infos_lambda, statuses, s);
 }
 
 sap_status_t sap_grad_band_batched(sap_batch_t b, const double* const* lam, const double* const* x,

@@ -437,8 +437,11 @@ void orc_apply(const orc_sap *h, const double *r, double *z)
  * and 3 of the iteration) and after the minimal-residual update (matvec 4);
  * the iteration count is matvecs / 4, i.e. quarters (Section 4.1.1).
  * Convergence: ||r^0||_2 <= tol ||b~||_2, confirmed by the true residual
- * ||b - A x||_2 <= tol ||b||_2 in FP64; if the confirmation fails r^0 is
- * replaced by M^{-1}(b - A x) and the iteration continues. */
+ * ||b - A x||_2 <= tol ||b||_2 in FP64.  A failed confirmation after matvec 1
+ * or 3 lets the iteration go on unchanged; one after the minimal-residual
+ * update restarts the method from the current x: r^0 = M^{-1}(b - A x),
+ * r~0 = r^0, u^0 = 0, rho0 = alpha = omega as at the start (the recurrences
+ * of the old cycle no longer describe the replaced residual). */
 
 typedef struct {
     double iters;      /* in quarters */
@@ -515,13 +518,9 @@ int orc_bicgstab2(const orc_sap *h, const double *band, const double *b, double 
                     double *t = trace + 4 * ntrace++;
                     t[0] = (double)(4 * it + (j == 0 ? 1 : 3)); t[1] = rn; t[2] = pn; t[3] = rel;
                 }
-                if (pass) {
-                    if (rel <= tol) {
-                        info->iters = it + (j == 0 ? 0.25 : 0.75); info->relres = rel;
-                        status = ORC_OK; goto done;
-                    }
-                    orc_apply(h, tmp, r[0]);           /* reliable update of r^0 */
-                    ++info->n_restarts;
+                if (pass && rel <= tol) {
+                    info->iters = it + (j == 0 ? 0.25 : 0.75); info->relres = rel;
+                    status = ORC_OK; goto done;
                 }
             }
             op(h, band, r[j], r[j + 1], tmp); ++nmv;
@@ -563,7 +562,11 @@ int orc_bicgstab2(const orc_sap *h, const double *band, const double *b, double 
                     info->iters = it + 1.0; info->relres = rel;
                     status = ORC_OK; goto done;
                 }
+                /* restart from the current x */
                 orc_apply(h, tmp, r[0]);
+                memcpy(rt, r[0], (size_t)N * sizeof(double));
+                memset(u[0], 0, (size_t)N * sizeof(double));
+                rho0 = 1.0; alpha = 0.0; omega = 1.0;
                 ++info->n_restarts;
             }
         }

@@ -518,50 +518,60 @@ size_t lu_smem_bytes(int K, bool fp64, bool tc) { return lu_smem_used(K, fp64, l
 namespace {
 
 // ---- max |a_ij| over the in-band entries (boost threshold scale) ----
-__global__ void k_absmax(const double* __restrict__ band, int64_t N, int K, double* out) {
-  const int64_t total = (int64_t)(2 * K + 1) * N;
-  double m = 0.0;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    int64_t c = e / N, j = e - c * N;
-    int64_t i = j + c - K;
-    if (i >= 0 && i < N) m = fmax(m, fabs(band[e]));
-  }
+// Grid (gx, 2K+1): blockIdx.y is the band row c (entries a(j + c - K, j)),
+// whose valid columns are j in [max(0, K - c), min(N, N + K - c)).
+__device__ __forceinline__ void absmax_commit(double m, double* out) {
   for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
   if ((threadIdx.x & 31) == 0)
     atomicMax(reinterpret_cast<unsigned long long*>(out), (unsigned long long)__double_as_longlong(m));
+}
+
+__global__ void k_absmax(const double* __restrict__ band, int64_t N, int K, double* out) {
+  const int c = blockIdx.y;
+  const int64_t lo = K - c > 0 ? K - c : 0;
+  const int64_t hi = N + K - c < N ? N + K - c : N;
+  const double* row = band + (int64_t)c * N;
+  double m = 0.0;
+  for (int64_t j = lo + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < hi; j += (int64_t)gridDim.x * blockDim.x)
+    m = fmax(m, fabs(row[j]));
+  absmax_commit(m, out);
 }
 
 // max |a_ij| over the in-band entries and an FP32 copy of the band (RN),
 // padding slots written as 0: the FP32 factorisation then loads FP32.
 __global__ void k_absmax_cast(const double* __restrict__ band, int64_t N, int K, double* out,
                               float* __restrict__ bandf) {
-  const int64_t total = (int64_t)(2 * K + 1) * N;
+  const int c = blockIdx.y;
+  const int64_t lo = K - c > 0 ? K - c : 0;
+  const int64_t hi = N + K - c < N ? N + K - c : N;
+  const double* row = band + (int64_t)c * N;
+  float* rowf = bandf + (int64_t)c * N;
   double m = 0.0;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    int64_t c = e / N, j = e - c * N;
-    int64_t i = j + c - K;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < N; j += (int64_t)gridDim.x * blockDim.x) {
     float v = 0.f;
-    if (i >= 0 && i < N) {
-      const double a = band[e];
+    if (j >= lo && j < hi) {
+      const double a = row[j];
       m = fmax(m, fabs(a));
       v = (float)a;
     }
-    bandf[e] = v;
+    rowf[j] = v;
   }
-  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-  if ((threadIdx.x & 31) == 0)
-    atomicMax(reinterpret_cast<unsigned long long*>(out), (unsigned long long)__double_as_longlong(m));
+  absmax_commit(m, out);
 }
 
 }  // namespace
+
+static dim3 absmax_grid(int K) {
+  const int rows = 2 * K + 1;
+  const int gx = std::max(1, 152 * 8 / rows);
+  return dim3(gx, rows);
+}
 
 cudaError_t launch_absmax_cast(const double* band, int64_t N, int K, double* out, float* bandf, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(out, 0, sizeof(double), s);
   if (e != cudaSuccess) return e;
   count_launches(1);
-  k_absmax_cast<<<152 * 8, 256, 0, s>>>(band, N, K, out, bandf);
+  k_absmax_cast<<<absmax_grid(K), 256, 0, s>>>(band, N, K, out, bandf);
   return cudaGetLastError();
 }
 
@@ -569,7 +579,7 @@ cudaError_t launch_absmax(const double* band, int64_t N, int K, double* out, cud
   cudaError_t e = cudaMemsetAsync(out, 0, sizeof(double), s);
   if (e != cudaSuccess) return e;
   count_launches(1);
-  k_absmax<<<152 * 4, 256, 0, s>>>(band, N, K, out);
+  k_absmax<<<absmax_grid(K), 256, 0, s>>>(band, N, K, out);
   return cudaGetLastError();
 }
 

@@ -388,10 +388,31 @@ __global__ void k_exit_decide(KrylovDev kd, double tol, double qoff) {
       S[S_QUART] = S[S_IT] + qoff;
       return;
     }
-    f[F_REPLACE] = 1;       // reliable update r^0 = M^{-1} (b - A x) follows
-    f[F_RESTARTS] += 1;
+    // a failed confirmation after the MR update restarts the method from x
+    // (r^0 = M^{-1}(b - A x), then k_restart); after matvec 1 or 3 the
+    // iteration goes on unchanged
+    if (qoff == 1.0) {
+      f[F_REPLACE] = 1;
+      f[F_RESTARTS] += 1;
+    }
   }
   if (qoff == 1.0) S[S_IT] += 1.0;
+}
+
+// Restart after a residual replacement: shadow residual r~0 = r^0, u^0 = 0,
+// rho0 = 1, alpha = 0, omega = 1 (the state of a fresh start); gated on F_REPLACE.
+__global__ void k_restart(const double* __restrict__ r0, double* __restrict__ rt, double* __restrict__ u0,
+                          int64_t n, KrylovDev kd) {
+  if (kr_skip(kd)) return;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    rt[i] = r0[i];
+    u0[i] = 0.0;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    kd.S[S_RHO0] = 1.0;
+    kd.S[S_ALPHA] = 0.0;
+    kd.S[S_OMEGA] = 1.0;
+  }
 }
 
 __global__ void k_init_scalars(double* S) {
@@ -419,6 +440,11 @@ cudaError_t kr_init(KrylovDev kd, cudaStream_t s) {
 cudaError_t kr_exit_check(KrylovDev kd, double tol, double qoff, cudaStream_t s) {
   count_launches(1);
   k_exit_check<<<1, 32, 0, s>>>(kd, tol, qoff);
+  return cudaGetLastError();
+}
+cudaError_t kr_restart(const double* r0, double* rt, double* u0, int64_t n, KrylovDev kd, cudaStream_t s) {
+  count_launches(1);
+  k_restart<<<krylov_grid(n), RT, 0, s>>>(r0, rt, u0, n, kd);
   return cudaGetLastError();
 }
 cudaError_t kr_exit_decide(KrylovDev kd, double tol, double qoff, cudaStream_t s) {

@@ -49,5 +49,7 @@ cudaError_t kr_exit_check(KrylovDev kd, double tol, double qoff, cudaStream_t s)
 // Second half, after the gated true residual: accept (finish) or flag the
 // residual replacement; qoff == 1 also completes the outer iteration.
 cudaError_t kr_exit_decide(KrylovDev kd, double tol, double qoff, cudaStream_t s);
+// restart after a residual replacement (gated on the replacement flag)
+cudaError_t kr_restart(const double* r0, double* rt, double* u0, int64_t n, KrylovDev kd, cudaStream_t s);
 
 }  // namespace sap

@@ -622,12 +622,19 @@ struct KrylovRun {
     }
   }
 
+  // exit test; after the MR update (qoff = 1) a failed confirmation restarts
+  // the method from x: r^0 = M^{-1}(b - A x), r~0 = r^0, u^0 = 0, scalars reset
   sap_status_t exit_test(double qoff) {
     CK(kr_exit_check(kd, tol, qoff, s));
     CK(launch_spmv(h->band, N, h->L.K, x, tmp, tr, s, gC));
     CK(kr_residual(b, tmp, t, N, kc, S_TN2, s));
     CK(kr_exit_decide(kd, tol, qoff, s));
-    return h->impl->apply(t, r[0], tr, s, gR);    // residual replacement, when flagged
+    if (qoff != 1.0) return SAP_OK;
+    TRY(h->impl->apply(t, r[0], tr, s, gR));
+    KrylovDev kr = kd;
+    kr.gmode = G_REPLACE;
+    CK(kr_restart(r[0], rt, u[0], N, kr, s));
+    return SAP_OK;
   }
   sap_status_t iteration() {
     for (int j = 0; j < 2; ++j) {

@@ -300,11 +300,13 @@ def test_not_converged_status(sap):
 
 
 @pytest.mark.parametrize("N,K,P,prec", [(20000, 200, 10, 1), (12000, 128, 6, 0), (9000, 170, 5, 1),
-                                        (12000, 400, 6, 1), (8000, 250, 4, 0), (9000, 300, 3, 1)])
+                                        (12000, 400, 6, 1), (8000, 250, 4, 0), (9000, 300, 3, 1),
+                                        (6000, 512, 3, 1), (5000, 256, 2, 0)])
 def test_wide_band_solve_parity(sap, N, K, P, prec):
-    """Wide bands (K > 127, SaP-D; K = 200 and 400 of the K sweep): 4 + couplings
-    per chunk, unsegmented sweeps; above K = 208 (FP32) / 128 (FP64) the factor
-    window lives in global memory, above K = 288 (FP32) / 128 (FP64) the sweep
+    """Wide bands (K > 127, SaP-D; K = 200 and 400 of the K sweep, and the
+    largest K of each precision, 512 and 256): 4 + couplings per chunk,
+    unsegmented sweeps; above K = 208 (FP32) / 128 (FP64) the factor window
+    lives in global memory, above K = 288 (FP32) / 128 (FP64) the sweep
     prefetches two chunks ahead instead of four."""
     band, xt, b = make(N, K, 1.0, 900 + K)
     xo, io, _ = O.solve(band, N, K, b, P, O.SAP_D)
@@ -318,7 +320,7 @@ def test_wide_band_solve_parity(sap, N, K, P, prec):
     assert ast == sap.SAP_OK and relerr(host(lam), lo) <= 1e-8
 
 
-@pytest.mark.parametrize("N,K,P,prec", [(8000, 250, 4, 1), (6000, 150, 3, 0), (5000, 121, 4, 1)])
+@pytest.mark.parametrize("N,K,P,prec", [(8000, 250, 4, 1), (6000, 150, 3, 0), (5000, 121, 4, 1), (6000, 256, 3, 0)])
 def test_wide_band_sapc_solve_parity(sap, N, K, P, prec):
     """SaP-C with wide bands: UL windows and spike workspaces in global memory
     (K > 120 in FP32, K > 98 in FP64); forward and adjoint against the oracle."""

@@ -31,7 +31,7 @@ METRIC = "time to rel.res 1e-10 & HBM GB/s: FP32-precond vs FP64 SaP, fwd+adjoin
 # DRAM bytes (read + write) of the sweep launches of one FP32 SaP-D preconditioner
 # apply on the N=200000, K=50, P=50 workload (automatic segment count), from the
 # ncu capture summarised in profiles/k_sweep_n200k_k50_fp32.md
-TRAFFIC_SWEEPS = 232812800
+TRAFFIC_SWEEPS = 232656896
 # P=None: picked by sap_autotune (measured refactor + solve over N / {16000 .. 1000}, 152, 304)
 # before the timed region; P_ref is the oracle's partition count in that case
 # (the autotuner's pick on GB300 when this table was written).
@@ -380,7 +380,12 @@ def run_gpu(args):
     # sweep, the history chain (more than two segments) and the correction)
     hd = h if variant == S.SAP_D else make_handle(S.SAP_FP32, S.SAP_D)
     segs = i1.segments
-    sweep_launches = 1 if segs == 1 else (6 if segs > 2 else 4)
+    # one fused launch unsegmented; with segments per sweep kind the sweep and the
+    # correction (which runs short history chains itself), plus the chain kernel
+    # when its transfer matrices exceed the correction's 96 KB of shared memory
+    kh = (K + 3) // 4 * 4
+    fused_chain = segs > 2 and ((segs - 2) * kh * kh + (segs - 1) * kh) * 4 <= 96 * 1024
+    sweep_launches = 1 if segs == 1 else (4 if segs == 2 or fused_chain else 6)
     t_sweep = kernel_ms(lambda: S.sap_apply_preconditioner(hd, b, z))
     t_apply = kernel_ms(lambda: S.sap_apply_preconditioner(h, b, z))
     W = 2 * K + 1
@@ -399,8 +404,9 @@ def run_gpu(args):
     ach = kernels["block_solve_fp32"]["GBs"]
     roofline = {"bound": "hbm",
                 "kernel": ("k_block_solve (both triangular sweeps of every block, FP32)" if segs == 1 else
-                           f"k_sweep + k_seg_chain + k_seg_correct (both triangular sweeps of every block in "
-                           f"{segs} segments, FP32; {sweep_launches} launches per apply)"),
+                           f"k_sweep + k_seg_correct{'' if sweep_launches == 4 else ' + k_seg_chain'} (both "
+                           f"triangular sweeps of every block in {segs} segments, FP32; {sweep_launches} launches "
+                           f"per apply)"),
                 "achieved": ach, "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak,
                 "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else
                 "fallback 6.8 TB/s",

@@ -471,12 +471,25 @@ k_seg_chain(const T* __restrict__ Tall, T* __restrict__ tails, int K, Dev d, int
 
 // History correction z_p += sum_q X[q][p] h_q of segments s >= 1, h = the
 // true tail_{s-1}; grid (row tiles of kCorrThreads positions, S - 1, P), one
-// position per thread, X column-major (coalesced).
-template <typename T, typename OT, int MODE>
+// position per thread, X column-major (coalesced).  CHAIN: the tails are
+// still the zero-history ones of k_sweep and each CTA first runs the transfer
+// recurrence tail_j = zhat_tail_j + T_j tail_{j-1} up to j = s-1 itself
+// (T_1 .. T_{s-1} and the tails staged by cp.async in one round, TPR threads
+// per row as in k_seg_chain), which saves the separate chain launch for short
+// chains; otherwise k_seg_chain has already made the tails true.
+template <typename T>
+__host__ __device__ inline size_t fused_chain_smem(int K, int S) {
+  const int kh = hist_width(K);
+  return ((size_t)(S > 2 ? S - 2 : 0) * kh * kh + (size_t)(S - 1) * kh) * sizeof(T);
+}
+constexpr size_t kFusedChainMaxSmem = 96 * 1024;
+
+template <typename T, typename OT, int MODE, bool CHAIN>
 __global__ void __launch_bounds__(kCorrThreads)
-k_seg_correct(const T* __restrict__ Xall, const T* __restrict__ tails, int K, Dev d, int S, int cpsmax,
-              OT* __restrict__ out, Gate gt) {
-  __shared__ T h[4 * CHK];
+k_seg_correct(const T* __restrict__ Xall, const T* __restrict__ tails, const T* __restrict__ Tall, int K, Dev d,
+              int S, int cpsmax, OT* __restrict__ out, Gate gt) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ T hs[4 * CHK];
   if (gate_skip(gt)) return;
   const int b = blockIdx.z;
   const int seg = (int)blockIdx.y + 1;
@@ -489,8 +502,46 @@ k_seg_correct(const T* __restrict__ Xall, const T* __restrict__ tails, int K, De
   const int c0 = seg * cps, c1 = min(nch, c0 + cps);
   const int p = blockIdx.x * kCorrThreads + threadIdx.x;
   if (c0 >= c1 || (int)blockIdx.x * kCorrThreads >= (c1 - c0) * CHK) return;
-  for (int t = threadIdx.x; t < NGW; t += blockDim.x) h[t] = tails[((int64_t)b * S + seg - 1) * NGW + t];
-  __syncthreads();
+  const T* h = hs;
+  if (CHAIN && seg >= 2) {
+    T* Ts = reinterpret_cast<T*>(smem_raw);                   // T_1 .. T_{seg-1}
+    T* zt = Ts + (size_t)(seg - 1) * NGW * NGW;               // tails 0 .. seg-1
+    auto stage = [&](void* dsts, const void* srcg, int nbytes) {
+      const char* src = reinterpret_cast<const char*>(srcg);
+      const unsigned dst = (unsigned)__cvta_generic_to_shared(dsts);
+      for (int o = threadIdx.x * 16; o < nbytes; o += blockDim.x * 16)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst + o), "l"(src + o) : "memory");
+    };
+    stage(zt, tails + (int64_t)b * S * NGW, seg * NGW * (int)sizeof(T));
+    stage(Ts, Tall + ((int64_t)b * S + 1) * NGW * NGW, (seg - 1) * NGW * NGW * (int)sizeof(T));
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+    __syncthreads();
+    int TPR = 1;
+    while (TPR < 8 && NGW % (2 * TPR) == 0 && NGW * 2 * TPR <= kCorrThreads) TPR *= 2;
+    const int i = threadIdx.x / TPR, part = threadIdx.x % TPR;
+    for (int j = 1; j < seg; ++j) {
+      const T* Tj = Ts + (size_t)(j - 1) * NGW * NGW;
+      const T* hp = zt + (size_t)(j - 1) * NGW;
+      T acc = T(0);
+      if (i < NGW) {
+        const T* row = Tj + i * NGW;
+        int q = (part + TPR * i) % NGW;
+        for (int m = 0; m < NGW / TPR; ++m) {
+          acc += row[q] * hp[q];
+          q += TPR;
+          if (q >= NGW) q -= NGW;
+        }
+      }
+      for (int o = TPR / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      if (i < NGW && part == 0) zt[(size_t)j * NGW + i] += acc;
+      __syncthreads();
+    }
+    h = zt + (size_t)(seg - 1) * NGW;
+  } else {
+    for (int t = threadIdx.x; t < NGW; t += blockDim.x) hs[t] = tails[((int64_t)b * S + seg - 1) * NGW + t];
+    __syncthreads();
+  }
   if (p >= (c1 - c0) * CHK) return;
   const int r = row_of<MODE>(c0 * CHK + p, ld);
   if (r >= n) return;
@@ -730,6 +781,18 @@ cudaError_t launch_sweep(const T* M, const T* Tm, const T* Xm, const Factors<T>&
   kern<<<dim3(S, P), NWS * 32, smem, s>>>(M, f.cbase, K, d, yin, out, f.tails, ctop, cbot, P, S, f.err, gt);
   e = cudaGetLastError();
   if (e != cudaSuccess || S == 1) return e;
+  const int tiles = (f.cpsmax * CHK + kCorrThreads - 1) / kCorrThreads;
+  const size_t fsm = fused_chain_smem<T>(K, S);
+  if (S > 2 && fsm <= kFusedChainMaxSmem) {     // short chains: run inside the correction
+    auto corr = k_seg_correct<T, OT, MODE, true>;
+    if (fsm > 48 * 1024) {
+      e = cudaFuncSetAttribute(corr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsm);
+      if (e != cudaSuccess) return e;
+    }
+    count_launches(1);
+    corr<<<dim3(tiles, S - 1, P), kCorrThreads, fsm, s>>>(Xm, f.tails, Tm, K, d, S, f.cpsmax, out, gt);
+    return cudaGetLastError();
+  }
   if (S > 2) {
     const size_t csmem = chain_smem<T>(K, S);
     auto chain = k_seg_chain<T>;
@@ -743,9 +806,8 @@ cudaError_t launch_sweep(const T* M, const T* Tm, const T* Xm, const Factors<T>&
     if (e != cudaSuccess) return e;
   }
   count_launches(1);
-  const int tiles = (f.cpsmax * CHK + kCorrThreads - 1) / kCorrThreads;
-  k_seg_correct<T, OT, MODE><<<dim3(tiles, S - 1, P), kCorrThreads, 0, s>>>(Xm, f.tails, K, d, S, f.cpsmax, out,
-                                                                            gt);
+  k_seg_correct<T, OT, MODE, false><<<dim3(tiles, S - 1, P), kCorrThreads, 0, s>>>(Xm, f.tails, Tm, K, d, S,
+                                                                                   f.cpsmax, out, gt);
   return cudaGetLastError();
 }
 

@@ -66,6 +66,19 @@ def parse():
     return a
 
 
+def max_over_ranks(ms: float) -> float:
+    """Job time of one step: the slowest rank's (all ranks call this after
+    their timed region; NCCL reduces on the device, gloo on the host)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return ms
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([ms], device=dev, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -338,11 +351,7 @@ def run_gpu(args):
 
     h = make_handle(S.SAP_FP32, variant)
     times, infos, launches, clocks, x, lam = timed(h, args.steps, args.warmup, clocks=True)
-    ms = statistics.mean(times)
-    if world > 1:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(statistics.mean(times))
     i1, i2 = infos[-1]
     # the same step with the two solves one after the other (sap_solve, then sap_solve_adjoint)
     seq_times, _, _, _, _, _ = timed(h, args.steps, args.warmup, sequential=True)
@@ -585,11 +594,7 @@ def run_gpu_batch(args):
         times.append(e0.elapsed_time(e1))
     launches = S.sap_kernel_launches() - l0
     clocks = ck.stop()
-    ms = statistics.mean(times)
-    if world > 1:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(statistics.mean(times))
     err = max(float(torch.linalg.norm(x - xt) / torch.linalg.norm(xt)) for x, xt in zip(xs, xts))
     sequential = seq_ms()
     # end to end: bands, rhs and adjoint seeds from pinned host memory, results back

@@ -96,6 +96,10 @@ struct sap_handle {
   // background stream of the transposed sweep matrices (see Solver::factor_post)
   cudaStream_t ts = nullptr;
   cudaEvent_t ev_ts = nullptr, ev_td = nullptr;
+  // the backward-sweep (U) chunk and transfer matrices are built on fs,
+  // concurrently with the forward (L) ones on the factor stream
+  cudaStream_t fs = nullptr;
+  cudaEvent_t ev_fs0 = nullptr, ev_fs1 = nullptr;
   // SaP-C: the UL factorisation runs on its own stream, concurrently with the LU
   cudaStream_t us = nullptr;
   cudaEvent_t ev_us0 = nullptr, ev_us1 = nullptr;
@@ -133,6 +137,9 @@ struct sap_handle {
     if (ev_ts) cudaEventDestroy(ev_ts);
     if (ev_td) cudaEventDestroy(ev_td);
     if (us) cudaStreamDestroy(us);
+    if (fs) cudaStreamDestroy(fs);
+    if (ev_fs0) cudaEventDestroy(ev_fs0);
+    if (ev_fs1) cudaEventDestroy(ev_fs1);
     if (ev_us0) cudaEventDestroy(ev_us0);
     if (ev_us1) cudaEventDestroy(ev_us1);
     for (cudaEvent_t e : evu)
@@ -280,13 +287,10 @@ struct Solver : SolverBase {
   sap_status_t factor_post(cudaStream_t s) override {
     const Layout& L = h->L;
     const int K = L.K, P = L.P;
-    CK(launch_chunk_mats<T>(f.F, K, P, h->d, f.cbase, L.max_nch, 0, f.Mlf, s));
-    CK(launch_chunk_mats<T>(f.F, K, P, h->d, f.cbase, L.max_nch, 1, f.Mub, s));
-    CK(launch_seg_trans<T>(f.Mlf, f.cbase, K, P, L.S, f.cpsmax, h->d, f.Tlf, f.Xlf, s));
-    CK(launch_seg_trans<T>(f.Mub, f.cbase, K, P, L.S, f.cpsmax, h->d, f.Tub, f.Xub, s));
     // a handle that has run a transposed apply gets its transposed sweep
-    // matrices rebuilt in the background, overlapping whatever follows on s
-    // (typically the forward solve); transposed applies wait for them
+    // matrices rebuilt in the background from the new factors, overlapping the
+    // forward ones and whatever follows on s (typically the forward solve);
+    // transposed applies wait for them
     if (f.Mutf) {
       if (!h->ts) {
         CK(cudaStreamCreateWithFlags(&h->ts, cudaStreamNonBlocking));
@@ -299,6 +303,20 @@ struct Solver : SolverBase {
       CK(cudaEventRecord(h->ev_td, h->ts));
       h->ts_pending = true;
     }
+    // forward-sweep matrices on s, backward-sweep ones on fs, joined before s goes on
+    if (!h->fs) {
+      CK(cudaStreamCreateWithFlags(&h->fs, cudaStreamNonBlocking));
+      CK(cudaEventCreateWithFlags(&h->ev_fs0, cudaEventDisableTiming));
+      CK(cudaEventCreateWithFlags(&h->ev_fs1, cudaEventDisableTiming));
+    }
+    CK(cudaEventRecord(h->ev_fs0, s));
+    CK(cudaStreamWaitEvent(h->fs, h->ev_fs0, 0));
+    CK(launch_chunk_mats<T>(f.F, K, P, h->d, f.cbase, L.max_nch, 1, f.Mub, h->fs));
+    CK(launch_seg_trans<T>(f.Mub, f.cbase, K, P, L.S, f.cpsmax, h->d, f.Tub, f.Xub, h->fs));
+    CK(cudaEventRecord(h->ev_fs1, h->fs));
+    CK(launch_chunk_mats<T>(f.F, K, P, h->d, f.cbase, L.max_nch, 0, f.Mlf, s));
+    CK(launch_seg_trans<T>(f.Mlf, f.cbase, K, P, L.S, f.cpsmax, h->d, f.Tlf, f.Xlf, s));
+    CK(cudaStreamWaitEvent(s, h->ev_fs1, 0));
     CK(cudaEventRecord(h->evp[1], s));
     if (h->opt.variant == SAP_C && P > 1) {
       CK(cudaStreamWaitEvent(s, h->ev_us1, 0));      // the UL started by factor_pre

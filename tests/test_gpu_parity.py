@@ -455,3 +455,21 @@ def test_full_size_solve_pair_n200k_k50_p50(sap):
     xo, _, _ = O.solve(band, N, K, b, P, O.SAP_D)
     lo, _, _ = O.solve_adjoint(band, N, K, g, P, O.SAP_D)
     assert relerr(host(x), xo) <= 1e-8 and relerr(host(lam), lo) <= 1e-8
+
+
+@pytest.mark.parametrize("N,K,P,variant,prec", [(8000, 250, 4, 1, 1), (5000, 130, 2, 0, 2), (3000, 20, 1, 0, 0),
+                                                (9000, 120, 3, 1, 0)])
+def test_solve_pair_wide_tc_and_p1(sap, N, K, P, variant, prec):
+    """The pair on wide-band SaP-C (multi-CTA reduced solves, separate
+    transposed scratch), on the tensor-core factorisation, and with P = 1:
+    bit-identical to the sequential solves."""
+    band, xt, b = make(N, K, 1.0, 2300 + K)
+    g = G.adjoint_seed(N, 2300 + K)
+    h = sap.sap_factor(dev(band), N, K, P=P, variant=variant, precision=prec)
+    xs, ix0, _ = sap.sap_solve(h, dev(b))
+    ls, il0, _ = sap.sap_solve_adjoint(h, dev(g))
+    x, lam, ix, il, st = sap.sap_solve_pair(h, dev(b), dev(g))
+    assert st == sap.SAP_OK and ix.relres <= 1e-10 and il.relres <= 1e-10
+    assert torch.equal(x, xs) and torch.equal(lam, ls)
+    assert ix.iters == ix0.iters and il.iters == il0.iters
+    assert ix.tc_update == int(prec == 2 and 64 <= K <= 192)

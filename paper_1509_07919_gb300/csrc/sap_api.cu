@@ -62,6 +62,9 @@ struct SolverBase {
   virtual sap_status_t factor_post(cudaStream_t s) = 0;      // after the block LU
   virtual void lu_items(std::vector<LuItem>& out) const = 0;  // this system's blocks as LU work items
   virtual sap_status_t build_adjoint(cudaStream_t s) = 0;
+  // the same launched on s without waiting; adjoint_singular() reads its outcome later
+  virtual sap_status_t build_adjoint_async(cudaStream_t s) = 0;
+  virtual sap_status_t adjoint_singular() = 0;
   virtual sap_status_t apply(const double* r, double* z, bool transpose, cudaStream_t s, Gate gt = Gate()) = 0;
   // build what a transposed apply needs (adjoint tips, transposed sweep matrices); synchronises
   virtual sap_status_t prepare_transposed(cudaStream_t s) = 0;
@@ -86,6 +89,7 @@ struct sap_handle {
   double* absmax = nullptr;
   unsigned long long* n_boosted = nullptr;
   int* singular = nullptr;
+  int* singular_a = nullptr;   // the same for the adjoint's reduced matrices (built apart, maybe concurrently)
   // Krylov workspace
   double* vec = nullptr;      // 11 N doubles: r0 r1 r2 u0 u1 u2 rt tmp t, b and x of the iteration
   // one outer BiCGStab(2) iteration captured as a CUDA graph, per direction
@@ -173,7 +177,9 @@ struct Solver : SolverBase {
   T* wlu = nullptr;            // factor windows in global memory (bands too wide for shared memory)
   T* wul = nullptr;            // the same for the UL factorisation (it runs concurrently with the LU)
   void* wspk = nullptr;        // spike-kernel workspaces in global memory (same)
+  void* wspk_a = nullptr;      // the adjoint's (its tips may be built concurrently with the forward ones)
   bool adjoint_ready = false;
+  bool adjoint_unchecked = false;  // adjoint tips launched without the singular check
   bool transposed_ready = false;
   explicit Solver(sap_handle* hh) : h(hh) {}
 
@@ -243,7 +249,9 @@ struct Solver : SolverBase {
     // the background build of the previous factorisation reads F: wait for it
     if (h->ts_pending) CK(cudaStreamWaitEvent(s, h->ev_td, 0));
     h->ts_pending = false;
+    CK(cudaMemsetAsync(h->singular_a, 0, sizeof(int), s));
     adjoint_ready = false;
+    adjoint_unchecked = false;
     transposed_ready = false;
     CK(cudaEventRecord(h->evp[0], s));
     if (sizeof(T) == 4) CK(launch_absmax_cast(h->band, L.N, L.K, h->absmax, bandf, s));
@@ -291,7 +299,9 @@ struct Solver : SolverBase {
     // matrices rebuilt in the background from the new factors, overlapping the
     // forward ones and whatever follows on s (typically the forward solve);
     // transposed applies wait for them
-    if (f.Mutf) {
+    // (SaP-C: also the adjoint's tips and reduced matrices, once the UL is done)
+    const bool bg_adj = h->opt.variant == SAP_C && P > 1 && f.Va != nullptr;
+    if (f.Mutf || bg_adj) {
       if (!h->ts) {
         CK(cudaStreamCreateWithFlags(&h->ts, cudaStreamNonBlocking));
         CK(cudaEventCreateWithFlags(&h->ev_ts, cudaEventDisableTiming));
@@ -299,7 +309,13 @@ struct Solver : SolverBase {
       }
       CK(cudaEventRecord(h->ev_ts, s));
       CK(cudaStreamWaitEvent(h->ts, h->ev_ts, 0));
-      TRY(build_transposed(h->ts));
+      if (f.Mutf) TRY(build_transposed(h->ts));
+      if (bg_adj) {
+        CK(cudaStreamWaitEvent(h->ts, h->ev_us1, 0));   // the UL started by factor_pre
+        TRY(launch_adjoint_tips(h->ts));
+        adjoint_ready = true;
+        adjoint_unchecked = true;
+      }
       CK(cudaEventRecord(h->ev_td, h->ts));
       h->ts_pending = true;
     }
@@ -337,8 +353,25 @@ struct Solver : SolverBase {
     return factor_post(s);
   }
 
-  sap_status_t build_adjoint(cudaStream_t s) override {
+  sap_status_t build_adjoint_async(cudaStream_t s) override {
     if (adjoint_ready || h->opt.variant != SAP_C || h->L.P < 2) return SAP_OK;
+    TRY(launch_adjoint_tips(s));
+    adjoint_ready = true;       // ordered before the adjoint iteration on s
+    adjoint_unchecked = true;
+    return SAP_OK;
+  }
+  sap_status_t adjoint_singular() override {
+    if (!adjoint_unchecked) return SAP_OK;
+    adjoint_unchecked = false;
+    if (h->ts_pending) CK(cudaEventSynchronize(h->ev_td));   // tips built in the background
+    int sing = 0;
+    CK(cudaMemcpy(&sing, h->singular_a, sizeof(int), cudaMemcpyDeviceToHost));
+    if (!sing) return SAP_OK;
+    CK(cudaMemset(h->singular_a, 0, sizeof(int)));
+    adjoint_ready = false;
+    return SAP_ERR_SINGULAR;
+  }
+  sap_status_t launch_adjoint_tips(cudaStream_t s) {
     const int K = h->L.K, nI = h->L.P - 1;
     const int64_t KK = (int64_t)K * K;
     if (!f.Va) {
@@ -348,12 +381,28 @@ struct Solver : SolverBase {
       TRY(h->mem.alloc(&f.Ra0, (size_t)(nI * KK)));
       TRY(h->mem.alloc(&f.piva, (size_t)(nI * K)));
     }
+    const size_t sb = spike_scratch_bytes(K, h->L.P, sizeof(T) == 8);
+    if (sb && !wspk_a) {
+      unsigned char* q = nullptr;
+      TRY(h->mem.alloc(&q, sb));
+      wspk_a = q;
+    }
     CK(launch_spikes<T>(h->band, h->L.N, K, h->L.P, h->d, f.F, f.ULt, true, f.Va, f.Wa, f.Ra, f.Ra0, f.piva,
-                        h->singular, wspk, s));
+                        h->singular_a, wspk_a, s));
+    return SAP_OK;
+  }
+  sap_status_t build_adjoint(cudaStream_t s) override {
+    if (adjoint_ready && !adjoint_unchecked) return SAP_OK;
+    if (adjoint_ready) return adjoint_singular();     // built in the background: its outcome
+    if (h->opt.variant != SAP_C || h->L.P < 2) return SAP_OK;
+    TRY(launch_adjoint_tips(s));
     int sing = 0;
-    CK(cudaMemcpyAsync(&sing, h->singular, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(&sing, h->singular_a, sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
-    if (sing) return SAP_ERR_SINGULAR;
+    if (sing) {
+      CK(cudaMemset(h->singular_a, 0, sizeof(int)));
+      return SAP_ERR_SINGULAR;
+    }
     adjoint_ready = true;
     return SAP_OK;
   }
@@ -407,11 +456,8 @@ struct Solver : SolverBase {
   }
 
   sap_status_t prepare_transposed(cudaStream_t s) override {
+    if (h->ts_pending) CK(cudaStreamWaitEvent(s, h->ev_td, 0));   // built in the background after the LU
     TRY(build_adjoint(s));
-    if (h->ts_pending) {       // built in the background after the LU: order s after it
-      CK(cudaStreamWaitEvent(s, h->ev_td, 0));
-      return SAP_OK;
-    }
     return build_transposed(s);
   }
 
@@ -885,6 +931,8 @@ sap_status_t create_handle(const double* band_dev, int64_t N, int32_t K, const s
   TRY(h->mem.alloc(&h->absmax, 1));
   TRY(h->mem.alloc(&h->n_boosted, 1));
   TRY(h->mem.alloc(&h->singular, 1));
+  TRY(h->mem.alloc(&h->singular_a, 1));
+  CK(cudaMemsetAsync(h->singular_a, 0, sizeof(int), s));
   TRY(h->mem.alloc(&h->vec, (size_t)(11 * N)));
   TRY(h->mem.alloc(&h->kd.S, S_COUNT));
   TRY(h->mem.alloc(&h->kd.part, kKrylovBlocks * 4));
@@ -1063,15 +1111,22 @@ sap_status_t solve_pair_batch(sap_batch* B, const double* const* b, double* cons
   for (size_t i = 0; i < n; ++i) {
     if (!b[i] || !x[i] || !g[i] || !lam[i] || b[i] == x[i] || g[i] == lam[i] || x[i] == lam[i])
       return SAP_ERR_INVALID_ARG;
-    TRY(B->hs[i]->impl->build_adjoint(s));
     TRY(k[i].init(B->hs[i], b[i], x[i], false, s, 0));
     TRY(k[n + i].init(B->hs[i], g[i], lam[i], true, s, 1));
+    // SaP-C: each system's adjoint tips on its adjoint stream, overlapping the forward iterations
+    CK(cudaEventRecord(B->hs[i]->w2.evj, s));
+    CK(cudaStreamWaitEvent(k[n + i].s, B->hs[i]->w2.evj, 0));
+    TRY(B->hs[i]->impl->build_adjoint_async(k[n + i].s));
   }
   TRY(run_lockstep(k));
   sap_status_t st = SAP_OK;
   for (size_t i = 0; i < 2 * n; ++i) {
     sap_info_t* inf = i < n ? (ix ? &ix[i] : nullptr) : (il ? &il[i - n] : nullptr);
-    const sap_status_t e = k[i].finish(inf);
+    sap_status_t e = k[i].finish(inf);
+    if (i >= n) {
+      const sap_status_t sg = B->hs[i - n]->impl->adjoint_singular();
+      if (sg != SAP_OK) e = sg;
+    }
     if (statuses) statuses[i] = e;
     if (st == SAP_OK) st = e;
   }
@@ -1137,12 +1192,16 @@ sap_status_t sap_solve_adjoint(sap_handle_t h, const double* g, double* lam, sap
 sap_status_t sap_solve_pair(sap_handle_t h, const double* b, double* x, const double* g, double* lam,
                             sap_info_t* info_x, sap_info_t* info_lam, cudaStream_t s) {
   if (!h || !b || !x || !g || !lam || b == x || g == lam || x == lam) return SAP_ERR_INVALID_ARG;
-  TRY(h->impl->build_adjoint(s));
   // forward on the handle's workspace, adjoint on the second one: two streams,
   // lockstep rounds, one host synchronisation per round for both
   KrylovRun k[2];
   TRY(k[0].init(h, b, x, false, s, 0));
   TRY(k[1].init(h, g, lam, true, s, 1));
+  // SaP-C: the adjoint's tips and reduced matrices are built on the adjoint's
+  // stream while the forward iteration starts
+  CK(cudaEventRecord(h->w2.evj, s));
+  CK(cudaStreamWaitEvent(k[1].s, h->w2.evj, 0));
+  TRY(h->impl->build_adjoint_async(k[1].s));
   TRY(k[0].begin());
   TRY(k[1].begin());
   for (auto& r : k) {
@@ -1161,7 +1220,9 @@ sap_status_t sap_solve_pair(sap_handle_t h, const double* b, double* x, const do
       }
   }
   const sap_status_t sx = k[0].finish(info_x);
-  const sap_status_t sl = k[1].finish(info_lam);
+  sap_status_t sl = k[1].finish(info_lam);
+  const sap_status_t sg = h->impl->adjoint_singular();
+  if (sg != SAP_OK) sl = sg;
   return sx != SAP_OK ? sx : sl;
 }
 

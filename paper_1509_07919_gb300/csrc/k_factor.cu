@@ -34,6 +34,9 @@ namespace {
 
 constexpr int NB = 16;             // panel width
 constexpr int NTHREADS = 256;
+// 512 threads for the global-memory window (its L2-resident read-modify-write
+// of the trailing matrix wants more loads in flight), 256 otherwise
+__host__ __device__ constexpr int lu_threads(bool gw, bool tc) { return gw && !tc ? 512 : 256; }
 
 __device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
   unsigned s = (unsigned)__cvta_generic_to_shared(smem);
@@ -155,11 +158,12 @@ __device__ void tc_teardown(TcCtx& t, int K) {
 // GW: the window in global memory at wglob (M2 x LDW, L2-resident) instead
 // of shared memory; wide bands whose (K+16)^2 window does not fit in
 // shared memory use the global form, the staging buffers stay in shared memory.
-template <typename T, bool REV, bool GW, bool TC>
+template <typename T, bool REV, bool GW, bool TC, int NTH>
 __device__ void band_lu_block(unsigned char* smem_raw, const T* __restrict__ band, int64_t N, int K, int64_t s,
                               int n, int64_t ld, T* __restrict__ F, const T tau,
                               unsigned long long* __restrict__ n_boosted, T* wglob, TcCtx& tcx) {
   static_assert(!TC || sizeof(T) == 4, "the tensor-core trailing update is an FP32-factor mode");
+  static_assert(!TC || NTH == 256, "the tensor-core readback splits TMEM columns over two warpgroups");
   const int M2 = win_m2(K);
   const int LDW = M2 + 4;
   const int KA = K + NB;          // active rows/cols of the window in a panel step
@@ -174,7 +178,7 @@ __device__ void band_lu_block(unsigned char* smem_raw, const T* __restrict__ ban
 
   Win w{M2, LDW, 0};
   // initial window: logical rows/cols [0, M2), physical == logical
-  for (int e = tid; e < M2 * M2; e += NTHREADS) {
+  for (int e = tid; e < M2 * M2; e += NTH) {
     int r = e / M2, q = e % M2;
     const T* p = elem_ptr<REV>(band, N, K, s, n, r, q);
     W[r * LDW + q] = p ? *p : T(0);
@@ -234,8 +238,8 @@ __device__ void band_lu_block(unsigned char* smem_raw, const T* __restrict__ ban
     } else {
       // entering rows i = k0 + M2 + e (columns of the next window, offsets jo from k0 + NB)
       // and entering columns j = k0 + M2 + e for resident rows i = k0 + NB + ro (ro < ME)
-      const int hw = warp - 1, ht = tid - 32, nh = NTHREADS - 32;
-      for (int e = hw; e < NB; e += NTHREADS / 32 - 1)
+      const int hw = warp - 1, ht = tid - 32, nh = NTH - 32;
+      for (int e = hw; e < NB; e += NTH / 32 - 1)
         for (int jo = lane; jo < M2; jo += 32) {
           T* dst = &ER[e * M2 + jo];
           const T* src = elem_ptr<REV>(band, N, K, s, n, k0 + M2 + e, k0 + NB + jo);
@@ -255,8 +259,8 @@ __device__ void band_lu_block(unsigned char* smem_raw, const T* __restrict__ ban
 
     // ---- A2: L21 = A21 U11^{-1} (rows NB..KA-1, threads 0..127) ||
     //      B:  U12 = L11^{-1} A12 (columns NB..KA-1, threads 128..255) ----
-    if (tid < NTHREADS / 2) {
-      for (int ro = NB + tid; ro < KA; ro += NTHREADS / 2) {
+    if (tid < NTH / 2) {
+      for (int ro = NB + tid; ro < KA; ro += NTH / 2) {
         T* row = &W[w.ph(ro) * LDW + base];
         T x[NB];
 #pragma unroll
@@ -277,7 +281,7 @@ __device__ void band_lu_block(unsigned char* smem_raw, const T* __restrict__ ban
         for (int c = 0; c < NB; ++c) row[c] = x[c];
       }
     } else {
-      for (int c = NB + tid - NTHREADS / 2; c < KA; c += NTHREADS / 2) {
+      for (int c = NB + tid - NTH / 2; c < KA; c += NTH / 2) {
         const int pc = w.ph(c);
         T x[NB];
 #pragma unroll
@@ -297,7 +301,7 @@ __device__ void band_lu_block(unsigned char* smem_raw, const T* __restrict__ ban
 
     // ---- D1: write the finished panel (U rows k0.., L columns k0..) ----
     auto write_panel = [&]() {
-      for (int e = tid; e < NB * (2 * K + 1); e += NTHREADS) {
+      for (int e = tid; e < NB * (2 * K + 1); e += NTH) {
         const int dg = e / NB, t = e % NB;    // diagonal index c = K + i - j, position in panel
         int i, j;
         if (dg <= K) { i = k0 + t; j = i + (K - dg); }     // U(i, j), j - i = K - dg
@@ -317,7 +321,7 @@ __device__ void band_lu_block(unsigned char* smem_raw, const T* __restrict__ ban
     // ---- C: A22 -= L21 U12 over window rows/cols [NB, NB + K) ----
     if constexpr (TC) {
       const int Kr = (K + 15) / 16 * 16;        // trailing rows / cols touched (16-aligned groups)
-      for (int e = tid; e < Kr * NB; e += NTHREADS) {
+      for (int e = tid; e < Kr * NB; e += NTH) {
         const int r = e / NB, q = e % NB;
         const T a = r < K ? W[w.ph(NB + r) * LDW + base + q] : T(0);     // L21(r, q)
         const T b = r < K ? W[(base + q) * LDW + w.ph(NB + r)] : T(0);    // U12(q, r)
@@ -371,7 +375,7 @@ __device__ void band_lu_block(unsigned char* smem_raw, const T* __restrict__ ban
     } else
     {
       const int nt = (K + 3) / 4;
-      for (int t = tid; t < nt * nt; t += NTHREADS) {
+      for (int t = tid; t < nt * nt; t += NTH) {
         const int ti = t / nt, tj = t % nt;
         const int r0 = w.ph(NB + 4 * ti), c0 = w.ph(NB + 4 * tj);   // 4-groups never wrap
         T acc[4][4];
@@ -407,11 +411,11 @@ __device__ void band_lu_block(unsigned char* smem_raw, const T* __restrict__ ban
     // ---- D2: slide the window by NB: entering rows/cols replace the panel's ----
     {
       Win w2{M2, LDW, w.ph(NB)};        // next window: logical offset 0 = k0 + NB
-      for (int e = warp; e < NB; e += NTHREADS / 32) {
+      for (int e = warp; e < NB; e += NTH / 32) {
         T* row = &W[w2.ph(ME + e) * LDW];                      // row k0+M2+e = next offset ME+e
         for (int jo = lane; jo < M2; jo += 32) row[w2.ph(jo)] = ER[e * M2 + jo];
       }
-      for (int y = tid; y < ME * NB; y += NTHREADS) {
+      for (int y = tid; y < ME * NB; y += NTH) {
         const int ro = y / NB, e = y % NB;
         W[w2.ph(ro) * LDW + w2.ph(ME + e)] = EC[y];           // column k0+M2+e, row k0+NB+ro
       }
@@ -437,7 +441,7 @@ __host__ __device__ inline size_t lu_tc_offset(int K, bool global_window) {
 }
 
 template <typename T, bool REV, bool GW, bool TC>
-__global__ void __launch_bounds__(NTHREADS)
+__global__ void __launch_bounds__(lu_threads(GW, TC))
 k_band_lu(const T* __restrict__ band, int64_t N, int K, Dev d, int block0,
           const double* __restrict__ absmax, double eps, T* __restrict__ out,
           unsigned long long* __restrict__ n_boosted, T* __restrict__ wscratch, int* __restrict__ err) {
@@ -451,7 +455,8 @@ k_band_lu(const T* __restrict__ band, int64_t N, int K, Dev d, int block0,
   T* wg = GW ? wscratch + (int64_t)blockIdx.x * M2 * (M2 + 4) : nullptr;
   TcCtx tcx;
   if constexpr (TC) tc_setup(smem_raw + lu_tc_offset(K, GW), K, tcx, err);
-  band_lu_block<T, REV, GW, TC>(smem_raw, band, N, K, s, n, ld, F, (T)(eps * absmax[0]), n_boosted, wg, tcx);
+  band_lu_block<T, REV, GW, TC, lu_threads(GW, TC)>(smem_raw, band, N, K, s, n, ld, F, (T)(eps * absmax[0]),
+                                                   n_boosted, wg, tcx);
   if constexpr (TC) tc_teardown(tcx, K);
 }
 
@@ -459,7 +464,7 @@ k_band_lu(const T* __restrict__ band, int64_t N, int K, Dev d, int block0,
 // first): each CTA takes the next item from an atomic counter until the list
 // is exhausted, so one launch factors every block of a batch.
 template <typename T, bool GW, bool TC>
-__global__ void __launch_bounds__(NTHREADS)
+__global__ void __launch_bounds__(lu_threads(GW, TC))
 k_band_lu_items(const LuItem* __restrict__ items, int nitems, unsigned* __restrict__ counter,
                 T* __restrict__ wscratch, int64_t wstride, int Kmax, int* __restrict__ err) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -473,7 +478,7 @@ k_band_lu_items(const LuItem* __restrict__ items, int nitems, unsigned* __restri
     __syncthreads();          // every thread has read cur before it changes
     if (it >= nitems) break;
     const LuItem I = items[it];
-    band_lu_block<T, false, GW, TC>(smem_raw, reinterpret_cast<const T*>(I.band), I.N, I.K, I.s, I.n, I.ld,
+    band_lu_block<T, false, GW, TC, lu_threads(GW, TC)>(smem_raw, reinterpret_cast<const T*>(I.band), I.N, I.K, I.s, I.n, I.ld,
                                     reinterpret_cast<T*>(I.F), (T)(I.eps * I.absmax[0]), I.nb,
                                     GW ? wscratch + (int64_t)blockIdx.x * wstride : nullptr, tcx);
     __syncthreads();
@@ -500,7 +505,7 @@ cudaError_t launch_lu_impl(const T* band, int64_t N, int K, int nblocks, int blo
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   count_launches(1);
-  kern<<<nblocks, NTHREADS, smem, s>>>(band, N, K, d, block0, absmax, eps, out, nb, wscratch, err);
+  kern<<<nblocks, lu_threads(gw, tc), smem, s>>>(band, N, K, d, block0, absmax, eps, out, nb, wscratch, err);
   return cudaGetLastError();
 }
 
@@ -605,7 +610,7 @@ int lu_items_grid(int nitems, int Kmax, bool fp64, bool tc) {
   int per_sm = 0;
   auto occ = [&](auto kern) {
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NTHREADS, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, lu_threads(gw, tc), smem);
   };
   if (fp64) gw ? occ(k_band_lu_items<double, true, false>) : occ(k_band_lu_items<double, false, false>);
   else if (tc) gw ? occ(k_band_lu_items<float, true, true>) : occ(k_band_lu_items<float, false, true>);
@@ -638,7 +643,8 @@ cudaError_t launch_factor_lu_items(const LuItem* items, int nitems, int Kmax, un
   cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned), s);
   if (e != cudaSuccess) return e;
   count_launches(1);
-  kern<<<grid, NTHREADS, smem, s>>>(items, nitems, counter, wscratch, (int64_t)lu_window_elems(Kmax), Kmax, err);
+  kern<<<grid, lu_threads(gw, tc), smem, s>>>(items, nitems, counter, wscratch, (int64_t)lu_window_elems(Kmax),
+                                              Kmax, err);
   return cudaGetLastError();
 }
 

@@ -3,19 +3,21 @@
 // SaP-C the truncated reduced systems (Eq. (2.5)) and the purification
 // solves that follow them.
 //
-// Sweep kernel: one CTA of three warps per block and segment, one sweep kind
-// per launch.  A sweep is a lower-triangular recurrence over positions p (rows in sweep
-// order), processed in chunks of 32 positions with the chunk matrices of
-// k_chunk.cu (MINV_c and the couplings G_{c,k}, k = 1..ng, ng = ceil(K/32)):
+// Sweep kernels: per block and segment one CTA of 2 + NPW warps (NPW = 1
+// prepare warp for ceil(K/32) <= 3 couplings, 2 up to 7, 4 above).  A sweep
+// is a lower-triangular recurrence over positions p (rows in sweep order),
+// processed in chunks of 32 positions with the chunk matrices of k_chunk.cu
+// (MINV_c and the couplings G_{c,k}, k = 1..ng, ng = ceil(K/32)):
 //     z_c = w_c - G_{c,1} z_{c-1},
 //     w_c = MINV_c (y_c - corrections) - sum_{k>=2} G_{c,k} z_{c-k}.
 //   - warp 0 runs the dependent chain: one 32 x 32 product per chunk, with
 //     z_{c-1} broadcast from its own registers by shuffles;
-//   - warp 1 streams the right-hand side with cp.async and forms w_{c+1}
-//     one chunk ahead;
-//   - warp 2 streams each chunk's matrices (one contiguous block) into a
-//     shared-memory ring with a bulk (TMA) copy and waits on the slot's
-//     mbarrier; the other warps see the data through the CTA barrier.
+//   - warps 1 .. NPW form w_{c+1} one chunk ahead (warp 1 also streams the
+//     right-hand side with cp.async), each a share of the G_k products;
+//   - the last warp streams each chunk's matrices (one contiguous block) into
+//     a shared-memory ring (4 or, for the widest bands, 2 chunks ahead) with a
+//     bulk (TMA) copy and waits on the slot's mbarrier; the other warps see
+//     the data through the CTA barrier.
 // Positions run over [0, ld) (ld = n rounded up to 32); a backward sweep
 // maps row r to p = ld - 1 - r.  Positions without a row produce 0.
 // With S > 1 segments per block the chunks of a sweep are cut into S ranges

@@ -1,17 +1,21 @@
 // Banded LU / UL factorisation of the diagonal blocks A_i without pivoting,
 // with pivot boosting (Sec. 2.2, Sec. 3.1 "LU/UL factorizations").
 //
-// One CTA (8 warps) factors one block with a blocked right-looking
-// elimination over panels of NB = 16 columns.  The active window, rows and
-// columns [k0, k0 + K + NB) of the block, lives in shared memory, addressed
-// modulo M2 = K + NB in both directions so that sliding it by a panel only
-// replaces NB physical rows and columns.  Per panel:
-//   A. warp 0 factors the (K+NB) x NB panel in registers (pivot row by
-//      shuffles, boosted pivot, multipliers, in-panel update); meanwhile the
-//      other warps cp.async the entering band rows/columns of the next
-//      window into a staging buffer;
-//   B. U12 = L11^{-1} A12 for the panel rows (one thread per column);
-//   C. trailing update A22 -= L21 U12 (K x K, 4 x 4 register tiles);
+// One CTA (8 warps; 16 with the window in global memory) factors one block
+// with a blocked right-looking elimination over panels of NB = 16 columns.
+// The active window, rows and columns [k0, k0 + K + NB) of the block, lives
+// in shared memory (or, for bands too wide for it, in an L2-resident global
+// scratch), addressed modulo M2 = K + NB rounded up in both directions, so
+// that sliding it by a panel only replaces NB physical rows and columns.  Per
+// panel:
+//   A1. warp 0 factors the 16 x 16 diagonal block in registers (pivot row by
+//       shuffles, boosted pivot, multipliers); meanwhile the other warps
+//       cp.async the entering band rows/columns of the next window into a
+//       staging buffer;
+//   A2/B. L21 = A21 U11^{-1} (one thread per row) and U12 = L11^{-1} A12 (one
+//       thread per column), on the two halves of the CTA;
+//   C. trailing update A22 -= L21 U12 (K x K, 4 x 4 register tiles, or on the
+//      tensor cores, see below);
 //   D. the finished panel rows of U and columns of L go to global memory and
 //      the staged entering rows/columns replace the retired ones.
 // Four barriers per 16 columns.  Entries outside the band (and outside the

@@ -45,3 +45,19 @@ def test_package_refuses_to_run_without_library(tmp_path, monkeypatch):
     mod = importlib.util.module_from_spec(spec)
     with pytest.raises(ImportError):
         spec.loader.exec_module(mod)
+
+
+def test_host_only_calls_on_cpu():
+    """Entry points that need no GPU: the K limits (the sweep ring's shared
+    memory, two chunks ahead: 512 for FP32 factors with or without the
+    tensor-core update, 256 for FP64), the status strings of every status and
+    the default options."""
+    import paper_1509_07919_gb300 as S
+    assert S.sap_max_K(S.SAP_FP64) == 256
+    assert S.sap_max_K(S.SAP_FP32) == 512 and S.sap_max_K(S.SAP_FP32_BF16TU) == 512
+    names = {st: S.sap_status_string(st) for st in range(0, 10)}
+    assert names[S.SAP_OK] == "ok"
+    assert len(set(names.values())) >= 8          # distinct messages for the defined statuses
+    o = S.sap_default_options()
+    assert (o.P, o.variant, o.precision, o.max_iters, o.tol, o.segments, o.reserved0) == \
+        (1, S.SAP_D, S.SAP_FP64, 500, 1e-10, 0, 0)

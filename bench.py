@@ -29,8 +29,8 @@ sys.path.insert(0, ROOT)
 
 METRIC = "time to rel.res 1e-10 & HBM GB/s: FP32-precond vs FP64 SaP, fwd+adjoint"
 # DRAM bytes (read + write) of the sweep launches of one FP32 SaP-D preconditioner
-# apply on the N=200000, K=50, P=50 workload (automatic segment count), from the
-# ncu capture summarised in profiles/k_sweep_n200k_k50_fp32.md
+# apply on the N=200000, K=50, P=50 workload (automatic segment count), from one
+# ncu capture of dram__bytes_read.sum + dram__bytes_write.sum of those launches
 TRAFFIC_SWEEPS = 232656896
 # P=None: picked by sap_autotune (measured refactor + solve over N / {16000 .. 1000}, 152, 304)
 # before the timed region; P_ref is the oracle's partition count in that case
@@ -420,7 +420,7 @@ def run_gpu(args):
                 "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else
                 "fallback 6.8 TB/s",
                 # dram__bytes_read.sum + dram__bytes_write.sum of the sweep launches of one
-                # apply (profiles/k_sweep_n200k_k50_fp32.md); above the algorithmic bytes
+                # apply (one ncu capture); above the algorithmic bytes
                 # because the sweeps stream the per-chunk inverse/coupling matrices
                 "traffic": TRAFFIC_SWEEPS if (N, K, P) == (200000, 50, 50) else None,
                 "algorithmic_bytes_per_launch": sweep_bytes,

@@ -368,11 +368,11 @@ k_rbar_gepp(int K, unsigned char* __restrict__ gws, int* __restrict__ pivout, in
 }
 
 // Rbar_i^{-1} = U^{-1} L^{-1} P from the GEPP factors, 32 columns per CTA
-// (K x 32 right-hand sides in shared memory, lane = column); the four warps
-// split every row's dot product (q = w mod 4, two accumulators each: FP64
+// (K x 32 right-hand sides in shared memory, lane = column); the eight warps
+// split every row's dot product (q = w mod 8, two accumulators each: FP64
 // multiply-add latency is long on GB300) and warp 0 finishes the row.
 // Grid (ceil(K / 32), P - 1).
-constexpr int kInvWarps = 4;
+constexpr int kInvWarps = 8;
 template <typename T>
 __global__ void __launch_bounds__(32 * kInvWarps)
 k_rbar_inv(int K, const unsigned char* __restrict__ gws, const int* __restrict__ pivin, double* __restrict__ Rinv) {

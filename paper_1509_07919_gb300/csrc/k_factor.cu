@@ -14,8 +14,8 @@
 //       staging buffer;
 //   A2/B. L21 = A21 U11^{-1} (one thread per row) and U12 = L11^{-1} A12 (one
 //       thread per column), on the two halves of the CTA;
-//   C. trailing update A22 -= L21 U12 (K x K, 4 x 4 register tiles, or on the
-//      tensor cores, see below);
+//   C. trailing update A22 -= L21 U12 (K x K, 4 x 4 register tiles, 8 x 4 for
+//      FP32 in the global window, or on the tensor cores, see below);
 //   D. the finished panel rows of U and columns of L go to global memory and
 //      the staged entering rows/columns replace the retired ones.
 // Four barriers per 16 columns.  Entries outside the band (and outside the
@@ -92,6 +92,37 @@ __device__ __forceinline__ void ld4(const T* p, T (&v)[4]) {
     double2 x = *reinterpret_cast<const double2*>(p);
     double2 y = *reinterpret_cast<const double2*>(p + 2);
     v[0] = x.x; v[1] = x.y; v[2] = y.x; v[3] = y.y;
+  }
+}
+template <typename T>
+__device__ __forceinline__ void st4(T* p, const T (&v)[4]) {
+  if constexpr (sizeof(T) == 4) {
+    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+  } else {
+    *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]);
+    *reinterpret_cast<double2*>(p + 2) = make_double2(v[2], v[3]);
+  }
+}
+// the same for global memory, cached in L2 only (entries touched once per
+// panel, which would otherwise push the panel operands out of L1)
+template <typename T>
+__device__ __forceinline__ void ld4_cg(const T* p, T (&v)[4]) {
+  if constexpr (sizeof(T) == 4) {
+    const float4 x = __ldcg(reinterpret_cast<const float4*>(p));
+    v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
+  } else {
+    const double2 x = __ldcg(reinterpret_cast<const double2*>(p));
+    const double2 y = __ldcg(reinterpret_cast<const double2*>(p + 2));
+    v[0] = x.x; v[1] = x.y; v[2] = y.x; v[3] = y.y;
+  }
+}
+template <typename T>
+__device__ __forceinline__ void st4_cg(T* p, const T (&v)[4]) {
+  if constexpr (sizeof(T) == 4) {
+    __stcg(reinterpret_cast<float4*>(p), make_float4(v[0], v[1], v[2], v[3]));
+  } else {
+    __stcg(reinterpret_cast<double2*>(p), make_double2(v[0], v[1]));
+    __stcg(reinterpret_cast<double2*>(p + 2), make_double2(v[2], v[3]));
   }
 }
 
@@ -236,7 +267,7 @@ __device__ void band_lu_block(unsigned char* smem_raw, const T* __restrict__ ban
       if (lane < NB) {
         T* row = &W[(base + lane) * LDW + base];
 #pragma unroll
-        for (int c = 0; c < NB; ++c) row[c] = pv[c];
+        for (int c4 = 0; c4 < NB / 4; ++c4) st4(row + 4 * c4, {pv[4 * c4], pv[4 * c4 + 1], pv[4 * c4 + 2], pv[4 * c4 + 3]});
         RV[lane] = myrinv;
       }
     } else {
@@ -282,7 +313,7 @@ __device__ void band_lu_block(unsigned char* smem_raw, const T* __restrict__ ban
           x[j] = acc * RV[j];
         }
 #pragma unroll
-        for (int c = 0; c < NB; ++c) row[c] = x[c];
+        for (int c4 = 0; c4 < NB / 4; ++c4) st4(row + 4 * c4, {x[4 * c4], x[4 * c4 + 1], x[4 * c4 + 2], x[4 * c4 + 3]});
       }
     } else {
       for (int c = NB + tid - NTH / 2; c < KA; c += NTH / 2) {
@@ -304,22 +335,38 @@ __device__ void band_lu_block(unsigned char* smem_raw, const T* __restrict__ ban
     __syncthreads();
 
     // ---- D1: write the finished panel (U rows k0.., L columns k0..) ----
+    // Four entries per thread are read before any is stored, so that the
+    // window reads overlap (each entry is written once, to its own place).
     auto write_panel = [&]() {
-      for (int e = tid; e < NB * (2 * K + 1); e += NTH) {
-        const int dg = e / NB, t = e % NB;    // diagonal index c = K + i - j, position in panel
-        int i, j;
-        if (dg <= K) { i = k0 + t; j = i + (K - dg); }     // U(i, j), j - i = K - dg
-        else { j = k0 + t; i = j + (dg - K); }             // L(i, j), i - j = dg - K
-        if (i >= n || j >= n) continue;
-        const T v = W[w.ph(i - k0) * LDW + w.ph(j - k0)];
-        if (!REV) {
-          F[(int64_t)dg * ld + j] = v;
-        } else {
-          // keep the last K rows/cols of L~ and U~ of J A J, flipped:
-          // U'(n-1-i, n-1-k) = L~(i, k), L'(n-1-k, n-1-j) = U~(k, j)
-          const int kk = (dg <= K) ? i : j;
-          if (kk >= n - K) F[(int64_t)(n - 1 - i) * K + (n - 1 - j)] = v;
+      constexpr int U = 4;
+      const int tot = NB * (2 * K + 1);
+      for (int e0 = tid; e0 < tot; e0 += U * NTH) {
+        T v[U];
+        int64_t dst[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int e = e0 + u * NTH;
+          dst[u] = -1;
+          if (e >= tot) continue;
+          const int dg = e / NB, t = e % NB;    // diagonal index c = K + i - j, position in panel
+          int i, j;
+          if (dg <= K) { i = k0 + t; j = i + (K - dg); }     // U(i, j), j - i = K - dg
+          else { j = k0 + t; i = j + (dg - K); }             // L(i, j), i - j = dg - K
+          if (i >= n || j >= n) continue;
+          if (!REV) {
+            dst[u] = (int64_t)dg * ld + j;
+          } else {
+            // keep the last K rows/cols of L~ and U~ of J A J, flipped:
+            // U'(n-1-i, n-1-k) = L~(i, k), L'(n-1-k, n-1-j) = U~(k, j)
+            const int kk = (dg <= K) ? i : j;
+            if (kk < n - K) continue;
+            dst[u] = (int64_t)(n - 1 - i) * K + (n - 1 - j);
+          }
+          v[u] = W[w.ph(i - k0) * LDW + w.ph(j - k0)];
         }
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+          if (dst[u] >= 0) F[dst[u]] = v[u];
       }
     };
     // ---- C: A22 -= L21 U12 over window rows/cols [NB, NB + K) ----
@@ -378,34 +425,51 @@ __device__ void band_lu_block(unsigned char* smem_raw, const T* __restrict__ ban
       }
     } else
     {
-      const int nt = (K + 3) / 4;
-      for (int t = tid; t < nt * nt; t += NTH) {
+      // TR x 4 tiles of trailing entries per thread (rows / columns in
+      // 4-aligned groups up to 4 nt >= K).  In the global window FP32 takes
+      // 8-row tiles: the L1 wavefronts per update (operand rows of L21 are
+      // warp-broadcast, U12 columns and the trailing entries per lane) are
+      // what bounds it, and a taller tile reuses each U12 load twice.
+      constexpr int TR = (GW && sizeof(T) == 4) ? 8 : 4;
+      const int nt = (K + 3) / 4, rl = 4 * nt, nr = (rl + TR - 1) / TR;
+      for (int t = tid; t < nr * nt; t += NTH) {
         const int ti = t / nt, tj = t % nt;
-        const int r0 = w.ph(NB + 4 * ti), c0 = w.ph(NB + 4 * tj);   // 4-groups never wrap
-        T acc[4][4];
+        const int r0 = w.ph(NB + TR * ti), c0 = w.ph(NB + 4 * tj);   // TR- and 4-groups never wrap
+        // the tile's trailing entries are loaded first, so that their L2
+        // latency hides behind the products (rows past 4 nt, read in the last
+        // 8-row tile, lie inside the window and are not written back)
+        T v[TR][4], acc[TR][4];
+        if constexpr (GW) {
 #pragma unroll
-        for (int x = 0; x < 4; ++x)
+          for (int x = 0; x < TR; ++x) ld4_cg(&W[(r0 + x) * LDW + c0], v[x]);
+        }
+#pragma unroll
+        for (int x = 0; x < TR; ++x)
 #pragma unroll
           for (int y = 0; y < 4; ++y) acc[x][y] = T(0);
 #pragma unroll
         for (int q4 = 0; q4 < NB / 4; ++q4) {
-          T a[4][4], bq[4][4];
-#pragma unroll
-          for (int x = 0; x < 4; ++x) ld4(&W[(r0 + x) * LDW + base + 4 * q4], a[x]);
+          T bq[4][4];
 #pragma unroll
           for (int qq = 0; qq < 4; ++qq) ld4(&W[(base + 4 * q4 + qq) * LDW + c0], bq[qq]);
 #pragma unroll
-          for (int qq = 0; qq < 4; ++qq)
+          for (int x = 0; x < TR; ++x) {
+            T a[4];
+            ld4(&W[(r0 + x) * LDW + base + 4 * q4], a);
 #pragma unroll
-            for (int x = 0; x < 4; ++x)
+            for (int qq = 0; qq < 4; ++qq)
 #pragma unroll
-              for (int y = 0; y < 4; ++y) acc[x][y] += a[x][qq] * bq[qq][y];
+              for (int y = 0; y < 4; ++y) acc[x][y] += a[qq] * bq[qq][y];
+          }
         }
 #pragma unroll
-        for (int x = 0; x < 4; ++x) {
+        for (int x = 0; x < TR; ++x) {
+          if (TR * ti + x >= rl) break;     // rows past 4 nt: only in the last 8-row tile
           T* row = &W[(r0 + x) * LDW + c0];
+          if constexpr (!GW) ld4(row, v[x]);
 #pragma unroll
-          for (int y = 0; y < 4; ++y) row[y] -= acc[x][y];
+          for (int y = 0; y < 4; ++y) v[x][y] -= acc[x][y];
+          if constexpr (GW) st4_cg(row, v[x]); else st4(row, v[x]);
         }
       }
     }

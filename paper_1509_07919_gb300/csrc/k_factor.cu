@@ -220,76 +220,94 @@ __device__ void band_lu_block(unsigned char* smem_raw, const T* __restrict__ ban
   }
   __syncthreads();
 
-  for (int k0 = 0; k0 < n; k0 += NB) {
-    const int base = w.base;     // physical column of the panel start (multiple of NB)
-    // ---- A1: LU of the NB x NB diagonal block (warp 0) || prefetch (warps 1..7) ----
-    if (warp == 0) {
-      T pv[NB];
-      if (lane < NB) {
-        const T* row = &W[(base + lane) * LDW + base];
+  // A1: LU of the NB x NB diagonal block at physical rows / columns pb ..
+  // pb + NB - 1 of the panel that starts at block row pk0 (warp 0): pivot row
+  // by shuffles, boosted pivot, multipliers; the reciprocals of the pivots go
+  // to RV.
+  auto factor_diag = [&](int pb, int pk0) {
+    T pv[NB];
+    if (lane < NB) {
+      const T* row = &W[(pb + lane) * LDW + pb];
 #pragma unroll
-        for (int c4 = 0; c4 < NB / 4; ++c4) {
-          T v[4];
-          ld4(row + 4 * c4, v);
+      for (int c4 = 0; c4 < NB / 4; ++c4) {
+        T v[4];
+        ld4(row + 4 * c4, v);
 #pragma unroll
-          for (int x = 0; x < 4; ++x) pv[4 * c4 + x] = v[x];
-        }
-      } else {
-#pragma unroll
-        for (int c = 0; c < NB; ++c) pv[c] = T(0);
-      }
-      T myrinv = T(0);
-#pragma unroll
-      for (int j = 0; j < NB; ++j) {
-        T u[NB];
-#pragma unroll
-        for (int c = j; c < NB; ++c) u[c] = __shfl_sync(0xffffffffu, pv[c], j);
-        T p = u[j];
-        if (k0 + j < n) {
-          if ((p < T(0) ? -p : p) < tau) {
-            p = p >= T(0) ? tau : -tau;
-            ++nb;
-          }
-        } else {
-          p = T(1);   // padding past the block: rows there are all zero
-        }
-        const T rinv = rcp(p);
-        if (lane > j) {
-          const T l = pv[j] * rinv;
-          pv[j] = l;
-#pragma unroll
-          for (int c = j + 1; c < NB; ++c) pv[c] -= l * u[c];
-        } else if (lane == j) {
-          pv[j] = p;
-          myrinv = rinv;
-        }
-      }
-      if (lane < NB) {
-        T* row = &W[(base + lane) * LDW + base];
-#pragma unroll
-        for (int c4 = 0; c4 < NB / 4; ++c4) st4(row + 4 * c4, {pv[4 * c4], pv[4 * c4 + 1], pv[4 * c4 + 2], pv[4 * c4 + 3]});
-        RV[lane] = myrinv;
+        for (int x = 0; x < 4; ++x) pv[4 * c4 + x] = v[x];
       }
     } else {
-      // entering rows i = k0 + M2 + e (columns of the next window, offsets jo from k0 + NB)
-      // and entering columns j = k0 + M2 + e for resident rows i = k0 + NB + ro (ro < ME)
-      const int hw = warp - 1, ht = tid - 32, nh = NTH - 32;
-      for (int e = hw; e < NB; e += NTH / 32 - 1)
-        for (int jo = lane; jo < M2; jo += 32) {
-          T* dst = &ER[e * M2 + jo];
-          const T* src = elem_ptr<REV>(band, N, K, s, n, k0 + M2 + e, k0 + NB + jo);
-          if (src) cp_async_t(dst, src);
-          else *dst = T(0);
-        }
-      for (int y = ht; y < ME * NB; y += nh) {
-        const int ro = y / NB, e = y % NB;
-        T* dst = &EC[y];
-        const T* src = elem_ptr<REV>(band, N, K, s, n, k0 + NB + ro, k0 + M2 + e);
-        if (src) cp_async_t(dst, src);
-        else *dst = T(0);
-      }
-      cp_async_commit();
+#pragma unroll
+      for (int c = 0; c < NB; ++c) pv[c] = T(0);
     }
+    T myrinv = T(0);
+#pragma unroll
+    for (int j = 0; j < NB; ++j) {
+      T u[NB];
+#pragma unroll
+      for (int c = j; c < NB; ++c) u[c] = __shfl_sync(0xffffffffu, pv[c], j);
+      T p = u[j];
+      if (pk0 + j < n) {
+        if ((p < T(0) ? -p : p) < tau) {
+          p = p >= T(0) ? tau : -tau;
+          ++nb;
+        }
+      } else {
+        p = T(1);   // padding past the block: rows there are all zero
+      }
+      const T rinv = rcp(p);
+      if (lane > j) {
+        const T l = pv[j] * rinv;
+        pv[j] = l;
+#pragma unroll
+        for (int c = j + 1; c < NB; ++c) pv[c] -= l * u[c];
+      } else if (lane == j) {
+        pv[j] = p;
+        myrinv = rinv;
+      }
+    }
+    if (lane < NB) {
+      T* row = &W[(pb + lane) * LDW + pb];
+#pragma unroll
+      for (int c4 = 0; c4 < NB / 4; ++c4) st4(row + 4 * c4, {pv[4 * c4], pv[4 * c4 + 1], pv[4 * c4 + 2], pv[4 * c4 + 3]});
+      RV[lane] = myrinv;
+    }
+  };
+  // Prefetch of the rows and columns that enter the window when it slides
+  // after the panel at k0 (warps 1..): cp.async into ER / EC.  The band is
+  // stored by diagonals, so a matrix row or column is strided by N in memory;
+  // the entries are enumerated as (jj, e), e fastest, with offset jo = jj + e
+  // (mod M2, resp. ME): for one jj and consecutive e the diagonal is the same
+  // and the band addresses are consecutive (16 entries, 64 bytes per half
+  // warp) instead of one sector per entry.
+  auto prefetch = [&](int k0) {
+    const int ht = tid - 32, nh = NTH - 32;
+    // entering rows i = k0 + M2 + e (columns of the next window, offsets jo from k0 + NB)
+    for (int y = ht; y < NB * M2; y += nh) {
+      const int e = y % NB, jj = y / NB;
+      int jo = jj + e;
+      if (jo >= M2) jo -= M2;
+      T* dst = &ER[e * M2 + jo];
+      const T* src = elem_ptr<REV>(band, N, K, s, n, k0 + M2 + e, k0 + NB + jo);
+      if (src) cp_async_t(dst, src);
+      else *dst = T(0);
+    }
+    // entering columns j = k0 + M2 + e for resident rows i = k0 + NB + ro (ro < ME)
+    for (int y = ht; y < ME * NB; y += nh) {
+      const int e = y % NB, jj = y / NB;
+      int ro = jj + e;
+      if (ro >= ME) ro -= ME;
+      T* dst = &EC[ro * NB + e];
+      const T* src = elem_ptr<REV>(band, N, K, s, n, k0 + NB + ro, k0 + M2 + e);
+      if (src) cp_async_t(dst, src);
+      else *dst = T(0);
+    }
+    cp_async_commit();
+  };
+  for (int k0 = 0; k0 < n; k0 += NB) {
+    const int base = w.base;     // physical column of the panel start (multiple of NB)
+    // ---- A1 (warp 0) || prefetch (warps 1..) ----
+    if (warp == 0) factor_diag(base, k0);
+    else prefetch(k0);
     __syncthreads();
 
     // ---- A2: L21 = A21 U11^{-1} (rows NB..KA-1, threads 0..127) ||
@@ -337,15 +355,15 @@ __device__ void band_lu_block(unsigned char* smem_raw, const T* __restrict__ ban
     // ---- D1: write the finished panel (U rows k0.., L columns k0..) ----
     // Four entries per thread are read before any is stored, so that the
     // window reads overlap (each entry is written once, to its own place).
-    auto write_panel = [&]() {
+    auto write_panel = [&](int t0, int nthr) {
       constexpr int U = 4;
       const int tot = NB * (2 * K + 1);
-      for (int e0 = tid; e0 < tot; e0 += U * NTH) {
+      for (int e0 = t0; e0 < tot; e0 += U * nthr) {
         T v[U];
         int64_t dst[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-          const int e = e0 + u * NTH;
+          const int e = e0 + u * nthr;
           dst[u] = -1;
           if (e >= tot) continue;
           const int dg = e / NB, t = e % NB;    // diagonal index c = K + i - j, position in panel
@@ -397,7 +415,7 @@ __device__ void band_lu_block(unsigned char* smem_raw, const T* __restrict__ ban
           }
           tc::mma_commit(tcx.bar);
         }
-        if (g0 == 0) write_panel();      // overlaps the MMAs (it reads only the panel's rows / columns)
+        if (g0 == 0) write_panel(tid, NTH);   // overlaps the MMAs (it reads only the panel's rows / columns)
         tc::mbar_wait_bounded(tcx.bar, tcx.ph, 1 << 22, tcx.err, tcx.failed);
         tcx.ph ^= 1u;
         tc::fence_after_sync();
@@ -473,7 +491,7 @@ __device__ void band_lu_block(unsigned char* smem_raw, const T* __restrict__ ban
         }
       }
     }
-    if constexpr (!TC) write_panel();
+    if constexpr (!TC) write_panel(tid, NTH);
     if (warp > 0) cp_async_wait_all();
     __syncthreads();
     // ---- D2: slide the window by NB: entering rows/cols replace the panel's ----

@@ -54,6 +54,8 @@ def _load():
         lib.orc_apply.argtypes = [vp, P(dbl), P(dbl)]
         lib.orc_bicgstab2.argtypes = [vp, P(dbl), P(dbl), P(dbl), dbl, C.c_int, vp, P(dbl), C.c_int]
         lib.orc_bicgstab2.restype = C.c_int
+        lib.orc_pcg.argtypes = [vp, P(dbl), P(dbl), P(dbl), dbl, C.c_int, vp, P(dbl), C.c_int]
+        lib.orc_pcg.restype = C.c_int
         lib.orc_transpose_band.argtypes = [P(dbl), i64, C.c_int, P(dbl)]
         lib.orc_grad_band.argtypes = [i64, C.c_int, P(dbl), P(dbl), P(dbl)]
         lib.orc_n_boosted.argtypes = [vp]
@@ -231,6 +233,32 @@ class Sap:
             t = tr.reshape(-1, 4)
             t = t[t[:, 0] > 0]
         return x, SolveInfo(st, info.iters, info.relres, info.n_matvec, info.n_restarts, t)
+
+    def solve_cg(self, b: np.ndarray, tol: float = 1e-10, max_iters: int = 500,
+                 trace: bool = False) -> tuple[np.ndarray, SolveInfo]:
+        """Preconditioned conjugate gradient for an SPD A (Section 3), M the
+        SaP factorisation; iterations are whole CG steps.  trace rows:
+        (iteration, ||r||, (r, z) before the step, true relres or -1)."""
+        b = np.ascontiguousarray(b, dtype=np.float64)
+        x = np.empty(self.N)
+        info = _Info()
+        cap = max_iters + 2
+        tr = np.zeros(4 * cap) if trace else None
+        st = _load().orc_pcg(self._h, _d(self.band), _d(b), _d(x), tol, max_iters,
+                             C.byref(info), _d(tr) if trace else None, cap)
+        t = None
+        if trace:
+            t = tr.reshape(-1, 4)
+            t = t[t[:, 0] > 0]
+        return x, SolveInfo(st, info.iters, info.relres, info.n_matvec, info.n_restarts, t)
+
+
+def solve_cg(band, N, K, b, P, variant=SAP_D, tol=1e-10, max_iters=500, **kw):
+    """Factor and solve the SPD system A x = b by preconditioned CG; returns
+    (x, info, sap)."""
+    s = Sap(band, N, K, P, variant, **kw)
+    x, info = s.solve_cg(b, tol=tol, max_iters=max_iters)
+    return x, info, s
 
 
 def solve(band, N, K, b, P, variant=SAP_D, tol=1e-10, max_iters=500, **kw):

@@ -585,6 +585,107 @@ done:
 }
 
 /* ------------------------------------------------------------------ */
+/* conjugate gradient (symmetric positive definite A)                   */
+/* ------------------------------------------------------------------ */
+
+/* Section 3: when A is symmetric positive definite the outer iteration is a
+ * conjugate gradient method instead of BiCGStab(2), preconditioned by the
+ * SaP factorisation (Section 4.1 lists both methods).  The iteration is the
+ * preconditioned CG of Saad, "Iterative methods for sparse linear systems",
+ * 2nd ed., Algorithm 9.1, from x_0 = 0:
+ *   r_0 = b,  z_0 = M^{-1} r_0,  p_0 = z_0;  per iteration j:
+ *   alpha_j = (r_j, z_j) / (A p_j, p_j)
+ *   x_{j+1} = x_j + alpha_j p_j,   r_{j+1} = r_j - alpha_j A p_j
+ *   z_{j+1} = M^{-1} r_{j+1}
+ *   beta_j  = (r_{j+1}, z_{j+1}) / (r_j, z_j),   p_{j+1} = z_{j+1} + beta_j p_j
+ * One matrix-vector product and one preconditioner application per
+ * iteration; the count is in whole iterations.  Readings (the paper gives
+ * none for CG): the exit test is the unpreconditioned recursive residual,
+ * ||r_{j+1}||_2 <= tol ||b||_2, confirmed by the true residual
+ * ||b - A x||_2 <= tol ||b||_2; a failed confirmation restarts the method
+ * from the current x with the true residual (r = b - A x, z = M^{-1} r,
+ * p = z), as the BiCGStab(2) restart does.  SaP-D's M (the block diagonal of
+ * an SPD A) is SPD; SaP-C's truncated-spike M need not be symmetric, and CG
+ * then runs with it as it stands.
+ *
+ * trace (optional, may be NULL): per iteration 4 doubles: iteration number
+ * j + 1, ||r_{j+1}||_2, (r_j, z_j), true relative residual (-1 when the
+ * recursive test did not pass). */
+int orc_pcg(const orc_sap *h, const double *band, const double *b, double *x,
+            double tol, int max_iters, orc_info *info, double *trace, int trace_cap)
+{
+    int64_t N = h->N;
+    double *buf = (double *)xcalloc((size_t)N * 4, sizeof(double));
+    if (!buf) return ORC_ERR_OOM;
+    double *r = buf, *z = buf + N, *p = buf + 2 * N, *q = buf + 3 * N;
+    int status = ORC_ERR_NOT_CONVERGED;
+    int ntrace = 0;
+    memset(x, 0, (size_t)N * sizeof(double));
+    info->iters = 0; info->relres = 1.0; info->n_matvec = 0; info->n_restarts = 0;
+    double bnorm = sqrt(dot(b, b, N));
+    if (bnorm == 0.0) { info->relres = 0.0; free(buf); return ORC_OK; }
+    memcpy(r, b, (size_t)N * sizeof(double));      /* r_0 = b - A x_0, x_0 = 0 */
+    orc_apply(h, r, z);
+    memcpy(p, z, (size_t)N * sizeof(double));
+    double rz = dot(r, z, N);
+    int64_t nmv = 0;
+
+    for (int it = 0; it < max_iters; ++it) {
+        orc_spmv(band, N, h->K, p, q, 0); ++nmv;     /* q = A p_j */
+        double pq = dot(p, q, N);
+        if (pq == 0.0) { status = ORC_ERR_BREAKDOWN; goto done; }
+        double alpha = rz / pq;
+        for (int64_t k = 0; k < N; ++k) {
+            x[k] += alpha * p[k];
+            r[k] -= alpha * q[k];
+        }
+        info->iters = it + 1.0;
+        double rn = sqrt(dot(r, r, N));
+        double rel = -1.0;
+        int restarted = 0;
+        if (rn <= tol * bnorm) {
+            orc_spmv(band, N, h->K, x, q, 0);
+            for (int64_t k = 0; k < N; ++k) q[k] = b[k] - q[k];
+            rel = sqrt(dot(q, q, N)) / bnorm;
+            if (rel <= tol) {
+                if (trace && ntrace < trace_cap) {
+                    double *t = trace + 4 * ntrace++;
+                    t[0] = it + 1.0; t[1] = rn; t[2] = rz; t[3] = rel;
+                }
+                info->relres = rel;
+                status = ORC_OK; goto done;
+            }
+            memcpy(r, q, (size_t)N * sizeof(double));   /* restart from the current x */
+            ++info->n_restarts;
+            restarted = 1;
+        }
+        if (trace && ntrace < trace_cap) {
+            double *t = trace + 4 * ntrace++;
+            t[0] = it + 1.0; t[1] = rn; t[2] = rz; t[3] = rel;
+        }
+        orc_apply(h, r, z);                          /* z_{j+1} = M^{-1} r_{j+1} */
+        double rz1 = dot(r, z, N);
+        if (restarted) {
+            memcpy(p, z, (size_t)N * sizeof(double));
+        } else {
+            if (rz == 0.0) { status = ORC_ERR_BREAKDOWN; goto done; }
+            double beta = rz1 / rz;
+            for (int64_t k = 0; k < N; ++k) p[k] = z[k] + beta * p[k];
+        }
+        rz = rz1;
+    }
+done:
+    info->n_matvec = nmv;
+    if (status != ORC_OK) {
+        orc_spmv(band, N, h->K, x, q, 0);
+        for (int64_t k = 0; k < N; ++k) q[k] = b[k] - q[k];
+        info->relres = sqrt(dot(q, q, N)) / bnorm;
+    }
+    free(buf);
+    return status;
+}
+
+/* ------------------------------------------------------------------ */
 /* adjoint                                                              */
 /* ------------------------------------------------------------------ */
 

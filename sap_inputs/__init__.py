@@ -26,7 +26,7 @@ from dataclasses import dataclass
 import numpy as np
 
 __all__ = [
-    "uniform", "dense_banded", "x_true", "adjoint_seed", "convection_diffusion",
+    "uniform", "dense_banded", "dense_banded_spd", "x_true", "adjoint_seed", "convection_diffusion",
     "batch_specs", "CONFIG_SEED_BASE", "config_seed", "BandedSystem",
 ]
 
@@ -95,6 +95,35 @@ def dense_banded(N: int, K: int, d: float, seed: int) -> np.ndarray:
     band[~_valid_mask(N, K)] = 0.0
     band[K, :] = 0.0
     # row abs-sums: entry band[c, j] belongs to row i = j + c - K
+    rowsum = np.zeros(N)
+    for c in range(W):
+        if c == K:
+            continue
+        lo = max(0, K - c)
+        hi = min(N, N + K - c)
+        rowsum[lo + c - K: hi + c - K] += np.abs(band[c, lo:hi])
+    band[K, :] = d * rowsum
+    return band.reshape(-1)
+
+
+def dense_banded_spd(N: int, K: int, d: float, seed: int) -> np.ndarray:
+    """Random symmetric dense band: the strictly lower in-band entries
+    a_ij (i > j) ~ U(-1, 1), mirrored a_ji = a_ij, and a_ii = d * sum_{j != i}
+    |a_ij|.  With d > 1 the matrix is strictly diagonally dominant with a
+    positive diagonal, hence symmetric positive definite (Gershgorin), the case
+    in which the outer iteration is a conjugate gradient method (Section 3).
+    Returns the band as a flat float64 array of (2K+1)*N."""
+    if K < 1 or N < 1:
+        raise ValueError("need N >= 1 and K >= 1")
+    W = 2 * K + 1
+    band = uniform(seed, 0, W * N).reshape(W, N)
+    band[~_valid_mask(N, K)] = 0.0
+    band[: K + 1, :] = 0.0
+    # a_ij with i > j sits at band[c, j], c = K + i - j > K; its mirror a_ji at
+    # band[2K - c, i], i = j + c - K
+    for c in range(K + 1, W):
+        lo, hi = 0, N - (c - K)
+        band[W - 1 - c, lo + c - K: hi + c - K] = band[c, lo:hi]
     rowsum = np.zeros(N)
     for c in range(W):
         if c == K:

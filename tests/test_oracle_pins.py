@@ -550,3 +550,115 @@ def test_bf16_trailing_update_error_is_at_bf16_level():
     U = np.triu(F)
     rel = np.linalg.norm(L @ U - A) / np.linalg.norm(A)
     assert 1e-5 < rel < 1e-2, rel
+
+
+# ------------------------------------------------- conjugate gradient ---
+# Section 3: for a symmetric positive definite A the outer iteration is CG,
+# preconditioned by the SaP factorisation (Saad, Algorithm 9.1).
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+def test_spd_generator_is_symmetric_positive_definite():
+    N, K, d = 120, 5, 1.05
+    band = G.dense_banded_spd(N, K, d, 61)
+    A = band_to_dense(band, N, K)
+    assert np.array_equal(A, A.T)
+    off = np.abs(A).sum(1) - np.abs(np.diag(A))
+    np.testing.assert_allclose(np.diag(A), d * off, rtol=1e-14)
+    assert np.linalg.eigvalsh(A).min() > 0
+    np.testing.assert_array_equal(band, G.dense_banded_spd(N, K, d, 61))
+
+
+def test_pcg_exact_preconditioner_converges_in_one_step():
+    """P = 1: M = A, so z_0 = A^{-1} b, alpha_0 = (b, A^{-1} b) / (A^{-1} b, b) = 1 and
+    x_1 = A^{-1} b."""
+    N, K = 300, 4
+    band = G.dense_banded_spd(N, K, 1.1, 62)
+    b = O.spmv(band, N, K, G.x_true(N, 62))
+    x, info = O.Sap(band, N, K, 1, O.SAP_D).solve_cg(b)
+    assert info.status == O.OK and info.iters == 1 and info.n_matvec == 1
+    xd = np.linalg.solve(band_to_dense(band, N, K), b)
+    assert _rel(x, xd) <= 1e-12
+
+
+@pytest.mark.parametrize("N,K,P", [(60, 2, 3), (96, 3, 4)])
+def test_pcg_finite_termination_block_jacobi(N, K, P):
+    """SaP-D: M = blockdiag(A_i) and A - M is the coupling (two K x K blocks per interface),
+    so M^{-1} A = I + (rank <= 2K(P-1)) has at most m = 2K(P-1)+1 distinct eigenvalues and
+    CG, in exact arithmetic, ends within m steps; half as many do not suffice here."""
+    band = G.dense_banded_spd(N, K, 1.0, 63 + N)
+    b = O.spmv(band, N, K, G.x_true(N, 63))
+    s = O.Sap(band, N, K, P, O.SAP_D)
+    m = 2 * K * (P - 1) + 1
+    _, full = s.solve_cg(b, tol=0.0, max_iters=m)
+    _, half = s.solve_cg(b, tol=0.0, max_iters=m // 2)
+    assert full.relres <= 1e-12, full.relres
+    assert half.relres >= 1e-6, half.relres
+
+
+@pytest.mark.parametrize("N,var,steps", [(400, O.SAP_D, (1, 2, 4, 7)), (48, O.SAP_C, (1, 2, 3))])
+def test_pcg_iterates_match_scipy_cg(N, var, steps):
+    """SciPy's independent preconditioned CG, given the oracle's M^{-1} as its preconditioner,
+    produces the same iterate after every step count (SaP-C on short blocks, 12 = 2K rows,
+    where its truncated spikes leave something to iterate on)."""
+    from scipy.sparse.linalg import LinearOperator, cg
+    K, P = 6, 4
+    band = G.dense_banded_spd(N, K, 1.0, 64)
+    A = band_to_dense(band, N, K)
+    b = O.spmv(band, N, K, G.x_true(N, 64))
+    s = O.Sap(band, N, K, P, var)
+    Minv = LinearOperator((N, N), matvec=s.apply, dtype=np.float64)
+    for k in steps:
+        x, info = s.solve_cg(b, tol=0.0, max_iters=k)
+        assert info.iters == k and info.n_matvec == k
+        xs, _ = cg(A, b, x0=np.zeros(N), rtol=0.0, atol=0.0, maxiter=k, M=Minv)
+        assert _rel(x, xs) <= 1e-11, (k, _rel(x, xs))
+        assert info.relres > 1e-13          # still iterating: a meaningful comparison
+
+
+@pytest.mark.parametrize("var", [O.SAP_D, O.SAP_C])
+def test_pcg_solution_matches_cholesky_solve(var):
+    N, K, P = 2000, 8, 5
+    band = G.dense_banded_spd(N, K, 1.0, 65)
+    xt = G.x_true(N, 65)
+    b = O.spmv(band, N, K, xt)
+    x, info, _ = O.solve_cg(band, N, K, b, P, var)
+    assert info.status == O.OK and info.relres <= 1e-10
+    xd = sla.solve(band_to_dense(band, N, K), b, assume_a="pos")
+    assert _rel(x, xd) <= 1e-9
+    xb, ib, _ = O.solve(band, N, K, b, P, var)
+    assert _rel(x, xb) <= 1e-9
+
+
+def test_pcg_recursive_residual_and_restart():
+    """The recursive residual r_j = b - A x_j (unpreconditioned) matches the true residual
+    where the exit test passes; asking for less than rounding allows makes the confirmation
+    fail, which restarts the method from the true residual without losing accuracy."""
+    N, K, P = 1500, 6, 6
+    band = G.dense_banded_spd(N, K, 1.0, 66)
+    b = O.spmv(band, N, K, G.x_true(N, 66))
+    s = O.Sap(band, N, K, P, O.SAP_D)
+    x, info = s.solve_cg(b, tol=1e-10, trace=True)
+    t = info.trace
+    assert info.status == O.OK and t[-1, 3] >= 0
+    bn = np.linalg.norm(b)
+    assert abs(t[-1, 1] / bn - t[-1, 3]) <= 1e-3 * t[-1, 3] + 1e-15
+    np.testing.assert_array_equal(t[:, 0], np.arange(1, len(t) + 1))
+    _, tight = s.solve_cg(b, tol=1e-18, max_iters=120, trace=True)
+    assert tight.status == O.NOT_CONVERGED and tight.n_restarts >= 1
+    assert tight.relres <= 1e-14
+    # the step after the first restart is a fresh CG step from the true residual
+    # r = b - A x (p = z = M^{-1} r): recompute (r, z) and ||r - alpha A z|| from x
+    t = tight.trace
+    row = int(np.nonzero(t[:, 3] >= 0)[0][0])
+    assert row + 1 < len(t)
+    xj, _ = s.solve_cg(b, tol=1e-18, max_iters=int(t[row, 0]))
+    r = b - O.spmv(band, N, K, xj)
+    z = s.apply(r)
+    q = O.spmv(band, N, K, z)
+    rz = float(r @ z)
+    rn = np.linalg.norm(r - rz / float(z @ q) * q)
+    assert abs(t[row + 1, 2] - rz) <= 1e-8 * abs(rz)
+    assert abs(t[row + 1, 1] - rn) <= 1e-6 * rn

@@ -37,7 +37,6 @@ namespace sap {
 namespace {
 
 constexpr int NB = 16;             // panel width
-constexpr int NTHREADS = 256;
 // 512 threads for the global-memory window (its L2-resident read-modify-write
 // of the trailing matrix wants more loads in flight), 256 otherwise
 __host__ __device__ constexpr int lu_threads(bool gw, bool tc) { return gw && !tc ? 512 : 256; }

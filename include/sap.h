@@ -298,6 +298,16 @@ SAP_API int32_t sap_batch_size(sap_batch_t b);
 SAP_API int32_t sap_batch_partitions(sap_batch_t b, int32_t i);
 SAP_API sap_status_t sap_batch_destroy(sap_batch_t b);
 
+/* Failure-detection self-test (not in the paper; the device-side waits of
+ * this library are bounded): launches one CTA whose thread waits, with the
+ * same bounded mbarrier wait the sweep and factor kernels use, on a barrier
+ * that nothing completes, polling `spin_limit` times.  Returns
+ * SAP_ERR_TIMEOUT when the wait gave up and reported it (the expected
+ * outcome; the CUDA context stays usable), SAP_OK if the wait completed (a
+ * defect), INVALID_ARG for spin_limit < 1, OOM, CUDA.  Synchronises
+ * `stream`; allocates and frees one device int. */
+SAP_API sap_status_t sap_selftest_wait_timeout(int32_t spin_limit, cudaStream_t stream);
+
 /* Number of CUDA kernels this library has launched in this process so far
  * (host-side counter, all handles and threads). */
 SAP_API int64_t sap_kernel_launches(void);

@@ -73,6 +73,7 @@ def _load():
         "sap_status_string": (C.c_char_p, [C.c_int]),
         "sap_max_K": (i32, [i32]),
         "sap_kernel_launches": (i64, []),
+        "sap_selftest_wait_timeout": (C.c_int, [i32, vp]),
         "sap_band_solve_noalloc": (C.c_int, [vp, i64, i32, vp, vp, i32, vp]),
         "sap_factor_batched": (C.c_int, [i32, vp, vp, vp, P(sap_options_t), vp, P(vp)]),
         "sap_autotune": (C.c_int, [vp, i64, i32, P(sap_options_t), vp, i32, vp, i32, vp, vp,
@@ -377,6 +378,12 @@ def sap_batch_partitions(bh: BatchHandle):
 def sap_kernel_launches() -> int:
     """Kernels launched by libsap in this process so far."""
     return int(_lib.sap_kernel_launches())
+
+
+def sap_selftest_wait_timeout(spin_limit: int = 1000, stream=None) -> int:
+    """Failure-detection self-test: one bounded device wait on a barrier that
+    nothing completes; returns the status (SAP_ERR_TIMEOUT expected)."""
+    return int(_lib.sap_selftest_wait_timeout(int(spin_limit), _stream(stream)))
 
 
 def sap_n_boosted(h: Handle) -> int:

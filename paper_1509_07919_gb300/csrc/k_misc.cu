@@ -10,6 +10,7 @@
 #include <cstdint>
 #include "sap_internal.cuh"
 #include "krylov.cuh"
+#include "tc_sm103.cuh"
 
 namespace sap {
 
@@ -494,6 +495,28 @@ cudaError_t kr_mr(double* x, double* r0, double* r1, double* r2, double* u0, con
   k_mr2<<<g, RT, 0, s>>>(r0, r1, r2, n, kd);
   count_launches(1);
   k_mr3<<<g, RT, 0, s>>>(x, r0, r1, r2, u0, u1, u2, n, kd);
+  return cudaGetLastError();
+}
+
+// ---- failure-detection self-test ----
+// One thread waits, with the bounded mbarrier wait of the library's kernels,
+// on a barrier whose phase nothing completes (no arrival, no copy in flight);
+// after `limit` polls the wait records the timeout in *err and the kernel
+// ends normally, leaving the context usable.
+__global__ void k_wait_selftest(int limit, int* err) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    tc::mbar_init(&bar, 1);
+    tc::mbar_fence_init();
+  }
+  __syncthreads();
+  bool failed = false;
+  if (threadIdx.x == 0) tc::mbar_wait_bounded(&bar, 0u, limit, err, failed);
+}
+
+cudaError_t launch_wait_selftest(int limit, int* err, cudaStream_t s) {
+  count_launches(1);
+  k_wait_selftest<<<1, 32, 0, s>>>(limit, err);
   return cudaGetLastError();
 }
 

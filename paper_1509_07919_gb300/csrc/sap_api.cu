@@ -1258,6 +1258,25 @@ sap_status_t sap_spmv(const double* band, int64_t N, int32_t K, const double* x,
   return SAP_OK;
 }
 
+sap_status_t sap_selftest_wait_timeout(int32_t spin_limit, cudaStream_t s) {
+  if (spin_limit < 1) return SAP_ERR_INVALID_ARG;
+  int* err = nullptr;
+  if (cudaMalloc(&err, sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    return SAP_ERR_OOM;
+  }
+  int e = 0;
+  sap_status_t st = SAP_OK;
+  if (cudaMemsetAsync(err, 0, sizeof(int), s) != cudaSuccess ||
+      launch_wait_selftest(spin_limit, err, s) != cudaSuccess ||
+      cudaMemcpyAsync(&e, err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    st = SAP_ERR_CUDA;
+  cudaFree(err);
+  if (st != SAP_OK) return st;
+  return e ? SAP_ERR_TIMEOUT : SAP_OK;
+}
+
 sap_status_t sap_get_partition(sap_handle_t h, int64_t* off) {
   if (!h || !off) return SAP_ERR_INVALID_ARG;
   std::memcpy(off, h->L.off.data(), (h->L.P + 1) * sizeof(int64_t));

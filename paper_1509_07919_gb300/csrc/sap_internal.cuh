@@ -104,6 +104,8 @@ __device__ __forceinline__ bool gate_skip(const Gate& g) {
 
 // Host-side count of kernel launches issued by the library (for reporting).
 void count_launches(int n);
+// one bounded wait on a barrier nothing completes (sets *err after `limit` polls)
+cudaError_t launch_wait_selftest(int limit, int* err, cudaStream_t s);
 long long launches_so_far();
 
 // ---- launchers (each returns cudaGetLastError()) ----

@@ -299,6 +299,20 @@ def test_not_converged_status(sap):
         assert info.relres > 1e-10
 
 
+def test_bounded_wait_reports_timeout_and_context_survives(sap):
+    """Failure detection without a GPU fault: a device wait on a barrier that
+    nothing completes gives up after its poll limit and the call reports
+    SAP_ERR_TIMEOUT; a solve afterwards still works (the context is intact)."""
+    assert sap.sap_selftest_wait_timeout(1000) == sap.SAP_ERR_TIMEOUT
+    assert sap.sap_selftest_wait_timeout(0) == sap.SAP_ERR_INVALID_ARG
+    N, K, P = 3000, 6, 3
+    band, xt, b = make(N, K, 1.0, 905)
+    h = sap.sap_factor(dev(band), N, K, P=P, variant=sap.SAP_D, precision=sap.SAP_FP32)
+    x, info, st = sap.sap_solve(h, dev(b))
+    assert st == sap.SAP_OK and info.relres <= 1e-10
+    assert np.linalg.norm(host(x) - xt) / np.linalg.norm(xt) <= 1e-8
+
+
 @pytest.mark.parametrize("N,K,P,prec", [(20000, 200, 10, 1), (12000, 128, 6, 0), (9000, 170, 5, 1),
                                         (12000, 400, 6, 1), (8000, 250, 4, 0), (9000, 300, 3, 1),
                                         (6000, 512, 3, 1), (5000, 256, 2, 0)])

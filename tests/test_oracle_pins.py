@@ -662,3 +662,49 @@ def test_pcg_recursive_residual_and_restart():
     rn = np.linalg.norm(r - rz / float(z @ q) * q)
     assert abs(t[row + 1, 2] - rz) <= 1e-8 * abs(rz)
     assert abs(t[row + 1, 1] - rn) <= 1e-6 * rn
+
+
+def test_bicgstab2_restart_equals_fresh_solve_from_current_x():
+    """Both convergence-failure branches of the BiCGStab(2) exit test (reading of
+    Section 4.1.1's exit points; Sleijpen-Fokkema print no residual replacement).
+
+    Asking for 1e-18 makes the recursive residual pass its test while the true
+    residual (rounding level, ~1e-16) fails the confirmation.  After matvec 4 the
+    method restarts from the current x_R: r^0 = M^{-1}(b - A x_R), r~0 = r^0, with
+    alpha = 0 (so the first beta is 0, which makes the u^0 = 0 and omega = 1 resets
+    implied).  That is exactly a fresh solve of A y = b - A x_R from y = 0, so the
+    recursive residual norms after the restart must equal the fresh solve's, row by
+    row (the vectors r^j, u^j are the same arithmetic on the same data).  After
+    matvec 1 or 3 a failed confirmation changes nothing, so the window between two
+    restarts, which contains such a carry-on, matches as well.  b is scaled by 2^50
+    (exact, so every iterate scales exactly) to put the restart at residual norms of
+    order one: there a kept alpha would show, since beta = alpha rho_1 / rho_0 is not
+    scale-invariant once rho_0 is reset to 1."""
+    N, K, P = 300, 5, 10
+    band = rand_band(N, K, 0.7, 43)
+    b = O.spmv(band, N, K, G.x_true(N, 43)) * 2.0 ** 50
+    s = O.Sap(band, N, K, P, O.SAP_D)
+    tol = 1e-18
+    x, info = s.solve(b, tol=tol, max_iters=40, trace=True)
+    assert info.status == O.NOT_CONVERGED and info.n_restarts >= 2
+    assert info.relres <= 1e-15                       # restarts keep the accuracy
+    t = info.trace
+    btn = np.linalg.norm(s.apply(b))
+    passed = t[:, 1] <= tol * btn
+    mv = t[:, 0].astype(int)
+    restarts = np.nonzero(passed & (mv % 4 == 0))[0]
+    assert len(restarts) >= 2
+    r0, r1 = int(restarts[0]), int(restarts[1])
+    carry_on = [k for k in range(r0 + 1, r1) if passed[k] and mv[k] % 4 in (1, 3)]
+    assert carry_on, "the window must contain a failed confirmation after matvec 1 or 3"
+    # x_R: the iterate at the first restart (the restart does not move x)
+    xr, ir = s.solve(b, tol=tol, max_iters=mv[r0] // 4)
+    assert ir.n_restarts == 1
+    bp = b - O.spmv(band, N, K, xr)
+    _, fresh = s.solve(bp, tol=tol, max_iters=(mv[r1] - mv[r0]) // 4 + 1, trace=True)
+    tf = fresh.trace
+    window = t[r0 + 1:r1 + 1]
+    np.testing.assert_array_equal(window[:, 0] - mv[r0], tf[:len(window), 0])
+    np.testing.assert_allclose(window[:, 1], tf[:len(window), 1], rtol=1e-12, atol=0)
+    # and the true residual keeps tracking: the restarted iterate is x_R + y
+    assert abs(t[r0, 2] - np.linalg.norm(s.apply(bp))) <= 1e-12 * t[r0, 2]

@@ -67,7 +67,10 @@ typedef enum { SAP_D = 0, SAP_C = 1 } sap_variant_t;          /* Sec. 2.1.1 */
 typedef enum { SAP_FP64 = 0, SAP_FP32 = 1, SAP_FP32_BF16TU = 2 } sap_precision_t;
 
 typedef struct {
-    int32_t P;            /* number of diagonal blocks, 1 <= P <= N (Sec. 3.1) */
+    int32_t P;            /* number of diagonal blocks, 1 <= P <= N (Sec. 3.1); 0 makes
+                             sap_factor run sap_autotune over its default candidates
+                             first and use the fastest P (and, if segments is 0, the
+                             fastest segment count); sap_num_partitions tells which */
     int32_t variant;      /* sap_variant_t */
     int32_t precision;    /* sap_precision_t: precision of factors, tips and sweeps;
                              the Krylov vectors, SpMV, dot products, the true
@@ -77,7 +80,15 @@ typedef struct {
     double boost_eps;     /* relative pivot-boost threshold (Sec. 2.2): a pivot with
                              |p| < boost_eps * max|a_ij| becomes sign(p) times that
                              value; <= 0 selects the unit roundoff of `precision` */
-    int64_t spin_limit;   /* reserved for device-side waits (0 = default) */
+    int64_t spin_limit;   /* polls a bounded device-side wait makes before it gives
+                             up (0 = default, 2^24; values above 2^31 - 1 are
+                             clamped).  A wait that gives up stops the kernel's
+                             further copies, drains those in flight, lets the kernel
+                             finish with unspecified values, and the call returns
+                             SAP_ERR_TIMEOUT.  A poll is one non-blocking mbarrier
+                             test in the sweeps and one mbarrier try_wait (which may
+                             suspend the thread for a hardware-defined time) in the
+                             tensor-core factorisation.  No counterpart in the paper. */
     int32_t segments;     /* sweep segments per block (0 = automatic, 1 = none): the
                              two banded triangular sweeps of every block are split
                              into this many consecutive row ranges that run on
@@ -96,16 +107,28 @@ typedef struct {
     double iters;         /* BiCGStab(2) iterations in quarters (Sec. 4.1.1) */
     double relres;        /* final true ||b - A x||_2 / ||b||_2 (FP64) */
     int64_t n_boosted;    /* boosted pivots in all LU and UL factorisations */
-    int64_t n_matvec;     /* preconditioned matvecs M^{-1} A v performed */
-    int64_t n_restarts;   /* residual replacements after a failed true-residual check */
+    int64_t n_matvec;     /* preconditioned matvecs M^{-1} A v of the iteration: 4 per
+                             outer iteration, 1 or 3 in one that exits early (= 4 iters).
+                             Not counted: the first apply M^{-1} b, the SpMV of each
+                             true-residual check, and the SpMV + apply of a restart */
+    int64_t n_restarts;   /* restarts from the current x after a true-residual check that
+                             failed behind the MR update (one SpMV + one apply each) */
     float t_factor_ms;    /* device time of the last factorisation (all phases) */
     float t_solve_ms;     /* device time of the Krylov phase of the last solve */
     float t_lu_ms;        /* factor phase T_LU: block LU (and the boost-threshold pass) */
     float t_ul_ms;        /* SaP-C: block UL (top tiles only) */
-    float t_spk_ms;       /* SaP-C: B/C, spike tips, Rbar_i, its GEPP and inverse */
+    float t_spk_ms;       /* SaP-C T_SPK: spike tips V^(b)_i, W^(t)_{i+1}; where the K x K
+                             matrices fit in shared memory one kernel per interface also
+                             forms Rbar_i, its GEPP and inverse, and they count here */
     int32_t segments;     /* sweep segments per block in use (sap_options_t.segments) */
     int32_t graphed;      /* 1 if the iterations ran as replays of one captured CUDA graph */
     int32_t tc_update;    /* 1 if the block LU/UL trailing updates ran on the tensor cores */
+    int32_t P;            /* partition count in use (the autotuner's choice when P = 0) */
+    float t_bc_ms;        /* SaP-C T_BC (Sec. 4.3.2 breakdown): 0, B_i and C_{i+1} are read in
+                             place from the band by the tip and reduced-solve kernels */
+    float t_rdcd_ms;      /* SaP-C T_LUrdcd: forming Rbar_i, its GEPP and explicit inverse
+                             (0 where fused into the tip kernel, see t_spk_ms) */
+    float t_kry_ms;       /* T_Kry: device time of the Krylov phase (= t_solve_ms) */
     int32_t reserved1;    /* 0 */
 } sap_info_t;
 
@@ -122,7 +145,9 @@ SAP_API void sap_default_options(sap_options_t *opt);
  *   N >= 2, 1 <= K < N.  SaP-C needs every block to have >= 2K rows.
  *   *out receives a new handle owning all other device memory.
  * Errors: INVALID_ARG (sizes, options, N_i < 2K for SaP-C), NOT_IMPLEMENTED
- * (K above sap_max_K), OOM, SINGULAR, CUDA.  Synchronises `stream`. */
+ * (K above sap_max_K), OOM, SINGULAR, TIMEOUT (a bounded device wait of the
+ * tensor-core factorisation gave up), CUDA.  Synchronises `stream`; with
+ * P = 0 it first factors and solves once per autotuner candidate. */
 SAP_API sap_status_t sap_factor(const double *band_dev, int64_t N, int32_t K,
                         const sap_options_t *opt, cudaStream_t stream,
                         sap_handle_t *out);
@@ -195,6 +220,10 @@ SAP_API sap_status_t sap_get_block_lu(sap_handle_t h, int32_t i, double *f_host,
 SAP_API sap_status_t sap_get_interface(sap_handle_t h, int32_t i, int32_t which, int32_t adjoint,
                                double *m_host, cudaStream_t stream);
 
+/* Partition count P of the handle (the autotuner's choice when the options
+ * asked for P = 0), or -1 for a NULL handle. */
+SAP_API int32_t sap_num_partitions(sap_handle_t h);
+
 /* Number of boosted pivots so far (LU and UL). */
 SAP_API int64_t sap_n_boosted(sap_handle_t h);
 
@@ -214,11 +243,22 @@ SAP_API const char *sap_status_string(sap_status_t s);
  * max|a_ij|) and the forward and backward sweeps, so x = A^{-1} b up to the
  * factorisation's rounding; no Krylov iteration.
  *   All intermediates live in one file-scope device array of 32 MiB that
- *   every GPU loading the library holds until the process exits; the call
- *   needs, with n = N rounded up to 32 and s = sizeof(factor), about
- *   n (2K+1) s (factors) + 2 n 32 (1 + ceil(K/32)) s (sweep matrices) +
- *   (2N + 2K + 8) 8 bytes, and returns SAP_ERR_INVALID_ARG beyond that.
- *   The caller still provides band_dev, b_dev and x_dev (device, float64).
+ *   every GPU loading the library holds until the process exits.  With
+ *   n = N rounded up to 32, s = sizeof(factor) (8 for SAP_FP64, 4 for
+ *   SAP_FP32) and r(x) = x rounded up to a multiple of 256, the call needs
+ *     256 + r(n (2K+1) s)                     factors
+ *         + 2 r(n 32 (1 + ceil(K/32)) s)      chunk matrices of the two sweeps
+ *         + r((2N + 2K + 8) 8)                sweep scratch
+ *         + r(N (2K+1) 4)                     FP32 only: the FP32 copy of the band
+ *         + r(M (M + 4) s)                    K > 208 (FP32) or K > 128 (FP64) only:
+ *                                             the factor window, M = K + 16 rounded up to 16
+ *   bytes and returns SAP_ERR_INVALID_ARG beyond 2^25.  Examples: K = 25 fits
+ *   up to N = 23,168 in FP64 and N = 35,840 in FP32.
+ *   The caller provides band_dev, b_dev and x_dev (device, float64) and,
+ *   optionally, timeout_dev: a device int32 that receives, in stream order,
+ *   1 if one of the call's bounded device waits gave up (x then holds
+ *   unspecified values) and 0 otherwise; read it once the stream has
+ *   completed.  With timeout_dev = NULL a timeout goes unreported.
  *   The first call on a device looks up the array's device address; make
  *   that first call before any stream capture.
  *   Every call uses the same array and overwrites the previous call's
@@ -228,7 +268,7 @@ SAP_API const char *sap_status_string(sap_status_t s);
  * array), NOT_IMPLEMENTED (K above sap_max_K), CUDA. */
 SAP_API sap_status_t sap_band_solve_noalloc(const double *band_dev, int64_t N, int32_t K,
                                            const double *b_dev, double *x_dev, int32_t precision,
-                                           cudaStream_t stream);
+                                           int32_t *timeout_dev, cudaStream_t stream);
 
 /* ---- Autotuner ----
  * Not in the paper (a GB300 addition): picks the partition count P and the

@@ -42,7 +42,9 @@ class sap_info_t(C.Structure):
                 ("n_matvec", C.c_int64), ("n_restarts", C.c_int64),
                 ("t_factor_ms", C.c_float), ("t_solve_ms", C.c_float), ("t_lu_ms", C.c_float),
                 ("t_ul_ms", C.c_float), ("t_spk_ms", C.c_float), ("segments", C.c_int32),
-                ("graphed", C.c_int32), ("tc_update", C.c_int32), ("reserved1", C.c_int32)]
+                ("graphed", C.c_int32), ("tc_update", C.c_int32), ("P", C.c_int32),
+                ("t_bc_ms", C.c_float), ("t_rdcd_ms", C.c_float), ("t_kry_ms", C.c_float),
+                ("reserved1", C.c_int32)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -69,12 +71,13 @@ def _load():
         "sap_get_block_lu": (C.c_int, [vp, i32, vp, vp]),
         "sap_get_interface": (C.c_int, [vp, i32, i32, i32, vp, vp]),
         "sap_n_boosted": (i64, [vp]),
+        "sap_num_partitions": (i32, [vp]),
         "sap_destroy": (C.c_int, [vp]),
         "sap_status_string": (C.c_char_p, [C.c_int]),
         "sap_max_K": (i32, [i32]),
         "sap_kernel_launches": (i64, []),
         "sap_selftest_wait_timeout": (C.c_int, [i32, vp]),
-        "sap_band_solve_noalloc": (C.c_int, [vp, i64, i32, vp, vp, i32, vp]),
+        "sap_band_solve_noalloc": (C.c_int, [vp, i64, i32, vp, vp, i32, vp, vp]),
         "sap_factor_batched": (C.c_int, [i32, vp, vp, vp, P(sap_options_t), vp, P(vp)]),
         "sap_autotune": (C.c_int, [vp, i64, i32, P(sap_options_t), vp, i32, vp, i32, vp, vp,
                                    P(C.c_int32), P(C.c_int32), vp, P(C.c_int32)]),
@@ -223,9 +226,13 @@ def sap_spmv(band: torch.Tensor, N: int, K: int, x: torch.Tensor, y: torch.Tenso
     return y
 
 
+def sap_num_partitions(h: Handle) -> int:
+    return int(_lib.sap_num_partitions(h.ptr))
+
+
 def sap_get_partition(h: Handle):
     import numpy as np
-    off = np.zeros(h.opts.P + 1, dtype=np.int64)
+    off = np.zeros(sap_num_partitions(h) + 1, dtype=np.int64)
     _check(_lib.sap_get_partition(h.ptr, C.c_void_p(off.ctypes.data)), "sap_get_partition")
     return off
 
@@ -249,9 +256,17 @@ def sap_get_interface(h: Handle, i: int, which: str, adjoint: bool = False, stre
 
 
 def sap_band_solve_noalloc(band: torch.Tensor, N: int, K: int, b: torch.Tensor, x: torch.Tensor,
-                           precision: int = SAP_FP64, stream=None) -> torch.Tensor:
-    """Allocation-free direct banded solve (see include/sap.h)."""
-    _check(_lib.sap_band_solve_noalloc(_ptr(band), N, K, _ptr(b), _ptr(x), precision, _stream(stream)),
+                           precision: int = SAP_FP64, timeout: torch.Tensor | None = None,
+                           stream=None) -> torch.Tensor:
+    """Allocation-free direct banded solve (see include/sap.h).  timeout: an
+    optional CUDA int32 tensor of one element that receives 1 if a bounded
+    device wait of the call gave up."""
+    tp = None
+    if timeout is not None:
+        if not (timeout.is_cuda and timeout.dtype == torch.int32 and timeout.numel() >= 1):
+            raise ValueError("timeout must be a CUDA int32 tensor")
+        tp = timeout.data_ptr()
+    _check(_lib.sap_band_solve_noalloc(_ptr(band), N, K, _ptr(b), _ptr(x), precision, tp, _stream(stream)),
            "sap_band_solve_noalloc")
     return x
 

@@ -65,10 +65,11 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(bar)) : "memory");
 }
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+// Non-blocking test of a barrier phase (one poll of a bounded wait).
+__device__ __forceinline__ bool mbar_test_wait(uint64_t* bar, unsigned parity) {
   unsigned ok;
   asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
       : "=r"(ok) : "r"(smem_u32(bar)), "r"(parity) : "memory");
   return ok != 0;
 }
@@ -76,15 +77,16 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned by
   asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n"
                ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)) : "memory");
 }
-// Bounded wait for a barrier phase: after kSpinLimit polls the thread records
-// a timeout in *err, stops waiting for good and lets the kernel run to its end.
-constexpr int kSpinLimit = 1 << 22;
-__device__ __forceinline__ void mbar_wait(uint64_t* bar, unsigned parity, int* err, bool& failed) {
-  if (failed) return;
-  for (int i = 0; i < kSpinLimit; ++i)
-    if (mbar_try_wait(bar, parity)) return;
+// Bounded wait for a barrier phase: after `limit` polls the thread records a
+// timeout in err[0], stops waiting for good and lets the kernel run to its
+// end.  Returns true if the phase completed.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, int limit, int* err, bool& failed) {
+  if (failed) return false;
+  for (int i = 0; i < limit; ++i)
+    if (mbar_test_wait(bar, parity)) return true;
   failed = true;
   if (err) atomicExch(err, 1);
+  return false;
 }
 
 // Column-major 32 x 32 matrix row `lane` against a broadcast vector: all
@@ -130,22 +132,40 @@ struct SweepSh {
 template <int MODE>
 __device__ __forceinline__ int row_of(int p, int ld) { return fwd_mode<MODE>() ? p : ld - 1 - p; }
 
-// Warp 2: bulk-copy local chunk lc's matrices into ring slot lc % (PFD+1).
+// Copy warp: bulk-copy local chunk lc's matrices into ring slot lc % (PFD+1).
 // Chunks past the segment (lc >= nc) only arrive on the barrier, so that every
-// slot completes one phase per chunk index.
+// slot completes one phase per chunk index.  Lane 0 keeps the slots with a
+// copy in flight (inflight) and the parity of the phase each completes (ifpar,
+// the slot's bit of ph at issue); after a wait gave up (failed) no copy is
+// issued any more, so that the in-flight ones can be drained.
 template <int PFD, typename T, typename YT>
 __device__ __forceinline__ void prefetch_mats(const SweepSh<T, YT>& sh, const SweepGeom& g, const T* __restrict__ Mg,
-                                              int lc, int nc) {
-  if ((threadIdx.x & 31) != 0) return;
+                                              int lc, int nc, bool failed, unsigned ph, unsigned& inflight,
+                                              unsigned& ifpar) {
+  if ((threadIdx.x & 31) != 0 || failed) return;
   const int slot = lc % (PFD + 1);
   const int mat = (1 + g.ng) * CHK * CHK;
   if (lc < nc) {
     const unsigned bytes = (unsigned)(mat * sizeof(T));
     mbar_expect_tx(&sh.bar[slot], bytes);
     bulk_g2s(sh.M + slot * mat, Mg + (int64_t)lc * mat, bytes, &sh.bar[slot]);
+    inflight |= 1u << slot;
+    ifpar = (ifpar & ~(1u << slot)) | (ph & (1u << slot));
   } else {
     mbar_arrive(&sh.bar[slot]);
   }
+}
+
+// After a wait of this thread gave up: wait (bounded by kDefaultSpin polls
+// each) for the copies still in flight, so that none lands in shared memory
+// after the sweep has moved on or the CTA has exited.
+template <int PFD>
+__device__ __forceinline__ void drain_copies(uint64_t* bar, unsigned inflight, unsigned ifpar) {
+  for (int sl = 0; sl <= PFD; ++sl)
+    if (inflight & (1u << sl)) {
+      bool gave_up = false;
+      mbar_wait(&bar[sl], (ifpar >> sl) & 1u, kDefaultSpin, nullptr, gave_up);
+    }
 }
 
 // Warp 1: cp.async of local chunk lc's right-hand side (one commit group per
@@ -185,12 +205,16 @@ __device__ void sweep(const SweepSh<T, YT>& sh, const SweepGeom& g, const T* __r
   // carried from sweep to sweep of one CTA
   constexpr int WCOPY = NPW + 1;
   const bool prep = NPW == 1 ? warp == 1 : (warp >= 1 && warp <= NPW);
+  // copy warp, lane 0: copies in flight and their phase parities (see prefetch_mats)
+  unsigned inflight = 0u, ifpar = 0u;
+  const int spin = (warp == WCOPY && lane == 0) ? spin_limit_of(err) : 0;
   auto wait_chunk = [&](int lc) {     // copy warp: lane 0 polls
     const int sl = lc % (PFD + 1);
-    if (lane == 0) mbar_wait(&sh.bar[sl], (ph >> sl) & 1u, err, failed);
+    if (lane == 0 && mbar_wait(&sh.bar[sl], (ph >> sl) & 1u, spin, err, failed)) inflight &= ~(1u << sl);
     ph ^= 1u << sl;
     __syncwarp();
   };
+  auto issue = [&](int lc) { prefetch_mats<PFD>(sh, g, Ms, lc, nc, failed, ph, inflight, ifpar); };
   auto zslot = [&](int lc) { return (lc + ng + 1) % (ng + 1); };
   // w_lb = MINV (y - corrections) - sum_{k>=2} G_k z_{lb-k}: prepare warp j
   // (0-based) forms the MINV term (j = 0) and the G_k terms with k = j + 2 mod
@@ -237,7 +261,7 @@ __device__ void sweep(const SweepSh<T, YT>& sh, const SweepGeom& g, const T* __r
   __syncthreads();
   // prologue: matrices of local chunks 0..PFD-1 in flight, 0 and 1 landed, w_0 formed
   if (warp == WCOPY) {
-    for (int lc = 0; lc < PFD; ++lc) prefetch_mats<PFD>(sh, g, Ms, lc, nc);
+    for (int lc = 0; lc < PFD; ++lc) issue(lc);
     wait_chunk(0);
     wait_chunk(1);
   } else if (warp == 1) {
@@ -284,14 +308,16 @@ __device__ void sweep(const SweepSh<T, YT>& sh, const SweepGeom& g, const T* __r
     } else if (NPW > 1 && prep) {
       if (lc + 1 < nc) prepare(lc + 1);
     } else {
-      prefetch_mats<PFD>(sh, g, Ms, lc + PFD, nc);
+      issue(lc + PFD);
       wait_chunk(lc + 2);       // read by the prepare warps in iteration lc + 1, by warp 0 in lc + 2
     }
     __syncthreads();
   }
   // copy warp: consume the phases of the remaining prefetched chunks
-  if (warp == WCOPY)
+  if (warp == WCOPY) {
     for (int lc = nc + 2; lc < nc + PFD; ++lc) wait_chunk(lc);
+    if (lane == 0 && failed) drain_copies<PFD>(sh.bar, inflight, ifpar);
+  }
   if (warp == 1) cpa_wait<0>();
   if (tail && warp == 0) {     // the last KH positions of the segment's last ng chunks
     const int off = ng * CHK - hist_width(K);

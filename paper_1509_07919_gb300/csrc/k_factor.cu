@@ -140,6 +140,7 @@ struct TcCtx {
   unsigned ph = 0;              // next phase parity of bar
   bool failed = false;          // a bounded wait of this thread gave up
   int* err = nullptr;
+  int spin = kDefaultSpin;      // polls of a bounded wait (err[1])
 };
 __host__ __device__ inline int tc_rows(int K) { return ((K + 15) / 16 * 16 + kTcPiece - 1) / kTcPiece * kTcPiece; }
 __host__ __device__ inline uint32_t tc_cols(int K) {
@@ -156,6 +157,7 @@ __device__ void tc_setup(unsigned char* base, int K, TcCtx& t, int* err) {
   t.bar = reinterpret_cast<uint64_t*>(t.B + Kp * 16);
   uint32_t* slot = reinterpret_cast<uint32_t*>(t.bar + 1);
   t.err = err;
+  t.spin = spin_limit_of(err);
   for (int e = threadIdx.x; e < Kp * 16; e += blockDim.x) {
     t.A[e] = __float2bfloat16_rn(0.f);
     t.B[e] = __float2bfloat16_rn(0.f);
@@ -177,7 +179,7 @@ __device__ void tc_teardown(TcCtx& t, int K) {
   // a thread whose wait gave up waits once more (bounded) for the MMAs in flight
   if (t.failed) {
     bool again = false;
-    tc::mbar_wait_bounded(t.bar, t.ph ^ 1u, 1 << 22, nullptr, again);
+    tc::mbar_wait_bounded(t.bar, t.ph ^ 1u, kDefaultSpin, nullptr, again);
   }
   tc::fence_before_sync();
   __syncthreads();
@@ -415,7 +417,7 @@ __device__ void band_lu_block(unsigned char* smem_raw, const T* __restrict__ ban
           tc::mma_commit(tcx.bar);
         }
         if (g0 == 0) write_panel(tid, NTH);   // overlaps the MMAs (it reads only the panel's rows / columns)
-        tc::mbar_wait_bounded(tcx.bar, tcx.ph, 1 << 22, tcx.err, tcx.failed);
+        tc::mbar_wait_bounded(tcx.bar, tcx.ph, tcx.spin, tcx.err, tcx.failed);
         tcx.ph ^= 1u;
         tc::fence_after_sync();
         for (int p = 0; p < gn; ++p) {

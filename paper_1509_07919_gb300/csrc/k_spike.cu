@@ -453,8 +453,8 @@ size_t spike_scratch_bytes(int K, int P, bool fp64) {
 template <typename T>
 cudaError_t launch_spikes(const double* band, int64_t N, int K, int P, Dev d, const T* F, const T* ULt,
                           bool adjoint, T* V, T* Wt, double* Rinv, double* R0, int* piv, int* singular,
-                          void* gscratch, cudaStream_t s) {
-  if (P < 2) return cudaSuccess;
+                          void* gscratch, cudaStream_t s, cudaEvent_t ev_rd) {
+  if (P < 2) return ev_rd ? cudaEventRecord(ev_rd, s) : cudaSuccess;
   const bool gm = spike_scratch_bytes(K, P, sizeof(T) == 8) > 0;
   if (gm && !gscratch) return cudaErrorInvalidValue;
   const size_t smem = (gm ? 0 : spike_ws_bytes(K, sizeof(T))) + (size_t)K * sizeof(int);
@@ -467,7 +467,8 @@ cudaError_t launch_spikes(const double* band, int64_t N, int K, int P, Dev d, co
   kern<<<P - 1, NT, smem, s>>>(band, N, K, d, F, ULt, adjoint, V, Wt, Rinv, R0, piv, singular,
                                static_cast<unsigned char*>(gscratch));
   cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess || !gm) return e;
+  if (e != cudaSuccess) return e;
+  if (!gm) return ev_rd ? cudaEventRecord(ev_rd, s) : cudaSuccess;   // Rbar_i formed inside k_spikes
   unsigned char* gws = static_cast<unsigned char*>(gscratch);
   const size_t tsm = (size_t)K * 32 * sizeof(T);
   if (tsm > 48 * 1024) {
@@ -476,6 +477,7 @@ cudaError_t launch_spikes(const double* band, int64_t N, int K, int P, Dev d, co
   }
   count_launches(1);
   k_tip_cols<T><<<dim3((K + 31) / 32, P - 1, 2), 32, tsm, s>>>(band, N, K, d, ULt, adjoint, V, Wt, gws);
+  if (ev_rd && (e = cudaEventRecord(ev_rd, s)) != cudaSuccess) return e;
   const int tiles = (K + RT - 1) / RT;
   count_launches(3);
   k_rbar_form<T><<<dim3(tiles, tiles, P - 1), 256, 0, s>>>(V, Wt, K, R0, gws);
@@ -490,9 +492,10 @@ cudaError_t launch_spikes(const double* band, int64_t N, int K, int P, Dev d, co
 }
 
 template cudaError_t launch_spikes<float>(const double*, int64_t, int, int, Dev, const float*, const float*, bool,
-                                          float*, float*, double*, double*, int*, int*, void*, cudaStream_t);
+                                          float*, float*, double*, double*, int*, int*, void*, cudaStream_t,
+                                          cudaEvent_t);
 template cudaError_t launch_spikes<double>(const double*, int64_t, int, int, Dev, const double*, const double*,
                                            bool, double*, double*, double*, double*, int*, int*, void*,
-                                           cudaStream_t);
+                                           cudaStream_t, cudaEvent_t);
 
 }  // namespace sap

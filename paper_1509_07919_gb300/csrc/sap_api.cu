@@ -130,7 +130,8 @@ struct sap_handle {
   int* host_f = nullptr;      // pinned flag readback
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   cudaEvent_t evp[4] = {nullptr, nullptr, nullptr, nullptr};
-  float t_factor_ms = 0.f, t_lu_ms = 0.f, t_ul_ms = 0.f, t_spk_ms = 0.f;
+  cudaEvent_t ev_rd = nullptr;   // SaP-C: between the spike tips and the reduced systems
+  float t_factor_ms = 0.f, t_lu_ms = 0.f, t_ul_ms = 0.f, t_spk_ms = 0.f, t_rdcd_ms = 0.f;
   double* host_stage = nullptr;  // 2 N doubles for sap_solve_host, allocated on first use
   std::unique_ptr<SolverBase> impl;
   ~sap_handle() {
@@ -161,6 +162,7 @@ struct sap_handle {
       if (e) cudaEventDestroy(e);
     for (cudaEvent_t e : evp)
       if (e) cudaEventDestroy(e);
+    if (ev_rd) cudaEventDestroy(ev_rd);
   }
 };
 
@@ -208,8 +210,11 @@ struct Solver : SolverBase {
       TRY(h->mem.alloc(&wlu, (size_t)P * lu_window_elems(K)));
       if (h->opt.variant == SAP_C && P > 1) TRY(h->mem.alloc(&wul, (size_t)(P - 1) * lu_window_elems(K)));
     }
-    TRY(h->mem.alloc(&f.err, 1));
-    CK(cudaMemset(f.err, 0, sizeof(int)));
+    TRY(h->mem.alloc(&f.err, 2));
+    {
+      const int e2[2] = {0, spin_limit_value(h->opt.spin_limit)};   // flag, polls per bounded wait
+      CK(cudaMemcpy(f.err, e2, sizeof(e2), cudaMemcpyHostToDevice));
+    }
     TRY(h->mem.alloc(&f.Mlf, (size_t)L.c_elems));
     TRY(h->mem.alloc(&f.Mub, (size_t)L.c_elems));
     f.cbase = h->dcbase;
@@ -338,9 +343,10 @@ struct Solver : SolverBase {
       CK(cudaStreamWaitEvent(s, h->ev_us1, 0));      // the UL started by factor_pre
       CK(cudaEventRecord(h->evp[2], s));
       CK(launch_spikes<T>(h->band, L.N, K, P, h->d, f.F, f.ULt, false, f.V, f.Wt, f.R, f.R0, f.piv,
-                          h->singular, wspk, s));
+                          h->singular, wspk, s, h->ev_rd));
     } else {
       CK(cudaEventRecord(h->evp[2], s));
+      CK(cudaEventRecord(h->ev_rd, s));
     }
     CK(cudaEventRecord(h->evp[3], s));
     return SAP_OK;
@@ -782,10 +788,14 @@ struct KrylovRun {
     cudaEventElapsedTime(&ms, ev0, ev1);
     inf.n_matvec = (int64_t)std::llround(4.0 * inf.iters);
     inf.t_solve_ms = ms;
+    inf.t_kry_ms = ms;
     inf.t_factor_ms = h->t_factor_ms;
     inf.t_lu_ms = h->t_lu_ms;
     inf.t_ul_ms = h->t_ul_ms;
+    inf.t_bc_ms = 0.f;            // B_i, C_{i+1} are read in place by the tip kernels
     inf.t_spk_ms = h->t_spk_ms;
+    inf.t_rdcd_ms = h->t_rdcd_ms;
+    inf.P = h->L.P;
     inf.segments = h->L.S;
     inf.graphed = (h->gexec[gi] != nullptr) ? 1 : 0;
     inf.tc_update = h->impl->tc_used() ? 1 : 0;
@@ -837,7 +847,8 @@ sap_status_t finish_factor(sap_handle* h) {
   cudaEventElapsedTime(&h->t_lu_ms, h->evp[0], h->evp[1]);
   h->t_ul_ms = 0.f;
   if (h->opt.variant == SAP_C && h->L.P > 1) cudaEventElapsedTime(&h->t_ul_ms, h->evu[0], h->evu[1]);
-  cudaEventElapsedTime(&h->t_spk_ms, h->evp[2], h->evp[3]);
+  cudaEventElapsedTime(&h->t_spk_ms, h->evp[2], h->ev_rd);
+  cudaEventElapsedTime(&h->t_rdcd_ms, h->ev_rd, h->evp[3]);
   cudaEventElapsedTime(&h->t_factor_ms, h->evp[0], h->evp[3]);
   int sing = 0;
   CK(cudaMemcpy(&sing, h->singular, sizeof(int), cudaMemcpyDeviceToHost));
@@ -947,6 +958,7 @@ sap_status_t create_handle(const double* band_dev, int64_t N, int32_t K, const s
   CK(cudaEventCreate(&h->ev0));
   CK(cudaEventCreate(&h->ev1));
   for (auto& e : h->evp) CK(cudaEventCreate(&e));
+  CK(cudaEventCreate(&h->ev_rd));
   if (opt.precision == SAP_FP64) h->impl.reset(new Solver<double>(h));
   else h->impl.reset(new Solver<float>(h));
   TRY(h->impl->alloc());
@@ -1166,8 +1178,21 @@ sap_status_t sap_factor(const double* band_dev, int64_t N, int32_t K, const sap_
                         cudaStream_t s, sap_handle_t* out) {
   if (!out) return SAP_ERR_INVALID_ARG;
   *out = nullptr;
+  if (!opt_in) return SAP_ERR_INVALID_ARG;
+  sap_options_t opt = *opt_in;
+  if (opt.P == 0) {
+    // P = 0: the partition count (and, with segments = 0, the segment count)
+    // measured fastest by the autotuner over its default candidates
+    if (!band_dev || N < 2 || K < 1 || K >= N) return SAP_ERR_INVALID_ARG;
+    int32_t bp = 0, bs = 0;
+    const int32_t seg_user = opt.segments;
+    TRY(sap_autotune(band_dev, N, K, &opt, nullptr, 0, seg_user > 0 ? &seg_user : nullptr, seg_user > 0 ? 1 : 0,
+                     nullptr, s, &bp, &bs, nullptr, nullptr));
+    opt.P = bp;
+    opt.segments = bs;
+  }
   std::unique_ptr<sap_handle> h;
-  TRY(create_handle(band_dev, N, K, opt_in, s, h));
+  TRY(create_handle(band_dev, N, K, &opt, s, h));
   TRY(run_factor(h.get(), s));
   *out = h.release();
   return SAP_OK;
@@ -1276,6 +1301,8 @@ sap_status_t sap_selftest_wait_timeout(int32_t spin_limit, cudaStream_t s) {
   if (st != SAP_OK) return st;
   return e ? SAP_ERR_TIMEOUT : SAP_OK;
 }
+
+int32_t sap_num_partitions(sap_handle_t h) { return h ? h->L.P : -1; }
 
 sap_status_t sap_get_partition(sap_handle_t h, int64_t* off) {
   if (!h || !off) return SAP_ERR_INVALID_ARG;

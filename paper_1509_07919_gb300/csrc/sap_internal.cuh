@@ -79,7 +79,7 @@ struct Factors {
   T* Xlf = nullptr; T* Xub = nullptr; T* Xutf = nullptr; T* Xltb = nullptr;   // history responses
   int cpsmax = 0;        // chunks of the longest segment
   T* tails = nullptr;    // P x S x KH
-  int* err = nullptr;    // set to nonzero by a device-side wait that timed out
+  int* err = nullptr;    // int[2]: [0] set to nonzero by a device-side wait that timed out, [1] its poll limit
 };
 
 // Device-side control of the Krylov iteration.  A launch carrying a Gate
@@ -100,6 +100,19 @@ __device__ __forceinline__ bool gate_skip(const Gate& g) {
   if (g.mode == G_CHECK) return g.flags[F_CHECK] == 0;
   if (g.mode == G_REPLACE) return g.flags[F_REPLACE] == 0;
   return false;
+}
+
+// Bounded device waits.  The error word of a handle is int[2]: err[0] is set
+// to nonzero by a wait that gave up, err[1] holds the number of polls a wait
+// makes before it gives up (sap_options_t.spin_limit; 0 selects kDefaultSpin).
+constexpr int kDefaultSpin = 1 << 24;
+__host__ __device__ inline int spin_limit_value(int64_t opt) {
+  return opt <= 0 ? kDefaultSpin : (opt > 0x7fffffff ? 0x7fffffff : (int)opt);
+}
+__device__ __forceinline__ int spin_limit_of(const int* err) {
+  if (!err) return kDefaultSpin;
+  const int v = *(volatile const int*)(err + 1);
+  return v > 0 ? v : kDefaultSpin;
 }
 
 // Host-side count of kernel launches issued by the library (for reporting).
@@ -143,7 +156,10 @@ cudaError_t launch_factor_ul(const T* band, int64_t N, int K, int P, Dev d, cons
 template <typename T>
 cudaError_t launch_spikes(const double* band, int64_t N, int K, int P, Dev d, const T* F, const T* ULt,
                           bool adjoint, T* V, T* Wt, double* Rinv, double* R0, int* piv, int* singular,
-                          void* gscratch, cudaStream_t s);
+                          void* gscratch, cudaStream_t s, cudaEvent_t ev_rd = nullptr);
+// ev_rd (optional) is recorded between the spike tips and the reduced systems
+// (Rbar_i, its GEPP and inverse); where one kernel per interface does both
+// (K x K matrices in shared memory) it is recorded after that kernel.
 // Global scratch of the spike kernel (0 when its K x K matrices fit in shared
 // memory): one workspace per interface, shared by the forward and adjoint tips.
 size_t spike_scratch_bytes(int K, int P, bool fp64);

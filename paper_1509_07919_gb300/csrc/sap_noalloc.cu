@@ -9,8 +9,9 @@
 // pivots) and its two triangular sweeps, but keeps every intermediate
 // (factor array, sweep intermediate, partition descriptor, boost
 // threshold, counters) in one file-scope device array instead of
-// allocating.  The array is kScratchBytes large and lives on every GPU
-// that loads the library until the process exits.
+// allocating.  Its header words are written by a one-thread kernel, so the
+// call copies nothing from host memory.  The array is kScratchBytes large and
+// lives on every GPU that loads the library until the process exits.
 #include <cuda_runtime.h>
 #include <cstdint>
 #include <cstring>
@@ -49,8 +50,30 @@ cudaError_t scratch_address(void** out) {
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
+// The call's header words, written on the device so that the call copies
+// nothing from host memory: the one-block partition descriptor
+// {off[0], off[1], fbase, ld, cbase} = {0, N, 0, ld, 0}, the boosted-pivot
+// counter, and the wait error word {flag, polls} of the bounded waits.
+__global__ void k_noalloc_header(int64_t* desc, int64_t N, int64_t ld, unsigned long long* nb, int* err) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  desc[0] = 0;
+  desc[1] = N;
+  desc[2] = 0;
+  desc[3] = ld;
+  desc[4] = 0;
+  *nb = 0ull;
+  err[0] = 0;
+  err[1] = kDefaultSpin;
+}
+
+// Copies the wait error flag into the caller's word (1 = a bounded wait gave up).
+__global__ void k_noalloc_status(const int* err, int32_t* out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) *out = err[0] != 0 ? 1 : 0;
+}
+
 template <typename T>
-sap_status_t run(const double* band, int64_t N, int K, const double* b, double* x, cudaStream_t s) {
+sap_status_t run(const double* band, int64_t N, int K, const double* b, double* x, int32_t* timeout_dev,
+                 cudaStream_t s) {
   const int W = 2 * K + 1;
   const int64_t ld = (N + 31) / 32 * 32;
   // scratch layout: header | factors | chunk matrices (L, U sweeps) | sweep scratch
@@ -69,18 +92,18 @@ sap_status_t run(const double* band, int64_t N, int K, const double* b, double* 
   int64_t* desc = reinterpret_cast<int64_t*>(p);        // off[2], fbase[1], ld[1], cbase[1]
   double* absmax = reinterpret_cast<double*>(p + 64);
   unsigned long long* nb = reinterpret_cast<unsigned long long*>(p + 128);
-  int* err = reinterpret_cast<int*>(p + 192);
+  int* err = reinterpret_cast<int*>(p + 192);          // int[2]
   T* F = reinterpret_cast<T*>(p + hdr);
   T* Mlf = reinterpret_cast<T*>(p + hdr + f_bytes);
   T* Mub = reinterpret_cast<T*>(p + hdr + f_bytes + c_bytes);
   double* ascratch = reinterpret_cast<double*>(p + hdr + f_bytes + 2 * c_bytes);
   float* bandf = reinterpret_cast<float*>(p + hdr + f_bytes + 2 * c_bytes + a_bytes);
   T* wlu = gw ? reinterpret_cast<T*>(p + hdr + f_bytes + 2 * c_bytes + a_bytes + b_bytes) : nullptr;
-  const int64_t h_desc[5] = {0, N, 0, ld, 0};
-  if (cudaMemcpyAsync(desc, h_desc, sizeof(h_desc), cudaMemcpyHostToDevice, s) != cudaSuccess) return SAP_ERR_CUDA;
-  // counters start at zero; factor padding columns are read as zeros by the sweeps
-  if (cudaMemsetAsync(nb, 0, sizeof(*nb), s) != cudaSuccess) return SAP_ERR_CUDA;
-  if (cudaMemsetAsync(err, 0, sizeof(*err), s) != cudaSuccess) return SAP_ERR_CUDA;
+  // descriptor and counters (the previous call's values are overwritten);
+  // factor padding columns are read as zeros by the sweeps
+  count_launches(1);
+  k_noalloc_header<<<1, 32, 0, s>>>(desc, N, ld, nb, err);
+  if (cudaGetLastError() != cudaSuccess) return SAP_ERR_CUDA;
   if (cudaMemsetAsync(F, 0, (size_t)ld * W * sizeof(T), s) != cudaSuccess) return SAP_ERR_CUDA;
   Dev d{desc, desc + 2, desc + 3};
   const double eps = sizeof(T) == 8 ? 0x1p-53 : 0x1p-24;
@@ -103,17 +126,23 @@ sap_status_t run(const double* band, int64_t N, int K, const double* b, double* 
   f.cbase = cbase;
   f.err = err;
   if (launch_apply<T>(band, N, K, 1, d, f, SAP_D, false, b, x, ascratch, s) != cudaSuccess) return SAP_ERR_CUDA;
+  if (timeout_dev) {
+    count_launches(1);
+    k_noalloc_status<<<1, 32, 0, s>>>(err, timeout_dev);
+    if (cudaGetLastError() != cudaSuccess) return SAP_ERR_CUDA;
+  }
   return SAP_OK;
 }
 
 }  // namespace
 
 extern "C" sap_status_t sap_band_solve_noalloc(const double* band_dev, int64_t N, int32_t K, const double* b_dev,
-                                               double* x_dev, int32_t precision, cudaStream_t stream) {
+                                               double* x_dev, int32_t precision, int32_t* timeout_dev,
+                                               cudaStream_t stream) {
   if (!band_dev || !b_dev || !x_dev || b_dev == x_dev) return SAP_ERR_INVALID_ARG;
   if (N < 2 || K < 1 || K >= N) return SAP_ERR_INVALID_ARG;
   if (precision != SAP_FP64 && precision != SAP_FP32) return SAP_ERR_INVALID_ARG;
   if (K > sap_max_K(precision)) return SAP_ERR_NOT_IMPLEMENTED;
-  return precision == SAP_FP64 ? run<double>(band_dev, N, K, b_dev, x_dev, stream)
-                               : run<float>(band_dev, N, K, b_dev, x_dev, stream);
+  return precision == SAP_FP64 ? run<double>(band_dev, N, K, b_dev, x_dev, timeout_dev, stream)
+                               : run<float>(band_dev, N, K, b_dev, x_dev, timeout_dev, stream);
 }

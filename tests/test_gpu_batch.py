@@ -135,8 +135,8 @@ def test_batched_autograd_matches_oracle_and_fd(sap):
 
 def test_batch_of_64_uneven_systems(sap):
     """The 64-system batch, N ~ U{10^4..10^5}, K ~ U{8..64}, d = 1, FP32
-    preconditioner with FP64 BiCGStab(2): every system to relres <= 1e-10,
-    the two smallest against the oracle."""
+    preconditioner with FP64 BiCGStab(2): every system to relres <= 1e-10 and
+    within 1e-8 of the oracle's solution with the same partition count."""
     specs = G.batch_specs(64)
     bands, xts, bs = make_batch(specs, 1.0)
     Ns = [s[0] for s in specs]
@@ -147,11 +147,11 @@ def test_batch_of_64_uneven_systems(sap):
     assert st == sap.SAP_OK
     for i, (N, K, _) in enumerate(specs):
         assert infos[i].relres <= 1e-10, (i, infos[i].relres)
-        assert relerr(host(xs[i]), xts[i]) <= 1e-5
-    for i in np.argsort(Ns)[:2]:
-        N, K, _ = specs[i]
-        xo, _, _ = O.solve(bands[i], N, K, bs[i], Ps[i], O.SAP_D)
-        assert relerr(host(xs[i]), xo) <= 1e-8
+        x = host(xs[i])
+        assert np.linalg.norm(bs[i] - O.spmv(bands[i], N, K, x)) / np.linalg.norm(bs[i]) <= 1e-10
+        xo, io, _ = O.solve(bands[i], N, K, bs[i], Ps[i], O.SAP_D)
+        assert io.status == O.OK
+        assert relerr(x, xo) <= 1e-8, (i, relerr(x, xo))
 
 
 def test_batch_with_a_wide_band_system(sap):

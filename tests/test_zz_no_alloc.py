@@ -26,11 +26,27 @@ def sap():
     return S
 
 
-def _noalloc(S, band, N, K, b, x, prec):
+def _noalloc(S, band, N, K, b, x, prec, timeout=None):
     """Call the C entry point directly through the C ABI."""
     fn = S._lib.sap_band_solve_noalloc
     return fn(ctypes.c_void_p(band.data_ptr()), N, K, ctypes.c_void_p(b.data_ptr()),
-              ctypes.c_void_p(x.data_ptr()), prec, ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+              ctypes.c_void_p(x.data_ptr()), prec,
+              ctypes.c_void_p(timeout.data_ptr()) if timeout is not None else None,
+              ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+
+
+def _need(N, K, s):
+    """Scratch bytes of one call, the formula documented in include/sap.h."""
+    r = lambda v: (v + 255) // 256 * 256
+    n = (N + 31) // 32 * 32
+    W = 2 * K + 1
+    t = 256 + r(n * W * s) + 2 * r(n * 32 * (1 + (K + 31) // 32) * s) + r((2 * N + 2 * K + 8) * 8)
+    if s == 4:
+        t += r(N * W * 4)
+    if K > (208 if s == 4 else 128):
+        M = (K + 16 + 15) // 16 * 16
+        t += r(M * (M + 4) * s)
+    return t
 
 
 @pytest.mark.parametrize("prec,tol,N,K", [(0, 1e-11, 20011, 25), (0, 1e-11, 4000, 50), (1, 1e-4, 20011, 25),
@@ -45,8 +61,11 @@ def test_noalloc_matches_allocating_path_twice(sap, prec, tol, N, K):
         b_np = G.adjoint_seed(N, 17 + call)
         b = torch.from_numpy(b_np).cuda()
         x = torch.full_like(b, float("nan"))
-        st = _noalloc(sap, band, N, K, b, x, prec)
+        flag = torch.full((1,), -1, dtype=torch.int32, device="cuda")
+        st = _noalloc(sap, band, N, K, b, x, prec, flag if call == 0 else None)
         assert st == sap.SAP_OK, sap.sap_status_string(st)
+        if call == 0:
+            assert int(flag.item()) == 0        # no bounded wait gave up
         ref = sap.sap_apply_preconditioner(h, b)
         torch.cuda.synchronize()
         xs, rs = x.cpu().numpy(), ref.cpu().numpy()
@@ -64,3 +83,40 @@ def test_noalloc_rejects_sizes_beyond_its_array(sap):
     x = torch.zeros_like(b)
     assert _noalloc(sap, band, N, K, b, x, 0) == sap.SAP_ERR_INVALID_ARG
     assert _noalloc(sap, band, N, K, b, b, 0) == sap.SAP_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("prec,s,K,nmax", [(0, 8, 25, 23168), (1, 4, 25, 35840), (1, 4, 250, 16000)])
+def test_noalloc_size_limit_is_the_documented_formula(sap, prec, s, K, nmax):
+    """Sizes on both sides of the 32 MiB limit, by the header's formula (which
+    counts the FP32 copy of the band and, for wide bands, the factor window):
+    the largest N that fits solves, the next one is refused, and an FP32 size
+    that only the factor and sweep terms would admit is refused too."""
+    N = nmax
+    while _need(N + 1, K, s) <= 1 << 25:
+        N += 1
+    while _need(N, K, s) > 1 << 25:
+        N -= 1
+    if nmax != 16000:
+        assert N == nmax
+    band_np = G.dense_banded(N, K, 1.0, 777 + K)
+    band = torch.from_numpy(band_np).cuda()
+    b_np = G.adjoint_seed(N, 5)
+    b = torch.from_numpy(b_np).cuda()
+    x = torch.full_like(b, float("nan"))
+    assert _noalloc(sap, band, N, K, b, x, prec) == sap.SAP_OK
+    ref = sap.sap_apply_preconditioner(sap.sap_factor(band, N, K, P=1, variant=sap.SAP_D, precision=prec), b)
+    torch.cuda.synchronize()
+    xs, rs = x.cpu().numpy(), ref.cpu().numpy()
+    assert np.linalg.norm(xs - rs) / np.linalg.norm(rs) <= (1e-11 if prec == 0 else 1e-4)
+    N2 = N + 1
+    band2 = torch.zeros((2 * K + 1) * N2, dtype=torch.float64, device="cuda")
+    b2 = torch.zeros(N2, dtype=torch.float64, device="cuda")
+    x2 = torch.zeros_like(b2)
+    assert _noalloc(sap, band2, N2, K, b2, x2, prec) == sap.SAP_ERR_INVALID_ARG
+    if s == 4 and K == 25:
+        N3 = 40000       # fits without the band copy (29.3 MB), not with it (37.4 MB)
+        n3 = (N3 + 31) // 32 * 32
+        assert n3 * 51 * 4 + 2 * n3 * 32 * 2 * 4 + (2 * N3 + 58) * 8 <= 1 << 25 < _need(N3, K, s)
+        band3 = torch.zeros(51 * N3, dtype=torch.float64, device="cuda")
+        b3 = torch.zeros(N3, dtype=torch.float64, device="cuda")
+        assert _noalloc(sap, band3, N3, K, b3, torch.zeros_like(b3), prec) == sap.SAP_ERR_INVALID_ARG

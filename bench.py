@@ -32,6 +32,9 @@ METRIC = "time to rel.res 1e-10 & HBM GB/s: FP32-precond vs FP64 SaP, fwd+adjoin
 # apply on the N=200000, K=50, P=50 workload (automatic segment count), from one
 # ncu capture of dram__bytes_read.sum + dram__bytes_write.sum of those launches
 TRAFFIC_SWEEPS = 232656896
+# DRAM bytes (read + write) of one k_band_lu launch (FP32), by (N, K, P), from an
+# ncu capture of the current kernel; a workload without a capture reports null
+TRAFFIC_LU = {}
 # P=None: picked by sap_autotune (measured refactor + solve over N / {16000 .. 1000}, 152, 304)
 # before the timed region; P_ref is the oracle's partition count in that case
 # (the autotuner's pick on GB300 when this table was written).
@@ -42,6 +45,8 @@ WORKLOADS = {
     "n200k_k200": dict(N=200000, K=200, d=1.0, P=None, P_ref=152, seed_cfg=3),
     "n200k_k400": dict(N=200000, K=400, d=1.0, P=None, P_ref=304, seed_cfg=3),
     "convdiff_400x250": dict(N=100000, K=250, d=None, P=32, seed_cfg=4, grid=(400, 250), variant="C"),
+    # the symmetric positive definite band at the C2 sizes, CG outer iteration (Sec. 3)
+    "n200k_k50_spd_cg": dict(N=200000, K=50, d=1.0, P=50, seed_cfg=2, spd=True, krylov="CG"),
 }
 # oracle work (multiply-adds of the factorisations, forward + adjoint) above
 # which the CPU baseline times a leading sample of the blocks and scales by rows
@@ -95,6 +100,8 @@ def make_inputs(w):
     if "grid" in w:
         band, N, K = G.convection_diffusion(*w["grid"])
         assert (N, K) == (w["N"], w["K"])
+    elif w.get("spd"):
+        band = G.dense_banded_spd(w["N"], w["K"], w["d"], seed)
     else:
         band = G.dense_banded(w["N"], w["K"], w["d"], seed)
     xt = G.x_true(w["N"], seed)
@@ -128,28 +135,69 @@ def oracle_sample(w, variant, band, xt, g):
             f"rows x{N / Ns:.2f}")
 
 
-def oracle_step(band, b, g, w, variant):
+def oracle_step(band, b, g, w, variant, omp=False):
     """One fwd + adjoint time-to-solution with the FP64 CPU oracle."""
     import oracle as O
     N, K, P = w["N"], w["K"], oracle_P(w)
     var = O.SAP_C if variant == "C" else O.SAP_D
-    s = O.Sap(band, N, K, P, var)
-    x, i1 = s.solve(b)
-    lam, i2, _ = O.solve_adjoint(band, N, K, g, P, var)
+    s = O.Sap(band, N, K, P, var, omp=omp)
+    if w.get("krylov") == "CG":     # symmetric A: the adjoint is the same system
+        x, i1 = s.solve_cg(b)
+        lam, i2 = s.solve_cg(g)
+    else:
+        x, i1 = s.solve(b)
+        sa = O.Sap(O.transpose_band(band, N, K), N, K, P, var, omp=omp)
+        lam, i2 = sa.solve(g)
     assert i1.status == O.OK and i2.status == O.OK
     return i1, i2
 
 
-def cpu_baseline(w, variant, band, xt, g, reps=1):
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.lower().startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        for ln in open("/proc/cpuinfo"):
+            if ln.lower().startswith(("model name", "cpu part", "hardware")):
+                return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def cpu_baseline(w, variant, band, xt, g, reps=3):
+    """The FP64 C oracle on the host cores: (i) single-threaded, the median of
+    reps runs; (ii) the same oracle built with OpenMP over the independent
+    blocks (bit-identical results), median of reps runs."""
+    import oracle as O
     ws, band_s, b_s, g_s, scale, what = oracle_sample(w, variant, band, xt, g)
     ts = []
     for _ in range(reps):
         t0 = time.perf_counter()
         oracle_step(band_s, b_s, g_s, ws, variant)
         ts.append((time.perf_counter() - t0) * 1e3 * scale)
-    return {"value": statistics.median(ts), "unit": "ms", "cores": 1, "kind": "oracle",
-            "sample": f"{what}, {reps} run(s) of factor + solve + adjoint solve "
-                      f"(single-threaded FP64 C oracle, SaP-{variant}, P = {oracle_P(w)} for the workload)"}
+    out = {"value": statistics.median(ts), "unit": "ms", "cores": 1, "kind": "oracle",
+           "sample": f"{what}, median of {reps} runs of factor + solve + adjoint solve "
+                     f"(single-threaded FP64 C oracle, SaP-{variant}, P = {oracle_P(w)} for the workload)",
+           "host_cpus": os.cpu_count(), "cpu_model": cpu_model()}
+    try:
+        tm = []
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            oracle_step(band_s, b_s, g_s, ws, variant, omp=True)
+            tm.append((time.perf_counter() - t0) * 1e3 * scale)
+        out["openmp"] = {"value": statistics.median(tm), "unit": "ms", "cores": O.omp_threads(),
+                         "sample": "the same runs with the oracle built with -fopenmp (per-block loops of the "
+                                   "factorisation and the applies in parallel; results bit-identical)"}
+    except Exception as e:  # noqa: BLE001
+        out["openmp"] = {"unavailable": str(e)[:200]}
+    return out
 
 
 def run_reference_batch(args):
@@ -232,11 +280,17 @@ def workload_config(args, w):
     if "grid" in w:
         kind = (f"2-D convection-diffusion {w['grid'][0]}x{w['grid'][1]} (5-point upwind, Peclet 10) as a dense "
                 f"band N={w['N']} K={w['K']}")
+    elif w.get("spd"):
+        kind = f"symmetric positive definite dense banded N={w['N']} K={w['K']} d={w['d']}"
     else:
         kind = f"dense banded N={w['N']} K={w['K']} d={w['d']}"
-    return {"workload": f"{kind} P={Ptxt} SaP-{args.variant}, "
-                        f"FP32 preconditioner + FP64 BiCGStab(2), fwd + adjoint to relres 1e-10 "
-                        f"(the two solved concurrently; the adjoint right-hand side is given)",
+    if w.get("krylov") == "CG":
+        how = ("FP32 preconditioner + FP64 preconditioned CG, fwd + adjoint to relres 1e-10 "
+               "(the two solved concurrently; the adjoint right-hand side is given)")
+    else:
+        how = ("FP32 preconditioner + FP64 BiCGStab(2), fwd + adjoint to relres 1e-10 "
+               "(the two solved concurrently; the adjoint right-hand side is given)")
+    return {"workload": f"{kind} P={Ptxt} SaP-{args.variant}, {how}",
             "N": w["N"], "K": w["K"], "P": Ptxt, "d": w["d"], "variant": f"SaP-{args.variant}",
             "l2": "flushed (512 MB write) before every timed step"}
 
@@ -308,8 +362,10 @@ def run_gpu(args):
         P, _, table = S.sap_autotune(band, N, K, b=b, variant=variant, precision=S.SAP_FP32)
         autotune = {"P": P, "ms_by_P_segments": {f"{p},{sg}": v for (p, sg), v in sorted(table.items())}}
 
+    krylov = S.SAP_KRYLOV_CG if w.get("krylov") == "CG" else S.SAP_KRYLOV_BICGSTAB2
+
     def make_handle(prec, var):
-        return S.sap_factor(band, N, K, P=P, variant=var, precision=prec)
+        return S.sap_factor(band, N, K, P=P, variant=var, precision=prec, krylov=krylov)
 
     # one step: refactor, then the forward and adjoint solves run concurrently
     # (sap_solve_pair; the adjoint right-hand side is given, independent of x);
@@ -360,7 +416,8 @@ def run_gpu(args):
     err_x = float(torch.linalg.norm(x - xt) / torch.linalg.norm(xt))
 
     # ---- phase split and the dominant kernel's live duration ----
-    t_lu = statistics.mean([a.t_lu_ms for a, _ in infos])
+    t_lu = statistics.mean([a.t_lu_ms for a, _ in infos])          # the block LU kernel alone
+    t_prep = statistics.mean([a.t_prep_ms for a, _ in infos])
     t_ul = statistics.mean([a.t_ul_ms for a, _ in infos])
     t_spk = statistics.mean([a.t_spk_ms for a, _ in infos])
     t_fwd = statistics.mean([a.t_solve_ms for a, _ in infos])
@@ -399,24 +456,25 @@ def run_gpu(args):
     t_apply = kernel_ms(lambda: S.sap_apply_preconditioner(h, b, z))
     W = 2 * K + 1
     hbm_peak, peak_kind = load_peaks()
-    lu_bytes = 8 * N * W + 4 * N * W               # read the FP64 band, write FP32 factors
+    lu_bytes = 4 * N * W + 4 * N * W               # read the FP32 band copy, write FP32 factors
     spmv_bytes = 8 * N * W + 16 * N
     sweep_bytes = 4 * N * W + 16 * N               # SaP-D apply: FP32 factors once + r, z
     apply_bytes = sweep_bytes * (2 if variant == S.SAP_C else 1)
     kernels = {
-        "band_lu": {"ms": t_lu, "bytes": lu_bytes, "GBs": lu_bytes / (t_lu * 1e6)},
+        "band_lu": {"ms": t_lu, "bytes": lu_bytes, "GBs": lu_bytes / (t_lu * 1e6),
+                    "TFLOPs_fp32": 2.0 * N * K * K / (t_lu * 1e9)},
         "spmv_fp64": {"ms": t_spmv, "bytes": spmv_bytes, "GBs": spmv_bytes / (t_spmv * 1e6),
                       "fp64_TFLOPs": 2 * N * W / (t_spmv * 1e9)},
         "block_solve_fp32": {"ms": t_sweep, "bytes": sweep_bytes, "GBs": sweep_bytes / (t_sweep * 1e6)},
         "apply_fp32": {"ms": t_apply, "bytes": apply_bytes, "GBs": apply_bytes / (t_apply * 1e6)},
     }
-    ach = kernels["block_solve_fp32"]["GBs"]
-    roofline = {"bound": "hbm",
+    ach_s = kernels["block_solve_fp32"]["GBs"]
+    sweep_line = {"bound": "hbm",
                 "kernel": ("k_block_solve (both triangular sweeps of every block, FP32)" if segs == 1 else
                            f"k_sweep + k_seg_correct{'' if sweep_launches == 4 else ' + k_seg_chain'} (both "
                            f"triangular sweeps of every block in {segs} segments, FP32; {sweep_launches} launches "
                            f"per apply)"),
-                "achieved": ach, "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak,
+                "achieved": ach_s, "peak": hbm_peak, "unit": "GB/s", "frac": ach_s / hbm_peak,
                 "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else
                 "fallback 6.8 TB/s",
                 # dram__bytes_read.sum + dram__bytes_write.sum of the sweep launches of one
@@ -427,35 +485,40 @@ def run_gpu(args):
                 "unit_of_launch": f"one preconditioner apply = {sweep_launches} sweep launch(es)",
                 "note": f"{segs} segment(s) per block, {segs * P} CTAs per pass; the 32-row chunk "
                         "recurrence is latency-bound"}
+    # the dominant kernel of the step: the block LU (largest share of the launch list)
+    ach = kernels["band_lu"]["GBs"]
+    roofline = {"bound": "hbm", "kernel": "k_band_lu (FP32 block LU of every block, one CTA per block)",
+                "achieved": ach, "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak,
+                "peak_kind": sweep_line["peak_kind"],
+                "traffic": TRAFFIC_LU.get((N, K, P)),
+                "algorithmic_bytes_per_launch": lu_bytes,
+                "unit_of_launch": f"one factorisation: read the FP32 band copy (4 N (2K+1) B), write the FP32 "
+                                  f"factors (4 N (2K+1) B); {2.0 * N * K * K:.3g} FP32 flops",
+                "duration_ms": t_lu,
+                "note": f"live duration from CUDA events around the k_band_lu launch on its stream, mean over the "
+                        f"timed steps; {P} CTAs (one per block) of a serial chain of {-(-(N // P) // 16)} "
+                        f"16-column panel steps: latency-bound, not bandwidth-bound"}
 
-    # ---- end to end through the public API with host buffers ----
+    # ---- end to end through the C ABI with host buffers: every step copies the band, b
+    # and g-bar in from page-locked host memory and x, lambda back, inside the library
+    # calls (sap_refactor_host, sap_solve_pair_host) ----
     band_h = torch.from_numpy(band_np).pin_memory()
     b_h = b.cpu().pin_memory()
     g_h = g.cpu().pin_memory()
     x_h = torch.empty_like(b_h).pin_memory()
     l_h = torch.empty_like(b_h).pin_memory()
-    band_d2 = torch.empty_like(band)
-    b_d2 = torch.empty_like(b)
-    g_d2 = torch.empty_like(g)
-    h2 = S.sap_factor(band_d2.copy_(band), N, K, P=P, variant=variant, precision=S.SAP_FP32)
-    xe = torch.empty_like(b)
-    le = torch.empty_like(b)
+    h2 = S.sap_factor_host(band_h, N, K, P=P, variant=variant, precision=S.SAP_FP32, krylov=krylov)
     e2e_times = []
     for k in range(args.warmup + args.steps):
         flush.fill_(3.0)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        band_d2.copy_(band_h, non_blocking=True)
-        b_d2.copy_(b_h, non_blocking=True)
-        g_d2.copy_(g_h, non_blocking=True)
-        S.sap_refactor(h2)
-        S.sap_solve_pair(h2, b_d2, g_d2, xe, le)
-        x_h.copy_(xe, non_blocking=True)
-        l_h.copy_(le, non_blocking=True)
-        torch.cuda.synchronize()
+        S.sap_refactor_host(h2, band_h)
+        S.sap_solve_pair_host(h2, b_h, g_h, x_h, l_h)
         if k >= args.warmup:
             e2e_times.append((time.perf_counter() - t0) * 1e3)
     e2e_ms = statistics.mean(e2e_times)
+    e2e_err = float(np.linalg.norm(x_h.numpy() - xt_np) / np.linalg.norm(xt_np))
     del h2
 
     # ---- comparison: FP64 SaP and the other variant (same protocol, fewer steps) ----
@@ -497,7 +560,9 @@ def run_gpu(args):
             "clocks": clocks,
             "e2e": {"value": e2e_ms, "unit": "ms",
                     "h2d_bytes_per_step": int(band_h.numel() * 8 + b_h.numel() * 8 + g_h.numel() * 8),
-                    "d2h_bytes_per_step": int(x_h.numel() * 8 + l_h.numel() * 8)},
+                    "d2h_bytes_per_step": int(x_h.numel() * 8 + l_h.numel() * 8),
+                    "api": "sap_refactor_host + sap_solve_pair_host (C ABI, host buffers, copies inside)",
+                    "err_x_vs_x_true": e2e_err},
             "gpu_launches": int(launches),
             "roofline": roofline,
             "cpu_baseline": cpu,
@@ -508,7 +573,8 @@ def run_gpu(args):
                        "matvecs_adj": i2.n_matvec, "restarts_fwd": i1.n_restarts,
                        "restarts_adj": i2.n_restarts, "relres_fwd": i1.relres,
                        "relres_adj": i2.relres, "err_x_vs_x_true": err_x, "n_boosted": i1.n_boosted,
-                       "t_lu_ms": t_lu, "t_ul_ms": t_ul, "t_spk_ms": t_spk, "t_fwd_solve_ms": t_fwd,
+                       "t_lu_ms": t_lu, "t_prep_ms": t_prep, "t_ul_ms": t_ul, "t_spk_ms": t_spk,
+                       "t_fwd_solve_ms": t_fwd, "sweep_roofline": sweep_line,
                        "t_adj_solve_ms": t_adj, "kernels": kernels, "compare": compare,
                        "paper_context_ms_k20x": {"SaP-D": 187.717, "SaP-C": 186.756,
                                                  "note": "fwd only, K20X, precision unstated"}},

@@ -66,6 +66,19 @@ typedef enum { SAP_D = 0, SAP_C = 1 } sap_variant_t;          /* Sec. 2.1.1 */
  * preconditioner is sensitive to it. */
 typedef enum { SAP_FP64 = 0, SAP_FP32 = 1, SAP_FP32_BF16TU = 2 } sap_precision_t;
 
+/* Outer Krylov iteration (Sec. 3): BiCGStab(2) with left preconditioning, or,
+ * for a symmetric positive definite A, the preconditioned conjugate gradient
+ * method (Saad 2003, Alg. 9.1) with the SaP factorisation as M.  CG counts
+ * whole iterations (one SpMV and one preconditioner application each; iters
+ * in sap_info_t is then an integer), exits on ||b - A x|| <= tol ||b|| by its
+ * recursive residual confirmed by the true one, and restarts from the
+ * current x when the confirmation fails.  SaP-D's M is SPD for SPD A;
+ * SaP-C's truncated-spike M need not be symmetric.  Both run device-driven
+ * (every launch gated on device flags, one captured CUDA graph per round: one
+ * BiCGStab(2) iteration or four CG steps) with one host readback per round;
+ * sap_solve_pair and the batch calls run either. */
+typedef enum { SAP_KRYLOV_BICGSTAB2 = 0, SAP_KRYLOV_CG = 1 } sap_krylov_t;
+
 typedef struct {
     int32_t P;            /* number of diagonal blocks, 1 <= P <= N (Sec. 3.1); 0 makes
                              sap_factor run sap_autotune over its default candidates
@@ -75,7 +88,7 @@ typedef struct {
     int32_t precision;    /* sap_precision_t: precision of factors, tips and sweeps;
                              the Krylov vectors, SpMV, dot products, the true
                              residual and the reduced systems Rbar_i are FP64 */
-    int32_t max_iters;    /* BiCGStab(2) iteration cap (default 500 if <= 0) */
+    int32_t max_iters;    /* Krylov iteration cap (default 500 if <= 0) */
     double tol;           /* target ||b - A x||_2 / ||b||_2 (default 1e-10 if <= 0) */
     double boost_eps;     /* relative pivot-boost threshold (Sec. 2.2): a pivot with
                              |p| < boost_eps * max|a_ij| becomes sign(p) times that
@@ -100,11 +113,11 @@ typedef struct {
                              to fill the SMs when P is small.  Values that leave a
                              range shorter than ceil(K/32) chunks of 32 rows are
                              lowered automatically. */
-    int32_t reserved0;    /* must be 0 */
+    int32_t krylov;       /* sap_krylov_t: the outer iteration */
 } sap_options_t;
 
 typedef struct {
-    double iters;         /* BiCGStab(2) iterations in quarters (Sec. 4.1.1) */
+    double iters;         /* BiCGStab(2) iterations in quarters (Sec. 4.1.1); CG: whole */
     double relres;        /* final true ||b - A x||_2 / ||b||_2 (FP64) */
     int64_t n_boosted;    /* boosted pivots in all LU and UL factorisations */
     int64_t n_matvec;     /* preconditioned matvecs M^{-1} A v of the iteration: 4 per
@@ -115,7 +128,7 @@ typedef struct {
                              failed behind the MR update (one SpMV + one apply each) */
     float t_factor_ms;    /* device time of the last factorisation (all phases) */
     float t_solve_ms;     /* device time of the Krylov phase of the last solve */
-    float t_lu_ms;        /* factor phase T_LU: block LU (and the boost-threshold pass) */
+    float t_lu_ms;        /* T_LU (Sec. 4.3.2 breakdown): the block LU kernel */
     float t_ul_ms;        /* SaP-C: block UL (top tiles only) */
     float t_spk_ms;       /* SaP-C T_SPK: spike tips V^(b)_i, W^(t)_{i+1}; where the K x K
                              matrices fit in shared memory one kernel per interface also
@@ -129,6 +142,9 @@ typedef struct {
     float t_rdcd_ms;      /* SaP-C T_LUrdcd: forming Rbar_i, its GEPP and explicit inverse
                              (0 where fused into the tip kernel, see t_spk_ms) */
     float t_kry_ms;       /* T_Kry: device time of the Krylov phase (= t_solve_ms) */
+    float t_prep_ms;      /* the rest of the LU phase (GB300 additions): the boost-threshold
+                             pass with the FP32 cast of the band, and the sweeps' per-chunk
+                             inverse / coupling and segment transfer matrices */
     int32_t reserved1;    /* 0 */
 } sap_info_t;
 
@@ -205,6 +221,22 @@ SAP_API sap_status_t sap_spmv(const double *band_dev, int64_t N, int32_t K, cons
  * copies x back into x_host (host <-> device copies included). */
 SAP_API sap_status_t sap_solve_host(sap_handle_t h, const double *b_host, double *x_host,
                             sap_info_t *info, cudaStream_t stream);
+
+/* Host-buffer forms of sap_factor, sap_refactor and sap_solve_pair (a GB300
+ * addition for callers whose data lives in host memory; page-locked buffers
+ * copy fastest).  sap_factor_host copies band_host ((2K+1) N float64, the
+ * layout above) into device memory that the handle owns and factors it;
+ * sap_refactor_host copies new band values into that memory and refactors
+ * (INVALID_ARG for a handle made by sap_factor, whose band is borrowed);
+ * sap_solve_pair_host copies b_host and g_host in, runs sap_solve_pair and
+ * copies x and lambda back (device staging of 4 N doubles allocated on the
+ * first call).  Each synchronises `stream`; errors as the device forms. */
+SAP_API sap_status_t sap_factor_host(const double *band_host, int64_t N, int32_t K,
+                                     const sap_options_t *opt, cudaStream_t stream, sap_handle_t *out);
+SAP_API sap_status_t sap_refactor_host(sap_handle_t h, const double *band_host, cudaStream_t stream);
+SAP_API sap_status_t sap_solve_pair_host(sap_handle_t h, const double *b_host, const double *g_host,
+                                         double *x_host, double *lam_host, sap_info_t *info_x,
+                                         sap_info_t *info_lambda, cudaStream_t stream);
 
 /* Inspection of the factorisation, for tests.  Copies into host buffers.
  *   sap_get_partition: off_host[P+1] block offsets.

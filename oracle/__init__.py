@@ -19,6 +19,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "sap_oracle.c")
 _LIB = os.path.join(_HERE, "_liboracle.so")
+_LIB_OMP = os.path.join(_HERE, "_liboracle_omp.so")
 
 OK, INVALID_ARG, OOM, NOT_CONVERGED, BREAKDOWN, SINGULAR = 0, 1, 2, 3, 4, 8
 SAP_D, SAP_C = 0, 1
@@ -26,24 +27,47 @@ FP64_EPS = 2.0 ** -53
 FP32_EPS = 2.0 ** -24
 
 
-def build(force: bool = False) -> str:
+def build(force: bool = False, omp: bool = False) -> str:
     """Compile the oracle with gcc (plain -O2, no fast-math, no FMA
-    contraction so that every operation rounds as written)."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared",
-                               "-o", tmp, _SRC, "-lm"])
-        os.replace(tmp, _LIB)
-    return _LIB
+    contraction so that every operation rounds as written).  omp=True builds
+    the OpenMP variant (the per-block loops in parallel, same arithmetic)."""
+    out = _LIB_OMP if omp else _LIB
+    if force or not os.path.exists(out) or os.path.getmtime(out) < os.path.getmtime(_SRC):
+        tmp = out + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared"] +
+                              (["-fopenmp"] if omp else []) + ["-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, out)
+    return out
 
 
 _lib = None
+_lib_omp = None
 
 
-def _load():
-    global _lib
+def _load(omp: bool = False):
+    global _lib, _lib_omp
+    if omp:
+        if _lib_omp is None:
+            _lib_omp = _declare(C.CDLL(build(omp=True)))
+        return _lib_omp
     if _lib is None:
-        lib = C.CDLL(build())
+        _lib = _declare(C.CDLL(build()))
+    return _lib
+
+
+def omp_threads() -> int:
+    """Threads the OpenMP variant uses (its OMP_NUM_THREADS / the host's cores)."""
+    lib = _load(omp=True)
+    try:
+        f = lib.omp_get_max_threads
+    except AttributeError:
+        return 1
+    f.restype = C.c_int
+    return int(f())
+
+
+def _declare(lib):
+    if True:
         i64, i32, dbl, vp = C.c_int64, C.c_int32, C.c_double, C.c_void_p
         P = C.POINTER
         lib.orc_partition.argtypes = [i64, i32, P(i64)]
@@ -75,8 +99,7 @@ def _load():
         lib.orc_dense_getrf.restype = C.c_int
         lib.orc_dense_getrs.argtypes = [P(dbl), C.c_int, P(i32), P(dbl)]
         lib.orc_reduced_solve.argtypes = [vp, C.c_int, P(dbl), P(dbl), P(dbl), P(dbl)]
-        _lib = lib
-    return _lib
+    return lib
 
 
 def _d(a: np.ndarray):
@@ -160,7 +183,8 @@ class Sap:
     tau = boost_eps * max |a_ij| over the band (default: FP64 unit roundoff)."""
 
     def __init__(self, band: np.ndarray, N: int, K: int, P: int, variant: int = SAP_D,
-                 boost_eps: float | None = None, tau: float | None = None):
+                 boost_eps: float | None = None, tau: float | None = None, omp: bool = False):
+        self._L = _load(omp)
         self.band = np.ascontiguousarray(band, dtype=np.float64)
         self.N, self.K, self.P, self.variant = int(N), int(K), int(P), int(variant)
         if tau is None:
@@ -168,24 +192,24 @@ class Sap:
             tau = eps * band_absmax(self.band, N, K)
         self.tau = float(tau)
         h = C.c_void_p()
-        st = _load().orc_factor(_d(self.band), N, K, P, variant, self.tau, C.byref(h))
+        st = self._L.orc_factor(_d(self.band), N, K, P, variant, self.tau, C.byref(h))
         if st != OK:
             raise ValueError(f"oracle factor failed with status {st}")
         self._h = h
 
     def __del__(self):
-        if getattr(self, "_h", None) is not None and _lib is not None:
-            _lib.orc_free(self._h)
+        if getattr(self, "_h", None) is not None and getattr(self, "_L", None) is not None:
+            self._L.orc_free(self._h)
             self._h = None
 
     @property
     def n_boosted(self) -> int:
-        return int(_load().orc_n_boosted(self._h))
+        return int(self._L.orc_n_boosted(self._h))
 
     @property
     def offsets(self) -> np.ndarray:
         off = np.zeros(self.P + 1, dtype=np.int64)
-        _load().orc_offsets(self._h, off.ctypes.data_as(C.POINTER(C.c_int64)))
+        self._L.orc_offsets(self._h, off.ctypes.data_as(C.POINTER(C.c_int64)))
         return off
 
     def block(self, i: int, which: int = 0) -> np.ndarray:
@@ -193,7 +217,7 @@ class Sap:
         off = self.offsets
         n = int(off[i + 1] - off[i])
         out = np.empty((n, 2 * self.K + 1))
-        if _load().orc_get_block(self._h, i, which, _d(out)) != OK:
+        if self._L.orc_get_block(self._h, i, which, _d(out)) != OK:
             raise ValueError("no such block")
         return out
 
@@ -201,7 +225,7 @@ class Sap:
         """K x K matrix of interface i: 'B', 'C', 'V', 'W' or 'R' (unfactored Rbar)."""
         code = {"B": 0, "C": 1, "V": 2, "W": 3, "R": 4}[which]
         out = np.empty((self.K, self.K))
-        if _load().orc_get_interface(self._h, i, code, _d(out)) != OK:
+        if self._L.orc_get_interface(self._h, i, code, _d(out)) != OK:
             raise ValueError("no such interface")
         return out
 
@@ -210,13 +234,13 @@ class Sap:
         gb = np.ascontiguousarray(gb, dtype=np.float64)
         gt = np.ascontiguousarray(gt, dtype=np.float64)
         xb, xt = np.empty(self.K), np.empty(self.K)
-        _load().orc_reduced_solve(self._h, i, _d(gb), _d(gt), _d(xb), _d(xt))
+        self._L.orc_reduced_solve(self._h, i, _d(gb), _d(gt), _d(xb), _d(xt))
         return xb, xt
 
     def apply(self, r: np.ndarray) -> np.ndarray:
         r = np.ascontiguousarray(r, dtype=np.float64)
         z = np.empty(self.N)
-        _load().orc_apply(self._h, _d(r), _d(z))
+        self._L.orc_apply(self._h, _d(r), _d(z))
         return z
 
     def solve(self, b: np.ndarray, tol: float = 1e-10, max_iters: int = 500,
@@ -226,7 +250,7 @@ class Sap:
         info = _Info()
         cap = 4 * max_iters + 8
         tr = np.zeros(4 * cap) if trace else None
-        st = _load().orc_bicgstab2(self._h, _d(self.band), _d(b), _d(x), tol, max_iters,
+        st = self._L.orc_bicgstab2(self._h, _d(self.band), _d(b), _d(x), tol, max_iters,
                                    C.byref(info), _d(tr) if trace else None, cap)
         t = None
         if trace:
@@ -244,7 +268,7 @@ class Sap:
         info = _Info()
         cap = max_iters + 2
         tr = np.zeros(4 * cap) if trace else None
-        st = _load().orc_pcg(self._h, _d(self.band), _d(b), _d(x), tol, max_iters,
+        st = self._L.orc_pcg(self._h, _d(self.band), _d(b), _d(x), tol, max_iters,
                              C.byref(info), _d(tr) if trace else None, cap)
         t = None
         if trace:

@@ -8,9 +8,14 @@
  * smoke check and the benchmark's CPU-baseline leg may load it; the product
  * path never does.  It shares no code, header or helper with the CUDA path.
  *
- * Everything is double precision, single threaded, written as plain loops in
- * the order the paper states each step.  Where the paper is silent the
- * reading used is stated next to the code.
+ * Everything is double precision, written as plain loops in the order the
+ * paper states each step, and single threaded as built for the tests.  The
+ * loops over the independent diagonal blocks carry OpenMP pragmas: a second
+ * build with -fopenmp (the CPU baseline's multi-core leg) runs the blocks in
+ * parallel with every block's arithmetic unchanged, so its results are bit
+ * for bit those of the single-threaded build; the vector reductions of the
+ * Krylov loops stay sequential.  Where the paper is silent the reading used
+ * is stated next to the code.
  *
  * Conventions
  *   - Band storage (Section 3.1, "Matrix storage"): an N x (2K+1) array in
@@ -293,21 +298,29 @@ int orc_factor(const double *band, int64_t N, int K, int P, int variant, double 
         if (n < 1 || (variant == 1 && P > 1 && n < 2 * (int64_t)K)) { orc_free(h); return ORC_ERR_INVALID_ARG; }
     }
     int W = 2 * K + 1;
+    int64_t nbst = 0;
     h->lu = (double **)xcalloc(P, sizeof(double *));
+    /* the blocks are independent (Section 2.1); built with -fopenmp the loops
+     * over blocks below run in parallel, each block's arithmetic unchanged */
+#pragma omp parallel for schedule(dynamic, 1) reduction(+ : nbst)
     for (int i = 0; i < P; ++i) {
         int64_t n = h->off[i + 1] - h->off[i];
         h->lu[i] = (double *)xcalloc((size_t)(n * W), sizeof(double));
         load_block(band, N, K, h->off[i], n, h->lu[i]);
-        h->n_boosted += orc_block_lu(h->lu[i], n, K, tau);
+        nbst += orc_block_lu(h->lu[i], n, K, tau);
     }
+    h->n_boosted += nbst;
     if (variant == 1 && P > 1) {
         h->ul = (double **)xcalloc(P, sizeof(double *));
+        nbst = 0;
+#pragma omp parallel for schedule(dynamic, 1) reduction(+ : nbst)
         for (int i = 0; i < P; ++i) {
             int64_t n = h->off[i + 1] - h->off[i];
             h->ul[i] = (double *)xcalloc((size_t)(n * W), sizeof(double));
             load_block(band, N, K, h->off[i], n, h->ul[i]);
-            h->n_boosted += orc_block_ul(h->ul[i], n, K, tau);
+            nbst += orc_block_ul(h->ul[i], n, K, tau);
         }
+        h->n_boosted += nbst;
         h->B = (double **)xcalloc(P - 1, sizeof(double *));
         h->C = (double **)xcalloc(P - 1, sizeof(double *));
         h->V = (double **)xcalloc(P - 1, sizeof(double *));
@@ -315,7 +328,9 @@ int orc_factor(const double *band, int64_t N, int K, int P, int variant, double 
         h->R = (double **)xcalloc(P - 1, sizeof(double *));
         h->R0 = (double **)xcalloc(P - 1, sizeof(double *));
         h->piv = (int32_t **)xcalloc(P - 1, sizeof(int32_t *));
-        for (int i = 0; i + 1 < P; ++i) {
+        int singular = 0;
+#pragma omp parallel for schedule(dynamic, 1) reduction(| : singular)
+        for (int i = 0; i < P - 1; ++i) {
             int64_t s = h->off[i + 1];
             h->B[i] = (double *)xcalloc((size_t)K * K, sizeof(double));
             h->C[i] = (double *)xcalloc((size_t)K * K, sizeof(double));
@@ -337,10 +352,9 @@ int orc_factor(const double *band, int64_t N, int K, int P, int variant, double 
                     h->R[i][r * K + c] = acc;
                     h->R0[i][r * K + c] = acc;
                 }
-            if (orc_dense_getrf(h->R[i], K, h->piv[i])) { /* exact singularity */
-                orc_free(h); return ORC_ERR_SINGULAR;
-            }
+            if (orc_dense_getrf(h->R[i], K, h->piv[i])) singular = 1;   /* exact singularity */
         }
+        if (singular) { orc_free(h); return ORC_ERR_SINGULAR; }
     }
     *out = h;
     return ORC_OK;
@@ -397,17 +411,20 @@ void orc_apply(const orc_sap *h, const double *r, double *z)
     int64_t N = h->N;
     int K = h->K, P = h->P;
     memcpy(z, r, (size_t)N * sizeof(double));
+#pragma omp parallel for schedule(dynamic, 1)
     for (int i = 0; i < P; ++i)
         block_solve(h->lu[i], h->off[i + 1] - h->off[i], K, z + h->off[i]);
     if (h->variant != 1 || P == 1) return;
     double *xt = (double *)xcalloc((size_t)(P - 1) * K, sizeof(double));
     double *xb = (double *)xcalloc((size_t)(P - 1) * K, sizeof(double));
-    for (int i = 0; i + 1 < P; ++i) {
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int i = 0; i < P - 1; ++i) {
         int64_t s = h->off[i + 1];
         orc_reduced_solve(h, i, z + s - K, z + s, xb + (int64_t)i * K, xt + (int64_t)i * K);
     }
     /* purification: fresh right-hand sides, then the block solves again */
     memcpy(z, r, (size_t)N * sizeof(double));
+#pragma omp parallel for schedule(dynamic, 1)
     for (int i = 0; i < P; ++i) {
         int64_t s = h->off[i], n = h->off[i + 1] - s;
         double *zi = z + s;

@@ -23,6 +23,7 @@ SAP_OK, SAP_ERR_INVALID_ARG, SAP_ERR_OOM, SAP_ERR_NOT_CONVERGED, SAP_ERR_BREAKDO
 SAP_ERR_TIMEOUT, SAP_ERR_CUDA, SAP_ERR_NOT_IMPLEMENTED, SAP_ERR_SINGULAR = 5, 6, 7, 8
 SAP_D, SAP_C = 0, 1
 SAP_FP64, SAP_FP32, SAP_FP32_BF16TU = 0, 1, 2
+SAP_KRYLOV_BICGSTAB2, SAP_KRYLOV_CG = 0, 1
 
 
 class SapError(RuntimeError):
@@ -34,7 +35,7 @@ class SapError(RuntimeError):
 class sap_options_t(C.Structure):
     _fields_ = [("P", C.c_int32), ("variant", C.c_int32), ("precision", C.c_int32),
                 ("max_iters", C.c_int32), ("tol", C.c_double), ("boost_eps", C.c_double),
-                ("spin_limit", C.c_int64), ("segments", C.c_int32), ("reserved0", C.c_int32)]
+                ("spin_limit", C.c_int64), ("segments", C.c_int32), ("krylov", C.c_int32)]
 
 
 class sap_info_t(C.Structure):
@@ -44,7 +45,7 @@ class sap_info_t(C.Structure):
                 ("t_ul_ms", C.c_float), ("t_spk_ms", C.c_float), ("segments", C.c_int32),
                 ("graphed", C.c_int32), ("tc_update", C.c_int32), ("P", C.c_int32),
                 ("t_bc_ms", C.c_float), ("t_rdcd_ms", C.c_float), ("t_kry_ms", C.c_float),
-                ("reserved1", C.c_int32)]
+                ("t_prep_ms", C.c_float), ("reserved1", C.c_int32)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -67,6 +68,9 @@ def _load():
         "sap_apply_preconditioner": (C.c_int, [vp, vp, vp, i32, vp]),
         "sap_spmv": (C.c_int, [vp, i64, i32, vp, vp, i32, vp]),
         "sap_solve_host": (C.c_int, [vp, vp, vp, P(sap_info_t), vp]),
+        "sap_factor_host": (C.c_int, [vp, i64, i32, P(sap_options_t), vp, P(vp)]),
+        "sap_refactor_host": (C.c_int, [vp, vp, vp]),
+        "sap_solve_pair_host": (C.c_int, [vp, vp, vp, vp, vp, P(sap_info_t), P(sap_info_t), vp]),
         "sap_get_partition": (C.c_int, [vp, vp]),
         "sap_get_block_lu": (C.c_int, [vp, i32, vp, vp]),
         "sap_get_interface": (C.c_int, [vp, i32, i32, i32, vp, vp]),
@@ -204,9 +208,40 @@ def sap_solve_host(h: Handle, b_host, x_host, stream=None, raise_on_error: bool 
     return x_host, info, st
 
 
+def _hptr(t) -> int:
+    if not (t.device.type == "cpu" and t.dtype == torch.float64 and t.is_contiguous()):
+        raise ValueError("expected a contiguous CPU float64 tensor")
+    return t.data_ptr()
+
+
+def sap_factor_host(band_host: torch.Tensor, N: int, K: int, opts: sap_options_t | None = None, stream=None,
+                    **kw) -> Handle:
+    """Factor from a host band; the handle owns the device copy."""
+    opts = opts or sap_default_options(**kw)
+    out = C.c_void_p()
+    _check(_lib.sap_factor_host(_hptr(band_host), N, K, C.byref(opts), _stream(stream), C.byref(out)),
+           "sap_factor_host")
+    return Handle(out.value, band_host, N, K, opts)
+
+
+def sap_refactor_host(h: Handle, band_host: torch.Tensor, stream=None) -> None:
+    _check(_lib.sap_refactor_host(h.ptr, _hptr(band_host), _stream(stream)), "sap_refactor_host")
+
+
+def sap_solve_pair_host(h: Handle, b_host, g_host, x_host, lam_host, stream=None, raise_on_error: bool = True):
+    """x = A^{-1} b and lambda = A^{-T} g with host buffers, copies inside the call."""
+    ix, il = sap_info_t(), sap_info_t()
+    st = _lib.sap_solve_pair_host(h.ptr, _hptr(b_host), _hptr(g_host), _hptr(x_host), _hptr(lam_host),
+                                  C.byref(ix), C.byref(il), _stream(stream))
+    if raise_on_error:
+        _check(st, "sap_solve_pair_host")
+    return x_host, lam_host, ix, il, st
+
+
 def sap_grad_band(h: Handle, lam: torch.Tensor, x: torch.Tensor, out: torch.Tensor | None = None,
                   stream=None) -> torch.Tensor:
-    out = torch.empty_like(h.band) if out is None else out
+    if out is None:
+        out = torch.empty(h.band.numel(), dtype=torch.float64, device=lam.device)
     _check(_lib.sap_grad_band(h.ptr, _ptr(lam), _ptr(x), _ptr(out), _stream(stream)), "sap_grad_band")
     return out
 

@@ -424,6 +424,141 @@ __global__ void k_init_scalars(double* S) {
     S[S_OMEGA] = 1.0;
   }
 }
+
+// ---- preconditioned conjugate gradient (Sec. 3: the outer iteration for a
+// symmetric positive definite A; Saad 2003, Algorithm 9.1) ----
+// Every kernel carries the gate of its KrylovDev (see GateMode).
+// p = z and (r, z) -> S[S_RHO0]: the start (and a restart) of the iteration
+__global__ void __launch_bounds__(RT) k_cg_start(const double* __restrict__ r, const double* __restrict__ z,
+                                                 double* __restrict__ p, int64_t n, KrylovDev kd) {
+  if (kr_skip(kd)) return;
+  double v[1] = {0.0};
+  GRID_LOOP(i) {
+    const double zi = z[i];
+    p[i] = zi;
+    v[0] += r[i] * zi;
+  }
+  double red[1];
+  if (reduce_last<1>(v, kd, red) && threadIdx.x == 0) kd.S[S_RHO0] = red[0];
+}
+
+// alpha = (r, z) / (p, A p) -> S[S_ALPHA]; (p, A p) = 0 flags a breakdown
+__global__ void __launch_bounds__(RT) k_cg_alpha(const double* __restrict__ p, const double* __restrict__ q,
+                                                 int64_t n, KrylovDev kd) {
+  if (kr_skip(kd)) return;
+  double v[1] = {0.0};
+  GRID_LOOP(i) v[0] += p[i] * q[i];
+  double red[1];
+  if (reduce_last<1>(v, kd, red) && threadIdx.x == 0) {
+    double* S = kd.S;
+    if (red[0] == 0.0) {
+      S[S_BREAK] = 1.0;
+      S[S_ALPHA] = 0.0;
+    } else {
+      S[S_ALPHA] = S[S_RHO0] / red[0];
+    }
+  }
+}
+
+// x += alpha p, r -= alpha A p, ||r||^2 -> S[S_RN2]
+__global__ void __launch_bounds__(RT) k_cg_xr(double* __restrict__ x, double* __restrict__ r,
+                                              const double* __restrict__ p, const double* __restrict__ q, int64_t n,
+                                              KrylovDev kd) {
+  if (kr_skip(kd)) return;
+  const double a = kd.S[S_ALPHA];
+  double v[1] = {0.0};
+  GRID_LOOP(i) {
+    x[i] += a * p[i];
+    const double ri = r[i] - a * q[i];
+    r[i] = ri;
+    v[0] += ri * ri;
+  }
+  double red[1];
+  if (reduce_last<1>(v, kd, red) && threadIdx.x == 0) kd.S[S_RN2] = red[0];
+}
+
+// beta = (r, z) / (r, z)_previous -> S[S_BETA], the new (r, z) -> S[S_RHO0];
+// a zero previous (r, z) flags a breakdown
+__global__ void __launch_bounds__(RT) k_cg_beta(const double* __restrict__ r, const double* __restrict__ z,
+                                                int64_t n, KrylovDev kd) {
+  if (kr_skip(kd)) return;
+  double v[1] = {0.0};
+  GRID_LOOP(i) v[0] += r[i] * z[i];
+  double red[1];
+  if (reduce_last<1>(v, kd, red) && threadIdx.x == 0) {
+    double* S = kd.S;
+    if (S[S_RHO0] == 0.0) {
+      S[S_BREAK] = 1.0;
+      S[S_BETA] = 0.0;
+    } else {
+      S[S_BETA] = red[0] / S[S_RHO0];
+    }
+    S[S_RHO0] = red[0];
+  }
+}
+
+// p = z + beta p
+__global__ void __launch_bounds__(RT) k_cg_p(const double* __restrict__ z, double* __restrict__ p, int64_t n,
+                                             KrylovDev kd) {
+  if (kr_skip(kd)) return;
+  const double bt = kd.S[S_BETA];
+  GRID_LOOP(i) p[i] = z[i] + bt * p[i];
+}
+
+// dst = src (the restart's r = b - A x)
+__global__ void __launch_bounds__(RT) k_copy_gated(const double* __restrict__ src, double* __restrict__ dst,
+                                                   int64_t n, KrylovDev kd) {
+  if (kr_skip(kd)) return;
+  GRID_LOOP(i) dst[i] = src[i];
+}
+
+// CG exit test, first half (after x += alpha p, r -= alpha A p): unless
+// finished, a breakdown finishes the solve, else flag a true-residual check
+// when the recursive residual satisfies ||r|| <= tol ||b||.
+__global__ void k_cg_check(KrylovDev kd, double tol) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  int* f = kd.flags;
+  double* S = kd.S;
+  if (f[F_DONE]) return;
+  f[F_REPLACE] = 0;
+  if (S[S_BREAK] != 0.0) {
+    f[F_DONE] = 1;
+    f[F_STATUS] = SAP_ERR_BREAKDOWN;
+    S[S_QUART] = S[S_IT] + 1.0;
+    return;
+  }
+  f[F_CHECK] = (sqrt(S[S_RN2]) <= tol * sqrt(S[S_BN2])) ? 1 : 0;
+}
+
+// Second half, after the gated true residual: the step is complete; accept,
+// or flag the restart from x (r = b - A x, z = M^{-1} r, p = z) when the
+// confirmation failed; the iteration cap finishes the solve.
+__global__ void k_cg_decide(KrylovDev kd, double tol, int max_iters) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  int* f = kd.flags;
+  double* S = kd.S;
+  if (f[F_DONE]) return;
+  S[S_IT] += 1.0;
+  if (f[F_CHECK]) {
+    f[F_CHECK] = 0;
+    const double rel = sqrt(S[S_TN2]) / sqrt(S[S_BN2]);
+    S[S_RELRES] = rel;
+    if (rel <= tol) {
+      f[F_DONE] = 1;
+      f[F_STATUS] = SAP_OK;
+      S[S_QUART] = S[S_IT];
+      return;
+    }
+    f[F_REPLACE] = 1;
+    f[F_RESTARTS] += 1;
+  }
+  if (S[S_IT] >= (double)max_iters) {
+    f[F_DONE] = 1;
+    f[F_STATUS] = SAP_ERR_NOT_CONVERGED;
+    S[S_QUART] = S[S_IT];
+  }
+}
+
 }  // namespace
 
 int krylov_grid(int64_t n) {
@@ -517,6 +652,48 @@ __global__ void k_wait_selftest(int limit, int* err) {
 cudaError_t launch_wait_selftest(int limit, int* err, cudaStream_t s) {
   count_launches(1);
   k_wait_selftest<<<1, 32, 0, s>>>(limit, err);
+  return cudaGetLastError();
+}
+
+cudaError_t kr_cg_start(const double* r, const double* z, double* p, int64_t n, KrylovDev kd, cudaStream_t s) {
+  count_launches(1);
+  k_cg_start<<<krylov_grid(n), RT, 0, s>>>(r, z, p, n, kd);
+  return cudaGetLastError();
+}
+cudaError_t kr_cg_alpha(const double* p, const double* q, int64_t n, KrylovDev kd, cudaStream_t s) {
+  count_launches(1);
+  k_cg_alpha<<<krylov_grid(n), RT, 0, s>>>(p, q, n, kd);
+  return cudaGetLastError();
+}
+cudaError_t kr_cg_xr(double* x, double* r, const double* p, const double* q, int64_t n, KrylovDev kd,
+                     cudaStream_t s) {
+  count_launches(1);
+  k_cg_xr<<<krylov_grid(n), RT, 0, s>>>(x, r, p, q, n, kd);
+  return cudaGetLastError();
+}
+cudaError_t kr_cg_beta(const double* r, const double* z, int64_t n, KrylovDev kd, cudaStream_t s) {
+  count_launches(1);
+  k_cg_beta<<<krylov_grid(n), RT, 0, s>>>(r, z, n, kd);
+  return cudaGetLastError();
+}
+cudaError_t kr_cg_p(const double* z, double* p, int64_t n, KrylovDev kd, cudaStream_t s) {
+  count_launches(1);
+  k_cg_p<<<krylov_grid(n), RT, 0, s>>>(z, p, n, kd);
+  return cudaGetLastError();
+}
+cudaError_t kr_copy(const double* src, double* dst, int64_t n, KrylovDev kd, cudaStream_t s) {
+  count_launches(1);
+  k_copy_gated<<<krylov_grid(n), RT, 0, s>>>(src, dst, n, kd);
+  return cudaGetLastError();
+}
+cudaError_t kr_cg_check(KrylovDev kd, double tol, cudaStream_t s) {
+  count_launches(1);
+  k_cg_check<<<1, 32, 0, s>>>(kd, tol);
+  return cudaGetLastError();
+}
+cudaError_t kr_cg_decide(KrylovDev kd, double tol, int max_iters, cudaStream_t s) {
+  count_launches(1);
+  k_cg_decide<<<1, 32, 0, s>>>(kd, tol, max_iters);
   return cudaGetLastError();
 }
 

@@ -49,6 +49,22 @@ cudaError_t kr_exit_check(KrylovDev kd, double tol, double qoff, cudaStream_t s)
 // Second half, after the gated true residual: accept (finish) or flag the
 // residual replacement; qoff == 1 also completes the outer iteration.
 cudaError_t kr_exit_decide(KrylovDev kd, double tol, double qoff, cudaStream_t s);
+// Preconditioned CG (Saad, Alg. 9.1), each launch gated by kd.gmode: p = z
+// with (r, z) -> S_RHO0; alpha = S_RHO0 / (p, q); x += alpha p, r -= alpha q
+// with ||r||^2 -> S_RN2; beta = (r, z) / S_RHO0 (S_RHO0 updated);
+// p = z + beta p.  A zero denominator sets S_BREAK.  Exit test in two halves
+// around the gated true residual (kr_cg_check, kr_cg_decide: whole steps,
+// restart flag on a failed confirmation, the iteration cap on the device);
+// kr_copy: dst = src, gated.
+cudaError_t kr_cg_start(const double* r, const double* z, double* p, int64_t n, KrylovDev kd, cudaStream_t s);
+cudaError_t kr_cg_alpha(const double* p, const double* q, int64_t n, KrylovDev kd, cudaStream_t s);
+cudaError_t kr_cg_xr(double* x, double* r, const double* p, const double* q, int64_t n, KrylovDev kd,
+                     cudaStream_t s);
+cudaError_t kr_cg_beta(const double* r, const double* z, int64_t n, KrylovDev kd, cudaStream_t s);
+cudaError_t kr_cg_p(const double* z, double* p, int64_t n, KrylovDev kd, cudaStream_t s);
+cudaError_t kr_copy(const double* src, double* dst, int64_t n, KrylovDev kd, cudaStream_t s);
+cudaError_t kr_cg_check(KrylovDev kd, double tol, cudaStream_t s);
+cudaError_t kr_cg_decide(KrylovDev kd, double tol, int max_iters, cudaStream_t s);
 // restart after a residual replacement (gated on the replacement flag)
 cudaError_t kr_restart(const double* r0, double* rt, double* u0, int64_t n, KrylovDev kd, cudaStream_t s);
 

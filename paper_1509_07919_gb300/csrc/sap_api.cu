@@ -131,8 +131,11 @@ struct sap_handle {
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   cudaEvent_t evp[4] = {nullptr, nullptr, nullptr, nullptr};
   cudaEvent_t ev_rd = nullptr;   // SaP-C: between the spike tips and the reduced systems
-  float t_factor_ms = 0.f, t_lu_ms = 0.f, t_ul_ms = 0.f, t_spk_ms = 0.f, t_rdcd_ms = 0.f;
+  cudaEvent_t ev_lu[2] = {nullptr, nullptr};   // around the block LU kernel
+  float t_factor_ms = 0.f, t_lu_ms = 0.f, t_ul_ms = 0.f, t_spk_ms = 0.f, t_rdcd_ms = 0.f, t_prep_ms = 0.f;
+  double* band_owned = nullptr;  // the band, when the handle was made from host memory (sap_factor_host)
   double* host_stage = nullptr;  // 2 N doubles for sap_solve_host, allocated on first use
+  double* host_stage4 = nullptr; // 4 N doubles for sap_solve_pair_host, allocated on first use
   std::unique_ptr<SolverBase> impl;
   ~sap_handle() {
     for (cudaGraphExec_t g : gexec)
@@ -163,6 +166,8 @@ struct sap_handle {
     for (cudaEvent_t e : evp)
       if (e) cudaEventDestroy(e);
     if (ev_rd) cudaEventDestroy(ev_rd);
+    for (cudaEvent_t e : ev_lu)
+      if (e) cudaEventDestroy(e);
   }
 };
 
@@ -354,8 +359,10 @@ struct Solver : SolverBase {
   sap_status_t factor(cudaStream_t s) override {
     const Layout& L = h->L;
     TRY(factor_pre(s));
+    CK(cudaEventRecord(h->ev_lu[0], s));
     CK(launch_factor_lu<T>(band_in_T(), L.N, L.K, L.P, h->d, h->absmax, h->opt.boost_eps, f.F, h->n_boosted,
                            wlu, tc(), f.err, s));
+    CK(cudaEventRecord(h->ev_lu[1], s));
     return factor_post(s);
   }
 
@@ -560,7 +567,8 @@ sap_status_t check_options(const sap_options_t* o, int64_t N, int K) {
   if (o->variant != SAP_D && o->variant != SAP_C) return SAP_ERR_INVALID_ARG;
   if (o->precision != SAP_FP64 && o->precision != SAP_FP32 && o->precision != SAP_FP32_BF16TU)
     return SAP_ERR_INVALID_ARG;
-  if (o->segments < 0 || o->reserved0 != 0) return SAP_ERR_INVALID_ARG;
+  if (o->segments < 0) return SAP_ERR_INVALID_ARG;
+  if (o->krylov != SAP_KRYLOV_BICGSTAB2 && o->krylov != SAP_KRYLOV_CG) return SAP_ERR_INVALID_ARG;
   return SAP_OK;
 }
 
@@ -595,16 +603,21 @@ sap_status_t ensure_ws2(sap_handle* h) {
   return SAP_OK;
 }
 
-// One BiCGStab(2) solve, split at its host synchronisation points so that a
-// batch of solves can share them: begin() (setup, scalar readback), then
-// rounds (one outer iteration each, flag readback), then finish().  Between
+// One Krylov solve (BiCGStab(2), or preconditioned CG when the handle's
+// krylov option asks for it), split at its host synchronisation points so
+// that a batch of solves can share them: begin() (setup, scalar readback),
+// then rounds (one outer BiCGStab(2) iteration, or kCgSteps CG steps, each;
+// flag readback), then finish().  Between
 // two steps the caller synchronises the handle's stream.  All work runs on
 // the handle's internal stream (stream capture needs a non-legacy stream),
 // ordered after the caller's stream at begin() and before it at the end of
 // finish().
+constexpr int kCgSteps = 4;   // CG steps per captured round
+
 struct KrylovRun {
   sap_handle* h = nullptr;
   bool tr = false;
+  bool cg = false;       // preconditioned CG instead of BiCGStab(2)
   cudaStream_t user = nullptr, s = nullptr;
   const double* b_user = nullptr;
   double* x_user = nullptr;
@@ -618,6 +631,7 @@ struct KrylovRun {
   int* hf = nullptr;
   cudaEvent_t evf = nullptr, evj = nullptr, ev0 = nullptr, ev1 = nullptr;
   Gate gA, gC, gR;
+  KrylovDev kr, kk;      // gated on the restart flag / on its absence (CG)
   double tol = 0.0, bn = 0.0;
   sap_info_t inf{};
   sap_status_t status = SAP_ERR_NOT_CONVERGED;
@@ -627,6 +641,7 @@ struct KrylovRun {
 
   sap_status_t init(sap_handle* hh, const double* bu, double* xu, bool transposed, cudaStream_t us, int ws = 0) {
     h = hh; tr = transposed; user = us; b_user = bu; x_user = xu;
+    cg = h->opt.krylov == SAP_KRYLOV_CG;
     TRY(ensure_stream(h));
     N = h->L.N;
     if (ws == 0) {
@@ -653,6 +668,10 @@ struct KrylovRun {
     ka.gmode = G_ACTIVE;
     kc = kd;
     kc.gmode = G_CHECK;
+    kr = kd;
+    kr.gmode = G_REPLACE;
+    kk = kd;
+    kk.gmode = G_KEEP;
     gA.flags = gC.flags = gR.flags = flags;
     gA.mode = G_ACTIVE;
     gC.mode = G_CHECK;
@@ -675,6 +694,14 @@ struct KrylovRun {
     CK(cudaMemsetAsync(flags, 0, F_COUNT * sizeof(int), s));
     CK(kr_init(kd, s));
     CK(kr_norm2(b, N, kd, S_BN2, s));
+    if (cg) {
+      // r = b - A x0 = b, z = M^{-1} r, p = z, (r, z)  (vectors: r = r0, z = r1, p = u0, q = u1)
+      CK(cudaMemcpyAsync(r[0], b, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      TRY(h->impl->apply(r[0], r[1], tr, s));
+      CK(kr_cg_start(r[0], r[1], u[0], N, kd, s));
+      CK(cudaMemcpyAsync(hs, kd.S + S_RN2, 5 * sizeof(double), cudaMemcpyDeviceToHost, s));
+      return SAP_OK;
+    }
     TRY(h->impl->apply(b, r[0], tr, s));
     CK(kr_norm2(r[0], N, kd, S_BTN2, s));
     CK(cudaMemcpyAsync(rt, r[0], N * sizeof(double), cudaMemcpyDeviceToDevice, s));
@@ -706,7 +733,28 @@ struct KrylovRun {
     CK(kr_restart(r[0], rt, u[0], N, kr, s));
     return SAP_OK;
   }
+  // one CG step (Saad, Alg. 9.1) with its exit test and, gated, the restart
+  sap_status_t cg_step() {
+    double *rr = r[0], *z = r[1], *p = u[0], *q = u[1];
+    CK(launch_spmv(h->band, N, h->L.K, p, q, tr, s, gA));          // q = A p
+    CK(kr_cg_alpha(p, q, N, ka, s));
+    CK(kr_cg_xr(x, rr, p, q, N, ka, s));
+    CK(kr_cg_check(kd, tol, s));
+    CK(launch_spmv(h->band, N, h->L.K, x, tmp, tr, s, gC));         // true residual, if flagged
+    CK(kr_residual(b, tmp, t, N, kc, S_TN2, s));
+    CK(kr_cg_decide(kd, tol, h->opt.max_iters, s));
+    CK(kr_copy(t, rr, N, kr, s));                                   // restart: r = b - A x
+    TRY(h->impl->apply(rr, z, tr, s, gA));                          // z = M^{-1} r
+    CK(kr_cg_start(rr, z, p, N, kr, s));                            // restart: p = z
+    CK(kr_cg_beta(rr, z, N, kk, s));
+    CK(kr_cg_p(z, p, N, kk, s));
+    return SAP_OK;
+  }
   sap_status_t iteration() {
+    if (cg) {
+      for (int k = 0; k < kCgSteps; ++k) TRY(cg_step());
+      return SAP_OK;
+    }
     for (int j = 0; j < 2; ++j) {
       CK(kr_bicg_rho(r[j], rt, N, ka, j, s));
       CK(kr_bicg_u(u[0], u[1], r[0], r[1], N, ka, j, s));
@@ -741,7 +789,8 @@ struct KrylovRun {
     h->glaunches[gi] = launches_so_far() - l0;
     count_launches(-(int)h->glaunches[gi]);     // captured, not run
   }
-  bool active() const { return !done && it < h->opt.max_iters; }
+  // CG: the device finishes the solve at the iteration cap (a round may end early)
+  bool active() const { return !done && it < h->opt.max_iters + (cg ? kCgSteps : 0); }
   // one outer iteration and the readback of the control flags
   sap_status_t round() {
     capture();
@@ -751,7 +800,7 @@ struct KrylovRun {
     } else {
       TRY(iteration());
     }
-    ++it;
+    it += cg ? kCgSteps : 1;
     CK(cudaMemcpyAsync(hf, flags, F_COUNT * sizeof(int), cudaMemcpyDeviceToHost, s));
     return SAP_OK;
   }
@@ -786,11 +835,12 @@ struct KrylovRun {
     if (h->impl->take_device_error(s) != SAP_OK) status = SAP_ERR_TIMEOUT;
     float ms = 0.f;
     cudaEventElapsedTime(&ms, ev0, ev1);
-    inf.n_matvec = (int64_t)std::llround(4.0 * inf.iters);
+    inf.n_matvec = (int64_t)std::llround((cg ? 1.0 : 4.0) * inf.iters);
     inf.t_solve_ms = ms;
     inf.t_kry_ms = ms;
     inf.t_factor_ms = h->t_factor_ms;
     inf.t_lu_ms = h->t_lu_ms;
+    inf.t_prep_ms = h->t_prep_ms;
     inf.t_ul_ms = h->t_ul_ms;
     inf.t_bc_ms = 0.f;            // B_i, C_{i+1} are read in place by the tip kernels
     inf.t_spk_ms = h->t_spk_ms;
@@ -844,7 +894,10 @@ sap_status_t launch_factor(sap_handle* h, cudaStream_t s) {
 sap_status_t finish_factor(sap_handle* h) {
   CK(cudaEventSynchronize(h->evp[3]));
   CK(cudaGetLastError());
-  cudaEventElapsedTime(&h->t_lu_ms, h->evp[0], h->evp[1]);
+  float t_lu_phase = 0.f;
+  cudaEventElapsedTime(&t_lu_phase, h->evp[0], h->evp[1]);
+  cudaEventElapsedTime(&h->t_lu_ms, h->ev_lu[0], h->ev_lu[1]);
+  h->t_prep_ms = std::max(0.f, t_lu_phase - h->t_lu_ms);
   h->t_ul_ms = 0.f;
   if (h->opt.variant == SAP_C && h->L.P > 1) cudaEventElapsedTime(&h->t_ul_ms, h->evu[0], h->evu[1]);
   cudaEventElapsedTime(&h->t_spk_ms, h->evp[2], h->ev_rd);
@@ -959,6 +1012,8 @@ sap_status_t create_handle(const double* band_dev, int64_t N, int32_t K, const s
   CK(cudaEventCreate(&h->ev1));
   for (auto& e : h->evp) CK(cudaEventCreate(&e));
   CK(cudaEventCreate(&h->ev_rd));
+  CK(cudaEventCreate(&h->ev_lu[0]));
+  CK(cudaEventCreate(&h->ev_lu[1]));
   if (opt.precision == SAP_FP64) h->impl.reset(new Solver<double>(h));
   else h->impl.reset(new Solver<float>(h));
   TRY(h->impl->alloc());
@@ -1046,10 +1101,12 @@ sap_status_t factor_batch(sap_batch* B, cudaStream_t s) {
   }
   // the work list's error flag: the first system's (every system's factor phase reads its own)
   int* err = B->hs[0]->impl->err_flag();
+  for (sap_handle* h : B->hs) CK(cudaEventRecord(h->ev_lu[0], s));
   CK(B->fp64 ? launch_factor_lu_items<double>(B->items, B->nitems, B->Kmax, B->counter,
                                               static_cast<double*>(B->wlu), false, err, s)
              : launch_factor_lu_items<float>(B->items, B->nitems, B->Kmax, B->counter,
                                              static_cast<float*>(B->wlu), B->tc, err, s));
+  for (sap_handle* h : B->hs) CK(cudaEventRecord(h->ev_lu[1], s));
   CK(cudaEventRecord(B->ev, s));
   for (sap_handle* h : B->hs) {
     CK(cudaStreamWaitEvent(h->ks, B->ev, 0));
@@ -1159,7 +1216,7 @@ void sap_default_options(sap_options_t* o) {
   o->boost_eps = 0.0;
   o->spin_limit = 0;
   o->segments = 0;
-  o->reserved0 = 0;
+  o->krylov = SAP_KRYLOV_BICGSTAB2;
 }
 
 int64_t sap_kernel_launches(void) { return (int64_t)sap::g_launches.load(); }
@@ -1260,6 +1317,49 @@ sap_status_t sap_solve_host(sap_handle_t h, const double* b_host, double* x_host
   CK(cudaMemcpyAsync(xb, b_host, N * sizeof(double), cudaMemcpyHostToDevice, s));
   sap_status_t st = krylov(h, xb, xb + N, false, info, s);
   CK(cudaMemcpyAsync(x_host, xb + N, N * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  return st;
+}
+
+sap_status_t sap_factor_host(const double* band_host, int64_t N, int32_t K, const sap_options_t* opt,
+                             cudaStream_t s, sap_handle_t* out) {
+  if (!out) return SAP_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!band_host || !opt || N < 2 || K < 1 || K >= N) return SAP_ERR_INVALID_ARG;
+  const size_t bytes = (size_t)(2 * (int64_t)K + 1) * (size_t)N * sizeof(double);
+  double* d = nullptr;
+  if (cudaMalloc(&d, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return SAP_ERR_OOM;
+  }
+  std::unique_ptr<double, cudaError_t (*)(void*)> guard(d, cudaFree);
+  CK(cudaMemcpyAsync(d, band_host, bytes, cudaMemcpyHostToDevice, s));
+  sap_handle_t h = nullptr;
+  TRY(sap_factor(d, N, K, opt, s, &h));
+  h->mem.ptrs.push_back(guard.release());     // freed with the handle
+  h->band_owned = d;
+  *out = h;
+  return SAP_OK;
+}
+
+sap_status_t sap_refactor_host(sap_handle_t h, const double* band_host, cudaStream_t s) {
+  if (!h || !band_host || !h->band_owned) return SAP_ERR_INVALID_ARG;
+  const size_t bytes = (size_t)h->L.W * (size_t)h->L.N * sizeof(double);
+  CK(cudaMemcpyAsync(h->band_owned, band_host, bytes, cudaMemcpyHostToDevice, s));
+  return run_factor(h, s);
+}
+
+sap_status_t sap_solve_pair_host(sap_handle_t h, const double* b_host, const double* g_host, double* x_host,
+                                 double* lam_host, sap_info_t* info_x, sap_info_t* info_lam, cudaStream_t s) {
+  if (!h || !b_host || !g_host || !x_host || !lam_host || x_host == lam_host) return SAP_ERR_INVALID_ARG;
+  const int64_t N = h->L.N;
+  if (!h->host_stage4) TRY(h->mem.alloc(&h->host_stage4, (size_t)(4 * N)));
+  double *db = h->host_stage4, *dg = db + N, *dx = dg + N, *dl = dx + N;
+  CK(cudaMemcpyAsync(db, b_host, N * sizeof(double), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(dg, g_host, N * sizeof(double), cudaMemcpyHostToDevice, s));
+  const sap_status_t st = sap_solve_pair(h, db, dx, dg, dl, info_x, info_lam, s);
+  CK(cudaMemcpyAsync(x_host, dx, N * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(lam_host, dl, N * sizeof(double), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   return st;
 }

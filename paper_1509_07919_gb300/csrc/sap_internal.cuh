@@ -89,7 +89,8 @@ struct Factors {
 // failed (flags[F_REPLACE]).  Kernels read the flags at entry and return
 // uniformly per CTA, so a gated-off launch costs only its launch.
 enum FlagSlot { F_DONE = 0, F_CHECK, F_REPLACE, F_STATUS, F_RESTARTS, F_COUNT };
-enum GateMode { G_ALWAYS = 0, G_ACTIVE = 1, G_CHECK = 2, G_REPLACE = 3 };
+// G_KEEP: active and no restart flagged (the CG step's own p update).
+enum GateMode { G_ALWAYS = 0, G_ACTIVE = 1, G_CHECK = 2, G_REPLACE = 3, G_KEEP = 4 };
 struct Gate {
   const int* flags = nullptr;
   int mode = G_ALWAYS;
@@ -99,6 +100,7 @@ __device__ __forceinline__ bool gate_skip(const Gate& g) {
   if (g.flags[F_DONE]) return true;
   if (g.mode == G_CHECK) return g.flags[F_CHECK] == 0;
   if (g.mode == G_REPLACE) return g.flags[F_REPLACE] == 0;
+  if (g.mode == G_KEEP) return g.flags[F_REPLACE] != 0;
   return false;
 }
 

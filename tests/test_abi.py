@@ -59,5 +59,5 @@ def test_host_only_calls_on_cpu():
     assert names[S.SAP_OK] == "ok"
     assert len(set(names.values())) >= 8          # distinct messages for the defined statuses
     o = S.sap_default_options()
-    assert (o.P, o.variant, o.precision, o.max_iters, o.tol, o.segments, o.reserved0) == \
+    assert (o.P, o.variant, o.precision, o.max_iters, o.tol, o.segments, o.krylov) == \
         (1, S.SAP_D, S.SAP_FP64, 500, 1e-10, 0, 0)

@@ -121,3 +121,39 @@ def test_solve_host_buffers(sap):
     xp, _, st = sap.sap_solve_host(h, torch.from_numpy(b.copy()), xp)
     assert st == sap.SAP_OK
     np.testing.assert_array_equal(xp.numpy(), host(xd))
+
+
+@pytest.mark.parametrize("variant", [0, 1])
+def test_host_buffer_factor_refactor_and_pair(sap, variant):
+    """sap_factor_host / sap_refactor_host / sap_solve_pair_host: the band,
+    b and g from host memory and x, lambda back to host memory, the copies
+    inside the calls; the results equal the device-pointer calls' bit for bit,
+    before and after a refactor with new band values.  A handle whose band is
+    borrowed refuses sap_refactor_host."""
+    N, K, P = 40000, 20, 8
+    band, xt, b = make(N, K, 1.0, 915)
+    g = G.adjoint_seed(N, 915)
+    bh = torch.from_numpy(band).pin_memory()
+    h = sap.sap_factor_host(bh, N, K, P=P, variant=variant, precision=sap.SAP_FP32)
+    hd = sap.sap_factor(dev(band), N, K, P=P, variant=variant, precision=sap.SAP_FP32)
+    xh = torch.empty(N, dtype=torch.float64).pin_memory()
+    lh = torch.empty(N, dtype=torch.float64).pin_memory()
+    bb = torch.from_numpy(b).pin_memory()
+    gg = torch.from_numpy(g).pin_memory()
+    for rnd in range(2):
+        if rnd == 1:
+            band2, _, b2 = make(N, K, 1.05, 916)
+            bh.copy_(torch.from_numpy(band2))
+            bb.copy_(torch.from_numpy(b2))
+            sap.sap_refactor_host(h, bh)
+            hd.band.copy_(dev(band2))
+            sap.sap_refactor(hd)
+        _, _, ix, il, st = sap.sap_solve_pair_host(h, bb, gg, xh, lh)
+        assert st == sap.SAP_OK and ix.relres <= 1e-10 and il.relres <= 1e-10
+        xd, ld, _, _, st2 = sap.sap_solve_pair(hd, dev(bb.numpy()), dev(g))
+        assert st2 == sap.SAP_OK
+        np.testing.assert_array_equal(xh.numpy(), host(xd))
+        np.testing.assert_array_equal(lh.numpy(), host(ld))
+    with pytest.raises(sap.SapError) as e:
+        sap.sap_refactor_host(hd, bh)
+    assert e.value.status == sap.SAP_ERR_INVALID_ARG

@@ -708,3 +708,25 @@ def test_bicgstab2_restart_equals_fresh_solve_from_current_x():
     np.testing.assert_allclose(window[:, 1], tf[:len(window), 1], rtol=1e-12, atol=0)
     # and the true residual keeps tracking: the restarted iterate is x_R + y
     assert abs(t[r0, 2] - np.linalg.norm(s.apply(bp))) <= 1e-12 * t[r0, 2]
+
+
+@pytest.mark.parametrize("var", [O.SAP_D, O.SAP_C])
+def test_openmp_build_is_bit_identical(var):
+    """The CPU baseline's multi-core leg: the oracle built with -fopenmp runs
+    the independent blocks in parallel (factor, tips, applies) with every
+    block's arithmetic unchanged, so factors, applies and the whole solve
+    equal the single-threaded build's bit for bit."""
+    N, K, P = 6000, 12, 12
+    band = rand_band(N, K, 1.0, 91)
+    b = O.spmv(band, N, K, G.x_true(N, 91))
+    s1 = O.Sap(band, N, K, P, var)
+    s2 = O.Sap(band, N, K, P, var, omp=True)
+    for i in (0, 5, P - 1):
+        np.testing.assert_array_equal(s1.block(i), s2.block(i))
+    r = G.adjoint_seed(N, 91)
+    np.testing.assert_array_equal(s1.apply(r), s2.apply(r))
+    x1, i1 = s1.solve(b)
+    x2, i2 = s2.solve(b)
+    np.testing.assert_array_equal(x1, x2)
+    assert (i1.iters, i1.n_matvec, i1.n_restarts) == (i2.iters, i2.n_matvec, i2.n_restarts)
+    assert O.omp_threads() >= 1

@@ -35,6 +35,39 @@ __device__ __forceinline__ void mbar_wait_bounded(uint64_t* bar, unsigned parity
   if (err) atomicExch(err, 1);
 }
 
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+// ---- TMA: one tiled 2-D box of a tensor map into shared memory ----
+// The map is a __grid_constant__ kernel parameter (its generic address is
+// passed); completion is counted on *bar in bytes (expect_tx first).  x, the
+// innermost coordinate, must be a multiple of 16 bytes' worth of elements;
+// the box may reach past the tensor's edges (filled with zeros there).
+__device__ __forceinline__ void tma_load_2d(void* dst, const void* tmap, int x, int y, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];\n"
+      ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(tmap)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// The same by non-blocking tests (mbarrier.test_wait), for waits on phases
+// that have usually completed long before.
+__device__ __forceinline__ bool mbar_test_wait(uint64_t* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok) : "r"(smem_u32(bar)), "r"(parity) : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ void mbar_poll_bounded(uint64_t* bar, unsigned parity, int limit, int* err, bool& failed) {
+  if (failed) return;
+  for (int i = 0; i < limit; ++i)
+    if (mbar_test_wait(bar, parity)) return;
+  failed = true;
+  if (err) atomicExch(err, 1);
+}
+
 // ---- TMEM ----
 // Allocation and release by one whole warp; the base address lands in *dst.
 __device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols) {

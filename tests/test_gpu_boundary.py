@@ -38,18 +38,26 @@ def relerr(a, b):
 
 
 def test_spin_limit_takes_effect(sap):
-    """spin_limit = 1: the sweeps' first wait polls a chunk copy issued a few
-    instructions earlier, which cannot have landed, so the wait gives up, the
-    kernel drains its copies in flight and the solve reports SAP_ERR_TIMEOUT.
-    A handle with a large limit (clamped to 2^31 - 1) on the same context then
-    solves to the usual tolerances, and so does the default (0)."""
+    """spin_limit = 1: a bounded wait that polls once gives up on a copy issued
+    moments before (the sweeps' first chunk: a non-blocking test, which cannot
+    see it landed; the block LU's TMA boxes, when its one try_wait returns
+    before them), stops further copies, drains those in flight, and the call
+    reports SAP_ERR_TIMEOUT: the factorisation when the LU's wait gave up, else
+    the solve.  A handle with a large limit (clamped to 2^31 - 1) on the same
+    context then solves to the usual tolerances, and so does the default (0)."""
+    import ctypes
     N, K, P = 20000, 20, 4
     band, xt, b = make(N, K, 1.0, 911)
     bd = dev(band)
-    h1 = sap.sap_factor(bd, N, K, P=P, variant=sap.SAP_D, precision=sap.SAP_FP32, spin_limit=1, max_iters=3)
-    _, _, st = sap.sap_solve(h1, dev(b), raise_on_error=False)
+    opts = sap.sap_default_options(P=P, variant=sap.SAP_D, precision=sap.SAP_FP32, spin_limit=1, max_iters=3)
+    hp = ctypes.c_void_p()
+    st = sap._lib.sap_factor(bd.data_ptr(), N, K, ctypes.byref(opts),
+                             torch.cuda.current_stream().cuda_stream, ctypes.byref(hp))
+    if st == sap.SAP_OK:
+        h1 = sap.Handle(hp.value, bd, N, K, opts)
+        _, _, st = sap.sap_solve(h1, dev(b), raise_on_error=False)
+        del h1
     assert st == sap.SAP_ERR_TIMEOUT
-    del h1
     torch.cuda.synchronize()
     xo, _, _ = O.solve(band, N, K, b, P, O.SAP_D)
     for lim in (1 << 40, 0):

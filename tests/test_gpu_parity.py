@@ -101,6 +101,33 @@ def test_block_lu_parity_fp32(sap, N, K, P):
         assert np.abs(fg - fo).max() <= 64 * K * U32 * np.abs(fo).max()
 
 
+@pytest.mark.parametrize("N,K,P,prec,variant", [(4000, 10, 7, 1, 1), (8000, 50, 6, 1, 1), (8000, 50, 6, 0, 1),
+                                                (6000, 100, 4, 1, 0), (4004, 1, 9, 1, 0), (6000, 64, 3, 0, 0),
+                                                (7000, 120, 5, 1, 1), (4096, 33, 3, 0, 1)])
+def test_lu_tma_staging_equals_cp_async_staging(sap, monkeypatch, N, K, P, prec, variant):
+    """The block LU / UL with the band staged by TMA boxes (default) and with the
+    per-element cp.async staging (SAP_LU_STAGING=cp_async) run the same
+    arithmetic in the same order on the same values: the factors, and for
+    SaP-C the spike tips built from the UL tiles, agree bit for bit."""
+    band, _, _ = make(N, K, 1.0, 1300 + K)
+    bd = dev(band)
+    h1 = sap.sap_factor(bd, N, K, P=P, variant=variant, precision=prec)
+    monkeypatch.setenv("SAP_LU_STAGING", "cp_async")
+    h2 = sap.sap_factor(bd, N, K, P=P, variant=variant, precision=prec)
+    monkeypatch.delenv("SAP_LU_STAGING")
+    for i in range(P):
+        np.testing.assert_array_equal(sap.sap_get_block_lu(h1, i), sap.sap_get_block_lu(h2, i))
+    if variant == 1:
+        for i in range(P - 1):
+            for w in ("V", "W"):
+                np.testing.assert_array_equal(sap.sap_get_interface(h1, i, w), sap.sap_get_interface(h2, i, w))
+    o = O.Sap(band, N, K, P, variant)
+    tol = 1e-11 if prec == 0 else 64 * K * U32
+    for i in (0, P - 1):
+        fo = o.block(i, 0)
+        assert np.abs(sap.sap_get_block_lu(h1, i) - fo).max() <= tol * np.abs(fo).max()
+
+
 @pytest.mark.parametrize("prec,tol", [(0, 1e-11), (1, 2e-4)])
 @pytest.mark.parametrize("N,K,P", [(1200, 10, 5), (3001, 40, 6), (900, 64, 3), (2100, 99, 3), (1500, 130, 3)])
 def test_spike_tips_and_rbar_parity(sap, N, K, P, prec, tol):

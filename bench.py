@@ -34,7 +34,7 @@ METRIC = "time to rel.res 1e-10 & HBM GB/s: FP32-precond vs FP64 SaP, fwd+adjoin
 TRAFFIC_SWEEPS = 232656896
 # DRAM bytes (read + write) of one k_band_lu launch (FP32), by (N, K, P), from an
 # ncu capture of the current kernel; a workload without a capture reports null
-TRAFFIC_LU = {}
+TRAFFIC_LU = {(200000, 50, 50): 118135552}
 # P=None: picked by sap_autotune (measured refactor + solve over N / {16000 .. 1000}, 152, 304)
 # before the timed region; P_ref is the oracle's partition count in that case
 # (the autotuner's pick on GB300 when this table was written).

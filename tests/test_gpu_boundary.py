@@ -38,31 +38,40 @@ def relerr(a, b):
 
 
 def test_spin_limit_takes_effect(sap):
-    """spin_limit = 1: a bounded wait that polls once gives up on a copy issued
-    moments before (the sweeps' first chunk: a non-blocking test, which cannot
-    see it landed; the block LU's TMA boxes, when its one try_wait returns
-    before them), stops further copies, drains those in flight, and the call
-    reports SAP_ERR_TIMEOUT: the factorisation when the LU's wait gave up, else
-    the solve.  A handle with a large limit (clamped to 2^31 - 1) on the same
-    context then solves to the usual tolerances, and so does the default (0)."""
+    """spin_limit = 1: a bounded wait that polls once gives up on a copy that
+    has not landed yet, stops further copies, drains those in flight, and the
+    call reports SAP_ERR_TIMEOUT (the factorisation when the block LU's wait
+    gave up, else the solve).  Whether one poll comes too early is a matter
+    of timing; on a wide band (K = 300, 45 KB of sweep matrices per 32-row
+    chunk, 2 chunks prefetched) the sweeps' first poll precedes the landing,
+    so the test asks for a timeout in one of three attempts, and every attempt
+    must end with TIMEOUT or a clean status.  A handle with a large limit
+    (clamped to 2^31 - 1) on the same context then solves to the usual
+    tolerances, and so does the default (0)."""
     import ctypes
-    N, K, P = 20000, 20, 4
+    N, K, P = 40000, 300, 4
     band, xt, b = make(N, K, 1.0, 911)
-    bd = dev(band)
-    opts = sap.sap_default_options(P=P, variant=sap.SAP_D, precision=sap.SAP_FP32, spin_limit=1, max_iters=3)
-    hp = ctypes.c_void_p()
-    st = sap._lib.sap_factor(bd.data_ptr(), N, K, ctypes.byref(opts),
-                             torch.cuda.current_stream().cuda_stream, ctypes.byref(hp))
-    if st == sap.SAP_OK:
-        h1 = sap.Handle(hp.value, bd, N, K, opts)
-        _, _, st = sap.sap_solve(h1, dev(b), raise_on_error=False)
-        del h1
-    assert st == sap.SAP_ERR_TIMEOUT
-    torch.cuda.synchronize()
+    bd, bdev = dev(band), dev(b)
+    seen = []
+    for attempt in range(3):
+        opts = sap.sap_default_options(P=P, variant=sap.SAP_D, precision=sap.SAP_FP32, spin_limit=1, max_iters=3)
+        hp = ctypes.c_void_p()
+        st = sap._lib.sap_factor(bd.data_ptr(), N, K, ctypes.byref(opts),
+                                 torch.cuda.current_stream().cuda_stream, ctypes.byref(hp))
+        if st == sap.SAP_OK:
+            h1 = sap.Handle(hp.value, bd, N, K, opts)
+            _, _, st = sap.sap_solve(h1, bdev, raise_on_error=False)
+            del h1
+        torch.cuda.synchronize()
+        seen.append(st)
+        assert st in (sap.SAP_ERR_TIMEOUT, sap.SAP_OK, sap.SAP_ERR_NOT_CONVERGED), seen
+        if st == sap.SAP_ERR_TIMEOUT:
+            break
+    assert sap.SAP_ERR_TIMEOUT in seen, seen
     xo, _, _ = O.solve(band, N, K, b, P, O.SAP_D)
     for lim in (1 << 40, 0):
         h = sap.sap_factor(bd, N, K, P=P, variant=sap.SAP_D, precision=sap.SAP_FP32, spin_limit=lim)
-        x, info, st = sap.sap_solve(h, dev(b))
+        x, info, st = sap.sap_solve(h, bdev)
         assert st == sap.SAP_OK and info.relres <= 1e-10
         assert relerr(host(x), xo) <= 1e-8
 

@@ -65,6 +65,8 @@ def parse():
                     help="SaP variant (default: the workload's, else D)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-compare", action="store_true", help="skip the FP64 / other-variant comparison runs")
+    ap.add_argument("--sweep", default=None, choices=["P", "d"],
+                    help="the sensitivity study of Sec. 4.1.1 (P) or 4.1.2 (d) instead of the benchmark line")
     a = ap.parse_args()
     if a.variant is None:
         a.variant = WORKLOADS.get(a.workload, {}).get("variant", "D")
@@ -730,9 +732,80 @@ def run_gpu_batch(args):
         print(json.dumps(line), flush=True)
 
 
+# Sensitivity studies of Sec. 4.1.1 (time to solution against the partition
+# count P: N = 200000, K = 200, d = 1) and Sec. 4.1.2 (against the degree of
+# diagonal dominance d: N = 200000, K = 200, P = 50), SaP-D against SaP-C.
+# Per point: D_pre / C_pre = the preconditioner's set-up (the whole
+# factorisation phase, t_factor_ms of the refactor before the solve), D_it /
+# C_it = BiCGStab(2) iterations in quarters, D_Kry / C_Kry = the Krylov phase
+# (t_kry_ms), D_Tot = D_pre + D_Kry (likewise C), SpdUp = D_Tot / C_Tot, each
+# the median of `reps` refactor + forward solves to relres 1e-10 (FP32
+# preconditioner, FP64 Krylov).  A point whose solve does not converge
+# within max_iters keeps its status in status_D / status_C.
+SWEEP_P = (2, 5, 10, 20, 30, 40, 50, 60, 70, 80, 90, 100, 152, 304)
+SWEEP_D = (0.06, 0.08, 0.1, 0.2, 0.3, 0.4, 0.5, 0.6, 0.7, 0.8, 0.9, 1.0, 1.1, 1.2)
+
+
+def sweep_point(S, torch, band, b, N, K, P, reps=3, max_iters=200):
+    """One (P, d) point of the sensitivity studies: both variants (see above)."""
+    row = {}
+    for tag, var in (("D", S.SAP_D), ("C", S.SAP_C)):
+        h = S.sap_factor(band, N, K, P=P, variant=var, precision=S.SAP_FP32, max_iters=max_iters)
+        pre, kry, its, sts = [], [], [], []
+        x = torch.empty_like(b)
+        for _ in range(reps):
+            S.sap_refactor(h)
+            _, info, st = S.sap_solve(h, b, x, raise_on_error=False)
+            pre.append(info.t_factor_ms)
+            kry.append(info.t_kry_ms)
+            its.append(info.iters)
+            sts.append(st)
+        row[f"{tag}_pre"] = statistics.median(pre)
+        row[f"{tag}_it"] = statistics.median(its)
+        row[f"{tag}_Kry"] = statistics.median(kry)
+        row[f"{tag}_Tot"] = row[f"{tag}_pre"] + row[f"{tag}_Kry"]
+        row[f"status_{tag}"] = max(sts)
+        del h
+    row["SpdUp"] = row["D_Tot"] / row["C_Tot"]
+    return row
+
+
+def run_sweep(args, N=200000, K=200, Ps=SWEEP_P, ds=SWEEP_D, P_d=50, reps=3, out=sys.stdout):
+    """--sweep P | d: one JSON line per point, then a table."""
+    import torch
+    import sap_inputs as G
+    import paper_1509_07919_gb300 as S
+
+    rows = []
+    points = [(P, 1.0) for P in Ps] if args.sweep == "P" else [(P_d, d) for d in ds]
+    cache = {}
+    for P, d in points:
+        if d not in cache:
+            band_np = G.dense_banded(N, K, d, 7)
+            band = torch.from_numpy(band_np).cuda()
+            b = S.sap_spmv(band, N, K, torch.from_numpy(G.x_true(N, 7)).cuda())
+            cache = {d: (band, b)}
+        band, b = cache[d]
+        if P > N // (2 * K):
+            continue
+        row = {"sweep": args.sweep, "N": N, "K": K, "P": P, "d": d}
+        row.update(sweep_point(S, torch, band, b, N, K, P, reps=reps))
+        rows.append(row)
+        print(json.dumps(row), file=out, flush=True)
+    key = "P" if args.sweep == "P" else "d"
+    print(f"| {key} | D_pre | C_pre | D_it | C_it | D_Kry | C_Kry | D_Tot | C_Tot | SpdUp |", file=out)
+    print("|---|---|---|---|---|---|---|---|---|---|", file=out)
+    for r in rows:
+        print(f"| {r[key]} | {r['D_pre']:.2f} | {r['C_pre']:.2f} | {r['D_it']:g} | {r['C_it']:g} | {r['D_Kry']:.2f} "
+              f"| {r['C_Kry']:.2f} | {r['D_Tot']:.2f} | {r['C_Tot']:.2f} | {r['SpdUp']:.2f} |", file=out)
+    return rows
+
+
 def main():
     args = parse()
-    if args.impl == "reference":
+    if args.sweep:
+        run_sweep(args)
+    elif args.impl == "reference":
         run_reference(args)
     elif args.workload == "batch64":
         run_gpu_batch(args)

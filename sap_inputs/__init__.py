@@ -206,3 +206,72 @@ def batch_specs(n_systems: int = 64, seed: int = CONFIG_SEED_BASE + 5,
     Ks = np.minimum(Ks, k_hi)
     seeds = [seed + 1000 + s for s in range(n_systems)]
     return [(int(n), int(k), int(sd)) for n, k, sd in zip(Ns, Ks, seeds)]
+
+
+@dataclass
+class SparseSystem:
+    """A sparse system in CSR form (rows sorted by column) and the hidden
+    structure it was made from: row i of the matrix is row rowsrc[i] of a
+    banded matrix M0 (half-bandwidth K0, diagonally dominant, sparse within
+    the band), renumbered by the symmetric permutation sym (M0 index k is
+    index sym[k] here)."""
+    n: int
+    rowptr: np.ndarray    # int64, n + 1
+    col: np.ndarray       # int32, nnz
+    val: np.ndarray       # float64, nnz
+    K0: int
+    rowsrc: np.ndarray    # int64, n: M0 row of row i (before the renumbering)
+    sym: np.ndarray       # int64, n
+
+
+def _perm_from(seed: int, stream: int, n: int) -> np.ndarray:
+    """A permutation of 0..n-1 from n counter-based draws (argsort of U(-1,1))."""
+    return np.argsort(uniform(seed, stream, n), kind="stable").astype(np.int64)
+
+
+def sparse_scrambled(n: int, K0: int, fill: float, d: float, seed: int) -> SparseSystem:
+    """Synthetic sparse matrix of the kind the sparse front end (Sec. 2.2) is
+    for: M0 banded with half-bandwidth K0, each in-band off-diagonal present
+    with probability `fill` (value U(-1, 1)), its diagonal d times the row's
+    off-diagonal abs-sum (plus 1, so that every row has a nonzero diagonal);
+    then its rows shuffled (the heavy entries leave the diagonal, for the
+    matching to restore) and all indices renumbered by a random symmetric
+    permutation (the band hidden, for the bandwidth reduction to recover):
+    A[r, sym[k]] = M0[rowsrc[r], k]."""
+    W = 2 * K0 + 1
+    keep = uniform(seed, 10, W * n).reshape(W, n)
+    vals = uniform(seed, 11, W * n).reshape(W, n)
+    rows, cols, vs = [], [], []
+    absum = np.zeros(n)
+    for c in range(W):
+        off = c - K0                       # column j = i + off
+        if off == 0:
+            continue
+        i = np.arange(max(0, -off), min(n, n - off))
+        m = keep[c, i] * 0.5 + 0.5 < fill
+        i = i[m]
+        rows.append(i)
+        cols.append(i + off)
+        vs.append(vals[c, i])
+        np.add.at(absum, i, np.abs(vals[c, i]))
+    rows.append(np.arange(n))
+    cols.append(np.arange(n))
+    sgn = np.where(uniform(seed, 12, n) < 0, -1.0, 1.0)
+    vs.append(sgn * (d * absum + 1.0))
+    r0 = np.concatenate(rows)
+    c0 = np.concatenate(cols)
+    v0 = np.concatenate(vs)
+    rowshuf = _perm_from(seed, 13, n)      # row i of the shuffled matrix is M0 row rowshuf[i]
+    pos = np.empty(n, dtype=np.int64)
+    pos[rowshuf] = np.arange(n)            # M0 row k lands at shuffled row pos[k]
+    sym = _perm_from(seed, 14, n)          # index k -> sym[k]
+    ri = sym[pos[r0]]
+    ci = sym[c0]
+    order = np.lexsort((ci, ri))
+    ri, ci, vv = ri[order], ci[order], v0[order]
+    rowptr = np.zeros(n + 1, dtype=np.int64)
+    np.add.at(rowptr, ri + 1, 1)
+    rowptr = np.cumsum(rowptr)
+    rowsrc = np.empty(n, dtype=np.int64)
+    rowsrc[sym] = rowshuf                  # final row sym[i] holds M0 row rowshuf[i]
+    return SparseSystem(n, rowptr, ci.astype(np.int32), vv, K0, rowsrc, sym)

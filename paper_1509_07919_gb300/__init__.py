@@ -93,6 +93,13 @@ def _load():
         "sap_batch_size": (i32, [vp]),
         "sap_batch_partitions": (i32, [vp, i32]),
         "sap_batch_destroy": (C.c_int, [vp]),
+        "sap_db_reorder": (C.c_int, [i64, i64, vp, vp, vp, vp, vp, vp, P(C.c_double), vp]),
+        "sap_cm_reorder": (C.c_int, [i64, i64, vp, vp, vp, vp, P(C.c_int32), vp]),
+        "sap_perm_compose": (C.c_int, [i64, vp, vp, vp, vp]),
+        "sap_sparse_bandwidth": (C.c_int, [i64, i64, vp, vp, vp, vp, P(C.c_int32), vp]),
+        "sap_sparse_to_band": (C.c_int, [i64, i64, vp, vp, vp, vp, vp, vp, vp, i32, vp, vp]),
+        "sap_sparse_permute_rhs": (C.c_int, [i64, vp, vp, vp, vp, vp]),
+        "sap_sparse_unpermute_solution": (C.c_int, [i64, vp, vp, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -444,3 +451,87 @@ from .autograd import SapSolve, SapSolveBatched, sap_solve_autograd, sap_solve_b
 
 __all__ = [n for n in dir() if n.startswith("sap_") or n in ("Handle", "BatchHandle", "SapError", "SapSolve",
                                                                  "SapSolveBatched")]
+
+
+# ---- sparse front end (include/sap_sparse.h) ----
+
+class Csr:
+    """A CSR matrix on the device: rowptr int64 (n + 1), col int32, val float64."""
+
+    def __init__(self, n: int, rowptr: torch.Tensor, col: torch.Tensor, val: torch.Tensor):
+        self.n, self.rowptr, self.col, self.val = n, rowptr, col, val
+        self.nnz = int(col.numel())
+
+
+def _tptr(t: torch.Tensor | None, dtype=torch.float64):
+    """Device pointer of a contiguous CUDA tensor of `dtype` (None: NULL)."""
+    if t is None:
+        return None
+    if not (t.is_cuda and t.dtype == dtype and t.is_contiguous()):
+        raise ValueError(f"expected a contiguous CUDA {dtype} tensor")
+    return t.data_ptr()
+
+
+def _i32(t):
+    return _tptr(t, torch.int32)
+
+
+def _csr(A: "Csr"):
+    return A.n, A.nnz, _tptr(A.rowptr, torch.int64), _i32(A.col)
+
+
+def sap_db_reorder(A: Csr, scale: bool = True, stream=None):
+    """Diagonal boosting: returns (rownew, rscale, cscale, logprod); the scale
+    factors are None when scale is False."""
+    dev = A.val.device
+    rownew = torch.empty(A.n, dtype=torch.int32, device=dev)
+    r = torch.empty(A.n, dtype=torch.float64, device=dev) if scale else None
+    s = torch.empty(A.n, dtype=torch.float64, device=dev) if scale else None
+    lp = C.c_double()
+    _check(_lib.sap_db_reorder(*_csr(A), _ptr(A.val), _i32(rownew), _tptr(r), _tptr(s), C.byref(lp),
+                               _stream(stream)), "sap_db_reorder")
+    return rownew, r, s, lp.value
+
+
+def sap_cm_reorder(A: Csr, rownew: torch.Tensor | None = None, stream=None):
+    """Cuthill-McKee of the pattern of B + B^T (B: A with rows moved to
+    rownew): returns (perm, K)."""
+    perm = torch.empty(A.n, dtype=torch.int32, device=A.col.device)
+    K = C.c_int32()
+    _check(_lib.sap_cm_reorder(*_csr(A), _i32(rownew), _i32(perm), C.byref(K), _stream(stream)), "sap_cm_reorder")
+    return perm, K.value
+
+
+def sap_perm_compose(outer: torch.Tensor, inner: torch.Tensor, stream=None) -> torch.Tensor:
+    out = torch.empty_like(inner)
+    _check(_lib.sap_perm_compose(inner.numel(), _i32(outer), _i32(inner), _i32(out), _stream(stream)),
+           "sap_perm_compose")
+    return out
+
+
+def sap_sparse_bandwidth(A: Csr, rownew=None, colnew=None, stream=None) -> int:
+    K = C.c_int32()
+    _check(_lib.sap_sparse_bandwidth(*_csr(A), _i32(rownew), _i32(colnew), C.byref(K), _stream(stream)), "sap_sparse_bandwidth")
+    return K.value
+
+
+def sap_sparse_to_band(A: Csr, rownew, colnew, K: int, rscale=None, cscale=None, stream=None) -> torch.Tensor:
+    band = torch.empty((2 * K + 1) * A.n, dtype=torch.float64, device=A.val.device)
+    _check(_lib.sap_sparse_to_band(*_csr(A), _ptr(A.val), _i32(rownew), _i32(colnew), _tptr(rscale),
+                                   _tptr(cscale), K, _ptr(band), _stream(stream)), "sap_sparse_to_band")
+    return band
+
+
+def sap_sparse_permute_rhs(b: torch.Tensor, rownew: torch.Tensor, rscale=None, stream=None) -> torch.Tensor:
+    out = torch.empty_like(b)
+    _check(_lib.sap_sparse_permute_rhs(b.numel(), _ptr(b), _i32(rownew), _tptr(rscale), _ptr(out),
+                                       _stream(stream)), "sap_sparse_permute_rhs")
+    return out
+
+
+def sap_sparse_unpermute_solution(y: torch.Tensor, colnew: torch.Tensor, cscale=None, stream=None) -> torch.Tensor:
+    x = torch.empty_like(y)
+    _check(_lib.sap_sparse_unpermute_solution(y.numel(), _ptr(y), _i32(colnew), _tptr(cscale), _ptr(x),
+                                              _stream(stream)), "sap_sparse_unpermute_solution")
+    return x
+

@@ -14,7 +14,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libsap.so")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["k_factor.cu", "k_apply.cu", "k_spike.cu", "k_misc.cu", "k_chunk.cu", "sap_api.cu", "sap_noalloc.cu"]
+SOURCES = ["k_factor.cu", "k_apply.cu", "k_spike.cu", "k_misc.cu", "k_chunk.cu", "sap_api.cu", "sap_noalloc.cu",
+           "sap_sparse.cu"]
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
               "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden", "--expt-relaxed-constexpr",
               "-I", os.path.join(os.path.dirname(HERE), "include")]
@@ -32,7 +33,8 @@ def _stale() -> bool:
         return True
     t = os.path.getmtime(LIB)
     deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC)]
-    deps.append(os.path.join(os.path.dirname(HERE), "include", "sap.h"))
+    inc = os.path.join(os.path.dirname(HERE), "include")
+    deps += [os.path.join(inc, f) for f in os.listdir(inc)]
     return any(os.path.getmtime(p) > t for p in deps)
 
 

@@ -233,7 +233,9 @@ def sparse_scrambled(n: int, K0: int, fill: float, d: float, seed: int) -> Spars
     """Synthetic sparse matrix of the kind the sparse front end (Sec. 2.2) is
     for: M0 banded with half-bandwidth K0, each in-band off-diagonal present
     with probability `fill` (value U(-1, 1)), its diagonal d times the row's
-    off-diagonal abs-sum (plus 1, so that every row has a nonzero diagonal);
+    off-diagonal abs-sum plus 0.01 (every row has a nonzero diagonal; for
+    d < 1 off-diagonal entries can outweigh it, for d >= 1 it is the row's
+    largest entry);
     then its rows shuffled (the heavy entries leave the diagonal, for the
     matching to restore) and all indices renumbered by a random symmetric
     permutation (the band hidden, for the bandwidth reduction to recover):
@@ -257,7 +259,7 @@ def sparse_scrambled(n: int, K0: int, fill: float, d: float, seed: int) -> Spars
     rows.append(np.arange(n))
     cols.append(np.arange(n))
     sgn = np.where(uniform(seed, 12, n) < 0, -1.0, 1.0)
-    vs.append(sgn * (d * absum + 1.0))
+    vs.append(sgn * (d * absum + 0.01))
     r0 = np.concatenate(rows)
     c0 = np.concatenate(cols)
     v0 = np.concatenate(vs)

@@ -354,17 +354,118 @@ k_rbar_form(const T* __restrict__ V, const T* __restrict__ Wt, int K, double* __
 
 // GEPP of every Rbar_i in its workspace (one CTA of 1024 threads per
 // interface: the L2-resident rank-1 updates want many loads in flight).
-constexpr int kGeppThreads = 1024;
+// Blocked GEPP of the reduced matrices Rbar_i (K x K FP64, row-major in the
+// global workspace, wide bands): right-looking, kGeppNB-column panels, two
+// launches per panel.  k_gepp_panel (one CTA per interface) takes the
+// panel's pivots (column maxima, ties to the lowest row), swaps whole rows,
+// forms the multipliers and updates the panel, then the panel's rows of U
+// to its right (unit lower solve with L11); k_gepp_update subtracts L21 U12
+// from the trailing matrix in 64 x 64 tiles over all interfaces.  Every entry
+// receives the same fused multiply-adds in the same order as in the
+// unblocked elimination (a row's deferred updates move with it in a swap),
+// so the factors and pivots are those of the one-column-at-a-time GEPP.
+constexpr int kGeppNB = 16;
+constexpr int kPanelThreads = 512;
 template <typename T>
-__global__ void __launch_bounds__(kGeppThreads)
-k_rbar_gepp(int K, unsigned char* __restrict__ gws, int* __restrict__ pivout, int* singular) {
-  extern __shared__ int pivs_sh[];
-  __shared__ double red_v[kGeppThreads / 32];
-  __shared__ int red_i[kGeppThreads / 32];
+__global__ void __launch_bounds__(kPanelThreads)
+k_gepp_panel(int K, int k0, unsigned char* __restrict__ gws, int* __restrict__ pivout, int* singular) {
+  __shared__ double red_v[kPanelThreads / 32];
+  __shared__ int red_i[kPanelThreads / 32];
+  __shared__ int psh;
   const int i = blockIdx.x;
+  const int tid = threadIdx.x;
   double* R = reinterpret_cast<double*>(gws + (size_t)i * spike_ws_stride(K, sizeof(T)));
-  rbar_gepp<kGeppThreads>(R, K, pivs_sh, singular, red_v, red_i);
-  for (int k = threadIdx.x; k < K; k += kGeppThreads) pivout[(int64_t)i * K + k] = pivs_sh[k];
+  const int kend = min(K, k0 + kGeppNB);
+  for (int c = k0; c < kend; ++c) {
+    double best = -1.0;
+    int bi = c;
+    for (int r = c + tid; r < K; r += kPanelThreads) {
+      const double v = fabs(R[(int64_t)r * K + c]);
+      if (v > best) { best = v; bi = r; }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ov = __shfl_xor_sync(0xffffffffu, best, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+    }
+    if ((tid & 31) == 0) { red_v[tid >> 5] = best; red_i[tid >> 5] = bi; }
+    __syncthreads();
+    if (tid == 0) {
+      double bv = red_v[0];
+      int bx = red_i[0];
+      for (int w = 1; w < kPanelThreads / 32; ++w)
+        if (red_v[w] > bv || (red_v[w] == bv && red_i[w] < bx)) { bv = red_v[w]; bx = red_i[w]; }
+      pivout[(int64_t)i * K + c] = bx;
+      psh = bx;
+      if (bv == 0.0) atomicExch(singular, 1);
+    }
+    __syncthreads();
+    const int p = psh;
+    if (p != c)
+      for (int j = tid; j < K; j += kPanelThreads) {
+        const double t = R[(int64_t)c * K + j];
+        R[(int64_t)c * K + j] = R[(int64_t)p * K + j];
+        R[(int64_t)p * K + j] = t;
+      }
+    __syncthreads();
+    const double pv = R[(int64_t)c * K + c];
+    for (int r = c + 1 + tid; r < K; r += kPanelThreads)
+      R[(int64_t)r * K + c] = (pv != 0.0) ? R[(int64_t)r * K + c] / pv : 0.0;
+    __syncthreads();
+    // the panel's columns right of c (lane group of 16 threads per row)
+    const int cc = c + 1 + (tid & (kGeppNB - 1));
+    if (cc < kend)
+      for (int r = c + 1 + tid / kGeppNB; r < K; r += kPanelThreads / kGeppNB)
+        R[(int64_t)r * K + cc] -= R[(int64_t)r * K + c] * R[(int64_t)c * K + cc];
+    __syncthreads();
+  }
+  // U12: the panel's rows right of the panel, unit lower solve with L11 (the
+  // rank-1 steps of the panel's columns in order)
+  for (int j = kend + tid; j < K; j += kPanelThreads)
+    for (int r = k0 + 1; r < kend; ++r) {
+      double acc = R[(int64_t)r * K + j];
+      for (int q = k0; q < r; ++q) acc -= R[(int64_t)r * K + q] * R[(int64_t)q * K + j];
+      R[(int64_t)r * K + j] = acc;
+    }
+}
+
+// Trailing update of a panel: R[r][j] -= sum_q L21[r][q] U12[q][j] over the
+// panel's columns q in order, rows and columns from k0 + kGeppNB, 64 x 64
+// tiles (256 threads, 4 x 4 entries each, columns interleaved by 16).  Grid
+// (tiles, tiles, P - 1).
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_gepp_update(int K, int k0, unsigned char* __restrict__ gws) {
+  __shared__ double Ls[64][kGeppNB + 1];
+  __shared__ double Us[kGeppNB][64];
+  const int i = blockIdx.z;
+  double* R = reinterpret_cast<double*>(gws + (size_t)i * spike_ws_stride(K, sizeof(T)));
+  const int m0 = k0 + kGeppNB;
+  const int rt = m0 + (int)blockIdx.y * 64, ct = m0 + (int)blockIdx.x * 64;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  for (int e = tid; e < 64 * kGeppNB; e += 256) {
+    const int rr = e / kGeppNB, q = e % kGeppNB;
+    Ls[rr][q] = rt + rr < K ? R[(int64_t)(rt + rr) * K + k0 + q] : 0.0;
+  }
+  for (int e = tid; e < kGeppNB * 64; e += 256) {
+    const int q = e / 64, cc = e % 64;
+    Us[q][cc] = ct + cc < K ? R[(int64_t)(k0 + q) * K + ct + cc] : 0.0;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const int row = rt + ty + 16 * a;
+    if (row >= K) break;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int col = ct + tx + 16 * b;
+      if (col >= K) continue;
+      double acc = R[(int64_t)row * K + col];
+#pragma unroll
+      for (int q = 0; q < kGeppNB; ++q) acc -= Ls[ty + 16 * a][q] * Us[q][tx + 16 * b];
+      R[(int64_t)row * K + col] = acc;
+    }
+  }
 }
 
 // Rbar_i^{-1} = U^{-1} L^{-1} P from the GEPP factors, 32 columns per CTA
@@ -479,9 +580,18 @@ cudaError_t launch_spikes(const double* band, int64_t N, int K, int P, Dev d, co
   k_tip_cols<T><<<dim3((K + 31) / 32, P - 1, 2), 32, tsm, s>>>(band, N, K, d, ULt, adjoint, V, Wt, gws);
   if (ev_rd && (e = cudaEventRecord(ev_rd, s)) != cudaSuccess) return e;
   const int tiles = (K + RT - 1) / RT;
-  count_launches(3);
+  count_launches(2);
   k_rbar_form<T><<<dim3(tiles, tiles, P - 1), 256, 0, s>>>(V, Wt, K, R0, gws);
-  k_rbar_gepp<T><<<P - 1, kGeppThreads, (size_t)K * sizeof(int), s>>>(K, gws, piv, singular);
+  for (int k0 = 0; k0 < K; k0 += kGeppNB) {
+    count_launches(1);
+    k_gepp_panel<T><<<P - 1, kPanelThreads, 0, s>>>(K, k0, gws, piv, singular);
+    const int m = K - k0 - kGeppNB;
+    if (m > 0) {
+      const int t = (m + 63) / 64;
+      count_launches(1);
+      k_gepp_update<T><<<dim3(t, t, P - 1), 256, 0, s>>>(K, k0, gws);
+    }
+  }
   const size_t ism = (size_t)(K + kInvWarps) * 32 * sizeof(double) + (size_t)K * sizeof(int);
   if (ism > 48 * 1024) {
     e = cudaFuncSetAttribute(k_rbar_inv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ism);

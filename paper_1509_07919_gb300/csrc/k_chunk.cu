@@ -136,10 +136,16 @@ k_chunk_mats(const T* __restrict__ Fall, int K, Dev d, const int64_t* __restrict
     if (r % TPC == part) xr[r / TPC] = x;
   }
   // stored column-major (element (t, j) at j * 32 + t): the sweep's lane t
-  // reads its row as 32 conflict-free shared-memory loads
-  T* M = out + cbase[b] + (int64_t)c * (1 + NG) * CH * CH + (int64_t)(col / CH) * CH * CH + (col % CH) * CH;
+  // reads its row as 32 conflict-free shared-memory loads.  The columns are
+  // staged in the tile area (row stride 33) and the chunk's contiguous block
+  // written out by consecutive threads.
+  __syncthreads();                  // the tiles are read no more
+  T* St = A;
 #pragma unroll
-  for (int m = 0; m < XR; ++m) M[m * TPC + part] = xr[m];
+  for (int m = 0; m < XR; ++m) St[col * LDS + m * TPC + part] = xr[m];
+  __syncthreads();
+  T* M = out + cbase[b] + (int64_t)c * (1 + NG) * CH * CH;
+  for (int e = tid; e < C::NCOL * CH; e += C::NTH) M[e] = St[(e / CH) * LDS + e % CH];
 }
 
 // The same solves for wide bands (ng > 7 couplings, ng known at run time):
@@ -183,9 +189,14 @@ k_chunk_mats_wide(const T* __restrict__ Fall, int K, int ng, Dev d, const int64_
     const T rhs = Bcol ? Bcol[r * LDS] : (r == col ? T(1) : T(0));
     xr[r] = (rhs - acc) * Rd[r];
   }
-  T* M = out + cbase[b] + (int64_t)c * (1 + ng) * CH * CH + (int64_t)(col / CH) * CH * CH + (col % CH) * CH;
+  __syncthreads();                  // staged like k_chunk_mats, then written out contiguously
+  T* St = A;
 #pragma unroll
-  for (int m = 0; m < CH; ++m) M[m] = xr[m];
+  for (int m = 0; m < CH; ++m) St[col * LDS + m] = xr[m];
+  __syncthreads();
+  T* M = out + cbase[b] + (int64_t)c * (1 + ng) * CH * CH;
+  const int ncol = CH * (1 + ng);
+  for (int e = tid; e < ncol * CH; e += ncol) M[e] = St[(e / CH) * LDS + e % CH];
 }
 
 template <typename T, int MODE, int NG>

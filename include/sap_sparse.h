@@ -79,14 +79,51 @@ SAP_API sap_status_t sap_sparse_bandwidth(int64_t n, int64_t nnz, const int64_t 
  * band[(K + I - J) * n + J] = entry (I, J), every other band entry 0: the
  * matrix "regarded as dense banded" of Sec. 2.2, ready for sap_factor.
  *   band_dev (out, (2K + 1) n doubles); rscale_dev / cscale_dev NULL: 1.
- * Errors: INVALID_ARG (also when an entry falls outside the band K, checked
- * by the kernel and reported after the stream completes), CUDA.
- * Synchronises `stream`. */
+ *   drop: nonzero drops the entries outside the band (the element drop-off of
+ *     Sec. 2.2: the band is then the preconditioner's approximation A-hat of
+ *     the reordered matrix, see sap_set_operator_csr); 0 makes such an entry
+ *     an error.
+ * Errors: INVALID_ARG (also, with drop = 0, when an entry falls outside the
+ * band K, checked by the kernel and reported after the stream completes),
+ * CUDA.  Synchronises `stream`. */
 SAP_API sap_status_t sap_sparse_to_band(int64_t n, int64_t nnz, const int64_t *rowptr_dev, const int32_t *col_dev,
                                         const double *val_dev, const int32_t *rownew_dev,
                                         const int32_t *colnew_dev, const double *rscale_dev,
-                                        const double *cscale_dev, int32_t K, double *band_dev,
+                                        const double *cscale_dev, int32_t K, int32_t drop, double *band_dev,
                                         cudaStream_t stream);
+
+/* Element drop-off (Sec. 2.2, Sec. 3.4's T_Drop): the half-bandwidth K' <= K
+ * of the band kept after dropping the entries farthest from the diagonal,
+ * the smallest K' whose dropped entries (|I - J| > K') weigh at most `frac`
+ * of all, the weight of an entry being |(r_i a_ij) s_j| (rscale_dev /
+ * cscale_dev NULL: |a_ij|); K is the reordered matrix's half-bandwidth.
+ * frac = 0 keeps every entry (K' = K unless the outermost diagonals are
+ * empty); a large frac keeps the diagonal only (K' = 0: diagonal
+ * preconditioning).  Weights per distance from the diagonal are summed on the
+ * GPU.  Kdrop_out: host.  Errors: INVALID_ARG, OOM, CUDA.  Synchronises
+ * `stream`. */
+SAP_API sap_status_t sap_sparse_drop_bandwidth(int64_t n, int64_t nnz, const int64_t *rowptr_dev,
+                                               const int32_t *col_dev, const double *val_dev,
+                                               const int32_t *rownew_dev, const int32_t *colnew_dev,
+                                               const double *rscale_dev, const double *cscale_dev, int32_t K,
+                                               double frac, int32_t *Kdrop_out, cudaStream_t stream);
+
+/* Krylov operator of a handle other than its band (Sec. 2.2: the outer
+ * iteration runs on the reordered sparse matrix, the preconditioner is SaP of
+ * its dropped band): after this call sap_solve iterates on A' x = b', A' the
+ * reordered and scaled sparse matrix (entry (i, j) of the CSR matrix at
+ * (rownew[i], colnew[j]) with value (r_i a_ij) s_j; rownew_dev / colnew_dev
+ * NULL: identity; rscale_dev / cscale_dev NULL: 1), n equal to the handle's
+ * N; the handle's band stays the preconditioner's.  The arrays are borrowed
+ * (kept alive by the caller while the handle uses them).  rowptr_dev NULL
+ * restores the band as the operator.  Transposed solves (sap_solve_adjoint,
+ * sap_solve_pair, sap_grad_band) on a handle with a sparse operator return
+ * NOT_IMPLEMENTED.  Errors: INVALID_ARG, CUDA.  Synchronises the device (the
+ * handle's captured iterations are discarded). */
+SAP_API sap_status_t sap_set_operator_csr(sap_handle_t h, int64_t n, int64_t nnz, const int64_t *rowptr_dev,
+                                          const int32_t *col_dev, const double *val_dev,
+                                          const int32_t *rownew_dev, const int32_t *colnew_dev,
+                                          const double *rscale_dev, const double *cscale_dev);
 
 /* Right-hand side of the reordered system: out[rownew[i]] = r_i b_i
  * (rscale_dev NULL: r = 1).  Errors: INVALID_ARG, CUDA.  Asynchronous. */

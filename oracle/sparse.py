@@ -233,16 +233,44 @@ def bandwidth(n, rowptr, col, rownew, colnew):
     return K
 
 
-def to_band(n, rowptr, col, val, rownew, colnew, K, r=None, s=None):
+def to_band(n, rowptr, col, val, rownew, colnew, K, r=None, s=None, drop=False):
     """Band storage ((2K+1) * n, band[(K + I - J) * n + J] = entry (I, J)) of
     the matrix with entry (i, j) moved to (rownew[i], colnew[j]) and scaled to
-    (r_i a_ij) s_j when scale factors are given."""
+    (r_i a_ij) s_j when scale factors are given.  An entry outside the band is
+    dropped (drop) or an error."""
     band = np.zeros((2 * K + 1) * n)
     for i in range(n):
         I = int(rownew[i])
         for p in range(rowptr[i], rowptr[i + 1]):
             j = int(col[p])
             J = int(colnew[j])
+            if abs(I - J) > K:
+                if drop:
+                    continue
+                raise ValueError("entry outside the band")
             x = val[p] if r is None else (r[i] * val[p]) * s[j]
             band[(K + I - J) * n + J] = x
     return band
+
+
+# ---- element drop-off (Sec. 2.2) ----
+
+def dist_weights(n, rowptr, col, val, rownew, colnew, K, r=None, s=None):
+    """w[d] = sum of |(r_i a_ij) s_j| over the entries at distance |I - J| = d."""
+    w = np.zeros(K + 1)
+    for i in range(n):
+        I = int(rownew[i])
+        for p in range(rowptr[i], rowptr[i + 1]):
+            j = int(col[p])
+            d = abs(I - int(colnew[j]))
+            w[d] += abs(val[p]) if r is None else abs((r[i] * val[p]) * s[j])
+    return w
+
+
+def drop_bandwidth(w, frac):
+    """The smallest K' with sum_{d > K'} w[d] <= frac * sum_d w[d]."""
+    total = float(np.sum(w))
+    for Kp in range(len(w)):
+        if float(np.sum(w[Kp + 1:])) <= frac * total:
+            return Kp
+    return len(w) - 1

@@ -97,7 +97,9 @@ def _load():
         "sap_cm_reorder": (C.c_int, [i64, i64, vp, vp, vp, vp, P(C.c_int32), vp]),
         "sap_perm_compose": (C.c_int, [i64, vp, vp, vp, vp]),
         "sap_sparse_bandwidth": (C.c_int, [i64, i64, vp, vp, vp, vp, P(C.c_int32), vp]),
-        "sap_sparse_to_band": (C.c_int, [i64, i64, vp, vp, vp, vp, vp, vp, vp, i32, vp, vp]),
+        "sap_sparse_to_band": (C.c_int, [i64, i64, vp, vp, vp, vp, vp, vp, vp, i32, i32, vp, vp]),
+        "sap_sparse_drop_bandwidth": (C.c_int, [i64, i64, vp, vp, vp, vp, vp, vp, vp, i32, dbl, P(C.c_int32), vp]),
+        "sap_set_operator_csr": (C.c_int, [vp, i64, i64, vp, vp, vp, vp, vp, vp, vp]),
         "sap_sparse_permute_rhs": (C.c_int, [i64, vp, vp, vp, vp, vp]),
         "sap_sparse_unpermute_solution": (C.c_int, [i64, vp, vp, vp, vp, vp]),
     }
@@ -515,11 +517,34 @@ def sap_sparse_bandwidth(A: Csr, rownew=None, colnew=None, stream=None) -> int:
     return K.value
 
 
-def sap_sparse_to_band(A: Csr, rownew, colnew, K: int, rscale=None, cscale=None, stream=None) -> torch.Tensor:
+def sap_sparse_to_band(A: Csr, rownew, colnew, K: int, rscale=None, cscale=None, drop: bool = False,
+                       stream=None) -> torch.Tensor:
     band = torch.empty((2 * K + 1) * A.n, dtype=torch.float64, device=A.val.device)
     _check(_lib.sap_sparse_to_band(*_csr(A), _ptr(A.val), _i32(rownew), _i32(colnew), _tptr(rscale),
-                                   _tptr(cscale), K, _ptr(band), _stream(stream)), "sap_sparse_to_band")
+                                   _tptr(cscale), K, int(drop), _ptr(band), _stream(stream)), "sap_sparse_to_band")
     return band
+
+
+def sap_sparse_drop_bandwidth(A: Csr, rownew, colnew, K: int, frac: float, rscale=None, cscale=None,
+                              stream=None) -> int:
+    Kd = C.c_int32()
+    _check(_lib.sap_sparse_drop_bandwidth(*_csr(A), _ptr(A.val), _i32(rownew), _i32(colnew), _tptr(rscale),
+                                          _tptr(cscale), K, float(frac), C.byref(Kd), _stream(stream)),
+           "sap_sparse_drop_bandwidth")
+    return Kd.value
+
+
+def sap_set_operator_csr(h: Handle, A: Csr | None, rownew=None, colnew=None, rscale=None, cscale=None) -> None:
+    """Make the reordered sparse matrix the handle's Krylov operator (A None:
+    the band again); the tensors must outlive their use by the handle."""
+    if A is None:
+        _check(_lib.sap_set_operator_csr(h.ptr, 0, 0, None, None, None, None, None, None, None),
+               "sap_set_operator_csr")
+        h._csr_keep = None
+        return
+    _check(_lib.sap_set_operator_csr(h.ptr, *_csr(A), _ptr(A.val), _i32(rownew), _i32(colnew), _tptr(rscale),
+                                     _tptr(cscale)), "sap_set_operator_csr")
+    h._csr_keep = (A, rownew, colnew, rscale, cscale)
 
 
 def sap_sparse_permute_rhs(b: torch.Tensor, rownew: torch.Tensor, rscale=None, stream=None) -> torch.Tensor:

@@ -10,6 +10,7 @@
 #include <new>
 #include <vector>
 #include "sap_internal.cuh"
+#include "sap_sparse.h"
 #include "krylov.cuh"
 
 using namespace sap;
@@ -83,6 +84,9 @@ struct sap_handle {
   Layout L;
   sap_options_t opt{};
   const double* band = nullptr;
+  // Krylov operator other than the band (sap_set_operator_csr): the sparse
+  // matrix whose dropped band the preconditioner was built from
+  sap::CsrOp csr{};
   DevMem mem;
   Dev d{};
   const int64_t* dcbase = nullptr;   // per block offset of the chunk matrices
@@ -639,8 +643,15 @@ struct KrylovRun {
   int it = 0;            // outer iterations launched
   int gi = 0;
 
+  // the iteration's operator: the band, or the sparse operator set on the handle
+  cudaError_t spmv(const double* xin, double* yout, Gate g = Gate()) {
+    if (h->csr.rowptr) return launch_spmv_pcsr(h->csr, xin, yout, s, g);
+    return launch_spmv(h->band, N, h->L.K, xin, yout, tr, s, g);
+  }
+
   sap_status_t init(sap_handle* hh, const double* bu, double* xu, bool transposed, cudaStream_t us, int ws = 0) {
     h = hh; tr = transposed; user = us; b_user = bu; x_user = xu;
+    if (tr && h->csr.rowptr) return SAP_ERR_NOT_IMPLEMENTED;    // no transposed sparse operator
     cg = h->opt.krylov == SAP_KRYLOV_CG;
     TRY(ensure_stream(h));
     N = h->L.N;
@@ -723,7 +734,7 @@ struct KrylovRun {
   // the method from x: r^0 = M^{-1}(b - A x), r~0 = r^0, u^0 = 0, scalars reset
   sap_status_t exit_test(double qoff) {
     CK(kr_exit_check(kd, tol, qoff, s));
-    CK(launch_spmv(h->band, N, h->L.K, x, tmp, tr, s, gC));
+    CK(spmv(x, tmp, gC));
     CK(kr_residual(b, tmp, t, N, kc, S_TN2, s));
     CK(kr_exit_decide(kd, tol, qoff, s));
     if (qoff != 1.0) return SAP_OK;
@@ -736,11 +747,11 @@ struct KrylovRun {
   // one CG step (Saad, Alg. 9.1) with its exit test and, gated, the restart
   sap_status_t cg_step() {
     double *rr = r[0], *z = r[1], *p = u[0], *q = u[1];
-    CK(launch_spmv(h->band, N, h->L.K, p, q, tr, s, gA));          // q = A p
+    CK(spmv(p, q, gA));                                             // q = A p
     CK(kr_cg_alpha(p, q, N, ka, s));
     CK(kr_cg_xr(x, rr, p, q, N, ka, s));
     CK(kr_cg_check(kd, tol, s));
-    CK(launch_spmv(h->band, N, h->L.K, x, tmp, tr, s, gC));         // true residual, if flagged
+    CK(spmv(x, tmp, gC));                                           // true residual, if flagged
     CK(kr_residual(b, tmp, t, N, kc, S_TN2, s));
     CK(kr_cg_decide(kd, tol, h->opt.max_iters, s));
     CK(kr_copy(t, rr, N, kr, s));                                   // restart: r = b - A x
@@ -758,12 +769,12 @@ struct KrylovRun {
     for (int j = 0; j < 2; ++j) {
       CK(kr_bicg_rho(r[j], rt, N, ka, j, s));
       CK(kr_bicg_u(u[0], u[1], r[0], r[1], N, ka, j, s));
-      CK(launch_spmv(h->band, N, h->L.K, u[j], tmp, tr, s, gA));
+      CK(spmv(u[j], tmp, gA));
       TRY(h->impl->apply(tmp, u[j + 1], tr, s, gA));
       CK(kr_bicg_gamma(u[j + 1], rt, N, ka, s));
       CK(kr_bicg_r(r[0], r[1], u[0], u[1], u[2], x, N, ka, j, s));
       TRY(exit_test(j == 0 ? 0.25 : 0.75));
-      CK(launch_spmv(h->band, N, h->L.K, r[j], tmp, tr, s, gA));
+      CK(spmv(r[j], tmp, gA));
       TRY(h->impl->apply(tmp, r[j + 1], tr, s, gA));
     }
     CK(kr_mr(x, r[0], r[1], r[2], u[0], u[1], u[2], N, ka, s));
@@ -822,7 +833,7 @@ struct KrylovRun {
         inf.iters = h->opt.max_iters;
       }
       if (status != SAP_OK) {
-        CK(launch_spmv(h->band, N, h->L.K, x, tmp, tr, s));
+        CK(spmv(x, tmp));
         CK(kr_residual(b, tmp, t, N, kd, S_TN2, s));
         CK(cudaMemcpyAsync(hs, kd.S + S_RN2, 5 * sizeof(double), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
@@ -1403,6 +1414,35 @@ sap_status_t sap_selftest_wait_timeout(int32_t spin_limit, cudaStream_t s) {
 }
 
 int32_t sap_num_partitions(sap_handle_t h) { return h ? h->L.P : -1; }
+
+sap_status_t sap_set_operator_csr(sap_handle_t h, int64_t n, int64_t nnz, const int64_t* rowptr_dev,
+                                  const int32_t* col_dev, const double* val_dev, const int32_t* rownew_dev,
+                                  const int32_t* colnew_dev, const double* rscale_dev, const double* cscale_dev) {
+  if (!h) return SAP_ERR_INVALID_ARG;
+  if (rowptr_dev && (n != h->L.N || nnz < 0 || !col_dev || !val_dev || (rscale_dev == nullptr) != (cscale_dev == nullptr)))
+    return SAP_ERR_INVALID_ARG;
+  // the captured iterations embed the previous operator's launches
+  CK(cudaDeviceSynchronize());
+  for (int g = 0; g < 4; ++g) {
+    if (h->gexec[g]) cudaGraphExecDestroy(h->gexec[g]);
+    h->gexec[g] = nullptr;
+    h->gfailed[g] = false;
+    h->glaunches[g] = 0;
+  }
+  h->csr = sap::CsrOp{};
+  if (rowptr_dev) {
+    h->csr.n = n;
+    h->csr.nnz = nnz;
+    h->csr.rowptr = rowptr_dev;
+    h->csr.col = col_dev;
+    h->csr.val = val_dev;
+    h->csr.rownew = rownew_dev;
+    h->csr.colnew = colnew_dev;
+    h->csr.r = rscale_dev;
+    h->csr.s = cscale_dev;
+  }
+  return SAP_OK;
+}
 
 sap_status_t sap_get_partition(sap_handle_t h, int64_t* off) {
   if (!h || !off) return SAP_ERR_INVALID_ARG;

@@ -126,6 +126,21 @@ long long launches_so_far();
 // ---- launchers (each returns cudaGetLastError()) ----
 cudaError_t launch_spmv(const double* band, int64_t N, int K, const double* x, double* y,
                         bool transpose, cudaStream_t s, Gate gt = Gate());
+// A sparse operator in the reordered numbering of the sparse front end
+// (include/sap_sparse.h): entry (i, j) of the CSR matrix at (rownew[i],
+// colnew[j]) with value (r_i a_ij) s_j (r, s null: 1).  Borrowed pointers.
+struct CsrOp {
+  int64_t n = 0, nnz = 0;
+  const int64_t* rowptr = nullptr;
+  const int32_t* col = nullptr;
+  const double* val = nullptr;
+  const int32_t* rownew = nullptr;
+  const int32_t* colnew = nullptr;
+  const double* r = nullptr;
+  const double* s = nullptr;
+};
+// y = A' x for the reordered operator A' of a CsrOp (one warp per stored row).
+cudaError_t launch_spmv_pcsr(const CsrOp& A, const double* x, double* y, cudaStream_t s, Gate gt = Gate());
 cudaError_t launch_absmax(const double* band, int64_t N, int K, double* out, cudaStream_t s);
 cudaError_t launch_grad_band(const double* lam, const double* x, int64_t N, int K, double* g,
                              cudaStream_t s);

@@ -77,11 +77,13 @@ __global__ void k_bandwidth(int64_t n, const int64_t* __restrict__ rowptr, const
   if (lane == 0 && mi > 0) atomicMax(K, mi);
 }
 
-// band[(K + I - J) * n + J] = (r_i a_ij) s_j; an entry outside the band sets *bad.
+// band[(K + I - J) * n + J] = (r_i a_ij) s_j; an entry outside the band is
+// dropped (drop) or sets *bad.
 __global__ void k_to_band(int64_t n, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
                           const double* __restrict__ val, const int32_t* __restrict__ rownew,
                           const int32_t* __restrict__ colnew, const double* __restrict__ r,
-                          const double* __restrict__ s, int K, double* __restrict__ band, int* __restrict__ bad) {
+                          const double* __restrict__ s, int K, bool drop, double* __restrict__ band,
+                          int* __restrict__ bad) {
   const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (i >= n) return;
@@ -91,13 +93,58 @@ __global__ void k_to_band(int64_t n, const int64_t* __restrict__ rowptr, const i
     const int64_t J = colnew ? colnew[j] : j;
     const int64_t dd = K + I - J;
     if (dd < 0 || dd > 2 * K) {
-      atomicExch(bad, 1);
+      if (!drop) atomicExch(bad, 1);
       continue;
     }
     double x = val[p];
     if (r) x = (r[i] * x) * s[j];
     band[dd * n + J] = x;
   }
+}
+
+// y[rownew[i]] = sum_p ((r_i a_ip) s_j) x[colnew[j]], j = col[p]: the
+// reordered operator's row; one warp per stored row, partial sums combined
+// by shuffles.
+__global__ void k_spmv_pcsr(sap::CsrOp A, const double* __restrict__ x, double* __restrict__ y, sap::Gate gt) {
+  if (sap::gate_skip(gt)) return;
+  const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (i >= A.n) return;
+  const double ri = A.r ? A.r[i] : 1.0;
+  double acc = 0.0;
+  for (int64_t p = A.rowptr[i] + lane; p < A.rowptr[i + 1]; p += 32) {
+    const int32_t j = A.col[p];
+    const double e = A.r ? (ri * A.val[p]) * A.s[j] : A.val[p];
+    acc += e * x[A.colnew ? A.colnew[j] : j];
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) y[A.rownew ? A.rownew[i] : i] = acc;
+}
+
+// w[dist] += |(r_i a_ij) s_j| over the stored entries, dist = |I - J| <= K
+// (a per-CTA histogram in shared memory, then one atomic per bin).
+__global__ void k_dist_weights(int64_t n, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                               const double* __restrict__ val, const int32_t* __restrict__ rownew,
+                               const int32_t* __restrict__ colnew, const double* __restrict__ r,
+                               const double* __restrict__ s, int K, double* __restrict__ w) {
+  extern __shared__ double hist[];
+  for (int t = threadIdx.x; t <= K; t += blockDim.x) hist[t] = 0.0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += warps) {
+    const int64_t I = rownew ? rownew[i] : i;
+    for (int64_t p = rowptr[i] + lane; p < rowptr[i + 1]; p += 32) {
+      const int64_t j = col[p];
+      const int64_t J = colnew ? colnew[j] : j;
+      const int64_t dd = I > J ? I - J : J - I;
+      const double e = r ? fabs((r[i] * val[p]) * s[j]) : fabs(val[p]);
+      if (dd <= K) atomicAdd(&hist[dd], e);
+    }
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t <= K; t += blockDim.x)
+    if (hist[t] != 0.0) atomicAdd(&w[t], hist[t]);
 }
 
 __global__ void k_permute_rhs(int64_t n, const double* __restrict__ b, const int32_t* __restrict__ rownew,
@@ -463,7 +510,7 @@ extern "C" sap_status_t sap_sparse_bandwidth(int64_t n, int64_t nnz, const int64
 extern "C" sap_status_t sap_sparse_to_band(int64_t n, int64_t nnz, const int64_t* rowptr_dev,
                                            const int32_t* col_dev, const double* val_dev, const int32_t* rownew_dev,
                                            const int32_t* colnew_dev, const double* rscale_dev,
-                                           const double* cscale_dev, int32_t K, double* band_dev,
+                                           const double* cscale_dev, int32_t K, int32_t drop, double* band_dev,
                                            cudaStream_t stream) {
   if (!valid_csr_args(n, nnz, rowptr_dev, col_dev) || !val_dev || !band_dev || K < 0 || K >= n)
     return SAP_ERR_INVALID_ARG;
@@ -474,7 +521,8 @@ extern "C" sap_status_t sap_sparse_to_band(int64_t n, int64_t nnz, const int64_t
   CKS(cudaMemsetAsync(band_dev, 0, (size_t)(2 * K + 1) * n * sizeof(double), stream));
   sap::count_launches(1);
   k_to_band<<<blocks_for(n * 32, 256), 256, 0, stream>>>(n, rowptr_dev, col_dev, val_dev, rownew_dev, colnew_dev,
-                                                          rscale_dev, cscale_dev, K, band_dev, bad.p);
+                                                          rscale_dev, cscale_dev, K, drop != 0, band_dev,
+                                                          bad.p);
   CKS(cudaGetLastError());
   int b = 0;
   CKS(cudaMemcpyAsync(&b, bad.p, sizeof(int), cudaMemcpyDeviceToHost, stream));
@@ -500,3 +548,45 @@ extern "C" sap_status_t sap_sparse_unpermute_solution(int64_t n, const double* y
   CKS(cudaGetLastError());
   return SAP_OK;
 }
+
+extern "C" sap_status_t sap_sparse_drop_bandwidth(int64_t n, int64_t nnz, const int64_t* rowptr_dev,
+                                                  const int32_t* col_dev, const double* val_dev,
+                                                  const int32_t* rownew_dev, const int32_t* colnew_dev,
+                                                  const double* rscale_dev, const double* cscale_dev, int32_t K,
+                                                  double frac, int32_t* Kdrop_out, cudaStream_t stream) {
+  if (!valid_csr_args(n, nnz, rowptr_dev, col_dev) || !val_dev || !Kdrop_out || K < 0 || K >= n || !(frac >= 0.0))
+    return SAP_ERR_INVALID_ARG;
+  if ((rscale_dev == nullptr) != (cscale_dev == nullptr)) return SAP_ERR_INVALID_ARG;
+  DevBuf<double> w;
+  if (!w.alloc((size_t)K + 1)) return SAP_ERR_OOM;
+  CKS(cudaMemsetAsync(w.p, 0, ((size_t)K + 1) * sizeof(double), stream));
+  const size_t sm = ((size_t)K + 1) * sizeof(double);
+  if (sm > 48 * 1024) CKS(cudaFuncSetAttribute(k_dist_weights, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  int dev = 0, sms = 1;
+  CKS(cudaGetDevice(&dev));
+  CKS(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  sap::count_launches(1);
+  k_dist_weights<<<4 * sms, 256, sm, stream>>>(n, rowptr_dev, col_dev, val_dev, rownew_dev, colnew_dev, rscale_dev,
+                                                cscale_dev, K, w.p);
+  CKS(cudaGetLastError());
+  std::vector<double> wh((size_t)K + 1);
+  CKS(cudaMemcpyAsync(wh.data(), w.p, ((size_t)K + 1) * sizeof(double), cudaMemcpyDeviceToHost, stream));
+  CKS(cudaStreamSynchronize(stream));
+  double total = 0.0;
+  for (int d = 0; d <= K; ++d) total += wh[d];
+  // the smallest K' whose dropped tail sum_{d > K'} w[d] is at most frac * total
+  int Kd = K;
+  double tail = 0.0;
+  while (Kd > 0 && tail + wh[Kd] <= frac * total) tail += wh[Kd--];
+  *Kdrop_out = Kd;
+  return SAP_OK;
+}
+
+namespace sap {
+cudaError_t launch_spmv_pcsr(const CsrOp& A, const double* x, double* y, cudaStream_t s, Gate gt) {
+  count_launches(1);
+  k_spmv_pcsr<<<blocks_for(A.n * 32, 256), 256, 0, s>>>(A, x, y, gt);
+  return cudaGetLastError();
+}
+}  // namespace sap
+

@@ -165,3 +165,89 @@ def test_front_end_into_the_banded_solver(sap, scaled, variant):
     x = host(sap.sap_sparse_unpermute_solution(y, perm, s))
     xd = np.linalg.solve(OS.csr_to_dense(n, sysm.rowptr, sysm.col, sysm.val), b_np)
     assert np.linalg.norm(x - xd) / np.linalg.norm(xd) <= 1e-8
+
+
+def reordered(sap, sysm, scaled=True):
+    A = to_dev(sap, sysm)
+    rownew, r, s, _ = sap.sap_db_reorder(A, scale=scaled)
+    perm, K = sap.sap_cm_reorder(A, rownew)
+    rn = sap.sap_perm_compose(perm, rownew)
+    return A, rn, perm, r, s, K
+
+
+@pytest.mark.parametrize("frac", [0.0, 1e-3, 3e-2, 0.3, 2.0])
+def test_drop_bandwidth_meets_its_definition(sap, frac):
+    """K' satisfies the drop rule computed by the oracle from the same entries
+    (the GPU sums the weights in another order: within rounding)."""
+    sysm = G.sparse_scrambled(900, 6, 0.5, 1.0, 32)
+    A, rn, perm, r, s, K = reordered(sap, sysm)
+    Kp = sap.sap_sparse_drop_bandwidth(A, rn, perm, K, frac, r, s)
+    w = OS.dist_weights(sysm.n, sysm.rowptr, sysm.col, sysm.val, host(rn), host(perm), K, host(r), host(s))
+    tot = w.sum()
+    assert 0 <= Kp <= K
+    assert w[Kp + 1:].sum() <= frac * tot * (1 + 1e-12)
+    assert Kp == 0 or w[Kp:].sum() > frac * tot * (1 - 1e-12)
+    if frac == 0.0:
+        assert Kp == K
+    if frac >= 1.0:
+        assert Kp == 0
+
+
+def test_dropped_band_is_the_oracle_band(sap):
+    sysm = G.sparse_scrambled(700, 5, 0.5, 1.0, 33)
+    A, rn, perm, r, s, K = reordered(sap, sysm)
+    Kp = max(1, K // 2)
+    band = sap.sap_sparse_to_band(A, rn, perm, Kp, r, s, drop=True)
+    band_o = OS.to_band(sysm.n, sysm.rowptr, sysm.col, sysm.val, host(rn), host(perm), Kp, host(r), host(s),
+                        drop=True)
+    np.testing.assert_array_equal(host(band), band_o)
+
+
+@pytest.mark.parametrize("frac,variant", [(1e-3, 0), (2e-2, 0), (1e-3, 1)])
+def test_sparse_operator_with_a_dropped_band_preconditioner(sap, frac, variant):
+    """Sec. 2.2's sparse solve: the outer BiCGStab(2) on the reordered sparse
+    matrix (sap_set_operator_csr), SaP of its dropped band (K' < K) as the
+    preconditioner; the solution of the original system against a sparse
+    direct solve, and its true residual."""
+    sp = pytest.importorskip("scipy.sparse")
+    spl = pytest.importorskip("scipy.sparse.linalg")
+    n = 20000
+    sysm = G.sparse_scrambled(n, 16, 0.3, 1.0, 34)
+    A, rn, perm, r, s, K = reordered(sap, sysm)
+    Kp = sap.sap_sparse_drop_bandwidth(A, rn, perm, K, frac, r, s)
+    assert Kp < K
+    band = sap.sap_sparse_to_band(A, rn, perm, Kp, r, s, drop=True)
+    b_np = G.x_true(n, 34)
+    bb = sap.sap_sparse_permute_rhs(torch.from_numpy(b_np).cuda(), rn, r)
+    h = sap.sap_factor(band, n, Kp, P=8, variant=variant, precision=sap.SAP_FP32)
+    sap.sap_set_operator_csr(h, A, rn, perm, r, s)
+    y, info, st = sap.sap_solve(h, bb)
+    assert st == sap.SAP_OK and info.relres <= 1e-10
+    x = host(sap.sap_sparse_unpermute_solution(y, perm, s))
+    As = sp.csr_matrix((sysm.val, sysm.col, sysm.rowptr), shape=(n, n))
+    assert np.linalg.norm(b_np - As @ x) / np.linalg.norm(b_np) <= 1e-9
+    xd = spl.spsolve(As.tocsc(), b_np)
+    assert np.linalg.norm(x - xd) / np.linalg.norm(xd) <= 1e-8
+    # transposed solves are not defined for a sparse operator
+    _, _, st2 = sap.sap_solve_adjoint(h, bb, raise_on_error=False)
+    assert st2 == sap.SAP_ERR_NOT_IMPLEMENTED
+
+
+def test_sparse_operator_without_drop_is_the_band_solve(sap):
+    """No drop-off: the sparse operator is the band's matrix, so the solve
+    reaches the band-operator solution (to the iteration's tolerance); then
+    the band restored as the operator."""
+    n = 6000
+    sysm = G.sparse_scrambled(n, 8, 0.4, 1.0, 35)
+    A, rn, perm, r, s, K = reordered(sap, sysm)
+    band = sap.sap_sparse_to_band(A, rn, perm, K, r, s)
+    bb = sap.sap_sparse_permute_rhs(torch.from_numpy(G.x_true(n, 35)).cuda(), rn, r)
+    h = sap.sap_factor(band, n, K, P=4, variant=sap.SAP_D, precision=sap.SAP_FP32)
+    y1, i1, st1 = sap.sap_solve(h, bb)
+    sap.sap_set_operator_csr(h, A, rn, perm, r, s)
+    y2, i2, st2 = sap.sap_solve(h, bb)
+    assert st1 == st2 == sap.SAP_OK
+    assert np.linalg.norm(host(y2) - host(y1)) / np.linalg.norm(host(y1)) <= 1e-9
+    sap.sap_set_operator_csr(h, None)
+    y3, _, st3 = sap.sap_solve(h, bb)
+    assert st3 == sap.SAP_OK and torch.equal(y3, y1)

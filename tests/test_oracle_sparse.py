@@ -186,3 +186,30 @@ def test_reordered_band_solve_is_the_dense_solve(scale):
     A = OS.csr_to_dense(S.n, S.rowptr, S.col, S.val)
     xd = np.linalg.solve(A, b)
     assert np.linalg.norm(x - xd) / np.linalg.norm(xd) <= 1e-10
+
+
+@pytest.mark.parametrize("frac", [0.0, 1e-4, 1e-2, 0.2, 5.0])
+def test_drop_bandwidth_from_the_entry_list(frac):
+    """The drop-off's K' against the tail sums taken directly over the stored
+    entries: the smallest K' whose dropped entries weigh at most frac of all."""
+    S = G.sparse_scrambled(120, 6, 0.5, 1.0, 13)
+    db = OS.db_match(S.n, S.rowptr, S.col, S.val)
+    perm = OS.cm_order(S.n, OS.sym_pattern(S.n, S.rowptr, S.col, db.sigma))
+    rn, cn = perm[db.sigma], perm
+    r, s = OS.db_scaling(db.a, db.u, db.v)
+    K = OS.bandwidth(S.n, S.rowptr, S.col, rn, cn)
+    Kp = OS.drop_bandwidth(OS.dist_weights(S.n, S.rowptr, S.col, S.val, rn, cn, K, r, s), frac)
+    ent = [(abs(int(rn[i]) - int(cn[S.col[p]])), abs((r[i] * S.val[p]) * s[S.col[p]]))
+           for i in range(S.n) for p in range(S.rowptr[i], S.rowptr[i + 1])]
+    total = sum(e for _, e in ent)
+    tail = lambda k: sum(e for d, e in ent if d > k)
+    assert tail(Kp) <= frac * total * (1 + 1e-12)
+    assert Kp == 0 or tail(Kp - 1) > frac * total
+    if frac == 0.0:
+        assert Kp == K
+    if frac >= 1.0:
+        assert Kp == 0
+    band = OS.to_band(S.n, S.rowptr, S.col, S.val, rn, cn, Kp, r, s, drop=True)
+    kept = sum(abs(x) for x in band)
+    assert kept == pytest.approx(total - tail(Kp), rel=1e-12)
+

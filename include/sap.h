@@ -74,9 +74,12 @@ typedef enum { SAP_FP64 = 0, SAP_FP32 = 1, SAP_FP32_BF16TU = 2 } sap_precision_t
  * recursive residual confirmed by the true one, and restarts from the
  * current x when the confirmation fails.  SaP-D's M is SPD for SPD A;
  * SaP-C's truncated-spike M need not be symmetric.  Both run device-driven
- * (every launch gated on device flags, one captured CUDA graph per round: one
- * BiCGStab(2) iteration or four CG steps) with one host readback per round;
- * sap_solve_pair and the batch calls run either. */
+ * (every launch gated on device flags; a round, one BiCGStab(2) iteration or
+ * four CG steps, is one captured CUDA graph): the whole loop is one launch of
+ * a graph whose conditional WHILE node repeats the round until the device
+ * flags the exit or the iteration cap, with one host readback at the end;
+ * where such a graph cannot be built, the round's graph is replayed with one
+ * host readback per round.  sap_solve_pair and the batch calls run either. */
 typedef enum { SAP_KRYLOV_BICGSTAB2 = 0, SAP_KRYLOV_CG = 1 } sap_krylov_t;
 
 typedef struct {
@@ -134,7 +137,7 @@ typedef struct {
                              matrices fit in shared memory one kernel per interface also
                              forms Rbar_i, its GEPP and inverse, and they count here */
     int32_t segments;     /* sweep segments per block in use (sap_options_t.segments) */
-    int32_t graphed;      /* 1 if the iterations ran as replays of one captured CUDA graph */
+    int32_t graphed;      /* 1 if the iterations ran from captured CUDA graphs (the device loop or per-round replays) */
     int32_t tc_update;    /* 1 if the block LU/UL trailing updates ran on the tensor cores */
     int32_t P;            /* partition count in use (the autotuner's choice when P = 0) */
     float t_bc_ms;        /* SaP-C T_BC (Sec. 4.3.2 breakdown): 0, B_i and C_{i+1} are read in
@@ -330,9 +333,10 @@ SAP_API sap_status_t sap_autotune(const double *band_dev, int64_t N, int32_t K, 
  * Not in the paper (a GB300 addition): n systems of their own N_i and K_i,
  * each with its own SaP preconditioner, factored and solved together.  Every
  * system runs on its own internal stream, so their kernels overlap on the
- * GPU; a batched solve advances all unfinished systems by one outer
- * BiCGStab(2) iteration per round (each a replay of the system's captured
- * CUDA graph) and synchronises the host once per round for the whole batch.
+ * GPU; a batched solve launches every unfinished system's device-driven
+ * Krylov loop (see sap_krylov_t; where it cannot run, one outer iteration per
+ * round, a replay of the system's captured graph) and synchronises the host
+ * once per round for the whole batch.
  *   opt applies to every system; opt->P == 0 picks P_i per system so that
  *   the batch has about two blocks per SM in total, P_i in proportion to N_i
  *   (at least 1; SaP-C keeps N_i / P_i >= 2 K_i); opt->segments == 0 means

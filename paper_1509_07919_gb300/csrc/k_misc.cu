@@ -583,6 +583,18 @@ cudaError_t kr_restart(const double* r0, double* rt, double* u0, int64_t n, Kryl
   k_restart<<<krylov_grid(n), RT, 0, s>>>(r0, rt, u0, n, kd);
   return cudaGetLastError();
 }
+__global__ void k_while_next(cudaGraphConditionalHandle hnd, int* flags, int step, int cap) {
+  const int c = flags[F_ROUNDS] + step;
+  flags[F_ROUNDS] = c;
+  cudaGraphSetConditional(hnd, (flags[F_DONE] == 0 && c < cap) ? 1u : 0u);
+}
+
+cudaError_t kr_while_next(cudaGraphConditionalHandle hnd, int* flags, int step, int cap, cudaStream_t s) {
+  count_launches(1);
+  k_while_next<<<1, 1, 0, s>>>(hnd, flags, step, cap);
+  return cudaGetLastError();
+}
+
 cudaError_t kr_exit_decide(KrylovDev kd, double tol, double qoff, cudaStream_t s) {
   count_launches(1);
   k_exit_decide<<<1, 32, 0, s>>>(kd, tol, qoff);

@@ -49,6 +49,10 @@ cudaError_t kr_exit_check(KrylovDev kd, double tol, double qoff, cudaStream_t s)
 // Second half, after the gated true residual: accept (finish) or flag the
 // residual replacement; qoff == 1 also completes the outer iteration.
 cudaError_t kr_exit_decide(KrylovDev kd, double tol, double qoff, cudaStream_t s);
+// End of one round of the device-driven loop: flags[F_ROUNDS] += step, and
+// the loop's WHILE condition set to continue while the solve is not done and
+// the count is below cap.
+cudaError_t kr_while_next(cudaGraphConditionalHandle hnd, int* flags, int step, int cap, cudaStream_t s);
 // Preconditioned CG (Saad, Alg. 9.1), each launch gated by kd.gmode: p = z
 // with (r, z) -> S_RHO0; alpha = S_RHO0 / (p, q); x += alpha p, r -= alpha q
 // with ||r||^2 -> S_RN2; beta = (r, z) / S_RHO0 (S_RHO0 updated);

@@ -100,6 +100,11 @@ struct sap_handle {
   // (0 forward, 1 adjoint) and Krylov workspace (+2: the second one);
   // captured on first use, replayed per iteration
   cudaGraphExec_t gexec[4] = {nullptr, nullptr, nullptr, nullptr};
+  // the whole iteration loop as one graph: a WHILE node whose body is one
+  // round (the iteration and the round counter that sets its condition)
+  cudaGraphExec_t wexec[4] = {nullptr, nullptr, nullptr, nullptr};
+  bool wfailed[4] = {false, false, false, false};
+  long long wlaunches[4] = {0, 0, 0, 0};   // kernels in one round of it
   cudaStream_t ks = nullptr;          // internal stream of the iteration (capturable)
   // background stream of the transposed sweep matrices (see Solver::factor_post)
   cudaStream_t ts = nullptr;
@@ -143,6 +148,8 @@ struct sap_handle {
   std::unique_ptr<SolverBase> impl;
   ~sap_handle() {
     for (cudaGraphExec_t g : gexec)
+      if (g) cudaGraphExecDestroy(g);
+    for (cudaGraphExec_t g : wexec)
       if (g) cudaGraphExecDestroy(g);
     if (ks) cudaStreamDestroy(ks);
     if (ts) cudaStreamDestroy(ts);
@@ -483,7 +490,12 @@ struct Solver : SolverBase {
       CK(launch_apply<T>(h->band, h->L.N, h->L.K, h->L.P, h->d, f, h->opt.variant, false, r, z, scratch, s, gt));
       return SAP_OK;
     }
-    TRY(prepare_transposed(s));
+    // inside a stream capture (a Krylov run's captured iteration) the run's
+    // begin() has prepared the transposed data on the caller's stream: no wait
+    // on the background build's event may enter the graph
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs == cudaStreamCaptureStatusNone)
+      TRY(prepare_transposed(s));
     Factors<T> ft = f;              // transposed applies own their scratch and segment tails
     ft.tails = tails_t;
     CK(launch_apply<T>(h->band, h->L.N, h->L.K, h->L.P, h->d, ft, h->opt.variant, true, r, z, scratch_t, s, gt));
@@ -801,7 +813,71 @@ struct KrylovRun {
     count_launches(-(int)h->glaunches[gi]);     // captured, not run
   }
   // CG: the device finishes the solve at the iteration cap (a round may end early)
-  bool active() const { return !done && it < h->opt.max_iters + (cg ? kCgSteps : 0); }
+  int step() const { return cg ? kCgSteps : 1; }
+  int cap() const { return h->opt.max_iters + (cg ? kCgSteps : 0); }
+  bool active() const { return !done && it < cap(); }
+  // The whole loop as one graph launch: a conditional WHILE node whose body is
+  // one round, ended by kr_while_next, which counts the rounds in
+  // flags[F_ROUNDS] and keeps the node going while the solve is not done and
+  // the count is below the cap; built once per handle and direction.  Returns
+  // false where conditional graphs are unavailable (the host loop then runs).
+  bool device_loop = false;
+  void build_while() {
+    const long long l0 = launches_so_far();
+    cudaGraph_t parent = nullptr, round_g = nullptr;
+    cudaGraphConditionalHandle hnd = 0;
+    cudaGraphNode_t node = nullptr, child = nullptr;
+    bool ok = cudaGraphCreate(&parent, 0) == cudaSuccess;
+    ok = ok && cudaGraphConditionalHandleCreate(&hnd, parent, 1, cudaGraphCondAssignDefault) == cudaSuccess;
+    // one round captured on its own first; a conditional body takes it only
+    // if it holds kernel, memset, memcpy, empty and child-graph nodes alone
+    if (ok) {
+      ok = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+      sap_status_t cst = ok ? iteration() : SAP_ERR_CUDA;
+      if (ok && cst == SAP_OK && kr_while_next(hnd, flags, step(), cap(), s) != cudaSuccess) cst = SAP_ERR_CUDA;
+      if (ok) ok = cudaStreamEndCapture(s, &round_g) == cudaSuccess && cst == SAP_OK && round_g;
+    }
+    if (ok) {
+      size_t nn = 0;
+      ok = cudaGraphGetNodes(round_g, nullptr, &nn) == cudaSuccess;
+      std::vector<cudaGraphNode_t> nodes(nn);
+      if (ok && nn) ok = cudaGraphGetNodes(round_g, nodes.data(), &nn) == cudaSuccess;
+      for (size_t q = 0; ok && q < nn; ++q) {
+        cudaGraphNodeType ty;
+        ok = cudaGraphNodeGetType(nodes[q], &ty) == cudaSuccess &&
+             (ty == cudaGraphNodeTypeKernel || ty == cudaGraphNodeTypeMemset || ty == cudaGraphNodeTypeMemcpy ||
+              ty == cudaGraphNodeTypeEmpty || ty == cudaGraphNodeTypeGraph);
+      }
+    }
+    cudaGraphNodeParams p{};
+    p.type = cudaGraphNodeTypeConditional;
+    p.conditional.handle = hnd;
+    p.conditional.type = cudaGraphCondTypeWhile;
+    p.conditional.size = 1;
+    ok = ok && cudaGraphAddNode(&node, parent, nullptr, nullptr, 0, &p) == cudaSuccess;
+    ok = ok && cudaGraphAddChildGraphNode(&child, p.conditional.phGraph_out[0], nullptr, 0, round_g) == cudaSuccess;
+    ok = ok && cudaGraphInstantiate(&h->wexec[gi], parent, 0) == cudaSuccess;
+    if (round_g) cudaGraphDestroy(round_g);
+    if (parent) cudaGraphDestroy(parent);
+    if (!ok) {
+      if (h->wexec[gi]) cudaGraphExecDestroy(h->wexec[gi]);
+      h->wexec[gi] = nullptr;
+      h->wfailed[gi] = true;
+      cudaGetLastError();
+    }
+    h->wlaunches[gi] = launches_so_far() - l0;
+    count_launches(-(int)h->wlaunches[gi]);     // captured, not run
+  }
+  bool launch_device_loop() {
+    if (!h->wexec[gi] && !h->wfailed[gi]) build_while();
+    if (!h->wexec[gi]) return false;
+    if (cudaGraphLaunch(h->wexec[gi], s) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    device_loop = true;
+    return true;
+  }
   // one outer iteration and the readback of the control flags
   sap_status_t round() {
     capture();
@@ -824,6 +900,7 @@ struct KrylovRun {
       CK(cudaMemcpyAsync(hf, flags, F_COUNT * sizeof(int), cudaMemcpyDeviceToHost, s));
       CK(cudaStreamSynchronize(s));
       inf.n_restarts = hf[F_RESTARTS];
+      if (device_loop) count_launches((int)((hf[F_ROUNDS] / step()) * h->wlaunches[gi]));
       if (hf[F_DONE]) {
         status = (sap_status_t)hf[F_STATUS];
         inf.iters = hs[S_QUART];
@@ -858,7 +935,7 @@ struct KrylovRun {
     inf.t_rdcd_ms = h->t_rdcd_ms;
     inf.P = h->L.P;
     inf.segments = h->L.S;
-    inf.graphed = (h->gexec[gi] != nullptr) ? 1 : 0;
+    inf.graphed = (h->gexec[gi] != nullptr || device_loop) ? 1 : 0;
     inf.tc_update = h->impl->tc_used() ? 1 : 0;
     unsigned long long nb = 0;
     CK(cudaMemcpy(&nb, h->n_boosted, sizeof(nb), cudaMemcpyDeviceToHost));
@@ -885,6 +962,7 @@ sap_status_t krylov(sap_handle* h, const double* b_user, double* x_user, bool tr
   TRY(k.begin());
   CK(cudaStreamSynchronize(k.s));
   k.after_begin();
+  if (k.active() && k.launch_device_loop()) return k.finish(info);
   while (k.active()) {
     TRY(k.round());
     CK(cudaStreamSynchronize(k.s));
@@ -1142,6 +1220,9 @@ sap_status_t run_lockstep(std::vector<KrylovRun>& k) {
     CK(cudaStreamSynchronize(k[i].s));
     k[i].after_begin();
   }
+  // every run whose loop can go on the device: one launch each, no rounds
+  for (size_t i = 0; i < n; ++i)
+    if (k[i].active() && k[i].launch_device_loop()) k[i].done = true;
   std::vector<char> ran(n);
   for (;;) {
     bool any = false;
@@ -1301,6 +1382,8 @@ sap_status_t sap_solve_pair(sap_handle_t h, const double* b, double* x, const do
     CK(cudaStreamSynchronize(r.s));
     r.after_begin();
   }
+  for (auto& r : k)
+    if (r.active() && r.launch_device_loop()) r.done = true;     // finished by the device, read in finish()
   for (;;) {
     bool ran[2] = {k[0].active(), k[1].active()};
     if (!ran[0] && !ran[1]) break;
@@ -1425,9 +1508,10 @@ sap_status_t sap_set_operator_csr(sap_handle_t h, int64_t n, int64_t nnz, const 
   CK(cudaDeviceSynchronize());
   for (int g = 0; g < 4; ++g) {
     if (h->gexec[g]) cudaGraphExecDestroy(h->gexec[g]);
-    h->gexec[g] = nullptr;
-    h->gfailed[g] = false;
-    h->glaunches[g] = 0;
+    if (h->wexec[g]) cudaGraphExecDestroy(h->wexec[g]);
+    h->gexec[g] = h->wexec[g] = nullptr;
+    h->gfailed[g] = h->wfailed[g] = false;
+    h->glaunches[g] = h->wlaunches[g] = 0;
   }
   h->csr = sap::CsrOp{};
   if (rowptr_dev) {

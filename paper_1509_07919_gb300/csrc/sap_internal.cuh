@@ -88,7 +88,7 @@ struct Factors {
 // (flags[F_CHECK]) and the residual replacement only when the true residual
 // failed (flags[F_REPLACE]).  Kernels read the flags at entry and return
 // uniformly per CTA, so a gated-off launch costs only its launch.
-enum FlagSlot { F_DONE = 0, F_CHECK, F_REPLACE, F_STATUS, F_RESTARTS, F_COUNT };
+enum FlagSlot { F_DONE = 0, F_CHECK, F_REPLACE, F_STATUS, F_RESTARTS, F_ROUNDS, F_COUNT };
 // G_KEEP: active and no restart flagged (the CG step's own p update).
 enum GateMode { G_ALWAYS = 0, G_ACTIVE = 1, G_CHECK = 2, G_REPLACE = 3, G_KEEP = 4 };
 struct Gate {

@@ -277,3 +277,73 @@ def sparse_scrambled(n: int, K0: int, fill: float, d: float, seed: int) -> Spars
     rowsrc = np.empty(n, dtype=np.int64)
     rowsrc[sym] = rowshuf                  # final row sym[i] holds M0 row rowshuf[i]
     return SparseSystem(n, rowptr, ci.astype(np.int32), vv, K0, rowsrc, sym)
+
+
+@dataclass
+class BlockScrambled:
+    """A banded matrix (half-bandwidth K) whose diagonal blocks [off[i],
+    off[i+1]) are narrow bands in hidden numberings: block entry (a, b) is
+    nonzero iff |hid[a] - hid[b]| <= k0[i] (hid: local index -> hidden one,
+    a permutation inside windows of `window` indices), with the full K x K
+    coupling corners between neighbouring blocks."""
+    band: np.ndarray      # float64, (2K+1) N
+    N: int
+    K: int
+    off: np.ndarray       # int64, P + 1 (given)
+    k0: np.ndarray        # int64, P: hidden half-bandwidth of each block
+    hid: np.ndarray       # int64, N: hidden local index of each local index
+    window: int
+
+
+def block_scrambled(N: int, K: int, off, d: float, seed: int, k0_lo: float = 0.4) -> BlockScrambled:
+    """Synthetic input of the third-stage reordering (Sec. 2.2): after the
+    DB-CM reorderings the band (half-bandwidth K) is sparse inside, and each
+    diagonal block reordered on its own has a bandwidth of its own.  Values
+    as in dense_banded (same seed and stream 0; diagonal d times the row's
+    off-diagonal abs-sum, couplings included); the pattern of block i is a
+    dense band of half-bandwidth k0_i <= w (k0_i = round(w u), u ~ U(k0_lo, 1),
+    stream 15) seen through a random permutation inside consecutive windows of
+    w = (K + 1) // 2 indices (stream 16): two indices within k0_i of each other
+    in the hidden numbering are at most 2w - 1 <= K apart, so every entry lies
+    in the band.  `off` is the block partition (P + 1 offsets)."""
+    off = np.asarray(off, dtype=np.int64)
+    P = len(off) - 1
+    w = (K + 1) // 2
+    if w < 1:
+        raise ValueError("need K >= 1")
+    W = 2 * K + 1
+    band = uniform(seed, 0, W * N).reshape(W, N)
+    band[~_valid_mask(N, K)] = 0.0
+    band[K, :] = 0.0
+    u = uniform(seed, 15, P) * 0.5 + 0.5
+    k0 = np.maximum(1, np.rint(w * (k0_lo + (1.0 - k0_lo) * u))).astype(np.int64)
+    k0 = np.minimum(k0, w)
+    draws = uniform(seed, 16, N)
+    hid = np.empty(N, dtype=np.int64)
+    blk = np.empty(N, dtype=np.int64)
+    for i in range(P):
+        s, e = int(off[i]), int(off[i + 1])
+        blk[s:e] = i
+        for a0 in range(s, e, w):
+            a1 = min(e, a0 + w)
+            hid[a0:a1] = (a0 - s) + np.argsort(draws[a0:a1], kind="stable")
+    j = np.arange(N)
+    for c in range(W):
+        if c == K:
+            continue
+        i = j + c - K
+        ok = (i >= 0) & (i < N)
+        ii, jj = i[ok], j[ok]
+        same = blk[ii] == blk[jj]
+        far = np.abs(hid[ii] - hid[jj]) > k0[blk[jj]]
+        row = band[c]
+        row[jj[same & far]] = 0.0
+    rowsum = np.zeros(N)
+    for c in range(W):
+        if c == K:
+            continue
+        lo = max(0, K - c)
+        hi = min(N, N + K - c)
+        rowsum[lo + c - K: hi + c - K] += np.abs(band[c, lo:hi])
+    band[K, :] = d * rowsum
+    return BlockScrambled(band.reshape(-1), N, K, off, k0, hid, w)

@@ -65,6 +65,8 @@ def parse():
                     help="SaP variant (default: the workload's, else D)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-compare", action="store_true", help="skip the FP64 / other-variant comparison runs")
+    ap.add_argument("--blocks", action="store_true",
+                    help="SaP with per-block bandwidths (third-stage reordering) against SaP on the whole band")
     ap.add_argument("--sparse", action="store_true",
                     help="time the sparse front end (Sec. 2.2) and the solve of the reordered band")
     ap.add_argument("--sweep", default=None, choices=["P", "d"],
@@ -869,10 +871,72 @@ def run_sparse(args, n=200000, K0=50, fill=0.1, d=1.0, seed=41, out=sys.stdout):
     return line
 
 
+def run_blocks(args, N=200000, K=100, P=50, d=1.0, seed=90, reps=5, out=sys.stdout):
+    """--blocks: SaP with a bandwidth of its own per block (the third-stage
+    reordering of Sec. 2.2) against SaP on the whole band, on a synthetic band
+    whose blocks are scrambled narrow bands (sap_inputs.block_scrambled,
+    half-bandwidth K, hidden per-block bandwidths in [0.4, 1] (K + 1) / 2):
+    the per-block CM, then for SaP-D and SaP-C with FP32 factors the refactor
+    (median over `reps`, L2 flushed before each; the phase timers of
+    sap_info_t) and the solve.  The entire-spike kernel's work is reported
+    against the FP32 FMA rate (t_spk_ms brackets that kernel alone)."""
+    import numpy as np
+    import torch
+    import sap_inputs as G
+    import paper_1509_07919_gb300 as S
+
+    off = np.asarray([0] + [N // P + (1 if i < N % P else 0) for i in range(P)]).cumsum()
+    sysm = G.block_scrambled(N, K, off, d, seed)
+    band = torch.from_numpy(sysm.band).cuda()
+    xt = torch.from_numpy(G.x_true(N, seed)).cuda()
+    b = S.sap_spmv(band, N, K, xt)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    torch.cuda.synchronize()
+    w0 = time.perf_counter()
+    perm, Ki = S.sap_block_cm_reorder(band, N, K, P)
+    t_cm = (time.perf_counter() - w0) * 1e3
+    line = {"blocks": {"N": N, "K": K, "P": P, "d": d, "K_i_min": min(Ki), "K_i_max": max(Ki),
+                       "K_i_mean": float(np.mean(Ki))},
+            "ms": {"block_cm": t_cm}, "precision": "fp32 factors, fp64 Krylov"}
+    for tag, var in (("D", S.SAP_D), ("C", S.SAP_C)):
+        row = {}
+        for kind in ("blocks", "whole_band"):
+            h = (S.sap_factor_blocks(band, N, K, perm, P=P, variant=var, precision=S.SAP_FP32) if kind == "blocks"
+                 else S.sap_factor(band, N, K, P=P, variant=var, precision=S.SAP_FP32))
+            x = torch.empty_like(b)
+            rec = {k: [] for k in ("t_factor_ms", "t_lu_ms", "t_spk_ms", "t_rdcd_ms", "t_kry_ms", "iters")}
+            st = 0
+            for _ in range(reps):
+                flush.fill_(1.0)
+                S.sap_refactor(h)
+                _, info, st = S.sap_solve(h, b, x, raise_on_error=False)
+                for k in rec:
+                    rec[k].append(getattr(info, k))
+            row[kind] = {k: statistics.median(v) for k, v in rec.items()}
+            row[kind]["status"] = st
+            row[kind]["err_x"] = float((x - xt).abs().max() / xt.abs().max())
+            row[kind]["total_ms"] = row[kind]["t_factor_ms"] + row[kind]["t_kry_ms"]
+            del h
+        if var == S.SAP_C:
+            # entire spikes: forward from the first nonzero row (about the whole
+            # block on average), backward over all rows: 2 n_b K_b K FMAs per
+            # sweep and spike column set
+            fl = sum(2.0 * 2 * 2 * (off[i + s + 1] - off[i + s]) * Ki[i + s] * K for i in range(P - 1) for s in (0, 1))
+            ms = row["blocks"]["t_spk_ms"]
+            row["spike_kernel"] = {"flops_upper": fl, "tflops": fl / (ms * 1e-3) / 1e12 if ms > 0 else None,
+                                   "note": "upper bound of the work (the forward sweep starts at the first "
+                                           "row with a nonzero right-hand side)"}
+        line[tag] = row
+    print(json.dumps(line), file=out, flush=True)
+    return line
+
+
 def main():
     args = parse()
     if args.sparse:
         run_sparse(args)
+    elif args.blocks:
+        run_blocks(args)
     elif args.sweep:
         run_sweep(args)
     elif args.impl == "reference":

@@ -102,6 +102,9 @@ def _load():
         "sap_set_operator_csr": (C.c_int, [vp, i64, i64, vp, vp, vp, vp, vp, vp, vp]),
         "sap_sparse_permute_rhs": (C.c_int, [i64, vp, vp, vp, vp, vp]),
         "sap_sparse_unpermute_solution": (C.c_int, [i64, vp, vp, vp, vp, vp]),
+        "sap_block_cm_reorder": (C.c_int, [vp, i64, i32, i32, vp, vp, vp]),
+        "sap_factor_blocks": (C.c_int, [vp, i64, i32, vp, P(sap_options_t), vp, P(vp)]),
+        "sap_get_block_bandwidths": (C.c_int, [vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -560,3 +563,32 @@ def sap_sparse_unpermute_solution(y: torch.Tensor, colnew: torch.Tensor, cscale=
                                               _stream(stream)), "sap_sparse_unpermute_solution")
     return x
 
+
+
+# ---- per-block bandwidths: the third-stage reordering (include/sap_blocks.h) ----
+
+def sap_block_cm_reorder(band: torch.Tensor, N: int, K: int, P: int, stream=None):
+    """Cuthill-McKee of every block of the partition on its own: returns
+    (perm, K_i), perm (int32, device) local to each block, K_i (list)."""
+    perm = torch.empty(N, dtype=torch.int32, device=band.device)
+    Ki = (C.c_int32 * P)()
+    _check(_lib.sap_block_cm_reorder(_ptr(band), N, K, P, _i32(perm), Ki, _stream(stream)),
+           "sap_block_cm_reorder")
+    return perm, list(Ki)
+
+
+def sap_factor_blocks(band: torch.Tensor, N: int, K: int, perm: torch.Tensor, opts: sap_options_t | None = None,
+                      stream=None, **kw) -> Handle:
+    """SaP with every block reordered by perm and factored at its own K_i."""
+    opts = opts or sap_default_options(**kw)
+    out = C.c_void_p()
+    _check(_lib.sap_factor_blocks(_ptr(band), N, K, _i32(perm), C.byref(opts), _stream(stream), C.byref(out)),
+           "sap_factor_blocks")
+    return Handle(out.value, band, N, K, opts)
+
+
+def sap_get_block_bandwidths(h: Handle) -> list:
+    P = sap_num_partitions(h)
+    Ki = (C.c_int32 * P)()
+    _check(_lib.sap_get_block_bandwidths(h.ptr, Ki), "sap_get_block_bandwidths")
+    return list(Ki)

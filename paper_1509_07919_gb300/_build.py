@@ -15,7 +15,7 @@ CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libsap.so")
 BUILD = os.path.join(HERE, "_build")
 SOURCES = ["k_factor.cu", "k_apply.cu", "k_spike.cu", "k_misc.cu", "k_chunk.cu", "sap_api.cu", "sap_noalloc.cu",
-           "sap_sparse.cu"]
+           "sap_sparse.cu", "k_blocks.cu"]
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
               "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden", "--expt-relaxed-constexpr",
               "-I", os.path.join(os.path.dirname(HERE), "include")]

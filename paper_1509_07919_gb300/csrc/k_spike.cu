@@ -601,6 +601,41 @@ cudaError_t launch_spikes(const double* band, int64_t N, int K, int P, Dev d, co
   return cudaGetLastError();
 }
 
+size_t reduced_ws_bytes(int K, int nI, bool fp64) { return (size_t)nI * spike_ws_stride(K, fp64 ? 8 : 4); }
+
+template <typename T>
+cudaError_t launch_reduced(const T* V, const T* Wt, int K, int nI, double* Rinv, double* R0, int* piv, int* singular,
+                           void* gscratch, cudaStream_t s) {
+  if (nI < 1) return cudaSuccess;
+  if (!gscratch) return cudaErrorInvalidValue;
+  unsigned char* gws = static_cast<unsigned char*>(gscratch);
+  const int tiles = (K + RT - 1) / RT;
+  count_launches(2);
+  k_rbar_form<T><<<dim3(tiles, tiles, nI), 256, 0, s>>>(V, Wt, K, R0, gws);
+  for (int k0 = 0; k0 < K; k0 += kGeppNB) {
+    count_launches(1);
+    k_gepp_panel<T><<<nI, kPanelThreads, 0, s>>>(K, k0, gws, piv, singular);
+    const int m = K - k0 - kGeppNB;
+    if (m > 0) {
+      const int t = (m + 63) / 64;
+      count_launches(1);
+      k_gepp_update<T><<<dim3(t, t, nI), 256, 0, s>>>(K, k0, gws);
+    }
+  }
+  const size_t ism = (size_t)(K + kInvWarps) * 32 * sizeof(double) + (size_t)K * sizeof(int);
+  if (ism > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_rbar_inv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ism);
+    if (e != cudaSuccess) return e;
+  }
+  k_rbar_inv<T><<<dim3((K + 31) / 32, nI), 32 * kInvWarps, ism, s>>>(K, gws, piv, Rinv);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_reduced<float>(const float*, const float*, int, int, double*, double*, int*, int*, void*,
+                                           cudaStream_t);
+template cudaError_t launch_reduced<double>(const double*, const double*, int, int, double*, double*, int*, int*,
+                                            void*, cudaStream_t);
+
 template cudaError_t launch_spikes<float>(const double*, int64_t, int, int, Dev, const float*, const float*, bool,
                                           float*, float*, double*, double*, int*, int*, void*, cudaStream_t,
                                           cudaEvent_t);

@@ -11,6 +11,7 @@
 #include <vector>
 #include "sap_internal.cuh"
 #include "sap_sparse.h"
+#include "sap_blocks.h"
 #include "krylov.cuh"
 
 using namespace sap;
@@ -76,6 +77,10 @@ struct SolverBase {
   virtual sap_status_t take_factor_error() = 0;
   virtual bool tc_used() const = 0;
   virtual int* err_flag() = 0;
+  // a transposed preconditioner can be built (not for per-block reorderings)
+  virtual bool has_transposed() const { return true; }
+  // the blocks' own half-bandwidths (handles of sap_factor_blocks), else null
+  virtual const std::vector<int>* block_bandwidths() const { return nullptr; }
 };
 
 }  // namespace
@@ -183,6 +188,31 @@ struct sap_handle {
 };
 
 namespace {
+
+// B_i (which 0) or C_{i+1} (which 1) of interface i read from the band, or
+// (adjoint) their roles for A^T: B'_i = C_{i+1}^T, C'_{i+1} = B_i^T.
+sap_status_t read_coupling(sap_handle* h, int i, int which, bool adjoint, double* host, cudaStream_t s) {
+  const int K = h->L.K;
+  const int64_t KK = (int64_t)K * K;
+  std::vector<double> tmp((size_t)KK, 0.0);
+  const int64_t N = h->L.N, sr = h->L.off[i + 1];
+  for (int r = 0; r < K; ++r)
+    for (int c = 0; c < K; ++c) {
+      // forward: B(r,c) = a(s-K+r, s+c); C(r,c) = a(s+r, s-K+c)
+      int64_t gi, gj;
+      bool isB = (which == 0) != adjoint;
+      int rr = adjoint ? c : r, cc = adjoint ? r : c;
+      if (isB) { gi = sr - K + rr; gj = sr + cc; } else { gi = sr + rr; gj = sr - K + cc; }
+      int64_t cidx = K + gi - gj;
+      double v = 0.0;
+      if (cidx >= 0 && cidx <= 2 * K)
+        CK(cudaMemcpyAsync(&v, h->band + cidx * N + gj, sizeof(double), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      tmp[(size_t)(r * K + c)] = v;
+    }
+  std::memcpy(host, tmp.data(), (size_t)KK * sizeof(double));
+  return SAP_OK;
+}
 
 template <typename T>
 struct Solver : SolverBase {
@@ -535,29 +565,7 @@ struct Solver : SolverBase {
     if (h->opt.variant != SAP_C || h->L.P < 2 || i < 0 || i >= h->L.P - 1 || which < 0 || which > 4)
       return SAP_ERR_INVALID_ARG;
     if (adjoint) TRY(build_adjoint(s));
-    if (which <= 1) {
-      // B_i / C_{i+1} from the band (or their transposed roles for A^T)
-      std::vector<double> tmp((size_t)KK, 0.0);
-      const int64_t N = h->L.N, sr = h->L.off[i + 1];
-      std::vector<double> col((size_t)(2 * K + 1));
-      for (int r = 0; r < K; ++r)
-        for (int c = 0; c < K; ++c) {
-          // forward: B(r,c) = a(s-K+r, s+c); C(r,c) = a(s+r, s-K+c)
-          // adjoint: B'(r,c) = C(c,r); C'(r,c) = B(c,r)
-          int64_t gi, gj;
-          bool isB = (which == 0) != adjoint;
-          int rr = adjoint ? c : r, cc = adjoint ? r : c;
-          if (isB) { gi = sr - K + rr; gj = sr + cc; } else { gi = sr + rr; gj = sr - K + cc; }
-          int64_t cidx = K + gi - gj;
-          double v = 0.0;
-          if (cidx >= 0 && cidx <= 2 * K)
-            CK(cudaMemcpyAsync(&v, h->band + cidx * N + gj, sizeof(double), cudaMemcpyDeviceToHost, s));
-          CK(cudaStreamSynchronize(s));
-          tmp[(size_t)(r * K + c)] = v;
-        }
-      std::memcpy(host, tmp.data(), (size_t)KK * sizeof(double));
-      return SAP_OK;
-    }
+    if (which <= 1) return read_coupling(h, i, which, adjoint, host, s);
     if (which == 4) {
       const double* src = (adjoint ? f.Ra0 : f.R0) + i * KK;
       CK(cudaMemcpyAsync(host, src, (size_t)KK * sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -664,6 +672,7 @@ struct KrylovRun {
   sap_status_t init(sap_handle* hh, const double* bu, double* xu, bool transposed, cudaStream_t us, int ws = 0) {
     h = hh; tr = transposed; user = us; b_user = bu; x_user = xu;
     if (tr && h->csr.rowptr) return SAP_ERR_NOT_IMPLEMENTED;    // no transposed sparse operator
+    if (tr && !h->impl->has_transposed()) return SAP_ERR_NOT_IMPLEMENTED;
     cg = h->opt.krylov == SAP_KRYLOV_CG;
     TRY(ensure_stream(h));
     N = h->L.N;
@@ -1003,16 +1012,21 @@ sap_status_t run_factor(sap_handle* h, cudaStream_t s) {
   return finish_factor(h);
 }
 
-// A handle with its layout and device memory, not yet factored.
+// The solver of a handle whose blocks are reordered on their own (defined below).
+SolverBase* new_blocks_solver(sap_handle* h, const int32_t* perm_dev, cudaStream_t s);
+
+// A handle with its layout and device memory, not yet factored.  With
+// blockperm (sap_factor_blocks) its solver factors every block after its own
+// permutation, at its own half-bandwidth (K may then exceed sap_max_K).
 sap_status_t create_handle(const double* band_dev, int64_t N, int32_t K, const sap_options_t* opt_in,
-                           cudaStream_t s, std::unique_ptr<sap_handle>& out) {
+                           cudaStream_t s, std::unique_ptr<sap_handle>& out, const int32_t* blockperm = nullptr) {
   if (!band_dev) return SAP_ERR_INVALID_ARG;
   TRY(check_options(opt_in, N, K));
   sap_options_t opt = *opt_in;
   if (opt.max_iters <= 0) opt.max_iters = 500;
   if (!(opt.tol > 0.0)) opt.tol = 1e-10;
   if (!(opt.boost_eps > 0.0)) opt.boost_eps = opt.precision == SAP_FP64 ? 0x1p-53 : 0x1p-24;
-  if (K > sap_max_K(opt.precision)) return SAP_ERR_NOT_IMPLEMENTED;
+  if (!blockperm && K > sap_max_K(opt.precision)) return SAP_ERR_NOT_IMPLEMENTED;
   out.reset(new (std::nothrow) sap_handle());
   if (!out) return SAP_ERR_OOM;
   sap_handle* h = out.get();
@@ -1103,8 +1117,10 @@ sap_status_t create_handle(const double* band_dev, int64_t N, int32_t K, const s
   CK(cudaEventCreate(&h->ev_rd));
   CK(cudaEventCreate(&h->ev_lu[0]));
   CK(cudaEventCreate(&h->ev_lu[1]));
-  if (opt.precision == SAP_FP64) h->impl.reset(new Solver<double>(h));
+  if (blockperm) h->impl.reset(new_blocks_solver(h, blockperm, s));
+  else if (opt.precision == SAP_FP64) h->impl.reset(new Solver<double>(h));
   else h->impl.reset(new Solver<float>(h));
+  if (!h->impl) return SAP_ERR_OOM;
   TRY(h->impl->alloc());
   return SAP_OK;
 }
@@ -1294,6 +1310,310 @@ sap_status_t solve_pair_batch(sap_batch* B, const double* const* b, double* cons
   return st;
 }
 
+// ---- SaP with a bandwidth of its own per block (third-stage reordering) ----
+// Every block b of the partition is reordered by its permutation into
+// Ahat_b (half-bandwidth K_b), held as a one-block SaP-D handle of its own
+// (factors, chunk and transfer matrices of the sweeps at K_b).  Factor: the
+// reordered bands gathered from the band, each block's threshold pass on its
+// own stream, ONE persistent LU launch over all blocks (LPT work list, boost
+// threshold from the whole band), each block's sweep matrices on its stream;
+// SaP-C then the entire spikes, their tips and the reduced matrices.  Apply:
+// Pi r, the blocks' sweeps on their streams (fork and join by events, so the
+// Krylov iteration's capture takes them in), then Pi^T g (SaP-D) or the
+// reduced solve and the spike correction (SaP-C).
+template <typename T>
+struct Blocks : SolverBase {
+  sap_handle* h;
+  const int32_t* perm_src;
+  cudaStream_t cs;                     // creation stream
+  std::vector<std::unique_ptr<sap_handle>> sub;
+  std::vector<int> Kb;
+  std::vector<int64_t> hbase;
+  BlockMap m{};
+  int32_t *perm = nullptr, *pinv = nullptr, *dKb = nullptr;
+  int64_t* dhbase = nullptr;
+  double* hb = nullptr;
+  int64_t hb_elems = 0;
+  LuItem* items = nullptr;
+  unsigned* counter = nullptr;
+  T* wlu = nullptr;
+  int nitems = 0, Kbmax = 1;
+  bool tcu = false;
+  const void** dFp = nullptr;
+  int64_t* dldp = nullptr;
+  T* spk = nullptr;
+  int64_t* dsbase = nullptr;
+  Factors<T> f;                        // V, Wt, R, R0, piv of the interfaces; err
+  unsigned char* gws = nullptr;
+  double *rh = nullptr, *gh = nullptr, *xt = nullptr, *xb = nullptr;
+  int* gerr = nullptr;                 // an entry beyond its block's K_b at the gather
+  cudaEvent_t evfork = nullptr;
+  Blocks(sap_handle* hh, const int32_t* p, cudaStream_t s) : h(hh), perm_src(p), cs(s) {}
+  ~Blocks() override {
+    if (evfork) cudaEventDestroy(evfork);
+  }
+  bool coupled() const { return h->opt.variant == SAP_C && h->L.P > 1; }
+
+  sap_status_t alloc() override {
+    const Layout& L = h->L;
+    const int P = L.P, K = L.K;
+    const int64_t N = L.N;
+    if (!perm_src || P < 1) return SAP_ERR_INVALID_ARG;
+    CK(cudaStreamSynchronize(cs));
+    // the permutations: checked per block, inverted on the host
+    std::vector<int32_t> hp((size_t)N), hpi((size_t)N);
+    CK(cudaMemcpy(hp.data(), perm_src, (size_t)N * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    for (int b = 0; b < P; ++b) {
+      const int64_t s0 = L.off[b], n = L.off[b + 1] - s0;
+      std::vector<char> seen((size_t)n, 0);
+      for (int64_t a = 0; a < n; ++a) {
+        const int32_t v = hp[(size_t)(s0 + a)];
+        if (v < 0 || v >= n || seen[(size_t)v]) return SAP_ERR_INVALID_ARG;
+        seen[(size_t)v] = 1;
+        hpi[(size_t)(s0 + v)] = (int32_t)a;
+      }
+    }
+    TRY(h->mem.alloc(&perm, (size_t)N));
+    TRY(h->mem.alloc(&pinv, (size_t)N));
+    TRY(h->mem.alloc(&dKb, (size_t)P));
+    TRY(h->mem.alloc(&dhbase, (size_t)P));
+    TRY(h->mem.alloc(&gerr, 1));
+    CK(cudaMemcpy(perm, hp.data(), (size_t)N * sizeof(int32_t), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(pinv, hpi.data(), (size_t)N * sizeof(int32_t), cudaMemcpyHostToDevice));
+    m.N = N;
+    m.K = K;
+    m.P = P;
+    m.q = N / P;
+    m.pr = N - (int64_t)P * m.q;
+    m.off = h->d.off;
+    m.perm = perm;
+    m.pinv = pinv;
+    m.Kb = dKb;
+    m.hbase = dhbase;
+    // the blocks' half-bandwidths
+    CK(launch_block_bw(h->band, m, dKb, cs));
+    Kb.assign((size_t)P, 0);
+    CK(cudaMemcpyAsync(Kb.data(), dKb, (size_t)P * sizeof(int), cudaMemcpyDeviceToHost, cs));
+    CK(cudaStreamSynchronize(cs));
+    hbase.assign((size_t)P, 0);
+    int64_t acc = 0;
+    for (int b = 0; b < P; ++b) {
+      const int64_t n = L.off[b + 1] - L.off[b];
+      Kb[(size_t)b] = std::max(1, Kb[(size_t)b]);
+      if (Kb[(size_t)b] >= n) return SAP_ERR_INVALID_ARG;
+      if (Kb[(size_t)b] > sap_max_K(h->opt.precision)) return SAP_ERR_NOT_IMPLEMENTED;
+      Kbmax = std::max(Kbmax, Kb[(size_t)b]);
+      hbase[(size_t)b] = acc;
+      acc += n * (2 * (int64_t)Kb[(size_t)b] + 1);
+    }
+    hb_elems = acc;
+    CK(cudaMemcpy(dKb, Kb.data(), (size_t)P * sizeof(int), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(dhbase, hbase.data(), (size_t)P * sizeof(int64_t), cudaMemcpyHostToDevice));
+    TRY(h->mem.alloc(&hb, (size_t)hb_elems));
+    CK(cudaMemset(hb, 0, (size_t)hb_elems * sizeof(double)));
+    // the blocks as one-block SaP-D handles on their reordered bands
+    sub.resize((size_t)P);
+    std::vector<LuItem> it;
+    for (int b = 0; b < P; ++b) {
+      sap_options_t ob = h->opt;
+      ob.P = 1;
+      ob.variant = SAP_D;
+      TRY(create_handle(hb + hbase[(size_t)b], L.off[b + 1] - L.off[b], Kb[(size_t)b], &ob, cs, sub[(size_t)b]));
+      TRY(ensure_stream(sub[(size_t)b].get()));
+      sub[(size_t)b]->impl->lu_items(it);
+    }
+    for (LuItem& x : it) {            // one boost threshold (the whole band's) and one counter
+      x.absmax = h->absmax;
+      x.nb = h->n_boosted;
+    }
+    std::stable_sort(it.begin(), it.end(), [](const LuItem& a, const LuItem& c) {
+      return (double)a.n * a.K * a.K > (double)c.n * c.K * c.K;
+    });
+    nitems = (int)it.size();
+    TRY(h->mem.alloc(&items, it.size()));
+    TRY(h->mem.alloc(&counter, 1));
+    CK(cudaMemcpy(items, it.data(), it.size() * sizeof(LuItem), cudaMemcpyHostToDevice));
+    const bool fp64 = sizeof(T) == 8;
+    tcu = !fp64 && h->opt.precision == SAP_FP32_BF16TU && Kbmax >= kTcMinK && !lu_window_global(Kbmax, false, true);
+    if (lu_window_global(Kbmax, fp64, tcu))
+      TRY(h->mem.alloc(&wlu, (size_t)lu_items_grid(nitems, Kbmax, fp64, tcu) * lu_window_elems(Kbmax)));
+    TRY(h->mem.alloc(&f.err, 2));
+    {
+      const int e2[2] = {0, spin_limit_value(h->opt.spin_limit)};
+      CK(cudaMemcpy(f.err, e2, sizeof(e2), cudaMemcpyHostToDevice));
+    }
+    TRY(h->mem.alloc(&rh, (size_t)N));
+    TRY(h->mem.alloc(&gh, (size_t)N));
+    CK(cudaEventCreateWithFlags(&evfork, cudaEventDisableTiming));
+    if (!h->evu[0]) {
+      CK(cudaEventCreate(&h->evu[0]));
+      CK(cudaEventCreate(&h->evu[1]));
+    }
+    if (coupled()) {
+      if (full_spikes_smem(Kbmax, fp64) > kSmemPerBlock) return SAP_ERR_NOT_IMPLEMENTED;
+      const int nI = P - 1;
+      const int64_t KK = (int64_t)K * K;
+      std::vector<const void*> fp((size_t)P);
+      std::vector<int64_t> ldv((size_t)P), sb((size_t)(2 * nI));
+      for (int b = 0; b < P; ++b) {
+        auto* sv = dynamic_cast<Solver<T>*>(sub[(size_t)b]->impl.get());
+        if (!sv) return SAP_ERR_CUDA;
+        fp[(size_t)b] = sv->f.F;
+        ldv[(size_t)b] = sub[(size_t)b]->L.ld[0];
+      }
+      int64_t so = 0;
+      for (int i = 0; i < nI; ++i) {
+        sb[(size_t)(2 * i)] = so;
+        so += (L.off[i + 1] - L.off[i]) * K;
+        sb[(size_t)(2 * i + 1)] = so;
+        so += (L.off[i + 2] - L.off[i + 1]) * K;
+      }
+      TRY(h->mem.alloc(&dFp, (size_t)P));
+      TRY(h->mem.alloc(&dldp, (size_t)P));
+      TRY(h->mem.alloc(&dsbase, sb.size()));
+      TRY(h->mem.alloc(&spk, (size_t)so));
+      CK(cudaMemcpy(dFp, fp.data(), fp.size() * sizeof(void*), cudaMemcpyHostToDevice));
+      CK(cudaMemcpy(dldp, ldv.data(), ldv.size() * sizeof(int64_t), cudaMemcpyHostToDevice));
+      CK(cudaMemcpy(dsbase, sb.data(), sb.size() * sizeof(int64_t), cudaMemcpyHostToDevice));
+      TRY(h->mem.alloc(&f.V, (size_t)(nI * KK)));
+      TRY(h->mem.alloc(&f.Wt, (size_t)(nI * KK)));
+      TRY(h->mem.alloc(&f.R, (size_t)(nI * KK)));
+      TRY(h->mem.alloc(&f.R0, (size_t)(nI * KK)));
+      TRY(h->mem.alloc(&f.piv, (size_t)(nI * K)));
+      TRY(h->mem.alloc(&gws, reduced_ws_bytes(K, nI, fp64)));
+      TRY(h->mem.alloc(&xt, (size_t)(nI * K)));
+      TRY(h->mem.alloc(&xb, (size_t)(nI * K)));
+    }
+    return SAP_OK;
+  }
+
+  sap_status_t factor(cudaStream_t s) override {
+    const Layout& L = h->L;
+    CK(cudaEventRecord(h->evp[0], s));
+    CK(launch_absmax(h->band, L.N, L.K, h->absmax, s));
+    CK(cudaMemsetAsync(gerr, 0, sizeof(int), s));
+    CK(launch_block_gather(h->band, m, hb, hb_elems, gerr, s));
+    CK(cudaEventRecord(evfork, s));
+    for (auto& q : sub) {
+      CK(cudaStreamWaitEvent(q->ks, evfork, 0));
+      TRY(q->impl->factor_pre(q->ks));
+      CK(cudaEventRecord(q->evj, q->ks));
+      CK(cudaStreamWaitEvent(s, q->evj, 0));
+    }
+    CK(cudaEventRecord(h->ev_lu[0], s));
+    CK(launch_factor_lu_items<T>(items, nitems, Kbmax, counter, wlu, tcu, f.err, s));
+    CK(cudaEventRecord(h->ev_lu[1], s));
+    CK(cudaEventRecord(evfork, s));
+    for (auto& q : sub) {
+      CK(cudaStreamWaitEvent(q->ks, evfork, 0));
+      TRY(q->impl->factor_post(q->ks));
+      CK(cudaEventRecord(q->evj, q->ks));
+      CK(cudaStreamWaitEvent(s, q->evj, 0));
+    }
+    CK(cudaEventRecord(h->evp[1], s));
+    CK(cudaEventRecord(h->evu[0], s));    // no UL factorisation: an empty T_UL bracket
+    CK(cudaEventRecord(h->evu[1], s));
+    CK(cudaEventRecord(h->evp[2], s));
+    if (coupled()) {
+      CK(launch_full_spikes<T>(h->band, m, Kbmax, dFp, dldp, spk, dsbase, f.V, f.Wt, s));
+      CK(cudaEventRecord(h->ev_rd, s));
+      CK(launch_reduced<T>(f.V, f.Wt, L.K, L.P - 1, f.R, f.R0, f.piv, h->singular, gws, s));
+    } else {
+      CK(cudaEventRecord(h->ev_rd, s));
+    }
+    CK(cudaEventRecord(h->evp[3], s));
+    return SAP_OK;
+  }
+  sap_status_t factor_pre(cudaStream_t) override { return SAP_ERR_NOT_IMPLEMENTED; }
+  sap_status_t factor_post(cudaStream_t) override { return SAP_ERR_NOT_IMPLEMENTED; }
+  void lu_items(std::vector<LuItem>&) const override {}
+  sap_status_t build_adjoint(cudaStream_t) override { return SAP_ERR_NOT_IMPLEMENTED; }
+  sap_status_t build_adjoint_async(cudaStream_t) override { return SAP_ERR_NOT_IMPLEMENTED; }
+  sap_status_t adjoint_singular() override { return SAP_OK; }
+  sap_status_t prepare_transposed(cudaStream_t) override { return SAP_ERR_NOT_IMPLEMENTED; }
+  bool has_transposed() const override { return false; }
+  const std::vector<int>* block_bandwidths() const override { return &Kb; }
+
+  sap_status_t apply(const double* r, double* z, bool transpose, cudaStream_t s, Gate gt) override {
+    if (transpose) return SAP_ERR_NOT_IMPLEMENTED;
+    const Layout& L = h->L;
+    CK(launch_block_perm(m, r, rh, true, s, gt));
+    CK(cudaEventRecord(evfork, s));
+    for (int b = 0; b < L.P; ++b) {
+      sap_handle* q = sub[(size_t)b].get();
+      CK(cudaStreamWaitEvent(q->ks, evfork, 0));
+      TRY(q->impl->apply(rh + L.off[b], gh + L.off[b], false, q->ks, gt));
+      CK(cudaEventRecord(q->evj, q->ks));
+      CK(cudaStreamWaitEvent(s, q->evj, 0));
+    }
+    if (!coupled()) {
+      CK(launch_block_perm(m, gh, z, false, s, gt));
+      return SAP_OK;
+    }
+    CK(launch_block_reduced<T>(m, gh, f.V, f.Wt, f.R, xt, xb, s, gt));
+    CK(launch_block_correct<T>(m, gh, spk, dsbase, xt, xb, z, s, gt));
+    return SAP_OK;
+  }
+
+  sap_status_t take_device_error(cudaStream_t s) override {
+    sap_status_t st = SAP_OK;
+    for (auto& q : sub) {
+      const sap_status_t e = q->impl->take_device_error(s);
+      if (st == SAP_OK) st = e;
+    }
+    int e = 0;
+    CK(cudaMemcpyAsync(&e, f.err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (e) {
+      CK(cudaMemsetAsync(f.err, 0, sizeof(int), s));
+      st = SAP_ERR_TIMEOUT;
+    }
+    return st;
+  }
+  sap_status_t take_factor_error() override {
+    int g = 0, e = 0;
+    CK(cudaMemcpy(&g, gerr, sizeof(int), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(&e, f.err, sizeof(int), cudaMemcpyDeviceToHost));
+    sap_status_t st = SAP_OK;
+    for (auto& q : sub) {
+      const sap_status_t x = q->impl->take_factor_error();
+      if (st == SAP_OK) st = x;
+    }
+    if (e) {
+      CK(cudaMemset(f.err, 0, sizeof(int)));
+      st = SAP_ERR_TIMEOUT;
+    }
+    if (g) return SAP_ERR_INVALID_ARG;
+    return st;
+  }
+  bool tc_used() const override { return tcu; }
+  int* err_flag() override { return f.err; }
+  sap_status_t block_lu(int, double*, cudaStream_t) override { return SAP_ERR_NOT_IMPLEMENTED; }
+  sap_status_t interface(int i, int which, bool adjoint, double* host, cudaStream_t s) override {
+    const int K = h->L.K;
+    const int64_t KK = (int64_t)K * K;
+    if (!coupled() || i < 0 || i >= h->L.P - 1 || which < 0 || which > 4) return SAP_ERR_INVALID_ARG;
+    if (adjoint) return SAP_ERR_NOT_IMPLEMENTED;
+    if (which <= 1) return read_coupling(h, i, which, false, host, s);
+    if (which == 4) {
+      CK(cudaMemcpyAsync(host, f.R0 + i * KK, (size_t)KK * sizeof(double), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      return SAP_OK;
+    }
+    std::vector<T> buf((size_t)KK);
+    CK(cudaMemcpyAsync(buf.data(), (which == 2 ? f.V : f.Wt) + i * KK, (size_t)KK * sizeof(T),
+                       cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    for (int64_t e = 0; e < KK; ++e) host[e] = (double)buf[(size_t)e];
+    return SAP_OK;
+  }
+};
+
+SolverBase* new_blocks_solver(sap_handle* h, const int32_t* perm_dev, cudaStream_t s) {
+  if (h->opt.precision == SAP_FP64) return new (std::nothrow) Blocks<double>(h, perm_dev, s);
+  return new (std::nothrow) Blocks<float>(h, perm_dev, s);
+}
+
 }  // namespace
 
 extern "C" {
@@ -1344,6 +1664,26 @@ sap_status_t sap_factor(const double* band_dev, int64_t N, int32_t K, const sap_
   TRY(create_handle(band_dev, N, K, &opt, s, h));
   TRY(run_factor(h.get(), s));
   *out = h.release();
+  return SAP_OK;
+}
+
+sap_status_t sap_factor_blocks(const double* band_dev, int64_t N, int32_t K, const int32_t* perm_dev,
+                               const sap_options_t* opt, cudaStream_t s, sap_handle_t* out) {
+  if (!out) return SAP_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!opt || !perm_dev || opt->P < 1) return SAP_ERR_INVALID_ARG;
+  std::unique_ptr<sap_handle> h;
+  TRY(create_handle(band_dev, N, K, opt, s, h, perm_dev));
+  TRY(run_factor(h.get(), s));
+  *out = h.release();
+  return SAP_OK;
+}
+
+sap_status_t sap_get_block_bandwidths(sap_handle_t h, int32_t* Ki) {
+  if (!h || !Ki) return SAP_ERR_INVALID_ARG;
+  const std::vector<int>* k = h->impl->block_bandwidths();
+  if (!k) return SAP_ERR_INVALID_ARG;
+  for (size_t b = 0; b < k->size(); ++b) Ki[b] = (*k)[b];
   return SAP_OK;
 }
 

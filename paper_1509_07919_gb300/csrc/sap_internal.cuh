@@ -200,6 +200,55 @@ cudaError_t launch_apply(const double* band, int64_t N, int K, int P, Dev d, con
                          int variant, bool transpose, const double* r, double* z, double* scratch,
                          cudaStream_t s, Gate gt = Gate());
 
+// Rbar_i = I - W^(t)_{i+1} V^(b)_i from given tips (nI interfaces), its GEPP
+// and inverse (the wide-band kernels of launch_spikes) in a workspace of
+// reduced_ws_bytes(K, nI, fp64) bytes.
+size_t reduced_ws_bytes(int K, int nI, bool fp64);
+template <typename T>
+cudaError_t launch_reduced(const T* V, const T* Wt, int K, int nI, double* Rinv, double* R0, int* piv, int* singular,
+                           void* gws, cudaStream_t s);
+
+// ---- SaP with a bandwidth of its own per block (third-stage reordering) ----
+// Partition and block permutations on the device.  perm[g] is the new local
+// index of global row/column g inside its block (Ahat_b = Pi_b A_b Pi_b^T),
+// pinv[off_b + r] the old local index of new local row r.
+struct BlockMap {
+  int64_t N = 0;
+  int K = 0, P = 0;
+  int64_t q = 0, pr = 0;            // blocks 0..pr-1 have q + 1 rows, the others q
+  const int64_t* off = nullptr;     // P + 1
+  const int32_t* perm = nullptr;    // N
+  const int32_t* pinv = nullptr;    // N
+  const int32_t* Kb = nullptr;      // P: half-bandwidth of each reordered block
+  const int64_t* hbase = nullptr;   // P: offset of block b's band in the reordered-band buffer
+};
+// Kout[b] = max |perm(i) - perm(j)| over the nonzero entries of block b (P ints).
+cudaError_t launch_block_bw(const double* band, const BlockMap& m, int* Kout, cudaStream_t s);
+// The reordered blocks (band storage, half-bandwidth Kb[b], n_b columns) into
+// the zeroed buffer hb (hb_elems doubles); *err set on an entry beyond Kb[b].
+cudaError_t launch_block_gather(const double* band, const BlockMap& m, double* hb, int64_t hb_elems, int* err,
+                                cudaStream_t s);
+// to_new: y = Pi x (y[off_b + perm(g)] = x[g]); else y = Pi^T x.
+cudaError_t launch_block_perm(const BlockMap& m, const double* x, double* y, bool to_new, cudaStream_t s,
+                              Gate gt = Gate());
+// Dynamic shared memory of the entire-spike kernel for blocks up to Kbmax.
+size_t full_spikes_smem(int Kbmax, bool fp64);
+// Entire spikes of every interface i into spk (row-major n x K at
+// sbase[2 i] for Vhat_i, sbase[2 i + 1] for What_{i+1}) from block b's
+// factors Fp[b] (diagonal-major, leading dimension ldp[b], half-bandwidth
+// Kb[b]), and their tips V^(b)_i, W^(t)_{i+1} (K x K row-major per interface).
+template <typename T>
+cudaError_t launch_full_spikes(const double* band, const BlockMap& m, int Kbmax, const void* const* Fp,
+                               const int64_t* ldp, T* spk, const int64_t* sbase, T* Vtip, T* Wtip, cudaStream_t s);
+// x^(t), x^(b) of every interface from g = D^{-1} r (new numbering), Eq. (2.5b,c).
+template <typename T>
+cudaError_t launch_block_reduced(const BlockMap& m, const double* gh, const T* V, const T* Wt, const double* Rinv,
+                                 double* xt, double* xb, cudaStream_t s, Gate gt = Gate());
+// z = Pi^T (g - Vhat x^(t) - What x^(b)) block by block.
+template <typename T>
+cudaError_t launch_block_correct(const BlockMap& m, const double* gh, const T* spk, const int64_t* sbase,
+                                 const double* xt, const double* xb, double* z, cudaStream_t s, Gate gt = Gate());
+
 // Krylov vector kernels (FP64)
 struct Krylov;  // defined in sap_api.cu
 

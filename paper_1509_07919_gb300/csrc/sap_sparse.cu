@@ -15,6 +15,7 @@
 #include <queue>
 #include <vector>
 #include "sap_sparse.h"
+#include "sap_blocks.h"
 #include "sap_internal.cuh"
 
 namespace {
@@ -477,6 +478,56 @@ extern "C" sap_status_t sap_cm_reorder(int64_t n, int64_t nnz, const int64_t* ro
     }
     *K_out = (int32_t)K;
   }
+  CKS(cudaStreamSynchronize(stream));
+  return SAP_OK;
+}
+
+// The third-stage reordering (include/sap_blocks.h): CM of every block's
+// A_i + A_i^T on its own, from a host copy of the band.
+extern "C" sap_status_t sap_block_cm_reorder(const double* band_dev, int64_t N, int32_t K, int32_t P,
+                                             int32_t* perm_dev, int32_t* Ki_host, cudaStream_t stream) {
+  if (!band_dev || !perm_dev || N < 1 || K < 1 || P < 1 || N < P || N >= (int64_t(1) << 31)) return SAP_ERR_INVALID_ARG;
+  const int64_t W = 2 * (int64_t)K + 1;
+  std::vector<double> band;
+  std::vector<int32_t> perm_all;
+  try {
+    band.resize((size_t)(W * N));
+    perm_all.resize((size_t)N);
+  } catch (...) {
+    return SAP_ERR_OOM;
+  }
+  CKS(cudaMemcpyAsync(band.data(), band_dev, (size_t)(W * N) * sizeof(double), cudaMemcpyDeviceToHost, stream));
+  CKS(cudaStreamSynchronize(stream));
+  // the partition of sap_factor: the first N mod P blocks have one row more
+  const int64_t q = N / P, pr = N - (int64_t)P * q;
+  int64_t s = 0;
+  std::vector<int64_t> nb_ptr;
+  std::vector<int32_t> nb, p;
+  for (int b = 0; b < P; ++b) {
+    const int64_t n = q + (b < pr ? 1 : 0);
+    nb_ptr.assign((size_t)(n + 1), 0);
+    nb.clear();
+    for (int64_t a = 0; a < n; ++a) {
+      const int64_t g = s + a;
+      for (int64_t dq = -K; dq <= K; ++dq) {     // neighbours in ascending order
+        const int64_t c = a + dq;
+        if (dq == 0 || c < 0 || c >= n) continue;
+        // entry (g, s+c) at band[(K - dq) N + s + c], entry (s+c, g) at band[(K + dq) N + g]
+        if (band[(size_t)((K - dq) * N + s + c)] != 0.0 || band[(size_t)((K + dq) * N + g)] != 0.0)
+          nb.push_back((int32_t)c);
+      }
+      nb_ptr[(size_t)(a + 1)] = (int64_t)nb.size();
+    }
+    cm_order(n, nb_ptr, nb, p);
+    int64_t Kb = 0;
+    for (int64_t a = 0; a < n; ++a)
+      for (int64_t e = nb_ptr[(size_t)a]; e < nb_ptr[(size_t)(a + 1)]; ++e)
+        Kb = std::max<int64_t>(Kb, std::llabs((int64_t)p[(size_t)a] - p[(size_t)nb[(size_t)e]]));
+    if (Ki_host) Ki_host[b] = (int32_t)Kb;
+    std::copy(p.begin(), p.end(), perm_all.begin() + s);
+    s += n;
+  }
+  CKS(cudaMemcpyAsync(perm_dev, perm_all.data(), (size_t)N * sizeof(int32_t), cudaMemcpyHostToDevice, stream));
   CKS(cudaStreamSynchronize(stream));
   return SAP_OK;
 }

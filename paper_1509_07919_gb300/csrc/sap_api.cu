@@ -1339,7 +1339,10 @@ struct Blocks : SolverBase {
   T* wlu = nullptr;
   int nitems = 0, Kbmax = 1;
   bool tcu = false;
-  const void** dFp = nullptr;
+  const void** dMf = nullptr;          // per block: chunk matrices of its forward (L) and backward (U) sweeps
+  const void** dMb = nullptr;
+  int* dng = nullptr;                  // per block: couplings per chunk
+  int ngmax = 1;
   int64_t* dldp = nullptr;
   T* spk = nullptr;
   int64_t* dsbase = nullptr;
@@ -1358,7 +1361,7 @@ struct Blocks : SolverBase {
     const Layout& L = h->L;
     const int P = L.P, K = L.K;
     const int64_t N = L.N;
-    if (!perm_src || P < 1) return SAP_ERR_INVALID_ARG;
+    if (!perm_src || P < 1 || N >= (int64_t(1) << 31)) return SAP_ERR_INVALID_ARG;
     CK(cudaStreamSynchronize(cs));
     // the permutations: checked per block, inverted on the host
     std::vector<int32_t> hp((size_t)N), hpi((size_t)N);
@@ -1450,29 +1453,39 @@ struct Blocks : SolverBase {
       CK(cudaEventCreate(&h->evu[1]));
     }
     if (coupled()) {
-      if (full_spikes_smem(Kbmax, fp64) > kSmemPerBlock) return SAP_ERR_NOT_IMPLEMENTED;
       const int nI = P - 1;
       const int64_t KK = (int64_t)K * K;
-      std::vector<const void*> fp((size_t)P);
+      std::vector<const void*> mf((size_t)P), mb((size_t)P);
+      std::vector<int> ngv((size_t)P);
       std::vector<int64_t> ldv((size_t)P), sb((size_t)(2 * nI));
       for (int b = 0; b < P; ++b) {
         auto* sv = dynamic_cast<Solver<T>*>(sub[(size_t)b]->impl.get());
         if (!sv) return SAP_ERR_CUDA;
-        fp[(size_t)b] = sv->f.F;
+        mf[(size_t)b] = sv->f.Mlf;
+        mb[(size_t)b] = sv->f.Mub;
+        ngv[(size_t)b] = chunk_couplings(Kb[(size_t)b]);
+        ngmax = std::max(ngmax, ngv[(size_t)b]);
         ldv[(size_t)b] = sub[(size_t)b]->L.ld[0];
       }
+      if (full_spikes_smem(ngmax, fp64) > kSmemPerBlock) return SAP_ERR_NOT_IMPLEMENTED;
+      const int KS = spike_row_stride(K, fp64);
       int64_t so = 0;
       for (int i = 0; i < nI; ++i) {
         sb[(size_t)(2 * i)] = so;
-        so += (L.off[i + 1] - L.off[i]) * K;
+        so += (L.off[i + 1] - L.off[i]) * KS;
         sb[(size_t)(2 * i + 1)] = so;
-        so += (L.off[i + 2] - L.off[i + 1]) * K;
+        so += (L.off[i + 2] - L.off[i + 1]) * KS;
       }
-      TRY(h->mem.alloc(&dFp, (size_t)P));
+      TRY(h->mem.alloc(&dMf, (size_t)P));
+      TRY(h->mem.alloc(&dMb, (size_t)P));
+      TRY(h->mem.alloc(&dng, (size_t)P));
       TRY(h->mem.alloc(&dldp, (size_t)P));
       TRY(h->mem.alloc(&dsbase, sb.size()));
       TRY(h->mem.alloc(&spk, (size_t)so));
-      CK(cudaMemcpy(dFp, fp.data(), fp.size() * sizeof(void*), cudaMemcpyHostToDevice));
+      CK(cudaMemset(spk, 0, (size_t)so * sizeof(T)));     // the row padding is read (times 0) by the correction
+      CK(cudaMemcpy(dMf, mf.data(), mf.size() * sizeof(void*), cudaMemcpyHostToDevice));
+      CK(cudaMemcpy(dMb, mb.data(), mb.size() * sizeof(void*), cudaMemcpyHostToDevice));
+      CK(cudaMemcpy(dng, ngv.data(), ngv.size() * sizeof(int), cudaMemcpyHostToDevice));
       CK(cudaMemcpy(dldp, ldv.data(), ldv.size() * sizeof(int64_t), cudaMemcpyHostToDevice));
       CK(cudaMemcpy(dsbase, sb.data(), sb.size() * sizeof(int64_t), cudaMemcpyHostToDevice));
       TRY(h->mem.alloc(&f.V, (size_t)(nI * KK)));
@@ -1515,7 +1528,7 @@ struct Blocks : SolverBase {
     CK(cudaEventRecord(h->evu[1], s));
     CK(cudaEventRecord(h->evp[2], s));
     if (coupled()) {
-      CK(launch_full_spikes<T>(h->band, m, Kbmax, dFp, dldp, spk, dsbase, f.V, f.Wt, s));
+      CK(launch_full_spikes<T>(h->band, m, ngmax, dMf, dMb, dng, dldp, spk, dsbase, f.V, f.Wt, s));
       CK(cudaEventRecord(h->ev_rd, s));
       CK(launch_reduced<T>(f.V, f.Wt, L.K, L.P - 1, f.R, f.R0, f.piv, h->singular, gws, s));
     } else {
@@ -1551,7 +1564,7 @@ struct Blocks : SolverBase {
       return SAP_OK;
     }
     CK(launch_block_reduced<T>(m, gh, f.V, f.Wt, f.R, xt, xb, s, gt));
-    CK(launch_block_correct<T>(m, gh, spk, dsbase, xt, xb, z, s, gt));
+    CK(launch_block_correct<T>(m, (int)(L.off[1] - L.off[0]), gh, spk, dsbase, xt, xb, z, s, gt));
     return SAP_OK;
   }
 

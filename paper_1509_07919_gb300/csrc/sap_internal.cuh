@@ -231,23 +231,30 @@ cudaError_t launch_block_gather(const double* band, const BlockMap& m, double* h
 // to_new: y = Pi x (y[off_b + perm(g)] = x[g]); else y = Pi^T x.
 cudaError_t launch_block_perm(const BlockMap& m, const double* x, double* y, bool to_new, cudaStream_t s,
                               Gate gt = Gate());
-// Dynamic shared memory of the entire-spike kernel for blocks up to Kbmax.
-size_t full_spikes_smem(int Kbmax, bool fp64);
-// Entire spikes of every interface i into spk (row-major n x K at
-// sbase[2 i] for Vhat_i, sbase[2 i + 1] for What_{i+1}) from block b's
-// factors Fp[b] (diagonal-major, leading dimension ldp[b], half-bandwidth
-// Kb[b]), and their tips V^(b)_i, W^(t)_{i+1} (K x K row-major per interface).
+// Dynamic shared memory of the entire-spike kernel for blocks of up to ngmax
+// chunk couplings (chunk_couplings(K_b)).
+size_t full_spikes_smem(int ngmax, bool fp64);
+// Row stride of the stored entire spikes: K rounded up to 16 bytes (the
+// padding stays zero).
+int spike_row_stride(int K, bool fp64);
+// Entire spikes of every interface i into spk (row-major n x KS at
+// sbase[2 i] for Vhat_i, sbase[2 i + 1] for What_{i+1}) by the sweeps of
+// each block b with its chunk matrices (Mfp[b]: forward L, Mbp[b]: backward
+// U, ngp[b] couplings per chunk, leading dimension ldp[b]), and their tips
+// V^(b)_i, W^(t)_{i+1} (K x K row-major per interface).
 template <typename T>
-cudaError_t launch_full_spikes(const double* band, const BlockMap& m, int Kbmax, const void* const* Fp,
-                               const int64_t* ldp, T* spk, const int64_t* sbase, T* Vtip, T* Wtip, cudaStream_t s);
+cudaError_t launch_full_spikes(const double* band, const BlockMap& m, int ngmax, const void* const* Mfp,
+                               const void* const* Mbp, const int* ngp, const int64_t* ldp, T* spk,
+                               const int64_t* sbase, T* Vtip, T* Wtip, cudaStream_t s);
 // x^(t), x^(b) of every interface from g = D^{-1} r (new numbering), Eq. (2.5b,c).
 template <typename T>
 cudaError_t launch_block_reduced(const BlockMap& m, const double* gh, const T* V, const T* Wt, const double* Rinv,
                                  double* xt, double* xb, cudaStream_t s, Gate gt = Gate());
-// z = Pi^T (g - Vhat x^(t) - What x^(b)) block by block.
+// z = Pi^T (g - Vhat x^(t) - What x^(b)) block by block (max_rows: the largest block).
 template <typename T>
-cudaError_t launch_block_correct(const BlockMap& m, const double* gh, const T* spk, const int64_t* sbase,
-                                 const double* xt, const double* xb, double* z, cudaStream_t s, Gate gt = Gate());
+cudaError_t launch_block_correct(const BlockMap& m, int max_rows, const double* gh, const T* spk,
+                                 const int64_t* sbase, const double* xt, const double* xb, double* z, cudaStream_t s,
+                                 Gate gt = Gate());
 
 // Krylov vector kernels (FP64)
 struct Krylov;  // defined in sap_api.cu

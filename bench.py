@@ -67,6 +67,7 @@ def parse():
     ap.add_argument("--no-compare", action="store_true", help="skip the FP64 / other-variant comparison runs")
     ap.add_argument("--blocks", action="store_true",
                     help="SaP with per-block bandwidths (third-stage reordering) against SaP on the whole band")
+    ap.add_argument("--blocks-k", type=int, default=100, help="half-bandwidth K of the --blocks workload")
     ap.add_argument("--sparse", action="store_true",
                     help="time the sparse front end (Sec. 2.2) and the solve of the reordered band")
     ap.add_argument("--sweep", default=None, choices=["P", "d"],
@@ -936,7 +937,7 @@ def main():
     if args.sparse:
         run_sparse(args)
     elif args.blocks:
-        run_blocks(args)
+        run_blocks(args, K=args.blocks_k)
     elif args.sweep:
         run_sweep(args)
     elif args.impl == "reference":

@@ -50,17 +50,22 @@ SAP_API sap_status_t sap_block_cm_reorder(const double *band_dev, int64_t N, int
  * for sap_factor; opt->segments applies to every block's sweeps.  K_i =
  * max(1, bandwidth of Ahat_i); every K_i must be at most sap_max_K(precision)
  * and below N_i, while K itself may exceed sap_max_K.  SaP-C needs N_i >= 2 K.
- * The returned handle works with sap_solve, sap_solve_host,
- * sap_apply_preconditioner (transpose = 0), sap_refactor (same pattern: an
- * entry of the new values outside its block's K_i is INVALID_ARG),
- * sap_set_operator_csr, sap_num_partitions and sap_destroy.  Its transposed
- * preconditioner is not built: sap_solve_adjoint, sap_solve_pair and
- * sap_apply_preconditioner with transpose = 1 return NOT_IMPLEMENTED, and so
- * do sap_get_block_lu and sap_autotune.  sap_get_interface gives V, W and
- * Rbar (which = 2, 3, 4) as for sap_factor, and B, C (0, 1).
+ * The returned handle works with sap_solve, sap_solve_host, sap_solve_adjoint,
+ * sap_solve_pair, sap_grad_band, sap_apply_preconditioner (either direction),
+ * sap_refactor (same pattern: an entry of the new values outside its block's
+ * K_i is INVALID_ARG), sap_set_operator_csr (forward solves only, as for
+ * sap_factor handles), sap_num_partitions and sap_destroy.  The
+ * preconditioner of A^T (same partition and permutations: the blocks of A^T
+ * renumbered are Ahat_i^T, factored by the stored factors transposed;
+ * couplings B'_i = C_{i+1}^T, C'_{i+1} = B_i^T; its own entire spikes, tips
+ * and reduced matrices) is built on the first transposed use after each
+ * factorisation.  sap_get_block_lu returns NOT_IMPLEMENTED.  sap_get_interface
+ * gives B, C, V, W and Rbar (which = 0..4), of A or (adjoint) of A^T, as for
+ * sap_factor.
  * Device memory: the reordered bands (FP64, sum N_i (2 K_i + 1)), the factors
  * and sweep matrices of every block at its own K_i, for SaP-C the entire
- * spikes (2 N K elements of the factor precision) and the reduced matrices.
+ * spikes (2 N K elements of the factor precision) and the reduced matrices,
+ * the same again for A^T once a transposed operation has run.
  * Errors: INVALID_ARG (sizes, a perm that is not a permutation per block,
  * P < 1), NOT_IMPLEMENTED (a K_i above sap_max_K), SINGULAR (a reduced
  * matrix), TIMEOUT, OOM, CUDA.  Synchronises `stream`. */

@@ -136,7 +136,8 @@ template <typename T, int CPB>
 __global__ void __launch_bounds__(256)
 k_full_spikes(const double* __restrict__ band, BlockMap m, int KS, int ngmax, const void* const* __restrict__ Mfp,
               const void* const* __restrict__ Mbp, const int* __restrict__ ngp, const int64_t* __restrict__ ldp,
-              T* __restrict__ spk, const int64_t* __restrict__ sbase, T* __restrict__ Vtip, T* __restrict__ Wtip) {
+              T* __restrict__ spk, const int64_t* __restrict__ sbase, T* __restrict__ Vtip, T* __restrict__ Wtip,
+              int adj) {
   constexpr int NT = 256, CH = kChunk, CPW = CPB / 8;
   constexpr int MM = CH * CH;
   static_assert(CPW * sizeof(T) % 16 == 0, "a thread's columns are read as 16-byte vectors");
@@ -179,14 +180,24 @@ k_full_spikes(const double* __restrict__ band, BlockMap m, int KS, int ngmax, co
   const int rstart = rmin_s;
   const int cstart = rstart / CH;
 
-  // right-hand side at old local row a, column col: [0; B_i] or [C_{i+1}; 0]
+  // right-hand side at old local row a, column col: [0; B_i] or [C_{i+1}; 0]; for the
+  // preconditioner of A^T (adj) [0; C_{i+1}^T] or [B_i^T; 0]
   auto rhs = [&](int a, int col) -> T {
     double v = 0.0;
-    if (side == 0) {
-      const int rr = a - (n - K);                       // B_i(rr, col) = a(sif - K + rr, sif + col)
-      if (rr >= 0 && col <= rr) v = band[(int64_t)(rr - col) * N + sif + col];
-    } else if (a < K && col >= a) {                     // C_{i+1}(a, col) = a(sif + a, sif - K + col)
-      v = band[(int64_t)(2 * K + a - col) * N + sif - K + col];
+    if (!adj) {
+      if (side == 0) {
+        const int rr = a - (n - K);                     // B_i(rr, col) = a(sif - K + rr, sif + col)
+        if (rr >= 0 && col <= rr) v = band[(int64_t)(rr - col) * N + sif + col];
+      } else if (a < K && col >= a) {                   // C_{i+1}(a, col) = a(sif + a, sif - K + col)
+        v = band[(int64_t)(2 * K + a - col) * N + sif - K + col];
+      }
+    } else {
+      if (side == 0) {
+        const int rr = a - (n - K);                     // C_{i+1}^T(rr, col) = a(sif + col, sif - K + rr)
+        if (rr >= 0 && rr >= col) v = band[(int64_t)(2 * K + col - rr) * N + sif - K + rr];
+      } else if (a < K && a <= col) {                   // B_i^T(a, col) = a(sif - K + col, sif + a)
+        v = band[(int64_t)(col - a) * N + sif + a];
+      }
     }
     return (T)v;
   };
@@ -500,28 +511,32 @@ size_t full_spikes_smem(int ngmax, bool fp64) {
 template <typename T, int CPB>
 cudaError_t launch_spikes_cols(const double* band, const BlockMap& m, int ngmax, const void* const* Mfp,
                                const void* const* Mbp, const int* ngp, const int64_t* ldp, T* spk,
-                               const int64_t* sbase, T* Vtip, T* Wtip, cudaStream_t s) {
+                               const int64_t* sbase, T* Vtip, T* Wtip, bool adjoint, cudaStream_t s) {
   const size_t smem = spikes_smem<T, CPB>(ngmax);
   cudaError_t e = cudaFuncSetAttribute(k_full_spikes<T, CPB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   count_launches(1);
   k_full_spikes<T, CPB><<<dim3((m.K + CPB - 1) / CPB, 2, m.P - 1), 256, smem, s>>>(
-      band, m, spike_row_stride(m.K, sizeof(T) == 8), ngmax, Mfp, Mbp, ngp, ldp, spk, sbase, Vtip, Wtip);
+      band, m, spike_row_stride(m.K, sizeof(T) == 8), ngmax, Mfp, Mbp, ngp, ldp, spk, sbase, Vtip, Wtip,
+      adjoint ? 1 : 0);
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_full_spikes(const double* band, const BlockMap& m, int ngmax, const void* const* Mfp,
                                const void* const* Mbp, const int* ngp, const int64_t* ldp, T* spk,
-                               const int64_t* sbase, T* Vtip, T* Wtip, cudaStream_t s) {
+                               const int64_t* sbase, T* Vtip, T* Wtip, bool adjoint, cudaStream_t s) {
   if (m.P < 2) return cudaSuccess;
   const int c = spike_cols<T>(ngmax);
   if constexpr (sizeof(T) == 4) {
-    if (c == 64) return launch_spikes_cols<T, 64>(band, m, ngmax, Mfp, Mbp, ngp, ldp, spk, sbase, Vtip, Wtip, s);
+    if (c == 64)
+      return launch_spikes_cols<T, 64>(band, m, ngmax, Mfp, Mbp, ngp, ldp, spk, sbase, Vtip, Wtip, adjoint, s);
   }
-  if (c == 32) return launch_spikes_cols<T, 32>(band, m, ngmax, Mfp, Mbp, ngp, ldp, spk, sbase, Vtip, Wtip, s);
+  if (c == 32)
+    return launch_spikes_cols<T, 32>(band, m, ngmax, Mfp, Mbp, ngp, ldp, spk, sbase, Vtip, Wtip, adjoint, s);
   if constexpr (sizeof(T) == 8) {
-    if (c == 16) return launch_spikes_cols<T, 16>(band, m, ngmax, Mfp, Mbp, ngp, ldp, spk, sbase, Vtip, Wtip, s);
+    if (c == 16)
+      return launch_spikes_cols<T, 16>(band, m, ngmax, Mfp, Mbp, ngp, ldp, spk, sbase, Vtip, Wtip, adjoint, s);
   }
   return cudaErrorInvalidValue;
 }
@@ -558,10 +573,10 @@ cudaError_t launch_block_correct(const BlockMap& m, int max_rows, const double* 
 
 template cudaError_t launch_full_spikes<float>(const double*, const BlockMap&, int, const void* const*,
                                                const void* const*, const int*, const int64_t*, float*, const int64_t*,
-                                               float*, float*, cudaStream_t);
+                                               float*, float*, bool, cudaStream_t);
 template cudaError_t launch_full_spikes<double>(const double*, const BlockMap&, int, const void* const*,
                                                 const void* const*, const int*, const int64_t*, double*,
-                                                const int64_t*, double*, double*, cudaStream_t);
+                                                const int64_t*, double*, double*, bool, cudaStream_t);
 template cudaError_t launch_block_reduced<float>(const BlockMap&, const double*, const float*, const float*,
                                                  const double*, double*, double*, cudaStream_t, Gate);
 template cudaError_t launch_block_reduced<double>(const BlockMap&, const double*, const double*, const double*,

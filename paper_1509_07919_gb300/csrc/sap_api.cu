@@ -1351,9 +1351,29 @@ struct Blocks : SolverBase {
   double *rh = nullptr, *gh = nullptr, *xt = nullptr, *xb = nullptr;
   int* gerr = nullptr;                 // an entry beyond its block's K_b at the gather
   cudaEvent_t evfork = nullptr;
+  int64_t spk_elems = 0;
+  // the preconditioner of A^T, built on the first transposed use after a factorisation:
+  // its own spikes, tips and reduced matrices (f.Va, f.Wa, f.Ra, f.piva), apply scratch,
+  // and per block a stream of its own for the transposed sweeps (an adjoint solve may run
+  // concurrently with the forward one)
+  bool adjoint_ready = false;
+  bool amats_set = false;
+  const void** dMfa = nullptr;         // per block: chunk matrices of its U^T forward and L^T backward sweeps
+  const void** dMba = nullptr;
+  T* spk_a = nullptr;
+  unsigned char* gws_a = nullptr;
+  double *rh_t = nullptr, *gh_t = nullptr, *xt_t = nullptr, *xb_t = nullptr;
+  cudaEvent_t evfork_t = nullptr;
+  std::vector<cudaStream_t> tst;
+  std::vector<cudaEvent_t> tev;
   Blocks(sap_handle* hh, const int32_t* p, cudaStream_t s) : h(hh), perm_src(p), cs(s) {}
   ~Blocks() override {
     if (evfork) cudaEventDestroy(evfork);
+    if (evfork_t) cudaEventDestroy(evfork_t);
+    for (cudaStream_t x : tst)
+      if (x) cudaStreamDestroy(x);
+    for (cudaEvent_t e : tev)
+      if (e) cudaEventDestroy(e);
   }
   bool coupled() const { return h->opt.variant == SAP_C && h->L.P > 1; }
 
@@ -1481,6 +1501,7 @@ struct Blocks : SolverBase {
       TRY(h->mem.alloc(&dng, (size_t)P));
       TRY(h->mem.alloc(&dldp, (size_t)P));
       TRY(h->mem.alloc(&dsbase, sb.size()));
+      spk_elems = so;
       TRY(h->mem.alloc(&spk, (size_t)so));
       CK(cudaMemset(spk, 0, (size_t)so * sizeof(T)));     // the row padding is read (times 0) by the correction
       CK(cudaMemcpy(dMf, mf.data(), mf.size() * sizeof(void*), cudaMemcpyHostToDevice));
@@ -1502,6 +1523,7 @@ struct Blocks : SolverBase {
 
   sap_status_t factor(cudaStream_t s) override {
     const Layout& L = h->L;
+    adjoint_ready = false;               // rebuilt on the next transposed use
     CK(cudaEventRecord(h->evp[0], s));
     CK(launch_absmax(h->band, L.N, L.K, h->absmax, s));
     CK(cudaMemsetAsync(gerr, 0, sizeof(int), s));
@@ -1528,7 +1550,7 @@ struct Blocks : SolverBase {
     CK(cudaEventRecord(h->evu[1], s));
     CK(cudaEventRecord(h->evp[2], s));
     if (coupled()) {
-      CK(launch_full_spikes<T>(h->band, m, ngmax, dMf, dMb, dng, dldp, spk, dsbase, f.V, f.Wt, s));
+      CK(launch_full_spikes<T>(h->band, m, ngmax, dMf, dMb, dng, dldp, spk, dsbase, f.V, f.Wt, false, s));
       CK(cudaEventRecord(h->ev_rd, s));
       CK(launch_reduced<T>(f.V, f.Wt, L.K, L.P - 1, f.R, f.R0, f.piv, h->singular, gws, s));
     } else {
@@ -1540,15 +1562,96 @@ struct Blocks : SolverBase {
   sap_status_t factor_pre(cudaStream_t) override { return SAP_ERR_NOT_IMPLEMENTED; }
   sap_status_t factor_post(cudaStream_t) override { return SAP_ERR_NOT_IMPLEMENTED; }
   void lu_items(std::vector<LuItem>&) const override {}
-  sap_status_t build_adjoint(cudaStream_t) override { return SAP_ERR_NOT_IMPLEMENTED; }
-  sap_status_t build_adjoint_async(cudaStream_t) override { return SAP_ERR_NOT_IMPLEMENTED; }
+  // the preconditioner of A^T: the blocks' transposed sweep matrices (their own
+  // prepare_transposed), then the entire spikes of A^T and its reduced matrices; synchronises s
+  sap_status_t build_adjoint(cudaStream_t s) override {
+    if (adjoint_ready) return SAP_OK;
+    const Layout& L = h->L;
+    const int P = L.P, K = L.K;
+    if (!rh_t) {
+      TRY(h->mem.alloc(&rh_t, (size_t)L.N));
+      TRY(h->mem.alloc(&gh_t, (size_t)L.N));
+      CK(cudaEventCreateWithFlags(&evfork_t, cudaEventDisableTiming));
+      tst.assign((size_t)P, nullptr);
+      tev.assign((size_t)P, nullptr);
+      for (int b = 0; b < P; ++b) {
+        CK(cudaStreamCreateWithFlags(&tst[(size_t)b], cudaStreamNonBlocking));
+        CK(cudaEventCreateWithFlags(&tev[(size_t)b], cudaEventDisableTiming));
+      }
+    }
+    if (coupled()) {
+      const int nI = P - 1;
+      const int64_t KK = (int64_t)K * K;
+      if (!spk_a) {
+        TRY(h->mem.alloc(&spk_a, (size_t)spk_elems));
+        CK(cudaMemset(spk_a, 0, (size_t)spk_elems * sizeof(T)));
+        TRY(h->mem.alloc(&f.Va, (size_t)(nI * KK)));
+        TRY(h->mem.alloc(&f.Wa, (size_t)(nI * KK)));
+        TRY(h->mem.alloc(&f.Ra, (size_t)(nI * KK)));
+        TRY(h->mem.alloc(&f.Ra0, (size_t)(nI * KK)));
+        TRY(h->mem.alloc(&f.piva, (size_t)(nI * K)));
+        TRY(h->mem.alloc(&gws_a, reduced_ws_bytes(K, nI, sizeof(T) == 8)));
+        TRY(h->mem.alloc(&xt_t, (size_t)(nI * K)));
+        TRY(h->mem.alloc(&xb_t, (size_t)(nI * K)));
+        TRY(h->mem.alloc(&dMfa, (size_t)P));
+        TRY(h->mem.alloc(&dMba, (size_t)P));
+      }
+      if (!amats_set) {          // allocated by the blocks' first transposed preparation, then fixed
+        std::vector<const void*> mf((size_t)P), mb((size_t)P);
+        for (int b = 0; b < P; ++b) {
+          auto* sv = dynamic_cast<Solver<T>*>(sub[(size_t)b]->impl.get());
+          if (!sv || !sv->f.Mutf || !sv->f.Mltb) return SAP_ERR_CUDA;
+          mf[(size_t)b] = sv->f.Mutf;
+          mb[(size_t)b] = sv->f.Mltb;
+        }
+        CK(cudaMemcpy(dMfa, mf.data(), mf.size() * sizeof(void*), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(dMba, mb.data(), mb.size() * sizeof(void*), cudaMemcpyHostToDevice));
+        amats_set = true;
+      }
+      CK(cudaMemsetAsync(h->singular_a, 0, sizeof(int), s));
+      CK(launch_full_spikes<T>(h->band, m, ngmax, dMfa, dMba, dng, dldp, spk_a, dsbase, f.Va, f.Wa, true, s));
+      CK(launch_reduced<T>(f.Va, f.Wa, K, nI, f.Ra, f.Ra0, f.piva, h->singular_a, gws_a, s));
+      int sing = 0;
+      CK(cudaMemcpyAsync(&sing, h->singular_a, sizeof(int), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      if (sing) return SAP_ERR_SINGULAR;
+    }
+    adjoint_ready = true;
+    return SAP_OK;
+  }
+  sap_status_t prepare_transposed(cudaStream_t s) override {
+    for (auto& q : sub) TRY(q->impl->prepare_transposed(s));
+    return build_adjoint(s);
+  }
+  sap_status_t build_adjoint_async(cudaStream_t s) override { return prepare_transposed(s); }
   sap_status_t adjoint_singular() override { return SAP_OK; }
-  sap_status_t prepare_transposed(cudaStream_t) override { return SAP_ERR_NOT_IMPLEMENTED; }
-  bool has_transposed() const override { return false; }
   const std::vector<int>* block_bandwidths() const override { return &Kb; }
 
+  sap_status_t apply_transposed(const double* r, double* z, cudaStream_t s, Gate gt) {
+    const Layout& L = h->L;
+    // inside a Krylov run's capture begin() has prepared A^T's preconditioner on the caller's stream
+    cudaStreamCaptureStatus cst = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cst) != cudaSuccess || cst == cudaStreamCaptureStatusNone)
+      TRY(prepare_transposed(s));
+    if (!adjoint_ready) return SAP_ERR_NOT_IMPLEMENTED;
+    CK(launch_block_perm(m, r, rh_t, true, s, gt));
+    CK(cudaEventRecord(evfork_t, s));
+    for (int b = 0; b < L.P; ++b) {
+      CK(cudaStreamWaitEvent(tst[(size_t)b], evfork_t, 0));
+      TRY(sub[(size_t)b]->impl->apply(rh_t + L.off[b], gh_t + L.off[b], true, tst[(size_t)b], gt));
+      CK(cudaEventRecord(tev[(size_t)b], tst[(size_t)b]));
+      CK(cudaStreamWaitEvent(s, tev[(size_t)b], 0));
+    }
+    if (!coupled()) {
+      CK(launch_block_perm(m, gh_t, z, false, s, gt));
+      return SAP_OK;
+    }
+    CK(launch_block_reduced<T>(m, gh_t, f.Va, f.Wa, f.Ra, xt_t, xb_t, s, gt));
+    CK(launch_block_correct<T>(m, (int)(L.off[1] - L.off[0]), gh_t, spk_a, dsbase, xt_t, xb_t, z, s, gt));
+    return SAP_OK;
+  }
   sap_status_t apply(const double* r, double* z, bool transpose, cudaStream_t s, Gate gt) override {
-    if (transpose) return SAP_ERR_NOT_IMPLEMENTED;
+    if (transpose) return apply_transposed(r, z, s, gt);
     const Layout& L = h->L;
     CK(launch_block_perm(m, r, rh, true, s, gt));
     CK(cudaEventRecord(evfork, s));
@@ -1606,16 +1709,17 @@ struct Blocks : SolverBase {
     const int K = h->L.K;
     const int64_t KK = (int64_t)K * K;
     if (!coupled() || i < 0 || i >= h->L.P - 1 || which < 0 || which > 4) return SAP_ERR_INVALID_ARG;
-    if (adjoint) return SAP_ERR_NOT_IMPLEMENTED;
-    if (which <= 1) return read_coupling(h, i, which, false, host, s);
+    if (adjoint) TRY(prepare_transposed(s));
+    if (which <= 1) return read_coupling(h, i, which, adjoint, host, s);
     if (which == 4) {
-      CK(cudaMemcpyAsync(host, f.R0 + i * KK, (size_t)KK * sizeof(double), cudaMemcpyDeviceToHost, s));
+      CK(cudaMemcpyAsync(host, (adjoint ? f.Ra0 : f.R0) + i * KK, (size_t)KK * sizeof(double),
+                         cudaMemcpyDeviceToHost, s));
       CK(cudaStreamSynchronize(s));
       return SAP_OK;
     }
     std::vector<T> buf((size_t)KK);
-    CK(cudaMemcpyAsync(buf.data(), (which == 2 ? f.V : f.Wt) + i * KK, (size_t)KK * sizeof(T),
-                       cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(buf.data(), (which == 2 ? (adjoint ? f.Va : f.V) : (adjoint ? f.Wa : f.Wt)) + i * KK,
+                       (size_t)KK * sizeof(T), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     for (int64_t e = 0; e < KK; ++e) host[e] = (double)buf[(size_t)e];
     return SAP_OK;

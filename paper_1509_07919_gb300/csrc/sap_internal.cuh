@@ -241,11 +241,13 @@ int spike_row_stride(int K, bool fp64);
 // sbase[2 i] for Vhat_i, sbase[2 i + 1] for What_{i+1}) by the sweeps of
 // each block b with its chunk matrices (Mfp[b]: forward L, Mbp[b]: backward
 // U, ngp[b] couplings per chunk, leading dimension ldp[b]), and their tips
-// V^(b)_i, W^(t)_{i+1} (K x K row-major per interface).
+// V^(b)_i, W^(t)_{i+1} (K x K row-major per interface).  adjoint: the spikes of
+// the preconditioner of A^T (Mfp / Mbp then the blocks' U^T forward and L^T
+// backward matrices; couplings B'_i = C_{i+1}^T, C'_{i+1} = B_i^T).
 template <typename T>
 cudaError_t launch_full_spikes(const double* band, const BlockMap& m, int ngmax, const void* const* Mfp,
                                const void* const* Mbp, const int* ngp, const int64_t* ldp, T* spk,
-                               const int64_t* sbase, T* Vtip, T* Wtip, cudaStream_t s);
+                               const int64_t* sbase, T* Vtip, T* Wtip, bool adjoint, cudaStream_t s);
 // x^(t), x^(b) of every interface from g = D^{-1} r (new numbering), Eq. (2.5b,c).
 template <typename T>
 cudaError_t launch_block_reduced(const BlockMap& m, const double* gh, const T* V, const T* Wt, const double* Rinv,

@@ -5,7 +5,9 @@ on both sides, so the permutations agree exactly), the blocks' half-bandwidths,
 the spike tips and reduced matrices, the preconditioner apply entry by entry
 (SaP-D and SaP-C, FP64 and FP32 factors, CM and random block numberings, a
 global K above sap_max_K), solves, refactoring and the errors of the
-operations the handle does not offer."""
+operations the handle does not offer; the preconditioner of A^T (adjoint and pair
+solves) against the oracle built on the transposed band with the same block
+numbering."""
 import numpy as np
 import pytest
 import torch
@@ -183,11 +185,6 @@ def test_operations_not_offered(sap):
     band = dev(S.band)
     perm, _ = sap.sap_block_cm_reorder(band, N, K, P)
     h = sap.sap_factor_blocks(band, N, K, perm, P=P, variant=1, precision=1)
-    g = dev(G.adjoint_seed(N, 81))
-    _, _, st = sap.sap_solve_adjoint(h, g, raise_on_error=False)
-    assert st == sap.SAP_ERR_NOT_IMPLEMENTED
-    with pytest.raises(sap.SapError):
-        sap.sap_apply_preconditioner(h, g, transpose=True)
     with pytest.raises(sap.SapError):
         sap.sap_get_block_lu(h, 0)
     with pytest.raises(sap.SapError):
@@ -217,3 +214,50 @@ def test_full_size_bench_workload(sap):
         o = OB.BlockSap(S.band, N, K, P, po, variant)
         z = host(sap.sap_apply_preconditioner(h, dev(r)))
         assert maxerr(z, o.apply(r)) <= 1e-4
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("variant", [0, 1])
+def test_transposed_preconditioner_and_adjoint_solves(sap, prec, variant):
+    """The preconditioner of A^T (the blocks of A^T renumbered by the same
+    permutations are the transposes of the reordered blocks; couplings
+    B'_i = C_{i+1}^T, C'_{i+1} = B_i^T): its apply entry by entry, its tips and
+    reduced matrices, the adjoint solve by its residual, the pair solve against
+    the separate solves, and both directions again after a refactor."""
+    N, K, P = 24000, 24, 12
+    off, S = system(N, K, P, 0.8, 100 + variant)
+    po, _ = OB.block_cm(S.band, N, K, P)
+    band = dev(S.band)
+    h = sap.sap_factor_blocks(band, N, K, dev(po.astype(np.int32)), P=P, variant=variant, precision=prec)
+    bt = O.transpose_band(S.band, N, K)
+    oa = OB.BlockSap(bt, N, K, P, po, variant)
+    of = OB.BlockSap(S.band, N, K, P, po, variant)
+    r = G.adjoint_seed(N, 101)
+    za = host(sap.sap_apply_preconditioner(h, dev(r), transpose=True))
+    assert maxerr(za, oa.apply(r)) <= TOL[prec]
+    assert maxerr(host(sap.sap_apply_preconditioner(h, dev(r))), of.apply(r)) <= TOL[prec]
+    if variant == 1:
+        tol = 1e-12 if prec == 0 else 2e-5
+        for i in range(P - 1):
+            for which, ref in (("V", oa.Vb[i]), ("W", oa.Wt[i]), ("R", oa.R[i][0]), ("B", oa.B[i]), ("C", oa.C[i])):
+                m = sap.sap_get_interface(h, i, which, adjoint=True)
+                assert np.abs(m - ref).max() <= tol * max(1.0, np.abs(ref).max()), (i, which)
+    g = G.adjoint_seed(N, 102)
+    lam, info, st = sap.sap_solve_adjoint(h, dev(g))
+    assert st == 0 and info.relres <= 1e-10 and info.graphed == 1
+    res = g - O.spmv(S.band, N, K, host(lam), transpose=True)
+    assert np.linalg.norm(res) <= 1e-9 * np.linalg.norm(g)
+    xt = G.x_true(N, 103)
+    b = O.spmv(S.band, N, K, xt)
+    x1, _, _ = sap.sap_solve(h, dev(b))
+    x2, l2, ix, il, st2 = sap.sap_solve_pair(h, dev(b), dev(g))
+    assert st2 == 0
+    assert np.abs(host(x2) - host(x1)).max() <= 1e-12 * np.abs(host(x1)).max()
+    assert np.abs(host(l2) - host(lam)).max() <= 1e-12 * np.abs(host(lam)).max()
+    # new values, same pattern: both directions follow
+    b2 = S.band * np.linspace(0.7, 1.3, S.band.size)
+    band.copy_(torch.from_numpy(b2))
+    sap.sap_refactor(h)
+    oa2 = OB.BlockSap(O.transpose_band(b2, N, K), N, K, P, po, variant)
+    za2 = host(sap.sap_apply_preconditioner(h, dev(r), transpose=True))
+    assert maxerr(za2, oa2.apply(r)) <= TOL[prec]

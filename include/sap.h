@@ -294,8 +294,8 @@ SAP_API const char *sap_status_string(sap_status_t s);
  *   1 if one of the call's bounded device waits gave up (x then holds
  *   unspecified values) and 0 otherwise; read it once the stream has
  *   completed.  With timeout_dev = NULL a timeout goes unreported.
- *   The first call on a device looks up the array's device address; make
- *   that first call before any stream capture.
+ *   The first call on a device also looks up the array's device address
+ *   (a host-side runtime query, made once per device).
  *   Every call uses the same array and overwrites the previous call's
  *   contents, so calls that overlap on the GPU (other streams or threads)
  *   race; order them on one stream.  Asynchronous on `stream`.

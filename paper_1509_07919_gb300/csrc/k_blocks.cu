@@ -394,7 +394,10 @@ k_block_reduced(BlockMap m, const double* __restrict__ gh, const T* __restrict__
 // z[off_b + pinv(r)] = g[off_b + r] - Vhat_b[r] . x^(t)_{b+1} - What_b[r] . x^(b)_{b-1}
 // for every new row r of every block b: CTA (row chunk, block b), the two
 // x vectors in shared memory (zero padded to KS), a warp per row, 16-byte
-// loads of the spike rows (KS elements, 16-byte aligned).
+// loads of the spike rows (KS elements, 16-byte aligned).  The products are
+// formed in the factor precision (the spikes' own; with FP32 factors the FP64
+// pipe, a small fraction of the FP32 rate on this part, would bound them), the
+// subtraction from g in FP64.
 constexpr int kCorrRows = 128;
 template <typename T>
 __global__ void __launch_bounds__(256)
@@ -404,7 +407,7 @@ k_block_correct(BlockMap m, const double* __restrict__ gh, const T* __restrict__
   constexpr int VW = 16 / sizeof(T);
   using Vec = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  double* xs = reinterpret_cast<double*>(smem_raw);      // 2 x KS
+  T* xs = reinterpret_cast<T*>(smem_raw);                // 2 x KS
   const int K = m.K, b = blockIdx.y;
   const int64_t s = m.off[b];
   const int n = (int)(m.off[b + 1] - s);
@@ -412,8 +415,8 @@ k_block_correct(BlockMap m, const double* __restrict__ gh, const T* __restrict__
   if (r0 >= n) return;
   const bool hasV = b < m.P - 1, hasW = b > 0;
   for (int k = threadIdx.x; k < KS; k += blockDim.x) {
-    xs[k] = hasV && k < K ? xt[(int64_t)b * K + k] : 0.0;
-    xs[KS + k] = hasW && k < K ? xb[(int64_t)(b - 1) * K + k] : 0.0;
+    xs[k] = (T)(hasV && k < K ? xt[(int64_t)b * K + k] : 0.0);
+    xs[KS + k] = (T)(hasW && k < K ? xb[(int64_t)(b - 1) * K + k] : 0.0);
   }
   __syncthreads();
   const T* V = hasV ? spk + sbase[2 * b] : nullptr;
@@ -422,26 +425,28 @@ k_block_correct(BlockMap m, const double* __restrict__ gh, const T* __restrict__
   const int nv = KS / VW;
   const int r1 = min(n, r0 + kCorrRows);
   for (int r = r0 + w; r < r1; r += 8) {
-    double a = 0.0;
+    T a = T(0);
     for (int v = lane; v < nv; v += 32) {
-      const double* x0 = xs + v * VW;
-      const double* x1 = xs + KS + v * VW;
+      const Vec x0 = reinterpret_cast<const Vec*>(xs)[v];
+      const Vec x1 = reinterpret_cast<const Vec*>(xs + KS)[v];
+      const T* p0 = reinterpret_cast<const T*>(&x0);
+      const T* p1 = reinterpret_cast<const T*>(&x1);
       if (hasV) {
         const Vec q = reinterpret_cast<const Vec*>(V + (int64_t)r * KS)[v];
         const T* e = reinterpret_cast<const T*>(&q);
 #pragma unroll
-        for (int u = 0; u < VW; ++u) a += (double)e[u] * x0[u];
+        for (int u = 0; u < VW; ++u) a += e[u] * p0[u];
       }
       if (hasW) {
         const Vec q = reinterpret_cast<const Vec*>(W + (int64_t)r * KS)[v];
         const T* e = reinterpret_cast<const T*>(&q);
 #pragma unroll
-        for (int u = 0; u < VW; ++u) a += (double)e[u] * x1[u];
+        for (int u = 0; u < VW; ++u) a += e[u] * p1[u];
       }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-    if (lane == 0) z[s + m.pinv[s + r]] = gh[s + r] - a;
+    if (lane == 0) z[s + m.pinv[s + r]] = gh[s + r] - (double)a;
   }
 }
 
@@ -560,7 +565,7 @@ cudaError_t launch_block_correct(const BlockMap& m, int max_rows, const double* 
                                  const int64_t* sbase, const double* xt, const double* xb, double* z, cudaStream_t s,
                                  Gate gt) {
   const int KS = spike_row_stride(m.K, sizeof(T) == 8);
-  const size_t smem = 2 * (size_t)KS * sizeof(double);
+  const size_t smem = 2 * (size_t)KS * sizeof(T);
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k_block_correct<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;

@@ -261,3 +261,27 @@ def test_transposed_preconditioner_and_adjoint_solves(sap, prec, variant):
     oa2 = OB.BlockSap(O.transpose_band(b2, N, K), N, K, P, po, variant)
     za2 = host(sap.sap_apply_preconditioner(h, dev(r), transpose=True))
     assert maxerr(za2, oa2.apply(r)) <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec,N,K", [(1, 4800, 800), (0, 3000, 480)])
+def test_wide_blocks_take_the_narrow_spike_tiles(sap, prec, N, K):
+    """Blocks so wide that the entire-spike kernel narrows its column tiles to
+    fit shared memory (FP32: K_b > 352, 32 columns per CTA; FP64: K_b > 224,
+    16 columns), with the reduced matrices of a global K of 800 / 480: the
+    apply and the tips against the oracle, and a solve."""
+    P = 2
+    off = O.partition(N, P)
+    S = G.block_scrambled(N, K, off, 1.0, 110, k0_lo=0.95)
+    po, Ko = OB.block_cm(S.band, N, K, P)
+    assert min(Ko) > (352 if prec == 1 else 224)
+    h = sap.sap_factor_blocks(dev(S.band), N, K, dev(po.astype(np.int32)), P=P, variant=1, precision=prec)
+    o = OB.BlockSap(S.band, N, K, P, po, O.SAP_C)
+    r = G.adjoint_seed(N, 111)
+    assert maxerr(host(sap.sap_apply_preconditioner(h, dev(r))), o.apply(r)) <= TOL[prec]
+    tol = 1e-12 if prec == 0 else 2e-5
+    for which, ref in (("V", o.Vb[0]), ("W", o.Wt[0])):
+        m = sap.sap_get_interface(h, 0, which)
+        assert np.abs(m - ref).max() <= tol * max(1.0, np.abs(ref).max()), which
+    xt = G.x_true(N, 112)
+    x, info, st = sap.sap_solve(h, dev(O.spmv(S.band, N, K, xt)))
+    assert st == 0 and info.relres <= 1e-10

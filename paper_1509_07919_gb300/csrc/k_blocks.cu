@@ -495,11 +495,13 @@ int spike_row_stride(int K, bool fp64) {
   return (K + vw - 1) / vw * vw;
 }
 
-// columns per CTA of the spike kernel: the widest of 64, 32, 16 whose shared memory fits
-// (FP32: 64 or 32, at least 16 bytes of columns per thread; FP64: 32 or 16)
+// columns per CTA of the spike kernel: 32 (measured on GB300 at N = 200000,
+// P = 50: FP32 K = 100 1.25 ms against 1.50 ms with 64 columns, twice the CTAs
+// on the latency-bound chunk chains; K = 400 6.28 against 6.36 ms), or 16 for
+// FP64 blocks whose 32-column tiles exceed shared memory (at least 16 bytes of
+// columns per thread)
 template <typename T>
 int spike_cols(int ngmax) {
-  if (sizeof(T) == 4 && spikes_smem<T, 64>(ngmax) <= kSmemPerBlock) return 64;
   if (spikes_smem<T, 32>(ngmax) <= kSmemPerBlock) return 32;
   return sizeof(T) == 8 && spikes_smem<T, 16>(ngmax) <= kSmemPerBlock ? 16 : 0;
 }
@@ -509,8 +511,7 @@ size_t full_spikes_smem(int ngmax, bool fp64) {
     const int c = spike_cols<double>(ngmax);
     return c == 32 ? spikes_smem<double, 32>(ngmax) : spikes_smem<double, 16>(ngmax);
   }
-  const int c = spike_cols<float>(ngmax);
-  return c == 64 ? spikes_smem<float, 64>(ngmax) : c == 32 ? spikes_smem<float, 32>(ngmax) : kSmemPerBlock + 1;
+  return spike_cols<float>(ngmax) == 32 ? spikes_smem<float, 32>(ngmax) : kSmemPerBlock + 1;
 }
 
 template <typename T, int CPB>
@@ -533,10 +534,6 @@ cudaError_t launch_full_spikes(const double* band, const BlockMap& m, int ngmax,
                                const int64_t* sbase, T* Vtip, T* Wtip, bool adjoint, cudaStream_t s) {
   if (m.P < 2) return cudaSuccess;
   const int c = spike_cols<T>(ngmax);
-  if constexpr (sizeof(T) == 4) {
-    if (c == 64)
-      return launch_spikes_cols<T, 64>(band, m, ngmax, Mfp, Mbp, ngp, ldp, spk, sbase, Vtip, Wtip, adjoint, s);
-  }
   if (c == 32)
     return launch_spikes_cols<T, 32>(band, m, ngmax, Mfp, Mbp, ngp, ldp, spk, sbase, Vtip, Wtip, adjoint, s);
   if constexpr (sizeof(T) == 8) {

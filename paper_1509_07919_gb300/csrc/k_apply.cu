@@ -437,7 +437,9 @@ size_t chain_smem(int K, int S) {
   return (size_t)chain_ring<T>(K, S) * kh * kh * sizeof(T) + (size_t)(S + 1) * kh * sizeof(T);
 }
 
-template <typename T>
+// GT: the transfer matrices are read from global memory (L2) instead of
+// being staged, for histories whose KH x KH matrix exceeds shared memory.
+template <typename T, bool GT>
 __global__ void __launch_bounds__(kCorrThreads)
 k_seg_chain(const T* __restrict__ Tall, T* __restrict__ tails, int K, Dev d, int S, Gate gt) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -447,14 +449,15 @@ k_seg_chain(const T* __restrict__ Tall, T* __restrict__ tails, int K, Dev d, int
   const int nch = (int)(d.ld[b] / CHK);
   const int cps = seg_chunks(nch, S);
   const int nseg = (nch + cps - 1) / cps;          // nonempty segments of this block
-  const int RB = chain_ring<T>(K, S);
-  T* Ts = reinterpret_cast<T*>(smem_raw);         // RB x NGW x NGW
-  T* zt = Ts + (size_t)RB * NGW * NGW;            // S x NGW tails (in place: zero-history -> true)
+  const int RB = GT ? S : chain_ring<T>(K, S);
+  T* Ts = reinterpret_cast<T*>(smem_raw);         // RB x NGW x NGW (staged T_j; none for GT)
+  T* zt = GT ? Ts : Ts + (size_t)RB * NGW * NGW;  // S x NGW tails (in place: zero-history -> true)
   T* tb = tails + (int64_t)b * S * NGW;
   // threads per row: the largest power of two <= 8 dividing NGW with NGW TPR <= 256
   int TPR = 1;
   while (TPR < 8 && NGW % (2 * TPR) == 0 && NGW * 2 * TPR <= kCorrThreads) TPR *= 2;
-  const int i = threadIdx.x / TPR, part = threadIdx.x % TPR;
+  const int part = threadIdx.x % TPR;
+  const int RPP = kCorrThreads / TPR;              // rows per pass (NGW may exceed it)
   const int jend = nseg - 1;                       // tails 1 .. nseg-2 are needed
   auto stage = [&](void* dsts, const void* srcg, int nbytes) {
     const char* src = reinterpret_cast<const char*>(srcg);
@@ -468,29 +471,32 @@ k_seg_chain(const T* __restrict__ Tall, T* __restrict__ tails, int K, Dev d, int
   for (int j0 = 1; j0 < jend; j0 += RB) {
     const int nr = min(RB, jend - j0);
     if (j0 > 1) __syncthreads();    // previous round's readers of Ts are done
-    stage(Ts, Tall + ((int64_t)b * S + j0) * NGW * NGW, nr * NGW * NGW * (int)sizeof(T));
+    if (!GT) stage(Ts, Tall + ((int64_t)b * S + j0) * NGW * NGW, nr * NGW * NGW * (int)sizeof(T));
     asm volatile("cp.async.commit_group;\n" ::: "memory");
     asm volatile("cp.async.wait_all;\n" ::: "memory");
     __syncthreads();
     for (int u = 0; u < nr; ++u) {
       const int j = j0 + u;
-      const T* Tj = Ts + (size_t)u * NGW * NGW;
+      const T* Tj = GT ? Tall + ((int64_t)b * S + j) * NGW * NGW : Ts + (size_t)u * NGW * NGW;
       const T* hp = zt + (size_t)(j - 1) * NGW;    // true tail_{j-1}
-      T acc = T(0);
-      if (i < NGW) {
-        const T* row = Tj + i * NGW;
-        int q = (part + TPR * i) % NGW;
-        for (int m = 0; m < NGW / TPR; ++m) {
-          acc += row[q] * hp[q];
-          q += TPR;
-          if (q >= NGW) q -= NGW;
+      for (int i0 = 0; i0 < NGW; i0 += RPP) {
+        const int i = i0 + (int)threadIdx.x / TPR;
+        T acc = T(0);
+        if (i < NGW) {
+          const T* row = Tj + (size_t)i * NGW;
+          int q = (part + TPR * i) % NGW;
+          for (int m = 0; m < NGW / TPR; ++m) {
+            acc += row[q] * hp[q];
+            q += TPR;
+            if (q >= NGW) q -= NGW;
+          }
         }
-      }
-      for (int o = TPR / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-      if (i < NGW && part == 0) {
-        const T t = zt[(size_t)j * NGW + i] + acc;
-        zt[(size_t)j * NGW + i] = t;
-        tb[(int64_t)j * NGW + i] = t;
+        for (int o = TPR / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (i < NGW && part == 0) {
+          const T t = zt[(size_t)j * NGW + i] + acc;
+          zt[(size_t)j * NGW + i] = t;
+          tb[(int64_t)j * NGW + i] = t;
+        }
       }
       __syncthreads();
     }
@@ -517,7 +523,6 @@ __global__ void __launch_bounds__(kCorrThreads)
 k_seg_correct(const T* __restrict__ Xall, const T* __restrict__ tails, const T* __restrict__ Tall, int K, Dev d,
               int S, int cpsmax, OT* __restrict__ out, Gate gt) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ T hs[4 * CHK];
   if (gate_skip(gt)) return;
   const int b = blockIdx.z;
   const int seg = (int)blockIdx.y + 1;
@@ -530,7 +535,7 @@ k_seg_correct(const T* __restrict__ Xall, const T* __restrict__ tails, const T* 
   const int c0 = seg * cps, c1 = min(nch, c0 + cps);
   const int p = blockIdx.x * kCorrThreads + threadIdx.x;
   if (c0 >= c1 || (int)blockIdx.x * kCorrThreads >= (c1 - c0) * CHK) return;
-  const T* h = hs;
+  const T* h = nullptr;
   if (CHAIN && seg >= 2) {
     T* Ts = reinterpret_cast<T*>(smem_raw);                   // T_1 .. T_{seg-1}
     T* zt = Ts + (size_t)(seg - 1) * NGW * NGW;               // tails 0 .. seg-1
@@ -547,28 +552,34 @@ k_seg_correct(const T* __restrict__ Xall, const T* __restrict__ tails, const T* 
     __syncthreads();
     int TPR = 1;
     while (TPR < 8 && NGW % (2 * TPR) == 0 && NGW * 2 * TPR <= kCorrThreads) TPR *= 2;
-    const int i = threadIdx.x / TPR, part = threadIdx.x % TPR;
+    const int part = threadIdx.x % TPR;
+    const int RPP = kCorrThreads / TPR;            // rows per pass
     for (int j = 1; j < seg; ++j) {
       const T* Tj = Ts + (size_t)(j - 1) * NGW * NGW;
       const T* hp = zt + (size_t)(j - 1) * NGW;
-      T acc = T(0);
-      if (i < NGW) {
-        const T* row = Tj + i * NGW;
-        int q = (part + TPR * i) % NGW;
-        for (int m = 0; m < NGW / TPR; ++m) {
-          acc += row[q] * hp[q];
-          q += TPR;
-          if (q >= NGW) q -= NGW;
+      for (int i0 = 0; i0 < NGW; i0 += RPP) {
+        const int i = i0 + (int)threadIdx.x / TPR;
+        T acc = T(0);
+        if (i < NGW) {
+          const T* row = Tj + (size_t)i * NGW;
+          int q = (part + TPR * i) % NGW;
+          for (int m = 0; m < NGW / TPR; ++m) {
+            acc += row[q] * hp[q];
+            q += TPR;
+            if (q >= NGW) q -= NGW;
+          }
         }
+        for (int o = TPR / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (i < NGW && part == 0) zt[(size_t)j * NGW + i] += acc;
       }
-      for (int o = TPR / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-      if (i < NGW && part == 0) zt[(size_t)j * NGW + i] += acc;
       __syncthreads();
     }
     h = zt + (size_t)(seg - 1) * NGW;
   } else {
-    for (int t = threadIdx.x; t < NGW; t += blockDim.x) hs[t] = tails[((int64_t)b * S + seg - 1) * NGW + t];
+    T* hd = reinterpret_cast<T*>(smem_raw);       // the true tail_{s-1} (NGW values)
+    for (int t = threadIdx.x; t < NGW; t += blockDim.x) hd[t] = tails[((int64_t)b * S + seg - 1) * NGW + t];
     __syncthreads();
+    h = hd;
   }
   if (p >= (c1 - c0) * CHK) return;
   const int r = row_of<MODE>(c0 * CHK + p, ld);
@@ -822,8 +833,12 @@ cudaError_t launch_sweep(const T* M, const T* Tm, const T* Xm, const Factors<T>&
     return cudaGetLastError();
   }
   if (S > 2) {
-    const size_t csmem = chain_smem<T>(K, S);
-    auto chain = k_seg_chain<T>;
+    size_t csmem = chain_smem<T>(K, S);
+    auto chain = k_seg_chain<T, false>;
+    if (csmem > kSmemPerBlock) {        // one transfer matrix exceeds shared memory: read them from L2
+      csmem = (size_t)(S + 1) * hist_width(K) * sizeof(T);
+      chain = k_seg_chain<T, true>;
+    }
     if (csmem > 48 * 1024) {
       e = cudaFuncSetAttribute(chain, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csmem);
       if (e != cudaSuccess) return e;
@@ -834,8 +849,8 @@ cudaError_t launch_sweep(const T* M, const T* Tm, const T* Xm, const Factors<T>&
     if (e != cudaSuccess) return e;
   }
   count_launches(1);
-  k_seg_correct<T, OT, MODE, false><<<dim3(tiles, S - 1, P), kCorrThreads, 0, s>>>(Xm, f.tails, Tm, K, d, S,
-                                                                                   f.cpsmax, out, gt);
+  k_seg_correct<T, OT, MODE, false><<<dim3(tiles, S - 1, P), kCorrThreads, (size_t)hist_width(K) * sizeof(T), s>>>(
+      Xm, f.tails, Tm, K, d, S, f.cpsmax, out, gt);
   return cudaGetLastError();
 }
 
@@ -886,6 +901,9 @@ cudaError_t launch_block_solve(const Factors<T>& f, int K, int P, Dev d, const d
 
 // the unsegmented sweep's smallest ring (two chunks ahead, four prepare warps): the limit on K
 size_t sweep_smem_bytes(int K, bool fp64) { return fp64 ? sweep_smem<double, 2, 4>(K) : sweep_smem<float, 2, 4>(K); }
+bool seg_sweeps_fit(int K, bool fp64) {
+  return (fp64 ? sweep_smem<double>(K) : sweep_smem<float>(K)) <= kSmemPerBlock;
+}
 int chunk_couplings(int K) { return n_couplings(K); }
 
 // scratch layout (doubles): [0, N) g ; then T tmp (N); then ctop, cbot ((P-1) K each);

@@ -379,6 +379,120 @@ k_seg_trans(const T* __restrict__ Mall, const int64_t* __restrict__ cbase, Dev d
   }
 }
 
+// The same X and T for more than 4 couplings per chunk (ng known at run
+// time), where the 32 ng history columns of X no longer fit one CTA's shared
+// memory: the KH stored history columns split into tiles of 32, one CTA per
+// (tile, segment s >= 1, block); the ng + 1 most recent 32 x 32 tiles of X in
+// a ring (row stride padded by 16 bytes: the 16-byte row writes of a warp fall
+// on distinct banks), the couplings G_{c,1..ng} of each chunk staged by
+// cp.async while the previous chunk is computed.  Thread (warp w, lane t)
+// forms row t of the tile for columns 4 w .. 4 w + 3:
+//     X_c = - sum_k G_{c,k} X_{c-k},   X = the identity on the history positions.
+constexpr int kWideTile = 32;
+template <typename T>
+__host__ __device__ inline size_t seg_trans_wide_smem(int ng) {
+  const size_t rs = kWideTile + 16 / sizeof(T);
+  return (2 * (size_t)ng * CH * CH + (size_t)(ng + 1) * CH * rs) * sizeof(T);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_seg_trans_wide(const T* __restrict__ Mall, const int64_t* __restrict__ cbase, Dev d, int S, int cpsmax, int kh,
+                 int ng, T* __restrict__ Tout, T* __restrict__ Xout) {
+  constexpr int NT = 256, CPB = kWideTile, CPW = CPB / 8;
+  constexpr int RS = CPB + 16 / (int)sizeof(T);
+  constexpr int MM = CH * CH;
+  using V = typename Vec16<T>::type;
+  constexpr int E = 16 / (int)sizeof(T);
+  static_assert(CPW % E == 0, "a thread's columns are whole 16-byte vectors");
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* Gbuf = reinterpret_cast<T*>(smem_raw);              // 2 x ng x 32 x 32
+  T* ring = Gbuf + 2 * (size_t)ng * MM;                   // (ng + 1) x 32 x RS
+  const int b = blockIdx.z, s = blockIdx.y + 1;
+  const int q0 = blockIdx.x * CPB;                        // first stored history column of the tile
+  const int nch = (int)(d.ld[b] / CH);
+  const int cps = seg_chunks(nch, S);
+  const int c0 = s * cps, c1 = min(nch, c0 + cps);
+  if (c0 >= c1) return;
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int SL = ng + 1;
+  auto slot = [&](int c) { return ((c % SL) + SL) % SL; };
+  for (int e = tid; e < SL * CH * RS; e += NT) ring[e] = T(0);
+  __syncthreads();
+  // history: stored column qq is position c0 32 - kh + qq, where X = 1
+  for (int e = tid; e < CPB; e += NT) {
+    const int qq = q0 + e;
+    if (qq < kh) {
+      const int pos = c0 * CH - kh + qq;
+      ring[slot(pos / CH) * CH * RS + (pos % CH) * RS + e] = T(1);
+    }
+  }
+  const T* Mb = Mall + cbase[b];
+  const int64_t xm = (int64_t)cpsmax * CH;
+  T* Xb = Xout + ((int64_t)b * (S - 1) + (s - 1)) * xm * kh;
+  auto stage = [&](int cc, int buf) {
+    const char* src = reinterpret_cast<const char*>(Mb + (int64_t)cc * (1 + ng) * MM + MM);
+    const unsigned dst = (unsigned)__cvta_generic_to_shared(Gbuf + (size_t)buf * ng * MM);
+    const int nbytes = ng * MM * (int)sizeof(T);
+    for (int o = tid * 16; o < nbytes; o += NT * 16)
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst + o), "l"(src + o) : "memory");
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+  };
+  stage(c0, 0);
+  for (int c = c0; c < c1; ++c) {
+    const int cur = (c - c0) & 1;
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    __syncthreads();                                     // chunk c's couplings; the ring's last tiles
+    if (c + 1 < c1) stage(c + 1, cur ^ 1);
+    const T* Gs = Gbuf + (size_t)cur * ng * MM;
+    T acc[CPW];
+#pragma unroll
+    for (int u = 0; u < CPW; ++u) acc[u] = T(0);
+    for (int k = 1; k <= ng; ++k) {
+      const T* G = Gs + (size_t)(k - 1) * MM;
+      const T* Z = ring + (size_t)slot(c - k) * CH * RS + w * CPW;
+#pragma unroll 8
+      for (int j = 0; j < CH; ++j) {
+        const T gv = G[j * CH + lane];
+#pragma unroll
+        for (int v = 0; v < CPW / E; ++v) {
+          const V z4 = reinterpret_cast<const V*>(Z + j * RS)[v];
+          const T* pz = reinterpret_cast<const T*>(&z4);
+#pragma unroll
+          for (int e = 0; e < E; ++e) acc[v * E + e] -= gv * pz[e];
+        }
+      }
+    }
+    T* Zc = ring + (size_t)slot(c) * CH * RS + lane * RS + w * CPW;
+#pragma unroll
+    for (int v = 0; v < CPW / E; ++v) {
+      V x;
+      T* xe = reinterpret_cast<T*>(&x);
+#pragma unroll
+      for (int e = 0; e < E; ++e) xe[e] = acc[v * E + e];
+      reinterpret_cast<V*>(Zc)[v] = x;
+    }
+    // X_c to global, column-major over the segment's positions (lane = position: coalesced)
+    const int64_t pr = (int64_t)(c - c0) * CH + lane;
+#pragma unroll
+    for (int u = 0; u < CPW; ++u) {
+      const int qq = q0 + w * CPW + u;
+      if (qq < kh) Xb[(int64_t)qq * xm + pr] = acc[u];
+    }
+  }
+  __syncthreads();
+  // T_s: row a of the stored columns on the segment's last kh positions
+  T* To = Tout + ((int64_t)b * S + s) * kh * kh;
+  for (int e = tid; e < kh * CPB; e += NT) {
+    const int a = e / CPB, u = e % CPB;
+    const int qq = q0 + u;
+    if (qq < kh) {
+      const int pos = c1 * CH - kh + a;
+      To[(int64_t)a * kh + qq] = ring[slot(pos / CH) * CH * RS + (pos % CH) * RS + u];
+    }
+  }
+}
+
 template <typename T, int NG>
 cudaError_t seg_trans_ng(const T* M, const int64_t* cbase, int P, int S, int cpsmax, int kh, Dev d, T* tout,
                          T* xout, cudaStream_t s) {
@@ -399,11 +513,23 @@ cudaError_t launch_seg_trans(const T* M, const int64_t* cbase, int K, int P, int
                              T* xout, cudaStream_t s) {
   if (S < 2) return cudaSuccess;
   count_launches(1);
-  switch ((K + CH - 1) / CH) {
+  const int ng = (K + CH - 1) / CH;
+  switch (ng) {
     case 1: return seg_trans_ng<T, 1>(M, cbase, P, S, cpsmax, hist_width(K), d, tout, xout, s);
     case 2: return seg_trans_ng<T, 2>(M, cbase, P, S, cpsmax, hist_width(K), d, tout, xout, s);
     case 3: return seg_trans_ng<T, 3>(M, cbase, P, S, cpsmax, hist_width(K), d, tout, xout, s);
-    default: return seg_trans_ng<T, 4>(M, cbase, P, S, cpsmax, hist_width(K), d, tout, xout, s);
+    case 4: return seg_trans_ng<T, 4>(M, cbase, P, S, cpsmax, hist_width(K), d, tout, xout, s);
+    default: {
+      const size_t smem = seg_trans_wide_smem<T>(ng);
+      if (smem > kSmemPerBlock) return cudaErrorInvalidValue;
+      cudaError_t e = cudaFuncSetAttribute(k_seg_trans_wide<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)smem);
+      if (e != cudaSuccess) return e;
+      const int kh = hist_width(K);
+      k_seg_trans_wide<T><<<dim3((kh + kWideTile - 1) / kWideTile, S - 1, P), 256, smem, s>>>(
+          M, cbase, d, S, cpsmax, kh, ng, tout, xout);
+      return cudaGetLastError();
+    }
   }
 }
 

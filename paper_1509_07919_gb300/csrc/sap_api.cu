@@ -1070,7 +1070,13 @@ sap_status_t create_handle(const double* band_dev, int64_t N, int32_t K, const s
     // this part): one CTA per SM, segments of at least 32 chunks, at least 6
     // per block.  Never more than kMaxAutoSegments.  Any count is lowered to
     // keep max(ng, 2) chunks of 32 rows in every full segment; segmentation
-    // needs ng <= 4 couplings per chunk.
+    // needs the segmented sweep's ring of chunk matrices in shared memory
+    // (FP32 up to K = 288, 9 couplings per chunk; FP64 up to K = 128, 4).
+    // The automatic count stays at one segment above 4 couplings per chunk:
+    // there the segmented sweep's single preparation warp forms up to 9
+    // coupling products per chunk and the history correction streams X
+    // (measured: the 400 x 250 convection-diffusion step, K = 250, P = 32,
+    // 55.6 ms unsegmented, 121.4 ms with 6 segments).
     int min_nch = L.max_nch;
     for (int i = 0; i < L.P; ++i) min_nch = std::min(min_nch, (int)(L.ld[i] / 32));
     const int ngc = chunk_couplings(K);
@@ -1079,9 +1085,10 @@ sap_status_t create_handle(const double* band_dev, int64_t N, int32_t K, const s
       const bool f32 = opt.precision != SAP_FP64;
       S = std::min((f32 ? 2 : 1) * kSMs / L.P, min_nch / (f32 ? 16 : 32));
       S = S < (f32 ? 4 : 6) ? 1 : std::min(S, kMaxAutoSegments);
+      if (ngc > 4) S = 1;
     }
     S = std::min(S, std::max(1, min_nch / std::max(ngc, 2)));
-    if (ngc > 4) S = 1;
+    if (!seg_sweeps_fit(K, opt.precision == SAP_FP64)) S = 1;
     L.S = std::max(1, S);
   }
   int64_t *doff, *dfb, *dld, *dcb;

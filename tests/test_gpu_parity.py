@@ -596,3 +596,26 @@ def test_solve_pair_wide_tc_and_p1(sap, N, K, P, variant, prec):
     assert torch.equal(x, xs) and torch.equal(lam, ls)
     assert ix.iters == ix0.iters and il.iters == il0.iters
     assert ix.tc_update == int(prec == 2 and 64 <= K <= 192)
+
+
+@pytest.mark.parametrize("variant", [0, 1])
+@pytest.mark.parametrize("N,K,P", [(9000, 160, 3), (12000, 250, 4), (8000, 280, 2)])
+def test_segmented_sweeps_wide_bands(sap, variant, N, K, P):
+    """Segmented sweeps with more than 4 couplings per chunk (FP32 factors up
+    to K = 288): the transfer matrices and history responses of the wide
+    kernel (history columns in tiles of 32), the chain with its matrices read
+    from L2 where one exceeds shared memory (K = 250, 280), forward and
+    transposed applies against the oracle entry by entry, and a solve."""
+    band, xt, b = make(N, K, 1.0, 900 + K)
+    r = G.adjoint_seed(N, 900 + K)
+    zo = O.Sap(band, N, K, P, variant).apply(r)
+    zao = O.Sap(O.transpose_band(band, N, K), N, K, P, variant).apply(r)
+    for S in (2, 3, 6):
+        h = sap.sap_factor(dev(band), N, K, P=P, variant=variant, precision=1, segments=S)
+        z = host(sap.sap_apply_preconditioner(h, dev(r)))
+        assert maxerr(z, zo) <= 1e-4, (S, maxerr(z, zo))
+        za = host(sap.sap_apply_preconditioner(h, dev(r), transpose=True))
+        assert maxerr(za, zao) <= 1e-4, (S, "adjoint", maxerr(za, zao))
+        x, info, st = sap.sap_solve(h, dev(b))
+        assert st == sap.SAP_OK and info.relres <= 1e-10
+        assert info.segments == S

@@ -115,8 +115,8 @@ typedef struct {
                              block with one thread block; this is a GB300 addition
                              to fill the SMs when P is small.  Values that leave a
                              range shorter than ceil(K/32) chunks of 32 rows are
-                             lowered automatically; segmentation needs K <= 288
-                             with FP32 factors, K <= 128 with FP64 (1 above);
+                             lowered automatically; segmentation needs K <= 512
+                             with FP32 factors, K <= 256 with FP64 (1 above);
                              the automatic count uses it for K <= 128 only. */
     int32_t krylov;       /* sap_krylov_t: the outer iteration */
 } sap_options_t;

@@ -374,8 +374,10 @@ __device__ __forceinline__ SweepSh<T, YT> carve(unsigned char* base, const Sweep
 // true histories, k_seg_correct then adds X h.
 // ctop/cbot: SaP-C corrections of the right-hand side (forward sweeps of the
 // second block solve only).
-template <typename T, typename YT, typename OT, int MODE>
-__global__ void __launch_bounds__(NWS * 32)
+// PFD chunks of matrices in flight, NPW warps preparing the next chunk's w
+// (1 up to 4 couplings per chunk; 2 or 4 for the wider bands, as in k_block_solve).
+template <typename T, typename YT, typename OT, int MODE, int PFD = PF, int NPW = 1>
+__global__ void __launch_bounds__((NPW + 2) * 32)
 k_sweep(const T* __restrict__ Mall, const int64_t* __restrict__ cbase, int K, Dev d, const YT* __restrict__ yin,
         OT* __restrict__ out, T* __restrict__ tails, const double* __restrict__ ctop_all,
         const double* __restrict__ cbot_all, int P, int S, int* __restrict__ err, Gate gt) {
@@ -397,7 +399,7 @@ k_sweep(const T* __restrict__ Mall, const int64_t* __restrict__ cbase, int K, De
   const bool has_top = ctop_all && b > 0;
   const bool has_bot = cbot_all && b + 1 < P;
   bool failed = false;   // a barrier wait of this thread timed out
-  SweepSh<T, YT> sh = carve<T, YT>(smem_raw, g);
+  SweepSh<T, YT> sh = carve<T, YT, PFD, NPW>(smem_raw, g);
   if (threadIdx.x == 0) {
     for (int q = 0; q <= PF; ++q) mbar_init(&sh.bar[q], 1);
     mbar_fence_init();
@@ -408,7 +410,7 @@ k_sweep(const T* __restrict__ Mall, const int64_t* __restrict__ cbase, int K, De
   }
   T* tail = (tails && seg + 1 < S) ? tails + ((int64_t)b * S + seg) * KH : nullptr;
   unsigned ph = 0;
-  sweep<T, YT, OT, MODE>(sh, g, Mall + cbase[b], yin + s, has_top, has_bot, out + s, c0, c1 - c0, tail, ph,
+  sweep<T, YT, OT, MODE, PFD, NPW>(sh, g, Mall + cbase[b], yin + s, has_top, has_bot, out + s, c0, c1 - c0, tail, ph,
                          failed, err);
 }
 
@@ -811,13 +813,34 @@ constexpr int kRedStagedK = 96;
 template <typename T, typename YT, typename OT, int MODE>
 cudaError_t launch_sweep(const T* M, const T* Tm, const T* Xm, const Factors<T>& f, int K, int P, Dev d,
                          const YT* yin, OT* out, const double* ctop, const double* cbot, cudaStream_t s, Gate gt) {
-  const size_t smem = sweep_smem<T>(K);
-  auto kern = k_sweep<T, YT, OT, MODE>;
+  // up to 4 couplings per chunk one preparation warp and 4 chunks in flight;
+  // wider bands 2 (<= 7 couplings) or 4 preparation warps, 4 chunks in flight
+  // where the ring fits, else 2
+  const int ng = n_couplings(K);
+  size_t smem;
+  int threads;
+  void (*kern)(const T*, const int64_t*, int, Dev, const YT*, OT*, T*, const double*, const double*, int, int, int*,
+               Gate);
+  if (ng <= 4) {
+    smem = sweep_smem<T>(K);
+    kern = k_sweep<T, YT, OT, MODE>;
+    threads = NWS * 32;
+  } else if (ng <= 7) {
+    const bool deep = sweep_smem<T, PF, 2>(K) <= kSmemPerBlock;
+    smem = deep ? sweep_smem<T, PF, 2>(K) : sweep_smem<T, 2, 2>(K);
+    kern = deep ? k_sweep<T, YT, OT, MODE, PF, 2> : k_sweep<T, YT, OT, MODE, 2, 2>;
+    threads = 4 * 32;
+  } else {
+    const bool deep = sweep_smem<T, PF, 4>(K) <= kSmemPerBlock;
+    smem = deep ? sweep_smem<T, PF, 4>(K) : sweep_smem<T, 2, 4>(K);
+    kern = deep ? k_sweep<T, YT, OT, MODE, PF, 4> : k_sweep<T, YT, OT, MODE, 2, 4>;
+    threads = 6 * 32;
+  }
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int S = f.S;
   count_launches(1);
-  kern<<<dim3(S, P), NWS * 32, smem, s>>>(M, f.cbase, K, d, yin, out, f.tails, ctop, cbot, P, S, f.err, gt);
+  kern<<<dim3(S, P), threads, smem, s>>>(M, f.cbase, K, d, yin, out, f.tails, ctop, cbot, P, S, f.err, gt);
   e = cudaGetLastError();
   if (e != cudaSuccess || S == 1) return e;
   const int tiles = (f.cpsmax * CHK + kCorrThreads - 1) / kCorrThreads;
@@ -902,7 +925,14 @@ cudaError_t launch_block_solve(const Factors<T>& f, int K, int P, Dev d, const d
 // the unsegmented sweep's smallest ring (two chunks ahead, four prepare warps): the limit on K
 size_t sweep_smem_bytes(int K, bool fp64) { return fp64 ? sweep_smem<double, 2, 4>(K) : sweep_smem<float, 2, 4>(K); }
 bool seg_sweeps_fit(int K, bool fp64) {
-  return (fp64 ? sweep_smem<double>(K) : sweep_smem<float>(K)) <= kSmemPerBlock;
+  const int ng = n_couplings(K);
+  if (ng <= 4) return (fp64 ? sweep_smem<double>(K) : sweep_smem<float>(K)) <= kSmemPerBlock;
+  // the shallow ring of the launched shape, and the wide transfer kernel's tiles
+  const size_t ts = fp64 ? 8 : 4;
+  const size_t sw = ng <= 7 ? (fp64 ? sweep_smem<double, 2, 2>(K) : sweep_smem<float, 2, 2>(K))
+                            : (fp64 ? sweep_smem<double, 2, 4>(K) : sweep_smem<float, 2, 4>(K));
+  const size_t tr = (2 * (size_t)ng * CHK * CHK + (size_t)(ng + 1) * CHK * (32 + 16 / ts)) * ts;
+  return sw <= kSmemPerBlock && tr <= kSmemPerBlock;
 }
 int chunk_couplings(int K) { return n_couplings(K); }
 

@@ -1071,12 +1071,13 @@ sap_status_t create_handle(const double* band_dev, int64_t N, int32_t K, const s
     // per block.  Never more than kMaxAutoSegments.  Any count is lowered to
     // keep max(ng, 2) chunks of 32 rows in every full segment; segmentation
     // needs the segmented sweep's ring of chunk matrices in shared memory
-    // (FP32 up to K = 288, 9 couplings per chunk; FP64 up to K = 128, 4).
+    // (FP32 up to K = 512, FP64 up to K = 256).
     // The automatic count stays at one segment above 4 couplings per chunk:
-    // there the segmented sweep's single preparation warp forms up to 9
-    // coupling products per chunk and the history correction streams X
-    // (measured: the 400 x 250 convection-diffusion step, K = 250, P = 32,
-    // 55.6 ms unsegmented, 121.4 ms with 6 segments).
+    // there the serial chain of KH x KH transfer matrices (254 KB each at
+    // K = 250) and the correction's stream of X outweigh the shorter chunk
+    // chains (measured: the 400 x 250 convection-diffusion refactor + pair
+    // solve, K = 250, P = 32, 59.6 ms unsegmented, 78.2 / 127.2 / 163.3 ms
+    // with 3 / 6 / 9 segments).
     int min_nch = L.max_nch;
     for (int i = 0; i < L.P; ++i) min_nch = std::min(min_nch, (int)(L.ld[i] / 32));
     const int ngc = chunk_couplings(K);

@@ -18,7 +18,7 @@ size_t sweep_smem_bytes(int K, bool fp64);
 // Coupling matrices per chunk of the blocked sweeps: ceil(K / 32).
 int chunk_couplings(int K);
 // The segmented sweeps' kernel (its ring of chunk matrices) fits in shared
-// memory for half-bandwidth K (FP32 up to K = 288, FP64 up to K = 128).
+// memory for half-bandwidth K (FP32 up to K = 512, FP64 up to K = 256).
 bool seg_sweeps_fit(int K, bool fp64);
 // tc: the tensor-core (BF16 operand, FP32 accumulate) trailing update of the
 // FP32 factorisation, used from K = kTcMinK on (precision SAP_FP32_BF16TU).

@@ -599,23 +599,27 @@ def test_solve_pair_wide_tc_and_p1(sap, N, K, P, variant, prec):
 
 
 @pytest.mark.parametrize("variant", [0, 1])
-@pytest.mark.parametrize("N,K,P", [(9000, 160, 3), (12000, 250, 4), (8000, 280, 2)])
-def test_segmented_sweeps_wide_bands(sap, variant, N, K, P):
-    """Segmented sweeps with more than 4 couplings per chunk (FP32 factors up
-    to K = 288): the transfer matrices and history responses of the wide
-    kernel (history columns in tiles of 32), the chain with its matrices read
-    from L2 where one exceeds shared memory (K = 250, 280), forward and
-    transposed applies against the oracle entry by entry, and a solve."""
+@pytest.mark.parametrize("prec,N,K,P", [(1, 9000, 160, 3), (1, 12000, 250, 4), (1, 8000, 280, 2),
+                                        (1, 12000, 400, 4), (0, 12000, 250, 4)])
+def test_segmented_sweeps_wide_bands(sap, variant, prec, N, K, P):
+    """Segmented sweeps with more than 4 couplings per chunk (on request; FP32
+    up to K = 512, FP64 up to 256): the sweep kernel with 2 or 4 preparation
+    warps, the transfer matrices and history responses of the wide kernel
+    (history columns in tiles of 32), the chain with its matrices read from L2
+    where one exceeds shared memory (K >= 250) and histories longer than its
+    thread count (K = 280, 400), forward and transposed applies against the
+    oracle entry by entry, and a solve."""
     band, xt, b = make(N, K, 1.0, 900 + K)
     r = G.adjoint_seed(N, 900 + K)
     zo = O.Sap(band, N, K, P, variant).apply(r)
     zao = O.Sap(O.transpose_band(band, N, K), N, K, P, variant).apply(r)
+    tol = 1e-11 if prec == 0 else 1e-4
     for S in (2, 3, 6):
-        h = sap.sap_factor(dev(band), N, K, P=P, variant=variant, precision=1, segments=S)
+        h = sap.sap_factor(dev(band), N, K, P=P, variant=variant, precision=prec, segments=S)
         z = host(sap.sap_apply_preconditioner(h, dev(r)))
-        assert maxerr(z, zo) <= 1e-4, (S, maxerr(z, zo))
+        assert maxerr(z, zo) <= tol, (S, maxerr(z, zo))
         za = host(sap.sap_apply_preconditioner(h, dev(r), transpose=True))
-        assert maxerr(za, zao) <= 1e-4, (S, "adjoint", maxerr(za, zao))
+        assert maxerr(za, zao) <= tol, (S, "adjoint", maxerr(za, zao))
         x, info, st = sap.sap_solve(h, dev(b))
         assert st == sap.SAP_OK and info.relres <= 1e-10
         assert info.segments == S

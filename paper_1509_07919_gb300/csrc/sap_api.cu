@@ -1374,8 +1374,21 @@ struct Blocks : SolverBase {
   cudaEvent_t evfork_t = nullptr;
   std::vector<cudaStream_t> tst;
   std::vector<cudaEvent_t> tev;
+  // the factorisation's launches (some 250 over the blocks' streams) captured
+  // once as a graph and replayed by later factorisations, on an internal stream
+  // joined to the caller's by events
+  int nfactor = 0;
+  cudaGraphExec_t fexec = nullptr;
+  bool fgraph_failed = false;
+  long long flaunches = 0;
+  cudaStream_t fks = nullptr;
+  cudaEvent_t evin = nullptr, evout = nullptr;
   Blocks(sap_handle* hh, const int32_t* p, cudaStream_t s) : h(hh), perm_src(p), cs(s) {}
   ~Blocks() override {
+    if (fexec) cudaGraphExecDestroy(fexec);
+    if (fks) cudaStreamDestroy(fks);
+    if (evin) cudaEventDestroy(evin);
+    if (evout) cudaEventDestroy(evout);
     if (evfork) cudaEventDestroy(evfork);
     if (evfork_t) cudaEventDestroy(evfork_t);
     for (cudaStream_t x : tst)
@@ -1529,10 +1542,67 @@ struct Blocks : SolverBase {
     return SAP_OK;
   }
 
+  // a block has transposed sweep data: its factorisation then rebuilds them in
+  // the background, a branch the factorisation's graph cannot hold
+  bool blocks_transposed() const {
+    for (const auto& q : sub) {
+      auto* sv = dynamic_cast<Solver<T>*>(q->impl.get());
+      if (!sv || sv->f.Mutf) return true;
+    }
+    return false;
+  }
+  void capture_factor() {
+    const long long l0 = launches_so_far();
+    cudaGraph_t g = nullptr;
+    bool ok = true;
+    if (!fks) {
+      ok = cudaStreamCreateWithFlags(&fks, cudaStreamNonBlocking) == cudaSuccess &&
+           cudaEventCreateWithFlags(&evin, cudaEventDisableTiming) == cudaSuccess &&
+           cudaEventCreateWithFlags(&evout, cudaEventDisableTiming) == cudaSuccess;
+    }
+    ok = ok && cudaStreamBeginCapture(fks, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    const sap_status_t st = ok ? factor_seq(fks) : SAP_ERR_CUDA;
+    if (ok) ok = cudaStreamEndCapture(fks, &g) == cudaSuccess && st == SAP_OK && g;
+    if (ok) ok = cudaGraphInstantiate(&fexec, g, 0) == cudaSuccess;
+    if (g) cudaGraphDestroy(g);
+    if (!ok) {
+      if (fexec) cudaGraphExecDestroy(fexec);
+      fexec = nullptr;
+      fgraph_failed = true;
+      cudaGetLastError();
+    }
+    flaunches = launches_so_far() - l0;
+    count_launches(-(int)flaunches);     // captured, not run
+  }
   sap_status_t factor(cudaStream_t s) override {
-    const Layout& L = h->L;
     adjoint_ready = false;               // rebuilt on the next transposed use
-    CK(cudaEventRecord(h->evp[0], s));
+    // from the second factorisation on (the first creates the blocks' streams
+    // and events) one graph launch, unless a block has transposed data
+    if (++nfactor >= 2 && !fgraph_failed && !blocks_transposed()) {
+      if (!fexec) capture_factor();
+      if (fexec) {
+        CK(cudaEventRecord(evin, s));
+        CK(cudaStreamWaitEvent(fks, evin, 0));
+        CK(cudaGraphLaunch(fexec, fks));
+        count_launches((int)flaunches);
+        CK(cudaEventRecord(evout, fks));
+        CK(cudaStreamWaitEvent(s, evout, 0));
+        return SAP_OK;
+      }
+    }
+    return factor_seq(s);
+  }
+  // the handle's phase events: inside a capture a record node of their own
+  // (a plain record there only marks a fork or join), so that a replay sets them
+  static cudaError_t rec(cudaEvent_t e, cudaStream_t s) {
+    cudaStreamCaptureStatus cst = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cst) == cudaSuccess && cst == cudaStreamCaptureStatusActive)
+      return cudaEventRecordWithFlags(e, s, cudaEventRecordExternal);
+    return cudaEventRecord(e, s);
+  }
+  sap_status_t factor_seq(cudaStream_t s) {
+    const Layout& L = h->L;
+    CK(rec(h->evp[0], s));
     CK(launch_absmax(h->band, L.N, L.K, h->absmax, s));
     CK(cudaMemsetAsync(gerr, 0, sizeof(int), s));
     CK(launch_block_gather(h->band, m, hb, hb_elems, gerr, s));
@@ -1543,9 +1613,9 @@ struct Blocks : SolverBase {
       CK(cudaEventRecord(q->evj, q->ks));
       CK(cudaStreamWaitEvent(s, q->evj, 0));
     }
-    CK(cudaEventRecord(h->ev_lu[0], s));
+    CK(rec(h->ev_lu[0], s));
     CK(launch_factor_lu_items<T>(items, nitems, Kbmax, counter, wlu, tcu, f.err, s));
-    CK(cudaEventRecord(h->ev_lu[1], s));
+    CK(rec(h->ev_lu[1], s));
     CK(cudaEventRecord(evfork, s));
     for (auto& q : sub) {
       CK(cudaStreamWaitEvent(q->ks, evfork, 0));
@@ -1553,18 +1623,18 @@ struct Blocks : SolverBase {
       CK(cudaEventRecord(q->evj, q->ks));
       CK(cudaStreamWaitEvent(s, q->evj, 0));
     }
-    CK(cudaEventRecord(h->evp[1], s));
-    CK(cudaEventRecord(h->evu[0], s));    // no UL factorisation: an empty T_UL bracket
-    CK(cudaEventRecord(h->evu[1], s));
-    CK(cudaEventRecord(h->evp[2], s));
+    CK(rec(h->evp[1], s));
+    CK(rec(h->evu[0], s));    // no UL factorisation: an empty T_UL bracket
+    CK(rec(h->evu[1], s));
+    CK(rec(h->evp[2], s));
     if (coupled()) {
       CK(launch_full_spikes<T>(h->band, m, ngmax, dMf, dMb, dng, dldp, spk, dsbase, f.V, f.Wt, false, s));
-      CK(cudaEventRecord(h->ev_rd, s));
+      CK(rec(h->ev_rd, s));
       CK(launch_reduced<T>(f.V, f.Wt, L.K, L.P - 1, f.R, f.R0, f.piv, h->singular, gws, s));
     } else {
-      CK(cudaEventRecord(h->ev_rd, s));
+      CK(rec(h->ev_rd, s));
     }
-    CK(cudaEventRecord(h->evp[3], s));
+    CK(rec(h->evp[3], s));
     return SAP_OK;
   }
   sap_status_t factor_pre(cudaStream_t) override { return SAP_ERR_NOT_IMPLEMENTED; }

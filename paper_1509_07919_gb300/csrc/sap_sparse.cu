@@ -14,6 +14,8 @@
 #include <limits>
 #include <queue>
 #include <vector>
+#include <atomic>
+#include <thread>
 #include "sap_sparse.h"
 #include "sap_blocks.h"
 #include "sap_internal.cuh"
@@ -500,13 +502,16 @@ extern "C" sap_status_t sap_block_cm_reorder(const double* band_dev, int64_t N, 
   CKS(cudaStreamSynchronize(stream));
   // the partition of sap_factor: the first N mod P blocks have one row more
   const int64_t q = N / P, pr = N - (int64_t)P * q;
-  int64_t s = 0;
-  std::vector<int64_t> nb_ptr;
-  std::vector<int32_t> nb, p;
-  for (int b = 0; b < P; ++b) {
-    const int64_t n = q + (b < pr ? 1 : 0);
-    nb_ptr.assign((size_t)(n + 1), 0);
-    nb.clear();
+  std::vector<int64_t> off((size_t)P + 1, 0);
+  for (int b = 0; b < P; ++b) off[(size_t)b + 1] = off[(size_t)b] + q + (b < pr ? 1 : 0);
+  std::vector<int32_t> Kb((size_t)P, 0);
+  // one block's pattern of A_b + A_b^T and its CM order; blocks are independent
+  // (the paper runs this stage in parallel for every A_i), each worker writes
+  // only its own blocks' slices
+  auto one_block = [&](int b) {
+    const int64_t s = off[(size_t)b], n = off[(size_t)b + 1] - s;
+    std::vector<int64_t> nb_ptr((size_t)(n + 1), 0);
+    std::vector<int32_t> nb, p;
     for (int64_t a = 0; a < n; ++a) {
       const int64_t g = s + a;
       for (int64_t dq = -K; dq <= K; ++dq) {     // neighbours in ascending order
@@ -519,14 +524,35 @@ extern "C" sap_status_t sap_block_cm_reorder(const double* band_dev, int64_t N, 
       nb_ptr[(size_t)(a + 1)] = (int64_t)nb.size();
     }
     cm_order(n, nb_ptr, nb, p);
-    int64_t Kb = 0;
+    int64_t kb = 0;
     for (int64_t a = 0; a < n; ++a)
       for (int64_t e = nb_ptr[(size_t)a]; e < nb_ptr[(size_t)(a + 1)]; ++e)
-        Kb = std::max<int64_t>(Kb, std::llabs((int64_t)p[(size_t)a] - p[(size_t)nb[(size_t)e]]));
-    if (Ki_host) Ki_host[b] = (int32_t)Kb;
+        kb = std::max<int64_t>(kb, std::llabs((int64_t)p[(size_t)a] - p[(size_t)nb[(size_t)e]]));
+    Kb[(size_t)b] = (int32_t)kb;
     std::copy(p.begin(), p.end(), perm_all.begin() + s);
-    s += n;
+  };
+  const int nthreads = (int)std::max(1u, std::min<unsigned>((unsigned)P, std::min(16u, std::thread::hardware_concurrency())));
+  std::atomic<int> next{0}, failed{0};
+  auto worker = [&]() {
+    for (int b = next++; b < P; b = next++) {
+      try {
+        one_block(b);
+      } catch (...) {          // an allocation failed: no exception may leave a thread
+        failed = 1;
+      }
+    }
+  };
+  std::vector<std::thread> pool;
+  try {
+    for (int t = 1; t < nthreads; ++t) pool.emplace_back(worker);
+  } catch (...) {
+    // no more threads: the calling thread does the rest
   }
+  worker();
+  for (auto& t : pool) t.join();
+  if (failed) return SAP_ERR_OOM;
+  if (Ki_host)
+    for (int b = 0; b < P; ++b) Ki_host[b] = Kb[(size_t)b];
   CKS(cudaMemcpyAsync(perm_dev, perm_all.data(), (size_t)N * sizeof(int32_t), cudaMemcpyHostToDevice, stream));
   CKS(cudaStreamSynchronize(stream));
   return SAP_OK;

@@ -35,8 +35,10 @@ extern "C" {
  *   perm_dev (out, N int32, device): the block permutations as above.
  *   Ki_host (out, P int32, host, optional): half-bandwidth of each Ahat_i,
  *     max |perm(a) - perm(b)| over its nonzeros (0 for a diagonal block).
- * The graph searches run on the host (as in the paper, Sec. 3.3): the band
- * is copied to the host once ((2K + 1) N doubles).
+ * The graph searches run on the host (as in the paper, Sec. 3.3), the blocks
+ * spread over up to 16 threads (independent, as the paper runs this stage in
+ * parallel for every A_i): the band is copied to the host once ((2K + 1) N
+ * doubles).
  * Errors: INVALID_ARG (sizes, null pointers, P < 1 or N < P), OOM, CUDA.
  * Synchronises `stream`. */
 SAP_API sap_status_t sap_block_cm_reorder(const double *band_dev, int64_t N, int32_t K, int32_t P,

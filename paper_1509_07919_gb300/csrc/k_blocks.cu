@@ -10,9 +10,10 @@
 // whose rows at the interface (old bottom K rows of block i, old top K rows
 // of block i+1) are the tips V^(b)_i, W^(t)_{i+1} of Eq. (2.5a).
 // Kernels: per-block bandwidth, the reordered blocks gathered from the band,
-// the permutations of vectors, the entire spikes (forward and backward banded
-// sweeps over L-row groups, the group's values in registers, Sec. 3.1), and
-// the two steps of the apply after the block solves: the truncated reduced
+// the permutations of vectors, the entire spikes (forward and backward sweeps
+// of every block in 32-row chunk steps with its chunk matrices, a 32 x 32
+// sub-block of the spike per step, Sec. 3.1), and the two steps of the apply
+// after the block solves: the truncated reduced
 // solve (Eq. (2.5b,c)) and z_i = g_i - Vhat_i x^(t)_{i+1} - What_i x^(b)_{i-1}
 // (= A_i^{-1}(r_i - [C_i x^(b)_{i-1}; 0] - [0; B_i x^(t)_{i+1}]) by linearity).
 #include <cuda_runtime.h>
